@@ -1,0 +1,249 @@
+"""CPU FP64 oracle of the spectral path tracer (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It is a plain, slow reference written
+from the paper (section 3 Eq. 1, section 4 Eqs. 2-3) and shares no code with the
+CUDA library.  ``build()`` compiles ``oracle.cpp`` with the host compiler into
+``oracle/_build/liboracle.so``; the binding below is argument marshalling only.
+
+Every function here is pinned by the ``-m "not gpu"`` tests against closed
+forms, invariants and brute force (Philox known-answer vectors, normal-incidence
+Fresnel, Brewster angle, lossless-plate 2R/(1+R), Beer-Lambert, the white
+furnace, the uniform sky, the sun-cone irradiance, brute-force intersection).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C++17, strict IEEE double, no fast-math)."""
+    src = os.path.join(_HERE, "oracle.cpp")
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+           "-fno-fast-math", src, "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _SceneDesc(C.Structure):
+    _fields_ = [
+        ("verts", C.POINTER(C.c_float)), ("n_verts", C.c_uint32),
+        ("tris", C.POINTER(C.c_uint32)), ("n_tris", C.c_uint32),
+        ("mat_id", C.POINTER(C.c_uint32)),
+        ("mat_type", C.POINTER(C.c_int32)), ("mat_thickness", C.POINTER(C.c_float)),
+        ("n_mat", C.c_uint32),
+        ("lambda_nm", C.POINTER(C.c_float)), ("n_bands", C.c_uint32),
+        ("sun_L", C.POINTER(C.c_float)), ("sun_dir", C.POINTER(C.c_float)),
+        ("sun_half_angle", C.c_float),
+        ("n_tab", C.POINTER(C.c_float)), ("k_tab", C.POINTER(C.c_float)),
+        ("rho_tab", C.POINTER(C.c_float)), ("le_tab", C.POINTER(C.c_float)),
+    ]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+            L.or_philox_batch.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32),
+                                          C.POINTER(C.c_uint32), C.c_uint64]
+            L.or_fresnel.restype = C.c_double
+            L.or_fresnel.argtypes = [C.c_double] * 3
+            L.or_slab.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
+            L.or_scene_create.restype = C.c_void_p
+            L.or_scene_create.argtypes = [C.POINTER(_SceneDesc), C.c_int]
+            L.or_scene_destroy.argtypes = [C.c_void_p]
+            L.or_scene_eps.restype = C.c_double
+            L.or_scene_eps.argtypes = [C.c_void_p]
+            L.or_closest_hits.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                          C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+            L.or_shadow_transmittance.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                                  C.POINTER(C.c_uint32), C.c_uint64,
+                                                  C.POINTER(C.c_double), C.POINTER(C.c_uint32)]
+            L.or_render.restype = C.c_int
+            L.or_render.argtypes = [C.c_void_p, C.POINTER(_Camera), C.c_uint32, C.c_uint32, C.c_uint32,
+                                    C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_uint32), C.c_uint64,
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint32),
+                                    C.c_int]
+            L.or_xyz.argtypes = [C.POINTER(C.c_double), C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                 C.POINTER(C.c_float), C.POINTER(C.c_double)]
+            L.or_hardware_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def philox4x32_10(key, ctr) -> np.ndarray:
+    k = np.asarray(key, np.uint32)
+    c = np.asarray(ctr, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_ptr(k, C.c_uint32), _ptr(c, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
+
+
+def philox_batch(key0: int, key1: int, ctr: np.ndarray) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    lib().or_philox_batch(key0, key1, _ptr(c, C.c_uint32), _ptr(out, C.c_uint32), c.shape[0])
+    return out
+
+
+def fresnel(cos_i: float, n: float, k: float) -> float:
+    return lib().or_fresnel(cos_i, n, k)
+
+
+def slab(cos_i, n, k, lambda_nm, d):
+    rs, ts = C.c_double(), C.c_double()
+    lib().or_slab(cos_i, n, k, lambda_nm, d, C.byref(rs), C.byref(ts))
+    return rs.value, ts.value
+
+
+def hardware_threads() -> int:
+    return int(lib().or_hardware_threads())
+
+
+def cameras_struct(cameras):
+    arr = (_Camera * len(cameras))()
+    for i, c in enumerate(cameras):
+        arr[i].pos[:] = list(map(float, c.pos))
+        arr[i].look[:] = list(map(float, c.look))
+        arr[i].up[:] = list(map(float, c.up))
+        arr[i].vfov_deg = float(c.vfov_deg)
+        arr[i].width = int(c.width)
+        arr[i].height = int(c.height)
+    return arr
+
+
+class OracleScene:
+    """FP64 reference scene built from a Scene/Spectra pair (duck-typed)."""
+
+    def __init__(self, scene, spectra, force_brute: bool = False):
+        self._keep = []
+
+        def f32(a):
+            a = np.ascontiguousarray(a, np.float32)
+            self._keep.append(a)
+            return _ptr(a, C.c_float)
+
+        def u32(a):
+            a = np.ascontiguousarray(a, np.uint32)
+            self._keep.append(a)
+            return _ptr(a, C.c_uint32)
+
+        mt = np.ascontiguousarray(scene.mat_type, np.int32)
+        self._keep.append(mt)
+        d = _SceneDesc()
+        d.verts = f32(scene.verts)
+        d.n_verts = scene.verts.shape[0]
+        d.tris = u32(scene.tris)
+        d.n_tris = scene.tris.shape[0]
+        d.mat_id = u32(scene.mat_id)
+        d.mat_type = _ptr(mt, C.c_int32)
+        d.mat_thickness = f32(scene.mat_thickness)
+        d.n_mat = mt.shape[0]
+        d.lambda_nm = f32(spectra.lambda_nm)
+        d.n_bands = spectra.lambda_nm.shape[0]
+        d.sun_L = f32(spectra.sun_L)
+        d.sun_dir = f32(spectra.sun_dir)
+        d.sun_half_angle = float(spectra.sun_half_angle)
+        d.n_tab = f32(spectra.n)
+        d.k_tab = f32(spectra.k)
+        d.rho_tab = f32(spectra.rho)
+        d.le_tab = f32(spectra.le)
+        self.n_bands = int(d.n_bands)
+        self.cmf_w = np.ascontiguousarray(spectra.cmf_w, np.float32)
+        self._h = lib().or_scene_create(C.byref(d), 1 if force_brute else 0)
+        self._keep = []  # the oracle copied everything
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_scene_destroy(h)
+            self._h = None
+
+    @property
+    def eps(self) -> float:
+        return lib().or_scene_eps(self._h)
+
+    def closest_hits(self, o, d):
+        o = np.ascontiguousarray(o, np.float32)
+        d = np.ascontiguousarray(d, np.float32)
+        n = o.shape[0]
+        t = np.zeros(n, np.float64)
+        p = np.zeros(n, np.int64)
+        lib().or_closest_hits(self._h, _ptr(o, C.c_float), _ptr(d, C.c_float), n,
+                              _ptr(t, C.c_double), _ptr(p, C.c_int64))
+        return t, p
+
+    def shadow_transmittance(self, o, d, band):
+        o = np.ascontiguousarray(o, np.float32)
+        d = np.ascontiguousarray(d, np.float32)
+        n = o.shape[0]
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(band, np.uint32), (n,)))
+        T = np.zeros(n, np.float64)
+        g = np.zeros(n, np.uint32)
+        lib().or_shadow_transmittance(self._h, _ptr(o, C.c_float), _ptr(d, C.c_float),
+                                      _ptr(b, C.c_uint32), n, _ptr(T, C.c_double), _ptr(g, C.c_uint32))
+        return T, g
+
+    def render(self, cameras, spp, depth, seed=0, band_first=0, band_count=None, pixels=None,
+               record_paths=False, n_threads=0):
+        """FP64 spectral sums over samples for the listed global pixels.
+
+        Returns dict(spectral_sum [n_pix, band_count], xyz [n_pix, 3], and with
+        record_paths path_L / path_sig [n_pix, spp, band_count])."""
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        n_all = sum(c.width * c.height for c in cameras)
+        pix = np.arange(n_all, dtype=np.uint32) if pixels is None else np.ascontiguousarray(pixels, np.uint32)
+        npx = pix.shape[0]
+        ssum = np.zeros((npx, band_count), np.float64)
+        pl = np.zeros((npx, spp, band_count), np.float64) if record_paths else None
+        ps = np.zeros((npx, spp, band_count), np.uint32) if record_paths else None
+        cams = cameras_struct(cameras)
+        rc = lib().or_render(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
+                             _ptr(pix, C.c_uint32), npx, _ptr(ssum, C.c_double),
+                             _ptr(pl, C.c_double) if pl is not None else None,
+                             _ptr(ps, C.c_uint32) if ps is not None else None, n_threads)
+        if rc != 0:
+            raise ValueError(f"or_render failed ({rc})")
+        out = {"spectral_sum": ssum, "xyz": xyz(ssum, band_first, spp, self.cmf_w)}
+        if record_paths:
+            out["path_L"] = pl
+            out["path_sig"] = ps
+        return out
+
+
+def xyz(spectral_sum, band_first, spp, cmf_w) -> np.ndarray:
+    s = np.ascontiguousarray(spectral_sum, np.float64)
+    npx, bc = s.shape
+    w = np.ascontiguousarray(cmf_w, np.float32)
+    out = np.zeros((npx, 3), np.float64)
+    lib().or_xyz(_ptr(s, C.c_double), npx, band_first, bc, spp, _ptr(w, C.c_float), _ptr(out, C.c_double))
+    return out

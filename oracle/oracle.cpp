@@ -1,0 +1,638 @@
+// CPU FP64 oracle for the spectral path tracer.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+// reference that the CUDA library is checked against.  Only the tests, the
+// smoke check and the bench's CPU-baseline leg load it.  It shares no code
+// with the CUDA library: its own Philox, its own intersection structures
+// (brute force, or a median-split BVH), its own Fresnel/slab/sampling code.
+//
+// What it computes (paper: section 3 Eq. 1 complex index; section 4 Eq. 2 the
+// reflection integral and Eq. 3 the sum over directional sources; section 3
+// the sun as a plane-wave source; section 6 colorimetry), estimated by Monte
+// Carlo path tracing with one wavelength band per path:
+//
+//   for each (pixel, sample s, band b):
+//     camera ray through the pixel jittered by Philox uniforms
+//     for vertex k = 1..depth:
+//       closest hit; on a miss add T*L_sun if the previous vertex was the
+//         camera or a mirror-like event and the direction is inside the cone
+//       Lambertian: next-event estimate towards the sun cone (Eq. 3 with the
+//         sun as the one directional source), through thin glass; then
+//         cosine sampling, T *= rho
+//       thin glass: reflect with probability R_s/(R_s+T_s), else pass
+//         straight through; T *= R_s + T_s
+//       conductor: mirror reflection, T *= R(theta, n, k)
+//   spectral sum over samples in sample order (FP64), then XYZ.
+//
+// Everything is double precision except the inputs, which arrive as float.
+
+#include <atomic>
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC 2011): ten rounds of two 32x32->64 multiplies with a Weyl
+// key schedule.
+// ---------------------------------------------------------------------------
+struct Ctr4 {
+  uint32_t w[4];
+};
+
+Ctr4 philox4x32_10(Ctr4 c, uint32_t k0, uint32_t k1) {
+  const uint64_t M0 = 0xD2511F53ull, M1 = 0xCD9E8D57ull;
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = M0 * c.w[0];
+    uint64_t p1 = M1 * c.w[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    Ctr4 n;
+    n.w[0] = hi1 ^ c.w[1] ^ k0;
+    n.w[1] = lo1;
+    n.w[2] = hi0 ^ c.w[3] ^ k1;
+    n.w[3] = lo0;
+    c = n;
+  }
+  return c;
+}
+
+// uniform in [0, 1) from the top 24 bits: exact in float and double
+double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+struct V3 {
+  double x, y, z;
+};
+V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+V3 normalize(V3 a) { return (1.0 / std::sqrt(dot(a, a))) * a; }
+double comp(V3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+
+// Orthonormal basis around a unit vector: Duff, Burgess, Christensen, Hery,
+// Kensler, Liani, Villemin, "Building an orthonormal basis, revisited",
+// JCGT 6(1), 2017.
+void onb(V3 n, V3* t1, V3* t2) {
+  double sign = std::copysign(1.0, n.z);
+  double a = -1.0 / (sign + n.z);
+  double b = n.x * n.y * a;
+  *t1 = {1.0 + sign * n.x * n.x * a, sign * b, -sign * n.x};
+  *t2 = {b, sign + n.y * n.y * a, -n.y};
+}
+
+// ---------------------------------------------------------------------------
+// optics (section 3, Eq. 1: n~ = n + i k)
+// ---------------------------------------------------------------------------
+
+// Unpolarised Fresnel reflectance from air (index 1) into a medium of complex
+// index eta = n + i k, for cos(theta_i) = c: the s and p amplitude ratios with
+// the complex cosine of the transmitted angle, averaged in intensity.
+double fresnel_complex(double c, double n, double k) {
+  std::complex<double> eta(n, k);
+  double s2 = 1.0 - c * c;
+  std::complex<double> ct = std::sqrt(1.0 - s2 / (eta * eta));
+  std::complex<double> rs = (c - eta * ct) / (c + eta * ct);
+  std::complex<double> rp = (eta * c - ct) / (eta * c + ct);
+  return 0.5 * (std::norm(rs) + std::norm(rp));
+}
+
+// Thin absorbing sheet of thickness d (metres): each face reflects R (complex
+// Fresnel), the interior attenuates by Beer-Lambert exp(-alpha d / cos_t),
+// alpha = 4 pi k / lambda, and the incoherent multiple reflections sum to
+//   R_s = R + (1-R)^2 R Ti^2 / (1 - R^2 Ti^2),  T_s = (1-R)^2 Ti / (1 - R^2 Ti^2).
+void slab(double c, double n, double k, double lambda_nm, double d, double* Rs, double* Ts) {
+  double R = fresnel_complex(c, n, k);
+  double sin2 = 1.0 - c * c;
+  double ct = std::sqrt(1.0 - sin2 / (n * n));
+  double alpha = 4.0 * M_PI * k / (lambda_nm * 1e-9);
+  double Ti = std::exp(-alpha * d / ct);
+  double den = 1.0 - R * R * Ti * Ti;
+  *Rs = R + (1.0 - R) * (1.0 - R) * R * Ti * Ti / den;
+  *Ts = (1.0 - R) * (1.0 - R) * Ti / den;
+}
+
+// ---------------------------------------------------------------------------
+// scene
+// ---------------------------------------------------------------------------
+enum { M_LAMBERT = 0, M_GLASS = 1, M_CONDUCTOR = 2, M_EMISSIVE = 3 };
+
+struct ONode {
+  double lo[3], hi[3];
+  int left = -1, right = -1;   // children, or -1 for a leaf
+  int first = 0, count = 0;    // leaf range in the permuted triangle list
+};
+
+struct OScene {
+  std::vector<V3> a, b, c;       // triangle vertices
+  std::vector<uint32_t> mat;     // material id per triangle
+  std::vector<int> mtype;
+  std::vector<double> mthick;
+  uint32_t n_mat = 0, B = 0;
+  std::vector<double> lam, sunL, ntab, ktab, rho, le;
+  V3 sun{0, 0, 1};
+  double cos_max = 1.0;
+  double eps = 0.0;              // origin offset: 1e-4 x scene diagonal
+  bool brute = true;
+  std::vector<ONode> nodes;
+  std::vector<uint32_t> perm;
+};
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, "Watertight ray/triangle
+// intersection", JCGT 2(1), 2013), in double precision.  An edge function of
+// exactly zero counts as inside.  Returns t > 0 or -1.
+struct RayPre {
+  V3 o, d;
+  int kx, ky, kz;
+  double Sx, Sy, Sz;
+};
+
+RayPre prep(V3 o, V3 d) {
+  RayPre r;
+  r.o = o;
+  r.d = d;
+  double ax = std::fabs(d.x), ay = std::fabs(d.y), az = std::fabs(d.z);
+  r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+  r.kx = (r.kz + 1) % 3;
+  r.ky = (r.kx + 1) % 3;
+  if (comp(d, r.kz) < 0.0) std::swap(r.kx, r.ky);
+  double dz = comp(d, r.kz);
+  r.Sx = comp(d, r.kx) / dz;
+  r.Sy = comp(d, r.ky) / dz;
+  r.Sz = 1.0 / dz;
+  return r;
+}
+
+double isect(const RayPre& r, V3 va, V3 vb, V3 vc) {
+  V3 A = va - r.o, Bv = vb - r.o, C = vc - r.o;
+  double Ax = comp(A, r.kx) - r.Sx * comp(A, r.kz);
+  double Ay = comp(A, r.ky) - r.Sy * comp(A, r.kz);
+  double Bx = comp(Bv, r.kx) - r.Sx * comp(Bv, r.kz);
+  double By = comp(Bv, r.ky) - r.Sy * comp(Bv, r.kz);
+  double Cx = comp(C, r.kx) - r.Sx * comp(C, r.kz);
+  double Cy = comp(C, r.ky) - r.Sy * comp(C, r.kz);
+  double U = Cx * By - Cy * Bx;
+  double V = Ax * Cy - Ay * Cx;
+  double W = Bx * Ay - By * Ax;
+  if ((U < 0 || V < 0 || W < 0) && (U > 0 || V > 0 || W > 0)) return -1.0;
+  double det = U + V + W;
+  if (det == 0.0) return -1.0;
+  double Az = r.Sz * comp(A, r.kz), Bz = r.Sz * comp(Bv, r.kz), Cz = r.Sz * comp(C, r.kz);
+  double T = U * Az + V * Bz + W * Cz;
+  double t = T / det;
+  return t > 0.0 ? t : -1.0;
+}
+
+bool box_hit(const ONode& nd, V3 o, V3 d, double tmax) {
+  double t0 = 0.0, t1 = tmax;
+  for (int i = 0; i < 3; ++i) {
+    double oi = comp(o, i), di = comp(d, i);
+    double pad = 1e-9 * (std::fabs(nd.lo[i]) + std::fabs(nd.hi[i])) + 1e-12;
+    double lo = nd.lo[i] - pad, hi = nd.hi[i] + pad;
+    if (di == 0.0) {
+      if (oi < lo || oi > hi) return false;
+      continue;
+    }
+    double ta = (lo - oi) / di, tb = (hi - oi) / di;
+    if (ta > tb) std::swap(ta, tb);
+    t0 = std::max(t0, ta);
+    t1 = std::min(t1, tb);
+    if (t0 > t1) return false;
+  }
+  return true;
+}
+
+// Median-split BVH over triangle centroids (longest centroid axis, leaves of
+// at most 4 triangles).  Only an accelerator for the brute-force definition.
+int build_node(OScene& S, int first, int count) {
+  ONode nd;
+  for (int i = 0; i < 3; ++i) {
+    nd.lo[i] = INFINITY;
+    nd.hi[i] = -INFINITY;
+  }
+  double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int j = first; j < first + count; ++j) {
+    uint32_t t = S.perm[j];
+    for (V3 v : {S.a[t], S.b[t], S.c[t]})
+      for (int i = 0; i < 3; ++i) {
+        nd.lo[i] = std::min(nd.lo[i], comp(v, i));
+        nd.hi[i] = std::max(nd.hi[i], comp(v, i));
+      }
+    V3 cen = (1.0 / 3.0) * (S.a[t] + S.b[t] + S.c[t]);
+    for (int i = 0; i < 3; ++i) {
+      clo[i] = std::min(clo[i], comp(cen, i));
+      chi[i] = std::max(chi[i], comp(cen, i));
+    }
+  }
+  int axis = 0;
+  for (int i = 1; i < 3; ++i)
+    if (chi[i] - clo[i] > chi[axis] - clo[axis]) axis = i;
+  int idx = (int)S.nodes.size();
+  S.nodes.push_back(nd);
+  if (count <= 4 || chi[axis] - clo[axis] <= 0.0) {
+    S.nodes[idx].first = first;
+    S.nodes[idx].count = count;
+    return idx;
+  }
+  int mid = first + count / 2;
+  auto key = [&](uint32_t t) { return comp(S.a[t] + S.b[t] + S.c[t], axis); };
+  std::nth_element(S.perm.begin() + first, S.perm.begin() + mid, S.perm.begin() + first + count,
+                   [&](uint32_t p, uint32_t q) { return key(p) < key(q) || (key(p) == key(q) && p < q); });
+  int l = build_node(S, first, mid - first);
+  int r = build_node(S, mid, first + count - mid);
+  S.nodes[idx].left = l;
+  S.nodes[idx].right = r;
+  return idx;
+}
+
+// Closest hit with t > 0; equal t resolved to the lower triangle id.
+bool closest(const OScene& S, V3 o, V3 d, double* t_out, uint32_t* prim_out) {
+  RayPre r = prep(o, d);
+  double best = INFINITY;
+  int64_t bid = -1;
+  auto test = [&](uint32_t t) {
+    double th = isect(r, S.a[t], S.b[t], S.c[t]);
+    if (th > 0.0 && (th < best || (th == best && (int64_t)t < bid))) {
+      best = th;
+      bid = t;
+    }
+  };
+  if (S.brute) {
+    for (uint32_t t = 0; t < S.a.size(); ++t) test(t);
+  } else {
+    std::vector<int> stack;
+    stack.reserve(128);
+    stack.push_back(0);
+    while (!stack.empty()) {
+      int ni = stack.back();
+      stack.pop_back();
+      const ONode& nd = S.nodes[ni];
+      if (!box_hit(nd, o, d, best)) continue;
+      if (nd.left < 0) {
+        for (int j = nd.first; j < nd.first + nd.count; ++j) test(S.perm[j]);
+      } else {
+        stack.push_back(nd.left);
+        stack.push_back(nd.right);
+      }
+    }
+  }
+  if (bid < 0) return false;
+  *t_out = best;
+  *prim_out = (uint32_t)bid;
+  return true;
+}
+
+// Transmittance of a ray to infinity: 0 if any opaque triangle is crossed,
+// else the product of the thin-glass T_s of every crossed sheet.  n_glass
+// returns the number of sheets crossed (or UINT32_MAX when blocked).
+double shadow_T(const OScene& S, V3 o, V3 d, uint32_t band, uint32_t* n_glass) {
+  RayPre r = prep(o, d);
+  double T = 1.0;
+  uint32_t ng = 0;
+  bool blocked = false;
+  auto visit = [&](uint32_t t) {
+    if (blocked) return;
+    double th = isect(r, S.a[t], S.b[t], S.c[t]);
+    if (!(th > 0.0)) return;
+    uint32_t m = S.mat[t];
+    if (S.mtype[m] != M_GLASS) {
+      blocked = true;
+      return;
+    }
+    V3 ng_ = cross(S.b[t] - S.a[t], S.c[t] - S.a[t]);
+    double c = std::fabs(dot(d, normalize(ng_)));
+    double Rs, Ts;
+    slab(c, S.ntab[m * S.B + band], S.ktab[m * S.B + band], S.lam[band], S.mthick[m], &Rs, &Ts);
+    T *= Ts;
+    ++ng;
+  };
+  if (S.brute) {
+    for (uint32_t t = 0; t < S.a.size() && !blocked; ++t) visit(t);
+  } else {
+    std::vector<int> stack;
+    stack.reserve(128);
+    stack.push_back(0);
+    while (!stack.empty() && !blocked) {
+      int ni = stack.back();
+      stack.pop_back();
+      const ONode& nd = S.nodes[ni];
+      if (!box_hit(nd, o, d, INFINITY)) continue;
+      if (nd.left < 0) {
+        for (int j = nd.first; j < nd.first + nd.count; ++j) visit(S.perm[j]);
+      } else {
+        stack.push_back(nd.left);
+        stack.push_back(nd.right);
+      }
+    }
+  }
+  if (blocked) {
+    *n_glass = 0xFFFFFFFFu;
+    return 0.0;
+  }
+  *n_glass = ng;
+  return T;
+}
+
+uint32_t mix(uint32_t h, uint32_t v) { return (h ^ v) * 16777619u; }
+
+struct OCam {
+  V3 pos, f, r, u;
+  double th, aspect;
+  uint32_t W, H;
+  uint64_t offset;
+};
+
+}  // namespace
+
+extern "C" {
+
+typedef struct {
+  const float* verts;
+  uint32_t n_verts;
+  const uint32_t* tris;
+  uint32_t n_tris;
+  const uint32_t* mat_id;
+  const int32_t* mat_type;
+  const float* mat_thickness;
+  uint32_t n_mat;
+  const float* lambda_nm;
+  uint32_t n_bands;
+  const float* sun_L;
+  const float* sun_dir;
+  float sun_half_angle;
+  const float* n_tab;
+  const float* k_tab;
+  const float* rho_tab;
+  const float* le_tab;
+} or_scene_desc;
+
+typedef struct {
+  float pos[3], look[3], up[3];
+  float vfov_deg;
+  uint32_t width, height;
+} or_camera;
+
+void or_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]) {
+  Ctr4 c{{ctr[0], ctr[1], ctr[2], ctr[3]}};
+  Ctr4 r = philox4x32_10(c, key[0], key[1]);
+  std::memcpy(out, r.w, 16);
+}
+
+void or_philox_batch(uint32_t key0, uint32_t key1, const uint32_t* ctr, uint32_t* out, uint64_t n) {
+  for (uint64_t i = 0; i < n; ++i) {
+    Ctr4 c{{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]}};
+    Ctr4 r = philox4x32_10(c, key0, key1);
+    std::memcpy(out + 4 * i, r.w, 16);
+  }
+}
+
+double or_fresnel(double cos_i, double n, double k) { return fresnel_complex(cos_i, n, k); }
+
+void or_slab(double cos_i, double n, double k, double lambda_nm, double d, double* Rs, double* Ts) {
+  slab(cos_i, n, k, lambda_nm, d, Rs, Ts);
+}
+
+void* or_scene_create(const or_scene_desc* sd, int force_brute) {
+  OScene* S = new OScene();
+  S->n_mat = sd->n_mat;
+  S->B = sd->n_bands;
+  uint32_t nt = sd->n_tris;
+  S->a.resize(nt);
+  S->b.resize(nt);
+  S->c.resize(nt);
+  S->mat.resize(nt);
+  auto vtx = [&](uint32_t i) {
+    return V3{(double)sd->verts[3 * i], (double)sd->verts[3 * i + 1], (double)sd->verts[3 * i + 2]};
+  };
+  V3 lo{INFINITY, INFINITY, INFINITY}, hi{-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t i = 0; i < sd->n_verts; ++i) {
+    V3 v = vtx(i);
+    lo = {std::min(lo.x, v.x), std::min(lo.y, v.y), std::min(lo.z, v.z)};
+    hi = {std::max(hi.x, v.x), std::max(hi.y, v.y), std::max(hi.z, v.z)};
+  }
+  S->eps = 1e-4 * std::sqrt(dot(hi - lo, hi - lo));
+  for (uint32_t t = 0; t < nt; ++t) {
+    S->a[t] = vtx(sd->tris[3 * t]);
+    S->b[t] = vtx(sd->tris[3 * t + 1]);
+    S->c[t] = vtx(sd->tris[3 * t + 2]);
+    S->mat[t] = sd->mat_id[t];
+  }
+  S->mtype.assign(sd->mat_type, sd->mat_type + sd->n_mat);
+  S->mthick.assign(sd->mat_thickness, sd->mat_thickness + sd->n_mat);
+  size_t MB = (size_t)sd->n_mat * sd->n_bands;
+  S->lam.assign(sd->lambda_nm, sd->lambda_nm + sd->n_bands);
+  S->sunL.assign(sd->sun_L, sd->sun_L + sd->n_bands);
+  S->ntab.assign(sd->n_tab, sd->n_tab + MB);
+  S->ktab.assign(sd->k_tab, sd->k_tab + MB);
+  S->rho.assign(sd->rho_tab, sd->rho_tab + MB);
+  S->le.assign(sd->le_tab, sd->le_tab + MB);
+  S->sun = normalize(V3{sd->sun_dir[0], sd->sun_dir[1], sd->sun_dir[2]});
+  S->cos_max = std::cos((double)sd->sun_half_angle);
+  S->brute = force_brute || nt <= 64;
+  if (!S->brute) {
+    S->perm.resize(nt);
+    std::iota(S->perm.begin(), S->perm.end(), 0u);
+    S->nodes.reserve(nt);
+    build_node(*S, 0, (int)nt);
+  }
+  return S;
+}
+
+void or_scene_destroy(void* s) { delete (OScene*)s; }
+
+double or_scene_eps(void* s) { return ((OScene*)s)->eps; }
+
+// Closest hits for n rays: t (or -1) and the triangle id (or -1).
+void or_closest_hits(void* s, const float* o, const float* d, uint64_t n, double* t_out, int64_t* prim_out) {
+  const OScene& S = *(OScene*)s;
+  for (uint64_t i = 0; i < n; ++i) {
+    V3 oo{o[3 * i], o[3 * i + 1], o[3 * i + 2]}, dd{d[3 * i], d[3 * i + 1], d[3 * i + 2]};
+    double t;
+    uint32_t p;
+    if (closest(S, oo, dd, &t, &p)) {
+      t_out[i] = t;
+      prim_out[i] = p;
+    } else {
+      t_out[i] = -1.0;
+      prim_out[i] = -1;
+    }
+  }
+}
+
+void or_shadow_transmittance(void* s, const float* o, const float* d, const uint32_t* band, uint64_t n,
+                             double* T_out, uint32_t* n_glass) {
+  const OScene& S = *(OScene*)s;
+  for (uint64_t i = 0; i < n; ++i) {
+    V3 oo{o[3 * i], o[3 * i + 1], o[3 * i + 2]}, dd{d[3 * i], d[3 * i + 1], d[3 * i + 2]};
+    T_out[i] = shadow_T(S, oo, dd, band[i], &n_glass[i]);
+  }
+}
+
+// Renders the listed global pixels.  spectral_sum[i*band_count + j] receives
+// the FP64 sum over samples (in sample order) of the path radiance of pixel
+// pixels[i], band band_first + j.  path_L / path_sig (optional) receive every
+// path's radiance and event signature, indexed [i][s][j].
+int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band_first,
+              uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed, const uint32_t* pixels,
+              uint64_t n_pixels, double* spectral_sum, double* path_L, uint32_t* path_sig,
+              int n_threads) {
+  const OScene& S = *(OScene*)scene;
+  if (band_first + band_count > S.B || depth == 0) return 1;
+  std::vector<OCam> oc(n_cams);
+  uint64_t off = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) {
+    const or_camera& c = cams[v];
+    V3 pos{c.pos[0], c.pos[1], c.pos[2]}, look{c.look[0], c.look[1], c.look[2]}, up{c.up[0], c.up[1], c.up[2]};
+    oc[v].pos = pos;
+    oc[v].f = normalize(look - pos);
+    oc[v].r = normalize(cross(oc[v].f, up));
+    oc[v].u = cross(oc[v].r, oc[v].f);
+    oc[v].th = std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
+    oc[v].aspect = (double)c.width / (double)c.height;
+    oc[v].W = c.width;
+    oc[v].H = c.height;
+    oc[v].offset = off;
+    off += (uint64_t)c.width * c.height;
+  }
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  // f / pdf for the sun cone: (rho / pi) * 2 pi (1 - cos_max) = rho * cone_w
+  const double cone_w = 2.0 * (1.0 - S.cos_max);
+
+  auto trace = [&](uint32_t pix, uint32_t s, uint32_t b, uint32_t* sig_out) -> double {
+    // locate the view
+    uint32_t v = 0;
+    while (v + 1 < n_cams && oc[v + 1].offset <= pix) ++v;
+    const OCam& C = oc[v];
+    uint32_t local = pix - (uint32_t)C.offset;
+    uint32_t x = local % C.W, y = local / C.W;
+    Ctr4 r0 = philox4x32_10(Ctr4{{pix, s, b, 0u}}, k0, k1);
+    double sx = (2.0 * ((double)x + u01(r0.w[0])) / C.W - 1.0) * C.th * C.aspect;
+    double sy = (1.0 - 2.0 * ((double)y + u01(r0.w[1])) / C.H) * C.th;
+    V3 d = normalize(C.f + sx * C.r + sy * C.u);
+    V3 o = C.pos;
+    double T = 1.0, L = 0.0;
+    bool covered = false;  // direct sun along this segment is already counted by NEE
+    uint32_t sig = 2166136261u;
+    for (uint32_t k = 1; k <= depth; ++k) {
+      double t;
+      uint32_t prim;
+      if (!closest(S, o, d, &t, &prim)) {
+        sig = mix(sig, 0xFFFFFFFFu);
+        if (!covered && dot(d, S.sun) >= S.cos_max) L += T * S.sunL[b];
+        break;
+      }
+      sig = mix(sig, prim);
+      V3 p = o + t * d;
+      V3 ng = normalize(cross(S.b[prim] - S.a[prim], S.c[prim] - S.a[prim]));
+      V3 n = dot(ng, d) < 0.0 ? ng : -1.0 * ng;
+      double cos_i = -dot(d, n);
+      uint32_t m = S.mat[prim];
+      size_t mb = (size_t)m * S.B + b;
+      int type = S.mtype[m];
+      Ctr4 r = philox4x32_10(Ctr4{{pix, s, b, 4u * k}}, k0, k1);
+      if (type == M_LAMBERT || type == M_EMISSIVE) {
+        if (type == M_EMISSIVE) L += T * S.le[mb];
+        // next-event estimate: direction uniform in the sun cone,
+        // pdf = 1 / (2 pi (1 - cos_max)); f = rho / pi
+        double ct = 1.0 - u01(r.w[0]) * (1.0 - S.cos_max);
+        double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+        double ph = 2.0 * M_PI * u01(r.w[1]);
+        V3 t1, t2;
+        onb(S.sun, &t1, &t2);
+        V3 w = (st * std::cos(ph)) * t1 + (st * std::sin(ph)) * t2 + ct * S.sun;
+        double c = dot(n, w);
+        if (c > 0.0) {
+          uint32_t ngl;
+          double Tr = shadow_T(S, p + S.eps * n, w, b, &ngl);
+          sig = mix(sig, ngl);
+          L += T * S.rho[mb] * c * S.sunL[b] * cone_w * Tr;
+        }
+        if (k == depth) break;
+        // cosine-weighted continuation: f cos / pdf = rho
+        double rr = std::sqrt(u01(r.w[2]));
+        double ph2 = 2.0 * M_PI * u01(r.w[3]);
+        double z = std::sqrt(std::max(0.0, 1.0 - u01(r.w[2])));
+        V3 b1, b2;
+        onb(n, &b1, &b2);
+        d = (rr * std::cos(ph2)) * b1 + (rr * std::sin(ph2)) * b2 + z * n;
+        o = p + S.eps * n;
+        T *= S.rho[mb];
+        covered = true;
+      } else if (type == M_GLASS) {
+        double Rs, Ts;
+        slab(cos_i, S.ntab[mb], S.ktab[mb], S.lam[b], S.mthick[m], &Rs, &Ts);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+        if (u01(r1.w[0]) < Rs / (Rs + Ts)) {
+          d = d - (2.0 * dot(d, n)) * n;
+          o = p + S.eps * n;
+          covered = false;
+        } else {
+          o = p - S.eps * n;
+        }
+        T *= Rs + Ts;
+      } else {  // conductor
+        double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
+        if (k == depth) break;
+        d = d - (2.0 * dot(d, n)) * n;
+        o = p + S.eps * n;
+        T *= R;
+        covered = false;
+      }
+    }
+    if (sig_out) *sig_out = sig;
+    return L;
+  };
+
+  std::atomic<uint64_t> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      uint64_t i = next.fetch_add(1);
+      if (i >= n_pixels) break;
+      uint32_t pix = pixels[i];
+      for (uint32_t j = 0; j < band_count; ++j) spectral_sum[i * band_count + j] = 0.0;
+      for (uint32_t s = 0; s < spp; ++s)
+        for (uint32_t j = 0; j < band_count; ++j) {
+          uint32_t sg = 0;
+          double L = trace(pix, s, band_first + j, path_sig ? &sg : nullptr);
+          spectral_sum[i * band_count + j] += L;
+          size_t pi = ((size_t)i * spp + s) * band_count + j;
+          if (path_L) path_L[pi] = L;
+          if (path_sig) path_sig[pi] = sg;
+        }
+    }
+  };
+  int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+// XYZ of spectral sums: xyz[i][c] = sum_j (spectral_sum[i][j] / spp) * cmf_w[band_first + j][c]
+void or_xyz(const double* spectral_sum, uint64_t n_pixels, uint32_t band_first, uint32_t band_count,
+            uint32_t spp, const float* cmf_w, double* xyz) {
+  for (uint64_t i = 0; i < n_pixels; ++i)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (uint32_t j = 0; j < band_count; ++j)
+        acc += spectral_sum[i * band_count + j] / spp * (double)cmf_w[(band_first + j) * 3 + c];
+      xyz[i * 3 + c] = acc;
+    }
+}
+
+int or_hardware_threads(void) { return (int)std::thread::hardware_concurrency(); }
+
+}  // extern "C"
