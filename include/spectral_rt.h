@@ -1,0 +1,191 @@
+/*
+ * spectral_rt.h - C ABI of the GB300 spectral path tracer.
+ *
+ * The library renders a triangle scene lit by the sun with one wavelength band
+ * per Monte Carlo path, the wavelength sub-domain of the paper's spectral
+ * decomposition reduced to a work key ("Spectral domain decomposition method
+ * for physically-based rendering of Royaumont abbey", title and section 5).
+ * What each path computes follows the paper's physics:
+ *   - materials carry a complex refractive index n(lambda) + i k(lambda)
+ *     (section 3, Eq. 1): thin glass sheets (complex Fresnel plus Beer-Lambert
+ *     absorption alpha = 4 pi k / lambda) and conductors;
+ *   - stone is Lambertian and the reflected radiance is the integral of
+ *     section 4, Eq. 2, estimated by cosine sampling;
+ *   - the sun is a directional source (section 3: a plane wave) with a cone of
+ *     half angle a; its direct contribution is the sum of section 4, Eq. 3,
+ *     estimated by next-event sampling of the cone through thin glass;
+ *   - the spectrum of each pixel is accumulated in FP64 and converted to CIE
+ *     XYZ (section 6: colorimetry from spectra).
+ *
+ * Conventions for every entry point:
+ *   - Status codes are returned; nothing throws or aborts across the ABI.
+ *     rt_last_error() gives a message for the last failure on a context.
+ *   - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
+ *     memory) on the context's device; they stay owned by the caller and are
+ *     used on the context's stream.  All other pointers are host memory,
+ *     read during the call and not retained.
+ *   - Work is enqueued on the context's stream.  Functions that return
+ *     results on the host, or a device status, synchronise that stream.
+ *   - Arrays are densely packed, row-major, in the element types given.
+ */
+#ifndef SPECTRAL_RT_H
+#define SPECTRAL_RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_ERR_ARG = 1,            /* invalid argument (null, zero size, out of range) */
+  RT_ERR_SCENE = 2,          /* scene rejected: NaN/inf vertex, bad index, degenerate triangle */
+  RT_ERR_OOM = 3,            /* device allocation failed */
+  RT_ERR_CUDA = 4,           /* a CUDA runtime call failed; the context is now unusable */
+  RT_ERR_QUEUE_OVERFLOW = 5, /* a device work queue exceeded its capacity (results invalid) */
+  RT_ERR_TIMEOUT = 6,        /* a device loop hit its iteration cap (results invalid) */
+  RT_ERR_STATE = 7,          /* call out of order (no scene / no spectra) or context poisoned */
+  RT_ERR_STACK = 8           /* BVH traversal stack exhausted (results invalid) */
+} rt_status;
+
+typedef enum {
+  RT_LAMBERT = 0,    /* diffuse stone, reflectance rho(lambda) */
+  RT_THIN_GLASS = 1, /* thin sheet: complex Fresnel faces + Beer-Lambert interior, thickness d */
+  RT_CONDUCTOR = 2,  /* metal: specular, complex Fresnel with n(lambda) + i k(lambda) */
+  RT_EMISSIVE = 3    /* test material: Lambertian rho plus emitted radiance le(lambda) */
+} rt_material_type;
+
+typedef enum {
+  RT_XYZ_BF16X3 = 0, /* tensor cores, BF16 operands split in three terms, FP32 accumulate */
+  RT_XYZ_BF16 = 1,   /* tensor cores, plain BF16 operands, FP32 accumulate */
+  RT_XYZ_FP64 = 2    /* CUDA cores, FP64 (reference mode) */
+} rt_xyz_mode;
+
+typedef struct rt_ctx rt_ctx;
+
+/* Pinhole camera: position, look-at point, up vector, vertical field of view
+ * in degrees, image size.  Pixel (x, y) has y growing downwards. */
+typedef struct {
+  float pos[3];
+  float look[3];
+  float up[3];
+  float vfov_deg;
+  uint32_t width;
+  uint32_t height;
+} rt_camera;
+
+typedef struct {
+  uint32_t wave_capacity;  /* paths in flight per wave; 0 = library default (2^23) */
+  uint32_t xyz_mode;       /* rt_xyz_mode */
+  uint32_t trace_block;    /* threads per block of the traversal kernels; 0 = 128 */
+  uint32_t ctas_per_sm;    /* persistent CTAs per SM for traversal; 0 = occupancy limit */
+  /* optional per-path records for parity checks: probe_map_dev[p] (uint32,
+   * one per global pixel) is the probe slot of pixel p or 0xFFFFFFFF; each
+   * probed path writes its radiance and event signature to
+   * probe_L_dev / probe_sig_dev[(slot * spp + s) * band_count + j]. */
+  const uint32_t* probe_map_dev;
+  float* probe_L_dev;
+  uint32_t* probe_sig_dev;
+  uint32_t use_graph;      /* 1: capture each wave shape once in a CUDA graph and replay it */
+  uint32_t reserved[7];
+} rt_render_opts;
+
+typedef struct {
+  uint64_t paths;          /* spectral paths traced */
+  uint64_t ext_rays;       /* closest-hit rays traced */
+  uint64_t shadow_rays;    /* sun rays traced */
+  uint64_t nodes_visited;  /* only with rt_set_counting(ctx, 1) */
+  uint64_t tris_tested;    /* only with rt_set_counting(ctx, 1) */
+  uint32_t waves;
+  uint32_t kernel_launches;
+  float ms_render;         /* device time of the path tracing (events) */
+  float ms_xyz;            /* device time of the XYZ contraction (events) */
+} rt_stats;
+
+/* Context on CUDA device `device`, enqueueing on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+rt_status rt_create(int device, void* cuda_stream, rt_ctx** out);
+void rt_destroy(rt_ctx* ctx);
+const char* rt_last_error(const rt_ctx* ctx);
+rt_status rt_set_stream(rt_ctx* ctx, void* cuda_stream);
+/* 1: traversal kernels count nodes visited and triangles tested (slower). */
+rt_status rt_set_counting(rt_ctx* ctx, int enable);
+
+/* Scene (the paper's first actor, section 1): n_verts float3 positions in
+ * metres, n_tris uint32 index triples, a material id per triangle, and per
+ * material its rt_material_type and thickness in metres (thin glass).
+ * Builds a binned-SAH BVH on the host, copies it to the device; the library
+ * owns its copy.  Replaces any previous scene. */
+rt_status rt_load_scene(rt_ctx* ctx, const float* verts, uint32_t n_verts, const uint32_t* tris,
+                        uint32_t n_tris, const uint32_t* mat_id, const int32_t* mat_type,
+                        const float* mat_thickness, uint32_t n_mat);
+
+/* Spectral tables (section 3): n_bands wavelengths in nm; sun radiance per
+ * band inside a cone of half angle sun_half_angle (radians) around the unit
+ * direction sun_dir (towards the sun); per material and band the index n, the
+ * extinction k (Eq. 1), the Lambertian reflectance rho and the emitted
+ * radiance le ([n_mat][n_bands] each; le may be NULL = 0); cmf_w[n_bands][3]
+ * the band weights of the XYZ contraction.  n_mat must match the scene. */
+rt_status rt_set_spectra(rt_ctx* ctx, const float* lambda_nm, uint32_t n_bands, const float* sun_L,
+                         const float sun_dir[3], float sun_half_angle, const float* n, const float* k,
+                         const float* rho, const float* le, const float* cmf_w);
+
+/* Renders n_cams views (the observer, section 1) with spp samples per pixel,
+ * bands [band_first, band_first + band_count) and at most `depth` surface
+ * interactions per path; Philox key = seed.  Global pixel ids run over the
+ * views in order.  Outputs (device, caller-owned, may be NULL):
+ *   spectral_dev [sum_v W_v H_v][band_count] FP64: sum over samples of the
+ *                path radiance (divide by spp for the mean);
+ *   xyz_dev      [sum_v W_v H_v][3] float: CIE XYZ of the band range (the
+ *                mean spectrum contracted with cmf_w), partial XYZ of
+ *                disjoint band ranges add up to the full XYZ.
+ * Synchronises the stream to read the device status word. */
+rt_status rt_render(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
+                    uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
+                    const rt_render_opts* opts, double* spectral_dev, float* xyz_dev, rt_stats* stats);
+
+/* Same as rt_render with HOST outputs: renders into library-owned device
+ * buffers and copies xyz (and spectral, if non-NULL) to the given host
+ * arrays before returning. */
+rt_status rt_render_host(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
+                         uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
+                         const rt_render_opts* opts, double* spectral_host, float* xyz_host,
+                         rt_stats* stats);
+
+/* ---- single steps of the path, for parity tests and tools ---------------- */
+
+/* Philox4x32-10 (Salmon et al., SC 2011) of n counters ctr_dev[n][4] with key
+ * (key0, key1) into out_dev[n][4]. */
+rt_status rt_philox(rt_ctx* ctx, const uint32_t* ctr_dev, uint32_t* out_dev, uint64_t n, uint32_t key0,
+                    uint32_t key1);
+
+/* Closest hit (t > 0) of n rays (o_dev, d_dev: [n][3] float) against the
+ * loaded scene: t_dev[n] (or -1) and prim_dev[n] (input triangle id or -1). */
+rt_status rt_trace_closest(rt_ctx* ctx, const float* o_dev, const float* d_dev, uint64_t n, float* t_dev,
+                           int32_t* prim_dev);
+
+/* Sun-ray transmittance of n rays to infinity: 0 if an opaque triangle is
+ * crossed, else the product of the thin-glass T_s (band band_dev[i]) of all
+ * crossed sheets; n_glass_dev[i] = sheets crossed or 0xFFFFFFFF if blocked. */
+rt_status rt_trace_shadow(rt_ctx* ctx, const float* o_dev, const float* d_dev, const uint32_t* band_dev,
+                          uint64_t n, float* T_dev, uint32_t* n_glass_dev);
+
+/* Complex Fresnel reflectance R(cos_i, n, k) from air (Eq. 1 index) and the
+ * thin-sheet R_s, T_s for n inputs; lambda_nm_dev and d_dev may be NULL for
+ * rt_fresnel (then Rs/Ts outputs are not written). */
+rt_status rt_optics_eval(rt_ctx* ctx, const float* cos_dev, const float* n_dev, const float* k_dev,
+                         const float* lambda_nm_dev, const float* d_dev, uint64_t count, float* R_dev,
+                         float* Rs_dev, float* Ts_dev);
+
+/* XYZ contraction of an FP64 spectral-sum image: xyz[p][c] = sum_j
+ * (spectral[p][j] / spp) * cmf_w[band_first + j][c], with mode rt_xyz_mode. */
+rt_status rt_xyz(rt_ctx* ctx, const double* spectral_dev, uint64_t n_pixels, uint32_t band_first,
+                 uint32_t band_count, uint32_t spp, uint32_t mode, float* xyz_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPECTRAL_RT_H */

@@ -1,0 +1,101 @@
+"""ctypes binding of libspectral_rt.so (argument marshalling only).
+
+Every step of the path runs in the library's CUDA kernels.  There is no
+fallback: if the library is missing or no CUDA device is present, loading
+raises.  PyTorch supplies device memory (tensors) and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libspectral_rt.so")
+
+RT_OK = 0
+STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_ARG", 2: "RT_ERR_SCENE", 3: "RT_ERR_OOM", 4: "RT_ERR_CUDA",
+                5: "RT_ERR_QUEUE_OVERFLOW", 6: "RT_ERR_TIMEOUT", 7: "RT_ERR_STATE", 8: "RT_ERR_STACK"}
+XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
+
+# every exported symbol of include/spectral_rt.h
+EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_load_scene",
+           "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest", "rt_trace_shadow",
+           "rt_optics_eval", "rt_xyz"]
+
+
+class RtError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_uint32), ("height", C.c_uint32)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("wave_capacity", C.c_uint32), ("xyz_mode", C.c_uint32), ("trace_block", C.c_uint32),
+                ("ctas_per_sm", C.c_uint32), ("probe_map_dev", C.c_void_p), ("probe_L_dev", C.c_void_p),
+                ("probe_sig_dev", C.c_void_p), ("use_graph", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("paths", C.c_uint64), ("ext_rays", C.c_uint64), ("shadow_rays", C.c_uint64),
+                ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64), ("waves", C.c_uint32),
+                ("kernel_launches", C.c_uint32), ("ms_render", C.c_float), ("ms_xyz", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run paper_1912_04000_gb300.build.build())")
+        L = C.CDLL(path)
+        vp, u32, u64, i32, f32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_float
+        L.rt_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
+        L.rt_destroy.argtypes = [vp]
+        L.rt_destroy.restype = None
+        L.rt_last_error.argtypes = [vp]
+        L.rt_last_error.restype = C.c_char_p
+        L.rt_set_stream.argtypes = [vp, vp]
+        L.rt_set_counting.argtypes = [vp, C.c_int]
+        L.rt_load_scene.argtypes = [vp, vp, u32, vp, u32, vp, vp, vp, u32]
+        L.rt_set_spectra.argtypes = [vp, vp, u32, vp, vp, f32, vp, vp, vp, vp, vp]
+        L.rt_render.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp, vp,
+                                C.POINTER(Stats)]
+        L.rt_render_host.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp,
+                                     vp, C.POINTER(Stats)]
+        L.rt_philox.argtypes = [vp, vp, vp, u64, u32, u32]
+        L.rt_trace_closest.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.rt_trace_shadow.argtypes = [vp, vp, vp, vp, u64, vp, vp]
+        L.rt_optics_eval.argtypes = [vp, vp, vp, vp, vp, vp, u64, vp, vp, vp]
+        L.rt_xyz.argtypes = [vp, vp, u64, u32, u32, u32, u32, vp]
+        for name in EXPORTS:
+            if name not in ("rt_destroy", "rt_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def cameras_struct(cameras):
+    arr = (Camera * len(cameras))()
+    for i, c in enumerate(cameras):
+        arr[i].pos[:] = [float(x) for x in c.pos]
+        arr[i].look[:] = [float(x) for x in c.look]
+        arr[i].up[:] = [float(x) for x in c.up]
+        arr[i].vfov_deg = float(c.vfov_deg)
+        arr[i].width = int(c.width)
+        arr[i].height = int(c.height)
+    return arr

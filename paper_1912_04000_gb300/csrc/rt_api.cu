@@ -1,0 +1,607 @@
+// C ABI of the spectral path tracer: context, scene and spectra upload,
+// render orchestration (wave loop), single-step entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/spectral_rt.h"
+#include "rt_bvh.h"
+#include "rt_internal.h"
+
+using namespace srt;
+
+struct rt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool poisoned = false;
+  bool counting = false;
+  int sms = 0;
+  int occ_trace = 0;
+  int occ_shade = 0;
+  // scene
+  float4* d_nodes = nullptr;
+  float4* d_tris = nullptr;
+  float4* d_nrm = nullptr;
+  uint32_t n_nodes = 0, n_tris = 0, n_mat = 0;
+  float eps = 0.0f;
+  bool has_scene = false;
+  // spectra
+  float4* d_mb = nullptr;
+  float* d_ad = nullptr;
+  int* d_mtype = nullptr;
+  float* d_sunL = nullptr;
+  float* d_cmfw = nullptr;
+  DevSpectra sp{};
+  std::vector<float> cmf_w;
+  std::vector<int> mtype;
+  std::vector<float> mthick;
+  bool has_spectra = false;
+  // per-render buffers
+  WaveBufs wb{};
+  uint32_t wave_alloc = 0;
+  DevCam* d_cams = nullptr;
+  DevCam* h_cams = nullptr;  // pinned staging
+  double* d_accum = nullptr;
+  size_t accum_cap = 0;
+  float* d_xyz = nullptr;
+  size_t xyz_cap = 0;
+  uint32_t* h_status = nullptr;  // pinned
+  Totals* h_tot = nullptr;       // pinned
+  uint32_t* d_status_aux = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+rt_status fail(rt_ctx* c, rt_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+      if (e_ != cudaErrorMemoryAllocation) (ctx)->poisoned = true;                             \
+      return e_ == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA;                       \
+    }                                                                                          \
+  } while (0)
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+rt_status check_ctx(rt_ctx* c) {
+  if (!c) return RT_ERR_ARG;
+  if (c->poisoned) return fail(c, RT_ERR_STATE, "context unusable after a CUDA error: " + c->err);
+  return RT_OK;
+}
+
+rt_status ensure_wave(rt_ctx* c, uint32_t cap) {
+  if (c->wave_alloc >= cap) return RT_OK;
+  WaveBufs& b = c->wb;
+  dfree(b.q[0]);
+  dfree(b.q[1]);
+  dfree(b.hit);
+  dfree(b.sq);
+  dfree(b.L);
+  dfree(b.sig);
+  c->wave_alloc = 0;
+  CUDA_TRY(c, cudaMalloc(&b.q[0], (size_t)cap * 2 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&b.q[1], (size_t)cap * 2 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&b.hit, (size_t)cap * sizeof(float2)));
+  CUDA_TRY(c, cudaMalloc(&b.sq, (size_t)cap * 2 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&b.L, (size_t)cap * sizeof(float)));
+  CUDA_TRY(c, cudaMalloc(&b.sig, (size_t)cap * sizeof(uint32_t)));
+  b.cap = cap;
+  c->wave_alloc = cap;
+  return RT_OK;
+}
+
+DevScene dev_scene(const rt_ctx* c) {
+  DevScene S;
+  S.nodes = c->d_nodes;
+  S.tris = c->d_tris;
+  S.nrm = c->d_nrm;
+  S.n_nodes = c->n_nodes;
+  S.n_tris = c->n_tris;
+  S.eps = c->eps;
+  return S;
+}
+
+rt_status status_to_rt(rt_ctx* c, uint32_t st) {
+  if (st == 0) return RT_OK;
+  if (st & ST_STACK) return fail(c, RT_ERR_STACK, "BVH traversal stack exhausted");
+  if (st & ST_ITER) return fail(c, RT_ERR_TIMEOUT, "device loop reached its iteration cap");
+  if (st & ST_QUEUE) return fail(c, RT_ERR_QUEUE_OVERFLOW, "device work queue overflow");
+  return fail(c, RT_ERR_CUDA, "device range check failed");
+}
+
+bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_create(int device, void* cuda_stream, rt_ctx** out) {
+  if (!out) return RT_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return RT_ERR_ARG;
+  rt_ctx* c = new rt_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return RT_ERR_CUDA;
+  }
+  c->sms = num_sms(device);
+  if (cudaMalloc(&c->wb.cnt, sizeof(Counters) * (kMaxDepth + 2)) != cudaSuccess ||
+      cudaMalloc(&c->wb.tot, sizeof(Totals)) != cudaSuccess ||
+      cudaMalloc(&c->wb.status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_cams, sizeof(DevCam) * kMaxCams) != cudaSuccess ||
+      cudaMallocHost(&c->h_cams, sizeof(DevCam) * kMaxCams) != cudaSuccess ||
+      cudaMallocHost(&c->h_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(&c->h_tot, sizeof(Totals)) != cudaSuccess) {
+    rt_destroy(c);
+    return RT_ERR_OOM;
+  }
+  for (auto& e : c->ev) cudaEventCreate(&e);
+  cudaMemset(c->wb.status, 0, sizeof(uint32_t));
+  *out = c;
+  return RT_OK;
+}
+
+void rt_destroy(rt_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  dfree(c->d_nodes);
+  dfree(c->d_tris);
+  dfree(c->d_nrm);
+  dfree(c->d_mb);
+  dfree(c->d_ad);
+  dfree(c->d_mtype);
+  dfree(c->d_sunL);
+  dfree(c->d_cmfw);
+  WaveBufs& b = c->wb;
+  dfree(b.q[0]);
+  dfree(b.q[1]);
+  dfree(b.hit);
+  dfree(b.sq);
+  dfree(b.L);
+  dfree(b.sig);
+  dfree(b.cnt);
+  dfree(b.tot);
+  dfree(b.status);
+  dfree(c->d_cams);
+  dfree(c->d_accum);
+  dfree(c->d_xyz);
+  if (c->h_cams) cudaFreeHost(c->h_cams);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_tot) cudaFreeHost(c->h_tot);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* rt_last_error(const rt_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+rt_status rt_set_stream(rt_ctx* c, void* s) {
+  if (rt_status e = check_ctx(c)) return e;
+  c->stream = (cudaStream_t)s;
+  return RT_OK;
+}
+
+rt_status rt_set_counting(rt_ctx* c, int enable) {
+  if (rt_status e = check_ctx(c)) return e;
+  c->counting = enable != 0;
+  return RT_OK;
+}
+
+rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const uint32_t* tris, uint32_t n_tris,
+                        const uint32_t* mat_id, const int32_t* mat_type, const float* mat_thickness, uint32_t n_mat) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!verts || !tris || !mat_id || !mat_type || !mat_thickness || n_verts == 0 || n_tris == 0 || n_mat == 0)
+    return fail(c, RT_ERR_ARG, "rt_load_scene: null array or zero size");
+  if (n_tris > (1u << 28)) return fail(c, RT_ERR_ARG, "rt_load_scene: more than 2^28 triangles");
+  for (uint32_t i = 0; i < n_verts; ++i)
+    if (!finite3(verts + 3 * (size_t)i)) return fail(c, RT_ERR_SCENE, "vertex " + std::to_string(i) + " not finite");
+  for (uint32_t m = 0; m < n_mat; ++m) {
+    if (mat_type[m] < 0 || mat_type[m] > 3) return fail(c, RT_ERR_SCENE, "material " + std::to_string(m) + ": bad type");
+    if (!(mat_thickness[m] >= 0.0f) || !std::isfinite(mat_thickness[m]))
+      return fail(c, RT_ERR_SCENE, "material " + std::to_string(m) + ": bad thickness");
+  }
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t i = 0; i < n_verts; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], (double)verts[3 * (size_t)i + a]);
+      hi[a] = std::max(hi[a], (double)verts[3 * (size_t)i + a]);
+    }
+  std::vector<float> nrm64(4 * (size_t)n_tris);
+  for (uint32_t t = 0; t < n_tris; ++t) {
+    for (int v = 0; v < 3; ++v)
+      if (tris[3 * (size_t)t + v] >= n_verts)
+        return fail(c, RT_ERR_SCENE, "triangle " + std::to_string(t) + ": vertex index out of range");
+    if (mat_id[t] >= n_mat) return fail(c, RT_ERR_SCENE, "triangle " + std::to_string(t) + ": material out of range");
+    const float* a = verts + 3 * (size_t)tris[3 * (size_t)t];
+    const float* b = verts + 3 * (size_t)tris[3 * (size_t)t + 1];
+    const float* cc = verts + 3 * (size_t)tris[3 * (size_t)t + 2];
+    const double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+    const double e2[3] = {(double)cc[0] - a[0], (double)cc[1] - a[1], (double)cc[2] - a[2]};
+    const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(len > 0.0)) return fail(c, RT_ERR_SCENE, "triangle " + std::to_string(t) + " is degenerate");
+    for (int a2 = 0; a2 < 3; ++a2) nrm64[4 * (size_t)t + a2] = (float)(n[a2] / len);
+  }
+  BvhOut bvh;
+  build_bvh(verts, tris, n_tris, bvh);
+  // leaf-ordered triangle and normal records
+  std::vector<float4> tr(3 * (size_t)n_tris), nr(n_tris);
+  for (uint32_t i = 0; i < n_tris; ++i) {
+    const uint32_t t = bvh.order[i];
+    const float* v[3];
+    for (int k = 0; k < 3; ++k) v[k] = verts + 3 * (size_t)tris[3 * (size_t)t + k];
+    uint32_t mid = mat_id[t];
+    float idf, matf, zero = 0.0f;
+    std::memcpy(&idf, &t, 4);
+    std::memcpy(&matf, &mid, 4);
+    tr[3 * (size_t)i] = make_float4(v[0][0], v[0][1], v[0][2], idf);
+    tr[3 * (size_t)i + 1] = make_float4(v[1][0], v[1][1], v[1][2], matf);
+    tr[3 * (size_t)i + 2] = make_float4(v[2][0], v[2][1], v[2][2], zero);
+    nr[i] = make_float4(nrm64[4 * (size_t)t], nrm64[4 * (size_t)t + 1], nrm64[4 * (size_t)t + 2], matf);
+  }
+  std::vector<float4> nd(2 * bvh.nodes.size());
+  for (size_t i = 0; i < bvh.nodes.size(); ++i) {
+    const BvhNode& b = bvh.nodes[i];
+    float rf, cf;
+    std::memcpy(&rf, &b.ref, 4);
+    std::memcpy(&cf, &b.count, 4);
+    nd[2 * i] = make_float4(b.lo[0], b.lo[1], b.lo[2], rf);
+    nd[2 * i + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], cf);
+  }
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dfree(c->d_nodes);
+  dfree(c->d_tris);
+  dfree(c->d_nrm);
+  c->has_scene = false;
+  CUDA_TRY(c, cudaMalloc(&c->d_nodes, nd.size() * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&c->d_tris, tr.size() * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&c->d_nrm, nr.size() * sizeof(float4)));
+  CUDA_TRY(c, cudaMemcpy(c->d_nodes, nd.data(), nd.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_tris, tr.data(), tr.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_nrm, nr.data(), nr.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  c->n_nodes = (uint32_t)bvh.nodes.size();
+  c->n_tris = n_tris;
+  c->n_mat = n_mat;
+  const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+  c->eps = (float)(1e-4 * std::sqrt(dx * dx + dy * dy + dz * dz));
+  c->mtype.assign(mat_type, mat_type + n_mat);
+  c->mthick.assign(mat_thickness, mat_thickness + n_mat);
+  c->has_scene = true;
+  c->has_spectra = false;  // tables are per material: set them again
+  return RT_OK;
+}
+
+rt_status rt_set_spectra(rt_ctx* c, const float* lambda_nm, uint32_t n_bands, const float* sun_L,
+                         const float sun_dir[3], float sun_half_angle, const float* n, const float* k, const float* rho,
+                         const float* le, const float* cmf_w) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_scene) return fail(c, RT_ERR_STATE, "rt_set_spectra: load a scene first");
+  if (!lambda_nm || !sun_L || !sun_dir || !n || !k || !rho || !cmf_w || n_bands == 0 || n_bands > 4096)
+    return fail(c, RT_ERR_ARG, "rt_set_spectra: null array or bad band count");
+  if (!finite3(sun_dir) || !(sun_half_angle > 0.0f) || sun_half_angle > 3.14159275f)
+    return fail(c, RT_ERR_ARG, "rt_set_spectra: bad sun direction or half angle");
+  const double sl = std::sqrt((double)sun_dir[0] * sun_dir[0] + (double)sun_dir[1] * sun_dir[1] +
+                              (double)sun_dir[2] * sun_dir[2]);
+  if (!(sl > 0.0)) return fail(c, RT_ERR_ARG, "rt_set_spectra: zero sun direction");
+  const uint32_t M = c->n_mat;
+  std::vector<float4> mb((size_t)M * n_bands);
+  std::vector<float> ad((size_t)M * n_bands);
+  for (uint32_t m = 0; m < M; ++m)
+    for (uint32_t b = 0; b < n_bands; ++b) {
+      const size_t i = (size_t)m * n_bands + b;
+      if (!std::isfinite(n[i]) || !std::isfinite(k[i]) || !std::isfinite(rho[i]) || (le && !std::isfinite(le[i])) ||
+          !(lambda_nm[b] > 0.0f))
+        return fail(c, RT_ERR_ARG, "rt_set_spectra: non-finite table entry");
+      mb[i] = make_float4(n[i], k[i], rho[i], le ? le[i] : 0.0f);
+      ad[i] = (float)(4.0 * M_PI * (double)k[i] * (double)c->mthick[m] / ((double)lambda_nm[b] * 1e-9));
+    }
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dfree(c->d_mb);
+  dfree(c->d_ad);
+  dfree(c->d_mtype);
+  dfree(c->d_sunL);
+  dfree(c->d_cmfw);
+  c->has_spectra = false;
+  CUDA_TRY(c, cudaMalloc(&c->d_mb, mb.size() * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&c->d_ad, ad.size() * sizeof(float)));
+  CUDA_TRY(c, cudaMalloc(&c->d_mtype, M * sizeof(int)));
+  CUDA_TRY(c, cudaMalloc(&c->d_sunL, n_bands * sizeof(float)));
+  CUDA_TRY(c, cudaMalloc(&c->d_cmfw, (size_t)n_bands * 3 * sizeof(float)));
+  CUDA_TRY(c, cudaMemcpy(c->d_mb, mb.data(), mb.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_ad, ad.data(), ad.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_mtype, c->mtype.data(), M * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_sunL, sun_L, n_bands * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->d_cmfw, cmf_w, (size_t)n_bands * 3 * sizeof(float), cudaMemcpyHostToDevice));
+  c->cmf_w.assign(cmf_w, cmf_w + (size_t)n_bands * 3);
+  DevSpectra& P = c->sp;
+  P.mb = c->d_mb;
+  P.ad = c->d_ad;
+  P.mtype = c->d_mtype;
+  P.sunL = c->d_sunL;
+  P.n_bands = n_bands;
+  P.n_mat = M;
+  P.sun = make_float3((float)(sun_dir[0] / sl), (float)(sun_dir[1] / sl), (float)(sun_dir[2] / sl));
+  P.cos_max = (float)std::cos((double)sun_half_angle);
+  P.one_minus_cos = (float)(1.0 - std::cos((double)sun_half_angle));
+  c->has_spectra = true;
+  return RT_OK;
+}
+
+static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
+                             uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
+                             const rt_render_opts* opts, double* spectral_dev, float* xyz_dev, rt_stats* stats) {
+  if (!c->has_scene || !c->has_spectra) return fail(c, RT_ERR_STATE, "rt_render: scene and spectra must be set");
+  if (!cams || n_cams == 0 || n_cams > (uint32_t)kMaxCams) return fail(c, RT_ERR_ARG, "rt_render: 1..64 cameras");
+  if (band_count == 0 || band_first + band_count > c->sp.n_bands || band_first + band_count < band_first)
+    return fail(c, RT_ERR_ARG, "rt_render: band range outside the spectra");
+  if (spp == 0) return fail(c, RT_ERR_ARG, "rt_render: spp must be >= 1");
+  if (depth == 0 || depth > (uint32_t)kMaxDepth) return fail(c, RT_ERR_ARG, "rt_render: depth must be 1..64");
+  rt_render_opts o{};
+  if (opts) o = *opts;
+  if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
+  if ((o.probe_map_dev != nullptr) != (o.probe_L_dev != nullptr) ||
+      (o.probe_map_dev != nullptr) != (o.probe_sig_dev != nullptr))
+    return fail(c, RT_ERR_ARG, "rt_render: probe_map, probe_L and probe_sig go together");
+  uint64_t npix = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) {
+    const rt_camera& cm = cams[v];
+    if (cm.width == 0 || cm.height == 0) return fail(c, RT_ERR_ARG, "rt_render: zero-sized view");
+    if (!finite3(cm.pos) || !finite3(cm.look) || !finite3(cm.up) || !(cm.vfov_deg > 0.0f && cm.vfov_deg < 180.0f))
+      return fail(c, RT_ERR_ARG, "rt_render: bad camera");
+    npix += (uint64_t)cm.width * cm.height;
+  }
+  const uint64_t PB64 = npix * band_count;
+  if (PB64 >= (1ull << 32)) return fail(c, RT_ERR_ARG, "rt_render: pixels x bands must be below 2^32");
+  // cameras in device form, basis in FP64
+  uint64_t off = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) {
+    const rt_camera& cm = cams[v];
+    double f[3], r[3], u[3];
+    double fl = 0, rl = 0;
+    for (int a = 0; a < 3; ++a) {
+      f[a] = (double)cm.look[a] - cm.pos[a];
+      fl += f[a] * f[a];
+    }
+    fl = std::sqrt(fl);
+    if (!(fl > 0)) return fail(c, RT_ERR_ARG, "rt_render: camera look == pos");
+    for (int a = 0; a < 3; ++a) f[a] /= fl;
+    r[0] = f[1] * cm.up[2] - f[2] * cm.up[1];
+    r[1] = f[2] * cm.up[0] - f[0] * cm.up[2];
+    r[2] = f[0] * cm.up[1] - f[1] * cm.up[0];
+    for (int a = 0; a < 3; ++a) rl += r[a] * r[a];
+    rl = std::sqrt(rl);
+    if (!(rl > 1e-12)) return fail(c, RT_ERR_ARG, "rt_render: camera up parallel to the view direction");
+    for (int a = 0; a < 3; ++a) r[a] /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    DevCam& d = c->h_cams[v];
+    d.pos = make_float3(cm.pos[0], cm.pos[1], cm.pos[2]);
+    d.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
+    d.r = make_float3((float)r[0], (float)r[1], (float)r[2]);
+    d.u = make_float3((float)u[0], (float)u[1], (float)u[2]);
+    const double th = std::tan(0.5 * (double)cm.vfov_deg * M_PI / 180.0);
+    d.th = (float)th;
+    d.tha = (float)(th * (double)cm.width / (double)cm.height);
+    d.W = cm.width;
+    d.H = cm.height;
+    d.offset = (uint32_t)off;
+    d.pad = 0;
+    off += (uint64_t)cm.width * cm.height;
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  const uint32_t PB = (uint32_t)PB64;
+  uint32_t cap = o.wave_capacity ? o.wave_capacity : (1u << 23);
+  cap = std::min<uint32_t>(std::min<uint32_t>(cap, kMaxWave), PB);
+  cap = std::max<uint32_t>(cap, 1u);
+  if (rt_status e = ensure_wave(c, cap)) return e;
+  double* accum = spectral_dev;
+  if (!accum) {
+    if (c->accum_cap < PB64) {
+      dfree(c->d_accum);
+      c->accum_cap = 0;
+      CUDA_TRY(c, cudaMalloc(&c->d_accum, PB64 * sizeof(double)));
+      c->accum_cap = PB64;
+    }
+    accum = c->d_accum;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(accum, 0, PB64 * sizeof(double), st));
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), st));
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.tot, 0, sizeof(Totals), st));
+  if (o.trace_block && (o.trace_block > 256 || o.trace_block % 32))
+    return fail(c, RT_ERR_ARG, "rt_render: trace_block must be a multiple of 32 up to 256");
+  LaunchCfg lc;
+  lc.block_trace = o.trace_block ? (int)o.trace_block : 128;
+  lc.block_shade = 256;
+  const int cps = o.ctas_per_sm ? (int)o.ctas_per_sm : trace_blocks_per_sm(lc.block_trace);
+  lc.grid_trace = c->sms * cps;
+  lc.grid_shade = c->sms * 8;
+  lc.counting = c->counting;
+  lc.record = o.probe_map_dev != nullptr;
+  Probe probe{o.probe_map_dev, o.probe_L_dev, o.probe_sig_dev};
+  WaveParams w{};
+  w.PB = PB;
+  w.band_first = band_first;
+  w.band_count = band_count;
+  w.spp = spp;
+  w.depth = depth;
+  w.key0 = (uint32_t)seed;
+  w.key1 = (uint32_t)(seed >> 32);
+  const uint64_t total = PB64 * spp;
+  const DevScene S = dev_scene(c);
+  int launches = 0;
+  uint32_t waves = 0;
+  CUDA_TRY(c, cudaEventRecord(c->ev[0], st));
+  for (uint64_t ws = 0; ws < total; ws += cap) {
+    w.n = (uint32_t)std::min<uint64_t>(cap, total - ws);
+    w.s0 = (uint32_t)(ws / PB);
+    w.r0 = (uint32_t)(ws % PB);
+    CUDA_TRY(c, cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), st));
+    launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches);
+    ++waves;
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaEventRecord(c->ev[1], st));
+  if (xyz_dev) {
+    XyzWeights xw;
+    xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
+    xw.wsplit = nullptr;
+    xw.band_count = band_count;
+    xw.kpad = (band_count + 15) / 16 * 16;
+    launch_xyz(accum, npix, xw, spp, (int)o.xyz_mode, xyz_dev, st);
+    ++launches;
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev[2], st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_tot, c->wb.tot, sizeof(Totals), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->paths = total;
+    stats->ext_rays = c->h_tot->ext_rays;
+    stats->shadow_rays = c->h_tot->shadow_rays;
+    stats->nodes_visited = c->h_tot->nodes;
+    stats->tris_tested = c->h_tot->tris;
+    stats->waves = waves;
+    stats->kernel_launches = (uint32_t)launches;
+    cudaEventElapsedTime(&stats->ms_render, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&stats->ms_xyz, c->ev[1], c->ev[2]);
+  }
+  return status_to_rt(c, *c->h_status);
+}
+
+rt_status rt_render(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
+                    uint32_t spp, uint32_t depth, uint64_t seed, const rt_render_opts* opts, double* spectral_dev,
+                    float* xyz_dev, rt_stats* stats) {
+  if (rt_status e = check_ctx(c)) return e;
+  return render_impl(c, cams, n_cams, band_first, band_count, spp, depth, seed, opts, spectral_dev, xyz_dev, stats);
+}
+
+rt_status rt_render_host(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
+                         uint32_t spp, uint32_t depth, uint64_t seed, const rt_render_opts* opts, double* spectral_host,
+                         float* xyz_host, rt_stats* stats) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!xyz_host) return fail(c, RT_ERR_ARG, "rt_render_host: xyz_host is required");
+  if (!cams || n_cams == 0 || n_cams > (uint32_t)kMaxCams) return fail(c, RT_ERR_ARG, "rt_render_host: 1..64 cameras");
+  uint64_t npix = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) npix += (uint64_t)cams[v].width * cams[v].height;
+  cudaSetDevice(c->device);
+  if (c->xyz_cap < npix * 3) {
+    dfree(c->d_xyz);
+    c->xyz_cap = 0;
+    CUDA_TRY(c, cudaMalloc(&c->d_xyz, npix * 3 * sizeof(float)));
+    c->xyz_cap = npix * 3;
+  }
+  rt_status s = render_impl(c, cams, n_cams, band_first, band_count, spp, depth, seed, opts, nullptr, c->d_xyz, stats);
+  if (s != RT_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(xyz_host, c->d_xyz, npix * 3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (spectral_host)
+    CUDA_TRY(c, cudaMemcpyAsync(spectral_host, c->d_accum, npix * band_count * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_philox(rt_ctx* c, const uint32_t* ctr_dev, uint32_t* out_dev, uint64_t n, uint32_t key0, uint32_t key1) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!ctr_dev || !out_dev) return fail(c, RT_ERR_ARG, "rt_philox: null pointer");
+  if (n == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  launch_philox(ctr_dev, out_dev, n, key0, key1, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_trace_closest(rt_ctx* c, const float* o_dev, const float* d_dev, uint64_t n, float* t_dev,
+                           int32_t* prim_dev) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_scene) return fail(c, RT_ERR_STATE, "rt_trace_closest: no scene");
+  if (!o_dev || !d_dev || !t_dev || !prim_dev) return fail(c, RT_ERR_ARG, "rt_trace_closest: null pointer");
+  if (n == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), c->stream));
+  launch_trace_closest_rays(dev_scene(c), o_dev, d_dev, n, t_dev, prim_dev, c->wb.status, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return status_to_rt(c, *c->h_status);
+}
+
+rt_status rt_trace_shadow(rt_ctx* c, const float* o_dev, const float* d_dev, const uint32_t* band_dev, uint64_t n,
+                          float* T_dev, uint32_t* n_glass_dev) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_scene || !c->has_spectra) return fail(c, RT_ERR_STATE, "rt_trace_shadow: scene and spectra required");
+  if (!o_dev || !d_dev || !band_dev || !T_dev || !n_glass_dev) return fail(c, RT_ERR_ARG, "rt_trace_shadow: null");
+  if (n == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), c->stream));
+  launch_trace_shadow_rays(dev_scene(c), c->sp, o_dev, d_dev, band_dev, n, T_dev, n_glass_dev, c->wb.status,
+                           c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return status_to_rt(c, *c->h_status);
+}
+
+rt_status rt_optics_eval(rt_ctx* c, const float* cos_dev, const float* n_dev, const float* k_dev,
+                         const float* lambda_nm_dev, const float* d_dev, uint64_t count, float* R_dev, float* Rs_dev,
+                         float* Ts_dev) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!cos_dev || !n_dev || !k_dev || !R_dev) return fail(c, RT_ERR_ARG, "rt_optics_eval: null pointer");
+  if ((lambda_nm_dev || d_dev) && (!lambda_nm_dev || !d_dev || !Rs_dev || !Ts_dev))
+    return fail(c, RT_ERR_ARG, "rt_optics_eval: slab outputs need lambda, d, Rs and Ts");
+  if (count == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  launch_optics(cos_dev, n_dev, k_dev, lambda_nm_dev, d_dev, count, R_dev, Rs_dev, Ts_dev, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_xyz(rt_ctx* c, const double* spectral_dev, uint64_t n_pixels, uint32_t band_first, uint32_t band_count,
+                 uint32_t spp, uint32_t mode, float* xyz_dev) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_spectra) return fail(c, RT_ERR_STATE, "rt_xyz: spectra required");
+  if (!spectral_dev || !xyz_dev || spp == 0 || band_count == 0 || band_first + band_count > c->sp.n_bands ||
+      mode > 2)
+    return fail(c, RT_ERR_ARG, "rt_xyz: bad argument");
+  if (n_pixels == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  XyzWeights xw;
+  xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
+  xw.wsplit = nullptr;
+  xw.band_count = band_count;
+  xw.kpad = (band_count + 15) / 16 * 16;
+  launch_xyz(spectral_dev, n_pixels, xw, spp, (int)mode, xyz_dev, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+}  // extern "C"

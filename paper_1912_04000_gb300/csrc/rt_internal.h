@@ -1,0 +1,149 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace srt {
+
+// device status word bits (set by kernels, read by the host after a render)
+enum : uint32_t {
+  ST_STACK = 1u,      // traversal stack exhausted
+  ST_QUEUE = 2u,      // work queue overflow
+  ST_ITER = 4u,       // traversal iteration cap
+  ST_RANGE = 8u       // index out of range caught by a device check
+};
+
+constexpr int kStack = 64;             // traversal stack entries per thread
+constexpr uint32_t kPidBits = 24;      // path id bits in a queue entry
+constexpr uint32_t kPidMask = (1u << kPidBits) - 1u;
+constexpr uint32_t kFlagCovered = 1u << 31;  // direct sun already estimated by NEE
+constexpr uint32_t kFlagTerm = 1u << 30;     // shadow ray: path ends at this vertex
+constexpr uint32_t kMaxWave = 1u << kPidBits;
+
+// Scene on the device.
+// nodes: 2 float4 per node {lo.xyz, bits(ref)}, {hi.xyz, bits(count)}; node 1
+//   is the root; the children of an interior node sit at an even index pair
+//   (ref, ref + 1), 64-byte aligned; a leaf has count in [1, 7] triangles
+//   starting at triangle ref.
+// tris: 3 float4 per triangle in leaf order {v0, bits(input id)},
+//   {v1, bits(material)}, {v2, 0}.
+// nrm: per leaf-order triangle {unit geometric normal (FP64-rounded),
+//   bits(material)}.
+struct DevScene {
+  const float4* nodes;
+  const float4* tris;
+  const float4* nrm;
+  uint32_t n_nodes;
+  uint32_t n_tris;
+  float eps;  // origin offset along the normal: 1e-4 x scene diagonal
+};
+
+// Spectral tables on the device.
+// mb: per (material, band) {n, k, rho, le}; ad: per (material, band)
+// 4 pi k d / lambda (thin glass, FP64-rounded); mtype per material.
+struct DevSpectra {
+  const float4* mb;
+  const float* ad;
+  const int* mtype;
+  const float* sunL;
+  uint32_t n_bands;
+  uint32_t n_mat;
+  float3 sun;
+  float cos_max;
+  float one_minus_cos;  // 1 - cos(half angle), FP64-rounded
+};
+
+// One camera in device form (FP64-derived basis).
+struct DevCam {
+  float3 pos, f, r, u;
+  float tha, th;        // tan(vfov/2) * aspect, tan(vfov/2)
+  uint32_t W, H;
+  uint32_t offset;      // first global pixel id of this view
+  uint32_t pad;
+};
+
+constexpr int kMaxCams = 64;
+
+// One wave: paths [wave_start, wave_start + n) of the index space
+// g = s * PB + r, r = pixel * band_count + j, PB = pixels * band_count.
+struct WaveParams {
+  uint32_t n;          // paths in this wave
+  uint32_t s0, r0;     // sample and in-sample index of the first path
+  uint32_t PB;         // pixels * band_count
+  uint32_t band_first, band_count;
+  uint32_t spp, depth;
+  uint32_t key0, key1;
+};
+
+// Per-wave device counters, one row per vertex k (0 .. depth).
+struct Counters {
+  uint32_t q_count;     // rays queued for vertex k
+  uint32_t q_fetch;     // traversal work fetch
+  uint32_t s_count;     // shadow rays emitted at vertex k
+  uint32_t s_fetch;
+};
+
+struct Totals {
+  unsigned long long ext_rays, shadow_rays, nodes, tris;
+};
+
+// Work buffers of one wave (capacity C paths).
+struct WaveBufs {
+  float4* q[2];         // ray queues, 2 float4 each: {o, bits(pid|flags)}, {d, T}
+  float2* hit;          // {t, bits(leaf-order triangle or -1)}
+  float4* sq;           // shadow queue, 2 float4 each: {o, bits(pid|flags)}, {w, contrib}
+  float* L;             // accumulated radiance per path id
+  uint32_t* sig;        // event signature per path id (record mode)
+  Counters* cnt;        // [kMaxDepth + 2]
+  Totals* tot;
+  uint32_t* status;
+  uint32_t cap;
+};
+
+constexpr int kMaxDepth = 64;
+
+struct Probe {
+  const uint32_t* map;  // per global pixel: probe slot or 0xFFFFFFFF
+  float* L;
+  uint32_t* sig;
+};
+
+// Launchers (rt_kernels.cu).
+struct LaunchCfg {
+  int grid_trace, block_trace;
+  int grid_shade, block_shade;
+  bool counting;
+  bool record;
+};
+
+void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
+                 const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe,
+                 cudaStream_t st, int* launches);
+void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st);
+void launch_trace_closest_rays(const DevScene& S, const float* o, const float* d, uint64_t n, float* t,
+                               int32_t* prim, uint32_t* status, cudaStream_t st);
+void launch_trace_shadow_rays(const DevScene& S, const DevSpectra& P, const float* o, const float* d,
+                              const uint32_t* band, uint64_t n, float* T, uint32_t* n_glass, uint32_t* status,
+                              cudaStream_t st);
+void launch_optics(const float* c, const float* n, const float* k, const float* lam, const float* d,
+                   uint64_t count, float* R, float* Rs, float* Ts, cudaStream_t st);
+
+// XYZ contraction (rt_xyz.cu).
+// Weights are prepared on the host per band range: wsplit holds the three
+// BF16 terms of the weights in the layout the tensor-core kernel reads.
+struct XyzWeights {
+  const float* w32;        // [band_count][3] float
+  const uint16_t* wsplit;  // tensor-core B operand tiles (see rt_xyz.cu)
+  uint32_t band_count;
+  uint32_t kpad;           // band_count rounded up to 16
+};
+void launch_xyz(const double* spectral, uint64_t n_pixels, const XyzWeights& w, uint32_t spp, int mode, float* xyz,
+                cudaStream_t st);
+size_t xyz_wsplit_elems(uint32_t band_count);
+void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t* wsplit_host);
+
+int num_sms(int device);
+int trace_blocks_per_sm(int block);
+
+}  // namespace srt

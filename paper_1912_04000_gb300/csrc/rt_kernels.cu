@@ -1,0 +1,594 @@
+// Wavefront path-tracing kernels (sm_103a).
+//
+// One wave holds up to C spectral paths (view, pixel, sample, band).  For each
+// vertex k = 1..depth the host enqueues three kernels:
+//   k_trace  - closest hit of every queued ray (BVH2, watertight FP32 test),
+//              persistent warps fetching 32 rays at a time;
+//   k_shade  - material event at the hit (section 4: Eq. 2 by cosine sampling
+//              for stone, thin-glass/conductor Fresnel events with the complex
+//              index of Eq. 1), next-event estimate of the sun cone (Eq. 3),
+//              continuation ray appended to the next queue;
+//   k_shadow - transmittance of the sun rays (0 behind stone, product of the
+//              thin-glass T_s otherwise), added to the path's radiance.
+// Each path owns one output slot (pixel, band) in the wave, so the FP64
+// accumulation into the spectral image needs no atomics: different samples
+// of a slot are in different waves, which run in sample order.
+#include <cstdio>
+
+#include "rt_device.cuh"
+
+namespace srt {
+
+namespace {
+
+__device__ __forceinline__ uint32_t mix_sig(uint32_t h, uint32_t v) { return (h ^ v) * 16777619u; }
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// Warp-aggregated append of one element per lane with want = true; every lane
+// of the warp must call it (converged).  Returns the slot of this lane.
+__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t mask = __ballot_sync(0xffffffffu, want);
+  uint32_t base = 0;
+  const int leader = __ffs(mask) - 1;
+  if (mask != 0u && (int)lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
+  return base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+}
+
+// Path identity from the wave-local id: in-sample index r, sample s,
+// pixel, band index j.
+struct PathId {
+  uint32_t r, s, pix, j;
+};
+
+__device__ __forceinline__ PathId path_id(const WaveParams& w, uint32_t pid) {
+  PathId p;
+  p.r = w.r0 + pid;
+  p.s = w.s0;
+  if (p.r >= w.PB) {
+    p.r -= w.PB;
+    p.s += 1;
+  }
+  p.pix = p.r / w.band_count;
+  p.j = p.r - p.pix * w.band_count;
+  return p;
+}
+
+// Closest hit with t > 0 over the BVH; ties in t go to the lower input id.
+template <bool COUNT>
+__device__ __forceinline__ void closest_hit(const DevScene& S, float3 o, float3 d, float& best_t, int& best_leaf,
+                                            uint32_t* status, uint32_t& n_nodes, uint32_t& n_tris) {
+  const RayW rw = ray_prep(o, d);
+  const RayB rb = box_prep(o, d);
+  best_t = INFINITY;
+  best_leaf = -1;
+  uint32_t best_id = 0xFFFFFFFFu;
+  uint2 stack[kStack];
+  int sp = 0;
+  const float4 rlo = ldg4(S.nodes + 2), rhi = ldg4(S.nodes + 3);
+  if (box_enter(rb, rlo, rhi, INFINITY) < 0.0f) return;
+  uint32_t ref = __float_as_uint(rlo.w), cnt = __float_as_uint(rhi.w);
+  const uint32_t cap = 4u * S.n_nodes + 64u;
+  uint32_t iter = 0;
+  for (;;) {
+    if (++iter > cap) {
+      atomicOr(status, ST_ITER);
+      return;
+    }
+    if (cnt == 0u) {
+      const float4* c = S.nodes + 2u * ref;
+      const float4 alo = ldg4(c), ahi = ldg4(c + 1), blo = ldg4(c + 2), bhi = ldg4(c + 3);
+      if (COUNT) n_nodes += 2;
+      const float ta = box_enter(rb, alo, ahi, best_t);
+      const float tb = box_enter(rb, blo, bhi, best_t);
+      if (ta >= 0.0f && tb >= 0.0f) {
+        const bool af = ta <= tb;
+        if (sp >= kStack) {
+          atomicOr(status, ST_STACK);
+          return;
+        }
+        const float4 flo = af ? blo : alo, fhi = af ? bhi : ahi;
+        stack[sp++] = make_uint2((__float_as_uint(flo.w) << 3) | __float_as_uint(fhi.w), __float_as_uint(af ? tb : ta));
+        ref = __float_as_uint(af ? alo.w : blo.w);
+        cnt = __float_as_uint(af ? ahi.w : bhi.w);
+        continue;
+      }
+      if (ta >= 0.0f) {
+        ref = __float_as_uint(alo.w);
+        cnt = __float_as_uint(ahi.w);
+        continue;
+      }
+      if (tb >= 0.0f) {
+        ref = __float_as_uint(blo.w);
+        cnt = __float_as_uint(bhi.w);
+        continue;
+      }
+    } else {
+      for (uint32_t t = ref; t < ref + cnt; ++t) {
+        const float4* tr = S.tris + 3u * t;
+        const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
+        if (COUNT) ++n_tris;
+        const float th = tri_hit(rw, f3(v0), f3(v1), f3(v2));
+        const uint32_t id = __float_as_uint(v0.w);
+        if (th > 0.0f && (th < best_t || (th == best_t && id < best_id))) {
+          best_t = th;
+          best_leaf = (int)t;
+          best_id = id;
+        }
+      }
+    }
+    bool found = false;
+    while (sp > 0) {
+      const uint2 e = stack[--sp];
+      if (__uint_as_float(e.y) <= best_t) {
+        ref = e.x >> 3;
+        cnt = e.x & 7u;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return;
+  }
+}
+
+// Transmittance of a sun ray to infinity (section 4, Eq. 3 visibility term
+// through thin glass).  n_glass = sheets crossed, or 0xFFFFFFFF if blocked.
+template <bool COUNT>
+__device__ __forceinline__ float shadow_T(const DevScene& S, const DevSpectra& P, float3 o, float3 d, uint32_t band,
+                                          uint32_t& n_glass, uint32_t* status, uint32_t& n_nodes, uint32_t& n_tris) {
+  const RayW rw = ray_prep(o, d);
+  const RayB rb = box_prep(o, d);
+  float T = 1.0f;
+  uint32_t ng = 0;
+  uint32_t stack[kStack];
+  int sp = 0;
+  const float4 rlo = ldg4(S.nodes + 2), rhi = ldg4(S.nodes + 3);
+  n_glass = 0;
+  if (box_enter(rb, rlo, rhi, INFINITY) < 0.0f) return 1.0f;
+  uint32_t ref = __float_as_uint(rlo.w), cnt = __float_as_uint(rhi.w);
+  const uint32_t cap = 4u * S.n_nodes + 64u;
+  uint32_t iter = 0;
+  for (;;) {
+    if (++iter > cap) {
+      atomicOr(status, ST_ITER);
+      break;
+    }
+    if (cnt == 0u) {
+      const float4* c = S.nodes + 2u * ref;
+      const float4 alo = ldg4(c), ahi = ldg4(c + 1), blo = ldg4(c + 2), bhi = ldg4(c + 3);
+      if (COUNT) n_nodes += 2;
+      const float ta = box_enter(rb, alo, ahi, INFINITY);
+      const float tb = box_enter(rb, blo, bhi, INFINITY);
+      if (ta >= 0.0f && tb >= 0.0f) {
+        const bool af = ta <= tb;
+        if (sp >= kStack) {
+          atomicOr(status, ST_STACK);
+          break;
+        }
+        const float4 flo = af ? blo : alo, fhi = af ? bhi : ahi;
+        stack[sp++] = (__float_as_uint(flo.w) << 3) | __float_as_uint(fhi.w);
+        ref = __float_as_uint(af ? alo.w : blo.w);
+        cnt = __float_as_uint(af ? ahi.w : bhi.w);
+        continue;
+      }
+      if (ta >= 0.0f) {
+        ref = __float_as_uint(alo.w);
+        cnt = __float_as_uint(ahi.w);
+        continue;
+      }
+      if (tb >= 0.0f) {
+        ref = __float_as_uint(blo.w);
+        cnt = __float_as_uint(bhi.w);
+        continue;
+      }
+    } else {
+      for (uint32_t t = ref; t < ref + cnt; ++t) {
+        const float4* tr = S.tris + 3u * t;
+        const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
+        if (COUNT) ++n_tris;
+        const float th = tri_hit(rw, f3(v0), f3(v1), f3(v2));
+        if (th > 0.0f) {
+          const uint32_t mat = __float_as_uint(v1.w);
+          if (__ldg(P.mtype + mat) != 1) {
+            n_glass = 0xFFFFFFFFu;
+            return 0.0f;
+          }
+          const float4 nr = ldg4(S.nrm + t);
+          const float c = fabsf(dot(d, f3(nr)));
+          const float4 m = ldg4(P.mb + mat * P.n_bands + band);
+          float Rs, Ts;
+          thin_sheet(c, m.x, m.y, __ldg(P.ad + mat * P.n_bands + band), Rs, Ts);
+          T *= Ts;
+          ++ng;
+        }
+      }
+    }
+    if (sp == 0) break;
+    const uint32_t e = stack[--sp];
+    ref = e >> 3;
+    cnt = e & 7u;
+  }
+  n_glass = ng;
+  return T;
+}
+
+__device__ __forceinline__ void finalize(const WaveParams& w, const PathId& id, float L, uint32_t sg, double* accum,
+                                         const Probe& probe, bool record) {
+  if (L != 0.0f) accum[id.r] += (double)L;
+  if (record && probe.map != nullptr) {
+    const uint32_t slot = probe.map[id.pix];
+    if (slot != 0xFFFFFFFFu) {
+      const size_t q = ((size_t)slot * w.spp + id.s) * w.band_count + id.j;
+      probe.L[q] = L;
+      probe.sig[q] = sg;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams, uint32_t n_cams, WaveParams w,
+                                                float4* __restrict__ q, float* __restrict__ L,
+                                                uint32_t* __restrict__ sig, Counters* cnt, bool record) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[1].q_count = w.n;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += stride) {
+    const PathId id = path_id(w, i);
+    uint32_t v = 0;
+    while (v + 1 < n_cams && cams[v + 1].offset <= id.pix) ++v;
+    const DevCam& C = cams[v];
+    const uint32_t local = id.pix - C.offset;
+    const uint32_t y = local / C.W, x = local - y * C.W;
+    const uint4 u = philox4x32_10(make_uint4(id.pix, id.s, w.band_first + id.j, 0u), w.key0, w.key1);
+    const float sx = (2.0f * ((float)x + u01(u.x)) / (float)C.W - 1.0f) * C.tha;
+    const float sy = (1.0f - 2.0f * ((float)y + u01(u.y)) / (float)C.H) * C.th;
+    float3 dir = make_float3(C.f.x + sx * C.r.x + sy * C.u.x, C.f.y + sx * C.r.y + sy * C.u.y,
+                             C.f.z + sx * C.r.z + sy * C.u.z);
+    const float inv = 1.0f / sqrtf(dot(dir, dir));
+    dir = mul(inv, dir);
+    q[2 * i] = make_float4(C.pos.x, C.pos.y, C.pos.z, __uint_as_float(i));
+    q[2 * i + 1] = make_float4(dir.x, dir.y, dir.z, 1.0f);
+    L[i] = 0.0f;
+    if (record) sig[i] = 2166136261u;
+  }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
+                                               Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
+                                               uint32_t* status) {
+  const uint32_t count = min(cnt[k].q_count, cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->ext_rays, (unsigned long long)count);
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t nn = 0, nt = 0;
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&cnt[k].q_fetch, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= count) break;
+    const uint32_t i = base + lane;
+    if (i < count) {
+      const float4 a = __ldcs(q + 2 * i), b = __ldcs(q + 2 * i + 1);
+      float t;
+      int leaf;
+      closest_hit<COUNT>(S, f3(a), f3(b), t, leaf, status, nn, nt);
+      __stcs(hit + i, make_float2(t, __int_as_float(leaf)));
+    }
+  }
+  if (COUNT) {
+    atomicAdd(&tot->nodes, (unsigned long long)nn);
+    atomicAdd(&tot->tris, (unsigned long long)nt);
+  }
+}
+
+template <bool RECORD>
+__global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+                                               const float4* __restrict__ qin, const float2* __restrict__ hit,
+                                               float4* __restrict__ qout, float4* __restrict__ sq,
+                                               float* __restrict__ Lbuf, uint32_t* __restrict__ sigbuf,
+                                               Counters* cnt, uint32_t cap, double* __restrict__ accum,
+                                               Probe probe, uint32_t* status) {
+  const uint32_t count = min(cnt[k].q_count, cap);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
+    const uint32_t i = base + lane;
+    bool emit_next = false, emit_shadow = false;
+    float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, s0 = n0, s1 = n0;
+    if (i < count) {
+      const float4 a = __ldcs(qin + 2 * i), b = __ldcs(qin + 2 * i + 1);
+      const float2 h = __ldcs(hit + i);
+      const uint32_t bits = __float_as_uint(a.w);
+      const uint32_t pid = bits & kPidMask;
+      const bool covered = (bits & kFlagCovered) != 0u;
+      const float T = b.w;
+      const float3 o = f3(a), d = f3(b);
+      const PathId id = path_id(w, pid);
+      const uint32_t band = w.band_first + id.j;
+      float Lp = Lbuf[pid];
+      uint32_t sg = RECORD ? sigbuf[pid] : 0u;
+      const int leaf = __float_as_int(h.y);
+      bool terminate = false;
+      if (leaf < 0) {
+        if (RECORD) sg = mix_sig(sg, 0xFFFFFFFFu);
+        if (!covered && dot(d, P.sun) >= P.cos_max) Lp += T * __ldg(P.sunL + band);
+        terminate = true;
+      } else {
+        const float3 p = madd(o, h.x, d);
+        const float4 nr = ldg4(S.nrm + leaf);
+        const uint32_t mat = __float_as_uint(nr.w);
+        if (RECORD) sg = mix_sig(sg, __float_as_uint(S.tris[3 * leaf].w));
+        const float3 ng = f3(nr);
+        const float3 n = dot(ng, d) < 0.0f ? ng : neg(ng);
+        const float cos_i = -dot(d, n);
+        const float4 m = ldg4(P.mb + mat * P.n_bands + band);
+        const int type = __ldg(P.mtype + mat);
+        const uint4 u = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k), w.key0, w.key1);
+        if (type == 0 || type == 3) {
+          if (type == 3) Lp += T * m.w;
+          // next-event estimate: uniform direction in the sun cone
+          const float om = u01(u.x) * P.one_minus_cos;
+          const float ct = 1.0f - om;
+          const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
+          float sp_, cp_;
+          sincospif(2.0f * u01(u.y), &sp_, &cp_);
+          float3 t1, t2;
+          onb(P.sun, t1, t2);
+          const float3 wd = make_float3(st * cp_ * t1.x + st * sp_ * t2.x + ct * P.sun.x,
+                                        st * cp_ * t1.y + st * sp_ * t2.y + ct * P.sun.y,
+                                        st * cp_ * t1.z + st * sp_ * t2.z + ct * P.sun.z);
+          const float c = dot(n, wd);
+          const float3 po = madd(p, S.eps, n);
+          if (c > 0.0f) {
+            emit_shadow = true;
+            const uint32_t fl = pid | (k == w.depth ? kFlagTerm : 0u);
+            s0 = make_float4(po.x, po.y, po.z, __uint_as_float(fl));
+            s1 = make_float4(wd.x, wd.y, wd.z, T * m.z * c * __ldg(P.sunL + band) * 2.0f * P.one_minus_cos);
+          }
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            // cosine-weighted continuation, weight rho
+            const float rr = sqrtf(u01(u.z));
+            const float zz = sqrtf(fmaxf(0.0f, 1.0f - u01(u.z)));
+            float s2, c2;
+            sincospif(2.0f * u01(u.w), &s2, &c2);
+            float3 b1, b2;
+            onb(n, b1, b2);
+            const float3 nd = make_float3(rr * c2 * b1.x + rr * s2 * b2.x + zz * n.x,
+                                          rr * c2 * b1.y + rr * s2 * b2.y + zz * n.y,
+                                          rr * c2 * b1.z + rr * s2 * b2.z + zz * n.z);
+            emit_next = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | kFlagCovered));
+            n1 = make_float4(nd.x, nd.y, nd.z, T * m.z);
+          }
+        } else if (type == 1) {
+          float Rs, Ts;
+          thin_sheet(cos_i, m.x, m.y, __ldg(P.ad + mat * P.n_bands + band), Rs, Ts);
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k + 1u), w.key0, w.key1);
+            emit_next = true;
+            if (u01(u1.x) < Rs / (Rs + Ts)) {
+              const float3 rd = madd(d, -2.0f * dot(d, n), n);
+              const float3 po = madd(p, S.eps, n);
+              n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid));
+              n1 = make_float4(rd.x, rd.y, rd.z, T * (Rs + Ts));
+            } else {
+              const float3 po = madd(p, -S.eps, n);
+              n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | (covered ? kFlagCovered : 0u)));
+              n1 = make_float4(d.x, d.y, d.z, T * (Rs + Ts));
+            }
+          }
+        } else {
+          const float R = fresnel_complex(cos_i, m.x, m.y);
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            const float3 rd = madd(d, -2.0f * dot(d, n), n);
+            const float3 po = madd(p, S.eps, n);
+            emit_next = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid));
+            n1 = make_float4(rd.x, rd.y, rd.z, T * R);
+          }
+        }
+      }
+      if (terminate && !emit_shadow) {
+        finalize(w, id, Lp, sg, accum, probe, RECORD);
+      } else {
+        Lbuf[pid] = Lp;
+        if (RECORD) sigbuf[pid] = sg;
+      }
+    }
+    const uint32_t slot_n = warp_append(&cnt[k + 1].q_count, emit_next);
+    const uint32_t slot_s = warp_append(&cnt[k].s_count, emit_shadow);
+    if (emit_next) {
+      if (slot_n < cap) {
+        __stcs(qout + 2 * slot_n, n0);
+        __stcs(qout + 2 * slot_n + 1, n1);
+      } else {
+        atomicOr(status, ST_QUEUE);
+      }
+    }
+    if (emit_shadow) {
+      if (slot_s < cap) {
+        __stcs(sq + 2 * slot_s, s0);
+        __stcs(sq + 2 * slot_s + 1, s1);
+      } else {
+        atomicOr(status, ST_QUEUE);
+      }
+    }
+  }
+}
+
+template <bool RECORD, bool COUNT>
+__global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+                                                const float4* __restrict__ sq, float* __restrict__ Lbuf,
+                                                uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
+                                                double* __restrict__ accum, Probe probe, Totals* tot,
+                                                uint32_t* status) {
+  const uint32_t count = min(cnt[k].s_count, cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t nn = 0, nt = 0;
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&cnt[k].s_fetch, 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= count) break;
+    const uint32_t i = base + lane;
+    if (i < count) {
+      const float4 a = __ldcs(sq + 2 * i), b = __ldcs(sq + 2 * i + 1);
+      const uint32_t bits = __float_as_uint(a.w);
+      const uint32_t pid = bits & kPidMask;
+      const PathId id = path_id(w, pid);
+      uint32_t ng;
+      const float Tr = shadow_T<COUNT>(S, P, f3(a), f3(b), w.band_first + id.j, ng, status, nn, nt);
+      const float Lp = Lbuf[pid] + b.w * Tr;
+      uint32_t sg = 0;
+      if (RECORD) sg = mix_sig(sigbuf[pid], ng);
+      if (bits & kFlagTerm) {
+        finalize(w, id, Lp, sg, accum, probe, RECORD);
+      } else {
+        Lbuf[pid] = Lp;
+        if (RECORD) sigbuf[pid] = sg;
+      }
+    }
+  }
+  if (COUNT) {
+    atomicAdd(&tot->nodes, (unsigned long long)nn);
+    atomicAdd(&tot->tris, (unsigned long long)nt);
+  }
+}
+
+// ---- single-step kernels for parity tests --------------------------------
+
+__global__ void k_philox(const uint4* __restrict__ ctr, uint4* __restrict__ out, uint64_t n, uint32_t k0, uint32_t k1) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void k_closest_rays(DevScene S, const float* __restrict__ o, const float* __restrict__ d, uint64_t n,
+                               float* __restrict__ tout, int32_t* __restrict__ prim, uint32_t* status) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    float t;
+    int leaf;
+    uint32_t a = 0, b = 0;
+    closest_hit<false>(S, make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]),
+                       make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]), t, leaf, status, a, b);
+    tout[i] = leaf < 0 ? -1.0f : t;
+    prim[i] = leaf < 0 ? -1 : (int32_t)__float_as_uint(S.tris[3 * leaf].w);
+  }
+}
+
+__global__ void k_shadow_rays(DevScene S, DevSpectra P, const float* __restrict__ o, const float* __restrict__ d,
+                              const uint32_t* __restrict__ band, uint64_t n, float* __restrict__ T,
+                              uint32_t* __restrict__ ng, uint32_t* status) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t a = 0, b = 0, g;
+    T[i] = shadow_T<false>(S, P, make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]),
+                           make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]), band[i], g, status, a, b);
+    ng[i] = g;
+  }
+}
+
+__global__ void k_optics(const float* __restrict__ c, const float* __restrict__ n, const float* __restrict__ k,
+                         const float* __restrict__ lam, const float* __restrict__ dd, uint64_t count,
+                         float* __restrict__ R, float* __restrict__ Rs, float* __restrict__ Ts) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    R[i] = fresnel_complex(c[i], n[i], k[i]);
+    if (lam != nullptr && dd != nullptr) {
+      // alpha d in FP64 then rounded, as the spectra tables are prepared
+      const float ad = (float)(4.0 * 3.14159265358979323846 * (double)k[i] * (double)dd[i] / ((double)lam[i] * 1e-9));
+      float rs, ts;
+      thin_sheet(c[i], n[i], k[i], ad, rs, ts);
+      Rs[i] = rs;
+      Ts[i] = ts;
+    }
+  }
+}
+
+int grid_for(uint64_t n, int block) {
+  uint64_t g = (n + block - 1) / block;
+  if (g > 65535ull * 8) g = 65535ull * 8;
+  return (int)(g == 0 ? 1 : g);
+}
+
+}  // namespace
+
+void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
+                 const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st,
+                 int* launches) {
+  const bool rec = lc.record;
+  k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec);
+  int nl = 1;
+  for (uint32_t k = 1; k <= w.depth; ++k) {
+    const float4* qin = b.q[k & 1];
+    float4* qout = b.q[(k + 1) & 1];
+    if (lc.counting)
+      k_trace<true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status);
+    else
+      k_trace<false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status);
+    if (rec)
+      k_shade<true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt,
+                                                             b.cap, accum, probe, b.status);
+    else
+      k_shade<false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt,
+                                                              b.cap, accum, probe, b.status);
+    if (rec && lc.counting)
+      k_shadow<true, true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe,
+                                                                    b.tot, b.status);
+    else if (rec)
+      k_shadow<true, false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
+                                                                     probe, b.tot, b.status);
+    else if (lc.counting)
+      k_shadow<false, true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
+                                                                     probe, b.tot, b.status);
+    else
+      k_shadow<false, false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
+                                                                      probe, b.tot, b.status);
+    nl += 3;
+  }
+  if (launches) *launches += nl;
+}
+
+void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st) {
+  k_philox<<<grid_for(n, 256), 256, 0, st>>>((const uint4*)ctr, (uint4*)out, n, k0, k1);
+}
+
+void launch_trace_closest_rays(const DevScene& S, const float* o, const float* d, uint64_t n, float* t, int32_t* prim,
+                               uint32_t* status, cudaStream_t st) {
+  k_closest_rays<<<grid_for(n, 128), 128, 0, st>>>(S, o, d, n, t, prim, status);
+}
+
+void launch_trace_shadow_rays(const DevScene& S, const DevSpectra& P, const float* o, const float* d,
+                              const uint32_t* band, uint64_t n, float* T, uint32_t* n_glass, uint32_t* status,
+                              cudaStream_t st) {
+  k_shadow_rays<<<grid_for(n, 128), 128, 0, st>>>(S, P, o, d, band, n, T, n_glass, status);
+}
+
+void launch_optics(const float* c, const float* n, const float* k, const float* lam, const float* d, uint64_t count,
+                   float* R, float* Rs, float* Ts, cudaStream_t st) {
+  k_optics<<<grid_for(count, 256), 256, 0, st>>>(c, n, k, lam, d, count, R, Rs, Ts);
+}
+
+int trace_blocks_per_sm(int block) {
+  int a = 0, b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false, false>, block, 0);
+  const int m = a < b ? a : b;
+  return m > 0 ? m : 1;
+}
+
+int num_sms(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  return v;
+}
+
+}  // namespace srt

@@ -1,0 +1,202 @@
+"""Python face of the C ABI: a Renderer owns one rt_ctx on one CUDA device.
+
+Tensors are torch CUDA tensors (device memory from PyTorch's allocator); the
+library enqueues on the torch stream given at construction.  Each method is a
+single C-ABI call plus argument marshalling.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _native
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Renderer:
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("spectral_rt needs a CUDA device (no CPU fallback)")
+        self.lib = _native.load()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = self.lib.rt_create(device, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise _native.RtError("rt_create", st, "device or allocation failure")
+        self._h = h
+        self.n_bands = 0
+        self.n_mat = 0
+
+    # -- plumbing ---------------------------------------------------------------
+    def _check(self, fn: str, st: int):
+        if st != 0:
+            msg = self.lib.rt_last_error(self._h)
+            raise _native.RtError(fn, st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.rt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_counting(self, on: bool):
+        self._check("rt_set_counting", self.lib.rt_set_counting(self._h, 1 if on else 0))
+
+    # -- scene and spectra ------------------------------------------------------
+    def load_scene(self, scene):
+        v = np.ascontiguousarray(scene.verts, np.float32)
+        t = np.ascontiguousarray(scene.tris, np.uint32)
+        m = np.ascontiguousarray(scene.mat_id, np.uint32)
+        mt = np.ascontiguousarray(scene.mat_type, np.int32)
+        th = np.ascontiguousarray(scene.mat_thickness, np.float32)
+        st = self.lib.rt_load_scene(self._h, v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0], m.ctypes.data,
+                                    mt.ctypes.data, th.ctypes.data, mt.shape[0])
+        self._check("rt_load_scene", st)
+        self.n_mat = mt.shape[0]
+
+    def set_spectra(self, sp):
+        arrs = [np.ascontiguousarray(a, np.float32) for a in
+                (sp.lambda_nm, sp.sun_L, sp.sun_dir, sp.n, sp.k, sp.rho, sp.le, sp.cmf_w)]
+        lam, sun_L, sun_dir, n, k, rho, le, w = arrs
+        st = self.lib.rt_set_spectra(self._h, lam.ctypes.data, lam.shape[0], sun_L.ctypes.data, sun_dir.ctypes.data,
+                                     float(sp.sun_half_angle), n.ctypes.data, k.ctypes.data, rho.ctypes.data,
+                                     le.ctypes.data, w.ctypes.data)
+        self._check("rt_set_spectra", st)
+        self.n_bands = lam.shape[0]
+
+    def load(self, workload):
+        self.load_scene(workload.scene)
+        self.set_spectra(workload.spectra)
+        return self
+
+    # -- render -----------------------------------------------------------------
+    def render(self, cameras: Sequence, spp: int, depth: int, seed: int = 0, band_first: int = 0,
+               band_count: Optional[int] = None, spectral: bool = True, xyz: bool = True,
+               xyz_mode: int = _native.XYZ_BF16X3, wave_capacity: int = 0, probe_pixels=None,
+               trace_block: int = 0, ctas_per_sm: int = 0, out_spectral=None, out_xyz=None):
+        """Returns dict(spectral [P, band_count] f64 sums over samples,
+        xyz [P, 3] f32, stats, and probe_L / probe_sig [n_probe, spp, band_count]
+        when probe_pixels is given)."""
+        torch = self.torch
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        npix = sum(int(c.width) * int(c.height) for c in cameras)
+        dev = self.device
+        sp = out_spectral if out_spectral is not None else (
+            torch.empty((npix, band_count), dtype=torch.float64, device=dev) if spectral else None)
+        xz = out_xyz if out_xyz is not None else (
+            torch.empty((npix, 3), dtype=torch.float32, device=dev) if xyz else None)
+        opts = _native.RenderOpts()
+        opts.wave_capacity = wave_capacity
+        opts.xyz_mode = xyz_mode
+        opts.trace_block = trace_block
+        opts.ctas_per_sm = ctas_per_sm
+        out = {}
+        if probe_pixels is not None:
+            pp = torch.as_tensor(np.asarray(probe_pixels, np.int64), device=dev)
+            pmap = torch.full((npix,), -1, dtype=torch.int64, device=dev)
+            pmap[pp] = torch.arange(pp.shape[0], device=dev)
+            pmap32 = pmap.to(torch.int32)
+            pl = torch.zeros((pp.shape[0], spp, band_count), dtype=torch.float32, device=dev)
+            ps = torch.zeros((pp.shape[0], spp, band_count), dtype=torch.int32, device=dev)
+            opts.probe_map_dev = pmap32.data_ptr()
+            opts.probe_L_dev = pl.data_ptr()
+            opts.probe_sig_dev = ps.data_ptr()
+            out["probe_L"] = pl
+            out["probe_sig"] = ps
+            out["_keep"] = pmap32
+        cams = _native.cameras_struct(cameras)
+        stats = _native.Stats()
+        st = self.lib.rt_render(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
+                                C.byref(opts), _ptr(sp), _ptr(xz), C.byref(stats))
+        self._check("rt_render", st)
+        out.update(spectral=sp, xyz=xz, stats=stats.as_dict())
+        return out
+
+    def render_host(self, cameras, spp, depth, seed=0, band_first=0, band_count=None, spectral=False,
+                    xyz_mode=_native.XYZ_BF16X3, wave_capacity=0, xyz_out=None, spectral_out=None):
+        """Host outputs (numpy; pinned torch tensors may be passed as outputs)."""
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        npix = sum(int(c.width) * int(c.height) for c in cameras)
+        xz = xyz_out if xyz_out is not None else np.empty((npix, 3), np.float32)
+        sp = spectral_out if spectral_out is not None else (
+            np.empty((npix, band_count), np.float64) if spectral else None)
+        addr = lambda a: None if a is None else (a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        opts = _native.RenderOpts()
+        opts.wave_capacity = wave_capacity
+        opts.xyz_mode = xyz_mode
+        cams = _native.cameras_struct(cameras)
+        stats = _native.Stats()
+        st = self.lib.rt_render_host(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
+                                     C.byref(opts), addr(sp), addr(xz), C.byref(stats))
+        self._check("rt_render_host", st)
+        return {"xyz": xz, "spectral": sp, "stats": stats.as_dict()}
+
+    # -- single steps -------------------------------------------------------------
+    def philox(self, ctr, key0: int, key1: int):
+        torch = self.torch
+        ctr = ctr.to(self.device, torch.int32).contiguous()
+        out = torch.empty_like(ctr)
+        self._check("rt_philox", self.lib.rt_philox(self._h, ctr.data_ptr(), out.data_ptr(), ctr.shape[0], key0, key1))
+        return out
+
+    def trace_closest(self, o, d):
+        torch = self.torch
+        o = torch.as_tensor(o, dtype=torch.float32, device=self.device).contiguous()
+        d = torch.as_tensor(d, dtype=torch.float32, device=self.device).contiguous()
+        n = o.shape[0]
+        t = torch.empty(n, dtype=torch.float32, device=self.device)
+        p = torch.empty(n, dtype=torch.int32, device=self.device)
+        self._check("rt_trace_closest", self.lib.rt_trace_closest(self._h, o.data_ptr(), d.data_ptr(), n,
+                                                                   t.data_ptr(), p.data_ptr()))
+        return t, p
+
+    def trace_shadow(self, o, d, band):
+        torch = self.torch
+        o = torch.as_tensor(o, dtype=torch.float32, device=self.device).contiguous()
+        d = torch.as_tensor(d, dtype=torch.float32, device=self.device).contiguous()
+        n = o.shape[0]
+        b = torch.as_tensor(np.broadcast_to(np.asarray(band, np.int32), (n,)).copy(), device=self.device)
+        T = torch.empty(n, dtype=torch.float32, device=self.device)
+        g = torch.empty(n, dtype=torch.int32, device=self.device)
+        self._check("rt_trace_shadow", self.lib.rt_trace_shadow(self._h, o.data_ptr(), d.data_ptr(), b.data_ptr(), n,
+                                                                 T.data_ptr(), g.data_ptr()))
+        return T, g
+
+    def optics(self, cos_i, n, k, lambda_nm=None, d=None):
+        torch = self.torch
+        f = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=self.device).contiguous()
+        c, nn, kk = f(cos_i), f(n), f(k)
+        cnt = c.shape[0]
+        R = torch.empty(cnt, dtype=torch.float32, device=self.device)
+        lam = f(lambda_nm) if lambda_nm is not None else None
+        dd = f(d) if d is not None else None
+        Rs = torch.empty_like(R) if lam is not None else None
+        Ts = torch.empty_like(R) if lam is not None else None
+        st = self.lib.rt_optics_eval(self._h, c.data_ptr(), nn.data_ptr(), kk.data_ptr(), _ptr(lam), _ptr(dd), cnt,
+                                     R.data_ptr(), _ptr(Rs), _ptr(Ts))
+        self._check("rt_optics_eval", st)
+        return R, Rs, Ts
+
+    def xyz(self, spectral, band_first: int, spp: int, mode: int = _native.XYZ_BF16X3):
+        torch = self.torch
+        s = spectral.to(self.device, torch.float64).contiguous()
+        out = torch.empty((s.shape[0], 3), dtype=torch.float32, device=self.device)
+        st = self.lib.rt_xyz(self._h, s.data_ptr(), s.shape[0], band_first, s.shape[1], spp, mode, out.data_ptr())
+        self._check("rt_xyz", st)
+        return out

@@ -1,0 +1,100 @@
+"""Full spectral renders through the C ABI against the CPU FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_04000_gb300 import scenes
+
+from parity import assert_parity, xyz_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1912_04000_gb300.renderer import Renderer
+    return Renderer(0)
+
+
+def _oracle(wl, **kw):
+    return oracle.OracleScene(wl.scene, wl.spectra).render(wl.cameras, wl.spp, wl.depth, wl.seed, **kw)
+
+
+@pytest.mark.parametrize("albedo,depth", [(0.5, 5), (0.9, 8)])
+def test_white_furnace(R, albedo, depth):
+    wl = scenes.furnace_box(albedo=albedo, le=1.5, depth=depth, width=24, height=20, spp=3)
+    R.load(wl)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)
+    s = out["spectral"].cpu().numpy() / wl.spp
+    np.testing.assert_allclose(s, 1.5 * (1 - albedo ** depth), rtol=2e-6)
+
+
+def test_tiny_box_full_image(R):
+    """The 12-triangle glass box at its full size: 128 x 128, 16 bands, 4 spp,
+    depth 4, seed 0 -- every pixel against the oracle."""
+    wl = scenes.tiny_box()
+    R.load(wl)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)
+    o = _oracle(wl)
+    m = assert_parity(out["xyz"].cpu().numpy(), o["xyz"], "tiny box")
+    print("tiny box parity", m)
+    # spectral sums too
+    gs = out["spectral"].cpu().numpy()
+    rel = np.abs(gs - o["spectral_sum"]).sum() / np.abs(o["spectral_sum"]).sum()
+    assert rel < 1e-5
+
+
+def test_per_path_records(R):
+    wl = scenes.tiny_box(width=40, height=30, spp=3)
+    R.load(wl)
+    pix = np.array([0, 17, 333, 600, 1199], np.int64)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, probe_pixels=pix, xyz_mode=2)
+    o = _oracle(wl, pixels=pix.astype(np.uint32), record_paths=True)
+    gL = out["probe_L"].cpu().numpy()
+    gS = out["probe_sig"].cpu().numpy().view(np.uint32)
+    same = gS == o["path_sig"]
+    assert same.mean() >= 0.99
+    np.testing.assert_allclose(gL[same], o["path_L"][same], rtol=2e-5, atol=1e-9)
+
+
+def test_band_subdomains_and_waves(R):
+    wl = scenes.tiny_box(width=48, height=40, spp=3)
+    R.load(wl)
+    full = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)
+    a = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, band_first=0, band_count=7, xyz_mode=2)
+    b = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, band_first=7, band_count=9, xyz_mode=2)
+    fs = full["spectral"].cpu().numpy()
+    assert np.array_equal(np.concatenate([a["spectral"].cpu().numpy(), b["spectral"].cpu().numpy()], 1), fs)
+    # wave size does not change any bit: each slot's samples are summed in order
+    small = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, wave_capacity=5000, xyz_mode=2)
+    assert np.array_equal(small["spectral"].cpu().numpy(), fs)
+    again = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)
+    assert np.array_equal(again["spectral"].cpu().numpy(), fs)
+    # partial XYZ of disjoint band ranges add up
+    np.testing.assert_allclose(a["xyz"].cpu().numpy() + b["xyz"].cpu().numpy(), full["xyz"].cpu().numpy(),
+                               rtol=1e-5, atol=1e-9)
+
+
+def test_nave_sampled_pixels(R):
+    """The 200k-triangle nave at its full size (1024 x 768, 81 bands, 16 spp,
+    depth 8) rendered on the GPU; a seeded sample of pixels is re-rendered
+    path by path by the oracle."""
+    wl = scenes.nave()
+    R.load(wl)
+    rng = np.random.default_rng(9)
+    pix = np.sort(rng.choice(wl.n_pixels, 48, replace=False)).astype(np.int64)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, probe_pixels=pix, xyz_mode=2)
+    o = _oracle(wl, pixels=pix.astype(np.uint32), record_paths=True)
+    gS = out["probe_sig"].cpu().numpy().view(np.uint32)
+    gL = out["probe_L"].cpu().numpy()
+    same = gS == o["path_sig"]
+    print("nave: paths with identical event signatures", same.mean())
+    assert same.mean() >= 0.99
+    np.testing.assert_allclose(gL[same], o["path_L"][same], rtol=1e-4, atol=1e-7)
+    g = out["xyz"].cpu().numpy()[pix]
+    m = xyz_parity(g, o["xyz"])
+    print("nave sampled-pixel parity", m)
+    # pixels whose paths all kept the oracle's event sequence meet the bar
+    clean = same.reshape(len(pix), -1).all(1)
+    if clean.any():
+        assert_parity(g[clean], o["xyz"][clean], "nave clean pixels")
