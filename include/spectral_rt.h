@@ -96,12 +96,18 @@ typedef struct {
   uint64_t paths;          /* spectral paths traced */
   uint64_t ext_rays;       /* closest-hit rays traced */
   uint64_t shadow_rays;    /* sun rays traced */
-  uint64_t nodes_visited;  /* only with rt_set_counting(ctx, 1) */
-  uint64_t tris_tested;    /* only with rt_set_counting(ctx, 1) */
+  uint64_t nodes_visited;  /* closest-hit BVH nodes, only with rt_set_counting(ctx, 1) */
+  uint64_t tris_tested;    /* closest-hit triangles, only with rt_set_counting(ctx, 1) */
+  uint64_t shadow_nodes_visited;  /* sun-ray BVH nodes, counting only */
+  uint64_t shadow_tris_tested;    /* sun-ray triangles, counting only */
   uint32_t waves;
   uint32_t kernel_launches;
   float ms_render;         /* device time of the path tracing (events) */
   float ms_xyz;            /* device time of the XYZ contraction (events) */
+  /* with rt_set_timing(ctx, 1): device time and launch count per stage:
+   * 0 camera rays, 1 closest hit, 2 shading + NEE, 3 sun rays, 4 XYZ */
+  float ms_stage[5];
+  uint32_t launches_stage[5];
 } rt_stats;
 
 /* Context on CUDA device `device`, enqueueing on `cuda_stream` (a
@@ -112,6 +118,9 @@ const char* rt_last_error(const rt_ctx* ctx);
 rt_status rt_set_stream(rt_ctx* ctx, void* cuda_stream);
 /* 1: traversal kernels count nodes visited and triangles tested (slower). */
 rt_status rt_set_counting(rt_ctx* ctx, int enable);
+/* 1: every kernel launch of a render is bracketed by CUDA events on the
+ * context's stream and the per-stage device times are returned in rt_stats. */
+rt_status rt_set_timing(rt_ctx* ctx, int enable);
 
 /* Scene (the paper's first actor, section 1): n_verts float3 positions in
  * metres, n_tris uint32 index triples, a material id per triangle, and per
@@ -183,6 +192,12 @@ rt_status rt_optics_eval(rt_ctx* ctx, const float* cos_dev, const float* n_dev, 
  * (spectral[p][j] / spp) * cmf_w[band_first + j][c], with mode rt_xyz_mode. */
 rt_status rt_xyz(rt_ctx* ctx, const double* spectral_dev, uint64_t n_pixels, uint32_t band_first,
                  uint32_t band_count, uint32_t spp, uint32_t mode, float* xyz_dev);
+
+/* Measurement tool: read bandwidth of the L2 cache.  Streams `bytes`
+ * (rounded down to 16; at most 96 MiB so that it stays L2-resident) `iters`
+ * times with 16-byte loads from a library-owned buffer and returns GB/s
+ * (bytes * iters / kernel time from CUDA events) in *gbs. */
+rt_status rt_probe_l2(rt_ctx* ctx, uint64_t bytes, uint32_t iters, float* gbs);
 
 #ifdef __cplusplus
 }

@@ -19,9 +19,9 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_ARG", 2: "RT_ERR_SCENE", 3: "RT_ERR_OOM",
 XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
 
 # every exported symbol of include/spectral_rt.h
-EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_load_scene",
-           "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest", "rt_trace_shadow",
-           "rt_optics_eval", "rt_xyz"]
+EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_set_timing",
+           "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
+           "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2"]
 
 
 class RtError(RuntimeError):
@@ -43,11 +43,17 @@ class RenderOpts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("paths", C.c_uint64), ("ext_rays", C.c_uint64), ("shadow_rays", C.c_uint64),
-                ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64), ("waves", C.c_uint32),
-                ("kernel_launches", C.c_uint32), ("ms_render", C.c_float), ("ms_xyz", C.c_float)]
+                ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64),
+                ("shadow_nodes_visited", C.c_uint64), ("shadow_tris_tested", C.c_uint64), ("waves", C.c_uint32),
+                ("kernel_launches", C.c_uint32), ("ms_render", C.c_float), ("ms_xyz", C.c_float),
+                ("ms_stage", C.c_float * 5), ("launches_stage", C.c_uint32 * 5)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if k in ("ms_stage", "launches_stage") else v
+        return d
 
 
 _lock = threading.Lock()
@@ -71,6 +77,8 @@ def load(path: str = LIB_PATH):
         L.rt_last_error.restype = C.c_char_p
         L.rt_set_stream.argtypes = [vp, vp]
         L.rt_set_counting.argtypes = [vp, C.c_int]
+        L.rt_set_timing.argtypes = [vp, C.c_int]
+        L.rt_probe_l2.argtypes = [vp, u64, u32, C.POINTER(C.c_float)]
         L.rt_load_scene.argtypes = [vp, vp, u32, vp, u32, vp, vp, vp, u32]
         L.rt_set_spectra.argtypes = [vp, vp, u32, vp, vp, f32, vp, vp, vp, vp, vp]
         L.rt_render.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp, vp,

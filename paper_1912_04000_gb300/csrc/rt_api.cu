@@ -53,6 +53,8 @@ struct rt_ctx {
   Totals* h_tot = nullptr;       // pinned
   uint32_t* d_status_aux = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool timing = false;
+  std::vector<cudaEvent_t> tpool;
 };
 
 namespace {
@@ -126,6 +128,44 @@ rt_status status_to_rt(rt_ctx* c, uint32_t st) {
 
 bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
+// Brackets launches with events from the context's pool; sums per stage
+// after the stream has been synchronised.
+struct EvTimer : StageTimer {
+  std::vector<cudaEvent_t>& pool;
+  size_t used = 0;
+  int open[STG_N] = {0, 0, 0, 0, 0};
+  struct Pair {
+    int stage, a, b;
+  };
+  std::vector<Pair> pairs;
+  explicit EvTimer(std::vector<cudaEvent_t>& p) : pool(p) {}
+  int next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return (int)used++;
+  }
+  void begin(int stage, cudaStream_t st) override {
+    open[stage] = next();
+    cudaEventRecord(pool[open[stage]], st);
+  }
+  void end(int stage, cudaStream_t st) override {
+    const int i = next();
+    cudaEventRecord(pool[i], st);
+    pairs.push_back({stage, open[stage], i});
+  }
+  void collect(float* ms, uint32_t* n) {
+    for (const Pair& p : pairs) {
+      float e = 0.0f;
+      cudaEventElapsedTime(&e, pool[p.a], pool[p.b]);
+      ms[p.stage] += e;
+      n[p.stage] += 1;
+    }
+  }
+};
+
 }  // namespace
 
 extern "C" {
@@ -190,6 +230,7 @@ void rt_destroy(rt_ctx* c) {
   if (c->h_tot) cudaFreeHost(c->h_tot);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->tpool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -204,6 +245,12 @@ rt_status rt_set_stream(rt_ctx* c, void* s) {
 rt_status rt_set_counting(rt_ctx* c, int enable) {
   if (rt_status e = check_ctx(c)) return e;
   c->counting = enable != 0;
+  return RT_OK;
+}
+
+rt_status rt_set_timing(rt_ctx* c, int enable) {
+  if (rt_status e = check_ctx(c)) return e;
+  c->timing = enable != 0;
   return RT_OK;
 }
 
@@ -455,13 +502,15 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   const DevScene S = dev_scene(c);
   int launches = 0;
   uint32_t waves = 0;
+  EvTimer timer(c->tpool);
+  StageTimer* tm = c->timing ? &timer : nullptr;
   CUDA_TRY(c, cudaEventRecord(c->ev[0], st));
   for (uint64_t ws = 0; ws < total; ws += cap) {
     w.n = (uint32_t)std::min<uint64_t>(cap, total - ws);
     w.s0 = (uint32_t)(ws / PB);
     w.r0 = (uint32_t)(ws % PB);
     CUDA_TRY(c, cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), st));
-    launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches);
+    launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches, tm);
     ++waves;
   }
   CUDA_TRY(c, cudaGetLastError());
@@ -472,7 +521,9 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     xw.wsplit = nullptr;
     xw.band_count = band_count;
     xw.kpad = (band_count + 15) / 16 * 16;
+    if (tm) tm->begin(STG_XYZ, st);
     launch_xyz(accum, npix, xw, spp, (int)o.xyz_mode, xyz_dev, st);
+    if (tm) tm->end(STG_XYZ, st);
     ++launches;
     CUDA_TRY(c, cudaGetLastError());
   }
@@ -487,6 +538,9 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     stats->shadow_rays = c->h_tot->shadow_rays;
     stats->nodes_visited = c->h_tot->nodes;
     stats->tris_tested = c->h_tot->tris;
+    stats->shadow_nodes_visited = c->h_tot->snodes;
+    stats->shadow_tris_tested = c->h_tot->stris;
+    if (tm) timer.collect(stats->ms_stage, stats->launches_stage);
     stats->waves = waves;
     stats->kernel_launches = (uint32_t)launches;
     cudaEventElapsedTime(&stats->ms_render, c->ev[0], c->ev[1]);
@@ -601,6 +655,30 @@ rt_status rt_xyz(rt_ctx* c, const double* spectral_dev, uint64_t n_pixels, uint3
   launch_xyz(spectral_dev, n_pixels, xw, spp, (int)mode, xyz_dev, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_probe_l2(rt_ctx* c, uint64_t bytes, uint32_t iters, float* gbs) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!gbs || bytes < 16 || bytes > (96ull << 20) || iters == 0) return fail(c, RT_ERR_ARG, "rt_probe_l2: bad argument");
+  cudaSetDevice(c->device);
+  const size_t n4 = bytes / 16;
+  float4* buf = nullptr;
+  float* sink = nullptr;
+  CUDA_TRY(c, cudaMalloc(&buf, n4 * 16));
+  CUDA_TRY(c, cudaMalloc(&sink, 16));
+  CUDA_TRY(c, cudaMemsetAsync(buf, 0, n4 * 16, c->stream));
+  launch_l2_probe(buf, n4, 2, sink, c->stream, c->sms);  // warm L2
+  CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
+  launch_l2_probe(buf, n4, (int)iters, sink, c->stream, c->sms);
+  CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+  cudaFree(buf);
+  cudaFree(sink);
+  *gbs = (float)((double)n4 * 16.0 * iters / (ms * 1e-3) / 1e9);
   return RT_OK;
 }
 

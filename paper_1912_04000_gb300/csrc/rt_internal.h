@@ -85,7 +85,15 @@ struct Counters {
 };
 
 struct Totals {
-  unsigned long long ext_rays, shadow_rays, nodes, tris;
+  unsigned long long ext_rays, shadow_rays, nodes, tris, snodes, stris;
+};
+
+// Per-stage CUDA-event timing of a render (host side, optional).
+enum Stage { STG_CAMERA = 0, STG_TRACE = 1, STG_SHADE = 2, STG_SHADOW = 3, STG_XYZ = 4, STG_N = 5 };
+struct StageTimer {
+  virtual void begin(int stage, cudaStream_t st) = 0;
+  virtual void end(int stage, cudaStream_t st) = 0;
+  virtual ~StageTimer() {}
 };
 
 // Work buffers of one wave (capacity C paths).
@@ -119,7 +127,8 @@ struct LaunchCfg {
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe,
-                 cudaStream_t st, int* launches);
+                 cudaStream_t st, int* launches, StageTimer* timer);
+void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaStream_t st, int sms);
 void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st);
 void launch_trace_closest_rays(const DevScene& S, const float* o, const float* d, uint64_t n, float* t,
                                int32_t* prim, uint32_t* status, cudaStream_t st);

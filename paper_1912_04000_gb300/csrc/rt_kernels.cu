@@ -461,9 +461,23 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WavePa
     }
   }
   if (COUNT) {
-    atomicAdd(&tot->nodes, (unsigned long long)nn);
-    atomicAdd(&tot->tris, (unsigned long long)nt);
+    atomicAdd(&tot->snodes, (unsigned long long)nn);
+    atomicAdd(&tot->stris, (unsigned long long)nt);
   }
+}
+
+// Streaming-read probe: every thread reads float4s of a buffer that fits in
+// L2, `iters` passes; the sum goes to a sink so the loads are not removed.
+__global__ void __launch_bounds__(512) k_l2_probe(const float4* __restrict__ buf, size_t n4, int iters,
+                                                  float* __restrict__ sink) {
+  float acc = 0.0f;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int it = 0; it < iters; ++it)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const float4 v = __ldcg(buf + i);
+      acc += v.x + v.y + v.z + v.w;
+    }
+  if (acc == 1.2345f) sink[0] = acc;
 }
 
 // ---- single-step kernels for parity tests --------------------------------
@@ -523,23 +537,30 @@ int grid_for(uint64_t n, int block) {
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st,
-                 int* launches) {
+                 int* launches, StageTimer* tm) {
   const bool rec = lc.record;
+  if (tm) tm->begin(STG_CAMERA, st);
   k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec);
+  if (tm) tm->end(STG_CAMERA, st);
   int nl = 1;
   for (uint32_t k = 1; k <= w.depth; ++k) {
     const float4* qin = b.q[k & 1];
     float4* qout = b.q[(k + 1) & 1];
+    if (tm) tm->begin(STG_TRACE, st);
     if (lc.counting)
       k_trace<true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status);
     else
       k_trace<false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status);
+    if (tm) tm->end(STG_TRACE, st);
+    if (tm) tm->begin(STG_SHADE, st);
     if (rec)
       k_shade<true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt,
                                                              b.cap, accum, probe, b.status);
     else
       k_shade<false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt,
                                                               b.cap, accum, probe, b.status);
+    if (tm) tm->end(STG_SHADE, st);
+    if (tm) tm->begin(STG_SHADOW, st);
     if (rec && lc.counting)
       k_shadow<true, true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe,
                                                                     b.tot, b.status);
@@ -552,6 +573,7 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
     else
       k_shadow<false, false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
                                                                       probe, b.tot, b.status);
+    if (tm) tm->end(STG_SHADOW, st);
     nl += 3;
   }
   if (launches) *launches += nl;
@@ -575,6 +597,10 @@ void launch_trace_shadow_rays(const DevScene& S, const DevSpectra& P, const floa
 void launch_optics(const float* c, const float* n, const float* k, const float* lam, const float* d, uint64_t count,
                    float* R, float* Rs, float* Ts, cudaStream_t st) {
   k_optics<<<grid_for(count, 256), 256, 0, st>>>(c, n, k, lam, d, count, R, Rs, Ts);
+}
+
+void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaStream_t st, int sms) {
+  k_l2_probe<<<sms * 4, 512, 0, st>>>(buf, n4, iters, sink);
 }
 
 int trace_blocks_per_sm(int block) {

@@ -56,6 +56,14 @@ class Renderer:
     def set_counting(self, on: bool):
         self._check("rt_set_counting", self.lib.rt_set_counting(self._h, 1 if on else 0))
 
+    def set_timing(self, on: bool):
+        self._check("rt_set_timing", self.lib.rt_set_timing(self._h, 1 if on else 0))
+
+    def probe_l2(self, nbytes: int = 48 << 20, iters: int = 50) -> float:
+        g = C.c_float()
+        self._check("rt_probe_l2", self.lib.rt_probe_l2(self._h, nbytes, iters, C.byref(g)))
+        return float(g.value)
+
     # -- scene and spectra ------------------------------------------------------
     def load_scene(self, scene):
         v = np.ascontiguousarray(scene.verts, np.float32)
