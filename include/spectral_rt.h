@@ -163,6 +163,27 @@ rt_status rt_render_host(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, ui
                          const rt_render_opts* opts, double* spectral_host, float* xyz_host,
                          rt_stats* stats);
 
+/* Same result as rt_render, for callers that may not allocate device memory
+ * (a framework that has reserved the device memory for its own pool, a fixed
+ * memory budget, or a loop that cannot take the implicit synchronisation of
+ * cudaMalloc / cudaFree).  The paper has no counterpart: this is an interface
+ * matter only.  The working memory (ray queues, hits, sun rays, per-path
+ * radiance, counters, status, camera table) comes from one array compiled
+ * into the library: 56 MiB (58,726,656 bytes), held by every GPU that loads
+ * the library until the process exits; waves are at most 524,288 paths.
+ * Limits: 1..64
+ * cameras, depth 1..64, pixels x bands below 2^32 (RT_ERR_ARG otherwise).
+ * spectral_dev (FP64 sums, [pixels][band_count]) is required; xyz_dev may be
+ * NULL.  No cudaMalloc, cudaFree or other allocating call is made.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture.  All calls share
+ * the array: counters and status are cleared by each call, and calls whose
+ * GPU work overlaps (other streams or contexts on the same device) race and
+ * give wrong results.  Synchronises the context's stream. */
+rt_status rt_render_static(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
+                           uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed, uint32_t xyz_mode,
+                           double* spectral_dev, float* xyz_dev);
+
 /* ---- single steps of the path, for parity tests and tools ---------------- */
 
 /* Philox4x32-10 (Salmon et al., SC 2011) of n counters ctr_dev[n][4] with key

@@ -21,7 +21,7 @@ XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
 # every exported symbol of include/spectral_rt.h
 EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_set_timing",
            "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
-           "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2"]
+           "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static"]
 
 
 class RtError(RuntimeError):
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
                                 C.POINTER(Stats)]
         L.rt_render_host.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp,
                                      vp, C.POINTER(Stats)]
+        L.rt_render_static.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, u32, vp, vp]
         L.rt_philox.argtypes = [vp, vp, vp, u64, u32, u32]
         L.rt_trace_closest.argtypes = [vp, vp, vp, u64, vp, vp]
         L.rt_trace_shadow.argtypes = [vp, vp, vp, vp, u64, vp, vp]

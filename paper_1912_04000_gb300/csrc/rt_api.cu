@@ -168,6 +168,31 @@ struct EvTimer : StageTimer {
 
 }  // namespace
 
+namespace srt {
+
+bool ctx_view(rt_ctx* c, CtxView* v) {
+  if (!c || c->poisoned) return false;
+  v->device = c->device;
+  v->stream = c->stream;
+  v->has_scene = c->has_scene;
+  v->has_spectra = c->has_spectra;
+  v->S = dev_scene(c);
+  v->P = c->sp;
+  v->cmfw = c->d_cmfw;
+  v->sms = c->sms;
+  v->h_cams = c->h_cams;
+  v->h_status = c->h_status;
+  return true;
+}
+
+void ctx_error(rt_ctx* c, const char* msg, bool fatal) {
+  if (!c) return;
+  c->err = msg;
+  if (fatal) c->poisoned = true;
+}
+
+}  // namespace srt
+
 extern "C" {
 
 rt_status rt_create(int device, void* cuda_stream, rt_ctx** out) {

@@ -155,4 +155,24 @@ void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t*
 int num_sms(int device);
 int trace_blocks_per_sm(int block);
 
+// Read-only view of a context for entry points defined outside rt_api.cu.
+struct CtxView {
+  int device;
+  cudaStream_t stream;
+  bool has_scene, has_spectra;
+  DevScene S;
+  DevSpectra P;
+  const float* cmfw;     // device [n_bands][3]
+  int sms;
+  DevCam* h_cams;        // pinned staging, kMaxCams entries
+  uint32_t* h_status;    // pinned
+};
+}  // namespace srt
+struct rt_ctx;
+namespace srt {
+// Fills *v; returns false for a null or poisoned context.
+bool ctx_view(rt_ctx* c, CtxView* v);
+// Records an error message on the context (and poisons it when fatal).
+void ctx_error(rt_ctx* c, const char* msg, bool fatal);
+
 }  // namespace srt
