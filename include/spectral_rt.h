@@ -89,7 +89,12 @@ typedef struct {
   float* probe_L_dev;
   uint32_t* probe_sig_dev;
   uint32_t use_graph;      /* 1: capture each wave shape once in a CUDA graph and replay it */
-  uint32_t reserved[7];
+  uint32_t trace_variant;  /* traversal loop: 0 = one node or leaf per step, 1 = while-while */
+  /* persistent traversal warps refill idle lanes from the queue once at least
+   * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
+   * lane between refill checks; 0 = library default (tuned) */
+  uint32_t trace_steps, trace_refill, shadow_steps, shadow_refill;
+  uint32_t reserved[2];
 } rt_render_opts;
 
 typedef struct {

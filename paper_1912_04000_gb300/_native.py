@@ -38,7 +38,9 @@ class Camera(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("wave_capacity", C.c_uint32), ("xyz_mode", C.c_uint32), ("trace_block", C.c_uint32),
                 ("ctas_per_sm", C.c_uint32), ("probe_map_dev", C.c_void_p), ("probe_L_dev", C.c_void_p),
-                ("probe_sig_dev", C.c_void_p), ("use_graph", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+                ("probe_sig_dev", C.c_void_p), ("use_graph", C.c_uint32), ("trace_variant", C.c_uint32),
+                ("trace_steps", C.c_uint32), ("trace_refill", C.c_uint32), ("shadow_steps", C.c_uint32),
+                ("shadow_refill", C.c_uint32), ("reserved", C.c_uint32 * 2)]
 
 
 class Stats(C.Structure):

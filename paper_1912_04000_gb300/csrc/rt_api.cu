@@ -331,14 +331,35 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     tr[3 * (size_t)i + 2] = make_float4(v[2][0], v[2][1], v[2][2], zero);
     nr[i] = make_float4(nrm64[4 * (size_t)t], nrm64[4 * (size_t)t + 1], nrm64[4 * (size_t)t + 2], matf);
   }
+  // Node boxes are padded by 2^-22 (max |coordinate| + origin offset) so that
+  // the traversal's FMA slab test, fma(plane, 1/d, -o/d), stays conservative
+  // for every origin inside the scene bounds (the rounding of o/d moves a
+  // plane by at most 2^-24 |o|).
+  const double diag = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  double mabs = 0.0;
+  for (int a = 0; a < 3; ++a) mabs = std::max(mabs, std::max(std::fabs(lo[a]), std::fabs(hi[a])));
+  const double pad = std::ldexp(mabs + 2e-4 * diag, -22);
+  auto down = [&](float v) {
+    const double x = (double)v - pad;
+    float f = (float)x;
+    while ((double)f > x) f = std::nextafter(f, -INFINITY);
+    return f;
+  };
+  auto up = [&](float v) {
+    const double x = (double)v + pad;
+    float f = (float)x;
+    while ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+  };
   std::vector<float4> nd(2 * bvh.nodes.size());
   for (size_t i = 0; i < bvh.nodes.size(); ++i) {
     const BvhNode& b = bvh.nodes[i];
     float rf, cf;
     std::memcpy(&rf, &b.ref, 4);
     std::memcpy(&cf, &b.count, 4);
-    nd[2 * i] = make_float4(b.lo[0], b.lo[1], b.lo[2], rf);
-    nd[2 * i + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], cf);
+    nd[2 * i] = make_float4(down(b.lo[0]), down(b.lo[1]), down(b.lo[2]), rf);
+    nd[2 * i + 1] = make_float4(up(b.hi[0]), up(b.hi[1]), up(b.hi[2]), cf);
   }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -433,6 +454,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   rt_render_opts o{};
   if (opts) o = *opts;
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
+  if (o.trace_variant > 1) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if ((o.probe_map_dev != nullptr) != (o.probe_L_dev != nullptr) ||
       (o.probe_map_dev != nullptr) != (o.probe_sig_dev != nullptr))
     return fail(c, RT_ERR_ARG, "rt_render: probe_map, probe_L and probe_sig go together");
@@ -514,6 +537,11 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   lc.grid_shade = c->sms * 8;
   lc.counting = c->counting;
   lc.record = o.probe_map_dev != nullptr;
+  lc.variant = (int)o.trace_variant;
+  lc.trace_steps = o.trace_steps ? (int)o.trace_steps : kDefaultTraceSteps;
+  lc.trace_refill = o.trace_refill ? (int)o.trace_refill : kDefaultTraceRefill;
+  lc.shadow_steps = o.shadow_steps ? (int)o.shadow_steps : kDefaultShadowSteps;
+  lc.shadow_refill = o.shadow_refill ? (int)o.shadow_refill : kDefaultShadowRefill;
   Probe probe{o.probe_map_dev, o.probe_L_dev, o.probe_sig_dev};
   WaveParams w{};
   w.PB = PB;

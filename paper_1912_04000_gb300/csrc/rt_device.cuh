@@ -160,32 +160,4 @@ __device__ __forceinline__ float tri_hit(const RayW& r, float3 va, float3 vb, fl
   return t > 0.0f ? t : -1.0f;
 }
 
-// Box slab test against [0, tmax].  Each slab distance is (plane - o) * inv
-// (two roundings, relative error below 2 ulp) and the far distance is widened
-// by 1 + 2 gamma_3 so that rounding never culls a box that the exact ray
-// enters (Ize, "Robust BVH ray traversal", JCGT 2(2), 2013).  Returns the
-// entry distance or -1.
-struct RayB {
-  float3 o, inv;
-};
-
-__device__ __forceinline__ RayB box_prep(float3 o, float3 d) {
-  RayB b;
-  const float tiny = 1e-20f;
-  b.o = o;
-  b.inv.x = 1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x));
-  b.inv.y = 1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y));
-  b.inv.z = 1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z));
-  return b;
-}
-
-__device__ __forceinline__ float box_enter(const RayB& r, float4 lo, float4 hi, float tmax) {
-  const float tx0 = __fmul_rn(__fsub_rn(lo.x, r.o.x), r.inv.x), tx1 = __fmul_rn(__fsub_rn(hi.x, r.o.x), r.inv.x);
-  const float ty0 = __fmul_rn(__fsub_rn(lo.y, r.o.y), r.inv.y), ty1 = __fmul_rn(__fsub_rn(hi.y, r.o.y), r.inv.y);
-  const float tz0 = __fmul_rn(__fsub_rn(lo.z, r.o.z), r.inv.z), tz1 = __fmul_rn(__fsub_rn(hi.z, r.o.z), r.inv.z);
-  const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-  const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-  return (tn <= tf * 1.0000008f) ? tn : -1.0f;
-}
-
 }  // namespace srt

@@ -117,12 +117,19 @@ struct Probe {
   uint32_t* sig;
 };
 
+// Default traversal loop parameters (set from measurements on a GB300).
+constexpr int kDefaultTraceSteps = 8, kDefaultTraceRefill = 8;
+constexpr int kDefaultShadowSteps = 4, kDefaultShadowRefill = 12;
+
 // Launchers (rt_kernels.cu).
 struct LaunchCfg {
   int grid_trace, block_trace;
   int grid_shade, block_shade;
   bool counting;
   bool record;
+  int variant;  // traversal loop: 0 = node-or-leaf steps, 1 = while-while steps
+  int trace_steps, trace_refill;    // closest hit: steps between refill checks, refill threshold
+  int shadow_steps, shadow_refill;  // sun rays: the same
 };
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,

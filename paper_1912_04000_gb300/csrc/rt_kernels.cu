@@ -56,160 +56,244 @@ __device__ __forceinline__ PathId path_id(const WaveParams& w, uint32_t pid) {
   return p;
 }
 
-// Closest hit with t > 0 over the BVH; ties in t go to the lower input id.
-template <bool COUNT>
-__device__ __forceinline__ void closest_hit(const DevScene& S, float3 o, float3 d, float& best_t, int& best_leaf,
-                                            uint32_t* status, uint32_t& n_nodes, uint32_t& n_tris) {
-  const RayW rw = ray_prep(o, d);
-  const RayB rb = box_prep(o, d);
-  best_t = INFINITY;
-  best_leaf = -1;
-  uint32_t best_id = 0xFFFFFFFFu;
-  uint2 stack[kStack];
-  int sp = 0;
+// ---------------------------------------------------------------------------
+// BVH traversal as a resumable per-lane state machine.  One call of a step
+// function visits one interior node (both children tested, the far one
+// pushed) or one leaf, then pops if needed; it returns true when the ray is
+// finished.  The persistent kernels below interleave steps with refills of
+// idle lanes, so a warp never waits for its longest ray with most lanes idle.
+//
+// FMA selects the box test: false = (plane - o) * inv (any origin); true =
+// fma(plane, inv, -o * inv), valid for origins within the scene bounds
+// because rt_load_scene pads every node box by 2^-22 (max |coordinate| + eps),
+// which covers the rounding of o * inv; the far distance is widened by
+// 1 + 2^-21 for the relative rounding of both distances.
+// ---------------------------------------------------------------------------
+struct Trav {
+  RayW rw;
+  float3 inv, oinv;
+  float best_t;
+  uint32_t best_id;
+  int best_leaf;
+  uint32_t ref, cnt;
+  int sp;
+  uint32_t iter;
+};
+
+template <bool FMA>
+__device__ __forceinline__ float box_t(const Trav& tv, float4 lo, float4 hi, float tmax) {
+  float tx0, tx1, ty0, ty1, tz0, tz1;
+  if (FMA) {
+    tx0 = fmaf(lo.x, tv.inv.x, -tv.oinv.x);
+    tx1 = fmaf(hi.x, tv.inv.x, -tv.oinv.x);
+    ty0 = fmaf(lo.y, tv.inv.y, -tv.oinv.y);
+    ty1 = fmaf(hi.y, tv.inv.y, -tv.oinv.y);
+    tz0 = fmaf(lo.z, tv.inv.z, -tv.oinv.z);
+    tz1 = fmaf(hi.z, tv.inv.z, -tv.oinv.z);
+  } else {
+    // oinv holds the origin itself in this mode
+    tx0 = __fmul_rn(__fsub_rn(lo.x, tv.oinv.x), tv.inv.x);
+    tx1 = __fmul_rn(__fsub_rn(hi.x, tv.oinv.x), tv.inv.x);
+    ty0 = __fmul_rn(__fsub_rn(lo.y, tv.oinv.y), tv.inv.y);
+    ty1 = __fmul_rn(__fsub_rn(hi.y, tv.oinv.y), tv.inv.y);
+    tz0 = __fmul_rn(__fsub_rn(lo.z, tv.oinv.z), tv.inv.z);
+    tz1 = __fmul_rn(__fsub_rn(hi.z, tv.oinv.z), tv.inv.z);
+  }
+  const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+  const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  return (tn <= tf * 1.0000005f) ? tn : -1.0f;
+}
+
+// Starts a ray; returns false if it misses the root box (finished).
+template <bool FMA>
+__device__ __forceinline__ bool trav_init(Trav& tv, const DevScene& S, float3 o, float3 d) {
+  tv.rw = ray_prep(o, d);
+  const float tiny = 1e-20f;
+  tv.inv.x = 1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x));
+  tv.inv.y = 1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y));
+  tv.inv.z = 1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z));
+  tv.oinv = FMA ? make_float3(o.x * tv.inv.x, o.y * tv.inv.y, o.z * tv.inv.z) : o;
+  tv.best_t = INFINITY;
+  tv.best_id = 0xFFFFFFFFu;
+  tv.best_leaf = -1;
+  tv.sp = 0;
+  tv.iter = 0;
   const float4 rlo = ldg4(S.nodes + 2), rhi = ldg4(S.nodes + 3);
-  if (box_enter(rb, rlo, rhi, INFINITY) < 0.0f) return;
-  uint32_t ref = __float_as_uint(rlo.w), cnt = __float_as_uint(rhi.w);
-  const uint32_t cap = 4u * S.n_nodes + 64u;
-  uint32_t iter = 0;
-  for (;;) {
-    if (++iter > cap) {
-      atomicOr(status, ST_ITER);
-      return;
+  tv.ref = __float_as_uint(rlo.w);
+  tv.cnt = __float_as_uint(rhi.w);
+  return box_t<FMA>(tv, rlo, rhi, INFINITY) >= 0.0f;
+}
+
+// Interior node: test both children of pair ref, descend into the nearer,
+// push the farther.  Returns false if neither child is entered.
+template <bool FMA, bool COUNT>
+__device__ __forceinline__ bool trav_interior(Trav& tv, uint2* stack, const DevScene& S, float tmax, uint32_t* status,
+                                              uint32_t& n_nodes) {
+  const float4* c = S.nodes + 2u * tv.ref;
+  const float4 alo = ldg4(c), ahi = ldg4(c + 1), blo = ldg4(c + 2), bhi = ldg4(c + 3);
+  if (COUNT) n_nodes += 2;
+  const float ta = box_t<FMA>(tv, alo, ahi, tmax);
+  const float tb = box_t<FMA>(tv, blo, bhi, tmax);
+  // branch-free: descend into the nearer entered child; the farther one is
+  // written to the stack unconditionally and kept only when both are entered
+  const bool ha = ta >= 0.0f, hb = tb >= 0.0f;
+  const bool an = ha && (!hb || ta <= tb);
+  const bool both = ha && hb;
+  if (both && tv.sp >= kStack) {
+    atomicOr(status, ST_STACK);
+    tv.sp = 0;
+    return false;
+  }
+  const uint32_t fref = __float_as_uint(an ? blo.w : alo.w), fcnt = __float_as_uint(an ? bhi.w : ahi.w);
+  stack[min(tv.sp, kStack - 1)] = make_uint2((fref << 3) | fcnt, __float_as_uint(an ? tb : ta));
+  tv.sp += both ? 1 : 0;
+  tv.ref = __float_as_uint(an ? alo.w : blo.w);
+  tv.cnt = __float_as_uint(an ? ahi.w : bhi.w);
+  return ha || hb;
+}
+
+// Pops the next stack entry whose entry distance is within tmax; false when
+// the stack is empty (traversal finished).
+__device__ __forceinline__ bool trav_pop(Trav& tv, const uint2* stack, float tmax) {
+  while (tv.sp > 0) {
+    const uint2 e = stack[--tv.sp];
+    if (__uint_as_float(e.y) <= tmax) {
+      tv.ref = e.x >> 3;
+      tv.cnt = e.x & 7u;
+      return true;
     }
-    if (cnt == 0u) {
-      const float4* c = S.nodes + 2u * ref;
-      const float4 alo = ldg4(c), ahi = ldg4(c + 1), blo = ldg4(c + 2), bhi = ldg4(c + 3);
-      if (COUNT) n_nodes += 2;
-      const float ta = box_enter(rb, alo, ahi, best_t);
-      const float tb = box_enter(rb, blo, bhi, best_t);
-      if (ta >= 0.0f && tb >= 0.0f) {
-        const bool af = ta <= tb;
-        if (sp >= kStack) {
-          atomicOr(status, ST_STACK);
-          return;
-        }
-        const float4 flo = af ? blo : alo, fhi = af ? bhi : ahi;
-        stack[sp++] = make_uint2((__float_as_uint(flo.w) << 3) | __float_as_uint(fhi.w), __float_as_uint(af ? tb : ta));
-        ref = __float_as_uint(af ? alo.w : blo.w);
-        cnt = __float_as_uint(af ? ahi.w : bhi.w);
-        continue;
-      }
-      if (ta >= 0.0f) {
-        ref = __float_as_uint(alo.w);
-        cnt = __float_as_uint(ahi.w);
-        continue;
-      }
-      if (tb >= 0.0f) {
-        ref = __float_as_uint(blo.w);
-        cnt = __float_as_uint(bhi.w);
-        continue;
-      }
-    } else {
-      for (uint32_t t = ref; t < ref + cnt; ++t) {
-        const float4* tr = S.tris + 3u * t;
-        const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
-        if (COUNT) ++n_tris;
-        const float th = tri_hit(rw, f3(v0), f3(v1), f3(v2));
-        const uint32_t id = __float_as_uint(v0.w);
-        if (th > 0.0f && (th < best_t || (th == best_t && id < best_id))) {
-          best_t = th;
-          best_leaf = (int)t;
-          best_id = id;
-        }
-      }
+  }
+  return false;
+}
+
+__device__ __forceinline__ void closest_leaf(Trav& tv, const DevScene& S, uint32_t& n_tris, bool count) {
+  for (uint32_t t = tv.ref; t < tv.ref + tv.cnt; ++t) {
+    const float4* tr = S.tris + 3u * t;
+    const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
+    if (count) ++n_tris;
+    const float th = tri_hit(tv.rw, f3(v0), f3(v1), f3(v2));
+    const uint32_t id = __float_as_uint(v0.w);
+    if (th > 0.0f && (th < tv.best_t || (th == tv.best_t && id < tv.best_id))) {
+      tv.best_t = th;
+      tv.best_leaf = (int)t;
+      tv.best_id = id;
     }
-    bool found = false;
-    while (sp > 0) {
-      const uint2 e = stack[--sp];
-      if (__uint_as_float(e.y) <= best_t) {
-        ref = e.x >> 3;
-        cnt = e.x & 7u;
-        found = true;
-        break;
-      }
-    }
-    if (!found) return;
   }
 }
 
-// Transmittance of a sun ray to infinity (section 4, Eq. 3 visibility term
-// through thin glass).  n_glass = sheets crossed, or 0xFFFFFFFF if blocked.
-template <bool COUNT>
+// One closest-hit step (t > 0; ties in t go to the lower input id).  With WW
+// (Aila and Laine's while-while form) the step runs interior nodes until the
+// lane reaches a leaf, then that leaf, so that a warp's lanes execute the same
+// phase together.
+template <bool FMA, bool COUNT, bool WW>
+__device__ __forceinline__ bool closest_step(Trav& tv, uint2* stack, const DevScene& S, uint32_t cap,
+                                             uint32_t* status, uint32_t& n_nodes, uint32_t& n_tris) {
+  if (WW) {
+    while (tv.cnt == 0u) {
+      if (++tv.iter > cap) {
+        atomicOr(status, ST_ITER);
+        return true;
+      }
+      if (!trav_interior<FMA, COUNT>(tv, stack, S, tv.best_t, status, n_nodes) && !trav_pop(tv, stack, tv.best_t))
+        return true;
+    }
+    closest_leaf(tv, S, n_tris, COUNT);
+    return !trav_pop(tv, stack, tv.best_t);
+  }
+  if (++tv.iter > cap) {
+    atomicOr(status, ST_ITER);
+    return true;
+  }
+  if (tv.cnt == 0u) {
+    if (trav_interior<FMA, COUNT>(tv, stack, S, tv.best_t, status, n_nodes)) return false;
+  } else {
+    closest_leaf(tv, S, n_tris, COUNT);
+  }
+  return !trav_pop(tv, stack, tv.best_t);
+}
+
+// Sun-ray leaf: product of thin-glass T_s over every crossed sheet; returns
+// true at the first opaque triangle (T = 0, n_glass = 0xFFFFFFFF).
+__device__ __forceinline__ bool shadow_leaf(Trav& tv, const DevScene& S, const DevSpectra& P, float3 d, uint32_t band,
+                                            float& T, uint32_t& ng, uint32_t& n_tris, bool count) {
+  for (uint32_t t = tv.ref; t < tv.ref + tv.cnt; ++t) {
+    const float4* tr = S.tris + 3u * t;
+    const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
+    if (count) ++n_tris;
+    const float th = tri_hit(tv.rw, f3(v0), f3(v1), f3(v2));
+    if (th > 0.0f) {
+      const uint32_t mat = __float_as_uint(v1.w);
+      if (__ldg(P.mtype + mat) != 1) {
+        T = 0.0f;
+        ng = 0xFFFFFFFFu;
+        return true;
+      }
+      const float4 nr = ldg4(S.nrm + t);
+      const float c = fabsf(dot(d, f3(nr)));
+      const float4 m = ldg4(P.mb + mat * P.n_bands + band);
+      float Rs, Ts;
+      thin_sheet(c, m.x, m.y, __ldg(P.ad + mat * P.n_bands + band), Rs, Ts);
+      T *= Ts;
+      ++ng;
+    }
+  }
+  return false;
+}
+
+// One sun-ray step (WW as for closest_step).
+template <bool FMA, bool COUNT, bool WW>
+__device__ __forceinline__ bool shadow_step(Trav& tv, uint2* stack, const DevScene& S, const DevSpectra& P, float3 d,
+                                            uint32_t band, float& T, uint32_t& ng, uint32_t cap, uint32_t* status,
+                                            uint32_t& n_nodes, uint32_t& n_tris) {
+  if (WW) {
+    while (tv.cnt == 0u) {
+      if (++tv.iter > cap) {
+        atomicOr(status, ST_ITER);
+        return true;
+      }
+      if (!trav_interior<FMA, COUNT>(tv, stack, S, INFINITY, status, n_nodes) && !trav_pop(tv, stack, INFINITY))
+        return true;
+    }
+    if (shadow_leaf(tv, S, P, d, band, T, ng, n_tris, COUNT)) return true;
+    return !trav_pop(tv, stack, INFINITY);
+  }
+  if (++tv.iter > cap) {
+    atomicOr(status, ST_ITER);
+    return true;
+  }
+  if (tv.cnt == 0u) {
+    if (trav_interior<FMA, COUNT>(tv, stack, S, INFINITY, status, n_nodes)) return false;
+  } else {
+    if (shadow_leaf(tv, S, P, d, band, T, ng, n_tris, COUNT)) return true;
+  }
+  return !trav_pop(tv, stack, INFINITY);
+}
+
+__device__ __forceinline__ uint32_t trav_cap(const DevScene& S) { return 4u * S.n_nodes + 64u; }
+
+// Whole-ray helpers for the single-step entry points (any origin).
+__device__ __forceinline__ void closest_hit(const DevScene& S, float3 o, float3 d, float& best_t, int& best_leaf,
+                                            uint32_t* status) {
+  Trav tv;
+  uint2 stack[kStack];
+  uint32_t a = 0, b = 0;
+  if (trav_init<false>(tv, S, o, d))
+    while (!closest_step<false, false, false>(tv, stack, S, trav_cap(S), status, a, b)) {
+    }
+  best_t = tv.best_t;
+  best_leaf = tv.best_leaf;
+}
+
 __device__ __forceinline__ float shadow_T(const DevScene& S, const DevSpectra& P, float3 o, float3 d, uint32_t band,
-                                          uint32_t& n_glass, uint32_t* status, uint32_t& n_nodes, uint32_t& n_tris) {
-  const RayW rw = ray_prep(o, d);
-  const RayB rb = box_prep(o, d);
+                                          uint32_t& n_glass, uint32_t* status) {
+  Trav tv;
+  uint2 stack[kStack];
+  uint32_t a = 0, b = 0;
   float T = 1.0f;
   uint32_t ng = 0;
-  uint32_t stack[kStack];
-  int sp = 0;
-  const float4 rlo = ldg4(S.nodes + 2), rhi = ldg4(S.nodes + 3);
-  n_glass = 0;
-  if (box_enter(rb, rlo, rhi, INFINITY) < 0.0f) return 1.0f;
-  uint32_t ref = __float_as_uint(rlo.w), cnt = __float_as_uint(rhi.w);
-  const uint32_t cap = 4u * S.n_nodes + 64u;
-  uint32_t iter = 0;
-  for (;;) {
-    if (++iter > cap) {
-      atomicOr(status, ST_ITER);
-      break;
+  if (trav_init<false>(tv, S, o, d))
+    while (!shadow_step<false, false, false>(tv, stack, S, P, d, band, T, ng, trav_cap(S), status, a, b)) {
     }
-    if (cnt == 0u) {
-      const float4* c = S.nodes + 2u * ref;
-      const float4 alo = ldg4(c), ahi = ldg4(c + 1), blo = ldg4(c + 2), bhi = ldg4(c + 3);
-      if (COUNT) n_nodes += 2;
-      const float ta = box_enter(rb, alo, ahi, INFINITY);
-      const float tb = box_enter(rb, blo, bhi, INFINITY);
-      if (ta >= 0.0f && tb >= 0.0f) {
-        const bool af = ta <= tb;
-        if (sp >= kStack) {
-          atomicOr(status, ST_STACK);
-          break;
-        }
-        const float4 flo = af ? blo : alo, fhi = af ? bhi : ahi;
-        stack[sp++] = (__float_as_uint(flo.w) << 3) | __float_as_uint(fhi.w);
-        ref = __float_as_uint(af ? alo.w : blo.w);
-        cnt = __float_as_uint(af ? ahi.w : bhi.w);
-        continue;
-      }
-      if (ta >= 0.0f) {
-        ref = __float_as_uint(alo.w);
-        cnt = __float_as_uint(ahi.w);
-        continue;
-      }
-      if (tb >= 0.0f) {
-        ref = __float_as_uint(blo.w);
-        cnt = __float_as_uint(bhi.w);
-        continue;
-      }
-    } else {
-      for (uint32_t t = ref; t < ref + cnt; ++t) {
-        const float4* tr = S.tris + 3u * t;
-        const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
-        if (COUNT) ++n_tris;
-        const float th = tri_hit(rw, f3(v0), f3(v1), f3(v2));
-        if (th > 0.0f) {
-          const uint32_t mat = __float_as_uint(v1.w);
-          if (__ldg(P.mtype + mat) != 1) {
-            n_glass = 0xFFFFFFFFu;
-            return 0.0f;
-          }
-          const float4 nr = ldg4(S.nrm + t);
-          const float c = fabsf(dot(d, f3(nr)));
-          const float4 m = ldg4(P.mb + mat * P.n_bands + band);
-          float Rs, Ts;
-          thin_sheet(c, m.x, m.y, __ldg(P.ad + mat * P.n_bands + band), Rs, Ts);
-          T *= Ts;
-          ++ng;
-        }
-      }
-    }
-    if (sp == 0) break;
-    const uint32_t e = stack[--sp];
-    ref = e >> 3;
-    cnt = e & 7u;
-  }
   n_glass = ng;
   return T;
 }
@@ -257,26 +341,58 @@ __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams,
   }
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
+constexpr uint32_t kNoRay = 0xFFFFFFFFu;
+
+// Persistent traversal loop: a warp refills its idle lanes from the queue
+// once at least `refill` lanes are idle, and each lane with a ray runs up to
+// `steps` traversal steps between refill checks (steps large and refill 32
+// give one batch of 32 rays per warp at a time).
+
+template <bool FMA, bool COUNT, bool WW>
+__global__ void __launch_bounds__(128) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
-                                               uint32_t* status) {
+                                               uint32_t* status, int steps, int refill) {
   const uint32_t count = min(cnt[k].q_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->ext_rays, (unsigned long long)count);
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t icap = trav_cap(S);
   uint32_t nn = 0, nt = 0;
+  Trav tv;
+  uint2 stack[kStack];
+  uint32_t ray = kNoRay;
+  bool drained = count == 0u;
   for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&cnt[k].q_fetch, 32u);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= count) break;
-    const uint32_t i = base + lane;
-    if (i < count) {
-      const float4 a = __ldcs(q + 2 * i), b = __ldcs(q + 2 * i + 1);
-      float t;
-      int leaf;
-      closest_hit<COUNT>(S, f3(a), f3(b), t, leaf, status, nn, nt);
-      __stcs(hit + i, make_float2(t, __int_as_float(leaf)));
+    const uint32_t idle = __ballot_sync(0xffffffffu, ray == kNoRay);
+    if (!drained && (int)__popc(idle) >= refill) {
+      const uint32_t n = __popc(idle);
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&cnt[k].q_fetch, n);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base + n >= count) drained = true;
+      if (ray == kNoRay) {
+        const uint32_t slot = base + __popc(idle & lt);
+        if (slot < count) {
+          const float4 a = __ldcs(q + 2 * slot), b = __ldcs(q + 2 * slot + 1);
+          if (trav_init<FMA>(tv, S, f3(a), f3(b))) {
+            ray = slot;
+          } else {
+            __stcs(hit + slot, make_float2(-1.0f, __int_as_float(-1)));
+          }
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, ray != kNoRay)) {
+      if (drained) break;
+      continue;
+    }
+    if (ray != kNoRay) {
+      bool done = false;
+      for (int i = 0; i < steps && !done; ++i) done = closest_step<FMA, COUNT, WW>(tv, stack, S, icap, status, nn, nt);
+      if (done) {
+        __stcs(hit + ray, make_float2(tv.best_leaf < 0 ? -1.0f : tv.best_t, __int_as_float(tv.best_leaf)));
+        ray = kNoRay;
+      }
     }
   }
   if (COUNT) {
@@ -426,30 +542,61 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
   }
 }
 
-template <bool RECORD, bool COUNT>
-__global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+template <bool RECORD, bool COUNT, bool WW>
+__global__ void __launch_bounds__(128) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
-                                                uint32_t* status) {
+                                                uint32_t* status, int steps, int refill) {
   const uint32_t count = min(cnt[k].s_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t icap = trav_cap(S);
   uint32_t nn = 0, nt = 0;
+  Trav tv;
+  uint2 stack[kStack];
+  uint32_t ray = kNoRay, bits = 0, band = 0, ng = 0;
+  float contrib = 0.0f, T = 1.0f;
+  float3 dir = make_float3(0.0f, 0.0f, 0.0f);
+  bool drained = count == 0u;
   for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&cnt[k].s_fetch, 32u);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= count) break;
-    const uint32_t i = base + lane;
-    if (i < count) {
-      const float4 a = __ldcs(sq + 2 * i), b = __ldcs(sq + 2 * i + 1);
-      const uint32_t bits = __float_as_uint(a.w);
+    const uint32_t idle = __ballot_sync(0xffffffffu, ray == kNoRay);
+    if (!drained && (int)__popc(idle) >= refill) {
+      const uint32_t n = __popc(idle);
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&cnt[k].s_fetch, n);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base + n >= count) drained = true;
+      if (ray == kNoRay) {
+        const uint32_t slot = base + __popc(idle & lt);
+        if (slot < count) {
+          const float4 a = __ldcs(sq + 2 * slot), b = __ldcs(sq + 2 * slot + 1);
+          ray = slot;
+          bits = __float_as_uint(a.w);
+          contrib = b.w;
+          dir = f3(b);
+          band = w.band_first + path_id(w, bits & kPidMask).j;
+          T = 1.0f;
+          ng = 0;
+          if (!trav_init<true>(tv, S, f3(a), dir)) tv.sp = -1;  // misses everything: finished
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, ray != kNoRay)) {
+      if (drained) break;
+      continue;
+    }
+    bool done = false;
+    if (ray != kNoRay) {
+      done = tv.sp < 0;
+      for (int i = 0; i < steps && !done; ++i)
+        done = shadow_step<true, COUNT, WW>(tv, stack, S, P, dir, band, T, ng, icap, status, nn, nt);
+    }
+    if (done) {
       const uint32_t pid = bits & kPidMask;
       const PathId id = path_id(w, pid);
-      uint32_t ng;
-      const float Tr = shadow_T<COUNT>(S, P, f3(a), f3(b), w.band_first + id.j, ng, status, nn, nt);
-      const float Lp = Lbuf[pid] + b.w * Tr;
+      const float Lp = Lbuf[pid] + contrib * T;
       uint32_t sg = 0;
       if (RECORD) sg = mix_sig(sigbuf[pid], ng);
       if (bits & kFlagTerm) {
@@ -458,6 +605,7 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WavePa
         Lbuf[pid] = Lp;
         if (RECORD) sigbuf[pid] = sg;
       }
+      ray = kNoRay;
     }
   }
   if (COUNT) {
@@ -492,9 +640,8 @@ __global__ void k_closest_rays(DevScene S, const float* __restrict__ o, const fl
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     float t;
     int leaf;
-    uint32_t a = 0, b = 0;
-    closest_hit<false>(S, make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]),
-                       make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]), t, leaf, status, a, b);
+    closest_hit(S, make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
+                t, leaf, status);
     tout[i] = leaf < 0 ? -1.0f : t;
     prim[i] = leaf < 0 ? -1 : (int32_t)__float_as_uint(S.tris[3 * leaf].w);
   }
@@ -504,9 +651,9 @@ __global__ void k_shadow_rays(DevScene S, DevSpectra P, const float* __restrict_
                               const uint32_t* __restrict__ band, uint64_t n, float* __restrict__ T,
                               uint32_t* __restrict__ ng, uint32_t* status) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t a = 0, b = 0, g;
-    T[i] = shadow_T<false>(S, P, make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]),
-                           make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]), band[i], g, status, a, b);
+    uint32_t g;
+    T[i] = shadow_T(S, P, make_float3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), make_float3(d[3 * i], d[3 * i + 1], d[3 * i + 2]),
+                    band[i], g, status);
     ng[i] = g;
   }
 }
@@ -533,6 +680,44 @@ int grid_for(uint64_t n, int block) {
   return (int)(g == 0 ? 1 : g);
 }
 
+template <bool FMA, bool COUNT, bool WW>
+void trace_t(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k, cudaStream_t st) {
+  k_trace<FMA, COUNT, WW><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status,
+                                                                   lc.trace_steps, lc.trace_refill);
+}
+
+void launch_trace(const LaunchCfg& lc, bool robust, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
+                  cudaStream_t st) {
+  const bool ww = lc.variant == 1;
+  if (robust) {
+    if (lc.counting) ww ? trace_t<false, true, true>(lc, S, qin, b, k, st) : trace_t<false, true, false>(lc, S, qin, b, k, st);
+    else ww ? trace_t<false, false, true>(lc, S, qin, b, k, st) : trace_t<false, false, false>(lc, S, qin, b, k, st);
+  } else {
+    if (lc.counting) ww ? trace_t<true, true, true>(lc, S, qin, b, k, st) : trace_t<true, true, false>(lc, S, qin, b, k, st);
+    else ww ? trace_t<true, false, true>(lc, S, qin, b, k, st) : trace_t<true, false, false>(lc, S, qin, b, k, st);
+  }
+}
+
+template <bool RECORD, bool COUNT, bool WW>
+void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
+              const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st) {
+  k_shadow<RECORD, COUNT, WW><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
+                                                                      probe, b.tot, b.status, lc.shadow_steps,
+                                                                      lc.shadow_refill);
+}
+
+void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
+                   const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st) {
+  const bool ww = lc.variant == 1;
+  if (lc.record) {
+    if (lc.counting) ww ? shadow_t<true, true, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<true, true, false>(lc, S, P, w, k, b, accum, probe, st);
+    else ww ? shadow_t<true, false, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<true, false, false>(lc, S, P, w, k, b, accum, probe, st);
+  } else {
+    if (lc.counting) ww ? shadow_t<false, true, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<false, true, false>(lc, S, P, w, k, b, accum, probe, st);
+    else ww ? shadow_t<false, false, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<false, false, false>(lc, S, P, w, k, b, accum, probe, st);
+  }
+}
+
 }  // namespace
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
@@ -547,10 +732,9 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
     const float4* qin = b.q[k & 1];
     float4* qout = b.q[(k + 1) & 1];
     if (tm) tm->begin(STG_TRACE, st);
-    if (lc.counting)
-      k_trace<true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status);
-    else
-      k_trace<false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status);
+    // vertex 1 starts at the cameras, which may lie anywhere: robust box
+    // test; later origins are surface points inside the padded bounds
+    launch_trace(lc, k == 1, S, qin, b, k, st);
     if (tm) tm->end(STG_TRACE, st);
     if (tm) tm->begin(STG_SHADE, st);
     if (rec)
@@ -561,18 +745,7 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
                                                               b.cap, accum, probe, b.status);
     if (tm) tm->end(STG_SHADE, st);
     if (tm) tm->begin(STG_SHADOW, st);
-    if (rec && lc.counting)
-      k_shadow<true, true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe,
-                                                                    b.tot, b.status);
-    else if (rec)
-      k_shadow<true, false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
-                                                                     probe, b.tot, b.status);
-    else if (lc.counting)
-      k_shadow<false, true><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
-                                                                     probe, b.tot, b.status);
-    else
-      k_shadow<false, false><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
-                                                                      probe, b.tot, b.status);
+    launch_shadow(lc, S, P, w, k, b, accum, probe, st);
     if (tm) tm->end(STG_SHADOW, st);
     nl += 3;
   }
@@ -605,8 +778,8 @@ void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaS
 
 int trace_blocks_per_sm(int block) {
   int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<false>, block, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false, false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<true, false, false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false, false, false>, block, 0);
   const int m = a < b ? a : b;
   return m > 0 ? m : 1;
 }

@@ -179,6 +179,11 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   lc.grid_shade = v.sms * 8;
   lc.counting = false;
   lc.record = false;
+  lc.variant = 0;
+  lc.trace_steps = kDefaultTraceSteps;
+  lc.trace_refill = kDefaultTraceRefill;
+  lc.shadow_steps = kDefaultShadowSteps;
+  lc.shadow_refill = kDefaultShadowRefill;
   const Probe probe{nullptr, nullptr, nullptr};
   WaveParams w{};
   w.PB = PB;

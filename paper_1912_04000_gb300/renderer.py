@@ -95,7 +95,8 @@ class Renderer:
     def render(self, cameras: Sequence, spp: int, depth: int, seed: int = 0, band_first: int = 0,
                band_count: Optional[int] = None, spectral: bool = True, xyz: bool = True,
                xyz_mode: int = _native.XYZ_BF16X3, wave_capacity: int = 0, probe_pixels=None,
-               trace_block: int = 0, ctas_per_sm: int = 0, out_spectral=None, out_xyz=None):
+               trace_block: int = 0, ctas_per_sm: int = 0, out_spectral=None, out_xyz=None, trace_variant: int = 0,
+               trace_steps: int = 0, trace_refill: int = 0, shadow_steps: int = 0, shadow_refill: int = 0):
         """Returns dict(spectral [P, band_count] f64 sums over samples,
         xyz [P, 3] f32, stats, and probe_L / probe_sig [n_probe, spp, band_count]
         when probe_pixels is given)."""
@@ -113,6 +114,9 @@ class Renderer:
         opts.xyz_mode = xyz_mode
         opts.trace_block = trace_block
         opts.ctas_per_sm = ctas_per_sm
+        opts.trace_variant = trace_variant
+        opts.trace_steps, opts.trace_refill = trace_steps, trace_refill
+        opts.shadow_steps, opts.shadow_refill = shadow_steps, shadow_refill
         out = {}
         if probe_pixels is not None:
             pp = torch.as_tensor(np.asarray(probe_pixels, np.int64), device=dev)
