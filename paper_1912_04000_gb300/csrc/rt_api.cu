@@ -454,6 +454,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   rt_render_opts o{};
   if (opts) o = *opts;
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
+  if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
+    return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
   if (o.trace_variant > 1) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if ((o.probe_map_dev != nullptr) != (o.probe_L_dev != nullptr) ||
@@ -513,6 +515,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   cap = std::min<uint32_t>(std::min<uint32_t>(cap, kMaxWave), PB);
   cap = std::max<uint32_t>(cap, 1u);
   if (rt_status e = ensure_wave(c, cap)) return e;
+  if (spectral_dev && ((uintptr_t)spectral_dev & 15u) != 0)
+    return fail(c, RT_ERR_ARG, "rt_render: spectral_dev must be 16-byte aligned");
   double* accum = spectral_dev;
   if (!accum) {
     if (c->accum_cap < PB64) {
@@ -575,7 +579,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     xw.band_count = band_count;
     xw.kpad = (band_count + 15) / 16 * 16;
     if (tm) tm->begin(STG_XYZ, st);
-    launch_xyz(accum, npix, xw, spp, (int)o.xyz_mode, xyz_dev, st);
+    launch_xyz(accum, npix, xw, spp, (int)o.xyz_mode, xyz_dev, st, c->wb.status, c->sms);
     if (tm) tm->end(STG_XYZ, st);
     ++launches;
     CUDA_TRY(c, cudaGetLastError());
@@ -698,17 +702,22 @@ rt_status rt_xyz(rt_ctx* c, const double* spectral_dev, uint64_t n_pixels, uint3
   if (!spectral_dev || !xyz_dev || spp == 0 || band_count == 0 || band_first + band_count > c->sp.n_bands ||
       mode > 2)
     return fail(c, RT_ERR_ARG, "rt_xyz: bad argument");
+  if (mode != 2 && band_count > kXyzMaxBandsTc)
+    return fail(c, RT_ERR_ARG, "rt_xyz: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
+  if (((uintptr_t)spectral_dev & 15u) != 0) return fail(c, RT_ERR_ARG, "rt_xyz: spectral_dev must be 16-byte aligned");
   if (n_pixels == 0) return RT_OK;
   cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), c->stream));
   XyzWeights xw;
   xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
   xw.wsplit = nullptr;
   xw.band_count = band_count;
   xw.kpad = (band_count + 15) / 16 * 16;
-  launch_xyz(spectral_dev, n_pixels, xw, spp, (int)mode, xyz_dev, c->stream);
+  launch_xyz(spectral_dev, n_pixels, xw, spp, (int)mode, xyz_dev, c->stream, c->wb.status, c->sms);
   CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return RT_OK;
+  return status_to_rt(c, *c->h_status);
 }
 
 rt_status rt_probe_l2(rt_ctx* c, uint64_t bytes, uint32_t iters, float* gbs) {

@@ -154,8 +154,11 @@ struct XyzWeights {
   uint32_t band_count;
   uint32_t kpad;           // band_count rounded up to 16
 };
+// Tensor-core modes keep all K-slices of a 128-pixel tile in shared memory:
+// at most kXyzMaxBandsTc bands.
+constexpr uint32_t kXyzMaxBandsTc = 192;
 void launch_xyz(const double* spectral, uint64_t n_pixels, const XyzWeights& w, uint32_t spp, int mode, float* xyz,
-                cudaStream_t st);
+                cudaStream_t st, uint32_t* status, int sms);
 size_t xyz_wsplit_elems(uint32_t band_count);
 void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t* wsplit_host);
 

@@ -94,6 +94,10 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   if (depth == 0 || depth > (uint32_t)kMaxDepth)
     return err(c, RT_ERR_ARG, "rt_render_static: depth must be 1..64 (counter rows in the static array)");
   if (xyz_mode > 2) return err(c, RT_ERR_ARG, "rt_render_static: unknown xyz_mode");
+  if (xyz_mode != 2 && band_count > kXyzMaxBandsTc)
+    return err(c, RT_ERR_ARG, "rt_render_static: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
+  if (((uintptr_t)spectral_dev & 15u) != 0)
+    return err(c, RT_ERR_ARG, "rt_render_static: spectral_dev must be 16-byte aligned");
   uint64_t npix = 0;
   for (uint32_t i = 0; i < n_cams; ++i) {
     const rt_camera& cm = cams[i];
@@ -208,7 +212,7 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
     xw.wsplit = nullptr;
     xw.band_count = band_count;
     xw.kpad = (band_count + 15) / 16 * 16;
-    launch_xyz(spectral_dev, npix, xw, spp, (int)xyz_mode, xyz_dev, st);
+    launch_xyz(spectral_dev, npix, xw, spp, (int)xyz_mode, xyz_dev, st, b.status, v.sms);
     STATIC_TRY(cudaGetLastError());
   }
   STATIC_TRY(cudaMemcpyAsync(v.h_status, b.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

@@ -2,7 +2,20 @@
 //
 //   xyz[p][c] = sum_j (spectral[p][j] / spp) * w[j][c]
 //
-// RT_XYZ_FP64: CUDA cores, FP64, one warp per pixel group (reference mode).
+// RT_XYZ_BF16X3 / RT_XYZ_BF16: 5th-generation tensor cores (tcgen05.mma,
+// accumulator in tensor memory).  One CTA (128 threads) processes tiles of
+// 128 pixels: the FP64 rows are streamed from HBM with coalesced 16-byte
+// loads, divided by spp, rounded to FP32 and split into BF16 terms
+// v = hi + mid + lo (each the BF16 rounding of the remainder), written to
+// shared memory in the K-major, non-swizzled canonical layout (8 x 16-byte
+// core matrices).  One thread issues D[128 x 16] += A[128 x 16] B[16 x 16]
+// for every 16-band slice: with the three-term split of both operands the six
+// products hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid carry FP32-level
+// accuracy (the dropped terms are below 2^-26 relative, after Henry, Tang and
+// Heinecke, ARITH 2019); RT_XYZ_BF16 uses hi.hi only.  The FP32 accumulator is
+// read back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = pixels).
+//
+// RT_XYZ_FP64: CUDA cores, FP64, the reference mode.
 #include <cstdint>
 
 #include "rt_internal.h"
@@ -11,11 +24,12 @@ namespace srt {
 
 namespace {
 
-// one thread per pixel row, the row staged through shared memory by the
-// whole block with coalesced loads
+// ---------------------------------------------------------------------------
+// FP64 reference kernel
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_xyz_fp64(const double* __restrict__ s, uint64_t np, uint32_t bc,
                                                   const float* __restrict__ w, double inv_spp, float* __restrict__ xyz) {
-  extern __shared__ double tile[];  // [256][bc]
+  extern __shared__ double tile[];  // [blockDim][bc]
   const uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x;
   const uint64_t rows = (np - p0) < blockDim.x ? (np - p0) : blockDim.x;
   const uint64_t elems = rows * bc;
@@ -38,6 +52,241 @@ __global__ void __launch_bounds__(256) k_xyz_fp64(const double* __restrict__ s, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 helpers (inline PTX, sm_100a family)
+// ---------------------------------------------------------------------------
+constexpr int kTileM = 128;        // pixels per tile = MMA M = TMEM lanes
+constexpr int kMmaN = 16;          // XYZ padded to 16 columns
+constexpr int kTmemCols = 32;      // smallest TMEM allocation
+constexpr uint32_t kATile = 4096;  // one 128 x 16 BF16 K-slice
+constexpr uint32_t kBTile = 512;   // one 16 x 16 BF16 K-slice
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Canonical K-major layout without swizzle: element (row r, k) of a K-slice
+// lives at (r % 8) * 16 + (r / 8) * 256 + (k % 8) * 2 + (k / 8) * 128 bytes:
+// core matrices of 8 rows x 16 bytes, 128 bytes apart along K (leading byte
+// offset) and 256 bytes apart along M/N (stride byte offset).
+__device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t k) {
+  return (r & 7u) * 16u + (r >> 3) * 256u + (k & 7u) * 2u + (k >> 3) * 128u;
+}
+
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
+// byte offset >> 4 (bits 16-29), stride byte offset >> 4 (bits 32-45),
+// descriptor version 1 (bit 46), no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 =
+// 1), B BF16 (bits 10-12 = 1), both K-major, N >> 3 (bits 17-22), M >> 4
+// (bits 24-28).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMmaN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+
+// Waits for the phase with the given parity; gives up after max_iter polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t max_iter) {
+  for (uint32_t i = 0; i < max_iter; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float& x, float& y, float& z, float& w) {
+  uint32_t a, b, c, d;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  x = __uint_as_float(a);
+  y = __uint_as_float(b);
+  z = __uint_as_float(c);
+  w = __uint_as_float(d);
+}
+
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// BF16 bits, round to nearest even (inputs are finite).
+__device__ __forceinline__ uint16_t bf16_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf16_val(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+
+// v = hi + mid + lo with each term the BF16 rounding of the remainder.
+__device__ __forceinline__ void split3(float v, uint16_t& h, uint16_t& m, uint16_t& l) {
+  h = bf16_bits(v);
+  const float r1 = v - bf16_val(h);
+  m = bf16_bits(r1);
+  const float r2 = r1 - bf16_val(m);
+  l = bf16_bits(r2);
+}
+
+constexpr int kXyzThreads = 256;
+constexpr int kUnroll = 8;
+
+// inv_bc = ceil(2^32 / bc): __umulhi(e, inv_bc) == e / bc for every element
+// index of a tile (e < 128 * 192).
+__global__ void __launch_bounds__(kXyzThreads) k_xyz_tc(const double* __restrict__ s, uint64_t np, uint32_t bc,
+                                                        uint32_t nk, uint32_t inv_bc, const float* __restrict__ w,
+                                                        double inv_spp, float* __restrict__ xyz, int n_split,
+                                                        uint32_t* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* A = smem;                                   // [3][nk][4096]
+  unsigned char* Bm = smem + 3u * nk * kATile;               // [3][nk][512]
+  uint64_t* mbar = (uint64_t*)(Bm + 3u * nk * kBTile);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+
+  // zero A (its padded K columns stay zero) and build the split weights
+  for (uint32_t i = tid; i < 3u * nk * kATile / 16u; i += blockDim.x) ((uint4*)A)[i] = make_uint4(0, 0, 0, 0);
+  for (uint32_t i = tid; i < (uint32_t)kMmaN * nk * 16u; i += blockDim.x) {
+    const uint32_t n = i / (nk * 16u), k = i - n * nk * 16u;
+    const float v = (n < 3u && k < bc) ? w[3u * k + n] : 0.0f;
+    uint16_t h, m, l;
+    split3(v, h, m, l);
+    const uint32_t off = (k >> 4) * kBTile + kmajor_off(n, k & 15u);
+    *(uint16_t*)(Bm + off) = h;
+    *(uint16_t*)(Bm + nk * kBTile + off) = m;
+    *(uint16_t*)(Bm + 2u * nk * kBTile + off) = l;
+  }
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, kTmemCols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  // products (a split, b split)
+  const uint32_t pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+  const uint64_t ntiles = (np + kTileM - 1) / kTileM;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (uint64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const uint64_t p0 = tile * kTileM;
+    const uint32_t rows = (uint32_t)((np - p0) < (uint64_t)kTileM ? (np - p0) : (uint64_t)kTileM);
+    const uint32_t nel = rows * bc;
+    const double* src = s + p0 * bc;
+    // coalesced 16-byte loads over the tile's contiguous rows, kUnroll in
+    // flight per thread before any conversion
+    const uint32_t npair = (nel + 1u) >> 1;
+    for (uint32_t q0 = tid; q0 < npair; q0 += blockDim.x * kUnroll) {
+      double2 v[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint32_t q = q0 + (uint32_t)u * blockDim.x;
+        if (2u * q + 1u < nel) {
+          v[u] = __ldcs((const double2*)src + q);
+        } else if (2u * q < nel) {
+          v[u] = make_double2(__ldcs(src + 2u * q), 0.0);
+        } else {
+          v[u] = make_double2(0.0, 0.0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint32_t q = q0 + (uint32_t)u * blockDim.x;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const uint32_t ee = 2u * q + (uint32_t)h2;
+          if (ee < nel) {
+            const uint32_t r = __umulhi(ee, inv_bc), k = ee - r * bc;
+            const float val = (float)((h2 ? v[u].y : v[u].x) * inv_spp);
+            uint16_t hh, mm, ll;
+            split3(val, hh, mm, ll);
+            const uint32_t off = (k >> 4) * kATile + kmajor_off(r, k & 15u);
+            *(uint16_t*)(A + off) = hh;
+            if (n_split > 1) {
+              *(uint16_t*)(A + nk * kATile + off) = mm;
+              *(uint16_t*)(A + 2u * nk * kATile + off) = ll;
+            }
+          }
+        }
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      const int nprod = n_split > 1 ? 6 : 1;
+      uint32_t acc = 0;
+      for (uint32_t kb = 0; kb < nk; ++kb)
+        for (int pr = 0; pr < nprod; ++pr) {
+          const uint64_t da = smem_desc(smem_u32(A + pa[pr] * nk * kATile + kb * kATile));
+          const uint64_t db = smem_desc(smem_u32(Bm + pb[pr] * nk * kBTile + kb * kBTile));
+          mma_bf16(tmem, da, db, acc);
+          acc = 1;
+        }
+      mma_commit(mbar);
+    }
+    const int timed_out = __syncthreads_or(mbar_wait(mbar, phase, 1u << 24) ? 0 : 1);
+    if (timed_out) {
+      if (tid == 0) atomicOr(status, ST_ITER);
+      ok = false;
+    }
+    phase ^= 1u;
+    fence_after_sync();
+    if (warp < 4) {  // warp w reads TMEM lanes 32w..32w+31 (pixels)
+      float x, y, z, pad;
+      tmem_ld4(tmem + ((warp * 32u) << 16), x, y, z, pad);
+      const uint32_t r = warp * 32u + lane;
+      if (ok && r < rows) {
+        float* o = xyz + 3 * (p0 + r);
+        o[0] = x;
+        o[1] = y;
+        o[2] = z;
+      }
+    }
+    fence_before_sync();
+    __syncthreads();
+  }
+  fence_after_sync();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
 }  // namespace
 
 size_t xyz_wsplit_elems(uint32_t band_count) { return (size_t)((band_count + 15) / 16 * 16) * 16 * 3; }
@@ -48,15 +297,34 @@ void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t*
   (void)wsplit_host;
 }
 
+size_t xyz_tc_smem(uint32_t band_count) {
+  const uint32_t nk = (band_count + 15) / 16;
+  return 3ull * nk * kATile + 3ull * nk * kBTile + 16;
+}
+
 void launch_xyz(const double* spectral, uint64_t n_pixels, const XyzWeights& w, uint32_t spp, int mode, float* xyz,
-                cudaStream_t st) {
-  (void)mode;
+                cudaStream_t st, uint32_t* status, int sms) {
   if (n_pixels == 0) return;
-  int block = (int)(49152 / (8 * (size_t)w.band_count));
-  block = block > 256 ? 256 : (block < 1 ? 1 : block);
-  const uint64_t grid = (n_pixels + block - 1) / block;
-  const size_t smem = (size_t)block * w.band_count * sizeof(double);
-  k_xyz_fp64<<<(unsigned)grid, block, smem, st>>>(spectral, n_pixels, w.band_count, w.w32, 1.0 / (double)spp, xyz);
+  if (mode == 2) {
+    int block = (int)(49152 / (8 * (size_t)w.band_count));
+    block = block > 256 ? 256 : (block < 1 ? 1 : block);
+    const uint64_t grid = (n_pixels + block - 1) / block;
+    const size_t smem = (size_t)block * w.band_count * sizeof(double);
+    k_xyz_fp64<<<(unsigned)grid, block, smem, st>>>(spectral, n_pixels, w.band_count, w.w32, 1.0 / (double)spp, xyz);
+    return;
+  }
+  const uint32_t nk = (w.band_count + 15) / 16;
+  const size_t smem = xyz_tc_smem(w.band_count);
+  cudaFuncSetAttribute(k_xyz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t ntiles = (n_pixels + kTileM - 1) / kTileM;
+  int per_sm = (int)((227u * 1024u) / (smem + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 4) per_sm = 4;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  const uint32_t inv_bc = (uint32_t)((0x100000000ull + w.band_count - 1) / w.band_count);
+  k_xyz_tc<<<(unsigned)grid, kXyzThreads, smem, st>>>(spectral, n_pixels, w.band_count, nk, inv_bc, w.w32,
+                                                      1.0 / (double)spp, xyz, mode == 0 ? 3 : 1, status);
 }
 
 }  // namespace srt

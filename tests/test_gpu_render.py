@@ -34,7 +34,7 @@ def test_tiny_box_full_image(R):
     depth 4, seed 0 -- every pixel against the oracle."""
     wl = scenes.tiny_box()
     R.load(wl)
-    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed)  # tensor-core XYZ (split BF16)
     o = _oracle(wl)
     m = assert_parity(out["xyz"].cpu().numpy(), o["xyz"], "tiny box")
     print("tiny box parity", m)
