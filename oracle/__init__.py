@@ -28,14 +28,14 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C++17, strict IEEE double, no fast-math)."""
-    src = os.path.join(_HERE, "oracle.cpp")
+    srcs = [os.path.join(_HERE, "oracle.cpp"), os.path.join(_HERE, "guide_oracle.cpp")]
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(s) for s in srcs)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
-           "-fno-fast-math", src, "-o", tmp]
+           "-fno-fast-math"] + srcs + ["-o", tmp]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -95,6 +95,14 @@ def lib():
             L.or_xyz.argtypes = [C.POINTER(C.c_double), C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.POINTER(C.c_float), C.POINTER(C.c_double)]
             L.or_hardware_threads.restype = C.c_int
+            fp, dp, up = C.POINTER(C.c_float), C.POINTER(C.c_double), C.POINTER(C.c_uint32)
+            L.or_guide_resolutions.argtypes = [C.c_float, C.c_float, up]
+            L.or_guide_forward.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_uint64, fp, fp, up,
+                                           fp, dp, dp, dp]
+            L.or_guide_loss_grad.restype = C.c_double
+            L.or_guide_loss_grad.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_uint64, fp, fp,
+                                             up, fp, fp, dp, dp]
+            L.or_guide_density.argtypes = [dp, C.c_uint64, dp, dp]
             _lib = L
     return _lib
 
@@ -247,3 +255,57 @@ def xyz(spectral_sum, band_first, spp, cmf_w) -> np.ndarray:
     out = np.zeros((npx, 3), np.float64)
     lib().or_xyz(_ptr(s, C.c_double), npx, band_first, bc, spp, _ptr(w, C.c_float), _ptr(out, C.c_double))
     return out
+
+
+# ---------------------------------------------------------------------------
+# learned guide (hash grid + MLP + vMF mixture), FP64
+# ---------------------------------------------------------------------------
+GUIDE_W_SIZE = 64 * 64 * 3 + 64 * 48
+GUIDE_LEVELS = 16
+
+
+def guide_resolutions(n_min=16.0, n_max=2048.0):
+    r = np.zeros(GUIDE_LEVELS, np.uint32)
+    lib().or_guide_resolutions(n_min, n_max, _ptr(r, C.c_uint32))
+    return r
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def guide_forward(log2_T, lo, hi, grid, W, pos, nrm, group, omega, n_min=16.0, n_max=2048.0):
+    """X [n, 64], Y [n, 48], q(omega) [n]."""
+    lo, hi, grid, W, pos, nrm, omega = map(_f32, (lo, hi, grid, W, pos, nrm, omega))
+    g = np.ascontiguousarray(group, np.uint32)
+    n = pos.shape[0]
+    X = np.zeros((n, 64))
+    Y = np.zeros((n, 48))
+    q = np.zeros(n)
+    fp = lambda a: _ptr(a, C.c_float)
+    dp = lambda a: _ptr(a, C.c_double)
+    lib().or_guide_forward(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W), n, fp(pos), fp(nrm),
+                           _ptr(g, C.c_uint32), fp(omega), dp(X), dp(Y), dp(q))
+    return X, Y, q
+
+
+def guide_loss_grad(log2_T, lo, hi, grid, W, pos, nrm, group, omega, wt, n_min=16.0, n_max=2048.0):
+    """(loss, dW [GUIDE_W_SIZE], dgrid [16 * 2^log2_T * 2])."""
+    lo, hi, grid, W, pos, nrm, omega, wt = map(_f32, (lo, hi, grid, W, pos, nrm, omega, wt))
+    g = np.ascontiguousarray(group, np.uint32)
+    n = pos.shape[0]
+    dW = np.zeros(GUIDE_W_SIZE)
+    dgrid = np.zeros(GUIDE_LEVELS * (1 << log2_T) * 2)
+    fp = lambda a: _ptr(a, C.c_float)
+    dp = lambda a: _ptr(a, C.c_double)
+    loss = lib().or_guide_loss_grad(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W), n, fp(pos), fp(nrm),
+                                    _ptr(g, C.c_uint32), fp(omega), fp(wt), dp(dW), dp(dgrid))
+    return loss, dW, dgrid
+
+
+def guide_density(Y, omega):
+    Y = np.ascontiguousarray(Y, np.float64)
+    om = np.ascontiguousarray(omega, np.float64)
+    q = np.zeros(om.shape[0])
+    lib().or_guide_density(_ptr(Y, C.c_double), om.shape[0], _ptr(om, C.c_double), _ptr(q, C.c_double))
+    return q
