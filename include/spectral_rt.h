@@ -189,6 +189,48 @@ rt_status rt_render_static(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, 
                            uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed, uint32_t xyz_mode,
                            double* spectral_dev, float* xyz_dev);
 
+/* ---- learned path guide (optional; a sampling density, not a change of the
+ * estimator: guided directions are mixed with cosine sampling by one-sample
+ * MIS, so the rendered expectation of section 4, Eq. 2 is unchanged) ------
+ *
+ * Network: hash-grid encoding of the position (16 levels x 2 features,
+ * 2^log2_table entries per level, resolutions n_min .. n_max over the scene
+ * bounds), real spherical harmonics of the normal (degree <= 3), a one-hot
+ * band group (9 groups); MLP 64 -> 64 -> 64 -> 64 -> 48 (ReLU, no biases) on
+ * BF16 tensor cores with FP32 accumulation; 8 von Mises-Fisher lobes (outputs
+ * 5j .. 5j + 4: logit, mean direction, kappa = 0.5 + softplus).
+ * Parameters: grid [16][2^log2_table][2] and W = W1 [64][64] | W2 [64][64] |
+ * W3 [64][64] | W4 [64][48] (row-major [in][out]), FP32 masters.
+ * Training record (12 floats): {pos.xyz, weight}, {normal.xyz, band group},
+ * {omega.xyz, 0}; loss -(1/N) sum_r (weight_r / mean weight) log q_r(omega_r). */
+typedef struct {
+  uint32_t log2_table;   /* 10..22; 0 = 19 */
+  float n_min, n_max;    /* 0 = 16, 2048 */
+  float lr_grid, lr_mlp; /* Adam learning rates; 0 = 1e-2, 1e-3 */
+  float beta1, beta2;    /* 0 = 0.9, 0.99 */
+  float eps;             /* 0 = 1e-15 */
+  float mis_alpha;       /* probability of sampling the guide at a guided vertex; 0 = 0.5 */
+  uint32_t guide_depth;  /* vertices 1..guide_depth are guided; 0 = 2 */
+  uint32_t reserved[6];
+} rt_guide_config;
+
+/* Creates (or re-creates) the guide of the loaded scene: parameters drawn
+ * from Philox with the given seed (grid uniform +-1e-4, weights Xavier
+ * uniform), Adam state zeroed.  The scene bounds fix the encoding. */
+rt_status rt_guide_init(rt_ctx* ctx, const rt_guide_config* cfg, uint64_t seed);
+/* Copies parameters in / out (host arrays of the sizes above; either pointer
+ * may be NULL).  Setting parameters resets the Adam state. */
+rt_status rt_guide_set_params(rt_ctx* ctx, const float* grid, const float* W);
+rt_status rt_guide_get_params(rt_ctx* ctx, float* grid, float* W);
+/* Network outputs Y_dev [n][48] and mixture density q_dev [n] at each
+ * record's omega, for n records rec_dev [n][12] (device, 16-byte aligned). */
+rt_status rt_guide_eval(rt_ctx* ctx, const float* rec_dev, uint64_t n, float* Y_dev, float* q_dev);
+/* Loss and gradients without an update: *loss (host), dgrid_dev and dW_dev
+ * (device, FP32, sizes as the parameters; either may be NULL). */
+rt_status rt_guide_grad(rt_ctx* ctx, const float* rec_dev, uint64_t n, float* loss, float* dgrid_dev, float* dW_dev);
+/* One Adam step on a batch of records; *loss (host, may be NULL) before the step. */
+rt_status rt_guide_train_step(rt_ctx* ctx, const float* rec_dev, uint64_t n, float* loss);
+
 /* ---- single steps of the path, for parity tests and tools ---------------- */
 
 /* Philox4x32-10 (Salmon et al., SC 2011) of n counters ctr_dev[n][4] with key

@@ -98,10 +98,10 @@ def lib():
             fp, dp, up = C.POINTER(C.c_float), C.POINTER(C.c_double), C.POINTER(C.c_uint32)
             L.or_guide_resolutions.argtypes = [C.c_float, C.c_float, up]
             L.or_guide_forward.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_uint64, fp, fp, up,
-                                           fp, dp, dp, dp]
+                                           fp, C.c_int, dp, dp, dp]
             L.or_guide_loss_grad.restype = C.c_double
             L.or_guide_loss_grad.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_uint64, fp, fp,
-                                             up, fp, fp, dp, dp]
+                                             up, fp, fp, C.c_int, dp, dp]
             L.or_guide_density.argtypes = [dp, C.c_uint64, dp, dp]
             _lib = L
     return _lib
@@ -274,8 +274,9 @@ def _f32(a):
     return np.ascontiguousarray(a, np.float32)
 
 
-def guide_forward(log2_T, lo, hi, grid, W, pos, nrm, group, omega, n_min=16.0, n_max=2048.0):
-    """X [n, 64], Y [n, 48], q(omega) [n]."""
+def guide_forward(log2_T, lo, hi, grid, W, pos, nrm, group, omega, n_min=16.0, n_max=2048.0, bf16_act=False):
+    """X [n, 64], Y [n, 48], q(omega) [n].  bf16_act: the BF16 network (layer
+    inputs rounded to BF16 before each product)."""
     lo, hi, grid, W, pos, nrm, omega = map(_f32, (lo, hi, grid, W, pos, nrm, omega))
     g = np.ascontiguousarray(group, np.uint32)
     n = pos.shape[0]
@@ -285,11 +286,11 @@ def guide_forward(log2_T, lo, hi, grid, W, pos, nrm, group, omega, n_min=16.0, n
     fp = lambda a: _ptr(a, C.c_float)
     dp = lambda a: _ptr(a, C.c_double)
     lib().or_guide_forward(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W), n, fp(pos), fp(nrm),
-                           _ptr(g, C.c_uint32), fp(omega), dp(X), dp(Y), dp(q))
+                           _ptr(g, C.c_uint32), fp(omega), 1 if bf16_act else 0, dp(X), dp(Y), dp(q))
     return X, Y, q
 
 
-def guide_loss_grad(log2_T, lo, hi, grid, W, pos, nrm, group, omega, wt, n_min=16.0, n_max=2048.0):
+def guide_loss_grad(log2_T, lo, hi, grid, W, pos, nrm, group, omega, wt, n_min=16.0, n_max=2048.0, bf16_act=False):
     """(loss, dW [GUIDE_W_SIZE], dgrid [16 * 2^log2_T * 2])."""
     lo, hi, grid, W, pos, nrm, omega, wt = map(_f32, (lo, hi, grid, W, pos, nrm, omega, wt))
     g = np.ascontiguousarray(group, np.uint32)
@@ -299,7 +300,8 @@ def guide_loss_grad(log2_T, lo, hi, grid, W, pos, nrm, group, omega, wt, n_min=1
     fp = lambda a: _ptr(a, C.c_float)
     dp = lambda a: _ptr(a, C.c_double)
     loss = lib().or_guide_loss_grad(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W), n, fp(pos), fp(nrm),
-                                    _ptr(g, C.c_uint32), fp(omega), fp(wt), dp(dW), dp(dgrid))
+                                    _ptr(g, C.c_uint32), fp(omega), fp(wt), 1 if bf16_act else 0, dp(dW),
+                                    dp(dgrid))
     return loss, dW, dgrid
 
 

@@ -21,8 +21,11 @@
 //   gradients:   by the chain rule through head, MLP and the trilinear
 //                interpolation of the grid.
 //
-// The GPU rounds X, activations and weights to BF16; the oracle takes the
-// same float parameters and computes everything in FP64.
+// The network runs in BF16 with FP32 accumulation: with bf16_act the oracle
+// rounds every layer input (X, H1, H2, H3) to BF16 as that definition says and
+// accumulates in FP64; without it the activations are exact (the form the
+// finite-difference pins check).  Weights arrive as floats (BF16-rounded by
+// the caller when comparing with the GPU).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -125,6 +128,23 @@ void matvec(const double* x, const float* W, int in, int out, double* y) {
 }
 
 double softplus(double x) { return x > 30.0 ? x : std::log1p(std::exp(x)); }
+
+// BF16 network: with bf16_act the inputs of every layer (X, H1, H2, H3) are
+// rounded to BF16 (round to nearest even of the float value) before the
+// product; gradients pass through the rounding unchanged.
+double round_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+void maybe_round(double* v, int n, int on) {
+  if (on)
+    for (int i = 0; i < n; ++i) v[i] = round_bf16(v[i]);
+}
 double sigmoid(double x) { return 1.0 / (1.0 + std::exp(-x)); }
 
 struct Head {
@@ -185,7 +205,7 @@ void or_guide_resolutions(float n_min, float n_max, uint32_t* res) {
 // W = W1 [64][64] | W2 [64][64] | W3 [64][64] | W4 [64][48], row-major [in][out].
 void or_guide_forward(uint32_t log2_T, const float* lo, const float* hi, float n_min, float n_max, const float* grid,
                       const float* W, uint64_t n, const float* pos, const float* nrm, const uint32_t* group,
-                      const float* omega, double* X_out, double* Y_out, double* q_out) {
+                      const float* omega, int bf16_act, double* X_out, double* Y_out, double* q_out) {
   const GCfg g = make_cfg(log2_T, lo, hi, n_min, n_max);
   const float* W1 = W;
   const float* W2 = W1 + kIn * kHid;
@@ -197,12 +217,16 @@ void or_guide_forward(uint32_t log2_T, const float* lo, const float* hi, float n
     double nn[3] = {nrm[3 * r], nrm[3 * r + 1], nrm[3 * r + 2]};
     double X[kIn], H1[kHid], H2[kHid], H3[kHid], Y[kOut];
     encode(g, grid, p, nn, group[r], X, &enc[0]);
+    maybe_round(X, kIn, bf16_act);
     matvec(X, W1, kIn, kHid, H1);
     for (double& v : H1) v = v > 0.0 ? v : 0.0;
+    maybe_round(H1, kHid, bf16_act);
     matvec(H1, W2, kHid, kHid, H2);
     for (double& v : H2) v = v > 0.0 ? v : 0.0;
+    maybe_round(H2, kHid, bf16_act);
     matvec(H2, W3, kHid, kHid, H3);
     for (double& v : H3) v = v > 0.0 ? v : 0.0;
+    maybe_round(H3, kHid, bf16_act);
     matvec(H3, W4, kHid, kOut, Y);
     if (X_out) std::memcpy(X_out + r * kIn, X, sizeof(X));
     if (Y_out) std::memcpy(Y_out + r * kOut, Y, sizeof(Y));
@@ -221,7 +245,8 @@ void or_guide_forward(uint32_t log2_T, const float* lo, const float* hi, float n
 // dW (same layout as W) and dgrid ([16 * T * 2]) are overwritten.
 double or_guide_loss_grad(uint32_t log2_T, const float* lo, const float* hi, float n_min, float n_max,
                           const float* grid, const float* W, uint64_t n, const float* pos, const float* nrm,
-                          const uint32_t* group, const float* omega, const float* wt, double* dW, double* dgrid) {
+                          const uint32_t* group, const float* omega, const float* wt, int bf16_act, double* dW,
+                          double* dgrid) {
   const GCfg g = make_cfg(log2_T, lo, hi, n_min, n_max);
   const uint32_t T = 1u << log2_T;
   const float* W1 = W;
@@ -246,12 +271,16 @@ double or_guide_loss_grad(uint32_t log2_T, const float* lo, const float* hi, flo
     double w[3] = {omega[3 * r], omega[3 * r + 1], omega[3 * r + 2]};
     double X[kIn], Z1[kHid], H1[kHid], Z2[kHid], H2[kHid], Z3[kHid], H3[kHid], Y[kOut];
     encode(g, grid, p, nn, group[r], X, &e);
+    maybe_round(X, kIn, bf16_act);
     matvec(X, W1, kIn, kHid, Z1);
     for (int i = 0; i < kHid; ++i) H1[i] = Z1[i] > 0.0 ? Z1[i] : 0.0;
+    maybe_round(H1, kHid, bf16_act);
     matvec(H1, W2, kHid, kHid, Z2);
     for (int i = 0; i < kHid; ++i) H2[i] = Z2[i] > 0.0 ? Z2[i] : 0.0;
+    maybe_round(H2, kHid, bf16_act);
     matvec(H2, W3, kHid, kHid, Z3);
     for (int i = 0; i < kHid; ++i) H3[i] = Z3[i] > 0.0 ? Z3[i] : 0.0;
+    maybe_round(H3, kHid, bf16_act);
     matvec(H3, W4, kHid, kOut, Y);
     Head h;
     head(Y, &h);

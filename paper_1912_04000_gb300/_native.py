@@ -21,7 +21,8 @@ XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
 # every exported symbol of include/spectral_rt.h
 EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_set_timing",
            "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
-           "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static"]
+           "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static", "rt_guide_init",
+           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step"]
 
 
 class RtError(RuntimeError):
@@ -41,6 +42,15 @@ class RenderOpts(C.Structure):
                 ("probe_sig_dev", C.c_void_p), ("use_graph", C.c_uint32), ("trace_variant", C.c_uint32),
                 ("trace_steps", C.c_uint32), ("trace_refill", C.c_uint32), ("shadow_steps", C.c_uint32),
                 ("shadow_refill", C.c_uint32), ("reserved", C.c_uint32 * 2)]
+
+
+class GuideConfig(C.Structure):
+    _fields_ = [("log2_table", C.c_uint32), ("n_min", C.c_float), ("n_max", C.c_float), ("lr_grid", C.c_float),
+                ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("mis_alpha", C.c_float), ("guide_depth", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+
+
+GUIDE_W_SIZE = 64 * 64 * 3 + 64 * 48
 
 
 class Stats(C.Structure):
@@ -88,6 +98,12 @@ def load(path: str = LIB_PATH):
         L.rt_render_host.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp,
                                      vp, C.POINTER(Stats)]
         L.rt_render_static.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, u32, vp, vp]
+        L.rt_guide_init.argtypes = [vp, C.POINTER(GuideConfig), u64]
+        L.rt_guide_set_params.argtypes = [vp, vp, vp]
+        L.rt_guide_get_params.argtypes = [vp, vp, vp]
+        L.rt_guide_eval.argtypes = [vp, vp, u64, vp, vp]
+        L.rt_guide_grad.argtypes = [vp, vp, u64, C.POINTER(C.c_float), vp, vp]
+        L.rt_guide_train_step.argtypes = [vp, vp, u64, C.POINTER(C.c_float)]
         L.rt_philox.argtypes = [vp, vp, vp, u64, u32, u32]
         L.rt_trace_closest.argtypes = [vp, vp, vp, u64, vp, vp]
         L.rt_trace_shadow.argtypes = [vp, vp, vp, vp, u64, vp, vp]

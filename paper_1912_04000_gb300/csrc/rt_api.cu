@@ -55,6 +55,18 @@ struct rt_ctx {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timing = false;
   std::vector<cudaEvent_t> tpool;
+  float lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};  // scene bounds
+  // learned guide
+  struct Guide {
+    bool init = false;
+    rt_guide_config cfg{};
+    float *grid = nullptr, *W = nullptr, *mg = nullptr, *vg = nullptr, *mW = nullptr, *vW = nullptr;
+    float *dgrid = nullptr, *dW = nullptr, *scratch = nullptr;  // scratch: wsum, loss
+    void* pack = nullptr;
+    uint64_t n_grid = 0;
+    uint32_t step = 0;
+    GuideDev dev{};
+  } guide;
 };
 
 namespace {
@@ -250,6 +262,16 @@ void rt_destroy(rt_ctx* c) {
   dfree(c->d_cams);
   dfree(c->d_accum);
   dfree(c->d_xyz);
+  dfree(c->guide.grid);
+  dfree(c->guide.W);
+  dfree(c->guide.mg);
+  dfree(c->guide.vg);
+  dfree(c->guide.mW);
+  dfree(c->guide.vW);
+  dfree(c->guide.dgrid);
+  dfree(c->guide.dW);
+  dfree(c->guide.scratch);
+  if (c->guide.pack) cudaFree(c->guide.pack);
   if (c->h_cams) cudaFreeHost(c->h_cams);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_tot) cudaFreeHost(c->h_tot);
@@ -380,6 +402,11 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   c->eps = (float)(1e-4 * std::sqrt(dx * dx + dy * dy + dz * dz));
   c->mtype.assign(mat_type, mat_type + n_mat);
   c->mthick.assign(mat_thickness, mat_thickness + n_mat);
+  for (int a = 0; a < 3; ++a) {
+    c->lo[a] = (float)lo[a];
+    c->hi[a] = (float)hi[a];
+  }
+  c->guide.init = false;
   c->has_scene = true;
   c->has_spectra = false;  // tables are per material: set them again
   return RT_OK;
@@ -718,6 +745,179 @@ rt_status rt_xyz(rt_ctx* c, const double* spectral_dev, uint64_t n_pixels, uint3
   CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return status_to_rt(c, *c->h_status);
+}
+
+namespace {
+
+rt_status guide_ready(rt_ctx* c) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->guide.init) return fail(c, RT_ERR_STATE, "guide not initialised (rt_guide_init after rt_load_scene)");
+  return RT_OK;
+}
+
+uint64_t guide_wcount() { return guide_wsize(); }
+
+}  // namespace
+
+rt_status rt_guide_init(rt_ctx* c, const rt_guide_config* cfg_in, uint64_t seed) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_scene) return fail(c, RT_ERR_STATE, "rt_guide_init: load a scene first");
+  rt_guide_config cfg{};
+  if (cfg_in) cfg = *cfg_in;
+  if (!cfg.log2_table) cfg.log2_table = 19;
+  if (cfg.n_min == 0.0f) cfg.n_min = 16.0f;
+  if (cfg.n_max == 0.0f) cfg.n_max = 2048.0f;
+  if (cfg.lr_grid == 0.0f) cfg.lr_grid = 1e-2f;
+  if (cfg.lr_mlp == 0.0f) cfg.lr_mlp = 1e-3f;
+  if (cfg.beta1 == 0.0f) cfg.beta1 = 0.9f;
+  if (cfg.beta2 == 0.0f) cfg.beta2 = 0.99f;
+  if (cfg.eps == 0.0f) cfg.eps = 1e-15f;
+  if (cfg.mis_alpha == 0.0f) cfg.mis_alpha = 0.5f;
+  if (!cfg.guide_depth) cfg.guide_depth = 2;
+  if (cfg.log2_table < 10 || cfg.log2_table > 22 || !(cfg.n_min >= 1.0f) || !(cfg.n_max >= cfg.n_min) ||
+      !(cfg.mis_alpha > 0.0f && cfg.mis_alpha < 1.0f) || cfg.guide_depth > (uint32_t)kMaxDepth)
+    return fail(c, RT_ERR_ARG, "rt_guide_init: bad configuration");
+  auto& G = c->guide;
+  cudaSetDevice(c->device);
+  const uint64_t T = 1ull << cfg.log2_table;
+  const uint64_t ng = 16ull * T * 2ull;
+  if (G.n_grid != ng) {
+    dfree(G.grid);
+    dfree(G.mg);
+    dfree(G.vg);
+    dfree(G.dgrid);
+    G.n_grid = 0;
+    CUDA_TRY(c, cudaMalloc(&G.grid, ng * 4));
+    CUDA_TRY(c, cudaMalloc(&G.mg, ng * 4));
+    CUDA_TRY(c, cudaMalloc(&G.vg, ng * 4));
+    CUDA_TRY(c, cudaMalloc(&G.dgrid, ng * 4));
+    G.n_grid = ng;
+  }
+  if (!G.W) {
+    CUDA_TRY(c, cudaMalloc(&G.W, guide_wcount() * 4));
+    CUDA_TRY(c, cudaMalloc(&G.mW, guide_wcount() * 4));
+    CUDA_TRY(c, cudaMalloc(&G.vW, guide_wcount() * 4));
+    CUDA_TRY(c, cudaMalloc(&G.dW, guide_wcount() * 4));
+    CUDA_TRY(c, cudaMalloc(&G.scratch, 64));
+    CUDA_TRY(c, cudaMalloc(&G.pack, guide_wpack_bytes()));
+  }
+  G.cfg = cfg;
+  GuideDev& d = G.dev;
+  d.grid = G.grid;
+  d.log2T = cfg.log2_table;
+  const double b = std::exp((std::log((double)cfg.n_max) - std::log((double)cfg.n_min)) / 15.0);
+  d.dense_mask = 0;
+  for (int l = 0; l < 16; ++l) {
+    d.res[l] = (uint32_t)std::floor((double)cfg.n_min * std::pow(b, l));
+    const uint64_t r1 = (uint64_t)d.res[l] + 1;
+    if (r1 * r1 * r1 <= T) d.dense_mask |= 1u << l;
+  }
+  for (int a = 0; a < 3; ++a) {
+    d.lo[a] = c->lo[a];
+    const float ext = c->hi[a] - c->lo[a];
+    d.inv_ext[a] = ext > 0.0f ? 1.0f / ext : 0.0f;
+  }
+  launch_guide_init(G.grid, ng, G.W, seed, c->stream);
+  CUDA_TRY(c, cudaMemsetAsync(G.mg, 0, ng * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.vg, 0, ng * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.mW, 0, guide_wcount() * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.vW, 0, guide_wcount() * 4, c->stream));
+  launch_guide_pack(G.W, G.pack, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  G.step = 0;
+  G.init = true;
+  return RT_OK;
+}
+
+rt_status rt_guide_set_params(rt_ctx* c, const float* grid, const float* W) {
+  if (rt_status e = guide_ready(c)) return e;
+  auto& G = c->guide;
+  cudaSetDevice(c->device);
+  if (grid) CUDA_TRY(c, cudaMemcpy(G.grid, grid, G.n_grid * 4, cudaMemcpyHostToDevice));
+  if (W) CUDA_TRY(c, cudaMemcpy(G.W, W, guide_wcount() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemsetAsync(G.mg, 0, G.n_grid * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.vg, 0, G.n_grid * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.mW, 0, guide_wcount() * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.vW, 0, guide_wcount() * 4, c->stream));
+  launch_guide_pack(G.W, G.pack, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  G.step = 0;
+  return RT_OK;
+}
+
+rt_status rt_guide_get_params(rt_ctx* c, float* grid, float* W) {
+  if (rt_status e = guide_ready(c)) return e;
+  auto& G = c->guide;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (grid) CUDA_TRY(c, cudaMemcpy(grid, G.grid, G.n_grid * 4, cudaMemcpyDeviceToHost));
+  if (W) CUDA_TRY(c, cudaMemcpy(W, G.W, guide_wcount() * 4, cudaMemcpyDeviceToHost));
+  return RT_OK;
+}
+
+rt_status rt_guide_eval(rt_ctx* c, const float* rec_dev, uint64_t n, float* Y_dev, float* q_dev) {
+  if (rt_status e = guide_ready(c)) return e;
+  if (!rec_dev || !Y_dev || !q_dev) return fail(c, RT_ERR_ARG, "rt_guide_eval: null pointer");
+  if (((uintptr_t)rec_dev & 15u) != 0) return fail(c, RT_ERR_ARG, "rt_guide_eval: records must be 16-byte aligned");
+  if (n == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, 4, c->stream));
+  launch_guide_eval(c->guide.dev, c->guide.pack, rec_dev, n, Y_dev, q_dev, c->wb.status, c->sms, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return status_to_rt(c, *c->h_status);
+}
+
+static rt_status guide_grad_impl(rt_ctx* c, const float* rec_dev, uint64_t n, float* loss_host) {
+  auto& G = c->guide;
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.dgrid, 0, G.n_grid * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.dW, 0, guide_wcount() * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(G.scratch, 0, 64, c->stream));
+  launch_guide_train(G.dev, G.pack, rec_dev, n, G.scratch, G.dW, G.dgrid, G.scratch + 1, c->wb.status, c->sms,
+                     c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  if (loss_host) CUDA_TRY(c, cudaMemcpyAsync(loss_host, G.scratch + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return status_to_rt(c, *c->h_status);
+}
+
+rt_status rt_guide_grad(rt_ctx* c, const float* rec_dev, uint64_t n, float* loss, float* dgrid_dev, float* dW_dev) {
+  if (rt_status e = guide_ready(c)) return e;
+  if (!rec_dev || n == 0) return fail(c, RT_ERR_ARG, "rt_guide_grad: no records");
+  if (((uintptr_t)rec_dev & 15u) != 0) return fail(c, RT_ERR_ARG, "rt_guide_grad: records must be 16-byte aligned");
+  cudaSetDevice(c->device);
+  if (rt_status e = guide_grad_impl(c, rec_dev, n, loss)) return e;
+  auto& G = c->guide;
+  if (dgrid_dev) CUDA_TRY(c, cudaMemcpyAsync(dgrid_dev, G.dgrid, G.n_grid * 4, cudaMemcpyDeviceToDevice, c->stream));
+  if (dW_dev) CUDA_TRY(c, cudaMemcpyAsync(dW_dev, G.dW, guide_wcount() * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_guide_train_step(rt_ctx* c, const float* rec_dev, uint64_t n, float* loss) {
+  if (rt_status e = guide_ready(c)) return e;
+  if (!rec_dev || n == 0) return fail(c, RT_ERR_ARG, "rt_guide_train_step: no records");
+  if (((uintptr_t)rec_dev & 15u) != 0)
+    return fail(c, RT_ERR_ARG, "rt_guide_train_step: records must be 16-byte aligned");
+  cudaSetDevice(c->device);
+  if (rt_status e = guide_grad_impl(c, rec_dev, n, loss)) return e;
+  auto& G = c->guide;
+  G.step += 1;
+  const float c1 = (float)(1.0 / (1.0 - std::pow((double)G.cfg.beta1, (double)G.step)));
+  const float c2 = (float)(1.0 / (1.0 - std::pow((double)G.cfg.beta2, (double)G.step)));
+  launch_adam(G.grid, G.dgrid, G.mg, G.vg, G.n_grid, G.cfg.lr_grid, G.cfg.beta1, G.cfg.beta2, G.cfg.eps, c1, c2,
+              c->stream);
+  launch_adam(G.W, G.dW, G.mW, G.vW, guide_wcount(), G.cfg.lr_mlp, G.cfg.beta1, G.cfg.beta2, G.cfg.eps, c1, c2,
+              c->stream);
+  launch_guide_pack(G.W, G.pack, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
 }
 
 rt_status rt_probe_l2(rt_ctx* c, uint64_t bytes, uint32_t iters, float* gbs) {

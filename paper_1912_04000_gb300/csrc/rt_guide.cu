@@ -1,0 +1,622 @@
+// Learned path guide on the GB300: hash-grid + SH encoding, a fused
+// 64-64-64-64-48 MLP on tcgen05 tensor cores (BF16 operands, FP32
+// accumulators in tensor memory), an 8-lobe von Mises-Fisher mixture head,
+// and online training (forward, loss gradient, backward, Adam) by the same
+// kernels.
+//
+// Definition (shared with the CPU oracle, written there in FP64):
+//   X (64)  = [hash-grid features of the position (16 levels x 2, trilinear;
+//              after Mueller et al. 2022, primes 1, 2654435761, 805459861),
+//              real SH of the normal up to degree 3 (16), one-hot band group
+//              (9), zeros (7)]
+//   H1 = relu(X W1), H2 = relu(H1 W2), H3 = relu(H2 W3), Y = H3 W4 (48)
+//   lobe j: pi = softmax(Y[5j]), mu = Y[5j+1..3] / |.|,
+//           kappa = 0.5 + softplus(Y[5j+4])
+//   q(w) = sum_j pi_j kappa_j / (2 pi (1 - e^{-2 kappa_j})) e^{kappa_j (mu_j.w - 1)}
+//   loss = -(1/N) sum_r (w_r / mean w) log q_r(omega_r)
+//
+// Tensor-core layout: a tile is 128 records (M = 128 = TMEM lanes).  Every
+// GEMM operand sits in shared memory in the K-major canonical layout
+// (rt_tc.cuh).  Forward B operands are W^T (N = out rows, K = in); backward
+// data-gradient B operands are W (N = in rows, K = out).  Weight gradients
+// dW = H^T dZ use A' = [H^T; 0] (128 rows, the upper 64 the input features,
+// K = the tile's 128 records) and B' = dZ^T, accumulated in TMEM across all
+// tiles of a CTA and added to global FP32 gradients at the end.
+#include <cmath>
+#include <cstdint>
+
+#include "rt_internal.h"
+#include "rt_tc.cuh"
+
+namespace srt {
+
+namespace {
+
+constexpr int kIn = 64, kHid = 64, kOut = 48, kLevels = 16, kLobes = 8;
+constexpr int kRows = 128;
+constexpr uint32_t kATileB = 16384;   // [128 x 64] BF16 activations
+constexpr uint32_t kSliceA = 4096;    // one 128 x 16 K-slice
+constexpr uint32_t kWPack = 61440;    // bytes of packed BF16 weights
+constexpr int kWSize = 15360;
+// byte offsets of layer l's forward (W^T) and backward (W) BF16 tiles in the
+// packed weights, and element offset of its FP32 master weights
+__host__ __device__ constexpr uint32_t wf_off(int l) { return 8192u * (uint32_t)l; }
+__host__ __device__ constexpr uint32_t wb_off(int l) { return 30720u + 8192u * (uint32_t)l; }
+__host__ __device__ constexpr int w_off(int l) { return 4096 * l; }
+
+__device__ __forceinline__ int layer_out(int l) { return l == 3 ? kOut : kHid; }
+
+// ---------------------------------------------------------------------------
+// encoding
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sh16(float x, float y, float z, float* o) {
+  const float pi = 3.14159265358979323846f;
+  const float rp = 1.0f / sqrtf(pi);
+  const float c0 = 0.5f * rp, c1 = sqrtf(3.0f) * 0.5f * rp, c2 = sqrtf(15.0f) * 0.5f * rp;
+  const float c3 = sqrtf(5.0f) * 0.25f * rp, c4 = sqrtf(15.0f) * 0.25f * rp;
+  const float c5 = sqrtf(35.0f / (2.0f * pi)) * 0.25f, c6 = sqrtf(105.0f) * 0.5f * rp;
+  const float c7 = sqrtf(21.0f / (2.0f * pi)) * 0.25f, c8 = sqrtf(7.0f) * 0.25f * rp, c9 = sqrtf(105.0f) * 0.25f * rp;
+  o[0] = c0;
+  o[1] = -c1 * y;
+  o[2] = c1 * z;
+  o[3] = -c1 * x;
+  o[4] = c2 * x * y;
+  o[5] = -c2 * y * z;
+  o[6] = c3 * (3.0f * z * z - 1.0f);
+  o[7] = -c2 * x * z;
+  o[8] = c4 * (x * x - y * y);
+  o[9] = -c5 * y * (3.0f * x * x - y * y);
+  o[10] = c6 * x * y * z;
+  o[11] = -c7 * y * (5.0f * z * z - 1.0f);
+  o[12] = c8 * z * (5.0f * z * z - 3.0f);
+  o[13] = -c7 * x * (5.0f * z * z - 1.0f);
+  o[14] = c9 * z * (x * x - y * y);
+  o[15] = -c5 * x * (x * x - 3.0f * y * y);
+}
+
+// Corner c (0..7) of level l at cell (cx, cy, cz): grid entry index.
+__device__ __forceinline__ uint32_t grid_index(const GuideDev& g, int l, uint32_t x, uint32_t y, uint32_t z) {
+  const uint32_t T = 1u << g.log2T;
+  if ((g.dense_mask >> l) & 1u) {
+    const uint32_t r1 = g.res[l] + 1u;
+    return x + y * r1 + z * r1 * r1;
+  }
+  return (x * 1u ^ y * 2654435761u ^ z * 805459861u) & (T - 1u);
+}
+
+struct LevelPos {
+  uint32_t c[3];
+  float f[3];
+};
+
+__device__ __forceinline__ LevelPos level_pos(const GuideDev& g, const float u[3], int l) {
+  LevelPos lp;
+  const float r = (float)g.res[l];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float s = u[a] * r;
+    float fl = floorf(s);
+    fl = fminf(fl, r - 1.0f);
+    lp.c[a] = (uint32_t)fl;
+    lp.f[a] = s - fl;
+  }
+  return lp;
+}
+
+__device__ __forceinline__ void unit_pos(const GuideDev& g, float3 p, float u[3]) {
+  u[0] = fminf(fmaxf((p.x - g.lo[0]) * g.inv_ext[0], 0.0f), 1.0f);
+  u[1] = fminf(fmaxf((p.y - g.lo[1]) * g.inv_ext[1], 0.0f), 1.0f);
+  u[2] = fminf(fmaxf((p.z - g.lo[2]) * g.inv_ext[2], 0.0f), 1.0f);
+}
+
+// X row of one record (FP32).
+__device__ __forceinline__ void encode(const GuideDev& g, float3 p, float3 n, uint32_t group, float* X) {
+  float u[3];
+  unit_pos(g, p, u);
+  const uint32_t T = 1u << g.log2T;
+#pragma unroll 1
+  for (int l = 0; l < kLevels; ++l) {
+    const LevelPos lp = level_pos(g, u, l);
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const float w = (dx ? lp.f[0] : 1.0f - lp.f[0]) * (dy ? lp.f[1] : 1.0f - lp.f[1]) * (dz ? lp.f[2] : 1.0f - lp.f[2]);
+      const uint32_t id = grid_index(g, l, lp.c[0] + dx, lp.c[1] + dy, lp.c[2] + dz);
+      const float2 v = __ldg((const float2*)g.grid + (size_t)l * T + id);
+      a0 = fmaf(w, v.x, a0);
+      a1 = fmaf(w, v.y, a1);
+    }
+    X[2 * l] = a0;
+    X[2 * l + 1] = a1;
+  }
+  sh16(n.x, n.y, n.z, X + 32);
+#pragma unroll
+  for (int i = 48; i < kIn; ++i) X[i] = 0.0f;
+  if (group < 9u) X[48 + group] = 1.0f;
+}
+
+// Scatter dL/dX[0..31] into the grid gradient.
+__device__ __forceinline__ void encode_backward(const GuideDev& g, float3 p, const float* dX, float* dgrid) {
+  float u[3];
+  unit_pos(g, p, u);
+  const uint32_t T = 1u << g.log2T;
+#pragma unroll 1
+  for (int l = 0; l < kLevels; ++l) {
+    const LevelPos lp = level_pos(g, u, l);
+    const float d0 = dX[2 * l], d1 = dX[2 * l + 1];
+    if (d0 == 0.0f && d1 == 0.0f) continue;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const float w = (dx ? lp.f[0] : 1.0f - lp.f[0]) * (dy ? lp.f[1] : 1.0f - lp.f[1]) * (dz ? lp.f[2] : 1.0f - lp.f[2]);
+      const uint32_t id = grid_index(g, l, lp.c[0] + dx, lp.c[1] + dy, lp.c[2] + dz);
+      float* dst = dgrid + ((size_t)l * T + id) * 2;
+      atomicAdd(dst, w * d0);
+      atomicAdd(dst + 1, w * d1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// head
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float softplusf(float x) { return x > 30.0f ? x : log1pf(expf(x)); }
+
+struct Mix {
+  float pi[kLobes], mu[kLobes][3], kappa[kLobes], mnorm[kLobes];
+};
+
+__device__ __forceinline__ void mixture(const float* Y, Mix& h) {
+  float mx = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < kLobes; ++j) mx = fmaxf(mx, Y[5 * j]);
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kLobes; ++j) {
+    h.pi[j] = expf(Y[5 * j] - mx);
+    s += h.pi[j];
+  }
+  const float is = 1.0f / s;
+#pragma unroll
+  for (int j = 0; j < kLobes; ++j) {
+    h.pi[j] *= is;
+    const float m0 = Y[5 * j + 1], m1 = Y[5 * j + 2], m2 = Y[5 * j + 3];
+    const float nm = fmaxf(sqrtf(m0 * m0 + m1 * m1 + m2 * m2), 1e-6f);
+    h.mnorm[j] = nm;
+    h.mu[j][0] = m0 / nm;
+    h.mu[j][1] = m1 / nm;
+    h.mu[j][2] = m2 / nm;
+    h.kappa[j] = 0.5f + softplusf(Y[5 * j + 4]);
+  }
+}
+
+__device__ __forceinline__ float vmf_pdf(float kappa, const float* mu, float3 w) {
+  const float c = mu[0] * w.x + mu[1] * w.y + mu[2] * w.z;
+  return kappa / (2.0f * 3.14159265358979323846f * (-expm1f(-2.0f * kappa))) * expf(kappa * (c - 1.0f));
+}
+
+__device__ __forceinline__ float mix_pdf(const Mix& h, float3 w) {
+  float q = 0.0f;
+#pragma unroll
+  for (int j = 0; j < kLobes; ++j) q += h.pi[j] * vmf_pdf(h.kappa[j], h.mu[j], w);
+  return q;
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory operand helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void put_row(unsigned char* A, uint32_t r, const float* v, int ncols) {
+  for (int c = 0; c < ncols; ++c)
+    *(uint16_t*)(A + (c >> 4) * kSliceA + tc_kmajor_off(r, c & 15)) = tc_bf16_bits(v[c]);
+}
+
+__device__ __forceinline__ float get_a(const unsigned char* A, uint32_t r, int c) {
+  return tc_bf16_val(*(const uint16_t*)(A + (c >> 4) * kSliceA + tc_kmajor_off(r, c & 15)));
+}
+
+// A' = [H^T; 0]: element (feature i, record b)
+__device__ __forceinline__ void put_at(unsigned char* Ap, uint32_t i, uint32_t b, uint16_t v) {
+  *(uint16_t*)(Ap + (b >> 4) * kSliceA + tc_kmajor_off(i, b & 15)) = v;
+}
+
+// B' = dZ^T with `out` rows: element (output o, record b)
+__device__ __forceinline__ void put_bt(unsigned char* Bp, uint32_t o, uint32_t b, uint32_t out, uint16_t v) {
+  *(uint16_t*)(Bp + (b >> 4) * (out * 32u) + tc_kmajor_off(o, b & 15)) = v;
+}
+
+// D (TMEM) = A B over nslices K-slices of 16.
+__device__ __forceinline__ void gemm(uint32_t d, const unsigned char* A, uint32_t a_slice, const unsigned char* B,
+                                     uint32_t b_slice, int nslices, uint32_t idesc, bool accumulate) {
+  for (int s = 0; s < nslices; ++s)
+    tc_mma_bf16(d, tc_smem_desc(smem_u32(A + s * a_slice)), tc_smem_desc(smem_u32(B + s * b_slice)), idesc,
+                (s > 0 || accumulate) ? 1u : 0u);
+}
+
+struct Sync {
+  uint64_t* mbar;
+  uint32_t phase;
+  bool ok;
+};
+
+// Thread 0 commits the issued MMAs; every thread waits for completion.
+__device__ __forceinline__ void mma_wait(Sync& s, uint32_t* status) {
+  if (threadIdx.x == 0) tc_commit(s.mbar);
+  const int bad = __syncthreads_or(tc_mbar_wait(s.mbar, s.phase, 1u << 24) ? 0 : 1);
+  s.phase ^= 1u;
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(status, ST_ITER);
+    s.ok = false;
+  }
+  tc_fence_after();
+}
+
+// All threads: generic smem writes done -> the next MMA may read them.
+__device__ __forceinline__ void publish() {
+  tc_fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ __forceinline__ void load_row(uint32_t tmem, uint32_t col, int ncols, float* v) {
+  const uint32_t warp = threadIdx.x >> 5;
+  for (int c = 0; c < ncols; c += 16) tc_tmem_ld16(tmem + ((warp * 32u) << 16) + col + (uint32_t)c, v + c);
+}
+
+__device__ __forceinline__ void load_weights(unsigned char* smem, const uint4* wpack) {
+  for (uint32_t i = threadIdx.x; i < kWPack / 16u; i += blockDim.x) ((uint4*)smem)[i] = __ldg(wpack + i);
+}
+
+// Record layout: 12 floats {pos.xyz, weight, nrm.xyz, group, omega.xyz, 0}.
+struct Rec {
+  float3 p, n, w;
+  float weight;
+  uint32_t group;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4* rec, uint64_t i) {
+  const float4 a = __ldg(rec + 3 * i), b = __ldg(rec + 3 * i + 1), c = __ldg(rec + 3 * i + 2);
+  Rec r;
+  r.p = make_float3(a.x, a.y, a.z);
+  r.weight = a.w;
+  r.n = make_float3(b.x, b.y, b.z);
+  r.group = (uint32_t)b.w;
+  r.w = make_float3(c.x, c.y, c.z);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// forward (evaluation): Y and q(omega) per record
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRows) k_guide_eval(GuideDev g, const uint4* __restrict__ wpack,
+                                                      const float4* __restrict__ rec, uint64_t n,
+                                                      float* __restrict__ Yout, float* __restrict__ qout,
+                                                      uint32_t* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* A0 = smem + kWPack;
+  unsigned char* A1 = A0 + kATileB;
+  uint64_t* mbar = (uint64_t*)(A1 + kATileB);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  load_weights(smem, wpack);
+  if (tid == 0) {
+    tc_mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc_tmem_alloc(tslot, 64);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  Sync sy{mbar, 0u, true};
+  const uint32_t id64 = tc_idesc_bf16(kRows, 64), id48 = tc_idesc_bf16(kRows, kOut);
+  const uint64_t ntiles = (n + kRows - 1) / kRows;
+  for (uint64_t tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
+    const uint64_t i = tile * kRows + tid;
+    float v[kIn];
+    Rec r{};
+    if (i < n) {
+      r = load_rec(rec, i);
+      encode(g, r.p, r.n, r.group, v);
+    } else {
+      for (int c = 0; c < kIn; ++c) v[c] = 0.0f;
+    }
+    put_row(A0, tid, v, kIn);
+    unsigned char* src = A0;
+    unsigned char* dst = A1;
+    for (int l = 0; l < 3; ++l) {
+      publish();
+      if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
+      mma_wait(sy, status);
+      load_row(tmem, 0, kHid, v);
+      for (int c = 0; c < kHid; ++c) v[c] = fmaxf(v[c], 0.0f);
+      put_row(dst, tid, v, kHid);
+      unsigned char* t = src;
+      src = dst;
+      dst = t;
+    }
+    publish();
+    if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
+    mma_wait(sy, status);
+    load_row(tmem, 0, kOut, v);
+    if (i < n && sy.ok) {
+      for (int c = 0; c < kOut; ++c) Yout[i * kOut + c] = v[c];
+      Mix h;
+      mixture(v, h);
+      qout[i] = mix_pdf(h, r.w);
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  tc_fence_after();
+  if (warp == 0) tc_tmem_dealloc(tmem, 64);
+}
+
+// ---------------------------------------------------------------------------
+// training: forward, loss gradient, backward, gradient accumulation
+// ---------------------------------------------------------------------------
+constexpr uint32_t kTrX = kWPack;
+constexpr uint32_t kTrH1 = kTrX + kATileB;
+constexpr uint32_t kTrH2 = kTrH1 + kATileB;
+constexpr uint32_t kTrH3 = kTrH2 + kATileB;
+constexpr uint32_t kTrDZ = kTrH3 + kATileB;
+constexpr uint32_t kTrAp = kTrDZ + kATileB;           // [128 x 128] = 32 KB
+constexpr uint32_t kTrBp = kTrAp + 8 * kSliceA;       // <= [64 x 128] = 16 KB
+constexpr uint32_t kTrMisc = kTrBp + 8 * 64 * 32;
+constexpr uint32_t kTrainSmem = kTrMisc + 64;
+static_assert(kTrainSmem <= 227 * 1024, "training kernel shared memory");
+
+__global__ void __launch_bounds__(kRows, 1) k_guide_train(GuideDev g, const uint4* __restrict__ wpack,
+                                                          const float4* __restrict__ rec, uint64_t n,
+                                                          const float* __restrict__ wsum, float* __restrict__ dW,
+                                                          float* __restrict__ dgrid, float* __restrict__ loss,
+                                                          uint32_t* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* AX = smem + kTrX;
+  unsigned char* AH[3] = {smem + kTrH1, smem + kTrH2, smem + kTrH3};
+  unsigned char* ADZ = smem + kTrDZ;
+  unsigned char* Ap = smem + kTrAp;
+  unsigned char* Bp = smem + kTrBp;
+  uint64_t* mbar = (uint64_t*)(smem + kTrMisc);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  float* lsum = (float*)(tslot + 1);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  load_weights(smem, wpack);
+  // A' rows 64..127 stay zero
+  for (uint32_t i = tid; i < 8u * kSliceA / 16u; i += blockDim.x) ((uint4*)Ap)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    tc_mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *lsum = 0.0f;
+  }
+  if (warp == 0) tc_tmem_alloc(tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  
+  Sync sy{mbar, 0u, true};
+  const uint32_t id64 = tc_idesc_bf16(kRows, 64), id48 = tc_idesc_bf16(kRows, kOut);
+  const float total = *wsum;
+  const uint64_t ntiles = (n + kRows - 1) / kRows;
+  bool first = true;
+  float my_loss = 0.0f;
+  for (uint64_t tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
+    const uint64_t i = tile * kRows + tid;
+    const bool valid = i < n;
+    float v[kIn];
+    Rec r{};
+    if (valid) {
+      r = load_rec(rec, i);
+      encode(g, r.p, r.n, r.group, v);
+    } else {
+      for (int c = 0; c < kIn; ++c) v[c] = 0.0f;
+    }
+    put_row(AX, tid, v, kIn);
+    // forward
+    const unsigned char* src = AX;
+    for (int l = 0; l < 3; ++l) {
+      publish();
+      if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
+      mma_wait(sy, status);
+      load_row(tmem, 0, kHid, v);
+      for (int c = 0; c < kHid; ++c) v[c] = fmaxf(v[c], 0.0f);
+      put_row(AH[l], tid, v, kHid);
+      src = AH[l];
+    }
+    publish();
+    if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
+    mma_wait(sy, status);
+    load_row(tmem, 0, kOut, v);
+    // head: loss and dL/dY
+    const float a = (valid && total > 0.0f) ? r.weight / total : 0.0f;
+    float dY[kOut];
+    for (int c = 0; c < kOut; ++c) dY[c] = 0.0f;
+    if (a > 0.0f) {
+      Mix h;
+      mixture(v, h);
+      float pj[kLobes], q = 0.0f;
+      for (int j = 0; j < kLobes; ++j) {
+        pj[j] = vmf_pdf(h.kappa[j], h.mu[j], r.w);
+        q += h.pi[j] * pj[j];
+      }
+      my_loss -= a * logf(q);
+      const float3 w = r.w;
+      for (int j = 0; j < kLobes; ++j) {
+        const float rj = h.pi[j] * pj[j] / q;
+        const float c = h.mu[j][0] * w.x + h.mu[j][1] * w.y + h.mu[j][2] * w.z;
+        dY[5 * j] = -a * (rj - h.pi[j]);
+        const float f = -a * rj * h.kappa[j] / h.mnorm[j];
+        dY[5 * j + 1] = f * (w.x - c * h.mu[j][0]);
+        dY[5 * j + 2] = f * (w.y - c * h.mu[j][1]);
+        dY[5 * j + 3] = f * (w.z - c * h.mu[j][2]);
+        const float k = h.kappa[j];
+        const float dlogp = 1.0f / k - 2.0f / expm1f(2.0f * k) + (c - 1.0f);
+        dY[5 * j + 4] = -a * rj * dlogp / (1.0f + expf(-v[5 * j + 4]));
+      }
+    }
+    // backward: layer l = 3 (W4, out 48) down to 0 (W1)
+    float* dz = dY;  // dZ_l of this row (FP32), out_l columns
+    float dh[kHid];
+    for (int l = 3; l >= 0; --l) {
+      const int out = layer_out(l);
+      const unsigned char* Hin = l == 0 ? AX : AH[l - 1];
+      // dZ_l into A (K = out) and B' (dZ^T); H_{l-1}^T into A' rows 0..63
+      put_row(ADZ, tid, dz, out);
+      for (int o = 0; o < out; ++o) put_bt(Bp, o, tid, out, tc_bf16_bits(dz[o]));
+      for (int c = 0; c < kHid; ++c) put_at(Ap, c, tid, *(const uint16_t*)(Hin + (c >> 4) * kSliceA + tc_kmajor_off(tid, c & 15)));
+      publish();
+      if (tid == 0) {
+        // dW_l (+)= H_{l-1}^T dZ_l : M 128 (64 used), N = out, K = 128 records
+        gemm(tmem + (64u * (uint32_t)(l + 1)), Ap, kSliceA, Bp, out * 32, 8, tc_idesc_bf16(kRows, out), !first);
+        // dH_{l-1} = dZ_l W_l^T : M 128, N 64, K = out
+        gemm(tmem, ADZ, kSliceA, smem + wb_off(l), 2048, out / 16, id64, false);
+      }
+      mma_wait(sy, status);
+      load_row(tmem, 0, kHid, dh);
+      if (l > 0) {
+        // dZ_{l-1} = dH_{l-1} where the forward activation was positive
+        for (int c = 0; c < kHid; ++c) dh[c] = get_a(AH[l - 1], tid, c) > 0.0f ? dh[c] : 0.0f;
+        for (int c = 0; c < kHid; ++c) v[c] = dh[c];
+        dz = v;
+      }
+      tc_fence_before();
+      __syncthreads();
+    }
+    // dX (first 32 columns = grid features) -> grid gradient
+    if (valid && a > 0.0f) encode_backward(g, r.p, dh, dgrid);
+    first = false;
+  }
+  // accumulated weight gradients: TMEM lanes 0..63 (warps 0, 1) = input rows
+  if (!first && sy.ok && warp < 2) {
+    for (int l = 0; l < 4; ++l) {
+      const int out = layer_out(l);
+      float row[kHid];
+      load_row(tmem, (64u * (uint32_t)(l + 1)), out, row);
+      const uint32_t in = warp * 32u + (tid & 31u);
+      for (int o = 0; o < out; ++o) atomicAdd(dW + w_off(l) + in * out + o, row[o]);
+    }
+  }
+  atomicAdd(lsum, my_loss);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) atomicAdd(loss, *lsum);
+  if (warp == 0) tc_tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------------------
+// small kernels: weight sum, Adam, BF16 packing, initialisation
+// ---------------------------------------------------------------------------
+__global__ void k_weight_sum(const float4* __restrict__ rec, uint64_t n, float* out) {
+  float s = 0.0f;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    s += __ldg(rec + 3 * i).w;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, uint64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+// FP32 master weights -> BF16 operand tiles (forward W^T, backward W).
+__global__ void k_pack_weights(const float* __restrict__ W, unsigned char* __restrict__ pack) {
+  for (int l = 0; l < 4; ++l) {
+    const int out = layer_out(l);
+    const float* Wl = W + w_off(l);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kIn * out; e += gridDim.x * blockDim.x) {
+      const int i = e / out, o = e - i * out;  // W_l[i][o]
+      const uint16_t b = tc_bf16_bits(Wl[e]);
+      // forward B: row o (N = out), K = i
+      *(uint16_t*)(pack + wf_off(l) + (i >> 4) * (out * 32) + tc_kmajor_off(o, i & 15)) = b;
+      // backward B: row i (N = in), K = o
+      *(uint16_t*)(pack + wb_off(l) + (o >> 4) * (kHid * 32) + tc_kmajor_off(i, o & 15)) = b;
+    }
+  }
+}
+
+__device__ __forceinline__ float philox_u(uint32_t seed0, uint32_t seed1, uint32_t a, uint32_t b) {
+  uint32_t k0 = seed0, k1 = seed1;
+  uint4 c = make_uint4(a, b, 0x6775u, 0x1de);
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return (float)(c.x >> 8) * 5.9604644775390625e-8f;
+}
+
+__global__ void k_guide_init(float* grid, uint64_t n_grid, float* W, uint32_t s0, uint32_t s1) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_grid; i += (uint64_t)gridDim.x * blockDim.x)
+    grid[i] = (philox_u(s0, s1, (uint32_t)i, (uint32_t)(i >> 32)) - 0.5f) * 2e-4f;
+  for (int l = 0; l < 4; ++l) {
+    const int out = layer_out(l);
+    const float s = sqrtf(6.0f / (float)(kIn + out));
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kIn * out; e += gridDim.x * blockDim.x)
+      W[w_off(l) + e] = (2.0f * philox_u(s0, s1, 0x80000000u + w_off(l) + e, 7u) - 1.0f) * s;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+size_t guide_eval_smem() { return kWPack + 2 * kATileB + 64; }
+size_t guide_train_smem() { return kTrainSmem; }
+uint32_t guide_wsize() { return kWSize; }
+uint32_t guide_wpack_bytes() { return kWPack; }
+
+void launch_guide_init(float* grid, uint64_t n_grid, float* W, uint64_t seed, cudaStream_t st) {
+  k_guide_init<<<512, 256, 0, st>>>(grid, n_grid, W, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+void launch_guide_pack(const float* W, void* pack, cudaStream_t st) {
+  k_pack_weights<<<16, 256, 0, st>>>(W, (unsigned char*)pack);
+}
+
+void launch_guide_eval(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* Y, float* q,
+                       uint32_t* status, int sms, cudaStream_t st) {
+  const size_t smem = guide_eval_smem();
+  cudaFuncSetAttribute(k_guide_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t tiles = (n + kRows - 1) / kRows;
+  uint64_t grid = (uint64_t)sms * 2;
+  if (grid > tiles) grid = tiles;
+  if (grid == 0) return;
+  k_guide_eval<<<(unsigned)grid, kRows, smem, st>>>(g, (const uint4*)pack, (const float4*)rec, n, Y, q, status);
+}
+
+void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* wsum, float* dW,
+                        float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st) {
+  cudaMemsetAsync(wsum, 0, sizeof(float), st);
+  k_weight_sum<<<sms * 4, 256, 0, st>>>((const float4*)rec, n, wsum);
+  const size_t smem = guide_train_smem();
+  cudaFuncSetAttribute(k_guide_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t tiles = (n + kRows - 1) / kRows;
+  uint64_t grid = (uint64_t)sms;
+  if (grid > tiles) grid = tiles;
+  if (grid == 0) return;
+  k_guide_train<<<(unsigned)grid, kRows, smem, st>>>(g, (const uint4*)pack, (const float4*)rec, n, wsum, dW, dgrid,
+                                                      loss, status);
+}
+
+void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
+                 float c1, float c2, cudaStream_t st) {
+  k_adam<<<1024, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+}
+
+}  // namespace srt

@@ -165,6 +165,27 @@ void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t*
 int num_sms(int device);
 int trace_blocks_per_sm(int block);
 
+// Learned guide (rt_guide.cu).
+struct GuideDev {
+  const float* grid;      // [16][2^log2T][2] FP32
+  uint32_t log2T;
+  uint32_t res[16];       // grid resolution per level
+  uint32_t dense_mask;    // bit l: level l indexed densely
+  float lo[3], inv_ext[3];
+};
+size_t guide_eval_smem();
+size_t guide_train_smem();
+uint32_t guide_wsize();
+uint32_t guide_wpack_bytes();
+void launch_guide_init(float* grid, uint64_t n_grid, float* W, uint64_t seed, cudaStream_t st);
+void launch_guide_pack(const float* W, void* pack, cudaStream_t st);
+void launch_guide_eval(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* Y, float* q,
+                       uint32_t* status, int sms, cudaStream_t st);
+void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* wsum, float* dW,
+                        float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st);
+void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
+                 float c1, float c2, cudaStream_t st);
+
 // Read-only view of a context for entry points defined outside rt_api.cu.
 struct CtxView {
   int device;

@@ -19,6 +19,7 @@
 #include <cstdint>
 
 #include "rt_internal.h"
+#include "rt_tc.cuh"
 
 namespace srt {
 
@@ -52,115 +53,12 @@ __global__ void __launch_bounds__(256) k_xyz_fp64(const double* __restrict__ s, 
   }
 }
 
-// ---------------------------------------------------------------------------
-// tcgen05 helpers (inline PTX, sm_100a family)
-// ---------------------------------------------------------------------------
 constexpr int kTileM = 128;        // pixels per tile = MMA M = TMEM lanes
 constexpr int kMmaN = 16;          // XYZ padded to 16 columns
 constexpr int kTmemCols = 32;      // smallest TMEM allocation
 constexpr uint32_t kATile = 4096;  // one 128 x 16 BF16 K-slice
 constexpr uint32_t kBTile = 512;   // one 16 x 16 BF16 K-slice
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Canonical K-major layout without swizzle: element (row r, k) of a K-slice
-// lives at (r % 8) * 16 + (r / 8) * 256 + (k % 8) * 2 + (k / 8) * 128 bytes:
-// core matrices of 8 rows x 16 bytes, 128 bytes apart along K (leading byte
-// offset) and 256 bytes apart along M/N (stride byte offset).
-__device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t k) {
-  return (r & 7u) * 16u + (r >> 3) * 256u + (k & 7u) * 2u + (k >> 3) * 128u;
-}
-
-// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
-// byte offset >> 4 (bits 16-29), stride byte offset >> 4 (bits 32-45),
-// descriptor version 1 (bit 46), no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
-         (1ull << 46);
-}
-
-// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 =
-// 1), B BF16 (bits 10-12 = 1), both K-major, N >> 3 (bits 17-22), M >> 4
-// (bits 24-28).
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMmaN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
-}
-
-// Waits for the phase with the given parity; gives up after max_iter polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t max_iter) {
-  for (uint32_t i = 0; i < max_iter; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float& x, float& y, float& z, float& w) {
-  uint32_t a, b, c, d;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  x = __uint_as_float(a);
-  y = __uint_as_float(b);
-  z = __uint_as_float(c);
-  w = __uint_as_float(d);
-}
-
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// BF16 bits, round to nearest even (inputs are finite).
-__device__ __forceinline__ uint16_t bf16_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
-}
-__device__ __forceinline__ float bf16_val(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
-
-// v = hi + mid + lo with each term the BF16 rounding of the remainder.
-__device__ __forceinline__ void split3(float v, uint16_t& h, uint16_t& m, uint16_t& l) {
-  h = bf16_bits(v);
-  const float r1 = v - bf16_val(h);
-  m = bf16_bits(r1);
-  const float r2 = r1 - bf16_val(m);
-  l = bf16_bits(r2);
-}
+constexpr uint32_t kIdesc = tc_idesc_bf16(kTileM, kMmaN);
 
 constexpr int kXyzThreads = 256;
 constexpr int kUnroll = 8;
@@ -184,20 +82,20 @@ __global__ void __launch_bounds__(kXyzThreads) k_xyz_tc(const double* __restrict
     const uint32_t n = i / (nk * 16u), k = i - n * nk * 16u;
     const float v = (n < 3u && k < bc) ? w[3u * k + n] : 0.0f;
     uint16_t h, m, l;
-    split3(v, h, m, l);
-    const uint32_t off = (k >> 4) * kBTile + kmajor_off(n, k & 15u);
+    tc_split3(v, h, m, l);
+    const uint32_t off = (k >> 4) * kBTile + tc_kmajor_off(n, k & 15u);
     *(uint16_t*)(Bm + off) = h;
     *(uint16_t*)(Bm + nk * kBTile + off) = m;
     *(uint16_t*)(Bm + 2u * nk * kBTile + off) = l;
   }
   if (tid == 0) {
-    mbar_init(mbar, 1);
+    tc_mbar_init(mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tslot, kTmemCols);
-  fence_before_sync();
+  if (warp == 0) tc_tmem_alloc(tslot, kTmemCols);
+  tc_fence_before();
   __syncthreads();
-  fence_after_sync();
+  tc_fence_after();
   const uint32_t tmem = *tslot;
 
   // products (a split, b split)
@@ -236,8 +134,8 @@ __global__ void __launch_bounds__(kXyzThreads) k_xyz_tc(const double* __restrict
             const uint32_t r = __umulhi(ee, inv_bc), k = ee - r * bc;
             const float val = (float)((h2 ? v[u].y : v[u].x) * inv_spp);
             uint16_t hh, mm, ll;
-            split3(val, hh, mm, ll);
-            const uint32_t off = (k >> 4) * kATile + kmajor_off(r, k & 15u);
+            tc_split3(val, hh, mm, ll);
+            const uint32_t off = (k >> 4) * kATile + tc_kmajor_off(r, k & 15u);
             *(uint16_t*)(A + off) = hh;
             if (n_split > 1) {
               *(uint16_t*)(A + nk * kATile + off) = mm;
@@ -247,31 +145,31 @@ __global__ void __launch_bounds__(kXyzThreads) k_xyz_tc(const double* __restrict
         }
       }
     }
-    fence_async_smem();
+    tc_fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      fence_after_sync();
+      tc_fence_after();
       const int nprod = n_split > 1 ? 6 : 1;
       uint32_t acc = 0;
       for (uint32_t kb = 0; kb < nk; ++kb)
         for (int pr = 0; pr < nprod; ++pr) {
-          const uint64_t da = smem_desc(smem_u32(A + pa[pr] * nk * kATile + kb * kATile));
-          const uint64_t db = smem_desc(smem_u32(Bm + pb[pr] * nk * kBTile + kb * kBTile));
-          mma_bf16(tmem, da, db, acc);
+          const uint64_t da = tc_smem_desc(smem_u32(A + pa[pr] * nk * kATile + kb * kATile));
+          const uint64_t db = tc_smem_desc(smem_u32(Bm + pb[pr] * nk * kBTile + kb * kBTile));
+          tc_mma_bf16(tmem, da, db, kIdesc, acc);
           acc = 1;
         }
-      mma_commit(mbar);
+      tc_commit(mbar);
     }
-    const int timed_out = __syncthreads_or(mbar_wait(mbar, phase, 1u << 24) ? 0 : 1);
+    const int timed_out = __syncthreads_or(tc_mbar_wait(mbar, phase, 1u << 24) ? 0 : 1);
     if (timed_out) {
       if (tid == 0) atomicOr(status, ST_ITER);
       ok = false;
     }
     phase ^= 1u;
-    fence_after_sync();
+    tc_fence_after();
     if (warp < 4) {  // warp w reads TMEM lanes 32w..32w+31 (pixels)
       float x, y, z, pad;
-      tmem_ld4(tmem + ((warp * 32u) << 16), x, y, z, pad);
+      tc_tmem_ld4(tmem + ((warp * 32u) << 16), x, y, z, pad);
       const uint32_t r = warp * 32u + lane;
       if (ok && r < rows) {
         float* o = xyz + 3 * (p0 + r);
@@ -280,11 +178,11 @@ __global__ void __launch_bounds__(kXyzThreads) k_xyz_tc(const double* __restrict
         o[2] = z;
       }
     }
-    fence_before_sync();
+    tc_fence_before();
     __syncthreads();
   }
-  fence_after_sync();
-  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  tc_fence_after();
+  if (warp == 0) tc_tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace

@@ -212,3 +212,54 @@ class Renderer:
         st = self.lib.rt_xyz(self._h, s.data_ptr(), s.shape[0], band_first, s.shape[1], spp, mode, out.data_ptr())
         self._check("rt_xyz", st)
         return out
+
+    # -- learned guide ------------------------------------------------------------
+    def guide_init(self, seed: int = 0, **cfg):
+        c = _native.GuideConfig()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self._check("rt_guide_init", self.lib.rt_guide_init(self._h, C.byref(c), seed))
+        self.guide_log2_table = c.log2_table or 19
+
+    def guide_set_params(self, grid=None, W=None):
+        g = None if grid is None else np.ascontiguousarray(grid, np.float32)
+        w = None if W is None else np.ascontiguousarray(W, np.float32)
+        st = self.lib.rt_guide_set_params(self._h, None if g is None else g.ctypes.data,
+                                          None if w is None else w.ctypes.data)
+        self._check("rt_guide_set_params", st)
+
+    def guide_get_params(self):
+        g = np.zeros(16 * (1 << self.guide_log2_table) * 2, np.float32)
+        w = np.zeros(_native.GUIDE_W_SIZE, np.float32)
+        self._check("rt_guide_get_params", self.lib.rt_guide_get_params(self._h, g.ctypes.data, w.ctypes.data))
+        return g, w
+
+    def _records(self, rec):
+        torch = self.torch
+        return torch.as_tensor(np.ascontiguousarray(rec, np.float32), device=self.device).contiguous()
+
+    def guide_eval(self, rec):
+        torch = self.torch
+        r = self._records(rec)
+        n = r.shape[0]
+        Y = torch.empty((n, 48), dtype=torch.float32, device=self.device)
+        q = torch.empty(n, dtype=torch.float32, device=self.device)
+        self._check("rt_guide_eval", self.lib.rt_guide_eval(self._h, r.data_ptr(), n, Y.data_ptr(), q.data_ptr()))
+        return Y, q
+
+    def guide_grad(self, rec):
+        torch = self.torch
+        r = self._records(rec)
+        loss = C.c_float()
+        dg = torch.empty(16 * (1 << self.guide_log2_table) * 2, dtype=torch.float32, device=self.device)
+        dw = torch.empty(_native.GUIDE_W_SIZE, dtype=torch.float32, device=self.device)
+        st = self.lib.rt_guide_grad(self._h, r.data_ptr(), r.shape[0], C.byref(loss), dg.data_ptr(), dw.data_ptr())
+        self._check("rt_guide_grad", st)
+        return loss.value, dg, dw
+
+    def guide_train_step(self, rec):
+        r = rec if hasattr(rec, "data_ptr") else self._records(rec)
+        loss = C.c_float()
+        self._check("rt_guide_train_step", self.lib.rt_guide_train_step(self._h, r.data_ptr(), r.shape[0],
+                                                                         C.byref(loss)))
+        return loss.value
