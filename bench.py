@@ -214,7 +214,7 @@ def main():
     ms_trace = 0.0
     n_trace = 0
     ext_rays = 0
-    stage_ms = [0.0] * 5
+    stage_ms = [0.0] * 7
     for _ in range(args.steps):
         st = step()["stats"]
         launches += st["kernel_launches"]
@@ -279,7 +279,7 @@ def main():
                 "hbm_peak_measured": 6777.0,
                 "algorithmic_bytes_per_ray": bytes_per_ray, "nodes_per_ray": ext_nodes,
                 "tris_per_ray": ext_tris, "launch_ms": launch_ms, "rays_per_launch": rays_per_launch,
-                "stage_ms_per_step": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz"],
+                "stage_ms_per_step": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
                                               [m / args.steps for m in stage_ms])),
             },
         }

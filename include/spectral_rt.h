@@ -94,6 +94,19 @@ typedef struct {
    * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
    * lane between refill checks; 0 = library default (tuned) */
   uint32_t trace_steps, trace_refill, shadow_steps, shadow_refill;
+  /* learned guide (rt_guide_init first): 1 = at Lambertian vertices
+   * 1..guide_depth the continuation is drawn from the guide with probability
+   * mis_alpha, else by cosine sampling, weighted by the one-sample MIS pdf */
+  uint32_t guided;
+  uint32_t guide_collect;      /* keep training records of every n-th path of a wave; 0 = none */
+  uint32_t guide_train_steps;  /* Adam steps after each wave on its records; 0 = guide frozen */
+  uint32_t guide_batch;        /* records per step; 0 = the wave's records / steps */
+  /* progressive rendering: this call renders samples [sample_first,
+   * sample_first + spp) (Philox counters), adds them to spectral_dev when
+   * accumulate = 1, and divides XYZ by spp_total (0 = spp) */
+  uint32_t sample_first;
+  uint32_t accumulate;
+  uint32_t spp_total;
   uint32_t reserved[2];
 } rt_render_opts;
 
@@ -110,9 +123,10 @@ typedef struct {
   float ms_render;         /* device time of the path tracing (events) */
   float ms_xyz;            /* device time of the XYZ contraction (events) */
   /* with rt_set_timing(ctx, 1): device time and launch count per stage:
-   * 0 camera rays, 1 closest hit, 2 shading + NEE, 3 sun rays, 4 XYZ */
-  float ms_stage[5];
-  uint32_t launches_stage[5];
+   * 0 camera rays, 1 closest hit, 2 shading + NEE, 3 sun rays, 4 XYZ,
+   * 5 guide sampling, 6 guide training */
+  float ms_stage[7];
+  uint32_t launches_stage[7];
 } rt_stats;
 
 /* Context on CUDA device `device`, enqueueing on `cuda_stream` (a

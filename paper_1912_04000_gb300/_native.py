@@ -41,7 +41,9 @@ class RenderOpts(C.Structure):
                 ("ctas_per_sm", C.c_uint32), ("probe_map_dev", C.c_void_p), ("probe_L_dev", C.c_void_p),
                 ("probe_sig_dev", C.c_void_p), ("use_graph", C.c_uint32), ("trace_variant", C.c_uint32),
                 ("trace_steps", C.c_uint32), ("trace_refill", C.c_uint32), ("shadow_steps", C.c_uint32),
-                ("shadow_refill", C.c_uint32), ("reserved", C.c_uint32 * 2)]
+                ("shadow_refill", C.c_uint32), ("guided", C.c_uint32), ("guide_collect", C.c_uint32),
+                ("guide_train_steps", C.c_uint32), ("guide_batch", C.c_uint32), ("sample_first", C.c_uint32),
+                ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("reserved", C.c_uint32 * 2)]
 
 
 class GuideConfig(C.Structure):
@@ -58,7 +60,7 @@ class Stats(C.Structure):
                 ("nodes_visited", C.c_uint64), ("tris_tested", C.c_uint64),
                 ("shadow_nodes_visited", C.c_uint64), ("shadow_tris_tested", C.c_uint64), ("waves", C.c_uint32),
                 ("kernel_launches", C.c_uint32), ("ms_render", C.c_float), ("ms_xyz", C.c_float),
-                ("ms_stage", C.c_float * 5), ("launches_stage", C.c_uint32 * 5)]
+                ("ms_stage", C.c_float * 7), ("launches_stage", C.c_uint32 * 7)]
 
     def as_dict(self):
         d = {}

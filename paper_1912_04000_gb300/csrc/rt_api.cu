@@ -66,6 +66,13 @@ struct rt_ctx {
     uint64_t n_grid = 0;
     uint32_t step = 0;
     GuideDev dev{};
+    // guided rendering buffers
+    float4* gq = nullptr;
+    uint32_t gq_cap = 0;
+    float4* raw = nullptr;
+    float* Lfinal = nullptr;
+    float* trec = nullptr;
+    uint64_t raw_cap = 0;
   } guide;
 };
 
@@ -145,7 +152,7 @@ bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1])
 struct EvTimer : StageTimer {
   std::vector<cudaEvent_t>& pool;
   size_t used = 0;
-  int open[STG_N] = {0, 0, 0, 0, 0};
+  int open[STG_N] = {};
   struct Pair {
     int stage, a, b;
   };
@@ -271,6 +278,10 @@ void rt_destroy(rt_ctx* c) {
   dfree(c->guide.dgrid);
   dfree(c->guide.dW);
   dfree(c->guide.scratch);
+  dfree(c->guide.gq);
+  dfree(c->guide.raw);
+  dfree(c->guide.Lfinal);
+  dfree(c->guide.trec);
   if (c->guide.pack) cudaFree(c->guide.pack);
   if (c->h_cams) cudaFreeHost(c->h_cams);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -469,6 +480,8 @@ rt_status rt_set_spectra(rt_ctx* c, const float* lambda_nm, uint32_t n_bands, co
   return RT_OK;
 }
 
+static void guide_train_enqueue(rt_ctx* c, const float* rec, uint64_t n);
+
 static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
                              uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
                              const rt_render_opts* opts, double* spectral_dev, float* xyz_dev, rt_stats* stats) {
@@ -485,6 +498,11 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
   if (o.trace_variant > 1) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
+  if (o.guided && !c->guide.init) return fail(c, RT_ERR_STATE, "rt_render: guided rendering needs rt_guide_init");
+  if (o.guide_train_steps && !(o.guided && o.guide_collect))
+    return fail(c, RT_ERR_ARG, "rt_render: guide training needs guided = 1 and guide_collect > 0");
+  if ((uint64_t)o.sample_first + spp > 0xFFFFFFFFull) return fail(c, RT_ERR_ARG, "rt_render: sample range overflows");
+  if (o.accumulate && !spectral_dev) return fail(c, RT_ERR_ARG, "rt_render: accumulate needs spectral_dev");
   if ((o.probe_map_dev != nullptr) != (o.probe_L_dev != nullptr) ||
       (o.probe_map_dev != nullptr) != (o.probe_sig_dev != nullptr))
     return fail(c, RT_ERR_ARG, "rt_render: probe_map, probe_L and probe_sig go together");
@@ -555,7 +573,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     accum = c->d_accum;
   }
   CUDA_TRY(c, cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(c, cudaMemsetAsync(accum, 0, PB64 * sizeof(double), st));
+  if (!o.accumulate) CUDA_TRY(c, cudaMemsetAsync(accum, 0, PB64 * sizeof(double), st));
   CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), st));
   CUDA_TRY(c, cudaMemsetAsync(c->wb.tot, 0, sizeof(Totals), st));
   if (o.trace_block && (o.trace_block > 256 || o.trace_block % 32))
@@ -582,8 +600,55 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   w.depth = depth;
   w.key0 = (uint32_t)seed;
   w.key1 = (uint32_t)(seed >> 32);
+  w.s_base = o.sample_first;
+  w.n_bands = c->sp.n_bands;
   const uint64_t total = PB64 * spp;
   const DevScene S = dev_scene(c);
+  // guided sampling buffers
+  GuideWave gw{};
+  uint32_t n_slots = 0, perm_mul = 1;
+  if (o.guided) {
+    auto& G = c->guide;
+    gw.on = true;
+    gw.depth = std::min<uint32_t>(G.cfg.guide_depth, depth);
+    gw.alpha = G.cfg.mis_alpha;
+    if (G.gq_cap < cap) {
+      dfree(G.gq);
+      G.gq_cap = 0;
+      CUDA_TRY(c, cudaMalloc(&G.gq, (size_t)cap * 3 * sizeof(float4)));
+      G.gq_cap = cap;
+    }
+    gw.gq = G.gq;
+    if (o.guide_collect) {
+      gw.collect = o.guide_collect;
+      gw.slots_per_vertex = (cap + o.guide_collect - 1) / o.guide_collect;
+      n_slots = gw.slots_per_vertex * gw.depth;
+      if (G.raw_cap < n_slots || !G.Lfinal) {
+        dfree(G.raw);
+        dfree(G.trec);
+        dfree(G.Lfinal);
+        G.raw_cap = 0;
+        CUDA_TRY(c, cudaMalloc(&G.raw, (size_t)n_slots * 4 * sizeof(float4)));
+        CUDA_TRY(c, cudaMalloc(&G.trec, (size_t)n_slots * 3 * sizeof(float4)));
+        CUDA_TRY(c, cudaMalloc(&G.Lfinal, (size_t)kMaxWave * sizeof(float)));
+        G.raw_cap = n_slots;
+      }
+      gw.raw = G.raw;
+      gw.Lfinal = G.Lfinal;
+      // odd multiplier coprime with n_slots: slot -> position is a bijection
+      auto gcd = [](uint64_t a, uint64_t b2) {
+        while (b2) {
+          uint64_t t = a % b2;
+          a = b2;
+          b2 = t;
+        }
+        return a;
+      };
+      perm_mul = (uint32_t)(2654435761ull % n_slots);
+      if (perm_mul == 0) perm_mul = 1;
+      while (gcd(perm_mul, n_slots) != 1) ++perm_mul;
+    }
+  }
   int launches = 0;
   uint32_t waves = 0;
   EvTimer timer(c->tpool);
@@ -591,10 +656,25 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   CUDA_TRY(c, cudaEventRecord(c->ev[0], st));
   for (uint64_t ws = 0; ws < total; ws += cap) {
     w.n = (uint32_t)std::min<uint64_t>(cap, total - ws);
-    w.s0 = (uint32_t)(ws / PB);
+    w.s0 = o.sample_first + (uint32_t)(ws / PB);
     w.r0 = (uint32_t)(ws % PB);
     CUDA_TRY(c, cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), st));
-    launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches, tm);
+    if (gw.collect) CUDA_TRY(c, cudaMemsetAsync(gw.raw, 0, (size_t)n_slots * 4 * sizeof(float4), st));
+    launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches, tm, &gw, &c->guide.dev,
+                c->guide.pack, c->sms);
+    if (gw.collect && o.guide_train_steps) {
+      if (tm) tm->begin(STG_TRAIN, st);
+      launch_guide_records(gw, n_slots, perm_mul, c->guide.trec, st);
+      const uint32_t steps = o.guide_train_steps;
+      uint64_t batch = o.guide_batch ? std::min<uint64_t>(o.guide_batch, n_slots) : std::max<uint64_t>(1, n_slots / steps);
+      for (uint32_t t = 0; t < steps; ++t) {
+        const uint64_t off = ((uint64_t)t * batch) % n_slots;
+        const uint64_t nb = std::min<uint64_t>(batch, n_slots - off);
+        guide_train_enqueue(c, c->guide.trec + 12 * off, nb);
+      }
+      if (tm) tm->end(STG_TRAIN, st);
+      launches += 1 + 5 * (int)steps;
+    }
     ++waves;
   }
   CUDA_TRY(c, cudaGetLastError());
@@ -606,7 +686,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     xw.band_count = band_count;
     xw.kpad = (band_count + 15) / 16 * 16;
     if (tm) tm->begin(STG_XYZ, st);
-    launch_xyz(accum, npix, xw, spp, (int)o.xyz_mode, xyz_dev, st, c->wb.status, c->sms);
+    launch_xyz(accum, npix, xw, o.spp_total ? o.spp_total : spp, (int)o.xyz_mode, xyz_dev, st, c->wb.status, c->sms);
     if (tm) tm->end(STG_XYZ, st);
     ++launches;
     CUDA_TRY(c, cudaGetLastError());
@@ -871,14 +951,38 @@ rt_status rt_guide_eval(rt_ctx* c, const float* rec_dev, uint64_t n, float* Y_de
   return status_to_rt(c, *c->h_status);
 }
 
+// Gradient of one batch into G.dgrid / G.dW (enqueued, no synchronisation).
+static void guide_grad_enqueue(rt_ctx* c, const float* rec_dev, uint64_t n) {
+  auto& G = c->guide;
+  cudaMemsetAsync(G.dgrid, 0, G.n_grid * 4, c->stream);
+  cudaMemsetAsync(G.dW, 0, guide_wcount() * 4, c->stream);
+  cudaMemsetAsync(G.scratch, 0, 64, c->stream);
+  launch_guide_train(G.dev, G.pack, rec_dev, n, G.scratch, G.dW, G.dgrid, G.scratch + 1, c->wb.status, c->sms,
+                     c->stream);
+}
+
+// Adam step on the gradient in G.dgrid / G.dW, then repack the BF16 weights.
+static void guide_update_enqueue(rt_ctx* c) {
+  auto& G = c->guide;
+  G.step += 1;
+  const float c1 = (float)(1.0 / (1.0 - std::pow((double)G.cfg.beta1, (double)G.step)));
+  const float c2 = (float)(1.0 / (1.0 - std::pow((double)G.cfg.beta2, (double)G.step)));
+  launch_adam(G.grid, G.dgrid, G.mg, G.vg, G.n_grid, G.cfg.lr_grid, G.cfg.beta1, G.cfg.beta2, G.cfg.eps, c1, c2,
+              c->stream);
+  launch_adam(G.W, G.dW, G.mW, G.vW, guide_wcount(), G.cfg.lr_mlp, G.cfg.beta1, G.cfg.beta2, G.cfg.eps, c1, c2,
+              c->stream);
+  launch_guide_pack(G.W, G.pack, c->stream);
+}
+
+static void guide_train_enqueue(rt_ctx* c, const float* rec, uint64_t n) {
+  guide_grad_enqueue(c, rec, n);
+  guide_update_enqueue(c);
+}
+
 static rt_status guide_grad_impl(rt_ctx* c, const float* rec_dev, uint64_t n, float* loss_host) {
   auto& G = c->guide;
   CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, 4, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(G.dgrid, 0, G.n_grid * 4, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(G.dW, 0, guide_wcount() * 4, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(G.scratch, 0, 64, c->stream));
-  launch_guide_train(G.dev, G.pack, rec_dev, n, G.scratch, G.dW, G.dgrid, G.scratch + 1, c->wb.status, c->sms,
-                     c->stream);
+  guide_grad_enqueue(c, rec_dev, n);
   CUDA_TRY(c, cudaGetLastError());
   if (loss_host) CUDA_TRY(c, cudaMemcpyAsync(loss_host, G.scratch + 1, 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -906,15 +1010,7 @@ rt_status rt_guide_train_step(rt_ctx* c, const float* rec_dev, uint64_t n, float
     return fail(c, RT_ERR_ARG, "rt_guide_train_step: records must be 16-byte aligned");
   cudaSetDevice(c->device);
   if (rt_status e = guide_grad_impl(c, rec_dev, n, loss)) return e;
-  auto& G = c->guide;
-  G.step += 1;
-  const float c1 = (float)(1.0 / (1.0 - std::pow((double)G.cfg.beta1, (double)G.step)));
-  const float c2 = (float)(1.0 / (1.0 - std::pow((double)G.cfg.beta2, (double)G.step)));
-  launch_adam(G.grid, G.dgrid, G.mg, G.vg, G.n_grid, G.cfg.lr_grid, G.cfg.beta1, G.cfg.beta2, G.cfg.eps, c1, c2,
-              c->stream);
-  launch_adam(G.W, G.dW, G.mW, G.vW, guide_wcount(), G.cfg.lr_mlp, G.cfg.beta1, G.cfg.beta2, G.cfg.eps, c1, c2,
-              c->stream);
-  launch_guide_pack(G.W, G.pack, c->stream);
+  guide_update_enqueue(c);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return RT_OK;

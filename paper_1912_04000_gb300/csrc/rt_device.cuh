@@ -160,4 +160,55 @@ __device__ __forceinline__ float tri_hit(const RayW& r, float3 va, float3 vb, fl
   return t > 0.0f ? t : -1.0f;
 }
 
+// ---------------------------------------------------------------------------
+// wavefront helpers shared by the path and guide kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t mix_sig(uint32_t h, uint32_t v) { return (h ^ v) * 16777619u; }
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// Warp-aggregated append of one element per lane with want = true; every lane
+// of the warp must call it (converged).  Returns the slot of this lane.
+__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t mask = __ballot_sync(0xffffffffu, want);
+  uint32_t base = 0;
+  const int leader = __ffs(mask) - 1;
+  if (mask != 0u && (int)lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
+  return base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+}
+
+// Path identity from the wave-local id: in-sample index r, sample s,
+// pixel, band index j.
+struct PathId {
+  uint32_t r, s, pix, j;
+};
+
+__device__ __forceinline__ PathId path_id(const WaveParams& w, uint32_t pid) {
+  PathId p;
+  p.r = w.r0 + pid;
+  p.s = w.s0;
+  if (p.r >= w.PB) {
+    p.r -= w.PB;
+    p.s += 1;
+  }
+  p.pix = p.r / w.band_count;
+  p.j = p.r - p.pix * w.band_count;
+  return p;
+}
+
+__device__ __forceinline__ void finalize(const WaveParams& w, const PathId& id, float L, uint32_t sg, double* accum,
+                                         const Probe& probe, bool record) {
+  if (L != 0.0f) accum[id.r] += (double)L;
+  if (record && probe.map != nullptr) {
+    const uint32_t slot = probe.map[id.pix];
+    if (slot != 0xFFFFFFFFu) {
+      const size_t q = ((size_t)slot * w.spp + (id.s - w.s_base)) * w.band_count + id.j;
+      probe.L[q] = L;
+      probe.sig[q] = sg;
+    }
+  }
+}
+
 }  // namespace srt

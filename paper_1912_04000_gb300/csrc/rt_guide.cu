@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "rt_device.cuh"
 #include "rt_internal.h"
 #include "rt_tc.cuh"
 
@@ -571,6 +572,188 @@ __global__ void k_guide_init(float* grid, uint64_t n_grid, float* W, uint32_t s0
   }
 }
 
+// ---------------------------------------------------------------------------
+// guided sampling inside the wavefront (one-sample MIS with cosine sampling)
+// ---------------------------------------------------------------------------
+// vMF direction (Jakob, "Numerically stable sampling of the von Mises-Fisher
+// distribution on S^2", 2012): w = 1 + log(u + (1 - u) e^{-2 kappa}) / kappa.
+__device__ __forceinline__ float3 vmf_sample(const float* mu, float kappa, float u, float v) {
+  const float w = 1.0f + logf(u + (1.0f - u) * expf(-2.0f * kappa)) / kappa;
+  const float r = sqrtf(fmaxf(0.0f, 1.0f - w * w));
+  float sp, cp;
+  sincospif(2.0f * v, &sp, &cp);
+  float3 t1, t2;
+  const float3 m = make_float3(mu[0], mu[1], mu[2]);
+  onb(m, t1, t2);
+  return make_float3(r * cp * t1.x + r * sp * t2.x + w * m.x, r * cp * t1.y + r * sp * t2.y + w * m.y,
+                     r * cp * t1.z + r * sp * t2.z + w * m.z);
+}
+
+constexpr uint32_t kSmWf = 30720;  // forward tiles only
+constexpr uint32_t kSampleSmem = kSmWf + 2 * kATileB + 64;
+
+__global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4* __restrict__ wpack, DevSpectra P,
+                                                        WaveParams w, uint32_t k, GuideWave gw,
+                                                        float4* __restrict__ qout, float4* __restrict__ sq,
+                                                        float* __restrict__ Lbuf, uint32_t* __restrict__ sigbuf,
+                                                        Counters* cnt, uint32_t cap, double* __restrict__ accum,
+                                                        Probe probe, bool record, uint32_t* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* A0 = smem + kSmWf;
+  unsigned char* A1 = A0 + kATileB;
+  uint64_t* mbar = (uint64_t*)(A1 + kATileB);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  for (uint32_t i = tid; i < kSmWf / 16u; i += blockDim.x) ((uint4*)smem)[i] = __ldg(wpack + i);
+  if (tid == 0) {
+    tc_mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc_tmem_alloc(tslot, 64);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  Sync sy{mbar, 0u, true};
+  const uint32_t id64 = tc_idesc_bf16(kRows, 64), id48 = tc_idesc_bf16(kRows, kOut);
+  const uint32_t count = min(cnt[k].g_count, cap);
+  const uint64_t ntiles = (count + kRows - 1) / kRows;
+  const float alpha = gw.alpha;
+  for (uint64_t tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
+    const uint32_t i = (uint32_t)(tile * kRows) + tid;
+    const bool valid = i < count;
+    float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
+    if (valid) {
+      q0 = __ldcs(gw.gq + 3 * i);
+      q1 = __ldcs(gw.gq + 3 * i + 1);
+      q2 = __ldcs(gw.gq + 3 * i + 2);
+    }
+    const uint32_t bits = __float_as_uint(q0.w), pid = bits & kPidMask;
+    const PathId id = path_id(w, pid);
+    const uint32_t band = w.band_first + id.j;
+    const uint32_t group = band * 9u / w.n_bands;
+    float v[kIn];
+    encode(g, f3(q0), f3(q1), group, v);
+    put_row(A0, tid, v, kIn);
+    unsigned char* src = A0;
+    unsigned char* dst = A1;
+    for (int l = 0; l < 3; ++l) {
+      publish();
+      if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
+      mma_wait(sy, status);
+      load_row(tmem, 0, kHid, v);
+      for (int c = 0; c < kHid; ++c) v[c] = fmaxf(v[c], 0.0f);
+      put_row(dst, tid, v, kHid);
+      unsigned char* t = src;
+      src = dst;
+      dst = t;
+    }
+    publish();
+    if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
+    mma_wait(sy, status);
+    load_row(tmem, 0, kOut, v);
+    tc_fence_before();
+    __syncthreads();
+    // one-sample MIS: guide with probability alpha, else cosine sampling
+    bool cont = false;
+    float4 r0 = make_float4(0, 0, 0, 0), r1 = r0;
+    float3 om = make_float3(0, 0, 1);
+    float pdf = 0.0f, c = 0.0f, Tn = 0.0f;
+    if (valid && sy.ok) {
+      Mix h;
+      mixture(v, h);
+      const float3 n = f3(q1);
+      const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k + 1u), w.key0, w.key1);
+      if (u01(u1.x) < alpha) {
+        const float ul = u01(u1.y);
+        int j = 0;
+        float acc = h.pi[0];
+        while (j < kLobes - 1 && ul >= acc) acc += h.pi[++j];
+        om = vmf_sample(h.mu[j], h.kappa[j], u01(u1.z), u01(u1.w));
+      } else {
+        const uint4 u0 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k), w.key0, w.key1);
+        const float rr = sqrtf(u01(u0.z));
+        const float zz = sqrtf(fmaxf(0.0f, 1.0f - u01(u0.z)));
+        float s2, c2;
+        sincospif(2.0f * u01(u0.w), &s2, &c2);
+        float3 b1, b2;
+        onb(n, b1, b2);
+        om = make_float3(rr * c2 * b1.x + rr * s2 * b2.x + zz * n.x, rr * c2 * b1.y + rr * s2 * b2.y + zz * n.y,
+                         rr * c2 * b1.z + rr * s2 * b2.z + zz * n.z);
+      }
+      c = dot(n, om);
+      pdf = alpha * mix_pdf(h, om) + (1.0f - alpha) * fmaxf(c, 0.0f) * 0.31830988618379067f;
+      if (c > 0.0f && pdf > 0.0f) {
+        cont = true;
+        Tn = q1.w * q2.x * 0.31830988618379067f * c / pdf;
+        r0 = make_float4(q0.x, q0.y, q0.z, __uint_as_float(bits));
+        r1 = make_float4(om.x, om.y, om.z, Tn);
+      } else {
+        // no continuation: the path ends here, after its pending sun ray
+        const uint32_t ss = __float_as_uint(q2.y);
+        if (ss != 0xFFFFFFFFu) {
+          float4* e = sq + 2 * ss;
+          e->w = __uint_as_float(__float_as_uint(e->w) | kFlagTerm);
+        } else {
+          const float Lp = Lbuf[pid];
+          finalize(w, id, Lp, record ? sigbuf[pid] : 0u, accum, probe, record);
+          if (gw.Lfinal) gw.Lfinal[pid] = Lp;
+        }
+      }
+      if (gw.collect != 0u && pid % gw.collect == 0u) {
+        float4* raw = gw.raw + 4u * ((k - 1u) * gw.slots_per_vertex + pid / gw.collect);
+        raw[0] = make_float4(q0.x, q0.y, q0.z, (float)group);
+        float* r1p = (float*)(raw + 1);
+        r1p[0] = q1.x;
+        r1p[1] = q1.y;
+        r1p[2] = q1.z;
+        raw[2] = make_float4(om.x, om.y, om.z, pdf);
+        raw[3] = make_float4(c, Tn, 1.0f, (float)pid);
+      }
+    }
+    const uint32_t slot = warp_append(&cnt[k + 1].q_count, cont);
+    if (cont) {
+      if (slot < cap) {
+        __stcs(qout + 2 * slot, r0);
+        __stcs(qout + 2 * slot + 1, r1);
+      } else {
+        atomicOr(status, ST_QUEUE);
+      }
+    }
+  }
+  tc_fence_after();
+  if (warp == 0) tc_tmem_dealloc(tmem, 64);
+}
+
+// Training records from the wave's slots: incident radiance along the sampled
+// direction L_in = (final radiance - radiance before the next vertex) /
+// throughput after the vertex; weight L_in cos / MIS pdf.  Slot s goes to
+// position (s * perm_mul) mod n_slots so that any contiguous batch spans
+// the whole image.
+__global__ void k_guide_records(GuideWave gw, uint32_t n_slots, uint32_t perm_mul, float4* __restrict__ out) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_slots; s += gridDim.x * blockDim.x) {
+    const float4* raw = gw.raw + 4u * s;
+    const float4 a = raw[0], b = raw[1], c = raw[2], d = raw[3];
+    float wt = 0.0f;
+    if (d.z > 0.5f && d.y > 0.0f && c.w > 0.0f) {
+      const uint32_t pid = (uint32_t)d.w;
+      const float Lin = (gw.Lfinal[pid] - b.w) / d.y;
+      wt = fmaxf(Lin, 0.0f) * d.x / c.w;
+    }
+    const uint32_t pos = (uint32_t)(((uint64_t)s * perm_mul) % n_slots);
+    float4* o = out + 3u * pos;
+    if (wt > 0.0f) {
+      o[0] = make_float4(a.x, a.y, a.z, wt);
+      o[1] = make_float4(b.x, b.y, b.z, a.w);
+      o[2] = make_float4(c.x, c.y, c.z, 0.0f);
+    } else {
+      o[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      o[1] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+      o[2] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -617,6 +800,18 @@ void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, u
 void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
                  float c1, float c2, cudaStream_t st) {
   k_adam<<<1024, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+}
+
+void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& P, const WaveParams& w, uint32_t k,
+                         const GuideWave& gw, const WaveBufs& b, double* accum, const Probe& probe, bool record,
+                         int sms, cudaStream_t st) {
+  cudaFuncSetAttribute(k_guide_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
+  k_guide_sample<<<sms * 3, kRows, kSampleSmem, st>>>(g, (const uint4*)pack, P, w, k, gw, b.q[(k + 1) & 1], b.sq, b.L,
+                                                      b.sig, b.cnt, b.cap, accum, probe, record, b.status);
+}
+
+void launch_guide_records(const GuideWave& gw, uint32_t n_slots, uint32_t perm_mul, float* train_rec, cudaStream_t st) {
+  k_guide_records<<<1024, 256, 0, st>>>(gw, n_slots, perm_mul, (float4*)train_rec);
 }
 
 }  // namespace srt

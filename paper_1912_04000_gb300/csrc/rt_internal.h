@@ -74,6 +74,26 @@ struct WaveParams {
   uint32_t band_first, band_count;
   uint32_t spp, depth;
   uint32_t key0, key1;
+  uint32_t s_base;     // first sample index of the render call (probe rows)
+  uint32_t n_bands;    // bands of the spectra (guide band groups)
+};
+
+// Guided sampling of one wave (on == false: plain cosine sampling).
+// gq: guide queries, 3 float4 each: {origin, bits(pid | flags)}, {normal,
+//   throughput}, {rho, bits(sun-ray slot or 0xFFFFFFFF), 0, 0}.
+// raw: training slots (collect != 0), one per (guided vertex v, path id with
+//   pid % collect == 0) at (v - 1) * slots_per_vertex + pid / collect, 4
+//   float4: {origin, group}, {normal, radiance before vertex v + 1},
+//   {omega, MIS pdf}, {cos, throughput after v, valid, pid}.
+struct GuideWave {
+  bool on;
+  uint32_t depth;
+  float alpha;
+  float4* gq;
+  uint32_t collect;
+  uint32_t slots_per_vertex;
+  float4* raw;
+  float* Lfinal;  // final radiance per path id (collect != 0)
 };
 
 // Per-wave device counters, one row per vertex k (0 .. depth).
@@ -82,6 +102,8 @@ struct Counters {
   uint32_t q_fetch;     // traversal work fetch
   uint32_t s_count;     // shadow rays emitted at vertex k
   uint32_t s_fetch;
+  uint32_t g_count;     // guide queries emitted at vertex k
+  uint32_t g_pad;
 };
 
 struct Totals {
@@ -89,7 +111,8 @@ struct Totals {
 };
 
 // Per-stage CUDA-event timing of a render (host side, optional).
-enum Stage { STG_CAMERA = 0, STG_TRACE = 1, STG_SHADE = 2, STG_SHADOW = 3, STG_XYZ = 4, STG_N = 5 };
+enum Stage { STG_CAMERA = 0, STG_TRACE = 1, STG_SHADE = 2, STG_SHADOW = 3, STG_XYZ = 4, STG_GUIDE = 5, STG_TRAIN = 6,
+             STG_N = 7 };
 struct StageTimer {
   virtual void begin(int stage, cudaStream_t st) = 0;
   virtual void end(int stage, cudaStream_t st) = 0;
@@ -132,9 +155,11 @@ struct LaunchCfg {
   int shadow_steps, shadow_refill;  // sun rays: the same
 };
 
+struct GuideDev;
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe,
-                 cudaStream_t st, int* launches, StageTimer* timer);
+                 cudaStream_t st, int* launches, StageTimer* timer, const GuideWave* gw = nullptr,
+                 const GuideDev* gdev = nullptr, const void* gpack = nullptr, int sms = 0);
 void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaStream_t st, int sms);
 void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st);
 void launch_trace_closest_rays(const DevScene& S, const float* o, const float* d, uint64_t n, float* t,
@@ -185,6 +210,10 @@ void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, u
                         float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st);
 void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
                  float c1, float c2, cudaStream_t st);
+void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& P, const WaveParams& w, uint32_t k,
+                         const GuideWave& gw, const WaveBufs& b, double* accum, const Probe& probe, bool record,
+                         int sms, cudaStream_t st);
+void launch_guide_records(const GuideWave& gw, uint32_t n_slots, uint32_t perm_mul, float* train_rec, cudaStream_t st);
 
 // Read-only view of a context for entry points defined outside rt_api.cu.
 struct CtxView {

@@ -21,41 +21,6 @@ namespace srt {
 
 namespace {
 
-__device__ __forceinline__ uint32_t mix_sig(uint32_t h, uint32_t v) { return (h ^ v) * 16777619u; }
-
-__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
-
-// Warp-aggregated append of one element per lane with want = true; every lane
-// of the warp must call it (converged).  Returns the slot of this lane.
-__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t mask = __ballot_sync(0xffffffffu, want);
-  uint32_t base = 0;
-  const int leader = __ffs(mask) - 1;
-  if (mask != 0u && (int)lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
-  return base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
-}
-
-// Path identity from the wave-local id: in-sample index r, sample s,
-// pixel, band index j.
-struct PathId {
-  uint32_t r, s, pix, j;
-};
-
-__device__ __forceinline__ PathId path_id(const WaveParams& w, uint32_t pid) {
-  PathId p;
-  p.r = w.r0 + pid;
-  p.s = w.s0;
-  if (p.r >= w.PB) {
-    p.r -= w.PB;
-    p.s += 1;
-  }
-  p.pix = p.r / w.band_count;
-  p.j = p.r - p.pix * w.band_count;
-  return p;
-}
-
 // ---------------------------------------------------------------------------
 // BVH traversal as a resumable per-lane state machine.  One call of a step
 // function visits one interior node (both children tested, the far one
@@ -298,19 +263,6 @@ __device__ __forceinline__ float shadow_T(const DevScene& S, const DevSpectra& P
   return T;
 }
 
-__device__ __forceinline__ void finalize(const WaveParams& w, const PathId& id, float L, uint32_t sg, double* accum,
-                                         const Probe& probe, bool record) {
-  if (L != 0.0f) accum[id.r] += (double)L;
-  if (record && probe.map != nullptr) {
-    const uint32_t slot = probe.map[id.pix];
-    if (slot != 0xFFFFFFFFu) {
-      const size_t q = ((size_t)slot * w.spp + id.s) * w.band_count + id.j;
-      probe.L[q] = L;
-      probe.sig[q] = sg;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -401,20 +353,21 @@ __global__ void __launch_bounds__(128) k_trace(DevScene S, const float4* __restr
   }
 }
 
-template <bool RECORD>
+template <bool RECORD, bool GUIDED>
 __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                const float4* __restrict__ qin, const float2* __restrict__ hit,
                                                float4* __restrict__ qout, float4* __restrict__ sq,
                                                float* __restrict__ Lbuf, uint32_t* __restrict__ sigbuf,
                                                Counters* cnt, uint32_t cap, double* __restrict__ accum,
-                                               Probe probe, uint32_t* status) {
+                                               Probe probe, uint32_t* status, GuideWave gw) {
   const uint32_t count = min(cnt[k].q_count, cap);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
     const uint32_t i = base + lane;
-    bool emit_next = false, emit_shadow = false;
+    bool emit_next = false, emit_shadow = false, emit_guide = false;
     float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, s0 = n0, s1 = n0;
+    float g_rho = 0.0f;
     if (i < count) {
       const float4 a = __ldcs(qin + 2 * i), b = __ldcs(qin + 2 * i + 1);
       const float2 h = __ldcs(hit + i);
@@ -427,6 +380,9 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
       const uint32_t band = w.band_first + id.j;
       float Lp = Lbuf[pid];
       uint32_t sg = RECORD ? sigbuf[pid] : 0u;
+      // training slot of the previous (guided) vertex: radiance gathered so far
+      if (GUIDED && gw.collect != 0u && k >= 2u && k - 1u <= gw.depth && pid % gw.collect == 0u)
+        ((float*)(gw.raw + 4u * ((k - 2u) * gw.slots_per_vertex + pid / gw.collect) + 1u))[3] = Lp;
       const int leaf = __float_as_int(h.y);
       bool terminate = false;
       if (leaf < 0) {
@@ -467,6 +423,12 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
           }
           if (k == w.depth) {
             terminate = true;
+          } else if (GUIDED && k <= gw.depth) {
+            // the continuation is sampled by the guide kernel (one-sample MIS)
+            emit_guide = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | kFlagCovered));
+            n1 = make_float4(n.x, n.y, n.z, T);
+            g_rho = m.z;
           } else {
             // cosine-weighted continuation, weight rho
             const float rr = sqrtf(u01(u.z));
@@ -516,6 +478,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
       }
       if (terminate && !emit_shadow) {
         finalize(w, id, Lp, sg, accum, probe, RECORD);
+        if (GUIDED && gw.Lfinal) gw.Lfinal[pid] = Lp;
       } else {
         Lbuf[pid] = Lp;
         if (RECORD) sigbuf[pid] = sg;
@@ -523,6 +486,19 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
     }
     const uint32_t slot_n = warp_append(&cnt[k + 1].q_count, emit_next);
     const uint32_t slot_s = warp_append(&cnt[k].s_count, emit_shadow);
+    if (GUIDED) {
+      const uint32_t slot_g = warp_append(&cnt[k].g_count, emit_guide);
+      if (emit_guide) {
+        if (slot_g < cap) {
+          gw.gq[3 * slot_g] = n0;
+          gw.gq[3 * slot_g + 1] = n1;
+          gw.gq[3 * slot_g + 2] =
+              make_float4(g_rho, __uint_as_float(emit_shadow && slot_s < cap ? slot_s : 0xFFFFFFFFu), 0.0f, 0.0f);
+        } else {
+          atomicOr(status, ST_QUEUE);
+        }
+      }
+    }
     if (emit_next) {
       if (slot_n < cap) {
         __stcs(qout + 2 * slot_n, n0);
@@ -547,7 +523,7 @@ __global__ void __launch_bounds__(128) k_shadow(DevScene S, DevSpectra P, WavePa
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
-                                                uint32_t* status, int steps, int refill) {
+                                                uint32_t* status, int steps, int refill, float* Lfinal) {
   const uint32_t count = min(cnt[k].s_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
   const uint32_t lane = threadIdx.x & 31u;
@@ -601,6 +577,7 @@ __global__ void __launch_bounds__(128) k_shadow(DevScene S, DevSpectra P, WavePa
       if (RECORD) sg = mix_sig(sigbuf[pid], ng);
       if (bits & kFlagTerm) {
         finalize(w, id, Lp, sg, accum, probe, RECORD);
+        if (Lfinal) Lfinal[pid] = Lp;
       } else {
         Lbuf[pid] = Lp;
         if (RECORD) sigbuf[pid] = sg;
@@ -700,21 +677,21 @@ void launch_trace(const LaunchCfg& lc, bool robust, const DevScene& S, const flo
 
 template <bool RECORD, bool COUNT, bool WW>
 void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
-              const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st) {
+              const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, cudaStream_t st) {
   k_shadow<RECORD, COUNT, WW><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
                                                                       probe, b.tot, b.status, lc.shadow_steps,
-                                                                      lc.shadow_refill);
+                                                                      lc.shadow_refill, Lfinal);
 }
 
 void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
-                   const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st) {
+                   const WaveBufs& b, double* accum, const Probe& probe, float* Lf, cudaStream_t st) {
   const bool ww = lc.variant == 1;
   if (lc.record) {
-    if (lc.counting) ww ? shadow_t<true, true, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<true, true, false>(lc, S, P, w, k, b, accum, probe, st);
-    else ww ? shadow_t<true, false, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<true, false, false>(lc, S, P, w, k, b, accum, probe, st);
+    if (lc.counting) ww ? shadow_t<true, true, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<true, true, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
+    else ww ? shadow_t<true, false, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<true, false, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
   } else {
-    if (lc.counting) ww ? shadow_t<false, true, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<false, true, false>(lc, S, P, w, k, b, accum, probe, st);
-    else ww ? shadow_t<false, false, true>(lc, S, P, w, k, b, accum, probe, st) : shadow_t<false, false, false>(lc, S, P, w, k, b, accum, probe, st);
+    if (lc.counting) ww ? shadow_t<false, true, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<false, true, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
+    else ww ? shadow_t<false, false, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<false, false, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
   }
 }
 
@@ -722,7 +699,11 @@ void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, 
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st,
-                 int* launches, StageTimer* tm) {
+                 int* launches, StageTimer* tm, const GuideWave* gwp, const GuideDev* gdev, const void* gpack,
+                 int sms) {
+  GuideWave gw{};
+  if (gwp) gw = *gwp;
+  const bool guided = gw.on;
   const bool rec = lc.record;
   if (tm) tm->begin(STG_CAMERA, st);
   k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec);
@@ -737,15 +718,30 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
     launch_trace(lc, k == 1, S, qin, b, k, st);
     if (tm) tm->end(STG_TRACE, st);
     if (tm) tm->begin(STG_SHADE, st);
-    if (rec)
-      k_shade<true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt,
-                                                             b.cap, accum, probe, b.status);
-    else
-      k_shade<false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt,
-                                                              b.cap, accum, probe, b.status);
+    if (guided) {
+      if (rec)
+        k_shade<true, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
+                                                                     b.cnt, b.cap, accum, probe, b.status, gw);
+      else
+        k_shade<false, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
+                                                                      b.cnt, b.cap, accum, probe, b.status, gw);
+    } else {
+      if (rec)
+        k_shade<true, false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
+                                                                      b.cnt, b.cap, accum, probe, b.status, gw);
+      else
+        k_shade<false, false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L,
+                                                                       b.sig, b.cnt, b.cap, accum, probe, b.status, gw);
+    }
     if (tm) tm->end(STG_SHADE, st);
+    if (guided && k <= gw.depth && k < w.depth) {
+      if (tm) tm->begin(STG_GUIDE, st);
+      launch_guide_sample(*gdev, gpack, P, w, k, gw, b, accum, probe, rec, sms, st);
+      if (tm) tm->end(STG_GUIDE, st);
+      ++nl;
+    }
     if (tm) tm->begin(STG_SHADOW, st);
-    launch_shadow(lc, S, P, w, k, b, accum, probe, st);
+    launch_shadow(lc, S, P, w, k, b, accum, probe, guided ? gw.Lfinal : nullptr, st);
     if (tm) tm->end(STG_SHADOW, st);
     nl += 3;
   }

@@ -96,7 +96,9 @@ class Renderer:
                band_count: Optional[int] = None, spectral: bool = True, xyz: bool = True,
                xyz_mode: int = _native.XYZ_BF16X3, wave_capacity: int = 0, probe_pixels=None,
                trace_block: int = 0, ctas_per_sm: int = 0, out_spectral=None, out_xyz=None, trace_variant: int = 0,
-               trace_steps: int = 0, trace_refill: int = 0, shadow_steps: int = 0, shadow_refill: int = 0):
+               trace_steps: int = 0, trace_refill: int = 0, shadow_steps: int = 0, shadow_refill: int = 0,
+               guided: bool = False, guide_collect: int = 0, guide_train_steps: int = 0, guide_batch: int = 0,
+               sample_first: int = 0, accumulate: bool = False, spp_total: int = 0):
         """Returns dict(spectral [P, band_count] f64 sums over samples,
         xyz [P, 3] f32, stats, and probe_L / probe_sig [n_probe, spp, band_count]
         when probe_pixels is given)."""
@@ -117,6 +119,9 @@ class Renderer:
         opts.trace_variant = trace_variant
         opts.trace_steps, opts.trace_refill = trace_steps, trace_refill
         opts.shadow_steps, opts.shadow_refill = shadow_steps, shadow_refill
+        opts.guided, opts.guide_collect = int(guided), guide_collect
+        opts.guide_train_steps, opts.guide_batch = guide_train_steps, guide_batch
+        opts.sample_first, opts.accumulate, opts.spp_total = sample_first, int(accumulate), spp_total
         out = {}
         if probe_pixels is not None:
             pp = torch.as_tensor(np.asarray(probe_pixels, np.int64), device=dev)
