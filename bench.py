@@ -42,6 +42,19 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1536, help="oracle sample size (pixels at full spp/bands)")
+    ap.add_argument("--guided-mse", action="store_true",
+                    help="equal-time MSE of the guided vs the plain tracer against a high-spp plain reference")
+    ap.add_argument("--mse-width", type=int, default=256)
+    ap.add_argument("--mse-height", type=int, default=192)
+    ap.add_argument("--mse-ref-spp", type=int, default=4096)
+    ap.add_argument("--mse-spp", type=int, default=256)
+    ap.add_argument("--mse-train-spp", type=int, default=32)
+    ap.add_argument("--guide-depth", type=int, default=2)
+    ap.add_argument("--guide-collect", type=int, default=4)
+    ap.add_argument("--guide-steps", type=int, default=8)
+    ap.add_argument("--mis-alpha", type=float, default=0.7)
+    ap.add_argument("--mse-configs", default="",
+                    help="extra guide settings depth:collect:steps:alpha separated by ';' (one shared reference)")
     return ap.parse_args()
 
 
@@ -166,10 +179,111 @@ def run_reference(args):
     return 0
 
 
+def run_guided_mse(args):
+    """Equal-time MSE, guided vs plain, on the nave view at a reduced
+    resolution (the 4096-spp plain reference is rendered by the GPU plain
+    tracer, itself parity-checked against the oracle)."""
+    import numpy as np
+    import torch
+
+    from paper_1912_04000_gb300 import scenes
+    from paper_1912_04000_gb300.renderer import Renderer
+
+    wl = scenes.nave(width=args.mse_width, height=args.mse_height)
+    R = Renderer(0).load(wl)
+    dev = R.device
+    P, B = wl.n_pixels, wl.band_count
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize(dev)
+        return out, time.perf_counter() - t0
+
+    # reference: plain tracer, independent seed
+    ref_sp = torch.zeros((P, B), dtype=torch.float64, device=dev)
+    ref, t_ref = timed(lambda: R.render(wl.cameras, args.mse_ref_spp, wl.depth, 777, out_spectral=ref_sp))
+    ref_xyz = ref["xyz"].cpu().numpy().astype(np.float64)
+
+    def mse(x):
+        return float(np.mean((x - ref_xyz) ** 2))
+
+    def relmse(x):
+        return float(np.mean((x - ref_xyz) ** 2 / (ref_xyz ** 2 + 1e-2 * np.mean(ref_xyz ** 2))))
+
+    # plain tracer at equal spp, and its time per spp
+    q_sp = torch.zeros((P, B), dtype=torch.float64, device=dev)
+    q_out, t_q = timed(lambda: R.render(wl.cameras, args.mse_spp, wl.depth, 0, out_spectral=q_sp))
+    q_xyz = q_out["xyz"].cpu().numpy().astype(np.float64)
+    t_per_spp = t_q / args.mse_spp
+
+    settings = [(args.guide_depth, args.guide_collect, args.guide_steps, args.mis_alpha, args.mse_train_spp)]
+    for item in filter(None, args.mse_configs.split(";")):
+        f = item.split(":")
+        settings.append((int(f[0]), int(f[1]), int(f[2]), float(f[3]), int(f[4]) if len(f) > 4 else args.mse_train_spp))
+    results = []
+    for depth_g, collect, steps, alpha, train_spp in settings:
+        # guided: online training over the first passes, then frozen
+        R.guide_init(seed=11, guide_depth=depth_g, mis_alpha=alpha)
+        g_sp = torch.zeros((P, B), dtype=torch.float64, device=dev)
+        n_train = min(train_spp, args.mse_spp)
+        stage = [0.0] * 7
+
+        def guided_run():
+            out = None
+            for s_ in range(n_train):
+                out = R.render(wl.cameras, 1, wl.depth, 0, out_spectral=g_sp, sample_first=s_, accumulate=s_ > 0,
+                               spp_total=args.mse_spp, guided=True, guide_collect=collect, guide_train_steps=steps)
+                for i_, v_ in enumerate(out["stats"]["ms_stage"]):
+                    stage[i_] += v_
+            if args.mse_spp > n_train:
+                out = R.render(wl.cameras, args.mse_spp - n_train, wl.depth, 0, out_spectral=g_sp,
+                               sample_first=n_train, accumulate=n_train > 0, spp_total=args.mse_spp, guided=True)
+                for i_, v_ in enumerate(out["stats"]["ms_stage"]):
+                    stage[i_] += v_
+            return out
+
+        R.set_timing(True)
+        g_out, t_guided = timed(guided_run)
+        R.set_timing(False)
+        g_xyz = g_out["xyz"].cpu().numpy().astype(np.float64)
+        # plain tracer with as many spp as fit in the guided time
+        spp_eq = max(1, int(round(t_guided / t_per_spp)))
+        p_sp = torch.zeros((P, B), dtype=torch.float64, device=dev)
+        p_out, t_plain = timed(lambda: R.render(wl.cameras, spp_eq, wl.depth, 0, out_spectral=p_sp))
+        p_xyz = p_out["xyz"].cpu().numpy().astype(np.float64)
+        results.append({
+            "guide_depth": depth_g, "guide_collect": collect, "guide_steps_per_wave": steps, "mis_alpha": alpha,
+            "train_spp": n_train,
+            "stage_ms": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
+                                 [round(v_, 1) for v_ in stage])),
+            "guided": {"seconds": t_guided, "spp": args.mse_spp, "mse": mse(g_xyz), "relmse": relmse(g_xyz)},
+            "plain_equal_time": {"seconds": t_plain, "spp": spp_eq, "mse": mse(p_xyz), "relmse": relmse(p_xyz)},
+            "mse_ratio_equal_time": mse(p_xyz) / max(mse(g_xyz), 1e-300),
+            "mse_ratio_equal_spp": mse(q_xyz) / max(mse(g_xyz), 1e-300),
+            "relmse_ratio_equal_time": relmse(p_xyz) / max(relmse(g_xyz), 1e-300),
+        })
+    best = max(results, key=lambda r: r["mse_ratio_equal_time"])
+    line = {
+        "metric": "equal-time MSE, guided vs plain (nave, XYZ, vs 4096-spp plain reference)",
+        "config": {"workload": f"nave_200k_{args.mse_width}x{args.mse_height}_b81_d8",
+                   "reference_spp": args.mse_ref_spp, "guided_spp": args.mse_spp, "train_spp": args.mse_train_spp},
+        "plain_equal_spp": {"spp": args.mse_spp, "seconds": t_q, "mse": mse(q_xyz), "relmse": relmse(q_xyz)},
+        "runs": results,
+        "mse_ratio_plain_over_guided_equal_time": best["mse_ratio_equal_time"],
+        "reference_seconds": t_ref,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.guided_mse:
+        return run_guided_mse(args)
 
     import numpy as np
     import torch

@@ -216,14 +216,19 @@ rt_status rt_render_static(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, 
  * Parameters: grid [16][2^log2_table][2] and W = W1 [64][64] | W2 [64][64] |
  * W3 [64][64] | W4 [64][48] (row-major [in][out]), FP32 masters.
  * Training record (12 floats): {pos.xyz, weight}, {normal.xyz, band group},
- * {omega.xyz, 0}; loss -(1/N) sum_r (weight_r / mean weight) log q_r(omega_r). */
+ * {omega.xyz, 0}; loss -(1/N) sum_r (weight_r / mean weight) log q_r(omega_r).
+ * In a guided render the direct sun at a guided vertex is estimated by two
+ * strategies combined with the balance heuristic: next-event sampling of the
+ * sun cone and the guided continuation escaping into the cone; both the
+ * continuation (incident radiance of the path suffix) and the sun sample
+ * (sun radiance x transmittance) become training records. */
 typedef struct {
   uint32_t log2_table;   /* 10..22; 0 = 19 */
   float n_min, n_max;    /* 0 = 16, 2048 */
   float lr_grid, lr_mlp; /* Adam learning rates; 0 = 1e-2, 1e-3 */
   float beta1, beta2;    /* 0 = 0.9, 0.99 */
   float eps;             /* 0 = 1e-15 */
-  float mis_alpha;       /* probability of sampling the guide at a guided vertex; 0 = 0.5 */
+  float mis_alpha;       /* probability of sampling the guide at a guided vertex; 0 = 0.7 */
   uint32_t guide_depth;  /* vertices 1..guide_depth are guided; 0 = 2 */
   uint32_t reserved[6];
 } rt_guide_config;

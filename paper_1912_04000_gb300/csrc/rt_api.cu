@@ -68,6 +68,7 @@ struct rt_ctx {
     GuideDev dev{};
     // guided rendering buffers
     float4* gq = nullptr;
+    float* wesc = nullptr;
     uint32_t gq_cap = 0;
     float4* raw = nullptr;
     float* Lfinal = nullptr;
@@ -279,6 +280,7 @@ void rt_destroy(rt_ctx* c) {
   dfree(c->guide.dW);
   dfree(c->guide.scratch);
   dfree(c->guide.gq);
+  dfree(c->guide.wesc);
   dfree(c->guide.raw);
   dfree(c->guide.Lfinal);
   dfree(c->guide.trec);
@@ -614,11 +616,14 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     gw.alpha = G.cfg.mis_alpha;
     if (G.gq_cap < cap) {
       dfree(G.gq);
+      dfree(G.wesc);
       G.gq_cap = 0;
       CUDA_TRY(c, cudaMalloc(&G.gq, (size_t)cap * 3 * sizeof(float4)));
+      CUDA_TRY(c, cudaMalloc(&G.wesc, (size_t)cap * sizeof(float)));
       G.gq_cap = cap;
     }
     gw.gq = G.gq;
+    gw.wesc = G.wesc;
     if (o.guide_collect) {
       gw.collect = o.guide_collect;
       gw.slots_per_vertex = (cap + o.guide_collect - 1) / o.guide_collect;
@@ -628,8 +633,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
         dfree(G.trec);
         dfree(G.Lfinal);
         G.raw_cap = 0;
-        CUDA_TRY(c, cudaMalloc(&G.raw, (size_t)n_slots * 4 * sizeof(float4)));
-        CUDA_TRY(c, cudaMalloc(&G.trec, (size_t)n_slots * 3 * sizeof(float4)));
+        CUDA_TRY(c, cudaMalloc(&G.raw, (size_t)n_slots * kRawF4 * sizeof(float4)));
+        CUDA_TRY(c, cudaMalloc(&G.trec, (size_t)n_slots * 2 * 3 * sizeof(float4)));
         CUDA_TRY(c, cudaMalloc(&G.Lfinal, (size_t)kMaxWave * sizeof(float)));
         G.raw_cap = n_slots;
       }
@@ -644,9 +649,10 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
         }
         return a;
       };
-      perm_mul = (uint32_t)(2654435761ull % n_slots);
+      const uint64_t n_rec = 2ull * n_slots;
+      perm_mul = (uint32_t)(2654435761ull % n_rec);
       if (perm_mul == 0) perm_mul = 1;
-      while (gcd(perm_mul, n_slots) != 1) ++perm_mul;
+      while (gcd(perm_mul, n_rec) != 1) ++perm_mul;
     }
   }
   int launches = 0;
@@ -659,17 +665,18 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     w.s0 = o.sample_first + (uint32_t)(ws / PB);
     w.r0 = (uint32_t)(ws % PB);
     CUDA_TRY(c, cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), st));
-    if (gw.collect) CUDA_TRY(c, cudaMemsetAsync(gw.raw, 0, (size_t)n_slots * 4 * sizeof(float4), st));
+    if (gw.collect) CUDA_TRY(c, cudaMemsetAsync(gw.raw, 0, (size_t)n_slots * kRawF4 * sizeof(float4), st));
     launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches, tm, &gw, &c->guide.dev,
                 c->guide.pack, c->sms);
     if (gw.collect && o.guide_train_steps) {
       if (tm) tm->begin(STG_TRAIN, st);
       launch_guide_records(gw, n_slots, perm_mul, c->guide.trec, st);
       const uint32_t steps = o.guide_train_steps;
-      uint64_t batch = o.guide_batch ? std::min<uint64_t>(o.guide_batch, n_slots) : std::max<uint64_t>(1, n_slots / steps);
+      const uint64_t n_rec = 2ull * n_slots;
+      uint64_t batch = o.guide_batch ? std::min<uint64_t>(o.guide_batch, n_rec) : std::max<uint64_t>(1, n_rec / steps);
       for (uint32_t t = 0; t < steps; ++t) {
-        const uint64_t off = ((uint64_t)t * batch) % n_slots;
-        const uint64_t nb = std::min<uint64_t>(batch, n_slots - off);
+        const uint64_t off = ((uint64_t)t * batch) % n_rec;
+        const uint64_t nb = std::min<uint64_t>(batch, n_rec - off);
         guide_train_enqueue(c, c->guide.trec + 12 * off, nb);
       }
       if (tm) tm->end(STG_TRAIN, st);
@@ -852,7 +859,7 @@ rt_status rt_guide_init(rt_ctx* c, const rt_guide_config* cfg_in, uint64_t seed)
   if (cfg.beta1 == 0.0f) cfg.beta1 = 0.9f;
   if (cfg.beta2 == 0.0f) cfg.beta2 = 0.99f;
   if (cfg.eps == 0.0f) cfg.eps = 1e-15f;
-  if (cfg.mis_alpha == 0.0f) cfg.mis_alpha = 0.5f;
+  if (cfg.mis_alpha == 0.0f) cfg.mis_alpha = 0.7f;
   if (!cfg.guide_depth) cfg.guide_depth = 2;
   if (cfg.log2_table < 10 || cfg.log2_table > 22 || !(cfg.n_min >= 1.0f) || !(cfg.n_max >= cfg.n_min) ||
       !(cfg.mis_alpha > 0.0f && cfg.mis_alpha < 1.0f) || cfg.guide_depth > (uint32_t)kMaxDepth)

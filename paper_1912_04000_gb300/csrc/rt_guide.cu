@@ -683,14 +683,29 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
       }
       c = dot(n, om);
       pdf = alpha * mix_pdf(h, om) + (1.0f - alpha) * fmaxf(c, 0.0f) * 0.31830988618379067f;
+      // direct sun by two strategies, balance heuristic: rescale the pending
+      // sun sample, weight a later escape of the continuation into the cone
+      const float p_cone = 1.0f / (2.0f * 3.14159265358979323846f * P.one_minus_cos);
+      const uint32_t ss = __float_as_uint(q2.y);
+      float3 wn = make_float3(0, 0, 1);
+      float cn = 0.0f;
+      if (ss != 0xFFFFFFFFu) {
+        float4* e = sq + 2 * ss + 1;
+        const float4 sv = *e;
+        wn = f3(sv);
+        cn = dot(n, wn);
+        const float pm = alpha * mix_pdf(h, wn) + (1.0f - alpha) * fmaxf(cn, 0.0f) * 0.31830988618379067f;
+        e->w = sv.w * (p_cone / (p_cone + pm));
+      }
       if (c > 0.0f && pdf > 0.0f) {
         cont = true;
         Tn = q1.w * q2.x * 0.31830988618379067f * c / pdf;
-        r0 = make_float4(q0.x, q0.y, q0.z, __uint_as_float(bits));
+        const bool in_cone = dot(om, P.sun) >= P.cos_max;
+        gw.wesc[pid] = in_cone ? pdf / (pdf + p_cone) : 0.0f;
+        r0 = make_float4(q0.x, q0.y, q0.z, __uint_as_float(bits | kFlagGuidedEsc));
         r1 = make_float4(om.x, om.y, om.z, Tn);
       } else {
         // no continuation: the path ends here, after its pending sun ray
-        const uint32_t ss = __float_as_uint(q2.y);
         if (ss != 0xFFFFFFFFu) {
           float4* e = sq + 2 * ss;
           e->w = __uint_as_float(__float_as_uint(e->w) | kFlagTerm);
@@ -701,7 +716,7 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
         }
       }
       if (gw.collect != 0u && pid % gw.collect == 0u) {
-        float4* raw = gw.raw + 4u * ((k - 1u) * gw.slots_per_vertex + pid / gw.collect);
+        float4* raw = gw.raw + kRawF4 * ((k - 1u) * gw.slots_per_vertex + pid / gw.collect);
         raw[0] = make_float4(q0.x, q0.y, q0.z, (float)group);
         float* r1p = (float*)(raw + 1);
         r1p[0] = q1.x;
@@ -709,6 +724,10 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
         r1p[2] = q1.z;
         raw[2] = make_float4(om.x, om.y, om.z, pdf);
         raw[3] = make_float4(c, Tn, 1.0f, (float)pid);
+        raw[4] = make_float4(wn.x, wn.y, wn.z, cn);
+        float* r5p = (float*)(raw + 5);  // r5.x (sun radiance) is written by the sun-ray kernel
+        r5p[1] = p_cone;
+        r5p[2] = (ss != 0xFFFFFFFFu && cn > 0.0f) ? 1.0f : 0.0f;
       }
     }
     const uint32_t slot = warp_append(&cnt[k + 1].q_count, cont);
@@ -725,32 +744,41 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
   if (warp == 0) tc_tmem_dealloc(tmem, 64);
 }
 
-// Training records from the wave's slots: incident radiance along the sampled
-// direction L_in = (final radiance - radiance before the next vertex) /
-// throughput after the vertex; weight L_in cos / MIS pdf.  Slot s goes to
-// position (s * perm_mul) mod n_slots so that any contiguous batch spans
-// the whole image.
+// Training records from the wave's slots, two per slot: the continuation,
+// with incident radiance L_in = (final radiance - radiance before the next
+// vertex) / throughput after the vertex and weight L_in cos / MIS pdf; and
+// the sun sample, weight (sun radiance x transmittance) cos / p_cone.  Record
+// r goes to position (r * perm_mul) mod (2 n_slots) so that any contiguous
+// batch spans the whole image.
+__device__ __forceinline__ void put_record(float4* out, uint32_t pos, float3 p, float wt, float3 n, float group,
+                                           float3 om) {
+  float4* o = out + 3u * pos;
+  if (wt > 0.0f) {
+    o[0] = make_float4(p.x, p.y, p.z, wt);
+    o[1] = make_float4(n.x, n.y, n.z, group);
+    o[2] = make_float4(om.x, om.y, om.z, 0.0f);
+  } else {
+    o[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    o[1] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+    o[2] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+  }
+}
+
 __global__ void k_guide_records(GuideWave gw, uint32_t n_slots, uint32_t perm_mul, float4* __restrict__ out) {
+  const uint64_t n_rec = 2ull * n_slots;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_slots; s += gridDim.x * blockDim.x) {
-    const float4* raw = gw.raw + 4u * s;
-    const float4 a = raw[0], b = raw[1], c = raw[2], d = raw[3];
+    const float4* raw = gw.raw + kRawF4 * s;
+    const float4 a = raw[0], b = raw[1], c = raw[2], d = raw[3], e = raw[4], f = raw[5];
     float wt = 0.0f;
     if (d.z > 0.5f && d.y > 0.0f && c.w > 0.0f) {
       const uint32_t pid = (uint32_t)d.w;
       const float Lin = (gw.Lfinal[pid] - b.w) / d.y;
       wt = fmaxf(Lin, 0.0f) * d.x / c.w;
     }
-    const uint32_t pos = (uint32_t)(((uint64_t)s * perm_mul) % n_slots);
-    float4* o = out + 3u * pos;
-    if (wt > 0.0f) {
-      o[0] = make_float4(a.x, a.y, a.z, wt);
-      o[1] = make_float4(b.x, b.y, b.z, a.w);
-      o[2] = make_float4(c.x, c.y, c.z, 0.0f);
-    } else {
-      o[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      o[1] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-      o[2] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-    }
+    float ws = 0.0f;
+    if (d.z > 0.5f && f.z > 0.5f && f.y > 0.0f) ws = fmaxf(f.x, 0.0f) * e.w / f.y;
+    put_record(out, (uint32_t)(((uint64_t)(2u * s) * perm_mul) % n_rec), f3(a), wt, f3(b), a.w, f3(c));
+    put_record(out, (uint32_t)(((uint64_t)(2u * s + 1u) * perm_mul) % n_rec), f3(a), ws, f3(b), a.w, f3(e));
   }
 }
 

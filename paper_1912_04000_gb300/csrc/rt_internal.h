@@ -19,6 +19,7 @@ constexpr uint32_t kPidBits = 24;      // path id bits in a queue entry
 constexpr uint32_t kPidMask = (1u << kPidBits) - 1u;
 constexpr uint32_t kFlagCovered = 1u << 31;  // direct sun already estimated by NEE
 constexpr uint32_t kFlagTerm = 1u << 30;     // shadow ray: path ends at this vertex
+constexpr uint32_t kFlagGuidedEsc = 1u << 29;  // sun reached by escape counts with MIS weight wesc[pid]
 constexpr uint32_t kMaxWave = 1u << kPidBits;
 
 // Scene on the device.
@@ -81,15 +82,22 @@ struct WaveParams {
 // Guided sampling of one wave (on == false: plain cosine sampling).
 // gq: guide queries, 3 float4 each: {origin, bits(pid | flags)}, {normal,
 //   throughput}, {rho, bits(sun-ray slot or 0xFFFFFFFF), 0, 0}.
+// At a guided vertex the direct sun is estimated by two strategies combined
+// with the balance heuristic: next-event sampling of the sun cone (weight
+// p_cone / (p_cone + p_mix)) and the guided continuation escaping into the
+// cone (weight p_mix / (p_cone + p_mix), kept per path in wesc).
 // raw: training slots (collect != 0), one per (guided vertex v, path id with
-//   pid % collect == 0) at (v - 1) * slots_per_vertex + pid / collect, 4
+//   pid % collect == 0) at (v - 1) * slots_per_vertex + pid / collect, 6
 //   float4: {origin, group}, {normal, radiance before vertex v + 1},
-//   {omega, MIS pdf}, {cos, throughput after v, valid, pid}.
+//   {omega, MIS pdf}, {cos, throughput after v, valid, pid},
+//   {sun sample direction, cos}, {sun radiance x transmittance, p_cone, valid, 0}.
+constexpr uint32_t kRawF4 = 6;
 struct GuideWave {
   bool on;
   uint32_t depth;
   float alpha;
   float4* gq;
+  float* wesc;    // per path id: MIS weight of a sun escape after a guided vertex
   uint32_t collect;
   uint32_t slots_per_vertex;
   float4* raw;
@@ -213,6 +221,7 @@ void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float
 void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& P, const WaveParams& w, uint32_t k,
                          const GuideWave& gw, const WaveBufs& b, double* accum, const Probe& probe, bool record,
                          int sms, cudaStream_t st);
+// Two training records per slot (continuation, sun sample): 2 * n_slots.
 void launch_guide_records(const GuideWave& gw, uint32_t n_slots, uint32_t perm_mul, float* train_rec, cudaStream_t st);
 
 // Read-only view of a context for entry points defined outside rt_api.cu.

@@ -382,12 +382,15 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
       uint32_t sg = RECORD ? sigbuf[pid] : 0u;
       // training slot of the previous (guided) vertex: radiance gathered so far
       if (GUIDED && gw.collect != 0u && k >= 2u && k - 1u <= gw.depth && pid % gw.collect == 0u)
-        ((float*)(gw.raw + 4u * ((k - 2u) * gw.slots_per_vertex + pid / gw.collect) + 1u))[3] = Lp;
+        ((float*)(gw.raw + kRawF4 * ((k - 2u) * gw.slots_per_vertex + pid / gw.collect) + 1u))[3] = Lp;
       const int leaf = __float_as_int(h.y);
       bool terminate = false;
       if (leaf < 0) {
         if (RECORD) sg = mix_sig(sg, 0xFFFFFFFFu);
-        if (!covered && dot(d, P.sun) >= P.cos_max) Lp += T * __ldg(P.sunL + band);
+        if (dot(d, P.sun) >= P.cos_max) {
+          if (!covered) Lp += T * __ldg(P.sunL + band);
+          else if (GUIDED && (bits & kFlagGuidedEsc)) Lp += T * __ldg(P.sunL + band) * gw.wesc[pid];
+        }
         terminate = true;
       } else {
         const float3 p = madd(o, h.x, d);
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
               n1 = make_float4(rd.x, rd.y, rd.z, T * (Rs + Ts));
             } else {
               const float3 po = madd(p, -S.eps, n);
-              n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | (covered ? kFlagCovered : 0u)));
+              n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | (bits & (kFlagCovered | kFlagGuidedEsc))));
               n1 = make_float4(d.x, d.y, d.z, T * (Rs + Ts));
             }
           }
@@ -523,7 +526,9 @@ __global__ void __launch_bounds__(128) k_shadow(DevScene S, DevSpectra P, WavePa
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
-                                                uint32_t* status, int steps, int refill, float* Lfinal) {
+                                                uint32_t* status, int steps, int refill, float* Lfinal,
+                                                GuideWave gw) {
+  const bool rec_sun = gw.on && gw.collect != 0u && k <= gw.depth && k < w.depth;
   const uint32_t count = min(cnt[k].s_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
   const uint32_t lane = threadIdx.x & 31u;
@@ -573,6 +578,9 @@ __global__ void __launch_bounds__(128) k_shadow(DevScene S, DevSpectra P, WavePa
       const uint32_t pid = bits & kPidMask;
       const PathId id = path_id(w, pid);
       const float Lp = Lbuf[pid] + contrib * T;
+      if (rec_sun && pid % gw.collect == 0u)
+        ((float*)(gw.raw + kRawF4 * ((k - 1u) * gw.slots_per_vertex + pid / gw.collect) + 5u))[0] =
+            T * __ldg(P.sunL + w.band_first + id.j);
       uint32_t sg = 0;
       if (RECORD) sg = mix_sig(sigbuf[pid], ng);
       if (bits & kFlagTerm) {
@@ -677,21 +685,23 @@ void launch_trace(const LaunchCfg& lc, bool robust, const DevScene& S, const flo
 
 template <bool RECORD, bool COUNT, bool WW>
 void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
-              const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, cudaStream_t st) {
+              const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, const GuideWave& gw,
+              cudaStream_t st) {
   k_shadow<RECORD, COUNT, WW><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
                                                                       probe, b.tot, b.status, lc.shadow_steps,
-                                                                      lc.shadow_refill, Lfinal);
+                                                                      lc.shadow_refill, Lfinal, gw);
 }
 
 void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
-                   const WaveBufs& b, double* accum, const Probe& probe, float* Lf, cudaStream_t st) {
+                   const WaveBufs& b, double* accum, const Probe& probe, float* Lf, const GuideWave& gw,
+                   cudaStream_t st) {
   const bool ww = lc.variant == 1;
   if (lc.record) {
-    if (lc.counting) ww ? shadow_t<true, true, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<true, true, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
-    else ww ? shadow_t<true, false, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<true, false, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
+    if (lc.counting) ww ? shadow_t<true, true, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<true, true, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+    else ww ? shadow_t<true, false, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<true, false, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   } else {
-    if (lc.counting) ww ? shadow_t<false, true, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<false, true, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
-    else ww ? shadow_t<false, false, true>(lc, S, P, w, k, b, accum, probe, Lf, st) : shadow_t<false, false, false>(lc, S, P, w, k, b, accum, probe, Lf, st);
+    if (lc.counting) ww ? shadow_t<false, true, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<false, true, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+    else ww ? shadow_t<false, false, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<false, false, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   }
 }
 
@@ -741,7 +751,7 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
       ++nl;
     }
     if (tm) tm->begin(STG_SHADOW, st);
-    launch_shadow(lc, S, P, w, k, b, accum, probe, guided ? gw.Lfinal : nullptr, st);
+    launch_shadow(lc, S, P, w, k, b, accum, probe, guided ? gw.Lfinal : nullptr, gw, st);
     if (tm) tm->end(STG_SHADOW, st);
     nl += 3;
   }
