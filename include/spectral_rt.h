@@ -88,7 +88,9 @@ typedef struct {
   const uint32_t* probe_map_dev;
   float* probe_L_dev;
   uint32_t* probe_sig_dev;
-  uint32_t use_graph;      /* 1: capture each wave shape once in a CUDA graph and replay it */
+  uint32_t use_graph;      /* 1: the whole render (all waves, XYZ) is captured once per launch
+                            * configuration into a CUDA graph and replayed (camera poses may change
+                            * between replays); excludes timing, counting, probes and guide training */
   uint32_t trace_variant;  /* traversal loop: 0 = one node or leaf per step, 1 = while-while */
   /* persistent traversal warps refill idle lanes from the queue once at least
    * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
@@ -279,6 +281,19 @@ rt_status rt_optics_eval(rt_ctx* ctx, const float* cos_dev, const float* n_dev, 
  * (spectral[p][j] / spp) * cmf_w[band_first + j][c], with mode rt_xyz_mode. */
 rt_status rt_xyz(rt_ctx* ctx, const double* spectral_dev, uint64_t n_pixels, uint32_t band_first,
                  uint32_t band_count, uint32_t spp, uint32_t mode, float* xyz_dev);
+
+/* Autotuner: times probe renders (spp_probe samples of the given views and
+ * bands, depth `depth`, results discarded) over the wave capacity, the
+ * traversal loop parameters and the traversal block size (coordinate
+ * descent, device time from CUDA events, one warm-up render per setting) and
+ * writes the fastest setting into opts (other fields are kept). */
+typedef struct {
+  uint32_t trials;   /* settings timed */
+  float best_ms;     /* device time of the probe render with the chosen setting */
+  float default_ms;  /* ... with the setting passed in */
+} rt_autotune_report;
+rt_status rt_autotune(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
+                      uint32_t spp_probe, uint32_t depth, rt_render_opts* opts, rt_autotune_report* report);
 
 /* Measurement tool: read bandwidth of the L2 cache.  Streams `bytes`
  * (rounded down to 16; at most 96 MiB so that it stays L2-resident) `iters`

@@ -22,7 +22,7 @@ XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
 EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_set_timing",
            "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
            "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static", "rt_guide_init",
-           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step"]
+           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step", "rt_autotune"]
 
 
 class RtError(RuntimeError):
@@ -44,6 +44,10 @@ class RenderOpts(C.Structure):
                 ("shadow_refill", C.c_uint32), ("guided", C.c_uint32), ("guide_collect", C.c_uint32),
                 ("guide_train_steps", C.c_uint32), ("guide_batch", C.c_uint32), ("sample_first", C.c_uint32),
                 ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("reserved", C.c_uint32 * 2)]
+
+
+class AutotuneReport(C.Structure):
+    _fields_ = [("trials", C.c_uint32), ("best_ms", C.c_float), ("default_ms", C.c_float)]
 
 
 class GuideConfig(C.Structure):
@@ -106,6 +110,8 @@ def load(path: str = LIB_PATH):
         L.rt_guide_eval.argtypes = [vp, vp, u64, vp, vp]
         L.rt_guide_grad.argtypes = [vp, vp, u64, C.POINTER(C.c_float), vp, vp]
         L.rt_guide_train_step.argtypes = [vp, vp, u64, C.POINTER(C.c_float)]
+        L.rt_autotune.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, C.POINTER(RenderOpts),
+                                  C.POINTER(AutotuneReport)]
         L.rt_philox.argtypes = [vp, vp, vp, u64, u32, u32]
         L.rt_trace_closest.argtypes = [vp, vp, vp, u64, vp, vp]
         L.rt_trace_shadow.argtypes = [vp, vp, vp, vp, u64, vp, vp]

@@ -55,6 +55,12 @@ struct rt_ctx {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool timing = false;
   std::vector<cudaEvent_t> tpool;
+  // captured render (rt_render_opts.use_graph)
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::string graph_key;
+  int graph_launches = 0;
+  uint32_t graph_waves = 0;
   float lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};  // scene bounds
   // learned guide
   struct Guide {
@@ -291,6 +297,8 @@ void rt_destroy(rt_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->tpool) cudaEventDestroy(e);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   delete c;
 }
 
@@ -574,10 +582,6 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     }
     accum = c->d_accum;
   }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, st));
-  if (!o.accumulate) CUDA_TRY(c, cudaMemsetAsync(accum, 0, PB64 * sizeof(double), st));
-  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), st));
-  CUDA_TRY(c, cudaMemsetAsync(c->wb.tot, 0, sizeof(Totals), st));
   if (o.trace_block && (o.trace_block > 256 || o.trace_block % 32))
     return fail(c, RT_ERR_ARG, "rt_render: trace_block must be a multiple of 32 up to 256");
   LaunchCfg lc;
@@ -659,46 +663,108 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   uint32_t waves = 0;
   EvTimer timer(c->tpool);
   StageTimer* tm = c->timing ? &timer : nullptr;
-  CUDA_TRY(c, cudaEventRecord(c->ev[0], st));
-  for (uint64_t ws = 0; ws < total; ws += cap) {
-    w.n = (uint32_t)std::min<uint64_t>(cap, total - ws);
-    w.s0 = o.sample_first + (uint32_t)(ws / PB);
-    w.r0 = (uint32_t)(ws % PB);
-    CUDA_TRY(c, cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), st));
-    if (gw.collect) CUDA_TRY(c, cudaMemsetAsync(gw.raw, 0, (size_t)n_slots * kRawF4 * sizeof(float4), st));
-    launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches, tm, &gw, &c->guide.dev,
-                c->guide.pack, c->sms);
-    if (gw.collect && o.guide_train_steps) {
-      if (tm) tm->begin(STG_TRAIN, st);
-      launch_guide_records(gw, n_slots, perm_mul, c->guide.trec, st);
-      const uint32_t steps = o.guide_train_steps;
-      const uint64_t n_rec = 2ull * n_slots;
-      uint64_t batch = o.guide_batch ? std::min<uint64_t>(o.guide_batch, n_rec) : std::max<uint64_t>(1, n_rec / steps);
-      for (uint32_t t = 0; t < steps; ++t) {
-        const uint64_t off = ((uint64_t)t * batch) % n_rec;
-        const uint64_t nb = std::min<uint64_t>(batch, n_rec - off);
-        guide_train_enqueue(c, c->guide.trec + 12 * off, nb);
+  const bool use_graph = o.use_graph != 0;
+  if (use_graph && (tm || lc.counting || lc.record || o.guide_train_steps))
+    return fail(c, RT_ERR_ARG, "rt_render: use_graph excludes timing, counting, probes and guide training");
+  // Everything one render enqueues, on stream `s`; with events the device
+  // time of the path tracing and of the XYZ contraction is bracketed.
+  auto enqueue = [&](cudaStream_t s, bool events) -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, s))) return e;
+    if (!o.accumulate && (e = cudaMemsetAsync(accum, 0, PB64 * sizeof(double), s))) return e;
+    if ((e = cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(c->wb.tot, 0, sizeof(Totals), s))) return e;
+    if (events && (e = cudaEventRecord(c->ev[0], s))) return e;
+    for (uint64_t ws = 0; ws < total; ws += cap) {
+      w.n = (uint32_t)std::min<uint64_t>(cap, total - ws);
+      w.s0 = o.sample_first + (uint32_t)(ws / PB);
+      w.r0 = (uint32_t)(ws % PB);
+      if ((e = cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), s))) return e;
+      if (gw.collect && (e = cudaMemsetAsync(gw.raw, 0, (size_t)n_slots * kRawF4 * sizeof(float4), s))) return e;
+      launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, s, &launches, tm, &gw, &c->guide.dev,
+                  c->guide.pack, c->sms);
+      if (gw.collect && o.guide_train_steps) {
+        if (tm) tm->begin(STG_TRAIN, s);
+        launch_guide_records(gw, n_slots, perm_mul, c->guide.trec, s);
+        const uint32_t steps = o.guide_train_steps;
+        const uint64_t n_rec = 2ull * n_slots;
+        uint64_t batch =
+            o.guide_batch ? std::min<uint64_t>(o.guide_batch, n_rec) : std::max<uint64_t>(1, n_rec / steps);
+        for (uint32_t t = 0; t < steps; ++t) {
+          const uint64_t off = ((uint64_t)t * batch) % n_rec;
+          const uint64_t nb = std::min<uint64_t>(batch, n_rec - off);
+          guide_train_enqueue(c, c->guide.trec + 12 * off, nb);
+        }
+        if (tm) tm->end(STG_TRAIN, s);
+        launches += 1 + 5 * (int)steps;
       }
-      if (tm) tm->end(STG_TRAIN, st);
-      launches += 1 + 5 * (int)steps;
+      ++waves;
     }
-    ++waves;
+    if ((e = cudaGetLastError())) return e;
+    if (events && (e = cudaEventRecord(c->ev[1], s))) return e;
+    if (xyz_dev) {
+      XyzWeights xw;
+      xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
+      xw.wsplit = nullptr;
+      xw.band_count = band_count;
+      xw.kpad = (band_count + 15) / 16 * 16;
+      if (tm) tm->begin(STG_XYZ, s);
+      launch_xyz(accum, npix, xw, o.spp_total ? o.spp_total : spp, (int)o.xyz_mode, xyz_dev, s, c->wb.status, c->sms);
+      if (tm) tm->end(STG_XYZ, s);
+      ++launches;
+      if ((e = cudaGetLastError())) return e;
+    }
+    if (events && (e = cudaEventRecord(c->ev[2], s))) return e;
+    return cudaSuccess;
+  };
+  if (!use_graph) {
+    CUDA_TRY(c, enqueue(st, true));
+  } else {
+    // one captured graph per launch configuration, replayed on an internal
+    // stream ordered after the caller's stream
+    char kb[512];
+    std::snprintf(kb, sizeof(kb), "%u|%llu|%u|%u|%u|%u|%llu|%u|%u|%u|%u|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%u|%u|%u|%u|%g",
+                  n_cams, (unsigned long long)npix, band_first, band_count, spp, depth, (unsigned long long)seed,
+                  o.sample_first, o.accumulate, o.spp_total, o.xyz_mode, (void*)accum, (void*)xyz_dev,
+                  (void*)c->d_nodes, (void*)c->d_mb, lc.grid_trace, lc.block_trace, lc.variant, lc.trace_steps,
+                  lc.trace_refill, lc.shadow_steps, lc.shadow_refill, (int)cap, o.guided, gw.depth, gw.collect,
+                  o.wave_capacity, (double)gw.alpha);
+    std::string key(kb);
+    char pb[160];
+    std::snprintf(pb, sizeof(pb), "|%p|%p|%p|%p|%p", (void*)c->wb.q[0], (void*)c->wb.sq, (void*)gw.gq,
+                  (void*)c->guide.grid, c->guide.pack);
+    key += pb;
+    for (uint32_t v = 0; v < n_cams; ++v) key += "|" + std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height);
+    if (!c->gstream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    if (!c->graph_exec || key != c->graph_key) {
+      if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+      }
+      CUDA_TRY(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t ce = enqueue(c->gstream, false);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(c->gstream, &g);
+      if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        CUDA_TRY(c, ce != cudaSuccess ? ce : ee);
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&c->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      CUDA_TRY(c, ie);
+      c->graph_key = key;
+      c->graph_launches = launches;
+      c->graph_waves = waves;
+    }
+    launches = c->graph_launches;
+    waves = c->graph_waves;
+    CUDA_TRY(c, cudaEventRecord(c->ev[0], st));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->gstream, c->ev[0], 0));
+    CUDA_TRY(c, cudaGraphLaunch(c->graph_exec, c->gstream));
+    CUDA_TRY(c, cudaEventRecord(c->ev[1], c->gstream));
+    CUDA_TRY(c, cudaStreamWaitEvent(st, c->ev[1], 0));
+    CUDA_TRY(c, cudaEventRecord(c->ev[2], st));
   }
-  CUDA_TRY(c, cudaGetLastError());
-  CUDA_TRY(c, cudaEventRecord(c->ev[1], st));
-  if (xyz_dev) {
-    XyzWeights xw;
-    xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
-    xw.wsplit = nullptr;
-    xw.band_count = band_count;
-    xw.kpad = (band_count + 15) / 16 * 16;
-    if (tm) tm->begin(STG_XYZ, st);
-    launch_xyz(accum, npix, xw, o.spp_total ? o.spp_total : spp, (int)o.xyz_mode, xyz_dev, st, c->wb.status, c->sms);
-    if (tm) tm->end(STG_XYZ, st);
-    ++launches;
-    CUDA_TRY(c, cudaGetLastError());
-  }
-  CUDA_TRY(c, cudaEventRecord(c->ev[2], st));
   CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaMemcpyAsync(c->h_tot, c->wb.tot, sizeof(Totals), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1020,6 +1086,101 @@ rt_status rt_guide_train_step(rt_ctx* c, const float* rec_dev, uint64_t n, float
   guide_update_enqueue(c);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_autotune(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
+                      uint32_t spp_probe, uint32_t depth, rt_render_opts* opts, rt_autotune_report* report) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!opts) return fail(c, RT_ERR_ARG, "rt_autotune: opts is required");
+  if (spp_probe == 0) spp_probe = 1;
+  rt_render_opts base = *opts;
+  base.probe_map_dev = nullptr;
+  base.probe_L_dev = nullptr;
+  base.probe_sig_dev = nullptr;
+  base.use_graph = 0;
+  base.accumulate = 0;
+  base.guide_train_steps = 0;
+  base.guide_collect = 0;
+  const bool timing = c->timing, counting = c->counting;
+  c->timing = false;
+  c->counting = false;
+  uint32_t trials = 0;
+  float default_ms = 0.0f;
+  auto run = [&](const rt_render_opts& o, float* ms) -> rt_status {
+    rt_stats st;
+    // warm-up render, then the timed one
+    for (int rep = 0; rep < 2; ++rep) {
+      rt_status e = render_impl(c, cams, n_cams, band_first, band_count, spp_probe, depth, 0x5eed, &o, nullptr,
+                                nullptr, &st);
+      if (e != RT_OK) return e;
+    }
+    *ms = st.ms_render;
+    ++trials;
+    return RT_OK;
+  };
+  float best_ms;
+  rt_status e = run(base, &best_ms);
+  if (e != RT_OK) {
+    c->timing = timing;
+    c->counting = counting;
+    return e;
+  }
+  default_ms = best_ms;
+  rt_render_opts best = base;
+  auto try_opt = [&](rt_render_opts o) -> rt_status {
+    float ms;
+    rt_status e2 = run(o, &ms);
+    if (e2 != RT_OK) return e2;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = o;
+    }
+    return RT_OK;
+  };
+  // coordinate descent: paths in flight, closest-hit loop, sun-ray loop, block
+  const uint32_t waves[] = {1u << 21, 1u << 22, 1u << 23, 1u << 24};
+  const uint32_t tl[][2] = {{8, 8}, {4, 12}, {16, 8}, {2, 16}, {1, 12}};
+  const uint32_t sl[][2] = {{4, 12}, {8, 8}, {1, 12}, {16, 16}};
+  const uint32_t blocks[] = {128, 64, 256};
+  rt_render_opts o;
+  for (uint32_t wv : waves) {
+    o = best;
+    o.wave_capacity = wv;
+    if ((e = try_opt(o))) break;
+  }
+  for (size_t i = 0; e == RT_OK && i < sizeof(tl) / sizeof(tl[0]); ++i) {
+    o = best;
+    o.trace_steps = tl[i][0];
+    o.trace_refill = tl[i][1];
+    e = try_opt(o);
+  }
+  for (size_t i = 0; e == RT_OK && i < sizeof(sl) / sizeof(sl[0]); ++i) {
+    o = best;
+    o.shadow_steps = sl[i][0];
+    o.shadow_refill = sl[i][1];
+    e = try_opt(o);
+  }
+  for (size_t i = 0; e == RT_OK && i < sizeof(blocks) / sizeof(blocks[0]); ++i) {
+    o = best;
+    o.trace_block = blocks[i];
+    e = try_opt(o);
+  }
+  c->timing = timing;
+  c->counting = counting;
+  if (e != RT_OK) return e;
+  // keep the caller's own fields; copy the tuned ones
+  opts->wave_capacity = best.wave_capacity;
+  opts->trace_steps = best.trace_steps;
+  opts->trace_refill = best.trace_refill;
+  opts->shadow_steps = best.shadow_steps;
+  opts->shadow_refill = best.shadow_refill;
+  opts->trace_block = best.trace_block;
+  if (report) {
+    report->trials = trials;
+    report->best_ms = best_ms;
+    report->default_ms = default_ms;
+  }
   return RT_OK;
 }
 

@@ -301,7 +301,7 @@ constexpr uint32_t kNoRay = 0xFFFFFFFFu;
 // give one batch of 32 rays per warp at a time).
 
 template <bool FMA, bool COUNT, bool WW>
-__global__ void __launch_bounds__(128) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
+__global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
                                                uint32_t* status, int steps, int refill) {
   const uint32_t count = min(cnt[k].q_count, cap);
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
 }
 
 template <bool RECORD, bool COUNT, bool WW>
-__global__ void __launch_bounds__(128) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+__global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,

@@ -98,7 +98,8 @@ class Renderer:
                trace_block: int = 0, ctas_per_sm: int = 0, out_spectral=None, out_xyz=None, trace_variant: int = 0,
                trace_steps: int = 0, trace_refill: int = 0, shadow_steps: int = 0, shadow_refill: int = 0,
                guided: bool = False, guide_collect: int = 0, guide_train_steps: int = 0, guide_batch: int = 0,
-               sample_first: int = 0, accumulate: bool = False, spp_total: int = 0):
+               sample_first: int = 0, accumulate: bool = False, spp_total: int = 0, use_graph: bool = False,
+               tuned: Optional[dict] = None):
         """Returns dict(spectral [P, band_count] f64 sums over samples,
         xyz [P, 3] f32, stats, and probe_L / probe_sig [n_probe, spp, band_count]
         when probe_pixels is given)."""
@@ -122,6 +123,9 @@ class Renderer:
         opts.guided, opts.guide_collect = int(guided), guide_collect
         opts.guide_train_steps, opts.guide_batch = guide_train_steps, guide_batch
         opts.sample_first, opts.accumulate, opts.spp_total = sample_first, int(accumulate), spp_total
+        opts.use_graph = int(use_graph)
+        for k_, v_ in (tuned or {}).items():
+            setattr(opts, k_, int(v_))
         out = {}
         if probe_pixels is not None:
             pp = torch.as_tensor(np.asarray(probe_pixels, np.int64), device=dev)
@@ -268,3 +272,20 @@ class Renderer:
         self._check("rt_guide_train_step", self.lib.rt_guide_train_step(self._h, r.data_ptr(), r.shape[0],
                                                                          C.byref(loss)))
         return loss.value
+
+    # -- autotuning ------------------------------------------------------------
+    TUNED_FIELDS = ("wave_capacity", "trace_steps", "trace_refill", "shadow_steps", "shadow_refill", "trace_block")
+
+    def autotune(self, cameras, depth, band_first=0, band_count=None, spp_probe=1):
+        """Native coordinate-descent autotuner (rt_autotune); returns
+        (tuned option dict, report dict)."""
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        opts = _native.RenderOpts()
+        rep = _native.AutotuneReport()
+        cams = _native.cameras_struct(cameras)
+        st = self.lib.rt_autotune(self._h, cams, len(cameras), band_first, band_count, spp_probe, depth,
+                                  C.byref(opts), C.byref(rep))
+        self._check("rt_autotune", st)
+        return ({k: getattr(opts, k) for k in self.TUNED_FIELDS},
+                {"trials": rep.trials, "best_ms": rep.best_ms, "default_ms": rep.default_ms})
