@@ -44,6 +44,9 @@ def main(argv=None):
     r.add_argument("--xyz-mode", type=int, default=0)
     r.add_argument("--wave", type=int, default=0, help="wave capacity (paths in flight)")
     r.add_argument("--repeat", type=int, default=1)
+    r.add_argument("--guided", action="store_true", help="learned guide at Lambertian vertices (freshly initialised)")
+    r.add_argument("--guide-collect", type=int, default=0)
+    r.add_argument("--guide-train-steps", type=int, default=0)
     r.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
@@ -51,10 +54,14 @@ def main(argv=None):
     wl = _workload(args)
     t0 = time.perf_counter()
     R = Renderer(0).load(wl)
+    if args.guided:
+        R.guide_init(seed=1)
     t_load = time.perf_counter() - t0
     out = None
     for _ in range(args.repeat):
-        out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=args.xyz_mode, wave_capacity=args.wave)
+        out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=args.xyz_mode, wave_capacity=args.wave,
+                       guided=args.guided, guide_collect=args.guide_collect,
+                       guide_train_steps=args.guide_train_steps)
     st = out["stats"]
     st.update(workload=wl.name, triangles=int(wl.scene.n_tris), load_s=t_load,
               paths_per_s=st["paths"] / (st["ms_render"] * 1e-3) if st["ms_render"] > 0 else None)
