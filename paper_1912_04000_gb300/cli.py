@@ -47,6 +47,8 @@ def main(argv=None):
     r.add_argument("--guided", action="store_true", help="learned guide at Lambertian vertices (freshly initialised)")
     r.add_argument("--guide-collect", type=int, default=0)
     r.add_argument("--guide-train-steps", type=int, default=0)
+    r.add_argument("--graph", action="store_true", help="capture the render in a CUDA graph and replay it")
+    r.add_argument("--tune", action="store_true", help="autotuned launch settings (cached per GPU and workload)")
     r.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
@@ -57,13 +59,17 @@ def main(argv=None):
     if args.guided:
         R.guide_init(seed=1)
     t_load = time.perf_counter() - t0
+    tuned = None
+    if args.tune:
+        from .autotune import tuned_options
+        tuned, _ = tuned_options(R, wl)
     out = None
     for _ in range(args.repeat):
         out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=args.xyz_mode, wave_capacity=args.wave,
                        guided=args.guided, guide_collect=args.guide_collect,
-                       guide_train_steps=args.guide_train_steps)
+                       guide_train_steps=args.guide_train_steps, use_graph=args.graph, tuned=tuned)
     st = out["stats"]
-    st.update(workload=wl.name, triangles=int(wl.scene.n_tris), load_s=t_load,
+    st.update(workload=wl.name, triangles=int(wl.scene.n_tris), load_s=t_load, tuned=tuned,
               paths_per_s=st["paths"] / (st["ms_render"] * 1e-3) if st["ms_render"] > 0 else None)
     print(json.dumps(st))
     if args.out:

@@ -137,28 +137,6 @@ __device__ __forceinline__ void encode(const GuideDev& g, float3 p, float3 n, ui
   if (group < 9u) X[48 + group] = 1.0f;
 }
 
-// Scatter dL/dX[0..31] into the grid gradient.
-__device__ __forceinline__ void encode_backward(const GuideDev& g, float3 p, const float* dX, float* dgrid) {
-  float u[3];
-  unit_pos(g, p, u);
-  const uint32_t T = 1u << g.log2T;
-#pragma unroll 1
-  for (int l = 0; l < kLevels; ++l) {
-    const LevelPos lp = level_pos(g, u, l);
-    const float d0 = dX[2 * l], d1 = dX[2 * l + 1];
-    if (d0 == 0.0f && d1 == 0.0f) continue;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-      const float w = (dx ? lp.f[0] : 1.0f - lp.f[0]) * (dy ? lp.f[1] : 1.0f - lp.f[1]) * (dz ? lp.f[2] : 1.0f - lp.f[2]);
-      const uint32_t id = grid_index(g, l, lp.c[0] + dx, lp.c[1] + dy, lp.c[2] + dz);
-      float* dst = dgrid + ((size_t)l * T + id) * 2;
-      atomicAdd(dst, w * d0);
-      atomicAdd(dst + 1, w * d1);
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // head
 // ---------------------------------------------------------------------------
@@ -210,20 +188,6 @@ __device__ __forceinline__ float mix_pdf(const Mix& h, float3 w) {
 __device__ __forceinline__ void put_row(unsigned char* A, uint32_t r, const float* v, int ncols) {
   for (int c = 0; c < ncols; ++c)
     *(uint16_t*)(A + (c >> 4) * kSliceA + tc_kmajor_off(r, c & 15)) = tc_bf16_bits(v[c]);
-}
-
-__device__ __forceinline__ float get_a(const unsigned char* A, uint32_t r, int c) {
-  return tc_bf16_val(*(const uint16_t*)(A + (c >> 4) * kSliceA + tc_kmajor_off(r, c & 15)));
-}
-
-// A' = [H^T; 0]: element (feature i, record b)
-__device__ __forceinline__ void put_at(unsigned char* Ap, uint32_t i, uint32_t b, uint16_t v) {
-  *(uint16_t*)(Ap + (b >> 4) * kSliceA + tc_kmajor_off(i, b & 15)) = v;
-}
-
-// B' = dZ^T with `out` rows: element (output o, record b)
-__device__ __forceinline__ void put_bt(unsigned char* Bp, uint32_t o, uint32_t b, uint32_t out, uint16_t v) {
-  *(uint16_t*)(Bp + (b >> 4) * (out * 32u) + tc_kmajor_off(o, b & 15)) = v;
 }
 
 // D (TMEM) = A B over nslices K-slices of 16.
@@ -354,9 +318,66 @@ __global__ void __launch_bounds__(kRows) k_guide_eval(GuideDev g, const uint4* _
   if (warp == 0) tc_tmem_dealloc(tmem, 64);
 }
 
+// Eight BF16 values to the K-major tile: columns c0 .. c0 + 7 (c0 % 8 == 0)
+// of row r form one 16-byte core-matrix row.
+__device__ __forceinline__ void put8(unsigned char* A, uint32_t r, int c0, const float* v) {
+  uint4 q;
+  q.x = tc_bf16x2_bits(v[0], v[1]);
+  q.y = tc_bf16x2_bits(v[2], v[3]);
+  q.z = tc_bf16x2_bits(v[4], v[5]);
+  q.w = tc_bf16x2_bits(v[6], v[7]);
+  *(uint4*)(A + (c0 >> 4) * kSliceA + tc_kmajor_off(r, (uint32_t)(c0 & 15))) = q;
+}
+
+// Hash-grid features of levels l0 .. l0 + 7 (the arithmetic of encode());
+// res: the per-level resolutions, staged in shared memory.
+__device__ __forceinline__ void encode_levels8(const GuideDev& g, const uint32_t* res, const float u[3], int l0,
+                                               float* f) {
+  const uint32_t T = 1u << g.log2T;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int l = l0 + i;
+    const float rl = (float)res[l];
+    uint32_t c[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float sa = u[a] * rl;
+      const float fl = fminf(floorf(sa), rl - 1.0f);
+      c[a] = (uint32_t)fl;
+      fr[a] = sa - fl;
+    }
+    const bool dense = (g.dense_mask >> l) & 1u;
+    const uint32_t r1 = res[l] + 1u;
+    const float2* tab = (const float2*)g.grid + (size_t)l * T;
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+      const float w = (dx ? fr[0] : 1.0f - fr[0]) * (dy ? fr[1] : 1.0f - fr[1]) * (dz ? fr[2] : 1.0f - fr[2]);
+      const uint32_t x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+      const uint32_t id = dense ? x + y * r1 + z * r1 * r1 : (x * 1u ^ y * 2654435761u ^ z * 805459861u) & (T - 1u);
+      const float2 v = __ldg(tab + id);
+      a0 = fmaf(w, v.x, a0);
+      a1 = fmaf(w, v.y, a1);
+    }
+    f[2 * i] = a0;
+    f[2 * i + 1] = a1;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // training: forward, loss gradient, backward, gradient accumulation
 // ---------------------------------------------------------------------------
+// A CTA of 256 threads serves 128 records per tile, two threads per record
+// (half h = t / 128; threads t and t + 128 share a TMEM lane).  Records of
+// zero weight add nothing to the loss or its gradient and are skipped: each
+// CTA walks a contiguous chunk of the batch and compacts the indices of the
+// weighted records into full tiles.  Weight gradients dW_l = H_{l-1}^T dZ_l
+// use A' = [H_{l-1}^T; 0] (M = 128) and B' = dZ_l^T, both made from the
+// K-major activation tiles by 8 x 8 transposes (ldmatrix / stmatrix.trans),
+// and accumulate in TMEM over all tiles of the CTA.
+constexpr int kTrainThreads = 2 * kRows;
 constexpr uint32_t kTrX = kWPack;
 constexpr uint32_t kTrH1 = kTrX + kATileB;
 constexpr uint32_t kTrH2 = kTrH1 + kATileB;
@@ -364,142 +385,296 @@ constexpr uint32_t kTrH3 = kTrH2 + kATileB;
 constexpr uint32_t kTrDZ = kTrH3 + kATileB;
 constexpr uint32_t kTrAp = kTrDZ + kATileB;           // [128 x 128] = 32 KB
 constexpr uint32_t kTrBp = kTrAp + 8 * kSliceA;       // <= [64 x 128] = 16 KB
-constexpr uint32_t kTrMisc = kTrBp + 8 * 64 * 32;
-constexpr uint32_t kTrainSmem = kTrMisc + 64;
+constexpr uint32_t kTrList = kTrBp + 8 * 64 * 32;     // record indices, 128 + 256 entries
+constexpr uint32_t kTrMisc = kTrList + 384 * 4;
+constexpr uint32_t kTrainSmem = kTrMisc + 128;
 static_assert(kTrainSmem <= 227 * 1024, "training kernel shared memory");
 
-__global__ void __launch_bounds__(kRows, 1) k_guide_train(GuideDev g, const uint4* __restrict__ wpack,
-                                                          const float4* __restrict__ rec, uint64_t n,
-                                                          const float* __restrict__ wsum, float* __restrict__ dW,
-                                                          float* __restrict__ dgrid, float* __restrict__ loss,
-                                                          uint32_t* status) {
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(addr)
+               : "memory");
+}
+
+__device__ __forceinline__ void stsm_x4_trans(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b),
+               "r"(c), "r"(d)
+               : "memory");
+}
+
+// Core matrix (row group g, column block b) of a K-major tile whose 16-wide
+// K-slices are `slice` bytes apart: address of its row i.
+__device__ __forceinline__ uint32_t core_row(uint32_t base, uint32_t slice, uint32_t g, uint32_t b, uint32_t i) {
+  return base + (b >> 1) * slice + i * 16u + g * 256u + (b & 1u) * 128u;
+}
+
+// Transposes of the 8 x 8 core matrices of a [128 records x ncols] K-major
+// tile (slices 4096 B) into a [ncols rows x 128 records] K-major tile
+// (slices dst_slice B): core (record group g, column block b) -> core
+// (column group b, record block g).  The whole CTA, 4 cores per warp op.
+__device__ __forceinline__ void transpose_tile(const unsigned char* src, unsigned char* dst, uint32_t dst_slice,
+                                               uint32_t ncols) {
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t ncores = 16u * (ncols / 8u);
+  const uint32_t s = smem_u32(src), d = smem_u32(dst);
+  for (uint32_t c0 = warp * 4u; c0 < ncores; c0 += (blockDim.x >> 5) * 4u) {
+    const uint32_t c = c0 + (lane >> 3), i = lane & 7u;
+    const uint32_t g = c & 15u, b = c >> 4;
+    uint32_t r0, r1, r2, r3;
+    ldsm_x4(core_row(s, kSliceA, g, b, i), r0, r1, r2, r3);
+    stsm_x4_trans(core_row(d, dst_slice, b, g, i), r0, r1, r2, r3);
+  }
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1)
+    k_guide_train(GuideDev g, const uint4* __restrict__ wpack, const float4* __restrict__ rec, uint64_t n,
+                  const float* __restrict__ wsum, float* __restrict__ dW, float* __restrict__ dgrid,
+                  float* __restrict__ loss, uint32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* AX = smem + kTrX;
-  unsigned char* AH[3] = {smem + kTrH1, smem + kTrH2, smem + kTrH3};
   unsigned char* ADZ = smem + kTrDZ;
   unsigned char* Ap = smem + kTrAp;
   unsigned char* Bp = smem + kTrBp;
+  uint32_t* list = (uint32_t*)(smem + kTrList);
   uint64_t* mbar = (uint64_t*)(smem + kTrMisc);
   uint32_t* tslot = (uint32_t*)(mbar + 1);
   float* lsum = (float*)(tslot + 1);
-  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  uint32_t* wcnt = (uint32_t*)(lsum + 1);  // [8] per-warp counts, [8] list length
+  uint32_t* sres = wcnt + 9;               // [16] grid resolutions
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+  const uint32_t r = tid & (kRows - 1), h = tid >> 7;
   load_weights(smem, wpack);
   // A' rows 64..127 stay zero
   for (uint32_t i = tid; i < 8u * kSliceA / 16u; i += blockDim.x) ((uint4*)Ap)[i] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l)
+    if (tid == (uint32_t)l) sres[l] = g.res[l];
   if (tid == 0) {
     tc_mbar_init(mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *lsum = 0.0f;
+    wcnt[8] = 0u;
   }
   if (warp == 0) tc_tmem_alloc(tslot, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  
+  const uint32_t trow = tmem + (((warp & 3u) * 32u) << 16);
   Sync sy{mbar, 0u, true};
   const uint32_t id64 = tc_idesc_bf16(kRows, 64), id48 = tc_idesc_bf16(kRows, kOut);
   const float total = *wsum;
-  const uint64_t ntiles = (n + kRows - 1) / kRows;
+  const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint64_t c0 = min((uint64_t)blockIdx.x * per, n), c1 = min(c0 + per, n);
+  uint64_t cur = c0;
   bool first = true;
   float my_loss = 0.0f;
-  for (uint64_t tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
-    const uint64_t i = tile * kRows + tid;
-    const bool valid = i < n;
-    float v[kIn];
-    Rec r{};
-    if (valid) {
-      r = load_rec(rec, i);
-      encode(g, r.p, r.n, r.group, v);
-    } else {
-      for (int c = 0; c < kIn; ++c) v[c] = 0.0f;
+  while (sy.ok) {
+    // compact the indices of weighted records until a tile is full
+    uint32_t nl = wcnt[8];
+    while (nl < (uint32_t)kRows && cur < c1) {
+      const uint64_t i = cur + tid;
+      const bool take = i < c1 && __ldg((const float*)(rec + 3 * i) + 3) > 0.0f;
+      const uint32_t m = __ballot_sync(0xffffffffu, take);
+      if (lane == 0) wcnt[warp] = __popc(m);
+      __syncthreads();
+      uint32_t off = nl;
+      for (uint32_t w2 = 0; w2 < warp; ++w2) off += wcnt[w2];
+      if (take) list[off + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(i - c0);
+      uint32_t tot = 0;
+      for (uint32_t w2 = 0; w2 < (blockDim.x >> 5); ++w2) tot += wcnt[w2];
+      __syncthreads();
+      nl += tot;
+      cur += blockDim.x;
     }
-    put_row(AX, tid, v, kIn);
+    if (nl == 0) break;
+    const uint32_t nt = min(nl, (uint32_t)kRows);
+    const bool valid = r < nt;
+    const uint64_t ri = valid ? c0 + list[r] : 0;
+    Rec rc{};
+    if (valid) rc = load_rec(rec, ri);
+    // carry the surplus indices over to the next tile
+    __syncthreads();
+    uint32_t carry = 0;
+    if (tid < nl - nt) carry = list[kRows + tid];
+    __syncthreads();
+    if (tid < nl - nt) list[tid] = carry;
+    if (tid == 0) wcnt[8] = nl - nt;
+    // encoding: half 0 grid levels 0-7 and SH, half 1 levels 8-15 and group
+    {
+      float u[3], f[16];
+      unit_pos(g, rc.p, u);
+      if (valid) {
+        encode_levels8(g, sres, u, 8 * (int)h, f);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) f[c] = 0.0f;
+      }
+      put8(AX, r, 16 * (int)h, f);
+      put8(AX, r, 16 * (int)h + 8, f + 8);
+      if (h == 0) {
+        if (valid) sh16(rc.n.x, rc.n.y, rc.n.z, f);
+        put8(AX, r, 32, f);
+        put8(AX, r, 40, f + 8);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) f[c] = (valid && (uint32_t)c == rc.group) ? 1.0f : 0.0f;
+        put8(AX, r, 48, f);
+        put8(AX, r, 56, f + 8);
+      }
+    }
     // forward
-    const unsigned char* src = AX;
     for (int l = 0; l < 3; ++l) {
       publish();
-      if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
+      if (tid == 0) gemm(tmem, smem + kTrX + kATileB * (uint32_t)l, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
       mma_wait(sy, status);
-      load_row(tmem, 0, kHid, v);
-      for (int c = 0; c < kHid; ++c) v[c] = fmaxf(v[c], 0.0f);
-      put_row(AH[l], tid, v, kHid);
-      src = AH[l];
+      float v[32];
+      tc_tmem_ld16x2(trow + 32u * h, v);
+      unsigned char* Hl = smem + kTrH1 + kATileB * (uint32_t)l;
+#pragma unroll
+      for (int c = 0; c < 32; c += 8) {
+        float t[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) t[e] = fmaxf(v[c + e], 0.0f);
+        put8(Hl, r, 32 * (int)h + c, t);
+      }
     }
     publish();
-    if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
+    if (tid == 0) gemm(tmem, smem + kTrH3, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
     mma_wait(sy, status);
-    load_row(tmem, 0, kOut, v);
-    // head: loss and dL/dY
-    const float a = (valid && total > 0.0f) ? r.weight / total : 0.0f;
-    float dY[kOut];
-    for (int c = 0; c < kOut; ++c) dY[c] = 0.0f;
-    if (a > 0.0f) {
-      Mix h;
-      mixture(v, h);
-      float pj[kLobes], q = 0.0f;
-      for (int j = 0; j < kLobes; ++j) {
-        pj[j] = vmf_pdf(h.kappa[j], h.mu[j], r.w);
-        q += h.pi[j] * pj[j];
+    // head (half 0): loss and dL/dY, written as dZ_3 into ADZ
+    if (h == 0) {
+      float y[48];
+      tc_tmem_ld16x2(trow, y);
+      tc_tmem_ld16(trow + 32u, y + 32);
+      const float a = (valid && total > 0.0f) ? rc.weight / total : 0.0f;
+      float dY[kOut];
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) dY[c] = 0.0f;
+      if (a > 0.0f) {
+        Mix mx;
+        mixture(y, mx);
+        float pj[kLobes], q = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kLobes; ++j) {
+          pj[j] = vmf_pdf(mx.kappa[j], mx.mu[j], rc.w);
+          q += mx.pi[j] * pj[j];
+        }
+        my_loss -= a * logf(q);
+        const float3 w = rc.w;
+#pragma unroll
+        for (int j = 0; j < kLobes; ++j) {
+          const float rj = mx.pi[j] * pj[j] / q;
+          const float c = mx.mu[j][0] * w.x + mx.mu[j][1] * w.y + mx.mu[j][2] * w.z;
+          dY[5 * j] = -a * (rj - mx.pi[j]);
+          const float fj = -a * rj * mx.kappa[j] / mx.mnorm[j];
+          dY[5 * j + 1] = fj * (w.x - c * mx.mu[j][0]);
+          dY[5 * j + 2] = fj * (w.y - c * mx.mu[j][1]);
+          dY[5 * j + 3] = fj * (w.z - c * mx.mu[j][2]);
+          const float k = mx.kappa[j];
+          const float dlogp = 1.0f / k - 2.0f / expm1f(2.0f * k) + (c - 1.0f);
+          dY[5 * j + 4] = -a * rj * dlogp / (1.0f + expf(-y[5 * j + 4]));
+        }
       }
-      my_loss -= a * logf(q);
-      const float3 w = r.w;
-      for (int j = 0; j < kLobes; ++j) {
-        const float rj = h.pi[j] * pj[j] / q;
-        const float c = h.mu[j][0] * w.x + h.mu[j][1] * w.y + h.mu[j][2] * w.z;
-        dY[5 * j] = -a * (rj - h.pi[j]);
-        const float f = -a * rj * h.kappa[j] / h.mnorm[j];
-        dY[5 * j + 1] = f * (w.x - c * h.mu[j][0]);
-        dY[5 * j + 2] = f * (w.y - c * h.mu[j][1]);
-        dY[5 * j + 3] = f * (w.z - c * h.mu[j][2]);
-        const float k = h.kappa[j];
-        const float dlogp = 1.0f / k - 2.0f / expm1f(2.0f * k) + (c - 1.0f);
-        dY[5 * j + 4] = -a * rj * dlogp / (1.0f + expf(-v[5 * j + 4]));
-      }
+#pragma unroll
+      for (int c = 0; c < kOut; c += 8) put8(ADZ, r, c, dY + c);
     }
     // backward: layer l = 3 (W4, out 48) down to 0 (W1)
-    float* dz = dY;  // dZ_l of this row (FP32), out_l columns
-    float dh[kHid];
     for (int l = 3; l >= 0; --l) {
-      const int out = layer_out(l);
-      const unsigned char* Hin = l == 0 ? AX : AH[l - 1];
-      // dZ_l into A (K = out) and B' (dZ^T); H_{l-1}^T into A' rows 0..63
-      put_row(ADZ, tid, dz, out);
-      for (int o = 0; o < out; ++o) put_bt(Bp, o, tid, out, tc_bf16_bits(dz[o]));
-      for (int c = 0; c < kHid; ++c) put_at(Ap, c, tid, *(const uint16_t*)(Hin + (c >> 4) * kSliceA + tc_kmajor_off(tid, c & 15)));
+      const uint32_t out = (uint32_t)layer_out(l);
+      const unsigned char* Hin = smem + kTrX + kATileB * (uint32_t)l;  // H_{l-1} (X for l = 0)
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      transpose_tile(ADZ, Bp, out * 32u, out);
+      transpose_tile(Hin, Ap, kSliceA, kHid);
       publish();
       if (tid == 0) {
         // dW_l (+)= H_{l-1}^T dZ_l : M 128 (64 used), N = out, K = 128 records
-        gemm(tmem + (64u * (uint32_t)(l + 1)), Ap, kSliceA, Bp, out * 32, 8, tc_idesc_bf16(kRows, out), !first);
+        gemm(tmem + 64u * (uint32_t)(l + 1), Ap, kSliceA, Bp, out * 32u, 8, tc_idesc_bf16(kRows, out), !first);
         // dH_{l-1} = dZ_l W_l^T : M 128, N 64, K = out
-        gemm(tmem, ADZ, kSliceA, smem + wb_off(l), 2048, out / 16, id64, false);
+        gemm(tmem, ADZ, kSliceA, smem + wb_off(l), 2048, (int)out / 16, id64, false);
       }
       mma_wait(sy, status);
-      load_row(tmem, 0, kHid, dh);
       if (l > 0) {
         // dZ_{l-1} = dH_{l-1} where the forward activation was positive
-        for (int c = 0; c < kHid; ++c) dh[c] = get_a(AH[l - 1], tid, c) > 0.0f ? dh[c] : 0.0f;
-        for (int c = 0; c < kHid; ++c) v[c] = dh[c];
-        dz = v;
+        float v[32];
+        tc_tmem_ld16x2(trow + 32u * h, v);
+        const unsigned char* Hm = smem + kTrX + kATileB * (uint32_t)l;
+#pragma unroll
+        for (int c = 0; c < 32; c += 8) {
+          const int col = 32 * (int)h + c;
+          const uint4 hb = *(const uint4*)(Hm + (col >> 4) * kSliceA + tc_kmajor_off(r, (uint32_t)(col & 15)));
+          const uint32_t hw[4] = {hb.x, hb.y, hb.z, hb.w};
+          float t[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const uint32_t bits = (hw[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+            t[e] = tc_bf16_val((uint16_t)bits) > 0.0f ? v[c + e] : 0.0f;
+          }
+          put8(ADZ, r, col, t);
+        }
+      } else {
+        // dX of grid levels 8h .. 8h + 7 -> grid gradient
+        float dx[16];
+        tc_tmem_ld16(trow + 16u * h, dx);
+        if (valid && rc.weight > 0.0f && total > 0.0f) {
+          float u[3];
+          unit_pos(g, rc.p, u);
+          const uint32_t T = 1u << g.log2T;
+#pragma unroll 1
+          for (int i = 0; i < 8; ++i) {
+            const int l2 = 8 * (int)h + i;
+            const float d0 = dx[2 * i], d1 = dx[2 * i + 1];
+            if (d0 == 0.0f && d1 == 0.0f) continue;
+            const float rl = (float)sres[l2];
+            uint32_t c[3];
+            float fr[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const float sa = u[a] * rl;
+              const float fl = fminf(floorf(sa), rl - 1.0f);
+              c[a] = (uint32_t)fl;
+              fr[a] = sa - fl;
+            }
+            const bool dense = (g.dense_mask >> l2) & 1u;
+            const uint32_t r1 = sres[l2] + 1u;
+            float2* dst = (float2*)dgrid + (size_t)l2 * T;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const uint32_t ddx = k & 1, ddy = (k >> 1) & 1, ddz = (k >> 2) & 1;
+              const float w = (ddx ? fr[0] : 1.0f - fr[0]) * (ddy ? fr[1] : 1.0f - fr[1]) *
+                              (ddz ? fr[2] : 1.0f - fr[2]);
+              const uint32_t x = c[0] + ddx, y = c[1] + ddy, z = c[2] + ddz;
+              const uint32_t id =
+                  dense ? x + y * r1 + z * r1 * r1 : (x * 1u ^ y * 2654435761u ^ z * 805459861u) & (T - 1u);
+              atomicAdd(dst + id, make_float2(w * d0, w * d1));
+            }
+          }
+        }
       }
-      tc_fence_before();
-      __syncthreads();
     }
-    // dX (first 32 columns = grid features) -> grid gradient
-    if (valid && a > 0.0f) encode_backward(g, r.p, dh, dgrid);
     first = false;
   }
-  // accumulated weight gradients: TMEM lanes 0..63 (warps 0, 1) = input rows
-  if (!first && sy.ok && warp < 2) {
+  // accumulated weight gradients: TMEM lanes 0..63 (warps 0, 1, 4, 5) = input rows
+  if (!first && sy.ok && (warp & 3u) < 2u) {
+    const uint32_t in = (warp & 1u) * 32u + lane;
     for (int l = 0; l < 4; ++l) {
       const int out = layer_out(l);
-      float row[kHid];
-      load_row(tmem, (64u * (uint32_t)(l + 1)), out, row);
-      const uint32_t in = warp * 32u + (tid & 31u);
-      for (int o = 0; o < out; ++o) atomicAdd(dW + w_off(l) + in * out + o, row[o]);
+      float row[32];
+      // half 0 columns 0..31, half 1 columns 32..out-1
+      const int o0 = 32 * (int)h, nc = min(32, out - o0);
+      const uint32_t col0 = 64u * (uint32_t)(l + 1) + (uint32_t)o0;
+      if (nc == 32) {
+        tc_tmem_ld16x2(trow + col0, row);
+      } else {
+        tc_tmem_ld16(trow + col0, row);
+      }
+      for (int o = 0; o < nc; ++o) atomicAdd(dW + w_off(l) + in * out + o0 + o, row[o]);
     }
   }
-  atomicAdd(lsum, my_loss);
+  if (my_loss != 0.0f) atomicAdd(lsum, my_loss);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -589,21 +764,40 @@ __device__ __forceinline__ float3 vmf_sample(const float* mu, float kappa, float
                      r * cp * t1.z + r * sp * t2.z + w * m.z);
 }
 
-constexpr uint32_t kSmWf = 30720;  // forward tiles only
-constexpr uint32_t kSampleSmem = kSmWf + 2 * kATileB + 64;
+constexpr uint32_t kSmWf = 30720;                      // forward weight tiles
+constexpr int kSampleThreads = 2 * kRows;              // two threads per query
+constexpr int kXch = 12;                               // head exchange floats per query
+constexpr uint32_t kSmXch = kSmWf + kATileB;           // one activation tile, updated in place
+constexpr uint32_t kSampleSmem = kSmXch + kRows * kXch * 4u + 128u;
+constexpr int kSampleCtasPerSm = 4;
 
-__global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4* __restrict__ wpack, DevSpectra P,
-                                                        WaveParams w, uint32_t k, GuideWave gw,
-                                                        float4* __restrict__ qout, float4* __restrict__ sq,
-                                                        float* __restrict__ Lbuf, uint32_t* __restrict__ sigbuf,
-                                                        Counters* cnt, uint32_t cap, double* __restrict__ accum,
-                                                        Probe probe, bool record, uint32_t* status) {
+// Guided continuation at the wave's guide queries of vertex k.  A CTA takes
+// tiles of 128 queries; thread t serves query t % 128 as half h = t / 128
+// (threads t and t + 128 share a TMEM lane).  Encoding: half 0 the grid
+// levels 0-7 and the SH of the normal, half 1 levels 8-15 and the band
+// group; each hidden layer runs on the tensor cores and the epilogue (ReLU,
+// BF16) rewrites the activation tile in place, half h taking columns
+// 32h .. 32h + 31.  Head: half h owns lobes 4h .. 4h + 3; the softmax
+// maximum and sum, the sampled direction and the two partial mixture
+// densities are exchanged through shared memory.  Half 0 then finishes the
+// query (MIS pdf, sun-sample weight, continuation ray, training slot).
+__global__ void __launch_bounds__(kSampleThreads, kSampleCtasPerSm)
+    k_guide_sample(GuideDev g, const uint4* __restrict__ wpack, DevSpectra P, WaveParams w, uint32_t k, GuideWave gw,
+                   float4* __restrict__ qout, float4* __restrict__ sq, float* __restrict__ Lbuf,
+                   uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap, double* __restrict__ accum, Probe probe,
+                   bool record, uint32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* A0 = smem + kSmWf;
-  unsigned char* A1 = A0 + kATileB;
-  uint64_t* mbar = (uint64_t*)(A1 + kATileB);
+  unsigned char* A = smem + kSmWf;
+  float* xch = (float*)(smem + kSmXch);
+  uint64_t* mbar = (uint64_t*)(smem + kSmXch + kRows * kXch * 4u);
   uint32_t* tslot = (uint32_t*)(mbar + 1);
+  uint32_t* sres = tslot + 1;
   const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t r = tid & (kRows - 1), h = tid >> 7;
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l)
+    if (tid == (uint32_t)l) sres[l] = g.res[l];
+  float* X = xch + r * kXch;
   for (uint32_t i = tid; i < kSmWf / 16u; i += blockDim.x) ((uint4*)smem)[i] = __ldg(wpack + i);
   if (tid == 0) {
     tc_mbar_init(mbar, 1);
@@ -614,62 +808,125 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const uint32_t trow = tmem + (((warp & 3u) * 32u) << 16);
   Sync sy{mbar, 0u, true};
   const uint32_t id64 = tc_idesc_bf16(kRows, 64), id48 = tc_idesc_bf16(kRows, kOut);
   const uint32_t count = min(cnt[k].g_count, cap);
   const uint64_t ntiles = (count + kRows - 1) / kRows;
   const float alpha = gw.alpha;
+  const float inv_pi = 0.31830988618379067f;
+  const float p_cone = 1.0f / (2.0f * 3.14159265358979323846f * P.one_minus_cos);
   for (uint64_t tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
-    const uint32_t i = (uint32_t)(tile * kRows) + tid;
+    const uint32_t i = (uint32_t)(tile * kRows) + r;
     const bool valid = i < count;
     float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
     if (valid) {
-      q0 = __ldcs(gw.gq + 3 * i);
-      q1 = __ldcs(gw.gq + 3 * i + 1);
-      q2 = __ldcs(gw.gq + 3 * i + 2);
+      q0 = __ldg(gw.gq + 3 * i);
+      q1 = __ldg(gw.gq + 3 * i + 1);
+      q2 = __ldg(gw.gq + 3 * i + 2);
     }
     const uint32_t bits = __float_as_uint(q0.w), pid = bits & kPidMask;
     const PathId id = path_id(w, pid);
     const uint32_t band = w.band_first + id.j;
     const uint32_t group = band * 9u / w.n_bands;
-    float v[kIn];
-    encode(g, f3(q0), f3(q1), group, v);
-    put_row(A0, tid, v, kIn);
-    unsigned char* src = A0;
-    unsigned char* dst = A1;
+    {
+      float u[3], f[16];
+      unit_pos(g, f3(q0), u);
+      encode_levels8(g, sres, u, 8 * (int)h, f);
+      put8(A, r, 16 * (int)h, f);
+      put8(A, r, 16 * (int)h + 8, f + 8);
+      if (h == 0) {
+        sh16(q1.x, q1.y, q1.z, f);
+        put8(A, r, 32, f);
+        put8(A, r, 40, f + 8);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) f[c] = (uint32_t)c == group ? 1.0f : 0.0f;
+        put8(A, r, 48, f);
+        put8(A, r, 56, f + 8);
+      }
+    }
     for (int l = 0; l < 3; ++l) {
       publish();
-      if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
+      if (tid == 0) gemm(tmem, A, kSliceA, smem + wf_off(l), 2048, 4, id64, false);
       mma_wait(sy, status);
-      load_row(tmem, 0, kHid, v);
-      for (int c = 0; c < kHid; ++c) v[c] = fmaxf(v[c], 0.0f);
-      put_row(dst, tid, v, kHid);
-      unsigned char* t = src;
-      src = dst;
-      dst = t;
+      float v[32];
+      tc_tmem_ld16x2(trow + 32u * h, v);
+#pragma unroll
+      for (int c = 0; c < 32; c += 8) {
+        float t[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) t[e] = fmaxf(v[c + e], 0.0f);
+        put8(A, r, 32 * (int)h + c, t);
+      }
     }
     publish();
-    if (tid == 0) gemm(tmem, src, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
+    if (tid == 0) gemm(tmem, A, kSliceA, smem + wf_off(3), kOut * 32, 4, id48, false);
     mma_wait(sy, status);
-    load_row(tmem, 0, kOut, v);
+    // head: lobes 4h .. 4h + 3 are Y[20h .. 20h + 19]; half 1 loads columns 16 .. 47
+    float y[32];
+    tc_tmem_ld16x2(trow + 16u * h, y);
+#pragma unroll
+    for (int c = 0; c < 20; ++c) y[c] = h ? y[c + 4] : y[c];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mx = fmaxf(mx, y[5 * j]);
+    X[h] = mx;
     tc_fence_before();
     __syncthreads();
-    // one-sample MIS: guide with probability alpha, else cosine sampling
-    bool cont = false;
-    float4 r0 = make_float4(0, 0, 0, 0), r1 = r0;
-    float3 om = make_float3(0, 0, 1);
-    float pdf = 0.0f, c = 0.0f, Tn = 0.0f;
-    if (valid && sy.ok) {
-      Mix h;
-      mixture(v, h);
-      const float3 n = f3(q1);
-      const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k + 1u), w.key0, w.key1);
-      if (u01(u1.x) < alpha) {
-        const float ul = u01(u1.y);
-        int j = 0;
-        float acc = h.pi[0];
-        while (j < kLobes - 1 && ul >= acc) acc += h.pi[++j];
-        om = vmf_sample(h.mu[j], h.kappa[j], u01(u1.z), u01(u1.w));
+    mx = fmaxf(X[0], X[1]);
+    float e[4], s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      e[j] = expf(y[5 * j] - mx);
+      s += e[j];
+    }
+    X[2 + h] = s;
+    __syncthreads();
+    const float s0 = X[2], S = s0 + X[3];
+    const float is = 1.0f / S;
+    float pi[4], mu[4][3], kap[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      pi[j] = e[j] * is;
+      const float m0 = y[5 * j + 1], m1 = y[5 * j + 2], m2 = y[5 * j + 3];
+      const float nm = fmaxf(sqrtf(m0 * m0 + m1 * m1 + m2 * m2), 1e-6f);
+      mu[j][0] = m0 / nm;
+      mu[j][1] = m1 / nm;
+      mu[j][2] = m2 / nm;
+      kap[j] = 0.5f + softplusf(y[5 * j + 4]);
+    }
+    // one-sample MIS: guide with probability alpha, else cosine sampling;
+    // lobe choice on the unnormalised cumulative sum (half 0 first)
+    const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k + 1u), w.key0, w.key1);
+    const bool guide = u01(u1.x) < alpha;
+    const float U = u01(u1.y) * S;
+    const bool mine = guide ? (h == 0 ? U < s0 : !(U < s0)) : h == 0;
+    const float3 n = f3(q1);
+    if (valid && mine) {
+      float3 om;
+      if (guide) {
+        float acc = h == 0 ? 0.0f : s0;
+        int sel = 3;
+        bool found = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc += e[j];
+          if (!found && U < acc) {
+            sel = j;
+            found = true;
+          }
+        }
+        float m[3] = {mu[0][0], mu[0][1], mu[0][2]}, kk = kap[0];
+#pragma unroll
+        for (int j = 1; j < 4; ++j)
+          if (sel == j) {
+            m[0] = mu[j][0];
+            m[1] = mu[j][1];
+            m[2] = mu[j][2];
+            kk = kap[j];
+          }
+        om = vmf_sample(m, kk, u01(u1.z), u01(u1.w));
       } else {
         const uint4 u0 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k), w.key0, w.key1);
         const float rr = sqrtf(u01(u0.z));
@@ -681,34 +938,56 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
         om = make_float3(rr * c2 * b1.x + rr * s2 * b2.x + zz * n.x, rr * c2 * b1.y + rr * s2 * b2.y + zz * n.y,
                          rr * c2 * b1.z + rr * s2 * b2.z + zz * n.z);
       }
-      c = dot(n, om);
-      pdf = alpha * mix_pdf(h, om) + (1.0f - alpha) * fmaxf(c, 0.0f) * 0.31830988618379067f;
+      X[4] = om.x;
+      X[5] = om.y;
+      X[6] = om.z;
+    }
+    __syncthreads();
+    const float3 om = make_float3(X[4], X[5], X[6]);
+    // partial mixture densities at the continuation and at the pending sun sample
+    const uint32_t ss = __float_as_uint(q2.y);
+    const bool has_sun = valid && ss != 0xFFFFFFFFu;
+    float4 sv = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+    if (has_sun) sv = sq[2 * ss + 1];
+    const float3 wn = has_sun ? f3(sv) : make_float3(0, 0, 1);
+    float qo = 0.0f, qn = 0.0f;
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        qo += pi[j] * vmf_pdf(kap[j], mu[j], om);
+        qn += pi[j] * vmf_pdf(kap[j], mu[j], wn);
+      }
+    }
+    X[7 + 2 * h] = qo;
+    X[8 + 2 * h] = qn;
+    __syncthreads();
+    if (h != 0) continue;  // half 1 goes on to the next tile's encoding; no barrier is skipped
+    bool cont = false;
+    float4 r0 = make_float4(0, 0, 0, 0), r1 = r0;
+    if (valid && sy.ok) {
+      const float c = dot(n, om);
+      const float pdf = alpha * (X[7] + X[9]) + (1.0f - alpha) * fmaxf(c, 0.0f) * inv_pi;
       // direct sun by two strategies, balance heuristic: rescale the pending
       // sun sample, weight a later escape of the continuation into the cone
-      const float p_cone = 1.0f / (2.0f * 3.14159265358979323846f * P.one_minus_cos);
-      const uint32_t ss = __float_as_uint(q2.y);
-      float3 wn = make_float3(0, 0, 1);
       float cn = 0.0f;
-      if (ss != 0xFFFFFFFFu) {
-        float4* e = sq + 2 * ss + 1;
-        const float4 sv = *e;
-        wn = f3(sv);
+      if (has_sun) {
         cn = dot(n, wn);
-        const float pm = alpha * mix_pdf(h, wn) + (1.0f - alpha) * fmaxf(cn, 0.0f) * 0.31830988618379067f;
-        e->w = sv.w * (p_cone / (p_cone + pm));
+        const float pm = alpha * (X[8] + X[10]) + (1.0f - alpha) * fmaxf(cn, 0.0f) * inv_pi;
+        sq[2 * ss + 1].w = sv.w * (p_cone / (p_cone + pm));
       }
+      float Tn = 0.0f;
       if (c > 0.0f && pdf > 0.0f) {
         cont = true;
-        Tn = q1.w * q2.x * 0.31830988618379067f * c / pdf;
+        Tn = q1.w * q2.x * inv_pi * c / pdf;
         const bool in_cone = dot(om, P.sun) >= P.cos_max;
         gw.wesc[pid] = in_cone ? pdf / (pdf + p_cone) : 0.0f;
         r0 = make_float4(q0.x, q0.y, q0.z, __uint_as_float(bits | kFlagGuidedEsc));
         r1 = make_float4(om.x, om.y, om.z, Tn);
       } else {
         // no continuation: the path ends here, after its pending sun ray
-        if (ss != 0xFFFFFFFFu) {
-          float4* e = sq + 2 * ss;
-          e->w = __uint_as_float(__float_as_uint(e->w) | kFlagTerm);
+        if (has_sun) {
+          float4* t = sq + 2 * ss;
+          t->w = __uint_as_float(__float_as_uint(t->w) | kFlagTerm);
         } else {
           const float Lp = Lbuf[pid];
           finalize(w, id, Lp, record ? sigbuf[pid] : 0u, accum, probe, record);
@@ -727,7 +1006,7 @@ __global__ void __launch_bounds__(kRows) k_guide_sample(GuideDev g, const uint4*
         raw[4] = make_float4(wn.x, wn.y, wn.z, cn);
         float* r5p = (float*)(raw + 5);  // r5.x (sun radiance) is written by the sun-ray kernel
         r5p[1] = p_cone;
-        r5p[2] = (ss != 0xFFFFFFFFu && cn > 0.0f) ? 1.0f : 0.0f;
+        r5p[2] = (has_sun && cn > 0.0f) ? 1.0f : 0.0f;
       }
     }
     const uint32_t slot = warp_append(&cnt[k + 1].q_count, cont);
@@ -821,7 +1100,7 @@ void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, u
   uint64_t grid = (uint64_t)sms;
   if (grid > tiles) grid = tiles;
   if (grid == 0) return;
-  k_guide_train<<<(unsigned)grid, kRows, smem, st>>>(g, (const uint4*)pack, (const float4*)rec, n, wsum, dW, dgrid,
+  k_guide_train<<<(unsigned)grid, kTrainThreads, smem, st>>>(g, (const uint4*)pack, (const float4*)rec, n, wsum, dW, dgrid,
                                                       loss, status);
 }
 
@@ -834,7 +1113,7 @@ void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& 
                          const GuideWave& gw, const WaveBufs& b, double* accum, const Probe& probe, bool record,
                          int sms, cudaStream_t st) {
   cudaFuncSetAttribute(k_guide_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
-  k_guide_sample<<<sms * 3, kRows, kSampleSmem, st>>>(g, (const uint4*)pack, P, w, k, gw, b.q[(k + 1) & 1], b.sq, b.L,
+  k_guide_sample<<<sms * kSampleCtasPerSm, kSampleThreads, kSampleSmem, st>>>(g, (const uint4*)pack, P, w, k, gw, b.q[(k + 1) & 1], b.sq, b.L,
                                                       b.sig, b.cnt, b.cap, accum, probe, record, b.status);
 }
 
