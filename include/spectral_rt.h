@@ -91,7 +91,9 @@ typedef struct {
   uint32_t use_graph;      /* 1: the whole render (all waves, XYZ) is captured once per launch
                             * configuration into a CUDA graph and replayed (camera poses may change
                             * between replays); excludes timing, counting, probes and guide training */
-  uint32_t trace_variant;  /* traversal loop: 0 = one node or leaf per step, 1 = while-while */
+  uint32_t trace_variant;  /* traversal loop: 0 = leaf batching (interior steps until leaf_batch
+                            * lanes of a warp wait at a leaf, then one leaf step for all of them),
+                            * 1 = while-while, 2 = one node or leaf per lane and step */
   /* persistent traversal warps refill idle lanes from the queue once at least
    * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
    * lane between refill checks; 0 = library default (tuned) */
@@ -109,7 +111,8 @@ typedef struct {
   uint32_t sample_first;
   uint32_t accumulate;
   uint32_t spp_total;
-  uint32_t reserved[2];
+  uint32_t leaf_batch;     /* trace_variant 0: 1..32 waiting lanes start a leaf phase; 0 = default */
+  uint32_t reserved[1];
 } rt_render_opts;
 
 typedef struct {
@@ -284,7 +287,7 @@ rt_status rt_xyz(rt_ctx* ctx, const double* spectral_dev, uint64_t n_pixels, uin
 
 /* Autotuner: times probe renders (spp_probe samples of the given views and
  * bands, depth `depth`, results discarded) over the wave capacity, the
- * traversal loop parameters and the traversal block size (coordinate
+ * leaf batch, the traversal loop parameters and the traversal block size (coordinate
  * descent, device time from CUDA events, one warm-up render per setting) and
  * writes the fastest setting into opts (other fields are kept). */
 typedef struct {

@@ -43,7 +43,8 @@ class RenderOpts(C.Structure):
                 ("trace_steps", C.c_uint32), ("trace_refill", C.c_uint32), ("shadow_steps", C.c_uint32),
                 ("shadow_refill", C.c_uint32), ("guided", C.c_uint32), ("guide_collect", C.c_uint32),
                 ("guide_train_steps", C.c_uint32), ("guide_batch", C.c_uint32), ("sample_first", C.c_uint32),
-                ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("reserved", C.c_uint32 * 2)]
+                ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("leaf_batch", C.c_uint32),
+                ("reserved", C.c_uint32 * 1)]
 
 
 class AutotuneReport(C.Structure):

@@ -506,7 +506,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
   if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
-  if (o.trace_variant > 1) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if (o.guided && !c->guide.init) return fail(c, RT_ERR_STATE, "rt_render: guided rendering needs rt_guide_init");
   if (o.guide_train_steps && !(o.guided && o.guide_collect))
@@ -593,6 +594,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   lc.counting = c->counting;
   lc.record = o.probe_map_dev != nullptr;
   lc.variant = (int)o.trace_variant;
+  lc.leaf_min = o.leaf_batch ? (int)o.leaf_batch : kDefaultLeafBatch;
   lc.trace_steps = o.trace_steps ? (int)o.trace_steps : kDefaultTraceSteps;
   lc.trace_refill = o.trace_refill ? (int)o.trace_refill : kDefaultTraceRefill;
   lc.shadow_steps = o.shadow_steps ? (int)o.shadow_steps : kDefaultShadowSteps;
@@ -723,12 +725,12 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     // one captured graph per launch configuration, replayed on an internal
     // stream ordered after the caller's stream
     char kb[512];
-    std::snprintf(kb, sizeof(kb), "%u|%llu|%u|%u|%u|%u|%llu|%u|%u|%u|%u|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%u|%u|%u|%u|%g",
+    std::snprintf(kb, sizeof(kb), "%u|%llu|%u|%u|%u|%u|%llu|%u|%u|%u|%u|%p|%p|%p|%p|%d|%d|%d|%d|%d|%d|%d|%d|%u|%u|%u|%u|%g|%d",
                   n_cams, (unsigned long long)npix, band_first, band_count, spp, depth, (unsigned long long)seed,
                   o.sample_first, o.accumulate, o.spp_total, o.xyz_mode, (void*)accum, (void*)xyz_dev,
                   (void*)c->d_nodes, (void*)c->d_mb, lc.grid_trace, lc.block_trace, lc.variant, lc.trace_steps,
                   lc.trace_refill, lc.shadow_steps, lc.shadow_refill, (int)cap, o.guided, gw.depth, gw.collect,
-                  o.wave_capacity, (double)gw.alpha);
+                  o.wave_capacity, (double)gw.alpha, lc.leaf_min);
     std::string key(kb);
     char pb[160];
     std::snprintf(pb, sizeof(pb), "|%p|%p|%p|%p|%p", (void*)c->wb.q[0], (void*)c->wb.sq, (void*)gw.gq,
@@ -1138,16 +1140,23 @@ rt_status rt_autotune(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_
     }
     return RT_OK;
   };
-  // coordinate descent: paths in flight, closest-hit loop, sun-ray loop, block
+  // coordinate descent: paths in flight, leaf batch, closest-hit loop,
+  // sun-ray loop, block
   const uint32_t waves[] = {1u << 21, 1u << 22, 1u << 23, 1u << 24};
-  const uint32_t tl[][2] = {{8, 8}, {4, 12}, {16, 8}, {2, 16}, {1, 12}};
-  const uint32_t sl[][2] = {{4, 12}, {8, 8}, {1, 12}, {16, 16}};
+  const uint32_t leaf[] = {8, 12, 24};
+  const uint32_t tl[][2] = {{16, 8}, {4, 8}, {8, 4}, {8, 16}};
+  const uint32_t sl[][2] = {{16, 12}, {4, 12}, {8, 4}, {8, 24}};
   const uint32_t blocks[] = {128, 64, 256};
   rt_render_opts o;
   for (uint32_t wv : waves) {
     o = best;
     o.wave_capacity = wv;
     if ((e = try_opt(o))) break;
+  }
+  for (size_t i = 0; e == RT_OK && base.trace_variant == 0 && i < sizeof(leaf) / sizeof(leaf[0]); ++i) {
+    o = best;
+    o.leaf_batch = leaf[i];
+    e = try_opt(o);
   }
   for (size_t i = 0; e == RT_OK && i < sizeof(tl) / sizeof(tl[0]); ++i) {
     o = best;
@@ -1176,6 +1185,7 @@ rt_status rt_autotune(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_
   opts->shadow_steps = best.shadow_steps;
   opts->shadow_refill = best.shadow_refill;
   opts->trace_block = best.trace_block;
+  opts->leaf_batch = best.leaf_batch;
   if (report) {
     report->trials = trials;
     report->best_ms = best_ms;

@@ -150,7 +150,8 @@ struct Probe {
 
 // Default traversal loop parameters (set from measurements on a GB300).
 constexpr int kDefaultTraceSteps = 8, kDefaultTraceRefill = 8;
-constexpr int kDefaultShadowSteps = 4, kDefaultShadowRefill = 12;
+constexpr int kDefaultShadowSteps = 8, kDefaultShadowRefill = 12;
+constexpr int kDefaultLeafBatch = 16;
 
 // Launchers (rt_kernels.cu).
 struct LaunchCfg {
@@ -158,7 +159,8 @@ struct LaunchCfg {
   int grid_shade, block_shade;
   bool counting;
   bool record;
-  int variant;  // traversal loop: 0 = node-or-leaf steps, 1 = while-while steps
+  int variant;  // traversal loop: 0 = leaf batching, 1 = while-while steps, 2 = node-or-leaf steps
+  int leaf_min;  // variant 2: lanes waiting at a leaf that start a leaf phase
   int trace_steps, trace_refill;    // closest hit: steps between refill checks, refill threshold
   int shadow_steps, shadow_refill;  // sun rays: the same
 };

@@ -300,10 +300,15 @@ constexpr uint32_t kNoRay = 0xFFFFFFFFu;
 // `steps` traversal steps between refill checks (steps large and refill 32
 // give one batch of 32 rays per warp at a time).
 
-template <bool FMA, bool COUNT, bool WW>
+// MODE 0: each lane runs up to `steps` node-or-leaf steps; 1: while-while
+// steps; 2 (the default loop, render option trace_variant 0): warp-synchronous phases - interior steps for the lanes at an
+// interior node until at least `leaf_min` lanes wait at a leaf (or none can
+// go on), then one leaf step for every waiting lane, so that the costly
+// triangle tests run with most of their lanes busy.
+template <bool FMA, bool COUNT, int MODE>
 __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
-                                               uint32_t* status, int steps, int refill) {
+                                               uint32_t* status, int steps, int refill, int leaf_min) {
   const uint32_t count = min(cnt[k].q_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->ext_rays, (unsigned long long)count);
   const uint32_t lane = threadIdx.x & 31u;
@@ -338,9 +343,35 @@ __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restr
       if (drained) break;
       continue;
     }
-    if (ray != kNoRay) {
+    if (MODE == 2) {
       bool done = false;
-      for (int i = 0; i < steps && !done; ++i) done = closest_step<FMA, COUNT, WW>(tv, stack, S, icap, status, nn, nt);
+      for (int i = 0; i < steps; ++i) {
+        const bool act = ray != kNoRay && !done;
+        const bool at_leaf = act && tv.cnt != 0u;
+        const uint32_t ml = __ballot_sync(0xffffffffu, at_leaf);
+        const uint32_t mi = __ballot_sync(0xffffffffu, act && !at_leaf);
+        if ((ml | mi) == 0u) break;
+        const bool leaf_phase = mi == 0u || (int)__popc(ml) >= leaf_min;
+        if (act && at_leaf == leaf_phase) {
+          if (++tv.iter > icap) {
+            atomicOr(status, ST_ITER);
+            done = true;
+          } else if (leaf_phase) {
+            closest_leaf(tv, S, nt, COUNT);
+            done = !trav_pop(tv, stack, tv.best_t);
+          } else if (!trav_interior<FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)) {
+            done = !trav_pop(tv, stack, tv.best_t);
+          }
+        }
+      }
+      if (ray != kNoRay && done) {
+        __stcs(hit + ray, make_float2(tv.best_leaf < 0 ? -1.0f : tv.best_t, __int_as_float(tv.best_leaf)));
+        ray = kNoRay;
+      }
+    } else if (ray != kNoRay) {
+      bool done = false;
+      for (int i = 0; i < steps && !done; ++i)
+        done = closest_step<FMA, COUNT, MODE == 1>(tv, stack, S, icap, status, nn, nt);
       if (done) {
         __stcs(hit + ray, make_float2(tv.best_leaf < 0 ? -1.0f : tv.best_t, __int_as_float(tv.best_leaf)));
         ray = kNoRay;
@@ -521,13 +552,13 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
   }
 }
 
-template <bool RECORD, bool COUNT, bool WW>
+template <bool RECORD, bool COUNT, int MODE>
 __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
                                                 uint32_t* status, int steps, int refill, float* Lfinal,
-                                                GuideWave gw) {
+                                                GuideWave gw, int leaf_min) {
   const bool rec_sun = gw.on && gw.collect != 0u && k <= gw.depth && k < w.depth;
   const uint32_t count = min(cnt[k].s_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
@@ -569,10 +600,30 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WavePa
       continue;
     }
     bool done = false;
-    if (ray != kNoRay) {
+    if (MODE == 2) {
+      done = ray != kNoRay && tv.sp < 0;
+      for (int i = 0; i < steps; ++i) {
+        const bool act = ray != kNoRay && !done;
+        const bool at_leaf = act && tv.cnt != 0u;
+        const uint32_t ml = __ballot_sync(0xffffffffu, at_leaf);
+        const uint32_t mi = __ballot_sync(0xffffffffu, act && !at_leaf);
+        if ((ml | mi) == 0u) break;
+        const bool leaf_phase = mi == 0u || (int)__popc(ml) >= leaf_min;
+        if (act && at_leaf == leaf_phase) {
+          if (++tv.iter > icap) {
+            atomicOr(status, ST_ITER);
+            done = true;
+          } else if (leaf_phase) {
+            done = shadow_leaf(tv, S, P, dir, band, T, ng, nt, COUNT) || !trav_pop(tv, stack, INFINITY);
+          } else if (!trav_interior<true, COUNT>(tv, stack, S, INFINITY, status, nn)) {
+            done = !trav_pop(tv, stack, INFINITY);
+          }
+        }
+      }
+    } else if (ray != kNoRay) {
       done = tv.sp < 0;
       for (int i = 0; i < steps && !done; ++i)
-        done = shadow_step<true, COUNT, WW>(tv, stack, S, P, dir, band, T, ng, icap, status, nn, nt);
+        done = shadow_step<true, COUNT, MODE == 1>(tv, stack, S, P, dir, band, T, ng, icap, status, nn, nt);
     }
     if (done) {
       const uint32_t pid = bits & kPidMask;
@@ -665,43 +716,57 @@ int grid_for(uint64_t n, int block) {
   return (int)(g == 0 ? 1 : g);
 }
 
-template <bool FMA, bool COUNT, bool WW>
+template <bool FMA, bool COUNT, int MODE>
 void trace_t(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k, cudaStream_t st) {
-  k_trace<FMA, COUNT, WW><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status,
-                                                                   lc.trace_steps, lc.trace_refill);
+  k_trace<FMA, COUNT, MODE><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status,
+                                                                     lc.trace_steps, lc.trace_refill, lc.leaf_min);
+}
+
+template <bool FMA, bool COUNT>
+void trace_m(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
+             cudaStream_t st) {
+  if (lc.variant == 2) trace_t<FMA, COUNT, 0>(lc, S, qin, b, k, st);
+  else if (lc.variant == 1) trace_t<FMA, COUNT, 1>(lc, S, qin, b, k, st);
+  else trace_t<FMA, COUNT, 2>(lc, S, qin, b, k, st);
 }
 
 void launch_trace(const LaunchCfg& lc, bool robust, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
                   cudaStream_t st) {
-  const bool ww = lc.variant == 1;
   if (robust) {
-    if (lc.counting) ww ? trace_t<false, true, true>(lc, S, qin, b, k, st) : trace_t<false, true, false>(lc, S, qin, b, k, st);
-    else ww ? trace_t<false, false, true>(lc, S, qin, b, k, st) : trace_t<false, false, false>(lc, S, qin, b, k, st);
+    if (lc.counting) trace_m<false, true>(lc, S, qin, b, k, st);
+    else trace_m<false, false>(lc, S, qin, b, k, st);
   } else {
-    if (lc.counting) ww ? trace_t<true, true, true>(lc, S, qin, b, k, st) : trace_t<true, true, false>(lc, S, qin, b, k, st);
-    else ww ? trace_t<true, false, true>(lc, S, qin, b, k, st) : trace_t<true, false, false>(lc, S, qin, b, k, st);
+    if (lc.counting) trace_m<true, true>(lc, S, qin, b, k, st);
+    else trace_m<true, false>(lc, S, qin, b, k, st);
   }
 }
 
-template <bool RECORD, bool COUNT, bool WW>
+template <bool RECORD, bool COUNT, int MODE>
 void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
               const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, const GuideWave& gw,
               cudaStream_t st) {
-  k_shadow<RECORD, COUNT, WW><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum,
-                                                                      probe, b.tot, b.status, lc.shadow_steps,
-                                                                      lc.shadow_refill, Lfinal, gw);
+  k_shadow<RECORD, COUNT, MODE><<<lc.grid_trace, lc.block_trace, 0, st>>>(
+      S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe, b.tot, b.status, lc.shadow_steps, lc.shadow_refill,
+      Lfinal, gw, lc.leaf_min);
+}
+
+template <bool RECORD, bool COUNT>
+void shadow_m(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
+              const WaveBufs& b, double* accum, const Probe& probe, float* Lf, const GuideWave& gw, cudaStream_t st) {
+  if (lc.variant == 2) shadow_t<RECORD, COUNT, 0>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  else if (lc.variant == 1) shadow_t<RECORD, COUNT, 1>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  else shadow_t<RECORD, COUNT, 2>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
 }
 
 void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
                    const WaveBufs& b, double* accum, const Probe& probe, float* Lf, const GuideWave& gw,
                    cudaStream_t st) {
-  const bool ww = lc.variant == 1;
   if (lc.record) {
-    if (lc.counting) ww ? shadow_t<true, true, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<true, true, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
-    else ww ? shadow_t<true, false, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<true, false, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+    if (lc.counting) shadow_m<true, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+    else shadow_m<true, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   } else {
-    if (lc.counting) ww ? shadow_t<false, true, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<false, true, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
-    else ww ? shadow_t<false, false, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st) : shadow_t<false, false, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+    if (lc.counting) shadow_m<false, true>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+    else shadow_m<false, false>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   }
 }
 

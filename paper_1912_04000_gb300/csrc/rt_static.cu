@@ -184,6 +184,7 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   lc.counting = false;
   lc.record = false;
   lc.variant = 0;
+  lc.leaf_min = kDefaultLeafBatch;
   lc.trace_steps = kDefaultTraceSteps;
   lc.trace_refill = kDefaultTraceRefill;
   lc.shadow_steps = kDefaultShadowSteps;

@@ -101,13 +101,16 @@ def test_nave_sampled_pixels(R):
 
 
 def test_traversal_loop_variants_agree(R):
-    """Loop shape (while-while or not, steps between refills, refill
-    threshold) changes only scheduling: closest hits are the same, sun-ray
-    glass products may differ by float rounding order."""
+    """Loop shape (while-while, leaf batching or one node per step, steps
+    between refills, refill threshold, leaf batch) changes only scheduling:
+    closest hits are the same, sun-ray glass products may differ by float
+    rounding order."""
     wl = scenes.nave(width=64, height=48, n_bands=8, spp=2)
     R.load(wl)
     base = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)["spectral"].cpu().numpy()
     for kw in (dict(trace_variant=1), dict(trace_steps=1, trace_refill=32, shadow_steps=1000, shadow_refill=32),
-               dict(trace_steps=3, trace_refill=5, shadow_steps=2, shadow_refill=20)):
+               dict(trace_steps=3, trace_refill=5, shadow_steps=2, shadow_refill=20),
+               dict(trace_variant=2), dict(leaf_batch=1, trace_steps=1, shadow_steps=3),
+               dict(leaf_batch=32, trace_steps=40, trace_refill=32, shadow_steps=7)):
         s = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2, **kw)["spectral"].cpu().numpy()
         np.testing.assert_allclose(s, base, rtol=1e-5, atol=1e-12)
