@@ -91,9 +91,10 @@ typedef struct {
   uint32_t use_graph;      /* 1: the whole render (all waves, XYZ) is captured once per launch
                             * configuration into a CUDA graph and replayed (camera poses may change
                             * between replays); excludes timing, counting, probes and guide training */
-  uint32_t trace_variant;  /* traversal loop: 0 = leaf batching (interior steps until leaf_batch
-                            * lanes of a warp wait at a leaf, then one leaf step for all of them),
-                            * 1 = while-while, 2 = one node or leaf per lane and step */
+  uint32_t trace_variant;  /* traversal: 0 = four-wide BVH with leaf batching (interior steps
+                            * until leaf_batch lanes of a warp wait at a leaf, then one leaf step
+                            * for all of them); binary BVH with 1 = while-while, 2 = one node or
+                            * leaf per lane and step, 3 = leaf batching */
   /* persistent traversal warps refill idle lanes from the queue once at least
    * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
    * lane between refill checks; 0 = library default (tuned) */

@@ -24,9 +24,10 @@ struct rt_ctx {
   int occ_shade = 0;
   // scene
   float4* d_nodes = nullptr;
+  float4* d_nodes4 = nullptr;
   float4* d_tris = nullptr;
   float4* d_nrm = nullptr;
-  uint32_t n_nodes = 0, n_tris = 0, n_mat = 0;
+  uint32_t n_nodes = 0, n_nodes4 = 0, n_tris = 0, n_mat = 0;
   float eps = 0.0f;
   bool has_scene = false;
   // spectra
@@ -136,9 +137,11 @@ rt_status ensure_wave(rt_ctx* c, uint32_t cap) {
 DevScene dev_scene(const rt_ctx* c) {
   DevScene S;
   S.nodes = c->d_nodes;
+  S.nodes4 = c->d_nodes4;
   S.tris = c->d_tris;
   S.nrm = c->d_nrm;
   S.n_nodes = c->n_nodes;
+  S.n_nodes4 = c->n_nodes4;
   S.n_tris = c->n_tris;
   S.eps = c->eps;
   return S;
@@ -256,6 +259,7 @@ void rt_destroy(rt_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   dfree(c->d_nodes);
+  dfree(c->d_nodes4);
   dfree(c->d_tris);
   dfree(c->d_nrm);
   dfree(c->d_mb);
@@ -404,19 +408,36 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     nd[2 * i] = make_float4(down(b.lo[0]), down(b.lo[1]), down(b.lo[2]), rf);
     nd[2 * i + 1] = make_float4(up(b.hi[0]), up(b.hi[1]), up(b.hi[2]), cf);
   }
+  // four-wide nodes, padded the same way (empty slots keep their +-inf box)
+  std::vector<Bvh4Node> b4;
+  collapse_bvh4(bvh, b4, nullptr);
+  for (Bvh4Node& n4 : b4)
+    for (int i = 0; i < 4; ++i)
+      if (n4.cnt[i] != kEmpty4) {
+        n4.lox[i] = down(n4.lox[i]);
+        n4.loy[i] = down(n4.loy[i]);
+        n4.loz[i] = down(n4.loz[i]);
+        n4.hix[i] = up(n4.hix[i]);
+        n4.hiy[i] = up(n4.hiy[i]);
+        n4.hiz[i] = up(n4.hiz[i]);
+      }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c->d_nodes);
+  dfree(c->d_nodes4);
   dfree(c->d_tris);
   dfree(c->d_nrm);
   c->has_scene = false;
   CUDA_TRY(c, cudaMalloc(&c->d_nodes, nd.size() * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&c->d_nodes4, b4.size() * sizeof(Bvh4Node)));
+  CUDA_TRY(c, cudaMemcpy(c->d_nodes4, b4.data(), b4.size() * sizeof(Bvh4Node), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMalloc(&c->d_tris, tr.size() * sizeof(float4)));
   CUDA_TRY(c, cudaMalloc(&c->d_nrm, nr.size() * sizeof(float4)));
   CUDA_TRY(c, cudaMemcpy(c->d_nodes, nd.data(), nd.size() * sizeof(float4), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->d_tris, tr.data(), tr.size() * sizeof(float4), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->d_nrm, nr.data(), nr.size() * sizeof(float4), cudaMemcpyHostToDevice));
   c->n_nodes = (uint32_t)bvh.nodes.size();
+  c->n_nodes4 = (uint32_t)b4.size();
   c->n_tris = n_tris;
   c->n_mat = n_mat;
   const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
@@ -506,7 +527,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
   if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
-  if (o.trace_variant > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant > 3) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
   if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if (o.guided && !c->guide.init) return fail(c, RT_ERR_STATE, "rt_render: guided rendering needs rt_guide_init");
@@ -1143,7 +1164,7 @@ rt_status rt_autotune(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_
   // coordinate descent: paths in flight, leaf batch, closest-hit loop,
   // sun-ray loop, block
   const uint32_t waves[] = {1u << 21, 1u << 22, 1u << 23, 1u << 24};
-  const uint32_t leaf[] = {8, 12, 24};
+  const uint32_t leaf[] = {12, 16, 32};
   const uint32_t tl[][2] = {{16, 8}, {4, 8}, {8, 4}, {8, 16}};
   const uint32_t sl[][2] = {{16, 12}, {4, 12}, {8, 4}, {8, 24}};
   const uint32_t blocks[] = {128, 64, 256};

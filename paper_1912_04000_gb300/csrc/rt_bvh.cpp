@@ -1,4 +1,5 @@
-// Binned SAH BVH2 builder (host, C++17), flattened to 32-byte nodes.
+// Binned SAH BVH2 builder (host, C++17), flattened to 32-byte nodes, and its
+// collapse to a four-wide BVH.
 //
 // Method: binned surface-area heuristic over triangle centroids (Wald, "On
 // fast construction of SAH-based bounding volume hierarchies", IEEE RT 2007),
@@ -11,6 +12,10 @@
 // at nodes ref and ref + 1 with ref even, so a sibling pair is one aligned
 // 64-byte line; a leaf holds `count` triangles from position `ref` of the
 // leaf-ordered triangle list.
+//
+// collapse_bvh4 turns the binary tree into a four-wide one (128-byte nodes,
+// one cache line each) with the same leaves, which the default traversal
+// reads: half the dependent node fetches per ray.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -181,6 +186,81 @@ int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out
   }
   out.order = std::move(idx);
   out.max_depth = max_depth;
+  return 0;
+}
+
+int collapse_bvh4(const BvhOut& b2, std::vector<Bvh4Node>& out, uint32_t* max_depth) {
+  const std::vector<BvhNode>& nb = b2.nodes;
+  auto area = [&](uint32_t i) {
+    const BvhNode& b = nb[i];
+    const double dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  };
+  out.clear();
+  out.reserve(nb.size() / 2 + 1);
+  struct Item {
+    uint32_t b2node, slot, depth;
+  };
+  std::vector<Item> todo;
+  out.push_back(Bvh4Node{});
+  todo.push_back({1u, 0u, 1u});
+  uint32_t md = 0;
+  while (!todo.empty()) {
+    const Item it = todo.back();
+    todo.pop_back();
+    md = std::max(md, it.depth);
+    // children of this four-wide node, as binary node indices
+    uint32_t ch[4];
+    int n = 0;
+    if (nb[it.b2node].count != 0) {
+      ch[n++] = it.b2node;  // a root that is a leaf
+    } else {
+      ch[n++] = nb[it.b2node].ref;
+      ch[n++] = nb[it.b2node].ref + 1;
+      while (n < 4) {
+        int best = -1;
+        double ba = -1.0;
+        for (int i = 0; i < n; ++i)
+          if (nb[ch[i]].count == 0 && area(ch[i]) > ba) {
+            ba = area(ch[i]);
+            best = i;
+          }
+        if (best < 0) break;
+        const uint32_t r = nb[ch[best]].ref;
+        ch[best] = r;
+        ch[n++] = r + 1;
+      }
+    }
+    Bvh4Node nd{};
+    for (int i = 0; i < 4; ++i) {
+      if (i < n) {
+        const BvhNode& b = nb[ch[i]];
+        nd.lox[i] = b.lo[0];
+        nd.loy[i] = b.lo[1];
+        nd.loz[i] = b.lo[2];
+        nd.hix[i] = b.hi[0];
+        nd.hiy[i] = b.hi[1];
+        nd.hiz[i] = b.hi[2];
+        if (b.count != 0) {
+          nd.ref[i] = b.ref;
+          nd.cnt[i] = b.count;
+        } else {
+          const uint32_t slot = (uint32_t)out.size();
+          out.push_back(Bvh4Node{});
+          nd.ref[i] = slot;
+          nd.cnt[i] = 0;
+          todo.push_back({ch[i], slot, it.depth + 1});
+        }
+      } else {
+        nd.lox[i] = nd.loy[i] = nd.loz[i] = INFINITY;
+        nd.hix[i] = nd.hiy[i] = nd.hiz[i] = -INFINITY;
+        nd.ref[i] = 0;
+        nd.cnt[i] = kEmpty4;
+      }
+    }
+    out[it.slot] = nd;
+  }
+  if (max_depth) *max_depth = md;
   return 0;
 }
 

@@ -23,4 +23,21 @@ struct BvhOut {
 // Builds the BVH of nt triangles (indices into verts[.][3]).  Returns 0.
 int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out);
 
+// Four-wide node: child boxes in structure-of-arrays order (one float4 per
+// plane), child i an interior node (cnt[i] = 0, ref[i] = node index), a leaf
+// (cnt[i] = 1..4 triangles from leaf position ref[i]) or empty (cnt[i] =
+// kEmpty4, box lo = +inf, hi = -inf, which no slab test enters).
+constexpr uint32_t kEmpty4 = 0xFFFFFFFFu;
+struct Bvh4Node {
+  float lox[4], hix[4], loy[4], hiy[4], loz[4], hiz[4];
+  uint32_t ref[4], cnt[4];
+};
+static_assert(sizeof(Bvh4Node) == 128, "128-byte node");
+
+// Collapses the binary BVH into a four-wide one (node 0 the root): every
+// interior node takes the children of its binary node and repeatedly replaces
+// the interior child of largest surface area by its two children until it
+// has four.  Leaves and the leaf order are those of the binary tree.
+int collapse_bvh4(const BvhOut& b2, std::vector<Bvh4Node>& out, uint32_t* max_depth);
+
 }  // namespace srt

@@ -14,7 +14,7 @@ enum : uint32_t {
   ST_RANGE = 8u       // index out of range caught by a device check
 };
 
-constexpr int kStack = 64;             // traversal stack entries per thread
+constexpr int kStack = 96;             // traversal stack entries per thread
 constexpr uint32_t kPidBits = 24;      // path id bits in a queue entry
 constexpr uint32_t kPidMask = (1u << kPidBits) - 1u;
 constexpr uint32_t kFlagCovered = 1u << 31;  // direct sun already estimated by NEE
@@ -32,10 +32,12 @@ constexpr uint32_t kMaxWave = 1u << kPidBits;
 // nrm: per leaf-order triangle {unit geometric normal (FP64-rounded),
 //   bits(material)}.
 struct DevScene {
-  const float4* nodes;
+  const float4* nodes;   // binary BVH: 2 float4 per node, node 1 the root
+  const float4* nodes4;  // four-wide BVH: 8 float4 per node, node 0 the root
   const float4* tris;
   const float4* nrm;
   uint32_t n_nodes;
+  uint32_t n_nodes4;
   uint32_t n_tris;
   float eps;  // origin offset along the normal: 1e-4 x scene diagonal
 };
@@ -151,7 +153,7 @@ struct Probe {
 // Default traversal loop parameters (set from measurements on a GB300).
 constexpr int kDefaultTraceSteps = 8, kDefaultTraceRefill = 8;
 constexpr int kDefaultShadowSteps = 8, kDefaultShadowRefill = 12;
-constexpr int kDefaultLeafBatch = 16;
+constexpr int kDefaultLeafBatch = 24;
 
 // Launchers (rt_kernels.cu).
 struct LaunchCfg {
@@ -159,7 +161,8 @@ struct LaunchCfg {
   int grid_shade, block_shade;
   bool counting;
   bool record;
-  int variant;  // traversal loop: 0 = leaf batching, 1 = while-while steps, 2 = node-or-leaf steps
+  int variant;  // traversal: 0 = four-wide, leaf batching; binary: 1 = while-while, 2 = node-or-leaf steps,
+                // 3 = leaf batching
   int leaf_min;  // variant 2: lanes waiting at a leaf that start a leaf phase
   int trace_steps, trace_refill;    // closest hit: steps between refill checks, refill threshold
   int shadow_steps, shadow_refill;  // sun rays: the same

@@ -43,6 +43,7 @@ struct Trav {
   uint32_t ref, cnt;
   int sp;
   uint32_t iter;
+  uint32_t oct;  // four-wide nodes: bit a set when the ray runs towards -axis a
 };
 
 template <bool FMA>
@@ -129,6 +130,144 @@ __device__ __forceinline__ bool trav_pop(Trav& tv, const uint2* stack, float tma
     }
   }
   return false;
+}
+
+// ---------------------------------------------------------------------------
+// Four-wide BVH (node = 8 float4: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the
+// four children, then their refs and counts).  Per axis the ray's direction
+// sign picks the entry plane (lo for a positive direction) and the exit
+// plane, so one slab test per child needs no min/max of the plane pair and an
+// empty child slot (lo = +inf, hi = -inf) is never entered.  The box test
+// rounds as box_t above.
+// ---------------------------------------------------------------------------
+template <bool FMA>
+__device__ __forceinline__ void trav_init4(Trav& tv, float3 o, float3 d) {
+  tv.rw = ray_prep(o, d);
+  const float tiny = 1e-20f;
+  tv.inv.x = 1.0f / (fabsf(d.x) > tiny ? d.x : copysignf(tiny, d.x));
+  tv.inv.y = 1.0f / (fabsf(d.y) > tiny ? d.y : copysignf(tiny, d.y));
+  tv.inv.z = 1.0f / (fabsf(d.z) > tiny ? d.z : copysignf(tiny, d.z));
+  tv.oinv = FMA ? make_float3(o.x * tv.inv.x, o.y * tv.inv.y, o.z * tv.inv.z) : o;
+  tv.best_t = INFINITY;
+  tv.best_id = 0xFFFFFFFFu;
+  tv.best_leaf = -1;
+  tv.sp = 0;
+  tv.iter = 0;
+  tv.ref = 0;
+  tv.cnt = 0;
+  tv.oct = (tv.inv.x < 0.0f ? 1u : 0u) | (tv.inv.y < 0.0f ? 2u : 0u) | (tv.inv.z < 0.0f ? 4u : 0u);
+}
+
+template <bool FMA>
+__device__ __forceinline__ float slab(float plane, float inv, float oinv) {
+  // robust mode: oinv holds the origin itself
+  return FMA ? fmaf(plane, inv, -oinv) : __fmul_rn(__fsub_rn(plane, oinv), inv);
+}
+
+template <bool FMA>
+__device__ __forceinline__ float child_t(const Trav& tv, float nx, float fx, float ny, float fy, float nz, float fz,
+                                         float tmax) {
+  const float tn = fmaxf(fmaxf(slab<FMA>(nx, tv.inv.x, tv.oinv.x), slab<FMA>(ny, tv.inv.y, tv.oinv.y)),
+                         fmaxf(slab<FMA>(nz, tv.inv.z, tv.oinv.z), 0.0f));
+  const float tf = fminf(fminf(slab<FMA>(fx, tv.inv.x, tv.oinv.x), slab<FMA>(fy, tv.inv.y, tv.oinv.y)),
+                         fminf(slab<FMA>(fz, tv.inv.z, tv.oinv.z), tmax));
+  return tn <= tf * 1.0000005f ? tn : INFINITY;
+}
+
+__device__ __forceinline__ void cswap(float& ta, uint32_t& pa, float& tb, uint32_t& pb) {
+  const bool sw = tb < ta;
+  const float t = sw ? tb : ta;
+  const uint32_t p = sw ? pb : pa;
+  tb = sw ? ta : tb;
+  pb = sw ? pa : pb;
+  ta = t;
+  pa = p;
+}
+
+// Interior node: test the four children, descend into the nearest entered
+// one and push the others, the nearer ones last (popped first); with ANY
+// (sun rays, which need every crossed sheet or one opaque hit, in any order)
+// descend into the first entered child and push the rest in slot order.
+// Returns false if no child is entered.
+template <bool FMA, bool COUNT, bool ANY = false>
+__device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const DevScene& S, float tmax,
+                                               uint32_t* status, uint32_t& n_nodes) {
+  const float4* nd = S.nodes4 + 8u * tv.ref;
+  const uint32_t ox = tv.oct & 1u, oy = (tv.oct >> 1) & 1u, oz = (tv.oct >> 2) & 1u;
+  const float4 nx = ldg4(nd + ox), fx = ldg4(nd + (ox ^ 1u));
+  const float4 ny = ldg4(nd + 2u + oy), fy = ldg4(nd + 2u + (oy ^ 1u));
+  const float4 nz = ldg4(nd + 4u + oz), fz = ldg4(nd + 4u + (oz ^ 1u));
+  const uint4 rf = __ldg((const uint4*)(nd + 6)), ct = __ldg((const uint4*)(nd + 7));
+  if (COUNT) n_nodes += 4;
+  float t0 = child_t<FMA>(tv, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, tmax);
+  float t1 = child_t<FMA>(tv, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, tmax);
+  float t2 = child_t<FMA>(tv, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, tmax);
+  float t3 = child_t<FMA>(tv, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, tmax);
+  // children packed as the stack stores them: ref << 3 | count
+  uint32_t p0 = (rf.x << 3) | (ct.x & 7u), p1 = (rf.y << 3) | (ct.y & 7u);
+  uint32_t p2 = (rf.z << 3) | (ct.z & 7u), p3 = (rf.w << 3) | (ct.w & 7u);
+  const int nh = (t0 < INFINITY) + (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
+  if (nh == 0) return false;
+  if (ANY) {
+    if (tv.sp + nh - 1 > kStack) {
+      atomicOr(status, ST_STACK);
+      tv.sp = 0;
+      return false;
+    }
+    bool first = true;
+    const float tt[4] = {t0, t1, t2, t3};
+    const uint32_t pp[4] = {p0, p1, p2, p3};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (tt[i] < INFINITY) {
+        if (first) {
+          tv.ref = pp[i] >> 3;
+          tv.cnt = pp[i] & 7u;
+          first = false;
+        } else {
+          stack[tv.sp++] = make_uint2(pp[i], 0u);
+        }
+      }
+    }
+    return true;
+  }
+  // sorting network of four (missed children, at +inf, end up last)
+  cswap(t0, p0, t1, p1);
+  cswap(t2, p2, t3, p3);
+  cswap(t0, p0, t2, p2);
+  cswap(t1, p1, t3, p3);
+  cswap(t1, p1, t2, p2);
+  if (tv.sp + nh - 1 > kStack) {
+    atomicOr(status, ST_STACK);
+    tv.sp = 0;
+    return false;
+  }
+  // entries 1 .. nh-1 go to stack[sp + nh - 1 - j] (entry 1 on top)
+  const int top = tv.sp + nh - 2;
+  if (nh > 1) stack[top] = make_uint2(p1, __float_as_uint(t1));
+  if (nh > 2) stack[top - 1] = make_uint2(p2, __float_as_uint(t2));
+  if (nh > 3) stack[top - 2] = make_uint2(p3, __float_as_uint(t3));
+  tv.sp += nh - 1;
+  tv.ref = p0 >> 3;
+  tv.cnt = p0 & 7u;
+  return true;
+}
+
+template <bool W4, bool FMA, bool COUNT, bool ANY = false>
+__device__ __forceinline__ bool interior_w(Trav& tv, uint2* stack, const DevScene& S, float tmax, uint32_t* status,
+                                           uint32_t& n_nodes) {
+  return W4 ? trav_interior4<FMA, COUNT, ANY>(tv, stack, S, tmax, status, n_nodes)
+            : trav_interior<FMA, COUNT>(tv, stack, S, tmax, status, n_nodes);
+}
+
+// Starts a ray; false if it misses the binary tree's root box.
+template <bool W4, bool FMA>
+__device__ __forceinline__ bool init_w(Trav& tv, const DevScene& S, float3 o, float3 d) {
+  if (W4) {
+    trav_init4<FMA>(tv, o, d);
+    return true;
+  }
+  return trav_init<FMA>(tv, S, o, d);
 }
 
 __device__ __forceinline__ void closest_leaf(Trav& tv, const DevScene& S, uint32_t& n_tris, bool count) {
@@ -242,9 +381,20 @@ __device__ __forceinline__ void closest_hit(const DevScene& S, float3 o, float3 
   Trav tv;
   uint2 stack[kStack];
   uint32_t a = 0, b = 0;
-  if (trav_init<false>(tv, S, o, d))
-    while (!closest_step<false, false, false>(tv, stack, S, trav_cap(S), status, a, b)) {
+  trav_init4<false>(tv, o, d);
+  const uint32_t cap = trav_cap(S);
+  for (;;) {
+    if (++tv.iter > cap) {
+      atomicOr(status, ST_ITER);
+      break;
     }
+    if (tv.cnt == 0u) {
+      if (trav_interior4<false, false>(tv, stack, S, tv.best_t, status, a)) continue;
+    } else {
+      closest_leaf(tv, S, b, false);
+    }
+    if (!trav_pop(tv, stack, tv.best_t)) break;
+  }
   best_t = tv.best_t;
   best_leaf = tv.best_leaf;
 }
@@ -256,9 +406,20 @@ __device__ __forceinline__ float shadow_T(const DevScene& S, const DevSpectra& P
   uint32_t a = 0, b = 0;
   float T = 1.0f;
   uint32_t ng = 0;
-  if (trav_init<false>(tv, S, o, d))
-    while (!shadow_step<false, false, false>(tv, stack, S, P, d, band, T, ng, trav_cap(S), status, a, b)) {
+  trav_init4<false>(tv, o, d);
+  const uint32_t cap = trav_cap(S);
+  for (;;) {
+    if (++tv.iter > cap) {
+      atomicOr(status, ST_ITER);
+      break;
     }
+    if (tv.cnt == 0u) {
+      if (trav_interior4<false, false>(tv, stack, S, INFINITY, status, a)) continue;
+    } else if (shadow_leaf(tv, S, P, d, band, T, ng, b, false)) {
+      break;
+    }
+    if (!trav_pop(tv, stack, INFINITY)) break;
+  }
   n_glass = ng;
   return T;
 }
@@ -294,6 +455,16 @@ __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams,
 }
 
 constexpr uint32_t kNoRay = 0xFFFFFFFFu;
+// sun-ray kernel: at least 4 blocks of 256 threads per SM (<= 64 registers)
+#ifndef SRT_SHADOW_MIN_BLOCKS
+#define SRT_SHADOW_MIN_BLOCKS 4
+#endif
+constexpr int kShadowMinBlocks = SRT_SHADOW_MIN_BLOCKS;
+#ifndef SRT_SHADOW_SORTED
+constexpr bool kShadowAnyOrder = true;
+#else
+constexpr bool kShadowAnyOrder = false;
+#endif
 
 // Persistent traversal loop: a warp refills its idle lanes from the queue
 // once at least `refill` lanes are idle, and each lane with a ray runs up to
@@ -301,10 +472,12 @@ constexpr uint32_t kNoRay = 0xFFFFFFFFu;
 // give one batch of 32 rays per warp at a time).
 
 // MODE 0: each lane runs up to `steps` node-or-leaf steps; 1: while-while
-// steps; 2 (the default loop, render option trace_variant 0): warp-synchronous phases - interior steps for the lanes at an
+// steps; 2: warp-synchronous phases - interior steps for the lanes at an
 // interior node until at least `leaf_min` lanes wait at a leaf (or none can
 // go on), then one leaf step for every waiting lane, so that the costly
-// triangle tests run with most of their lanes busy.
+// triangle tests run with most of their lanes busy; 3 (the default, render
+// option trace_variant 0): as 2 over the four-wide BVH.  Modes 0-2 traverse
+// the binary BVH.
 template <bool FMA, bool COUNT, int MODE>
 __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
@@ -331,7 +504,7 @@ __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restr
         const uint32_t slot = base + __popc(idle & lt);
         if (slot < count) {
           const float4 a = __ldcs(q + 2 * slot), b = __ldcs(q + 2 * slot + 1);
-          if (trav_init<FMA>(tv, S, f3(a), f3(b))) {
+          if (init_w<MODE == 3, FMA>(tv, S, f3(a), f3(b))) {
             ray = slot;
           } else {
             __stcs(hit + slot, make_float2(-1.0f, __int_as_float(-1)));
@@ -343,7 +516,7 @@ __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restr
       if (drained) break;
       continue;
     }
-    if (MODE == 2) {
+    if (MODE >= 2) {
       bool done = false;
       for (int i = 0; i < steps; ++i) {
         const bool act = ray != kNoRay && !done;
@@ -359,7 +532,7 @@ __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restr
           } else if (leaf_phase) {
             closest_leaf(tv, S, nt, COUNT);
             done = !trav_pop(tv, stack, tv.best_t);
-          } else if (!trav_interior<FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)) {
+          } else if (!interior_w<MODE == 3, FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)) {
             done = !trav_pop(tv, stack, tv.best_t);
           }
         }
@@ -553,7 +726,7 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
 }
 
 template <bool RECORD, bool COUNT, int MODE>
-__global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+__global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
@@ -591,7 +764,7 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WavePa
           band = w.band_first + path_id(w, bits & kPidMask).j;
           T = 1.0f;
           ng = 0;
-          if (!trav_init<true>(tv, S, f3(a), dir)) tv.sp = -1;  // misses everything: finished
+          if (!init_w<MODE == 3, true>(tv, S, f3(a), dir)) tv.sp = -1;  // misses everything: finished
         }
       }
     }
@@ -600,7 +773,7 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WavePa
       continue;
     }
     bool done = false;
-    if (MODE == 2) {
+    if (MODE >= 2) {
       done = ray != kNoRay && tv.sp < 0;
       for (int i = 0; i < steps; ++i) {
         const bool act = ray != kNoRay && !done;
@@ -615,7 +788,7 @@ __global__ void __launch_bounds__(256) k_shadow(DevScene S, DevSpectra P, WavePa
             done = true;
           } else if (leaf_phase) {
             done = shadow_leaf(tv, S, P, dir, band, T, ng, nt, COUNT) || !trav_pop(tv, stack, INFINITY);
-          } else if (!trav_interior<true, COUNT>(tv, stack, S, INFINITY, status, nn)) {
+          } else if (!interior_w<MODE == 3, true, COUNT, kShadowAnyOrder>(tv, stack, S, INFINITY, status, nn)) {
             done = !trav_pop(tv, stack, INFINITY);
           }
         }
@@ -725,9 +898,10 @@ void trace_t(const LaunchCfg& lc, const DevScene& S, const float4* qin, const Wa
 template <bool FMA, bool COUNT>
 void trace_m(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
              cudaStream_t st) {
-  if (lc.variant == 2) trace_t<FMA, COUNT, 0>(lc, S, qin, b, k, st);
+  if (lc.variant == 3) trace_t<FMA, COUNT, 2>(lc, S, qin, b, k, st);
+  else if (lc.variant == 2) trace_t<FMA, COUNT, 0>(lc, S, qin, b, k, st);
   else if (lc.variant == 1) trace_t<FMA, COUNT, 1>(lc, S, qin, b, k, st);
-  else trace_t<FMA, COUNT, 2>(lc, S, qin, b, k, st);
+  else trace_t<FMA, COUNT, 3>(lc, S, qin, b, k, st);
 }
 
 void launch_trace(const LaunchCfg& lc, bool robust, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
@@ -753,9 +927,10 @@ void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const
 template <bool RECORD, bool COUNT>
 void shadow_m(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
               const WaveBufs& b, double* accum, const Probe& probe, float* Lf, const GuideWave& gw, cudaStream_t st) {
-  if (lc.variant == 2) shadow_t<RECORD, COUNT, 0>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  if (lc.variant == 3) shadow_t<RECORD, COUNT, 2>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  else if (lc.variant == 2) shadow_t<RECORD, COUNT, 0>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   else if (lc.variant == 1) shadow_t<RECORD, COUNT, 1>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
-  else shadow_t<RECORD, COUNT, 2>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  else shadow_t<RECORD, COUNT, 3>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
 }
 
 void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
@@ -849,8 +1024,8 @@ void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaS
 
 int trace_blocks_per_sm(int block) {
   int a = 0, b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<true, false, false>, block, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false, false, false>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<true, false, 3>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false, false, 3>, block, 0);
   const int m = a < b ? a : b;
   return m > 0 ? m : 1;
 }
