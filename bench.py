@@ -51,10 +51,11 @@ def parse():
     ap.add_argument("--mse-train-spp", type=int, default=32)
     ap.add_argument("--guide-depth", type=int, default=2)
     ap.add_argument("--guide-collect", type=int, default=4)
-    ap.add_argument("--guide-steps", type=int, default=8)
+    ap.add_argument("--guide-steps", type=int, default=32)
     ap.add_argument("--mis-alpha", type=float, default=0.7)
     ap.add_argument("--mse-configs", default="",
-                    help="extra guide settings depth:collect:steps:alpha separated by ';' (one shared reference)")
+                    help="extra guide settings depth:collect:steps:alpha[:train_spp[:order]] separated by ';' "
+                         "(one shared reference; order 1 = queue order of the guide queries)")
     return ap.parse_args()
 
 
@@ -218,12 +219,13 @@ def run_guided_mse(args):
     q_xyz = q_out["xyz"].cpu().numpy().astype(np.float64)
     t_per_spp = t_q / args.mse_spp
 
-    settings = [(args.guide_depth, args.guide_collect, args.guide_steps, args.mis_alpha, args.mse_train_spp)]
+    settings = [(args.guide_depth, args.guide_collect, args.guide_steps, args.mis_alpha, args.mse_train_spp, 0)]
     for item in filter(None, args.mse_configs.split(";")):
         f = item.split(":")
-        settings.append((int(f[0]), int(f[1]), int(f[2]), float(f[3]), int(f[4]) if len(f) > 4 else args.mse_train_spp))
+        settings.append((int(f[0]), int(f[1]), int(f[2]), float(f[3]), int(f[4]) if len(f) > 4 else args.mse_train_spp,
+                         int(f[5]) if len(f) > 5 else 0))
     results = []
-    for depth_g, collect, steps, alpha, train_spp in settings:
+    for depth_g, collect, steps, alpha, train_spp, order in settings:
         # guided: online training over the first passes, then frozen
         R.guide_init(seed=11, guide_depth=depth_g, mis_alpha=alpha)
         g_sp = torch.zeros((P, B), dtype=torch.float64, device=dev)
@@ -234,12 +236,14 @@ def run_guided_mse(args):
             out = None
             for s_ in range(n_train):
                 out = R.render(wl.cameras, 1, wl.depth, 0, out_spectral=g_sp, sample_first=s_, accumulate=s_ > 0,
-                               spp_total=args.mse_spp, guided=True, guide_collect=collect, guide_train_steps=steps)
+                               spp_total=args.mse_spp, guided=True, guide_collect=collect, guide_train_steps=steps,
+                               guide_order=order)
                 for i_, v_ in enumerate(out["stats"]["ms_stage"]):
                     stage[i_] += v_
             if args.mse_spp > n_train:
                 out = R.render(wl.cameras, args.mse_spp - n_train, wl.depth, 0, out_spectral=g_sp,
-                               sample_first=n_train, accumulate=n_train > 0, spp_total=args.mse_spp, guided=True)
+                               sample_first=n_train, accumulate=n_train > 0, spp_total=args.mse_spp, guided=True,
+                               guide_order=order)
                 for i_, v_ in enumerate(out["stats"]["ms_stage"]):
                     stage[i_] += v_
             return out
@@ -255,6 +259,7 @@ def run_guided_mse(args):
         p_xyz = p_out["xyz"].cpu().numpy().astype(np.float64)
         results.append({
             "guide_depth": depth_g, "guide_collect": collect, "guide_steps_per_wave": steps, "mis_alpha": alpha,
+            "guide_order": "queue" if order else "spatial",
             "train_spp": n_train,
             "stage_ms": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
                                  [round(v_, 1) for v_ in stage])),

@@ -113,7 +113,8 @@ typedef struct {
   uint32_t accumulate;
   uint32_t spp_total;
   uint32_t leaf_batch;     /* trace_variant 0: 1..32 waiting lanes start a leaf phase; 0 = default */
-  uint32_t reserved[1];
+  uint32_t guide_order;    /* guided: 0 = guide queries sorted by position (Morton order of a 64^3
+                            * grid) before the network runs, 1 = queue order */
 } rt_render_opts;
 
 typedef struct {

@@ -76,6 +76,9 @@ struct rt_ctx {
     // guided rendering buffers
     float4* gq = nullptr;
     float* wesc = nullptr;
+    uint32_t* perm = nullptr;
+    uint32_t* skey = nullptr;
+    uint32_t* bins = nullptr;
     uint32_t gq_cap = 0;
     float4* raw = nullptr;
     float* Lfinal = nullptr;
@@ -291,6 +294,9 @@ void rt_destroy(rt_ctx* c) {
   dfree(c->guide.scratch);
   dfree(c->guide.gq);
   dfree(c->guide.wesc);
+  dfree(c->guide.perm);
+  dfree(c->guide.skey);
+  dfree(c->guide.bins);
   dfree(c->guide.raw);
   dfree(c->guide.Lfinal);
   dfree(c->guide.trec);
@@ -529,6 +535,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
   if (o.trace_variant > 3) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
   if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");
+  if (o.guide_order > 1) return fail(c, RT_ERR_ARG, "rt_render: guide_order is 0 or 1");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if (o.guided && !c->guide.init) return fail(c, RT_ERR_STATE, "rt_render: guided rendering needs rt_guide_init");
   if (o.guide_train_steps && !(o.guided && o.guide_collect))
@@ -644,13 +651,24 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     if (G.gq_cap < cap) {
       dfree(G.gq);
       dfree(G.wesc);
+      dfree(G.perm);
+      dfree(G.skey);
       G.gq_cap = 0;
       CUDA_TRY(c, cudaMalloc(&G.gq, (size_t)cap * 3 * sizeof(float4)));
       CUDA_TRY(c, cudaMalloc(&G.wesc, (size_t)cap * sizeof(float)));
+      CUDA_TRY(c, cudaMalloc(&G.perm, (size_t)cap * sizeof(uint32_t)));
+      CUDA_TRY(c, cudaMalloc(&G.skey, (size_t)cap * sizeof(uint32_t)));
       G.gq_cap = cap;
     }
+    // bins, then the chunk totals of the scan
+    if (!G.bins) CUDA_TRY(c, cudaMalloc(&G.bins, (size_t)(kGuideSortBins + kGuideSortBins / 1024u) * sizeof(uint32_t)));
     gw.gq = G.gq;
     gw.wesc = G.wesc;
+    if (o.guide_order == 0) {
+      gw.perm = G.perm;
+      gw.skey = G.skey;
+      gw.bins = G.bins;
+    }
     if (o.guide_collect) {
       gw.collect = o.guide_collect;
       gw.slots_per_vertex = (cap + o.guide_collect - 1) / o.guide_collect;
@@ -751,7 +769,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
                   o.sample_first, o.accumulate, o.spp_total, o.xyz_mode, (void*)accum, (void*)xyz_dev,
                   (void*)c->d_nodes, (void*)c->d_mb, lc.grid_trace, lc.block_trace, lc.variant, lc.trace_steps,
                   lc.trace_refill, lc.shadow_steps, lc.shadow_refill, (int)cap, o.guided, gw.depth, gw.collect,
-                  o.wave_capacity, (double)gw.alpha, lc.leaf_min);
+                  o.wave_capacity, (double)gw.alpha, lc.leaf_min * 2 + (int)o.guide_order);
     std::string key(kb);
     char pb[160];
     std::snprintf(pb, sizeof(pb), "|%p|%p|%p|%p|%p", (void*)c->wb.q[0], (void*)c->wb.sq, (void*)gw.gq,

@@ -817,10 +817,11 @@ __global__ void __launch_bounds__(kSampleThreads, kSampleCtasPerSm)
   const float inv_pi = 0.31830988618379067f;
   const float p_cone = 1.0f / (2.0f * 3.14159265358979323846f * P.one_minus_cos);
   for (uint64_t tile = blockIdx.x; tile < ntiles && sy.ok; tile += gridDim.x) {
-    const uint32_t i = (uint32_t)(tile * kRows) + r;
-    const bool valid = i < count;
+    const uint32_t jq = (uint32_t)(tile * kRows) + r;
+    const bool valid = jq < count;
     float4 q0 = make_float4(0, 0, 0, 0), q1 = make_float4(0, 0, 1, 0), q2 = make_float4(0, 0, 0, 0);
     if (valid) {
+      const uint32_t i = gw.perm ? __ldg(gw.perm + jq) : jq;
       q0 = __ldg(gw.gq + 3 * i);
       q1 = __ldg(gw.gq + 3 * i + 1);
       q2 = __ldg(gw.gq + 3 * i + 2);
@@ -1023,6 +1024,90 @@ __global__ void __launch_bounds__(kSampleThreads, kSampleCtasPerSm)
   if (warp == 0) tc_tmem_dealloc(tmem, 64);
 }
 
+// ---------------------------------------------------------------------------
+// spatial order of a wave's guide queries (counting sort on a 64^3 Morton
+// grid): queries of one 128-query tile then lie in one or a few cells, so
+// their hash-grid gathers share cache lines at all but the finest levels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  // bits b0..b5 -> positions 0, 3, 6, .., 15
+  uint32_t r = 0;
+#pragma unroll
+  for (uint32_t b = 0; b < kGuideSortBits; ++b) r |= ((v >> b) & 1u) << (3u * b);
+  return r;
+}
+
+__global__ void k_gsort_hist(GuideDev g, GuideWave gw, const Counters* __restrict__ cnt, uint32_t k, uint32_t cap) {
+  const uint32_t count = min(cnt[k].g_count, cap);
+  const float cells = (float)(1u << kGuideSortBits);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const float4 q0 = __ldg(gw.gq + 3 * i);
+    float u[3];
+    unit_pos(g, f3(q0), u);
+    uint32_t c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = min((uint32_t)(u[a] * cells), (1u << kGuideSortBits) - 1u);
+    const uint32_t key = spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+    gw.skey[i] = key;
+    atomicAdd(gw.bins + key, 1u);
+  }
+}
+
+// Exclusive prefix sum of the bins: each block of 1024 threads scans one
+// chunk of 1024 bins in place and writes the chunk total; the chunk totals
+// (kGuideSortBins / 1024 of them) are then scanned by one block, and the
+// scatter adds the chunk's offset.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t& total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (uint32_t o = 1; o < 32u; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31u) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+    for (uint32_t o = 1; o < 32u; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) warp_sums[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  total = warp_sums[nw - 1];
+  const uint32_t before = warp == 0 ? 0u : warp_sums[warp - 1];
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_gsort_scan_chunks(uint32_t* __restrict__ bins, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t ws[32];
+  const uint32_t i = blockIdx.x * 1024u + threadIdx.x;
+  uint32_t tot;
+  const uint32_t ex = block_exclusive_scan(bins[i], ws, tot);
+  bins[i] = ex;
+  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kGuideSortBins / 1024u) k_gsort_scan_totals(uint32_t* __restrict__ totals) {
+  __shared__ uint32_t ws[32];
+  uint32_t tot;
+  const uint32_t ex = block_exclusive_scan(totals[threadIdx.x], ws, tot);
+  __syncthreads();
+  totals[threadIdx.x] = ex;
+}
+
+__global__ void k_gsort_scatter(GuideWave gw, const Counters* __restrict__ cnt, uint32_t k, uint32_t cap) {
+  const uint32_t count = min(cnt[k].g_count, cap);
+  const uint32_t* totals = gw.bins + kGuideSortBins;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint32_t key = gw.skey[i];
+    gw.perm[__ldg(totals + (key >> 10)) + atomicAdd(gw.bins + key, 1u)] = i;
+  }
+}
+
 // Training records from the wave's slots, two per slot: the continuation,
 // with incident radiance L_in = (final radiance - radiance before the next
 // vertex) / throughput after the vertex and weight L_in cos / MIS pdf; and
@@ -1112,6 +1197,13 @@ void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float
 void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& P, const WaveParams& w, uint32_t k,
                          const GuideWave& gw, const WaveBufs& b, double* accum, const Probe& probe, bool record,
                          int sms, cudaStream_t st) {
+  if (gw.perm) {
+    cudaMemsetAsync(gw.bins, 0, kGuideSortBins * sizeof(uint32_t), st);
+    k_gsort_hist<<<sms * 8, 256, 0, st>>>(g, gw, b.cnt, k, b.cap);
+    k_gsort_scan_chunks<<<kGuideSortBins / 1024u, 1024, 0, st>>>(gw.bins, gw.bins + kGuideSortBins);
+    k_gsort_scan_totals<<<1, kGuideSortBins / 1024u, 0, st>>>(gw.bins + kGuideSortBins);
+    k_gsort_scatter<<<sms * 8, 256, 0, st>>>(gw, b.cnt, k, b.cap);
+  }
   cudaFuncSetAttribute(k_guide_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
   k_guide_sample<<<sms * kSampleCtasPerSm, kSampleThreads, kSampleSmem, st>>>(g, (const uint4*)pack, P, w, k, gw, b.q[(k + 1) & 1], b.sq, b.L,
                                                       b.sig, b.cnt, b.cap, accum, probe, record, b.status);

@@ -104,7 +104,16 @@ struct GuideWave {
   uint32_t slots_per_vertex;
   float4* raw;
   float* Lfinal;  // final radiance per path id (collect != 0)
+  // spatial order of the queries (null: queue order): perm[j] = query index
+  // of the j-th query in Morton order of a 64^3 grid over the scene box;
+  // skey[i] = cell of query i; bins = per-cell counts, then cursors within
+  // chunks of 1024 cells, followed by the chunks' offsets
+  uint32_t* perm;
+  uint32_t* skey;
+  uint32_t* bins;
 };
+constexpr uint32_t kGuideSortBits = 6;  // cells per axis = 2^6
+constexpr uint32_t kGuideSortBins = 1u << (3 * kGuideSortBits);
 
 // Per-wave device counters, one row per vertex k (0 .. depth).
 struct Counters {

@@ -49,6 +49,18 @@ def test_guided_is_unbiased(R, trained):
     assert not np.array_equal(guided, plain)
 
 
+def test_query_order_changes_nothing(R):
+    """With a frozen guide every query is evaluated on its own (one MMA row,
+    its own Philox counters), so sorting the queries by position before the
+    network runs changes no bit of the image."""
+    wl = scenes.nave(width=96, height=64, n_bands=9, spp=2, depth=4)
+    R.load(wl)
+    R.guide_init(seed=3, log2_table=16)
+    a = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, guided=True, xyz=False)["spectral"].cpu().numpy()
+    b = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, guided=True, xyz=False, guide_order=1)["spectral"].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
 def test_training_in_render_changes_guide(R):
     wl = scenes.nave(width=96, height=64, n_bands=9, spp=2, depth=4)
     R.load(wl)
