@@ -125,6 +125,8 @@ rt_status ensure_wave(rt_ctx* c, uint32_t cap) {
   dfree(b.sq);
   dfree(b.L);
   dfree(b.sig);
+  dfree(b.rperm);
+  dfree(b.rkey);
   c->wave_alloc = 0;
   CUDA_TRY(c, cudaMalloc(&b.q[0], (size_t)cap * 2 * sizeof(float4)));
   CUDA_TRY(c, cudaMalloc(&b.q[1], (size_t)cap * 2 * sizeof(float4)));
@@ -132,6 +134,10 @@ rt_status ensure_wave(rt_ctx* c, uint32_t cap) {
   CUDA_TRY(c, cudaMalloc(&b.sq, (size_t)cap * 2 * sizeof(float4)));
   CUDA_TRY(c, cudaMalloc(&b.L, (size_t)cap * sizeof(float)));
   CUDA_TRY(c, cudaMalloc(&b.sig, (size_t)cap * sizeof(uint32_t)));
+  CUDA_TRY(c, cudaMalloc(&b.rperm, (size_t)cap * sizeof(uint32_t)));
+  CUDA_TRY(c, cudaMalloc(&b.rkey, (size_t)cap * sizeof(uint32_t)));
+  if (!b.rbins)
+    CUDA_TRY(c, cudaMalloc(&b.rbins, (size_t)(kCellSortBins + kCellSortBins / 1024u) * sizeof(uint32_t)));
   b.cap = cap;
   c->wave_alloc = cap;
   return RT_OK;
@@ -145,6 +151,11 @@ DevScene dev_scene(const rt_ctx* c) {
   S.nrm = c->d_nrm;
   S.n_nodes = c->n_nodes;
   S.n_nodes4 = c->n_nodes4;
+  for (int a = 0; a < 3; ++a) {
+    S.blo[a] = c->lo[a];
+    const float ext = c->hi[a] - c->lo[a];
+    S.binv[a] = ext > 0.0f ? 1.0f / ext : 0.0f;
+  }
   S.n_tris = c->n_tris;
   S.eps = c->eps;
   return S;
@@ -277,6 +288,9 @@ void rt_destroy(rt_ctx* c) {
   dfree(b.sq);
   dfree(b.L);
   dfree(b.sig);
+  dfree(b.rperm);
+  dfree(b.rkey);
+  dfree(b.rbins);
   dfree(b.cnt);
   dfree(b.tot);
   dfree(b.status);
@@ -536,6 +550,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.trace_variant > 3) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
   if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");
   if (o.guide_order > 1) return fail(c, RT_ERR_ARG, "rt_render: guide_order is 0 or 1");
+  if (o.ray_order > 1) return fail(c, RT_ERR_ARG, "rt_render: ray_order is 0 or 1");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if (o.guided && !c->guide.init) return fail(c, RT_ERR_STATE, "rt_render: guided rendering needs rt_guide_init");
   if (o.guide_train_steps && !(o.guided && o.guide_collect))
@@ -623,6 +638,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   lc.record = o.probe_map_dev != nullptr;
   lc.variant = (int)o.trace_variant;
   lc.leaf_min = o.leaf_batch ? (int)o.leaf_batch : kDefaultLeafBatch;
+  lc.sort_rays = o.ray_order == 1;
   lc.trace_steps = o.trace_steps ? (int)o.trace_steps : kDefaultTraceSteps;
   lc.trace_refill = o.trace_refill ? (int)o.trace_refill : kDefaultTraceRefill;
   lc.shadow_steps = o.shadow_steps ? (int)o.shadow_steps : kDefaultShadowSteps;
@@ -769,7 +785,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
                   o.sample_first, o.accumulate, o.spp_total, o.xyz_mode, (void*)accum, (void*)xyz_dev,
                   (void*)c->d_nodes, (void*)c->d_mb, lc.grid_trace, lc.block_trace, lc.variant, lc.trace_steps,
                   lc.trace_refill, lc.shadow_steps, lc.shadow_refill, (int)cap, o.guided, gw.depth, gw.collect,
-                  o.wave_capacity, (double)gw.alpha, lc.leaf_min * 2 + (int)o.guide_order);
+                  o.wave_capacity, (double)gw.alpha, lc.leaf_min * 4 + (int)o.guide_order * 2 + (int)o.ray_order);
     std::string key(kb);
     char pb[160];
     std::snprintf(pb, sizeof(pb), "|%p|%p|%p|%p|%p", (void*)c->wb.q[0], (void*)c->wb.sq, (void*)gw.gq,

@@ -1053,52 +1053,6 @@ __global__ void k_gsort_hist(GuideDev g, GuideWave gw, const Counters* __restric
   }
 }
 
-// Exclusive prefix sum of the bins: each block of 1024 threads scans one
-// chunk of 1024 bins in place and writes the chunk total; the chunk totals
-// (kGuideSortBins / 1024 of them) are then scanned by one block, and the
-// scatter adds the chunk's offset.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t& total) {
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (uint32_t o = 1; o < 32u; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31u) warp_sums[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < nw ? warp_sums[lane] : 0u;
-#pragma unroll
-    for (uint32_t o = 1; o < 32u; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < nw) warp_sums[lane] = w;  // inclusive over warps
-  }
-  __syncthreads();
-  total = warp_sums[nw - 1];
-  const uint32_t before = warp == 0 ? 0u : warp_sums[warp - 1];
-  return before + x - v;
-}
-
-__global__ void __launch_bounds__(1024) k_gsort_scan_chunks(uint32_t* __restrict__ bins, uint32_t* __restrict__ totals) {
-  __shared__ uint32_t ws[32];
-  const uint32_t i = blockIdx.x * 1024u + threadIdx.x;
-  uint32_t tot;
-  const uint32_t ex = block_exclusive_scan(bins[i], ws, tot);
-  bins[i] = ex;
-  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kGuideSortBins / 1024u) k_gsort_scan_totals(uint32_t* __restrict__ totals) {
-  __shared__ uint32_t ws[32];
-  uint32_t tot;
-  const uint32_t ex = block_exclusive_scan(totals[threadIdx.x], ws, tot);
-  __syncthreads();
-  totals[threadIdx.x] = ex;
-}
-
 __global__ void k_gsort_scatter(GuideWave gw, const Counters* __restrict__ cnt, uint32_t k, uint32_t cap) {
   const uint32_t count = min(cnt[k].g_count, cap);
   const uint32_t* totals = gw.bins + kGuideSortBins;
@@ -1200,8 +1154,7 @@ void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& 
   if (gw.perm) {
     cudaMemsetAsync(gw.bins, 0, kGuideSortBins * sizeof(uint32_t), st);
     k_gsort_hist<<<sms * 8, 256, 0, st>>>(g, gw, b.cnt, k, b.cap);
-    k_gsort_scan_chunks<<<kGuideSortBins / 1024u, 1024, 0, st>>>(gw.bins, gw.bins + kGuideSortBins);
-    k_gsort_scan_totals<<<1, kGuideSortBins / 1024u, 0, st>>>(gw.bins + kGuideSortBins);
+    launch_cell_scan(gw.bins, st);
     k_gsort_scatter<<<sms * 8, 256, 0, st>>>(gw, b.cnt, k, b.cap);
   }
   cudaFuncSetAttribute(k_guide_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);

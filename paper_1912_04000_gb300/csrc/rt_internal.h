@@ -39,6 +39,7 @@ struct DevScene {
   uint32_t n_nodes;
   uint32_t n_nodes4;
   uint32_t n_tris;
+  float blo[3], binv[3];  // scene box: lower corner and 1 / extent per axis
   float eps;  // origin offset along the normal: 1e-4 x scene diagonal
 };
 
@@ -114,6 +115,10 @@ struct GuideWave {
 };
 constexpr uint32_t kGuideSortBits = 6;  // cells per axis = 2^6
 constexpr uint32_t kGuideSortBins = 1u << (3 * kGuideSortBits);
+constexpr uint32_t kCellSortBins = kGuideSortBins;  // 2^18 keys for every cell sort
+// Exclusive scan of kCellSortBins counts in place, chunk offsets after them
+// (rt_kernels.cu).
+void launch_cell_scan(uint32_t* bins, cudaStream_t st);
 
 // Per-wave device counters, one row per vertex k (0 .. depth).
 struct Counters {
@@ -149,6 +154,12 @@ struct WaveBufs {
   Totals* tot;
   uint32_t* status;
   uint32_t cap;
+  // spatial order of the ray queues (null: queue order): rperm[j] = queue
+  // slot of the j-th ray in cell order; rkey = cell per slot; rbins as the
+  // guide-query bins (kCellSortBins counts, then kCellSortBins / 1024 offsets)
+  uint32_t* rperm;
+  uint32_t* rkey;
+  uint32_t* rbins;
 };
 
 constexpr int kMaxDepth = 64;
@@ -172,6 +183,7 @@ struct LaunchCfg {
   bool record;
   int variant;  // traversal: 0 = four-wide, leaf batching; binary: 1 = while-while, 2 = node-or-leaf steps,
                 // 3 = leaf batching
+  bool sort_rays;  // reorder the vertex >= 2 and sun-ray queues by cell (needs b.rperm)
   int leaf_min;  // variant 2: lanes waiting at a leaf that start a leaf phase
   int trace_steps, trace_refill;    // closest hit: steps between refill checks, refill threshold
   int shadow_steps, shadow_refill;  // sun rays: the same

@@ -424,6 +424,106 @@ __device__ __forceinline__ float shadow_T(const DevScene& S, const DevSpectra& P
   return T;
 }
 
+// Exclusive prefix sum of the bins: each block of 1024 threads scans one
+// chunk of 1024 bins in place and writes the chunk total; the chunk totals
+// (kCellSortBins / 1024 of them) are then scanned by one block, and the
+// scatter adds the chunk's offset.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t& total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (uint32_t o = 1; o < 32u; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31u) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+    for (uint32_t o = 1; o < 32u; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) warp_sums[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  total = warp_sums[nw - 1];
+  const uint32_t before = warp == 0 ? 0u : warp_sums[warp - 1];
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_cell_scan_chunks(uint32_t* __restrict__ bins, uint32_t* __restrict__ totals) {
+  __shared__ uint32_t ws[32];
+  const uint32_t i = blockIdx.x * 1024u + threadIdx.x;
+  uint32_t tot;
+  const uint32_t ex = block_exclusive_scan(bins[i], ws, tot);
+  bins[i] = ex;
+  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kCellSortBins / 1024u) k_cell_scan_totals(uint32_t* __restrict__ totals) {
+  __shared__ uint32_t ws[32];
+  uint32_t tot;
+  const uint32_t ex = block_exclusive_scan(totals[threadIdx.x], ws, tot);
+  __syncthreads();
+  totals[threadIdx.x] = ex;
+}
+
+// ---------------------------------------------------------------------------
+// Cell sort of a ray queue (counting sort, 2^18 keys): vertex >= 2 rays by
+// the Morton cell of their origin on a 32^3 grid over the scene box and
+// their direction octant, sun rays (all nearly parallel) by the Morton cell
+// on a 64^3 grid.  Rays of one warp then start close together and share the
+// nodes they fetch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z, uint32_t bits) {
+  uint32_t r = 0;
+  for (uint32_t b = 0; b < bits; ++b)
+    r |= (((x >> b) & 1u) << (3u * b)) | (((y >> b) & 1u) << (3u * b + 1u)) | (((z >> b) & 1u) << (3u * b + 2u));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cell_of(const DevScene& S, float3 o, uint32_t bits) {
+  const float n = (float)(1u << bits);
+  const uint32_t m = (1u << bits) - 1u;
+  const uint32_t x = min((uint32_t)fmaxf((o.x - S.blo[0]) * S.binv[0] * n, 0.0f), m);
+  const uint32_t y = min((uint32_t)fmaxf((o.y - S.blo[1]) * S.binv[1] * n, 0.0f), m);
+  const uint32_t z = min((uint32_t)fmaxf((o.z - S.blo[2]) * S.binv[2] * n, 0.0f), m);
+  return morton3(x, y, z, bits);
+}
+
+template <bool SUN>
+__global__ void k_rsort_hist(DevScene S, const float4* __restrict__ q, const Counters* __restrict__ cnt, uint32_t k,
+                             uint32_t cap, uint32_t* __restrict__ key, uint32_t* __restrict__ bins) {
+  const uint32_t count = min(SUN ? cnt[k].s_count : cnt[k].q_count, cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const float4 a = __ldg(q + 2 * i);
+    uint32_t kk;
+    if (SUN) {
+      kk = cell_of(S, f3(a), 6u);
+    } else {
+      const float4 b = __ldg(q + 2 * i + 1);
+      const uint32_t oct = (b.x < 0.0f ? 1u : 0u) | (b.y < 0.0f ? 2u : 0u) | (b.z < 0.0f ? 4u : 0u);
+      kk = cell_of(S, f3(a), 5u) | (oct << 15);
+    }
+    key[i] = kk;
+    atomicAdd(bins + kk, 1u);
+  }
+}
+
+template <bool SUN>
+__global__ void k_rsort_scatter(const Counters* __restrict__ cnt, uint32_t k, uint32_t cap,
+                                const uint32_t* __restrict__ key, uint32_t* __restrict__ bins,
+                                uint32_t* __restrict__ perm) {
+  const uint32_t count = min(SUN ? cnt[k].s_count : cnt[k].q_count, cap);
+  const uint32_t* totals = bins + kCellSortBins;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint32_t kk = key[i];
+    perm[__ldg(totals + (kk >> 10)) + atomicAdd(bins + kk, 1u)] = i;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -481,7 +581,8 @@ constexpr bool kShadowAnyOrder = false;
 template <bool FMA, bool COUNT, int MODE>
 __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
-                                               uint32_t* status, int steps, int refill, int leaf_min) {
+                                               uint32_t* status, int steps, int refill, int leaf_min,
+                                               const uint32_t* __restrict__ perm) {
   const uint32_t count = min(cnt[k].q_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->ext_rays, (unsigned long long)count);
   const uint32_t lane = threadIdx.x & 31u;
@@ -503,11 +604,12 @@ __global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restr
       if (ray == kNoRay) {
         const uint32_t slot = base + __popc(idle & lt);
         if (slot < count) {
-          const float4 a = __ldcs(q + 2 * slot), b = __ldcs(q + 2 * slot + 1);
+          const uint32_t ri = perm ? __ldg(perm + slot) : slot;
+          const float4 a = __ldcs(q + 2 * ri), b = __ldcs(q + 2 * ri + 1);
           if (init_w<MODE == 3, FMA>(tv, S, f3(a), f3(b))) {
-            ray = slot;
+            ray = ri;
           } else {
-            __stcs(hit + slot, make_float2(-1.0f, __int_as_float(-1)));
+            __stcs(hit + ri, make_float2(-1.0f, __int_as_float(-1)));
           }
         }
       }
@@ -731,7 +833,7 @@ __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, De
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
                                                 uint32_t* status, int steps, int refill, float* Lfinal,
-                                                GuideWave gw, int leaf_min) {
+                                                GuideWave gw, int leaf_min, const uint32_t* __restrict__ perm) {
   const bool rec_sun = gw.on && gw.collect != 0u && k <= gw.depth && k < w.depth;
   const uint32_t count = min(cnt[k].s_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
@@ -756,8 +858,9 @@ __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, De
       if (ray == kNoRay) {
         const uint32_t slot = base + __popc(idle & lt);
         if (slot < count) {
-          const float4 a = __ldcs(sq + 2 * slot), b = __ldcs(sq + 2 * slot + 1);
-          ray = slot;
+          const uint32_t ri = perm ? __ldg(perm + slot) : slot;
+          const float4 a = __ldcs(sq + 2 * ri), b = __ldcs(sq + 2 * ri + 1);
+          ray = ri;
           bits = __float_as_uint(a.w);
           contrib = b.w;
           dir = f3(b);
@@ -891,8 +994,10 @@ int grid_for(uint64_t n, int block) {
 
 template <bool FMA, bool COUNT, int MODE>
 void trace_t(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k, cudaStream_t st) {
+  const uint32_t* perm = (lc.sort_rays && k >= 2 && b.rperm) ? b.rperm : nullptr;
   k_trace<FMA, COUNT, MODE><<<lc.grid_trace, lc.block_trace, 0, st>>>(S, qin, b.hit, b.cnt, k, b.cap, b.tot, b.status,
-                                                                     lc.trace_steps, lc.trace_refill, lc.leaf_min);
+                                                                     lc.trace_steps, lc.trace_refill, lc.leaf_min,
+                                                                     perm);
 }
 
 template <bool FMA, bool COUNT>
@@ -919,9 +1024,10 @@ template <bool RECORD, bool COUNT, int MODE>
 void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
               const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, const GuideWave& gw,
               cudaStream_t st) {
+  const uint32_t* perm = (lc.sort_rays && b.rperm) ? b.rperm : nullptr;
   k_shadow<RECORD, COUNT, MODE><<<lc.grid_trace, lc.block_trace, 0, st>>>(
       S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe, b.tot, b.status, lc.shadow_steps, lc.shadow_refill,
-      Lfinal, gw, lc.leaf_min);
+      Lfinal, gw, lc.leaf_min, perm);
 }
 
 template <bool RECORD, bool COUNT>
@@ -945,7 +1051,22 @@ void launch_shadow(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, 
   }
 }
 
+template <bool SUN>
+void sort_queue(const DevScene& S, const float4* q, const WaveBufs& b, uint32_t k, cudaStream_t st, int sms) {
+  const int g = sms > 0 ? sms * 8 : 1024;
+  cudaMemsetAsync(b.rbins, 0, kCellSortBins * sizeof(uint32_t), st);
+  k_rsort_hist<SUN><<<g, 256, 0, st>>>(S, q, b.cnt, k, b.cap, b.rkey, b.rbins);
+  k_cell_scan_chunks<<<kCellSortBins / 1024u, 1024, 0, st>>>(b.rbins, b.rbins + kCellSortBins);
+  k_cell_scan_totals<<<1, kCellSortBins / 1024u, 0, st>>>(b.rbins + kCellSortBins);
+  k_rsort_scatter<SUN><<<g, 256, 0, st>>>(b.cnt, k, b.cap, b.rkey, b.rbins, b.rperm);
+}
+
 }  // namespace
+
+void launch_cell_scan(uint32_t* bins, cudaStream_t st) {
+  k_cell_scan_chunks<<<kCellSortBins / 1024u, 1024, 0, st>>>(bins, bins + kCellSortBins);
+  k_cell_scan_totals<<<1, kCellSortBins / 1024u, 0, st>>>(bins + kCellSortBins);
+}
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st,
@@ -963,6 +1084,10 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
     const float4* qin = b.q[k & 1];
     float4* qout = b.q[(k + 1) & 1];
     if (tm) tm->begin(STG_TRACE, st);
+    if (lc.sort_rays && k >= 2 && b.rperm) {
+      sort_queue<false>(S, qin, b, k, st, sms);
+      nl += 4;
+    }
     // vertex 1 starts at the cameras, which may lie anywhere: robust box
     // test; later origins are surface points inside the padded bounds
     launch_trace(lc, k == 1, S, qin, b, k, st);
@@ -988,9 +1113,13 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
       if (tm) tm->begin(STG_GUIDE, st);
       launch_guide_sample(*gdev, gpack, P, w, k, gw, b, accum, probe, rec, sms, st);
       if (tm) tm->end(STG_GUIDE, st);
-      ++nl;
+      nl += gw.perm ? 5 : 1;  // with the query sort: histogram, 2 scans, scatter
     }
     if (tm) tm->begin(STG_SHADOW, st);
+    if (lc.sort_rays && b.rperm) {
+      sort_queue<true>(S, b.sq, b, k, st, sms);
+      nl += 4;
+    }
     launch_shadow(lc, S, P, w, k, b, accum, probe, guided ? gw.Lfinal : nullptr, gw, st);
     if (tm) tm->end(STG_SHADOW, st);
     nl += 3;

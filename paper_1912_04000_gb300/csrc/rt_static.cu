@@ -185,6 +185,7 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   lc.record = false;
   lc.variant = 0;
   lc.leaf_min = kDefaultLeafBatch;
+  lc.sort_rays = false;  // the static scratch holds no sort buffers; ray order changes no result
   lc.trace_steps = kDefaultTraceSteps;
   lc.trace_refill = kDefaultTraceRefill;
   lc.shadow_steps = kDefaultShadowSteps;

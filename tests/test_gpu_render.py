@@ -100,6 +100,16 @@ def test_nave_sampled_pixels(R):
         assert_parity(g[clean], o["xyz"][clean], "nave clean pixels")
 
 
+def test_ray_order_changes_nothing(R):
+    """Each path owns its slot and its Philox counters, so tracing the queues
+    in the order of the cell sort or in queue order gives the same bits."""
+    wl = scenes.nave(width=64, height=48, n_bands=8, spp=2)
+    R.load(wl)
+    a = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)["spectral"].cpu().numpy()
+    b = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2, ray_order=1)["spectral"].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
 def test_traversal_loop_variants_agree(R):
     """Loop shape (while-while, leaf batching or one node per step, steps
     between refills, refill threshold, leaf batch) changes only scheduling:
