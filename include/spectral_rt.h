@@ -79,7 +79,8 @@ typedef struct {
 typedef struct {
   uint32_t wave_capacity;  /* paths in flight per wave; 0 = library default (2^23) */
   uint32_t xyz_mode;       /* rt_xyz_mode */
-  uint32_t trace_block;    /* threads per block of the traversal kernels; 0 = 128 */
+  uint32_t trace_block;    /* threads per block of the traversal kernels, a multiple of 32 up to 128;
+                            * 0 = 128 */
   uint32_t ctas_per_sm;    /* persistent CTAs per SM for traversal; 0 = occupancy limit */
   /* optional per-path records for parity checks: probe_map_dev[p] (uint32,
    * one per global pixel) is the probe slot of pixel p or 0xFFFFFFFF; each

@@ -3,8 +3,8 @@
 The tuning itself is native (rt_autotune: coordinate descent over the wave
 capacity, the traversal loop parameters and the traversal block size, timed
 with CUDA events on probe renders).  This module only keys, stores and
-reloads the results: key = GPU name | triangles (rounded to 2 significant
-digits) | pixels (rounded likewise) | bands | depth.
+reloads the results: key = cache version | GPU name | triangles (rounded to 2
+significant digits) | pixels (rounded likewise) | bands | depth.
 """
 from __future__ import annotations
 
@@ -23,8 +23,13 @@ def _round2(x: int) -> int:
     return int(round(x / 10 ** e) * 10 ** e)
 
 
+# Bumped whenever the tuned fields or their valid ranges change, so that
+# entries written by an older library are not reused.
+CACHE_VERSION = 2
+
+
 def workload_key(gpu_name: str, n_tris: int, n_pixels: int, n_bands: int, depth: int) -> str:
-    return f"{gpu_name}|{_round2(n_tris)}|{_round2(n_pixels)}|{n_bands}|{depth}"
+    return f"v{CACHE_VERSION}|{gpu_name}|{_round2(n_tris)}|{_round2(n_pixels)}|{n_bands}|{depth}"
 
 
 def load(path: str = DEFAULT_CACHE) -> dict:

@@ -381,6 +381,7 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     if (!(len > 0.0)) return fail(c, RT_ERR_SCENE, "triangle " + std::to_string(t) + " is degenerate");
     for (int a2 = 0; a2 < 3; ++a2) nrm64[4 * (size_t)t + a2] = (float)(n[a2] / len);
   }
+  if (n_tris >= (1u << 28)) return fail(c, RT_ERR_SCENE, "at most 2^28 triangles");
   BvhOut bvh;
   build_bvh(verts, tris, n_tris, bvh);
   // leaf-ordered triangle and normal records
@@ -429,10 +430,13 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     nd[2 * i + 1] = make_float4(up(b.hi[0]), up(b.hi[1]), up(b.hi[2]), cf);
   }
   // four-wide nodes, padded the same way (empty slots keep their +-inf box)
+  // device layout per node: the six plane float4s, then the children packed
+  // as the traversal stack stores them (ref << 3 | count; 0 for an empty
+  // slot, whose box is never entered), then 16 bytes of padding
   std::vector<Bvh4Node> b4;
   collapse_bvh4(bvh, b4, nullptr);
   for (Bvh4Node& n4 : b4)
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i) {
       if (n4.cnt[i] != kEmpty4) {
         n4.lox[i] = down(n4.lox[i]);
         n4.loy[i] = down(n4.loy[i]);
@@ -440,7 +444,12 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
         n4.hix[i] = up(n4.hix[i]);
         n4.hiy[i] = up(n4.hiy[i]);
         n4.hiz[i] = up(n4.hiz[i]);
+        n4.ref[i] = (n4.ref[i] << 3) | n4.cnt[i];
+      } else {
+        n4.ref[i] = 0;
       }
+      n4.cnt[i] = 0;
+    }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c->d_nodes);
@@ -626,13 +635,13 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     }
     accum = c->d_accum;
   }
-  if (o.trace_block && (o.trace_block > 256 || o.trace_block % 32))
-    return fail(c, RT_ERR_ARG, "rt_render: trace_block must be a multiple of 32 up to 256");
+  if (o.trace_block && (o.trace_block > 128 || o.trace_block % 32))
+    return fail(c, RT_ERR_ARG, "rt_render: trace_block must be a multiple of 32 up to 128");
   LaunchCfg lc;
   lc.block_trace = o.trace_block ? (int)o.trace_block : 128;
   lc.block_shade = 256;
-  const int cps = o.ctas_per_sm ? (int)o.ctas_per_sm : trace_blocks_per_sm(lc.block_trace);
-  lc.grid_trace = c->sms * cps;
+  lc.grid_trace = c->sms * (o.ctas_per_sm ? (int)o.ctas_per_sm : trace_blocks_per_sm(lc.block_trace));
+  lc.grid_shadow = c->sms * (o.ctas_per_sm ? (int)o.ctas_per_sm : shadow_blocks_per_sm(lc.block_trace));
   lc.grid_shade = c->sms * 8;
   lc.counting = c->counting;
   lc.record = o.probe_map_dev != nullptr;
@@ -1199,9 +1208,9 @@ rt_status rt_autotune(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_
   // sun-ray loop, block
   const uint32_t waves[] = {1u << 21, 1u << 22, 1u << 23, 1u << 24};
   const uint32_t leaf[] = {12, 16, 32};
-  const uint32_t tl[][2] = {{16, 8}, {4, 8}, {8, 4}, {8, 16}};
-  const uint32_t sl[][2] = {{16, 12}, {4, 12}, {8, 4}, {8, 24}};
-  const uint32_t blocks[] = {128, 64, 256};
+  const uint32_t tl[][2] = {{8, 8}, {2, 8}, {4, 4}, {4, 16}};
+  const uint32_t sl[][2] = {{8, 12}, {2, 12}, {4, 4}, {4, 24}};
+  const uint32_t blocks[] = {128, 64, 96};
   rt_render_opts o;
   for (uint32_t wv : waves) {
     o = best;

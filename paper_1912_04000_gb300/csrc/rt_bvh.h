@@ -26,7 +26,8 @@ int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out
 // Four-wide node: child boxes in structure-of-arrays order (one float4 per
 // plane), child i an interior node (cnt[i] = 0, ref[i] = node index), a leaf
 // (cnt[i] = 1..4 triangles from leaf position ref[i]) or empty (cnt[i] =
-// kEmpty4, box lo = +inf, hi = -inf, which no slab test enters).
+// kEmpty4, box lo = +inf, hi = -inf, which no slab test enters).  The upload
+// packs ref[i] as ref << 3 | count for the device and zeroes cnt.
 constexpr uint32_t kEmpty4 = 0xFFFFFFFFu;
 struct Bvh4Node {
   float lox[4], hix[4], loy[4], hiy[4], loz[4], hiz[4];

@@ -171,13 +171,14 @@ struct Probe {
 };
 
 // Default traversal loop parameters (set from measurements on a GB300).
-constexpr int kDefaultTraceSteps = 8, kDefaultTraceRefill = 8;
-constexpr int kDefaultShadowSteps = 8, kDefaultShadowRefill = 12;
+constexpr int kDefaultTraceSteps = 4, kDefaultTraceRefill = 8;
+constexpr int kDefaultShadowSteps = 4, kDefaultShadowRefill = 12;
 constexpr int kDefaultLeafBatch = 24;
 
 // Launchers (rt_kernels.cu).
 struct LaunchCfg {
-  int grid_trace, block_trace;
+  int grid_trace, block_trace;  // block_trace also sizes the sun-ray kernel's blocks
+  int grid_shadow;
   int grid_shade, block_shade;
   bool counting;
   bool record;
@@ -223,6 +224,7 @@ void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t*
 
 int num_sms(int device);
 int trace_blocks_per_sm(int block);
+int shadow_blocks_per_sm(int block);
 
 // Learned guide (rt_guide.cu).
 struct GuideDev {

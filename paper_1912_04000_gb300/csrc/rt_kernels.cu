@@ -134,7 +134,7 @@ __device__ __forceinline__ bool trav_pop(Trav& tv, const uint2* stack, float tma
 
 // ---------------------------------------------------------------------------
 // Four-wide BVH (node = 8 float4: lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the
-// four children, then their refs and counts).  Per axis the ray's direction
+// four children, then the children packed as ref << 3 | count, then padding).  Per axis the ray's direction
 // sign picks the entry plane (lo for a positive direction) and the exit
 // plane, so one slab test per child needs no min/max of the plane pair and an
 // empty child slot (lo = +inf, hi = -inf) is never entered.  The box test
@@ -197,15 +197,13 @@ __device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const Dev
   const float4 nx = ldg4(nd + ox), fx = ldg4(nd + (ox ^ 1u));
   const float4 ny = ldg4(nd + 2u + oy), fy = ldg4(nd + 2u + (oy ^ 1u));
   const float4 nz = ldg4(nd + 4u + oz), fz = ldg4(nd + 4u + (oz ^ 1u));
-  const uint4 rf = __ldg((const uint4*)(nd + 6)), ct = __ldg((const uint4*)(nd + 7));
+  const uint4 pk = __ldg((const uint4*)(nd + 6));  // children: ref << 3 | count
   if (COUNT) n_nodes += 4;
   float t0 = child_t<FMA>(tv, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, tmax);
   float t1 = child_t<FMA>(tv, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, tmax);
   float t2 = child_t<FMA>(tv, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, tmax);
   float t3 = child_t<FMA>(tv, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, tmax);
-  // children packed as the stack stores them: ref << 3 | count
-  uint32_t p0 = (rf.x << 3) | (ct.x & 7u), p1 = (rf.y << 3) | (ct.y & 7u);
-  uint32_t p2 = (rf.z << 3) | (ct.z & 7u), p3 = (rf.w << 3) | (ct.w & 7u);
+  uint32_t p0 = pk.x, p1 = pk.y, p2 = pk.z, p3 = pk.w;
   const int nh = (t0 < INFINITY) + (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
   if (nh == 0) return false;
   if (ANY) {
@@ -555,6 +553,9 @@ __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams,
 }
 
 constexpr uint32_t kNoRay = 0xFFFFFFFFu;
+// closest-hit kernel: blocks of at most 128 threads, 9 of them per SM
+// (<= 56 registers, 36 warps)
+constexpr int kTraceMaxThreads = 128, kTraceMinBlocks = 9;
 // sun-ray kernel: at least 4 blocks of 256 threads per SM (<= 64 registers)
 #ifndef SRT_SHADOW_MIN_BLOCKS
 #define SRT_SHADOW_MIN_BLOCKS 4
@@ -579,7 +580,7 @@ constexpr bool kShadowAnyOrder = false;
 // option trace_variant 0): as 2 over the four-wide BVH.  Modes 0-2 traverse
 // the binary BVH.
 template <bool FMA, bool COUNT, int MODE>
-__global__ void __launch_bounds__(256) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
+__global__ void __launch_bounds__(kTraceMaxThreads, kTraceMinBlocks) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
                                                uint32_t* status, int steps, int refill, int leaf_min,
                                                const uint32_t* __restrict__ perm) {
@@ -1025,7 +1026,7 @@ void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const
               const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, const GuideWave& gw,
               cudaStream_t st) {
   const uint32_t* perm = (lc.sort_rays && b.rperm) ? b.rperm : nullptr;
-  k_shadow<RECORD, COUNT, MODE><<<lc.grid_trace, lc.block_trace, 0, st>>>(
+  k_shadow<RECORD, COUNT, MODE><<<lc.grid_shadow, lc.block_trace, 0, st>>>(
       S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe, b.tot, b.status, lc.shadow_steps, lc.shadow_refill,
       Lfinal, gw, lc.leaf_min, perm);
 }
@@ -1152,11 +1153,15 @@ void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaS
 }
 
 int trace_blocks_per_sm(int block) {
-  int a = 0, b = 0;
+  int a = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_trace<true, false, 3>, block, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_shadow<false, false, 3>, block, 0);
-  const int m = a < b ? a : b;
-  return m > 0 ? m : 1;
+  return a > 0 ? a : 1;
+}
+
+int shadow_blocks_per_sm(int block) {
+  int a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_shadow<false, false, 3>, block, 0);
+  return a > 0 ? a : 1;
 }
 
 int num_sms(int device) {

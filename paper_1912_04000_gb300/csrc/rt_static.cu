@@ -180,6 +180,7 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   lc.block_trace = 128;
   lc.block_shade = 256;
   lc.grid_trace = v.sms * trace_blocks_per_sm(lc.block_trace);
+  lc.grid_shadow = v.sms * shadow_blocks_per_sm(lc.block_trace);
   lc.grid_shade = v.sms * 8;
   lc.counting = false;
   lc.record = false;
