@@ -2,7 +2,7 @@
 // sm_100a family: shared-memory operand descriptors in the K-major
 // non-swizzled canonical layout, BF16 MMA with an FP32 accumulator in tensor
 // memory, commit to an mbarrier with a bounded wait, TMEM allocation and
-// 32x32b loads.
+// 32x32b loads, and untiled TMA bulk copies counted on an mbarrier.
 #pragma once
 
 #include <cstdint>
@@ -71,6 +71,21 @@ __device__ __forceinline__ bool tc_mbar_wait(uint64_t* mbar, uint32_t parity, ui
     if (done) return true;
   }
   return false;
+}
+
+// Arrive on the mbarrier (count 1) and add `bytes` to the transaction count
+// that must complete before its phase flips.
+__device__ __forceinline__ void tc_mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// Bulk copy (TMA, untiled) global -> shared of `bytes` (a multiple of 16,
+// both addresses 16-byte aligned); completion is counted on the mbarrier.
+__device__ __forceinline__ void tc_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
 }
 
 // Warp-wide: allocate ncols TMEM columns (power of two >= 32), address to *slot.

@@ -18,7 +18,8 @@ def R():
 
 @pytest.mark.parametrize("n_pix,n_bands,band_first,band_count,spp",
                          [(1000, 16, 0, 16, 4), (3001, 81, 0, 81, 16), (517, 81, 7, 33, 3), (128, 17, 0, 17, 1),
-                          (1, 81, 0, 81, 16), (40000, 81, 0, 81, 16)])
+                          (1, 81, 0, 81, 16), (40000, 81, 0, 81, 16), (1280, 96, 0, 96, 2),
+                          (1300, 150, 0, 150, 2)])
 def test_xyz_modes(R, n_pix, n_bands, band_first, band_count, spp):
     import torch
     wl = scenes.tiny_box(n_bands=n_bands, width=8, height=8)
