@@ -329,6 +329,35 @@ __device__ __forceinline__ void put8(unsigned char* A, uint32_t r, int c0, const
   *(uint4*)(A + (c0 >> 4) * kSliceA + tc_kmajor_off(r, (uint32_t)(c0 & 15))) = q;
 }
 
+// Grid entries of the 8 corners k = dx + 2 dy + 4 dz of the level-l cell c:
+// the index arithmetic of grid_index() with the per-axis terms formed once
+// (identical results: the sums and products wrap modulo 2^32 alike).
+__device__ __forceinline__ void corner_ids(const GuideDev& g, const uint32_t* res, int l, const uint32_t c[3],
+                                           uint32_t T, uint32_t id[8]) {
+  if ((g.dense_mask >> l) & 1u) {
+    const uint32_t r1 = res[l] + 1u, r2 = r1 * r1;
+    const uint32_t base = c[0] + c[1] * r1 + c[2] * r2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) id[k] = base + (uint32_t)(k & 1) + ((k >> 1) & 1 ? r1 : 0u) + ((k >> 2) & 1 ? r2 : 0u);
+  } else {
+    const uint32_t hy0 = c[1] * 2654435761u, hz0 = c[2] * 805459861u;
+    const uint32_t hy1 = hy0 + 2654435761u, hz1 = hz0 + 805459861u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      id[k] = ((c[0] + (uint32_t)(k & 1)) ^ ((k >> 1) & 1 ? hy1 : hy0) ^ ((k >> 2) & 1 ? hz1 : hz0)) & (T - 1u);
+  }
+}
+
+// Trilinear weights of the 8 corners, each (w_x w_y) w_z as in encode().
+__device__ __forceinline__ void corner_weights(const float fr[3], float w[8]) {
+  const float wx[2] = {1.0f - fr[0], fr[0]}, wy[2] = {1.0f - fr[1], fr[1]}, wz[2] = {1.0f - fr[2], fr[2]};
+  float wxy[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) wxy[j] = wx[j & 1] * wy[j >> 1];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = wxy[k & 3] * wz[k >> 2];
+}
+
 // Hash-grid features of levels l0 .. l0 + 7 (the arithmetic of encode());
 // res: the per-level resolutions, staged in shared memory.
 __device__ __forceinline__ void encode_levels8(const GuideDev& g, const uint32_t* res, const float u[3], int l0,
@@ -347,19 +376,17 @@ __device__ __forceinline__ void encode_levels8(const GuideDev& g, const uint32_t
       c[a] = (uint32_t)fl;
       fr[a] = sa - fl;
     }
-    const bool dense = (g.dense_mask >> l) & 1u;
-    const uint32_t r1 = res[l] + 1u;
+    uint32_t id[8];
+    corner_ids(g, res, l, c, T, id);
+    float w[8];
+    corner_weights(fr, w);
     const float2* tab = (const float2*)g.grid + (size_t)l * T;
     float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
-      const float w = (dx ? fr[0] : 1.0f - fr[0]) * (dy ? fr[1] : 1.0f - fr[1]) * (dz ? fr[2] : 1.0f - fr[2]);
-      const uint32_t x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
-      const uint32_t id = dense ? x + y * r1 + z * r1 * r1 : (x * 1u ^ y * 2654435761u ^ z * 805459861u) & (T - 1u);
-      const float2 v = __ldg(tab + id);
-      a0 = fmaf(w, v.x, a0);
-      a1 = fmaf(w, v.y, a1);
+      const float2 v = __ldg(tab + id[k]);
+      a0 = fmaf(w[k], v.x, a0);
+      a1 = fmaf(w[k], v.y, a1);
     }
     f[2 * i] = a0;
     f[2 * i + 1] = a1;
@@ -638,19 +665,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
               c[a] = (uint32_t)fl;
               fr[a] = sa - fl;
             }
-            const bool dense = (g.dense_mask >> l2) & 1u;
-            const uint32_t r1 = sres[l2] + 1u;
+            uint32_t id[8];
+            corner_ids(g, sres, l2, c, T, id);
+            float w[8];
+            corner_weights(fr, w);
             float2* dst = (float2*)dgrid + (size_t)l2 * T;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const uint32_t ddx = k & 1, ddy = (k >> 1) & 1, ddz = (k >> 2) & 1;
-              const float w = (ddx ? fr[0] : 1.0f - fr[0]) * (ddy ? fr[1] : 1.0f - fr[1]) *
-                              (ddz ? fr[2] : 1.0f - fr[2]);
-              const uint32_t x = c[0] + ddx, y = c[1] + ddy, z = c[2] + ddz;
-              const uint32_t id =
-                  dense ? x + y * r1 + z * r1 * r1 : (x * 1u ^ y * 2654435761u ^ z * 805459861u) & (T - 1u);
-              atomicAdd(dst + id, make_float2(w * d0, w * d1));
-            }
+            for (int k = 0; k < 8; ++k) atomicAdd(dst + id[k], make_float2(w[k] * d0, w[k] * d1));
           }
         }
       }
