@@ -3,7 +3,7 @@
 //
 // Method: binned surface-area heuristic over triangle centroids (Wald, "On
 // fast construction of SAH-based bounding volume hierarchies", IEEE RT 2007),
-// 16 bins per axis, leaves of at most 4 triangles.  Past depth 40 the builder
+// 32 bins per axis, leaves of at most 4 triangles.  Past depth 40 the builder
 // switches to median splits so the tree depth, and with it the traversal
 // stack, stays below 64.
 //
@@ -54,7 +54,7 @@ struct Task {
   uint32_t node, begin, end, depth;
 };
 
-constexpr int kBins = 16;
+constexpr int kBins = 32;
 constexpr uint32_t kMaxLeaf = 4;
 constexpr uint32_t kMedianDepth = 40;
 
