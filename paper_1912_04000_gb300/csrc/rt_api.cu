@@ -771,7 +771,6 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     if (xyz_dev) {
       XyzWeights xw;
       xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
-      xw.wsplit = nullptr;
       xw.band_count = band_count;
       xw.kpad = (band_count + 15) / 16 * 16;
       if (tm) tm->begin(STG_XYZ, s);
@@ -956,7 +955,6 @@ rt_status rt_xyz(rt_ctx* c, const double* spectral_dev, uint64_t n_pixels, uint3
   CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), c->stream));
   XyzWeights xw;
   xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
-  xw.wsplit = nullptr;
   xw.band_count = band_count;
   xw.kpad = (band_count + 15) / 16 * 16;
   launch_xyz(spectral_dev, n_pixels, xw, spp, (int)mode, xyz_dev, c->stream, c->wb.status, c->sms);

@@ -205,12 +205,10 @@ void launch_trace_shadow_rays(const DevScene& S, const DevSpectra& P, const floa
 void launch_optics(const float* c, const float* n, const float* k, const float* lam, const float* d,
                    uint64_t count, float* R, float* Rs, float* Ts, cudaStream_t st);
 
-// XYZ contraction (rt_xyz.cu).
-// Weights are prepared on the host per band range: wsplit holds the three
-// BF16 terms of the weights in the layout the tensor-core kernel reads.
+// XYZ contraction (rt_xyz.cu).  The kernels split the FP32 weights into
+// their BF16 operand tiles themselves.
 struct XyzWeights {
   const float* w32;        // [band_count][3] float
-  const uint16_t* wsplit;  // tensor-core B operand tiles (see rt_xyz.cu)
   uint32_t band_count;
   uint32_t kpad;           // band_count rounded up to 16
 };
@@ -219,8 +217,6 @@ struct XyzWeights {
 constexpr uint32_t kXyzMaxBandsTc = 192;
 void launch_xyz(const double* spectral, uint64_t n_pixels, const XyzWeights& w, uint32_t spp, int mode, float* xyz,
                 cudaStream_t st, uint32_t* status, int sms);
-size_t xyz_wsplit_elems(uint32_t band_count);
-void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t* wsplit_host);
 
 int num_sms(int device);
 int trace_blocks_per_sm(int block);

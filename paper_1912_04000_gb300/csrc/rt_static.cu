@@ -212,7 +212,6 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   if (xyz_dev) {
     XyzWeights xw;
     xw.w32 = v.cmfw + 3 * (size_t)band_first;
-    xw.wsplit = nullptr;
     xw.band_count = band_count;
     xw.kpad = (band_count + 15) / 16 * 16;
     launch_xyz(spectral_dev, npix, xw, spp, (int)xyz_mode, xyz_dev, st, b.status, v.sms);

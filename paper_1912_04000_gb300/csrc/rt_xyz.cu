@@ -431,14 +431,6 @@ size_t xyz_tma_smem(uint32_t band_count) {
 
 }  // namespace
 
-size_t xyz_wsplit_elems(uint32_t band_count) { return (size_t)((band_count + 15) / 16 * 16) * 16 * 3; }
-
-void xyz_prepare_weights(const float* cmf_w_rows, uint32_t band_count, uint16_t* wsplit_host) {
-  (void)cmf_w_rows;
-  (void)band_count;
-  (void)wsplit_host;
-}
-
 size_t xyz_tc_smem(uint32_t band_count) {
   const uint32_t nk = (band_count + 15) / 16;
   return 3ull * nk * kATile + 3ull * nk * kBTile + 16;
