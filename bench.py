@@ -301,6 +301,7 @@ def main():
     torch.cuda.set_device(dev)
     wl = scenes.nave()
     R = Renderer(info.local_rank).load(wl)
+    bvh_info = R.scene_info()
     seed = multigpu.rank_seed(wl.seed, info.rank)
     stream = R.stream
     spectral = torch.empty((wl.n_pixels, wl.band_count), dtype=torch.float64, device=dev)
@@ -386,6 +387,8 @@ def main():
                 "l2": "inputs larger than L2: 1.1 GB of wave queues and a 0.5 GB FP64 spectral image per step; "
                       "the 22 MB BVH stays L2-resident by design",
                 "partition": "each rank renders the whole image with its own Philox key",
+                "bvh": {"builder": bvh_info["builder"], "build_ms": round(bvh_info["build_ms"], 1),
+                        "nodes4": bvh_info["n_nodes4"]},
             },
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48 * len(wl.cameras),

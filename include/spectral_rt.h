@@ -162,6 +162,21 @@ rt_status rt_load_scene(rt_ctx* ctx, const float* verts, uint32_t n_verts, const
                         uint32_t n_tris, const uint32_t* mat_id, const int32_t* mat_type,
                         const float* mat_thickness, uint32_t n_mat);
 
+/* BVH builder of the following rt_load_scene calls: 0 = binned SAH on the
+ * host (default; also provides the binary tree of trace_variant 1-3),
+ * 1 = linear BVH built on the device (Morton codes, radix sort, Karras
+ * hierarchy, collapse to the four-wide tree; at most 2^24 triangles; only
+ * trace_variant 0).  The traversal results do not depend on the builder. */
+rt_status rt_set_bvh_builder(rt_ctx* ctx, uint32_t builder);
+
+typedef struct {
+  uint32_t n_tris;    /* triangles of the loaded scene */
+  uint32_t n_nodes4;  /* four-wide BVH nodes */
+  uint32_t builder;   /* builder used: 0 host SAH, 1 device LBVH */
+  float build_ms;     /* BVH build time: host wall clock, or device time (CUDA events) */
+} rt_scene_info;
+rt_status rt_get_scene_info(rt_ctx* ctx, rt_scene_info* info);
+
 /* Spectral tables (section 3): n_bands wavelengths in nm; sun radiance per
  * band inside a cone of half angle sun_half_angle (radians) around the unit
  * direction sun_dir (towards the sun); per material and band the index n, the

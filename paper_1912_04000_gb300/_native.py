@@ -22,7 +22,8 @@ XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
 EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_set_timing",
            "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
            "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static", "rt_guide_init",
-           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step", "rt_autotune"]
+           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step", "rt_autotune",
+           "rt_set_bvh_builder", "rt_get_scene_info"]
 
 
 class RtError(RuntimeError):
@@ -45,6 +46,10 @@ class RenderOpts(C.Structure):
                 ("guide_train_steps", C.c_uint32), ("guide_batch", C.c_uint32), ("sample_first", C.c_uint32),
                 ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("leaf_batch", C.c_uint32),
                 ("guide_order", C.c_uint32), ("ray_order", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+
+
+class SceneInfo(C.Structure):
+    _fields_ = [("n_tris", C.c_uint32), ("n_nodes4", C.c_uint32), ("builder", C.c_uint32), ("build_ms", C.c_float)]
 
 
 class AutotuneReport(C.Structure):
@@ -99,6 +104,8 @@ def load(path: str = LIB_PATH):
         L.rt_set_timing.argtypes = [vp, C.c_int]
         L.rt_probe_l2.argtypes = [vp, u64, u32, C.POINTER(C.c_float)]
         L.rt_load_scene.argtypes = [vp, vp, u32, vp, u32, vp, vp, vp, u32]
+        L.rt_set_bvh_builder.argtypes = [vp, u32]
+        L.rt_get_scene_info.argtypes = [vp, C.POINTER(SceneInfo)]
         L.rt_set_spectra.argtypes = [vp, vp, u32, vp, vp, f32, vp, vp, vp, vp, vp]
         L.rt_render.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp, vp,
                                 C.POINTER(Stats)]

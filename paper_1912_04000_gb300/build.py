@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspectral_rt.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["rt_api.cu", "rt_kernels.cu", "rt_xyz.cu", "rt_static.cu", "rt_guide.cu", "rt_bvh.cpp"]
+SOURCES = ["rt_api.cu", "rt_kernels.cu", "rt_xyz.cu", "rt_static.cu", "rt_guide.cu", "rt_lbvh.cu", "rt_bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -49,13 +49,15 @@ def main(argv=None):
     r.add_argument("--guide-train-steps", type=int, default=0)
     r.add_argument("--graph", action="store_true", help="capture the render in a CUDA graph and replay it")
     r.add_argument("--tune", action="store_true", help="autotuned launch settings (cached per GPU and workload)")
+    r.add_argument("--builder", default="host", choices=["host", "device"],
+                   help="BVH builder: binned SAH on the host or linear BVH on the device")
     r.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
     from .renderer import Renderer
     wl = _workload(args)
     t0 = time.perf_counter()
-    R = Renderer(0).load(wl)
+    R = Renderer(0).load(wl, builder=1 if args.builder == "device" else 0)
     if args.guided:
         R.guide_init(seed=1)
     t_load = time.perf_counter() - t0
@@ -69,7 +71,7 @@ def main(argv=None):
                        guided=args.guided, guide_collect=args.guide_collect,
                        guide_train_steps=args.guide_train_steps, use_graph=args.graph, tuned=tuned)
     st = out["stats"]
-    st.update(workload=wl.name, triangles=int(wl.scene.n_tris), load_s=t_load, tuned=tuned,
+    st.update(workload=wl.name, triangles=int(wl.scene.n_tris), load_s=t_load, tuned=tuned, bvh=R.scene_info(),
               paths_per_s=st["paths"] / (st["ms_render"] * 1e-3) if st["ms_render"] > 0 else None)
     print(json.dumps(st))
     if args.out:

@@ -1,6 +1,7 @@
 // C ABI of the spectral path tracer: context, scene and spectra upload,
 // render orchestration (wave loop), single-step entry points.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +31,9 @@ struct rt_ctx {
   uint32_t n_nodes = 0, n_nodes4 = 0, n_tris = 0, n_mat = 0;
   float eps = 0.0f;
   bool has_scene = false;
+  uint32_t builder = 0;       // BVH builder for the next rt_load_scene: 0 host SAH, 1 device LBVH
+  uint32_t builder_used = 0;  // builder of the loaded scene
+  float build_ms = 0.0f;      // its build time
   // spectra
   float4* d_mb = nullptr;
   float* d_ad = nullptr;
@@ -340,6 +344,24 @@ rt_status rt_set_counting(rt_ctx* c, int enable) {
   return RT_OK;
 }
 
+rt_status rt_set_bvh_builder(rt_ctx* c, uint32_t builder) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (builder > 1) return fail(c, RT_ERR_ARG, "rt_set_bvh_builder: 0 (host SAH) or 1 (device LBVH)");
+  c->builder = builder;
+  return RT_OK;
+}
+
+rt_status rt_get_scene_info(rt_ctx* c, rt_scene_info* info) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!info) return fail(c, RT_ERR_ARG, "rt_get_scene_info: info is required");
+  if (!c->has_scene) return fail(c, RT_ERR_STATE, "rt_get_scene_info: no scene loaded");
+  info->n_tris = c->n_tris;
+  info->n_nodes4 = c->n_nodes4;
+  info->builder = c->builder_used;
+  info->build_ms = c->build_ms;
+  return RT_OK;
+}
+
 rt_status rt_set_timing(rt_ctx* c, int enable) {
   if (rt_status e = check_ctx(c)) return e;
   c->timing = enable != 0;
@@ -382,23 +404,8 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     for (int a2 = 0; a2 < 3; ++a2) nrm64[4 * (size_t)t + a2] = (float)(n[a2] / len);
   }
   if (n_tris >= (1u << 28)) return fail(c, RT_ERR_SCENE, "at most 2^28 triangles");
-  BvhOut bvh;
-  build_bvh(verts, tris, n_tris, bvh);
-  // leaf-ordered triangle and normal records
-  std::vector<float4> tr(3 * (size_t)n_tris), nr(n_tris);
-  for (uint32_t i = 0; i < n_tris; ++i) {
-    const uint32_t t = bvh.order[i];
-    const float* v[3];
-    for (int k = 0; k < 3; ++k) v[k] = verts + 3 * (size_t)tris[3 * (size_t)t + k];
-    uint32_t mid = mat_id[t];
-    float idf, matf, zero = 0.0f;
-    std::memcpy(&idf, &t, 4);
-    std::memcpy(&matf, &mid, 4);
-    tr[3 * (size_t)i] = make_float4(v[0][0], v[0][1], v[0][2], idf);
-    tr[3 * (size_t)i + 1] = make_float4(v[1][0], v[1][1], v[1][2], matf);
-    tr[3 * (size_t)i + 2] = make_float4(v[2][0], v[2][1], v[2][2], zero);
-    nr[i] = make_float4(nrm64[4 * (size_t)t], nrm64[4 * (size_t)t + 1], nrm64[4 * (size_t)t + 2], matf);
-  }
+  const bool dev_build = c->builder == 1;
+  if (dev_build && n_tris > kLbvhMaxTris) return fail(c, RT_ERR_ARG, "device BVH builder: at most 2^24 triangles");
   // Node boxes are padded by 2^-22 (max |coordinate| + origin offset) so that
   // the traversal's FMA slab test, fma(plane, 1/d, -o/d), stays conservative
   // for every origin inside the scene bounds (the rounding of o/d moves a
@@ -420,36 +427,58 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     while ((double)f < x) f = std::nextafter(f, INFINITY);
     return f;
   };
-  std::vector<float4> nd(2 * bvh.nodes.size());
-  for (size_t i = 0; i < bvh.nodes.size(); ++i) {
-    const BvhNode& b = bvh.nodes[i];
-    float rf, cf;
-    std::memcpy(&rf, &b.ref, 4);
-    std::memcpy(&cf, &b.count, 4);
-    nd[2 * i] = make_float4(down(b.lo[0]), down(b.lo[1]), down(b.lo[2]), rf);
-    nd[2 * i + 1] = make_float4(up(b.hi[0]), up(b.hi[1]), up(b.hi[2]), cf);
+  const auto t_build0 = std::chrono::steady_clock::now();
+  // host build: binned SAH, leaf order from the tree; device build: the
+  // records go up in input order and are sorted there
+  BvhOut bvh;
+  if (!dev_build) build_bvh(verts, tris, n_tris, bvh);
+  std::vector<float4> tr(3 * (size_t)n_tris), nr(n_tris);
+  for (uint32_t i = 0; i < n_tris; ++i) {
+    const uint32_t t = dev_build ? i : bvh.order[i];
+    const float* v[3];
+    for (int k = 0; k < 3; ++k) v[k] = verts + 3 * (size_t)tris[3 * (size_t)t + k];
+    uint32_t mid = mat_id[t];
+    float idf, matf, zero = 0.0f;
+    std::memcpy(&idf, &t, 4);
+    std::memcpy(&matf, &mid, 4);
+    tr[3 * (size_t)i] = make_float4(v[0][0], v[0][1], v[0][2], idf);
+    tr[3 * (size_t)i + 1] = make_float4(v[1][0], v[1][1], v[1][2], matf);
+    tr[3 * (size_t)i + 2] = make_float4(v[2][0], v[2][1], v[2][2], zero);
+    nr[i] = make_float4(nrm64[4 * (size_t)t], nrm64[4 * (size_t)t + 1], nrm64[4 * (size_t)t + 2], matf);
   }
-  // four-wide nodes, padded the same way (empty slots keep their +-inf box)
-  // device layout per node: the six plane float4s, then the children packed
-  // as the traversal stack stores them (ref << 3 | count; 0 for an empty
-  // slot, whose box is never entered), then 16 bytes of padding
+  std::vector<float4> nd;
   std::vector<Bvh4Node> b4;
-  collapse_bvh4(bvh, b4, nullptr);
-  for (Bvh4Node& n4 : b4)
-    for (int i = 0; i < 4; ++i) {
-      if (n4.cnt[i] != kEmpty4) {
-        n4.lox[i] = down(n4.lox[i]);
-        n4.loy[i] = down(n4.loy[i]);
-        n4.loz[i] = down(n4.loz[i]);
-        n4.hix[i] = up(n4.hix[i]);
-        n4.hiy[i] = up(n4.hiy[i]);
-        n4.hiz[i] = up(n4.hiz[i]);
-        n4.ref[i] = (n4.ref[i] << 3) | n4.cnt[i];
-      } else {
-        n4.ref[i] = 0;
-      }
-      n4.cnt[i] = 0;
+  if (!dev_build) {
+    nd.resize(2 * bvh.nodes.size());
+    for (size_t i = 0; i < bvh.nodes.size(); ++i) {
+      const BvhNode& b = bvh.nodes[i];
+      float rf, cf;
+      std::memcpy(&rf, &b.ref, 4);
+      std::memcpy(&cf, &b.count, 4);
+      nd[2 * i] = make_float4(down(b.lo[0]), down(b.lo[1]), down(b.lo[2]), rf);
+      nd[2 * i + 1] = make_float4(up(b.hi[0]), up(b.hi[1]), up(b.hi[2]), cf);
     }
+    // four-wide nodes, padded the same way (empty slots keep their +-inf box)
+    // device layout per node: the six plane float4s, then the children packed
+    // as the traversal stack stores them (ref << 3 | count; 0 for an empty
+    // slot, whose box is never entered), then 16 bytes of padding
+    collapse_bvh4(bvh, b4, nullptr);
+    for (Bvh4Node& n4 : b4)
+      for (int i = 0; i < 4; ++i) {
+        if (n4.cnt[i] != kEmpty4) {
+          n4.lox[i] = down(n4.lox[i]);
+          n4.loy[i] = down(n4.loy[i]);
+          n4.loz[i] = down(n4.loz[i]);
+          n4.hix[i] = up(n4.hix[i]);
+          n4.hiy[i] = up(n4.hiy[i]);
+          n4.hiz[i] = up(n4.hiz[i]);
+          n4.ref[i] = (n4.ref[i] << 3) | n4.cnt[i];
+        } else {
+          n4.ref[i] = 0;
+        }
+        n4.cnt[i] = 0;
+      }
+  }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c->d_nodes);
@@ -457,16 +486,74 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   dfree(c->d_tris);
   dfree(c->d_nrm);
   c->has_scene = false;
-  CUDA_TRY(c, cudaMalloc(&c->d_nodes, nd.size() * sizeof(float4)));
-  CUDA_TRY(c, cudaMalloc(&c->d_nodes4, b4.size() * sizeof(Bvh4Node)));
-  CUDA_TRY(c, cudaMemcpy(c->d_nodes4, b4.data(), b4.size() * sizeof(Bvh4Node), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMalloc(&c->d_tris, tr.size() * sizeof(float4)));
   CUDA_TRY(c, cudaMalloc(&c->d_nrm, nr.size() * sizeof(float4)));
-  CUDA_TRY(c, cudaMemcpy(c->d_nodes, nd.data(), nd.size() * sizeof(float4), cudaMemcpyHostToDevice));
-  CUDA_TRY(c, cudaMemcpy(c->d_tris, tr.data(), tr.size() * sizeof(float4), cudaMemcpyHostToDevice));
-  CUDA_TRY(c, cudaMemcpy(c->d_nrm, nr.data(), nr.size() * sizeof(float4), cudaMemcpyHostToDevice));
-  c->n_nodes = (uint32_t)bvh.nodes.size();
-  c->n_nodes4 = (uint32_t)b4.size();
+  if (!dev_build) {
+    CUDA_TRY(c, cudaMalloc(&c->d_nodes, nd.size() * sizeof(float4)));
+    CUDA_TRY(c, cudaMalloc(&c->d_nodes4, b4.size() * sizeof(Bvh4Node)));
+    CUDA_TRY(c, cudaMemcpy(c->d_nodes4, b4.data(), b4.size() * sizeof(Bvh4Node), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_nodes, nd.data(), nd.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_tris, tr.data(), tr.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_nrm, nr.data(), nr.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    c->n_nodes = (uint32_t)bvh.nodes.size();
+    c->n_nodes4 = (uint32_t)b4.size();
+    c->build_ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_build0).count();
+  } else {
+    // device build from the uploaded geometry and input-order records
+    float *d_verts = nullptr;
+    uint32_t* d_idx = nullptr;
+    float4 *d_tr_in = nullptr, *d_nr_in = nullptr;
+    void* scratch = nullptr;
+    rt_status st = RT_OK;
+    auto release = [&]() {
+      dfree(d_verts);
+      dfree(d_idx);
+      dfree(d_tr_in);
+      dfree(d_nr_in);
+      dfree(scratch);
+    };
+    const size_t n4cap = std::max<size_t>(n_tris - 1, 1);
+    cudaError_t e = cudaMalloc(&d_verts, 3 * (size_t)n_verts * sizeof(float));
+    if (!e) e = cudaMalloc(&d_idx, 3 * (size_t)n_tris * sizeof(uint32_t));
+    if (!e) e = cudaMalloc(&d_tr_in, tr.size() * sizeof(float4));
+    if (!e) e = cudaMalloc(&d_nr_in, nr.size() * sizeof(float4));
+    if (!e) e = cudaMalloc(&scratch, lbvh_scratch_bytes(n_tris));
+    if (!e) e = cudaMalloc(&c->d_nodes4, n4cap * 8 * sizeof(float4));
+    if (!e) e = cudaMemcpy(d_verts, verts, 3 * (size_t)n_verts * sizeof(float), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_idx, tris, 3 * (size_t)n_tris * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_tr_in, tr.data(), tr.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d_nr_in, nr.data(), nr.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e) {
+      release();
+      CUDA_TRY(c, e);
+    }
+    float padf = (float)pad;
+    if ((double)padf < pad) padf = std::nextafter(padf, INFINITY);
+    const float flo[3] = {(float)lo[0], (float)lo[1], (float)lo[2]}, fhi[3] = {(float)hi[0], (float)hi[1], (float)hi[2]};
+    cudaStream_t bs = c->stream;
+    uint32_t* d_counts = nullptr;
+    cudaEventRecord(c->ev[0], bs);
+    launch_lbvh(d_verts, d_idx, n_tris, flo, fhi, padf, d_tr_in, d_nr_in, scratch, (float4*)c->d_nodes4,
+                (float4*)c->d_tris, (float4*)c->d_nrm, &d_counts, c->sms, bs);
+    cudaEventRecord(c->ev[1], bs);
+    uint32_t counts[2] = {0, 0};
+    e = cudaGetLastError();
+    if (!e) e = cudaMemcpyAsync(counts, d_counts, sizeof(uint32_t), cudaMemcpyDeviceToHost, bs);
+    if (!e) e = cudaMemcpyAsync(counts + 1, d_counts + kLbvhLevels, sizeof(uint32_t), cudaMemcpyDeviceToHost, bs);
+    if (!e) e = cudaStreamSynchronize(bs);
+    float ms = 0.0f;
+    if (!e) e = cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    release();
+    CUDA_TRY(c, e);
+    if (counts[1] != 0u || counts[0] == 0u || counts[0] > n4cap)
+      st = fail(c, RT_ERR_SCENE, "device BVH builder: tree deeper than the collapse levels");
+    if (st != RT_OK) return st;
+    c->d_nodes = nullptr;  // no binary tree: the binary-tree traversal variants are unavailable
+    c->n_nodes = 2 * n_tris - 1;
+    c->n_nodes4 = counts[0];
+    c->build_ms = ms;
+  }
+  c->builder_used = dev_build ? 1u : 0u;
   c->n_tris = n_tris;
   c->n_mat = n_mat;
   const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
@@ -557,6 +644,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
   if (o.trace_variant > 3) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant != 0 && !c->d_nodes)
+    return fail(c, RT_ERR_ARG, "rt_render: binary-tree traversal variants need the host-built BVH");
   if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");
   if (o.guide_order > 1) return fail(c, RT_ERR_ARG, "rt_render: guide_order is 0 or 1");
   if (o.ray_order > 1) return fail(c, RT_ERR_ARG, "rt_render: ray_order is 0 or 1");

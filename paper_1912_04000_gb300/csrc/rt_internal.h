@@ -119,6 +119,18 @@ constexpr uint32_t kCellSortBins = kGuideSortBins;  // 2^18 keys for every cell 
 // Exclusive scan of kCellSortBins counts in place, chunk offsets after them
 // (rt_kernels.cu).
 void launch_cell_scan(uint32_t* bins, cudaStream_t st);
+// The same for n counts (n a multiple of 32768, at most 2^20): data[i] becomes
+// the exclusive prefix within its chunk of 1024, data[n + c] the exclusive
+// prefix of chunk c's total.
+void launch_scan(uint32_t* data, size_t n, cudaStream_t st);
+
+// Device BVH builder (rt_lbvh.cu).
+constexpr uint32_t kLbvhMaxTris = 1u << 24;
+size_t lbvh_scratch_bytes(uint32_t n);
+void launch_lbvh(const float* verts, const uint32_t* tri, uint32_t n, const float lo[3], const float hi[3], float pad,
+                 const float4* tri_in, const float4* nrm_in, void* scratch, float4* nodes4, float4* tri_out,
+                 float4* nrm_out, uint32_t** counts_out, int sms, cudaStream_t st);
+constexpr int kLbvhLevels = 64;  // collapse levels launched (counts has 2 + kLbvhLevels entries)
 
 // Per-wave device counters, one row per vertex k (0 .. depth).
 struct Counters {

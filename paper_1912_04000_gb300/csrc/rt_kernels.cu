@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(1024) k_cell_scan_chunks(uint32_t* __restrict_
   if (threadIdx.x == 0) totals[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kCellSortBins / 1024u) k_cell_scan_totals(uint32_t* __restrict__ totals) {
+__global__ void __launch_bounds__(1024) k_cell_scan_totals(uint32_t* __restrict__ totals) {
   __shared__ uint32_t ws[32];
   uint32_t tot;
   const uint32_t ex = block_exclusive_scan(totals[threadIdx.x], ws, tot);
@@ -1064,9 +1064,11 @@ void sort_queue(const DevScene& S, const float4* q, const WaveBufs& b, uint32_t 
 
 }  // namespace
 
-void launch_cell_scan(uint32_t* bins, cudaStream_t st) {
-  k_cell_scan_chunks<<<kCellSortBins / 1024u, 1024, 0, st>>>(bins, bins + kCellSortBins);
-  k_cell_scan_totals<<<1, kCellSortBins / 1024u, 0, st>>>(bins + kCellSortBins);
+void launch_cell_scan(uint32_t* bins, cudaStream_t st) { launch_scan(bins, kCellSortBins, st); }
+
+void launch_scan(uint32_t* data, size_t n, cudaStream_t st) {
+  k_cell_scan_chunks<<<(unsigned)(n / 1024u), 1024, 0, st>>>(data, data + n);
+  k_cell_scan_totals<<<1, (unsigned)(n / 1024u), 0, st>>>(data + n);
 }
 
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,

@@ -65,7 +65,9 @@ class Renderer:
         return float(g.value)
 
     # -- scene and spectra ------------------------------------------------------
-    def load_scene(self, scene):
+    def load_scene(self, scene, builder: int = 0):
+        """builder 0: binned SAH on the host; 1: linear BVH on the device."""
+        self._check("rt_set_bvh_builder", self.lib.rt_set_bvh_builder(self._h, int(builder)))
         v = np.ascontiguousarray(scene.verts, np.float32)
         t = np.ascontiguousarray(scene.tris, np.uint32)
         m = np.ascontiguousarray(scene.mat_id, np.uint32)
@@ -86,10 +88,16 @@ class Renderer:
         self._check("rt_set_spectra", st)
         self.n_bands = lam.shape[0]
 
-    def load(self, workload):
-        self.load_scene(workload.scene)
+    def load(self, workload, builder: int = 0):
+        self.load_scene(workload.scene, builder)
         self.set_spectra(workload.spectra)
         return self
+
+    def scene_info(self) -> dict:
+        info = _native.SceneInfo()
+        self._check("rt_get_scene_info", self.lib.rt_get_scene_info(self._h, C.byref(info)))
+        return {"n_tris": info.n_tris, "n_nodes4": info.n_nodes4, "builder": ("host_sah", "device_lbvh")[info.builder],
+                "build_ms": info.build_ms}
 
     # -- render -----------------------------------------------------------------
     def render(self, cameras: Sequence, spp: int, depth: int, seed: int = 0, band_first: int = 0,

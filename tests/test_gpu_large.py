@@ -46,3 +46,24 @@ def test_large_nave_guided_runs(large):
     out = R.render(wl.cameras, 1, wl.depth, wl.seed, guided=True, guide_collect=8, guide_train_steps=2)
     s = out["spectral"].cpu().numpy()
     assert np.isfinite(s).all() and (s >= 0).all() and s.sum() > 0
+
+
+def test_large_nave_device_build(large):
+    """The device builder on 2M triangles: the same closest hits as the host
+    SAH tree for seeded rays, and its build time next to the host's."""
+    R, wl = large
+    rng = np.random.default_rng(4)
+    lo, hi = wl.scene.verts.min(0), wl.scene.verts.max(0)
+    o = (lo + (hi - lo) * rng.uniform(0.02, 0.98, size=(20000, 3))).astype(np.float32)
+    d = rng.normal(size=(20000, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    t0, p0 = (x.cpu().numpy() for x in R.trace_closest(o, d))
+    host = R.scene_info()
+    try:
+        R.load(wl, builder=1)
+        dev = R.scene_info()
+        t1, p1 = (x.cpu().numpy() for x in R.trace_closest(o, d))
+    finally:
+        R.load(wl, builder=0)
+    print("host build", host, "device build", dev)
+    assert np.array_equal(p0, p1) and np.array_equal(t0, t1)
