@@ -76,6 +76,9 @@ def lib():
                                           C.POINTER(C.c_uint32), C.c_uint64]
             L.or_fresnel.restype = C.c_double
             L.or_fresnel.argtypes = [C.c_double] * 3
+            L.or_refract.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
+                                     C.POINTER(C.c_double)]
+            L.or_refract.restype = C.c_int
             L.or_slab.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)] * 2
             L.or_scene_create.restype = C.c_void_p
             L.or_scene_create.argtypes = [C.POINTER(_SceneDesc), C.c_int]
@@ -124,6 +127,17 @@ def philox_batch(key0: int, key1: int, ctr: np.ndarray) -> np.ndarray:
 
 def fresnel(cos_i: float, n: float, k: float) -> float:
     return lib().or_fresnel(cos_i, n, k)
+
+
+def refract(d, n, eta):
+    """Refracted unit direction of d at normal n (facing the incident side)
+    into relative index eta, or None on total internal reflection."""
+    L = lib()
+    dd = np.ascontiguousarray(d, np.float64)
+    nn = np.ascontiguousarray(n, np.float64)
+    out = np.zeros(3, np.float64)
+    ok = L.or_refract(_ptr(dd, C.c_double), _ptr(nn, C.c_double), float(eta), _ptr(out, C.c_double))
+    return out if ok else None
 
 
 def slab(cos_i, n, k, lambda_nm, d):

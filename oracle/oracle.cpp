@@ -22,6 +22,12 @@
 //       thin glass: reflect with probability R_s/(R_s+T_s), else pass
 //         straight through; T *= R_s + T_s
 //       conductor: mirror reflection, T *= R(theta, n, k)
+//       solid refracting glass (section 3 Eq. 1; closed mesh, outward
+//         normals, no other surface inside): arriving from inside,
+//         T *= exp(-4 pi k |p - p_prev| / lambda) for the distance crossed;
+//         reflect with the Fresnel R of the relative index (n in, 1/n out),
+//         else refract by Snell's law with n(lambda); the next ray starts
+//         on the true ray; sun rays treat the solid as opaque
 //   spectral sum over samples in sample order (FP64), then XYZ.
 //
 // Everything is double precision except the inputs, which arrive as float.
@@ -127,7 +133,21 @@ void slab(double c, double n, double k, double lambda_nm, double d, double* Rs, 
 // ---------------------------------------------------------------------------
 // scene
 // ---------------------------------------------------------------------------
-enum { M_LAMBERT = 0, M_GLASS = 1, M_CONDUCTOR = 2, M_EMISSIVE = 3 };
+enum { M_LAMBERT = 0, M_GLASS = 1, M_CONDUCTOR = 2, M_EMISSIVE = 3, M_DIELECTRIC = 4 };
+
+// Refraction of the unit direction d at a surface with unit normal n facing
+// the incident side (dot(d, n) < 0), from index 1 into relative index eta
+// (eta < 1 when leaving the denser medium): Snell's law
+// sin(theta_t) = sin(theta_i) / eta in the plane of d and n.  Returns false
+// on total internal reflection.
+bool refract(V3 d, V3 n, double eta, V3* t) {
+  const double ci = -dot(d, n);
+  const double r = 1.0 / eta;
+  const double k = 1.0 - r * r * (1.0 - ci * ci);
+  if (k < 0.0) return false;
+  *t = r * d + (r * ci - std::sqrt(k)) * n;
+  return true;
+}
 
 struct ONode {
   double lo[3], hi[3];
@@ -400,6 +420,15 @@ void or_philox_batch(uint32_t key0, uint32_t key1, const uint32_t* ctr, uint32_t
 
 double or_fresnel(double cos_i, double n, double k) { return fresnel_complex(cos_i, n, k); }
 
+int or_refract(const double d[3], const double n[3], double eta, double t[3]) {
+  V3 r;
+  if (!refract(V3{d[0], d[1], d[2]}, V3{n[0], n[1], n[2]}, eta, &r)) return 0;
+  t[0] = r.x;
+  t[1] = r.y;
+  t[2] = r.z;
+  return 1;
+}
+
 void or_slab(double cos_i, double n, double k, double lambda_nm, double d, double* Rs, double* Ts) {
   slab(cos_i, n, k, lambda_nm, d, Rs, Ts);
 }
@@ -523,6 +552,7 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
     V3 d = normalize(C.f + sx * C.r + sy * C.u);
     V3 o = C.pos;
     double T = 1.0, L = 0.0;
+    V3 pprev = C.pos;      // the previous vertex (camera or surface point)
     bool covered = false;  // direct sun along this segment is already counted by NEE
     uint32_t sig = 2166136261u;
     for (uint32_t k = 1; k <= depth; ++k) {
@@ -583,6 +613,28 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
           o = p - S.eps * n;
         }
         T *= Rs + Ts;
+      } else if (type == M_DIELECTRIC) {
+        // solid refracting glass (a closed mesh, normals outward, holding
+        // no other surface): light that reaches this interface from inside
+        // crossed the medium from the previous interface point, so it is
+        // attenuated by Beer-Lambert exp(-alpha |p - p_prev|), alpha =
+        // 4 pi k / lambda.  The interface reflects with the Fresnel
+        // reflectance of the relative index (n entering, 1/n leaving; total
+        // internal reflection gives 1), else refracts (Snell; dispersion
+        // through n(lambda)).  The next ray starts on the true ray, a short
+        // step eps / max(|cos|, 1/16) along it, so the distance to the next
+        // interface is exact.
+        const bool inside = dot(ng, d) > 0.0;
+        if (inside) T *= std::exp(-4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9) * std::sqrt(dot(p - pprev, p - pprev)));
+        const double eta = inside ? 1.0 / S.ntab[mb] : S.ntab[mb];
+        const double R = fresnel_complex(cos_i, eta, 0.0);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+        V3 tdir;
+        if (u01(r1.w[0]) < R || !refract(d, n, eta, &tdir)) d = d - (2.0 * dot(d, n)) * n;
+        else d = normalize(tdir);
+        o = p + (S.eps / std::max(std::fabs(dot(d, n)), 0.0625)) * d;
+        covered = false;
       } else {  // conductor
         double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
         if (k == depth) break;
@@ -591,6 +643,7 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
         T *= R;
         covered = false;
       }
+      pprev = p;
     }
     if (sig_out) *sig_out = sig;
     return L;

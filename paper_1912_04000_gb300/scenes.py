@@ -35,7 +35,7 @@ from typing import List, Sequence, Tuple
 
 import numpy as np
 
-LAMBERT, THIN_GLASS, CONDUCTOR, EMISSIVE = 0, 1, 2, 3
+LAMBERT, THIN_GLASS, CONDUCTOR, EMISSIVE, DIELECTRIC = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -258,6 +258,32 @@ def _box_quads(mb: MeshBuilder, lo, hi, mats):
     mb.quad((x0, y0, z1), (x0, y1, z1), (x1, y1, z1), (x1, y0, z1), mats[5])
 
 
+def _solid(mb: MeshBuilder, faces, mat):
+    """Closed solid from planar polygons (lists of points); each face is fanned
+    into triangles and wound so that its normal points away from the solid's
+    centroid (the dielectric's side test reads the winding)."""
+    pts = np.array([p for f in faces for p in f], np.float64)
+    ctr = pts.mean(0)
+    for f in faces:
+        f = [np.asarray(q, np.float64) for q in f]
+        nrm = np.cross(f[1] - f[0], f[2] - f[0])
+        if np.dot(nrm, f[0] - ctr) < 0.0:
+            f = f[::-1]
+        for j in range(1, len(f) - 1):
+            mb.tri(f[0], f[j], f[j + 1], mat)
+
+
+def _solid_box(mb: MeshBuilder, lo, hi, mat):
+    x0, y0, z0 = lo
+    x1, y1, z1 = hi
+    _solid(mb, [[(x0, y0, z0), (x0, y1, z0), (x0, y1, z1), (x0, y0, z1)],
+                [(x1, y0, z0), (x1, y1, z0), (x1, y1, z1), (x1, y0, z1)],
+                [(x0, y0, z0), (x1, y0, z0), (x1, y0, z1), (x0, y0, z1)],
+                [(x0, y1, z0), (x1, y1, z0), (x1, y1, z1), (x0, y1, z1)],
+                [(x0, y0, z0), (x1, y0, z0), (x1, y1, z0), (x0, y1, z0)],
+                [(x0, y0, z1), (x1, y0, z1), (x1, y1, z1), (x0, y1, z1)]], mat)
+
+
 def _flat_spectra(n_mat, B):
     z = np.zeros((n_mat, B), np.float64)
     return z.copy(), z.copy(), z.copy(), z.copy()
@@ -295,6 +321,82 @@ def tiny_box(width=128, height=128, n_bands=16, spp=4, depth=4, seed=0) -> Workl
     spec = _spectra(lam, sun_spectrum(lam), sun, 0.25, n, k, rho, le)
     cam = Camera((2.0, 1.5, 0.3), (2.0, 1.0, 5.0), (0.0, 1.0, 0.0), 60.0, width, height)
     return Workload("tiny_box", scene, spec, [cam], spp, depth, seed)
+
+
+def prism_room(width=96, height=72, n_bands=16, spp=4, depth=8, seed=0) -> Workload:
+    """The tiny box room (sunlight through the thin-glass z = 5 wall) with a
+    solid triangular prism of dispersive flint-like glass on the floor in the
+    sun patch: refraction with n(lambda), total internal reflection and
+    Beer-Lambert absorption inside.  20 triangles."""
+    mb = MeshBuilder()
+    STONE, GLASS, PRISM = 0, 1, 2
+    _box_quads(mb, (0.0, 0.0, 0.0), (4.0, 3.0, 5.0), (STONE, STONE, STONE, STONE, STONE, GLASS))
+    # equilateral cross-section in x-y, 0.8 m wide, extruded along z
+    a, h = 0.8, 0.8 * math.sqrt(3.0) / 2.0
+    x0, z0, z1 = 1.6, 2.6, 3.6
+    tri0 = [(x0, 0.001, z0), (x0 + a, 0.001, z0), (x0 + 0.5 * a, 0.001 + h, z0)]
+    tri1 = [(x, y, z1) for (x, y, _) in tri0]
+    faces = [tri0, tri1] + [[tri0[i], tri0[(i + 1) % 3], tri1[(i + 1) % 3], tri1[i]] for i in range(3)]
+    _solid(mb, faces, PRISM)
+    scene = mb.build([LAMBERT, THIN_GLASS, DIELECTRIC], [0.0, 0.01, 0.0])
+    lam = band_wavelengths(400.0, 700.0, n_bands)
+    n, k, rho, le = _flat_spectra(3, n_bands)
+    rho[STONE] = 0.7
+    n[STONE] = 1.0
+    n[GLASS] = cauchy_n(lam, 1.5, 0.004)
+    k[GLASS] = 1e-6
+    n[PRISM] = cauchy_n(lam, 1.62, 0.012)
+    k[PRISM] = 2e-8
+    sun = sun_direction(35.0, 200.0)
+    spec = _spectra(lam, sun_spectrum(lam), sun, 0.25, n, k, rho, le)
+    cam = Camera((3.4, 1.4, 0.6), (2.0, 0.3, 3.1), (0.0, 1.0, 0.0), 45.0, width, height)
+    return Workload("prism_room", scene, spec, [cam], spp, depth, seed)
+
+
+def solid_slab_view(n_glass=1.5, k_glass=2e-6, thickness=0.01, lambda_nm=(450.0, 550.0, 650.0),
+                    tilt_deg=30.0, spp=256, depth=8, seed=7) -> Workload:
+    """Camera looks through a wide solid slab of refracting glass (a closed
+    6 x 6 m box of the given thickness, tilted about x) at the sun behind it.
+    Both faces are parallel, so every transmitted path leaves in its original
+    direction; summing the internal reflections, the pixel's expectation is
+    the thin-sheet T_s(theta) L_sun of the same glass."""
+    mb = MeshBuilder()
+    t = math.radians(tilt_deg)
+    ay = np.array([0.0, math.cos(t), -math.sin(t)])
+    nz = np.array([0.0, math.sin(t), math.cos(t)])
+    ax = np.array([1.0, 0.0, 0.0])
+    corners = lambda off: [s1 * 3.0 * ax + s2 * 3.0 * ay + off * nz for s1, s2 in ((-1, -1), (1, -1), (1, 1), (-1, 1))]
+    lo_f, hi_f = corners(-0.5 * thickness), corners(0.5 * thickness)
+    faces = [lo_f, hi_f] + [[lo_f[i], lo_f[(i + 1) % 4], hi_f[(i + 1) % 4], hi_f[i]] for i in range(4)]
+    _solid(mb, faces, 0)
+    scene = mb.build([DIELECTRIC], [0.0])
+    lam = np.asarray(lambda_nm, np.float64)
+    B = lam.shape[0]
+    n, k, rho, le = _flat_spectra(1, B)
+    n[0] = n_glass
+    k[0] = k_glass
+    spec = _spectra(lam, np.ones(B), np.array([0.0, 0.0, 1.0]), 0.2, n, k, rho, le)
+    cam = Camera((0.0, 0.0, -2.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0), 0.05, 2, 2)
+    return Workload("solid_slab_view", scene, spec, [cam], spp, depth, seed)
+
+
+def dielectric_furnace(albedo=0.3, le=1.0, n_bands=3, width=8, height=8, spp=4, depth=64, seed=11) -> Workload:
+    """The furnace box (walls emit le (1 - albedo), Lambertian albedo) with a
+    lossless refracting cube inside.  Refraction and reflection keep the
+    throughput, so a path returns le (1 - albedo^m) for its m Lambertian
+    vertices: within 1e-6 of le once m >= 12."""
+    mb = MeshBuilder()
+    _box_quads(mb, (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (0,) * 6)
+    _solid_box(mb, (-0.3, -0.35, -0.25), (0.25, 0.2, 0.3), 1)
+    scene = mb.build([EMISSIVE, DIELECTRIC], [0.0, 0.0])
+    lam = band_wavelengths(450.0, 650.0, n_bands)
+    n, k, rho, lt = _flat_spectra(2, n_bands)
+    rho[0] = albedo
+    lt[0] = le * (1.0 - albedo)
+    n[1] = cauchy_n(lam, 1.5, 0.004)
+    spec = _spectra(lam, np.ones(n_bands), np.array([0.3, 0.8, 0.2]), 0.25, n, k, rho, lt)
+    cam = Camera((0.6, 0.5, 0.7), (-0.1, -0.1, 0.0), (0.0, 1.0, 0.0), 50.0, width, height)
+    return Workload("dielectric_furnace", scene, spec, [cam], spp, depth, seed)
 
 
 def furnace_box(albedo=0.5, le=1.0, n_bands=4, width=16, height=16, spp=2, depth=5,
