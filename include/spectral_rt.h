@@ -54,7 +54,12 @@ typedef enum {
   RT_LAMBERT = 0,    /* diffuse stone, reflectance rho(lambda) */
   RT_THIN_GLASS = 1, /* thin sheet: complex Fresnel faces + Beer-Lambert interior, thickness d */
   RT_CONDUCTOR = 2,  /* metal: specular, complex Fresnel with n(lambda) + i k(lambda) */
-  RT_EMISSIVE = 3    /* test material: Lambertian rho plus emitted radiance le(lambda) */
+  RT_EMISSIVE = 3,   /* test material: Lambertian rho plus emitted radiance le(lambda) */
+  RT_DIELECTRIC = 4  /* solid refracting glass (section 3, Eq. 1): the triangles of a material of
+                        this type form closed solids with outward (counter-clockwise) winding and
+                        no other surface inside; Fresnel of the relative index, Snell refraction
+                        with n(lambda), Beer-Lambert 4 pi k / lambda per metre inside; opaque to
+                        sun rays.  Its thickness entry is ignored. */
 } rt_material_type;
 
 typedef enum {

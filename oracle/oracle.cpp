@@ -23,11 +23,11 @@
 //         straight through; T *= R_s + T_s
 //       conductor: mirror reflection, T *= R(theta, n, k)
 //       solid refracting glass (section 3 Eq. 1; closed mesh, outward
-//         normals, no other surface inside): arriving from inside,
-//         T *= exp(-4 pi k |p - p_prev| / lambda) for the distance crossed;
-//         reflect with the Fresnel R of the relative index (n in, 1/n out),
-//         else refract by Snell's law with n(lambda); the next ray starts
-//         on the true ray; sun rays treat the solid as opaque
+//         normals, no other surface inside): T *= exp(-4 pi k s / lambda)
+//         for every stretch s travelled inside; reflect with the Fresnel R
+//         of the relative index (n in, 1/n out), else refract by Snell's
+//         law with n(lambda); the next ray starts on the true ray, a short
+//         step along it; sun rays treat the solid as opaque
 //   spectral sum over samples in sample order (FP64), then XYZ.
 //
 // Everything is double precision except the inputs, which arrive as float.
@@ -552,7 +552,6 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
     V3 d = normalize(C.f + sx * C.r + sy * C.u);
     V3 o = C.pos;
     double T = 1.0, L = 0.0;
-    V3 pprev = C.pos;      // the previous vertex (camera or surface point)
     bool covered = false;  // direct sun along this segment is already counted by NEE
     uint32_t sig = 2166136261u;
     for (uint32_t k = 1; k <= depth; ++k) {
@@ -615,17 +614,18 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
         T *= Rs + Ts;
       } else if (type == M_DIELECTRIC) {
         // solid refracting glass (a closed mesh, normals outward, holding
-        // no other surface): light that reaches this interface from inside
-        // crossed the medium from the previous interface point, so it is
-        // attenuated by Beer-Lambert exp(-alpha |p - p_prev|), alpha =
-        // 4 pi k / lambda.  The interface reflects with the Fresnel
-        // reflectance of the relative index (n entering, 1/n leaving; total
-        // internal reflection gives 1), else refracts (Snell; dispersion
-        // through n(lambda)).  The next ray starts on the true ray, a short
-        // step eps / max(|cos|, 1/16) along it, so the distance to the next
-        // interface is exact.
+        // no other surface): light is attenuated by Beer-Lambert
+        // exp(-alpha s), alpha = 4 pi k / lambda, over every stretch s it
+        // travels inside -- the segment that ends here when it arrives from
+        // inside, and the short start step of a new ray that heads inside.
+        // The face reflects with the Fresnel reflectance of the relative
+        // index (n entering, 1/n leaving; total internal reflection gives
+        // 1), else refracts (Snell; dispersion through n(lambda)).  The next
+        // ray starts on the true ray, a step eps / max(|cos|, 1/16) along
+        // it, so the distance crossed inside is exact.
         const bool inside = dot(ng, d) > 0.0;
-        if (inside) T *= std::exp(-4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9) * std::sqrt(dot(p - pprev, p - pprev)));
+        const double alpha = 4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9);
+        if (inside) T *= std::exp(-alpha * t);
         const double eta = inside ? 1.0 / S.ntab[mb] : S.ntab[mb];
         const double R = fresnel_complex(cos_i, eta, 0.0);
         if (k == depth) break;
@@ -633,7 +633,9 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
         V3 tdir;
         if (u01(r1.w[0]) < R || !refract(d, n, eta, &tdir)) d = d - (2.0 * dot(d, n)) * n;
         else d = normalize(tdir);
-        o = p + (S.eps / std::max(std::fabs(dot(d, n)), 0.0625)) * d;
+        const double step = S.eps / std::max(std::fabs(dot(d, n)), 0.0625);
+        if (dot(d, ng) < 0.0) T *= std::exp(-alpha * step);
+        o = p + step * d;
         covered = false;
       } else {  // conductor
         double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
@@ -643,7 +645,6 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
         T *= R;
         covered = false;
       }
-      pprev = p;
     }
     if (sig_out) *sig_out = sig;
     return L;

@@ -377,7 +377,7 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   for (uint32_t i = 0; i < n_verts; ++i)
     if (!finite3(verts + 3 * (size_t)i)) return fail(c, RT_ERR_SCENE, "vertex " + std::to_string(i) + " not finite");
   for (uint32_t m = 0; m < n_mat; ++m) {
-    if (mat_type[m] < 0 || mat_type[m] > 3) return fail(c, RT_ERR_SCENE, "material " + std::to_string(m) + ": bad type");
+    if (mat_type[m] < 0 || mat_type[m] > 4) return fail(c, RT_ERR_SCENE, "material " + std::to_string(m) + ": bad type");
     if (!(mat_thickness[m] >= 0.0f) || !std::isfinite(mat_thickness[m]))
       return fail(c, RT_ERR_SCENE, "material " + std::to_string(m) + ": bad thickness");
   }
@@ -592,7 +592,9 @@ rt_status rt_set_spectra(rt_ctx* c, const float* lambda_nm, uint32_t n_bands, co
           !(lambda_nm[b] > 0.0f))
         return fail(c, RT_ERR_ARG, "rt_set_spectra: non-finite table entry");
       mb[i] = make_float4(n[i], k[i], rho[i], le ? le[i] : 0.0f);
-      ad[i] = (float)(4.0 * M_PI * (double)k[i] * (double)c->mthick[m] / ((double)lambda_nm[b] * 1e-9));
+      // thin glass: alpha d for its thickness; solid glass: alpha per metre
+      const double len = c->mtype[m] == 4 ? 1.0 : (double)c->mthick[m];
+      ad[i] = (float)(4.0 * M_PI * (double)k[i] * len / ((double)lambda_nm[b] * 1e-9));
     }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);

@@ -773,6 +773,41 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
               n1 = make_float4(d.x, d.y, d.z, T * (Rs + Ts));
             }
           }
+        } else if (type == 4) {
+          // solid refracting glass (section 3 Eq. 1): a segment that ends
+          // here from inside crossed the medium, Beer-Lambert with alpha =
+          // 4 pi k / lambda per metre; the face reflects with the Fresnel
+          // reflectance of the relative index (n entering, 1/n leaving,
+          // 1 past the critical angle), else refracts by Snell's law with
+          // n(lambda).  The next ray starts a short step along itself so
+          // that the distance crossed inside stays exact; the step's share
+          // of the attenuation is taken now.
+          const bool inside = dot(ng, d) > 0.0f;
+          const float alpha = __ldg(P.ad + mat * P.n_bands + band);
+          float Tn = inside ? T * expf(-alpha * h.x) : T;
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            const float eta = inside ? 1.0f / m.x : m.x;
+            const float R = fresnel_complex(cos_i, eta, 0.0f);
+            const float r = inside ? m.x : 1.0f / m.x;
+            const float kk = 1.0f - r * r * (1.0f - cos_i * cos_i);
+            const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, band, 4u * k + 1u), w.key0, w.key1);
+            float3 nd;
+            if (u01(u1.x) < R || kk < 0.0f) {
+              nd = madd(d, -2.0f * dot(d, n), n);
+            } else {
+              const float3 td = madd(make_float3(r * d.x, r * d.y, r * d.z), r * cos_i - sqrtf(kk), n);
+              const float il = rsqrtf(dot(td, td));
+              nd = make_float3(td.x * il, td.y * il, td.z * il);
+            }
+            const float step = S.eps / fmaxf(fabsf(dot(nd, n)), 0.0625f);
+            if (dot(nd, ng) < 0.0f) Tn *= expf(-alpha * step);
+            const float3 po = madd(p, step, nd);
+            emit_next = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid));
+            n1 = make_float4(nd.x, nd.y, nd.z, Tn);
+          }
         } else {
           const float R = fresnel_complex(cos_i, m.x, m.y);
           if (k == w.depth) {
