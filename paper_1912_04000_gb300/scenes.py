@@ -31,7 +31,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import List, Sequence, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -130,9 +130,33 @@ def planck(lambda_nm: np.ndarray, temp_k: float) -> np.ndarray:
     return 2.0 * h * c * c / lam ** 5 / np.expm1(h * c / (lam * kb * temp_k))
 
 
-def sun_spectrum(lambda_nm: np.ndarray, temp_k: float = 5778.0) -> np.ndarray:
-    """Sun radiance inside its cone: black body normalised to 1 at 560 nm."""
-    return planck(lambda_nm, temp_k) / planck(np.array([560.0]), temp_k)[0]
+def rayleigh_optical_depth(lambda_nm: np.ndarray) -> np.ndarray:
+    """Vertical Rayleigh optical depth of the standard sea-level atmosphere,
+    Hansen and Travis (Space Sci. Rev. 16, 1974) fit with lambda in um:
+    tau = 0.008569 lambda^-4 (1 + 0.0113 lambda^-2 + 0.00013 lambda^-4)."""
+    l2 = (np.asarray(lambda_nm, np.float64) * 1e-3) ** -2
+    return 0.008569 * l2 * l2 * (1.0 + 0.0113 * l2 + 0.00013 * l2 * l2)
+
+
+def air_mass(elevation_deg: float) -> float:
+    """Relative optical air mass at solar elevation h (degrees), Kasten and
+    Young (Appl. Opt. 28, 1989): 1 / (sin h + 0.50572 (h + 6.07995)^-1.6364)."""
+    h = float(elevation_deg)
+    if not -6.0 < h <= 90.0:
+        raise ValueError("elevation out of range")
+    return 1.0 / (math.sin(math.radians(h)) + 0.50572 * (h + 6.07995) ** -1.6364)
+
+
+def sun_spectrum(lambda_nm: np.ndarray, temp_k: float = 5778.0, elevation_deg: Optional[float] = None) -> np.ndarray:
+    """Sun radiance inside its cone: black body normalised to 1 at 560 nm.
+    With an elevation, the direct beam is attenuated by Rayleigh scattering
+    along the air mass of that elevation, exp(-tau(lambda) m(h)) (section 3:
+    the sun's spectrum seen from the ground changes with the hour of the
+    day; a low sun is redder)."""
+    s = planck(lambda_nm, temp_k) / planck(np.array([560.0]), temp_k)[0]
+    if elevation_deg is not None:
+        s = s * np.exp(-rayleigh_optical_depth(lambda_nm) * air_mass(elevation_deg))
+    return s
 
 
 def _lobe(lam, mu, s1, s2):
@@ -348,7 +372,7 @@ def prism_room(width=96, height=72, n_bands=16, spp=4, depth=8, seed=0) -> Workl
     n[PRISM] = cauchy_n(lam, 1.62, 0.012)
     k[PRISM] = 2e-8
     sun = sun_direction(35.0, 200.0)
-    spec = _spectra(lam, sun_spectrum(lam), sun, 0.25, n, k, rho, le)
+    spec = _spectra(lam, sun_spectrum(lam, elevation_deg=35.0), sun, 0.25, n, k, rho, le)
     cam = Camera((3.4, 1.4, 0.6), (2.0, 0.3, 3.1), (0.0, 1.0, 0.0), 45.0, width, height)
     return Workload("prism_room", scene, spec, [cam], spp, depth, seed)
 

@@ -54,3 +54,40 @@ def test_cmf_weights_normalised():
         lam = scenes.band_wavelengths(lo, hi, B)
         w = scenes.xyz_weights(lam)
         assert abs(w[:, 1].sum() - 1.0) < 1e-12
+
+
+def test_rayleigh_optical_depth_published_values():
+    # sea-level Rayleigh optical depth: about 0.364 at 400 nm, 0.097 at
+    # 550 nm and 0.036 at 700 nm (published sea-level values, e.g. Bucholtz,
+    # Appl. Opt. 34, 1995)
+    tau = scenes.rayleigh_optical_depth(np.array([400.0, 550.0, 700.0]))
+    np.testing.assert_allclose(tau, [0.364, 0.0973, 0.0362], rtol=0.02)
+    # close to the lambda^-4 law, a little steeper
+    r = tau[0] / tau[2]
+    assert (700.0 / 400.0) ** 4 < r < (700.0 / 400.0) ** 4.2
+
+
+def test_air_mass_published_values():
+    # Kasten and Young's formula: 1 at the zenith, about 1/sin h for a high
+    # sun, 37.9 at the horizon
+    assert abs(scenes.air_mass(90.0) - 1.0) < 1e-3
+    assert abs(scenes.air_mass(30.0) - 2.0) < 0.01
+    assert abs(scenes.air_mass(0.0) - 37.92) < 0.05
+    ms = [scenes.air_mass(h) for h in (90, 60, 30, 10, 5, 0)]
+    assert all(a < b for a, b in zip(ms, ms[1:]))
+
+
+def test_low_sun_is_redder():
+    lam = scenes.band_wavelengths(400, 700, 16)
+    top = scenes.sun_spectrum(lam)
+    prev = None
+    for h in (90.0, 35.0, 10.0, 2.0):
+        s = scenes.sun_spectrum(lam, elevation_deg=h)
+        assert np.all(s < top) and np.all(s > 0)
+        ratio = s[0] / s[-1]   # blue over red
+        if prev is not None:
+            assert ratio < prev
+        prev = ratio
+    wl = scenes.prism_room()
+    np.testing.assert_allclose(wl.spectra.sun_L, scenes.sun_spectrum(wl.spectra.lambda_nm.astype(np.float64),
+                                                                     elevation_deg=35.0), rtol=1e-6)
