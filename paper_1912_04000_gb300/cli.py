@@ -20,6 +20,9 @@ def _workload(args):
     if args.workload == "nave":
         return scenes.nave(width=args.width or 1024, height=args.height or 768, spp=args.spp or 16,
                            depth=args.depth or 8, seed=args.seed, n_bands=args.bands or 81)
+    if args.workload == "crystal_nave":
+        return scenes.crystal_nave(width=args.width or 1024, height=args.height or 768, spp=args.spp or 16,
+                                   depth=args.depth or 8, seed=args.seed, n_bands=args.bands or 81)
     if args.workload == "nave_views":
         wl = scenes.nave_views(n_views=args.views or 32, spp=args.spp or 8, depth=args.depth or 8, seed=args.seed)
         return wl
@@ -33,7 +36,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(prog="paper_1912_04000_gb300.cli")
     sub = ap.add_subparsers(dest="cmd", required=True)
     r = sub.add_parser("render")
-    r.add_argument("--workload", default="nave", choices=["tiny_box", "nave", "nave_views", "large_nave"])
+    r.add_argument("--workload", default="nave", choices=["tiny_box", "nave", "crystal_nave", "nave_views", "large_nave"])
     r.add_argument("--width", type=int, default=0)
     r.add_argument("--height", type=int, default=0)
     r.add_argument("--spp", type=int, default=0)

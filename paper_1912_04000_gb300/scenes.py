@@ -630,6 +630,74 @@ def nave(width=1024, height=768, n_bands=81, spp=16, depth=8, seed=0, scene_key=
     return Workload("nave", scene, spec, [cam], spp, depth, seed)
 
 
+def _icosphere(level: int):
+    """Unit sphere from a subdivided icosahedron: 20 * 4^level triangles."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.asarray(p, np.float64) / np.linalg.norm(p) for p in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+             (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+
+        def m(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                q = verts[a] + verts[b]
+                verts.append(q / np.linalg.norm(q))
+                mid[key] = len(verts) - 1
+            return mid[key]
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = m(a, b), m(b, c), m(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return np.array(verts), faces
+
+
+def crystal_nave(width=1024, height=768, n_bands=81, spp=16, depth=8, seed=0, scene_key=1, n_solids=8,
+                 col_seg=64, col_rings=64) -> Workload:
+    """The procedural nave with solid refracting glass in the sunlit aisle:
+    n_solids objects on the centre line, alternating faceted spheres (320
+    triangles, crown glass) and triangular prisms (flint glass, a blue
+    absorption band), under a sun whose spectrum is Rayleigh-attenuated for
+    its 35 degree elevation."""
+    base = nave(width=width, height=height, n_bands=n_bands, spp=spp, depth=depth, seed=seed,
+                scene_key=scene_key, col_seg=col_seg, col_rings=col_rings)
+    lam = band_wavelengths(380.0, 780.0, n_bands)
+    n_old = base.scene.n_mat
+    CROWN, FLINT = n_old, n_old + 1
+    mb = MeshBuilder()
+    mb.add_arrays(base.scene.verts.astype(np.float64), base.scene.tris, 0)
+    mb.mats[:] = [int(m) for m in base.scene.mat_id]
+    sv, sf = _icosphere(2)
+    for i in range(n_solids):
+        xc = 15.0 + 50.0 * i / max(1, n_solids - 1)
+        if i % 2 == 0:
+            r, c = 0.8, np.array([xc, 1.2, 10.0])
+            _solid(mb, [[tuple(c + r * sv[a]) for a in f] for f in sf], CROWN)
+        else:
+            a, h, y0 = 1.2, 1.2 * math.sqrt(3.0) / 2.0, 0.4
+            tri0 = [(xc - 0.5 * a, y0, 9.0), (xc + 0.5 * a, y0, 9.0), (xc, y0 + h, 9.0)]
+            tri1 = [(x, y, 11.0) for (x, y, _) in tri0]
+            faces = [tri0, tri1] + [[tri0[j], tri0[(j + 1) % 3], tri1[(j + 1) % 3], tri1[j]] for j in range(3)]
+            _solid(mb, faces, FLINT)
+    sc = mb.build(list(base.scene.mat_type) + [DIELECTRIC, DIELECTRIC],
+                  list(base.scene.mat_thickness) + [0.0, 0.0])
+    sp = base.spectra
+    B = n_bands
+    n = np.concatenate([sp.n.astype(np.float64), np.stack([cauchy_n(lam, 1.52, 0.0042), cauchy_n(lam, 1.62, 0.012)])])
+    k = np.concatenate([sp.k.astype(np.float64), np.stack([np.full(B, 1e-8),
+                                                          1e-8 + 3e-7 * np.exp(-0.5 * ((lam - 600.0) / 40.0) ** 2)])])
+    rho = np.concatenate([sp.rho.astype(np.float64), np.zeros((2, B))])
+    le = np.concatenate([sp.le.astype(np.float64), np.zeros((2, B))])
+    spec = _spectra(lam, sun_spectrum(lam, elevation_deg=35.0), sp.sun_dir.astype(np.float64), sp.sun_half_angle,
+                    n, k, rho, le)
+    return Workload("crystal_nave", sc, spec, base.cameras, spp, depth, seed)
+
+
 def nave_views(n_views=32, n_bands=81, spp=8, depth=8, seed=0, view_key=2, base=None) -> Workload:
     """32 seeded camera views of the nave at uneven resolutions: W and H each
     uniform in {256, 272, ..., 1024}."""

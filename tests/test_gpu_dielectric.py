@@ -118,3 +118,47 @@ def test_prism_room_guided_unbiased(R):
     assert np.isfinite(guided).all() and (guided >= 0).all()
     d = (guided - plain).ravel()
     assert abs(d.mean()) / (d.std() / np.sqrt(d.size)) < 5.0
+
+
+def _project(cam, X):
+    """Pixel (x, y) of point X for the pinhole camera (vertical field of view,
+    y growing downwards)."""
+    pos = np.asarray(cam.pos, np.float64)
+    f = np.asarray(cam.look, np.float64) - pos
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(cam.up, np.float64))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    v = np.asarray(X, np.float64) - pos
+    th = math.tan(math.radians(cam.vfov_deg) / 2.0)
+    asp = cam.width / cam.height
+    xc, yc = (v @ r) / (v @ f), (v @ u) / (v @ f)
+    return int((xc / (th * asp) + 1.0) / 2.0 * cam.width), int((1.0 - yc / th) / 2.0 * cam.height)
+
+
+def test_crystal_nave_sampled_pixels(R):
+    """The nave with eight solid glass objects (spheres and dispersive
+    prisms) at its full size, 1024 x 768, 81 bands, 16 spp, depth 8; pixels
+    that look at the solids are re-rendered path by path by the oracle."""
+    wl = scenes.crystal_nave()
+    cam = wl.cameras[0]
+    pix = []
+    for i in range(8):
+        xc = 15.0 + 50.0 * i / 7
+        y = 1.2 if i % 2 == 0 else 0.8
+        px, py = _project(cam, (xc, y, 10.0))
+        for dx, dy in ((0, 0), (3, 1), (-2, 2), (1, -3), (-4, -1), (2, 4)):
+            pix.append((py + dy) * cam.width + px + dx)
+    pix = np.array(sorted(set(pix)), np.int64)
+    R.load(wl)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, probe_pixels=pix, xyz_mode=2)
+    o = _oracle(wl, pixels=pix.astype(np.uint32), record_paths=True)
+    gS = out["probe_sig"].cpu().numpy().view(np.uint32)
+    gL = out["probe_L"].cpu().numpy()
+    same = gS == o["path_sig"]
+    print("crystal nave: paths with identical event signatures", same.mean())
+    assert same.mean() >= 0.99
+    np.testing.assert_allclose(gL[same], o["path_L"][same], rtol=1e-4, atol=1e-7)
+    clean = same.reshape(len(pix), -1).all(1)
+    assert clean.mean() > 0.5
+    assert_parity(out["xyz"].cpu().numpy()[pix][clean], o["xyz"][clean], "crystal nave clean pixels")

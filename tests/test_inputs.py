@@ -1,5 +1,8 @@
 """Seeded input generators: sizes and structure of the synthetic workloads."""
+import math
+
 import numpy as np
+import pytest
 
 from paper_1912_04000_gb300 import scenes
 
@@ -91,3 +94,26 @@ def test_low_sun_is_redder():
     wl = scenes.prism_room()
     np.testing.assert_allclose(wl.spectra.sun_L, scenes.sun_spectrum(wl.spectra.lambda_nm.astype(np.float64),
                                                                      elevation_deg=35.0), rtol=1e-6)
+
+
+def test_crystal_nave_solids():
+    wl = scenes.crystal_nave(width=32, height=24)
+    base = scenes.nave(width=32, height=24)
+    sc = wl.scene
+    nb = base.scene.n_tris
+    assert sc.n_tris == nb + 4 * 320 + 4 * 8
+    assert np.array_equal(sc.mat_id[:nb], base.scene.mat_id)
+    assert list(sc.mat_type[-2:]) == [scenes.DIELECTRIC, scenes.DIELECTRIC]
+    crown, flint = sc.n_mat - 2, sc.n_mat - 1
+
+    def volume(m):
+        t = sc.verts[sc.tris[sc.mat_id == m]].astype(np.float64)
+        return np.einsum("ij,ij->i", t[:, 0], np.cross(t[:, 1], t[:, 2])).sum() / 6.0
+
+    # outward winding gives positive volumes: four 1.2 m prisms 2 m long and
+    # four 320-face spheres of radius 0.8 (a little under the true sphere)
+    assert volume(flint) == pytest.approx(4 * (math.sqrt(3.0) / 4.0 * 1.2 ** 2) * 2.0, rel=1e-5)
+    vs = 4 * 4.0 / 3.0 * math.pi * 0.8 ** 3
+    assert 0.95 * vs < volume(crown) < vs
+    # dispersion: the flint bends blue more than red
+    assert wl.spectra.n[flint][0] > wl.spectra.n[flint][-1] > 1.6
