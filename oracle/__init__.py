@@ -95,6 +95,8 @@ def lib():
                                     C.c_uint32, C.c_uint32, C.c_uint64, C.POINTER(C.c_uint32), C.c_uint64,
                                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_uint32),
                                     C.c_int]
+            L.or_render4.restype = C.c_int
+            L.or_render4.argtypes = L.or_render.argtypes
             L.or_xyz.argtypes = [C.POINTER(C.c_double), C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.POINTER(C.c_float), C.POINTER(C.c_double)]
             L.or_hardware_threads.restype = C.c_int
@@ -235,11 +237,14 @@ class OracleScene:
         return T, g
 
     def render(self, cameras, spp, depth, seed=0, band_first=0, band_count=None, pixels=None,
-               record_paths=False, n_threads=0):
+               record_paths=False, n_threads=0, bands_per_path=1):
         """FP64 spectral sums over samples for the listed global pixels.
 
         Returns dict(spectral_sum [n_pix, band_count], xyz [n_pix, 3], and with
-        record_paths path_L / path_sig [n_pix, spp, band_count])."""
+        record_paths path_L / path_sig [n_pix, spp, band_count]).
+        bands_per_path = 4: every path carries four consecutive bands."""
+        if bands_per_path not in (1, 4):
+            raise ValueError("bands_per_path is 1 or 4")
         if band_count is None:
             band_count = self.n_bands - band_first
         n_all = sum(c.width * c.height for c in cameras)
@@ -249,7 +254,8 @@ class OracleScene:
         pl = np.zeros((npx, spp, band_count), np.float64) if record_paths else None
         ps = np.zeros((npx, spp, band_count), np.uint32) if record_paths else None
         cams = cameras_struct(cameras)
-        rc = lib().or_render(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
+        fn = lib().or_render if bands_per_path == 1 else lib().or_render4
+        rc = fn(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
                              _ptr(pix, C.c_uint32), npx, _ptr(ssum, C.c_double),
                              _ptr(pl, C.c_double) if pl is not None else None,
                              _ptr(ps, C.c_uint32) if ps is not None else None, n_threads)

@@ -404,6 +404,49 @@ typedef struct {
   uint32_t width, height;
 } or_camera;
 
+}  // extern "C"
+
+namespace {
+
+std::vector<OCam> setup_cams(const or_camera* cams, uint32_t n_cams) {
+  std::vector<OCam> oc(n_cams);
+  uint64_t off = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) {
+    const or_camera& c = cams[v];
+    V3 pos{c.pos[0], c.pos[1], c.pos[2]}, look{c.look[0], c.look[1], c.look[2]}, up{c.up[0], c.up[1], c.up[2]};
+    oc[v].pos = pos;
+    oc[v].f = normalize(look - pos);
+    oc[v].r = normalize(cross(oc[v].f, up));
+    oc[v].u = cross(oc[v].r, oc[v].f);
+    oc[v].th = std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
+    oc[v].aspect = (double)c.width / (double)c.height;
+    oc[v].W = c.width;
+    oc[v].H = c.height;
+    oc[v].offset = off;
+    off += (uint64_t)c.width * c.height;
+  }
+  return oc;
+}
+
+// Primary ray of global pixel pix, sample s, Philox stream of band b.
+void camera_ray(const std::vector<OCam>& oc, uint32_t pix, uint32_t s, uint32_t b, uint32_t k0, uint32_t k1, V3* o,
+                V3* d) {
+  uint32_t v = 0;
+  while (v + 1 < oc.size() && oc[v + 1].offset <= pix) ++v;
+  const OCam& C = oc[v];
+  uint32_t local = pix - (uint32_t)C.offset;
+  uint32_t x = local % C.W, y = local / C.W;
+  Ctr4 r0 = philox4x32_10(Ctr4{{pix, s, b, 0u}}, k0, k1);
+  double sx = (2.0 * ((double)x + u01(r0.w[0])) / C.W - 1.0) * C.th * C.aspect;
+  double sy = (1.0 - 2.0 * ((double)y + u01(r0.w[1])) / C.H) * C.th;
+  *d = normalize(C.f + sx * C.r + sy * C.u);
+  *o = C.pos;
+}
+
+}  // namespace
+
+extern "C" {
+
 void or_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]) {
   Ctr4 c{{ctr[0], ctr[1], ctr[2], ctr[3]}};
   Ctr4 r = philox4x32_10(c, key[0], key[1]);
@@ -519,38 +562,14 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
               int n_threads) {
   const OScene& S = *(OScene*)scene;
   if (band_first + band_count > S.B || depth == 0) return 1;
-  std::vector<OCam> oc(n_cams);
-  uint64_t off = 0;
-  for (uint32_t v = 0; v < n_cams; ++v) {
-    const or_camera& c = cams[v];
-    V3 pos{c.pos[0], c.pos[1], c.pos[2]}, look{c.look[0], c.look[1], c.look[2]}, up{c.up[0], c.up[1], c.up[2]};
-    oc[v].pos = pos;
-    oc[v].f = normalize(look - pos);
-    oc[v].r = normalize(cross(oc[v].f, up));
-    oc[v].u = cross(oc[v].r, oc[v].f);
-    oc[v].th = std::tan(0.5 * (double)c.vfov_deg * M_PI / 180.0);
-    oc[v].aspect = (double)c.width / (double)c.height;
-    oc[v].W = c.width;
-    oc[v].H = c.height;
-    oc[v].offset = off;
-    off += (uint64_t)c.width * c.height;
-  }
+  const std::vector<OCam> oc = setup_cams(cams, n_cams);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   // f / pdf for the sun cone: (rho / pi) * 2 pi (1 - cos_max) = rho * cone_w
   const double cone_w = 2.0 * (1.0 - S.cos_max);
 
   auto trace = [&](uint32_t pix, uint32_t s, uint32_t b, uint32_t* sig_out) -> double {
-    // locate the view
-    uint32_t v = 0;
-    while (v + 1 < n_cams && oc[v + 1].offset <= pix) ++v;
-    const OCam& C = oc[v];
-    uint32_t local = pix - (uint32_t)C.offset;
-    uint32_t x = local % C.W, y = local / C.W;
-    Ctr4 r0 = philox4x32_10(Ctr4{{pix, s, b, 0u}}, k0, k1);
-    double sx = (2.0 * ((double)x + u01(r0.w[0])) / C.W - 1.0) * C.th * C.aspect;
-    double sy = (1.0 - 2.0 * ((double)y + u01(r0.w[1])) / C.H) * C.th;
-    V3 d = normalize(C.f + sx * C.r + sy * C.u);
-    V3 o = C.pos;
+    V3 o, d;
+    camera_ray(oc, pix, s, b, k0, k1, &o, &d);
     double T = 1.0, L = 0.0;
     bool covered = false;  // direct sun along this segment is already counted by NEE
     uint32_t sig = 2166136261u;
@@ -665,6 +684,203 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
           size_t pi = ((size_t)i * spp + s) * band_count + j;
           if (path_L) path_L[pi] = L;
           if (path_sig) path_sig[pi] = sg;
+        }
+    }
+  };
+  int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+// The same estimate with four bands per path (band_first + 4 g .. + 3 for
+// path unit g; the last group may have fewer).  The bands share the path's
+// geometry; Philox counters are those of the group's first band.  At each
+// vertex the "carried" bands are those with throughput != 0 (all existing
+// bands if none is):
+//   Lambertian / emissive: shared sun-ray direction and cosine continuation,
+//     per-band emission, NEE (sun-ray transmittance per band) and rho;
+//   thin glass: reflect if u < p = mean over carried bands of
+//     R_s / (R_s + T_s); then each band is weighted R_s / p, else T_s / (1 - p);
+//   conductor: mirror, each band weighted by its R;
+//   solid glass: reflect if u < p = mean carried Fresnel R; each band
+//     weighted R / p; else refraction, which bends every band differently:
+//     the carried band of rank floor(u' m) (m carried bands) continues with
+//     weight m (1 - R) / (1 - p), the others carry nothing further; a band
+//     past its critical angle has R = 1 and so weight 0.
+// Every choice keeps each band's one-band expectation.  spectral_sum,
+// path_L and path_sig are laid out as in or_render.
+int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
+               uint32_t spp, uint32_t depth, uint64_t seed, const uint32_t* pixels, uint64_t n_pixels,
+               double* spectral_sum, double* path_L, uint32_t* path_sig, int n_threads) {
+  const OScene& S = *(OScene*)scene;
+  if (band_first + band_count > S.B || depth == 0) return 1;
+  const std::vector<OCam> oc = setup_cams(cams, n_cams);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const double cone_w = 2.0 * (1.0 - S.cos_max);
+  const uint32_t groups = (band_count + 3) / 4;
+
+  // radiance of bands b0 .. b0 + nv - 1 of one path into L[0..nv)
+  auto trace4 = [&](uint32_t pix, uint32_t s, uint32_t b0, uint32_t nv, double* L, uint32_t* sig_out) {
+    V3 o, d;
+    camera_ray(oc, pix, s, b0, k0, k1, &o, &d);
+    double T[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint32_t q = 0; q < nv; ++q) {
+      T[q] = 1.0;
+      L[q] = 0.0;
+    }
+    bool covered = false;
+    uint32_t sig = 2166136261u;
+    for (uint32_t k = 1; k <= depth; ++k) {
+      double t;
+      uint32_t prim;
+      if (!closest(S, o, d, &t, &prim)) {
+        sig = mix(sig, 0xFFFFFFFFu);
+        if (!covered && dot(d, S.sun) >= S.cos_max)
+          for (uint32_t q = 0; q < nv; ++q) L[q] += T[q] * S.sunL[b0 + q];
+        break;
+      }
+      sig = mix(sig, prim);
+      V3 p = o + t * d;
+      V3 ng = normalize(cross(S.b[prim] - S.a[prim], S.c[prim] - S.a[prim]));
+      V3 n = dot(ng, d) < 0.0 ? ng : -1.0 * ng;
+      double cos_i = -dot(d, n);
+      uint32_t m = S.mat[prim];
+      size_t mb = (size_t)m * S.B + b0;
+      int type = S.mtype[m];
+      // carried bands
+      bool carried[4] = {false, false, false, false};
+      uint32_t n_car = 0;
+      for (uint32_t q = 0; q < nv; ++q)
+        if (T[q] != 0.0) {
+          carried[q] = true;
+          ++n_car;
+        }
+      if (n_car == 0) {
+        for (uint32_t q = 0; q < nv; ++q) carried[q] = true;
+        n_car = nv;
+      }
+      Ctr4 r = philox4x32_10(Ctr4{{pix, s, b0, 4u * k}}, k0, k1);
+      if (type == M_LAMBERT || type == M_EMISSIVE) {
+        if (type == M_EMISSIVE)
+          for (uint32_t q = 0; q < nv; ++q) L[q] += T[q] * S.le[mb + q];
+        double ct = 1.0 - u01(r.w[0]) * (1.0 - S.cos_max);
+        double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+        double ph = 2.0 * M_PI * u01(r.w[1]);
+        V3 t1, t2;
+        onb(S.sun, &t1, &t2);
+        V3 w = (st * std::cos(ph)) * t1 + (st * std::sin(ph)) * t2 + ct * S.sun;
+        double c = dot(n, w);
+        if (c > 0.0) {
+          uint32_t ngl = 0;
+          for (uint32_t q = 0; q < nv; ++q) {
+            double Tr = shadow_T(S, p + S.eps * n, w, b0 + q, &ngl);
+            L[q] += T[q] * S.rho[mb + q] * c * S.sunL[b0 + q] * cone_w * Tr;
+          }
+          sig = mix(sig, ngl);
+        }
+        if (k == depth) break;
+        double rr = std::sqrt(u01(r.w[2]));
+        double ph2 = 2.0 * M_PI * u01(r.w[3]);
+        double z = std::sqrt(std::max(0.0, 1.0 - u01(r.w[2])));
+        V3 b1, b2;
+        onb(n, &b1, &b2);
+        d = (rr * std::cos(ph2)) * b1 + (rr * std::sin(ph2)) * b2 + z * n;
+        o = p + S.eps * n;
+        for (uint32_t q = 0; q < nv; ++q) T[q] *= S.rho[mb + q];
+        covered = true;
+      } else if (type == M_GLASS) {
+        double Rs[4], Ts[4];
+        for (uint32_t q = 0; q < nv; ++q) slab(cos_i, S.ntab[mb + q], S.ktab[mb + q], S.lam[b0 + q], S.mthick[m], &Rs[q], &Ts[q]);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b0, 4u * k + 1u}}, k0, k1);
+        double pr = 0.0;
+        for (uint32_t q = 0; q < nv; ++q)
+          if (carried[q]) pr += Rs[q] / (Rs[q] + Ts[q]);
+        pr /= n_car;
+        if (u01(r1.w[0]) < pr) {
+          for (uint32_t q = 0; q < nv; ++q) T[q] *= Rs[q] / pr;
+          d = d - (2.0 * dot(d, n)) * n;
+          o = p + S.eps * n;
+          covered = false;
+        } else {
+          for (uint32_t q = 0; q < nv; ++q) T[q] *= Ts[q] / (1.0 - pr);
+          o = p - S.eps * n;
+        }
+      } else if (type == M_DIELECTRIC) {
+        const bool inside = dot(ng, d) > 0.0;
+        double alpha[4];
+        for (uint32_t q = 0; q < nv; ++q) {
+          alpha[q] = 4.0 * M_PI * S.ktab[mb + q] / (S.lam[b0 + q] * 1e-9);
+          if (inside) T[q] *= std::exp(-alpha[q] * t);
+        }
+        if (k == depth) break;
+        double R[4], eta[4];
+        for (uint32_t q = 0; q < nv; ++q) {
+          eta[q] = inside ? 1.0 / S.ntab[mb + q] : S.ntab[mb + q];
+          R[q] = fresnel_complex(cos_i, eta[q], 0.0);
+        }
+        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b0, 4u * k + 1u}}, k0, k1);
+        double pr = 0.0;
+        for (uint32_t q = 0; q < nv; ++q)
+          if (carried[q]) pr += R[q];
+        pr /= n_car;
+        if (u01(r1.w[0]) < pr) {
+          for (uint32_t q = 0; q < nv; ++q) T[q] *= R[q] / pr;
+          d = d - (2.0 * dot(d, n)) * n;
+        } else {
+          const uint32_t rank = std::min((uint32_t)(u01(r1.w[1]) * n_car), n_car - 1);
+          uint32_t c = 0, seen = 0;
+          for (uint32_t q = 0; q < nv; ++q)
+            if (carried[q]) {
+              if (seen == rank) c = q;
+              ++seen;
+            }
+          const double wgt = n_car * (1.0 - R[c]) / (1.0 - pr);
+          for (uint32_t q = 0; q < nv; ++q) T[q] = q == c ? T[q] * wgt : 0.0;
+          V3 tdir;
+          if (refract(d, n, eta[c], &tdir)) d = normalize(tdir);
+          else d = d - (2.0 * dot(d, n)) * n;  // R = 1: the weight is 0
+        }
+        const double step = S.eps / std::max(std::fabs(dot(d, n)), 0.0625);
+        if (dot(d, ng) < 0.0)
+          for (uint32_t q = 0; q < nv; ++q) T[q] *= std::exp(-alpha[q] * step);
+        o = p + step * d;
+        covered = false;
+      } else {  // conductor
+        double R[4];
+        for (uint32_t q = 0; q < nv; ++q) R[q] = fresnel_complex(cos_i, S.ntab[mb + q], S.ktab[mb + q]);
+        if (k == depth) break;
+        d = d - (2.0 * dot(d, n)) * n;
+        o = p + S.eps * n;
+        for (uint32_t q = 0; q < nv; ++q) T[q] *= R[q];
+        covered = false;
+      }
+    }
+    if (sig_out) *sig_out = sig;
+  };
+
+  std::atomic<uint64_t> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      uint64_t i = next.fetch_add(1);
+      if (i >= n_pixels) break;
+      uint32_t pix = pixels[i];
+      for (uint32_t j = 0; j < band_count; ++j) spectral_sum[i * band_count + j] = 0.0;
+      for (uint32_t s = 0; s < spp; ++s)
+        for (uint32_t g = 0; g < groups; ++g) {
+          const uint32_t nv = std::min(4u, band_count - 4 * g);
+          double L[4];
+          uint32_t sg = 0;
+          trace4(pix, s, band_first + 4 * g, nv, L, path_sig ? &sg : nullptr);
+          for (uint32_t q = 0; q < nv; ++q) {
+            const uint32_t j = 4 * g + q;
+            spectral_sum[i * band_count + j] += L[q];
+            size_t pi = ((size_t)i * spp + s) * band_count + j;
+            if (path_L) path_L[pi] = L[q];
+            if (path_sig) path_sig[pi] = sg;
+          }
         }
     }
   };
