@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=1536, help="oracle sample size (pixels at full spp/bands)")
     ap.add_argument("--guided-mse", action="store_true",
                     help="equal-time MSE of the guided vs the plain tracer against a high-spp plain reference")
+    ap.add_argument("--bands-mse", action="store_true",
+                    help="equal-time MSE, four bands per path vs one (nave or crystal nave)")
+    ap.add_argument("--bands-workload", default="nave", choices=["nave", "crystal_nave"])
     ap.add_argument("--mse-width", type=int, default=256)
     ap.add_argument("--mse-height", type=int, default=192)
     ap.add_argument("--mse-ref-spp", type=int, default=4096)
@@ -283,8 +286,67 @@ def run_guided_mse(args):
     return 0
 
 
+def run_bands_mse(args):
+    """Equal-time MSE of four bands per path against one band per path on a
+    nave view at reduced resolution; the reference is the one-band tracer at
+    --mse-ref-spp with an independent seed."""
+    import numpy as np
+    import torch
+
+    from paper_1912_04000_gb300 import scenes
+    from paper_1912_04000_gb300.renderer import Renderer
+
+    make = scenes.crystal_nave if args.bands_workload == "crystal_nave" else scenes.nave
+    wl = make(width=args.mse_width, height=args.mse_height)
+    R = Renderer(0).load(wl)
+    dev = R.device
+    P, B = wl.n_pixels, wl.band_count
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize(dev)
+        return out, time.perf_counter() - t0
+
+    def run(spp, seed, bpp):
+        sp = torch.zeros((P, B), dtype=torch.float64, device=dev)
+        out, t = timed(lambda: R.render(wl.cameras, spp, wl.depth, seed, out_spectral=sp, bands_per_path=bpp))
+        return out["xyz"].cpu().numpy().astype(np.float64), sp.cpu().numpy() / spp, t, out["stats"]
+
+    ref_xyz, ref_sp, t_ref, _ = run(args.mse_ref_spp, 777, 1)
+
+    def errs(x, s):
+        return {"mse_xyz": float(np.mean((x - ref_xyz) ** 2)), "mse_spectral": float(np.mean((s - ref_sp) ** 2))}
+
+    run(8, 5, 4)  # warm both paths
+    run(8, 5, 1)
+    spp1 = args.mse_spp
+    x1, s1, t1, st1 = run(spp1, 0, 1)
+    _, _, t4probe, _ = run(spp1, 0, 4)
+    spp4 = max(1, int(round(spp1 * t1 / t4probe)))
+    x4, s4, t4, st4 = run(spp4, 0, 4)
+    e1, e4 = errs(x1, s1), errs(x4, s4)
+    line = {
+        "metric": "equal-time MSE, four bands per path vs one (XYZ and spectral, vs a one-band reference)",
+        "config": {"workload": f"{args.bands_workload}_{args.mse_width}x{args.mse_height}_b{B}_d{wl.depth}",
+                   "reference_spp": args.mse_ref_spp},
+        "one_band": {"spp": spp1, "seconds": t1, "estimates_per_s": st1["paths"] / t1, "ext_rays": st1["ext_rays"],
+                     **e1},
+        "four_bands": {"spp": spp4, "seconds": t4, "estimates_per_s": st4["paths"] / t4,
+                       "ext_rays": st4["ext_rays"], **e4},
+        "mse_xyz_ratio_one_over_four_equal_time": e1["mse_xyz"] / max(e4["mse_xyz"], 1e-300),
+        "mse_spectral_ratio_one_over_four_equal_time": e1["mse_spectral"] / max(e4["mse_spectral"], 1e-300),
+        "reference_seconds": t_ref,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.bands_mse:
+        return run_bands_mse(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.guided_mse:

@@ -124,11 +124,24 @@ typedef struct {
   uint32_t ray_order;      /* 0 = queue order; 1 = rays of vertices >= 2 and sun rays traced in the
                             * order of a counting sort by origin cell (and direction octant): the
                             * same result, measured no faster on the nave */
-  uint32_t reserved[3];
+  uint32_t bands_per_path; /* 0 or 1: every path carries one band (the method as specified);
+                            * 4: path j of a pixel and sample carries the range's bands j + q G,
+                            * q = 0..3, G = ceil(band_count / 4) (those inside the range), spread
+                            * over the spectrum; they share its geometry until the first dispersive
+                            * event (refraction into or out of solid glass), where one of them,
+                            * chosen uniformly, goes on with weight n (1 - R) / (1 - p); thin-glass
+                            * and solid-glass reflections choose with the bands' mean probability
+                            * and weight each band by its own.  The same expectation per band; one
+                            * closest-hit and one sun ray serve four bands.  The grouping depends
+                            * on the band range, so disjoint ranges are independent estimates
+                            * rather than bit-exact pieces of one render.  Excludes guided
+                            * sampling and trace_variant != 0.  rt_stats.paths counts (pixel,
+                            * sample, band) estimates in both modes */
+  uint32_t reserved[2];
 } rt_render_opts;
 
 typedef struct {
-  uint64_t paths;          /* spectral paths traced */
+  uint64_t paths;          /* spectral (pixel, sample, band) estimates: paths traced x bands per path */
   uint64_t ext_rays;       /* closest-hit rays traced */
   uint64_t shadow_rays;    /* sun rays traced */
   uint64_t nodes_visited;  /* closest-hit BVH nodes, only with rt_set_counting(ctx, 1) */

@@ -694,9 +694,10 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
   return 0;
 }
 
-// The same estimate with four bands per path (band_first + 4 g .. + 3 for
-// path unit g; the last group may have fewer).  The bands share the path's
-// geometry; Philox counters are those of the group's first band.  At each
+// The same estimate with four bands per path: path unit g of a pixel and
+// sample carries bands band_first + g + q G, q = 0..3, G = ceil(band_count
+// / 4), those inside the range.  The bands share the path's geometry;
+// Philox counters are those of band g.  At each
 // vertex the "carried" bands are those with throughput != 0 (all existing
 // bands if none is):
 //   Lambertian / emissive: shared sun-ray direction and cosine continuation,
@@ -721,8 +722,8 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
   const double cone_w = 2.0 * (1.0 - S.cos_max);
   const uint32_t groups = (band_count + 3) / 4;
 
-  // radiance of bands b0 .. b0 + nv - 1 of one path into L[0..nv)
-  auto trace4 = [&](uint32_t pix, uint32_t s, uint32_t b0, uint32_t nv, double* L, uint32_t* sig_out) {
+  // radiance of bands b0 + q G, q < nv, of one path into L[0..nv)
+  auto trace4 = [&](uint32_t pix, uint32_t s, uint32_t b0, uint32_t G, uint32_t nv, double* L, uint32_t* sig_out) {
     V3 o, d;
     camera_ray(oc, pix, s, b0, k0, k1, &o, &d);
     double T[4] = {0.0, 0.0, 0.0, 0.0};
@@ -738,7 +739,7 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
       if (!closest(S, o, d, &t, &prim)) {
         sig = mix(sig, 0xFFFFFFFFu);
         if (!covered && dot(d, S.sun) >= S.cos_max)
-          for (uint32_t q = 0; q < nv; ++q) L[q] += T[q] * S.sunL[b0 + q];
+          for (uint32_t q = 0; q < nv; ++q) L[q] += T[q] * S.sunL[b0 + q * G];
         break;
       }
       sig = mix(sig, prim);
@@ -764,7 +765,7 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
       Ctr4 r = philox4x32_10(Ctr4{{pix, s, b0, 4u * k}}, k0, k1);
       if (type == M_LAMBERT || type == M_EMISSIVE) {
         if (type == M_EMISSIVE)
-          for (uint32_t q = 0; q < nv; ++q) L[q] += T[q] * S.le[mb + q];
+          for (uint32_t q = 0; q < nv; ++q) L[q] += T[q] * S.le[mb + q * G];
         double ct = 1.0 - u01(r.w[0]) * (1.0 - S.cos_max);
         double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
         double ph = 2.0 * M_PI * u01(r.w[1]);
@@ -775,8 +776,8 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
         if (c > 0.0) {
           uint32_t ngl = 0;
           for (uint32_t q = 0; q < nv; ++q) {
-            double Tr = shadow_T(S, p + S.eps * n, w, b0 + q, &ngl);
-            L[q] += T[q] * S.rho[mb + q] * c * S.sunL[b0 + q] * cone_w * Tr;
+            double Tr = shadow_T(S, p + S.eps * n, w, b0 + q * G, &ngl);
+            L[q] += T[q] * S.rho[mb + q * G] * c * S.sunL[b0 + q * G] * cone_w * Tr;
           }
           sig = mix(sig, ngl);
         }
@@ -788,11 +789,12 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
         onb(n, &b1, &b2);
         d = (rr * std::cos(ph2)) * b1 + (rr * std::sin(ph2)) * b2 + z * n;
         o = p + S.eps * n;
-        for (uint32_t q = 0; q < nv; ++q) T[q] *= S.rho[mb + q];
+        for (uint32_t q = 0; q < nv; ++q) T[q] *= S.rho[mb + q * G];
         covered = true;
       } else if (type == M_GLASS) {
         double Rs[4], Ts[4];
-        for (uint32_t q = 0; q < nv; ++q) slab(cos_i, S.ntab[mb + q], S.ktab[mb + q], S.lam[b0 + q], S.mthick[m], &Rs[q], &Ts[q]);
+        for (uint32_t q = 0; q < nv; ++q)
+          slab(cos_i, S.ntab[mb + q * G], S.ktab[mb + q * G], S.lam[b0 + q * G], S.mthick[m], &Rs[q], &Ts[q]);
         if (k == depth) break;
         Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b0, 4u * k + 1u}}, k0, k1);
         double pr = 0.0;
@@ -812,13 +814,13 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
         const bool inside = dot(ng, d) > 0.0;
         double alpha[4];
         for (uint32_t q = 0; q < nv; ++q) {
-          alpha[q] = 4.0 * M_PI * S.ktab[mb + q] / (S.lam[b0 + q] * 1e-9);
+          alpha[q] = 4.0 * M_PI * S.ktab[mb + q * G] / (S.lam[b0 + q * G] * 1e-9);
           if (inside) T[q] *= std::exp(-alpha[q] * t);
         }
         if (k == depth) break;
         double R[4], eta[4];
         for (uint32_t q = 0; q < nv; ++q) {
-          eta[q] = inside ? 1.0 / S.ntab[mb + q] : S.ntab[mb + q];
+          eta[q] = inside ? 1.0 / S.ntab[mb + q * G] : S.ntab[mb + q * G];
           R[q] = fresnel_complex(cos_i, eta[q], 0.0);
         }
         Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b0, 4u * k + 1u}}, k0, k1);
@@ -850,7 +852,7 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
         covered = false;
       } else {  // conductor
         double R[4];
-        for (uint32_t q = 0; q < nv; ++q) R[q] = fresnel_complex(cos_i, S.ntab[mb + q], S.ktab[mb + q]);
+        for (uint32_t q = 0; q < nv; ++q) R[q] = fresnel_complex(cos_i, S.ntab[mb + q * G], S.ktab[mb + q * G]);
         if (k == depth) break;
         d = d - (2.0 * dot(d, n)) * n;
         o = p + S.eps * n;
@@ -870,12 +872,13 @@ int or_render4(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t ban
       for (uint32_t j = 0; j < band_count; ++j) spectral_sum[i * band_count + j] = 0.0;
       for (uint32_t s = 0; s < spp; ++s)
         for (uint32_t g = 0; g < groups; ++g) {
-          const uint32_t nv = std::min(4u, band_count - 4 * g);
+          uint32_t nv = 0;
+          while (nv < 4 && g + nv * groups < band_count) ++nv;
           double L[4];
           uint32_t sg = 0;
-          trace4(pix, s, band_first + 4 * g, nv, L, path_sig ? &sg : nullptr);
+          trace4(pix, s, band_first + g, groups, nv, L, path_sig ? &sg : nullptr);
           for (uint32_t q = 0; q < nv; ++q) {
-            const uint32_t j = 4 * g + q;
+            const uint32_t j = g + q * groups;
             spectral_sum[i * band_count + j] += L[q];
             size_t pi = ((size_t)i * spp + s) * band_count + j;
             if (path_L) path_L[pi] = L[q];

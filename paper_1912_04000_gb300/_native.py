@@ -45,7 +45,8 @@ class RenderOpts(C.Structure):
                 ("shadow_refill", C.c_uint32), ("guided", C.c_uint32), ("guide_collect", C.c_uint32),
                 ("guide_train_steps", C.c_uint32), ("guide_batch", C.c_uint32), ("sample_first", C.c_uint32),
                 ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("leaf_batch", C.c_uint32),
-                ("guide_order", C.c_uint32), ("ray_order", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+                ("guide_order", C.c_uint32), ("ray_order", C.c_uint32), ("bands_per_path", C.c_uint32),
+                ("reserved", C.c_uint32 * 2)]
 
 
 class SceneInfo(C.Structure):

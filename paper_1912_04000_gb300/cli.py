@@ -54,6 +54,8 @@ def main(argv=None):
     r.add_argument("--tune", action="store_true", help="autotuned launch settings (cached per GPU and workload)")
     r.add_argument("--builder", default="host", choices=["host", "device"],
                    help="BVH builder: binned SAH on the host or linear BVH on the device")
+    r.add_argument("--bands-per-path", type=int, default=1, choices=[1, 4],
+                   help="4: every path carries four bands until its first refraction")
     r.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
@@ -72,7 +74,8 @@ def main(argv=None):
     for _ in range(args.repeat):
         out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=args.xyz_mode, wave_capacity=args.wave,
                        guided=args.guided, guide_collect=args.guide_collect,
-                       guide_train_steps=args.guide_train_steps, use_graph=args.graph, tuned=tuned)
+                       guide_train_steps=args.guide_train_steps, use_graph=args.graph, tuned=tuned,
+                       bands_per_path=args.bands_per_path)
     st = out["stats"]
     st.update(workload=wl.name, triangles=int(wl.scene.n_tris), load_s=t_load, tuned=tuned, bvh=R.scene_info(),
               paths_per_s=st["paths"] / (st["ms_render"] * 1e-3) if st["ms_render"] > 0 else None)

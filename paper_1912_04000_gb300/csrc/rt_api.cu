@@ -48,6 +48,7 @@ struct rt_ctx {
   // per-render buffers
   WaveBufs wb{};
   uint32_t wave_alloc = 0;
+  uint32_t four_band_alloc = 0;
   DevCam* d_cams = nullptr;
   DevCam* h_cams = nullptr;  // pinned staging
   double* d_accum = nullptr;
@@ -144,6 +145,22 @@ rt_status ensure_wave(rt_ctx* c, uint32_t cap) {
     CUDA_TRY(c, cudaMalloc(&b.rbins, (size_t)(kCellSortBins + kCellSortBins / 1024u) * sizeof(uint32_t)));
   b.cap = cap;
   c->wave_alloc = cap;
+  return RT_OK;
+}
+
+// Per-path four-band state (radiance, throughput, pending sun-ray
+// contribution), allocated on the first render that asks for it.
+rt_status ensure_four_band(rt_ctx* c, uint32_t cap) {
+  if (c->four_band_alloc >= cap) return RT_OK;
+  WaveBufs& b = c->wb;
+  dfree(b.L4);
+  dfree(b.T4);
+  dfree(b.C4);
+  c->four_band_alloc = 0;
+  CUDA_TRY(c, cudaMalloc(&b.L4, (size_t)cap * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&b.T4, (size_t)cap * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&b.C4, (size_t)cap * sizeof(float4)));
+  c->four_band_alloc = cap;
   return RT_OK;
 }
 
@@ -295,6 +312,9 @@ void rt_destroy(rt_ctx* c) {
   dfree(b.rperm);
   dfree(b.rkey);
   dfree(b.rbins);
+  dfree(b.L4);
+  dfree(b.T4);
+  dfree(b.C4);
   dfree(b.cnt);
   dfree(b.tot);
   dfree(b.status);
@@ -651,6 +671,12 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");
   if (o.guide_order > 1) return fail(c, RT_ERR_ARG, "rt_render: guide_order is 0 or 1");
   if (o.ray_order > 1) return fail(c, RT_ERR_ARG, "rt_render: ray_order is 0 or 1");
+  if (o.bands_per_path != 0 && o.bands_per_path != 1 && o.bands_per_path != 4)
+    return fail(c, RT_ERR_ARG, "rt_render: bands_per_path is 1 or 4");
+  const uint32_t nb = o.bands_per_path == 4 ? 4u : 1u;
+  if (nb == 4 && o.guided) return fail(c, RT_ERR_ARG, "rt_render: four bands per path exclude guided sampling");
+  if (nb == 4 && o.trace_variant != 0)
+    return fail(c, RT_ERR_ARG, "rt_render: four bands per path use the four-wide tree (trace_variant 0)");
   if (o.trace_refill > 32 || o.shadow_refill > 32) return fail(c, RT_ERR_ARG, "rt_render: refill thresholds are 1..32");
   if (o.guided && !c->guide.init) return fail(c, RT_ERR_STATE, "rt_render: guided rendering needs rt_guide_init");
   if (o.guide_train_steps && !(o.guided && o.guide_collect))
@@ -668,8 +694,11 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
       return fail(c, RT_ERR_ARG, "rt_render: bad camera");
     npix += (uint64_t)cm.width * cm.height;
   }
-  const uint64_t PB64 = npix * band_count;
-  if (PB64 >= (1ull << 32)) return fail(c, RT_ERR_ARG, "rt_render: pixels x bands must be below 2^32");
+  // path units per pixel: one per band, or one per group of four bands
+  const uint32_t units = nb == 4 ? (band_count + 3) / 4 : band_count;
+  const uint64_t ACC64 = npix * band_count;  // spectral slots
+  const uint64_t PB64 = npix * units;
+  if (ACC64 >= (1ull << 32)) return fail(c, RT_ERR_ARG, "rt_render: pixels x bands must be below 2^32");
   // cameras in device form, basis in FP64
   uint64_t off = 0;
   for (uint32_t v = 0; v < n_cams; ++v) {
@@ -714,15 +743,17 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   cap = std::min<uint32_t>(std::min<uint32_t>(cap, kMaxWave), PB);
   cap = std::max<uint32_t>(cap, 1u);
   if (rt_status e = ensure_wave(c, cap)) return e;
+  if (nb == 4)
+    if (rt_status e = ensure_four_band(c, cap)) return e;
   if (spectral_dev && ((uintptr_t)spectral_dev & 15u) != 0)
     return fail(c, RT_ERR_ARG, "rt_render: spectral_dev must be 16-byte aligned");
   double* accum = spectral_dev;
   if (!accum) {
-    if (c->accum_cap < PB64) {
+    if (c->accum_cap < ACC64) {
       dfree(c->d_accum);
       c->accum_cap = 0;
-      CUDA_TRY(c, cudaMalloc(&c->d_accum, PB64 * sizeof(double)));
-      c->accum_cap = PB64;
+      CUDA_TRY(c, cudaMalloc(&c->d_accum, ACC64 * sizeof(double)));
+      c->accum_cap = ACC64;
     }
     accum = c->d_accum;
   }
@@ -747,7 +778,9 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   WaveParams w{};
   w.PB = PB;
   w.band_first = band_first;
-  w.band_count = band_count;
+  w.band_count = units;
+  w.nb = nb;
+  w.B = band_count;
   w.spp = spp;
   w.depth = depth;
   w.key0 = (uint32_t)seed;
@@ -828,7 +861,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   auto enqueue = [&](cudaStream_t s, bool events) -> cudaError_t {
     cudaError_t e;
     if ((e = cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, s))) return e;
-    if (!o.accumulate && (e = cudaMemsetAsync(accum, 0, PB64 * sizeof(double), s))) return e;
+    if (!o.accumulate && (e = cudaMemsetAsync(accum, 0, ACC64 * sizeof(double), s))) return e;
     if ((e = cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), s))) return e;
     if ((e = cudaMemsetAsync(c->wb.tot, 0, sizeof(Totals), s))) return e;
     if (events && (e = cudaEventRecord(c->ev[0], s))) return e;
@@ -884,7 +917,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
                   o.sample_first, o.accumulate, o.spp_total, o.xyz_mode, (void*)accum, (void*)xyz_dev,
                   (void*)c->d_nodes, (void*)c->d_mb, lc.grid_trace, lc.block_trace, lc.variant, lc.trace_steps,
                   lc.trace_refill, lc.shadow_steps, lc.shadow_refill, (int)cap, o.guided, gw.depth, gw.collect,
-                  o.wave_capacity, (double)gw.alpha, lc.leaf_min * 4 + (int)o.guide_order * 2 + (int)o.ray_order);
+                  o.wave_capacity, (double)gw.alpha,
+                  (lc.leaf_min * 4 + (int)o.guide_order * 2 + (int)o.ray_order) * 8 + (int)nb);
     std::string key(kb);
     char pb[160];
     std::snprintf(pb, sizeof(pb), "|%p|%p|%p|%p|%p", (void*)c->wb.q[0], (void*)c->wb.sq, (void*)gw.gq,
@@ -926,7 +960,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   CUDA_TRY(c, cudaStreamSynchronize(st));
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->paths = total;
+    stats->paths = ACC64 * spp;  // spectral (pixel, sample, band) estimates
     stats->ext_rays = c->h_tot->ext_rays;
     stats->shadow_rays = c->h_tot->shadow_rays;
     stats->nodes_visited = c->h_tot->nodes;

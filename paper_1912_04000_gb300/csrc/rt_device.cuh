@@ -211,4 +211,34 @@ __device__ __forceinline__ void finalize(const WaveParams& w, const PathId& id, 
   }
 }
 
+// Bands carried by four-band path unit j: j + q G for q = 0..3 (G =
+// band_count = ceil(B / 4) units per pixel), those below B.
+__device__ __forceinline__ uint32_t four_band_count(const WaveParams& w, uint32_t j) {
+  return min(4u, (w.B - j + w.band_count - 1u) / w.band_count);
+}
+
+// Termination of a path that carries four bands: each existing band adds
+// its radiance to its own (pixel, band) slot, as four one-band paths would.
+__device__ __forceinline__ void finalize4(const WaveParams& w, const PathId& id, const float (&L)[4], uint32_t sg,
+                                          double* accum, const Probe& probe, bool record) {
+  const uint32_t G = w.band_count;
+  const uint32_t nv = four_band_count(w, id.j);
+  const size_t base = (size_t)id.pix * w.B + id.j;
+#pragma unroll
+  for (uint32_t q = 0; q < 4u; ++q)
+    if (q < nv && L[q] != 0.0f) accum[base + q * G] += (double)L[q];
+  if (record && probe.map != nullptr) {
+    const uint32_t slot = probe.map[id.pix];
+    if (slot != 0xFFFFFFFFu) {
+      const size_t r = ((size_t)slot * w.spp + (id.s - w.s_base)) * w.B + id.j;
+#pragma unroll
+      for (uint32_t q = 0; q < 4u; ++q)
+        if (q < nv) {
+          probe.L[r + q * G] = L[q];
+          probe.sig[r + q * G] = sg;
+        }
+    }
+  }
+}
+
 }  // namespace srt

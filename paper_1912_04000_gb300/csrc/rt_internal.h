@@ -80,6 +80,10 @@ struct WaveParams {
   uint32_t key0, key1;
   uint32_t s_base;     // first sample index of the render call (probe rows)
   uint32_t n_bands;    // bands of the spectra (guide band groups)
+  // bands carried per path: 1, or 4 (band_count = G = ceil(B / 4) units
+  // per pixel; unit j stands for bands band_first + j + q G, q = 0..3, those
+  // below B, the render's band count); with 1, B = band_count
+  uint32_t nb, B;
 };
 
 // Guided sampling of one wave (on == false: plain cosine sampling).
@@ -172,6 +176,11 @@ struct WaveBufs {
   uint32_t* rperm;
   uint32_t* rkey;
   uint32_t* rbins;
+  // four bands per path: radiance, throughput and the pending sun-ray
+  // contribution per path id and band
+  float4* L4;
+  float4* T4;
+  float4* C4;
 };
 
 constexpr int kMaxDepth = 64;

@@ -342,6 +342,41 @@ __device__ __forceinline__ bool shadow_leaf(Trav& tv, const DevScene& S, const D
   return false;
 }
 
+// Sun-ray leaf for a path that carries bands band0 + q G, q < nv: the
+// product of thin-glass T_s per band.
+__device__ __forceinline__ bool shadow_leaf4(Trav& tv, const DevScene& S, const DevSpectra& P, float3 d,
+                                             uint32_t band0, uint32_t G, uint32_t nv, float (&T)[4], uint32_t& ng,
+                                             uint32_t& n_tris, bool count) {
+  for (uint32_t t = tv.ref; t < tv.ref + tv.cnt; ++t) {
+    const float4* tr = S.tris + 3u * t;
+    const float4 v0 = ldg4(tr), v1 = ldg4(tr + 1), v2 = ldg4(tr + 2);
+    if (count) ++n_tris;
+    const float th = tri_hit(tv.rw, f3(v0), f3(v1), f3(v2));
+    if (th > 0.0f) {
+      const uint32_t mat = __float_as_uint(v1.w);
+      if (__ldg(P.mtype + mat) != 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) T[q] = 0.0f;
+        ng = 0xFFFFFFFFu;
+        return true;
+      }
+      const float4 nr = ldg4(S.nrm + t);
+      const float c = fabsf(dot(d, f3(nr)));
+#pragma unroll
+      for (uint32_t q = 0; q < 4u; ++q)
+        if (q < nv) {
+          const uint32_t mb = mat * P.n_bands + band0 + q * G;
+          const float4 m = ldg4(P.mb + mb);
+          float Rs, Ts;
+          thin_sheet(c, m.x, m.y, __ldg(P.ad + mb), Rs, Ts);
+          T[q] *= Ts;
+        }
+      ++ng;
+    }
+  }
+  return false;
+}
+
 // One sun-ray step (WW as for closest_step).
 template <bool FMA, bool COUNT, bool WW>
 __device__ __forceinline__ bool shadow_step(Trav& tv, uint2* stack, const DevScene& S, const DevSpectra& P, float3 d,
@@ -528,7 +563,8 @@ __global__ void k_rsort_scatter(const Counters* __restrict__ cnt, uint32_t k, ui
 
 __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams, uint32_t n_cams, WaveParams w,
                                                 float4* __restrict__ q, float* __restrict__ L,
-                                                uint32_t* __restrict__ sig, Counters* cnt, bool record) {
+                                                uint32_t* __restrict__ sig, Counters* cnt, bool record,
+                                                float4* __restrict__ L4, float4* __restrict__ T4) {
   if (blockIdx.x == 0 && threadIdx.x == 0) cnt[1].q_count = w.n;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += stride) {
@@ -547,7 +583,14 @@ __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams,
     dir = mul(inv, dir);
     q[2 * i] = make_float4(C.pos.x, C.pos.y, C.pos.z, __uint_as_float(i));
     q[2 * i + 1] = make_float4(dir.x, dir.y, dir.z, 1.0f);
-    L[i] = 0.0f;
+    if (w.nb == 4u) {
+      // bands past the render's range carry nothing
+      const uint32_t nv = four_band_count(w, id.j);
+      L4[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      T4[i] = make_float4(1.0f, nv > 1u ? 1.0f : 0.0f, nv > 2u ? 1.0f : 0.0f, nv > 3u ? 1.0f : 0.0f);
+    } else {
+      L[i] = 0.0f;
+    }
     if (record) sig[i] = 2166136261u;
   }
 }
@@ -863,13 +906,288 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
   }
 }
 
-template <bool RECORD, bool COUNT, int MODE>
+// Shading for paths that carry four bands: path unit j of a pixel and
+// sample carries bands band_first + j + q G, q = 0..3, G = ceil(B / 4) --
+// spread over the spectrum like hero wavelengths, so that the bands of one
+// path fall under different parts of the colour matching functions (four
+// neighbouring bands would add their correlated noise into X, Y and Z
+// almost undiluted); Philox counters are those of band j.  The bands share
+// every direction until the first dispersive event:
+//   Lambertian / emissive: one sun-ray direction and one cosine-sampled
+//     continuation for all; per-band weights rho, emitted radiance, NEE;
+//   thin glass: reflect with the mean over the carried bands of
+//     R_s / (R_s + T_s), weights R_s / p or T_s / (1 - p) per band;
+//   conductor: mirror, weight R per band;
+//   solid glass: reflect with the mean Fresnel reflectance p, weight R / p;
+//     else refraction bends each band differently, so one carried band,
+//     chosen uniformly, continues with weight n_carried (1 - R) / (1 - p)
+//     and the others stop (their radiance so far is kept).
+// "Carried" = throughput != 0; with one band left every rule is the
+// one-band rule of k_shade.  Each choice has the one-band expectation per
+// band, so the four-band estimate of every band is unbiased.
+template <bool RECORD>
+__global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+                                                const float4* __restrict__ qin, const float2* __restrict__ hit,
+                                                float4* __restrict__ qout, float4* __restrict__ sq,
+                                                float4* __restrict__ L4, float4* __restrict__ T4,
+                                                float4* __restrict__ C4, uint32_t* __restrict__ sigbuf,
+                                                Counters* cnt, uint32_t cap, double* __restrict__ accum,
+                                                Probe probe, uint32_t* status) {
+  const uint32_t count = min(cnt[k].q_count, cap);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
+    const uint32_t i = base + lane;
+    bool emit_next = false, emit_shadow = false;
+    float4 n0 = make_float4(0, 0, 0, 0), n1 = n0, s0 = n0, s1 = n0;
+    if (i < count) {
+      const float4 a = __ldcs(qin + 2 * i), b = __ldcs(qin + 2 * i + 1);
+      const float2 h = __ldcs(hit + i);
+      const uint32_t bits = __float_as_uint(a.w);
+      const uint32_t pid = bits & kPidMask;
+      const bool covered = (bits & kFlagCovered) != 0u;
+      const float3 o = f3(a), d = f3(b);
+      const PathId id = path_id(w, pid);
+      const uint32_t b0 = w.band_first + id.j, G = w.band_count;
+      const uint32_t nv = four_band_count(w, id.j);
+      const float4 t4 = T4[pid], l4 = L4[pid];
+      float T[4] = {t4.x, t4.y, t4.z, t4.w}, L[4] = {l4.x, l4.y, l4.z, l4.w};
+      uint32_t sg = RECORD ? sigbuf[pid] : 0u;
+      const int leaf = __float_as_int(h.y);
+      bool terminate = false;
+      if (leaf < 0) {
+        if (RECORD) sg = mix_sig(sg, 0xFFFFFFFFu);
+        if (!covered && dot(d, P.sun) >= P.cos_max) {
+#pragma unroll
+          for (uint32_t q = 0; q < 4u; ++q)
+            if (q < nv) L[q] += T[q] * __ldg(P.sunL + b0 + q * G);
+        }
+        terminate = true;
+      } else {
+        const float3 p = madd(o, h.x, d);
+        const float4 nr = ldg4(S.nrm + leaf);
+        const uint32_t mat = __float_as_uint(nr.w);
+        if (RECORD) sg = mix_sig(sg, __float_as_uint(S.tris[3 * leaf].w));
+        const float3 ng = f3(nr);
+        const float3 n = dot(ng, d) < 0.0f ? ng : neg(ng);
+        const float cos_i = -dot(d, n);
+        const uint32_t mrow = mat * P.n_bands + b0;
+        float4 m[4];
+#pragma unroll
+        for (uint32_t q = 0; q < 4u; ++q)
+          m[q] = q < nv ? ldg4(P.mb + mrow + q * G) : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        const int type = __ldg(P.mtype + mat);
+        const uint4 u = philox4x32_10(make_uint4(id.pix, id.s, b0, 4u * k), w.key0, w.key1);
+        // the bands still carried (throughput != 0), else every band of the path
+        uint32_t act = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < 4u; ++q)
+          if (q < nv && T[q] != 0.0f) act |= 1u << q;
+        if (act == 0u) act = (1u << nv) - 1u;
+        const float na = (float)__popc(act);
+        if (type == 0 || type == 3) {
+          if (type == 3) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) L[q] += T[q] * m[q].w;
+          }
+          const float om = u01(u.x) * P.one_minus_cos;
+          const float ct = 1.0f - om;
+          const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
+          float sp_, cp_;
+          sincospif(2.0f * u01(u.y), &sp_, &cp_);
+          float3 t1, t2;
+          onb(P.sun, t1, t2);
+          const float3 wd = make_float3(st * cp_ * t1.x + st * sp_ * t2.x + ct * P.sun.x,
+                                        st * cp_ * t1.y + st * sp_ * t2.y + ct * P.sun.y,
+                                        st * cp_ * t1.z + st * sp_ * t2.z + ct * P.sun.z);
+          const float c = dot(n, wd);
+          const float3 po = madd(p, S.eps, n);
+          if (c > 0.0f) {
+            emit_shadow = true;
+            float C[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4u; ++q)
+              C[q] = q < nv ? T[q] * m[q].z * c * __ldg(P.sunL + b0 + q * G) * 2.0f * P.one_minus_cos : 0.0f;
+            C4[pid] = make_float4(C[0], C[1], C[2], C[3]);
+            const uint32_t fl = pid | (k == w.depth ? kFlagTerm : 0u);
+            s0 = make_float4(po.x, po.y, po.z, __uint_as_float(fl));
+            s1 = make_float4(wd.x, wd.y, wd.z, 0.0f);
+          }
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            const float rr = sqrtf(u01(u.z));
+            const float zz = sqrtf(fmaxf(0.0f, 1.0f - u01(u.z)));
+            float s2, c2;
+            sincospif(2.0f * u01(u.w), &s2, &c2);
+            float3 b1, b2;
+            onb(n, b1, b2);
+            const float3 nd = make_float3(rr * c2 * b1.x + rr * s2 * b2.x + zz * n.x,
+                                          rr * c2 * b1.y + rr * s2 * b2.y + zz * n.y,
+                                          rr * c2 * b1.z + rr * s2 * b2.z + zz * n.z);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) T[q] *= m[q].z;
+            emit_next = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | kFlagCovered));
+            n1 = make_float4(nd.x, nd.y, nd.z, 0.0f);
+          }
+        } else if (type == 1) {
+          float Rs[4], Ts[4];
+#pragma unroll
+          for (uint32_t q = 0; q < 4u; ++q) {
+            Rs[q] = 0.0f;
+            Ts[q] = 1.0f;
+            if (q < nv) thin_sheet(cos_i, m[q].x, m[q].y, __ldg(P.ad + mrow + q * G), Rs[q], Ts[q]);
+          }
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, b0, 4u * k + 1u), w.key0, w.key1);
+            float pr = 0.0f;
+#pragma unroll
+            for (uint32_t q = 0; q < 4u; ++q)
+              if (act & (1u << q)) pr += Rs[q] / (Rs[q] + Ts[q]);
+            pr /= na;
+            emit_next = true;
+            if (u01(u1.x) < pr) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) T[q] *= Rs[q] / pr;
+              const float3 rd = madd(d, -2.0f * dot(d, n), n);
+              const float3 po = madd(p, S.eps, n);
+              n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid));
+              n1 = make_float4(rd.x, rd.y, rd.z, 0.0f);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) T[q] *= Ts[q] / (1.0f - pr);
+              const float3 po = madd(p, -S.eps, n);
+              n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | (bits & kFlagCovered)));
+              n1 = make_float4(d.x, d.y, d.z, 0.0f);
+            }
+          }
+        } else if (type == 4) {
+          const bool inside = dot(ng, d) > 0.0f;
+          float alpha[4];
+#pragma unroll
+          for (uint32_t q = 0; q < 4u; ++q) alpha[q] = q < nv ? __ldg(P.ad + mrow + q * G) : 0.0f;
+          if (inside) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) T[q] *= expf(-alpha[q] * h.x);
+          }
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+            float R[4];
+#pragma unroll
+            for (uint32_t q = 0; q < 4u; ++q)
+              R[q] = q < nv ? fresnel_complex(cos_i, inside ? 1.0f / m[q].x : m[q].x, 0.0f) : 1.0f;
+            const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, b0, 4u * k + 1u), w.key0, w.key1);
+            float pr = 0.0f;
+#pragma unroll
+            for (uint32_t q = 0; q < 4u; ++q)
+              if (act & (1u << q)) pr += R[q];
+            pr /= na;
+            float3 nd;
+            if (u01(u1.x) < pr) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) T[q] *= R[q] / pr;
+              nd = madd(d, -2.0f * dot(d, n), n);
+            } else {
+              // refraction is the dispersive event: one carried band goes on
+              uint32_t pick = min((uint32_t)(u01(u1.y) * na), (uint32_t)na - 1u);
+              uint32_t c = 0;
+#pragma unroll
+              for (uint32_t q = 0; q < 4u; ++q)
+                if (act & (1u << q)) {
+                  if (pick == 0u) c = q;
+                  pick = pick == 0u ? 0xFFFFFFFFu : pick - 1u;
+                }
+              float Rc = R[0], nc = m[0].x;
+#pragma unroll
+              for (uint32_t q = 1; q < 4u; ++q)
+                if (q == c) {
+                  Rc = R[q];
+                  nc = m[q].x;
+                }
+              const float wgt = na * (1.0f - Rc) / (1.0f - pr);
+#pragma unroll
+              for (uint32_t q = 0; q < 4u; ++q) T[q] = q == c ? T[q] * wgt : 0.0f;
+              const float r = inside ? nc : 1.0f / nc;
+              const float kk = 1.0f - r * r * (1.0f - cos_i * cos_i);
+              if (kk < 0.0f) {
+                nd = madd(d, -2.0f * dot(d, n), n);  // R = 1 there: the weight is already 0
+              } else {
+                const float3 td = madd(make_float3(r * d.x, r * d.y, r * d.z), r * cos_i - sqrtf(kk), n);
+                const float il = rsqrtf(dot(td, td));
+                nd = make_float3(td.x * il, td.y * il, td.z * il);
+              }
+            }
+            const float step = S.eps / fmaxf(fabsf(dot(nd, n)), 0.0625f);
+            if (dot(nd, ng) < 0.0f) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) T[q] *= expf(-alpha[q] * step);
+            }
+            const float3 po = madd(p, step, nd);
+            emit_next = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid));
+            n1 = make_float4(nd.x, nd.y, nd.z, 0.0f);
+          }
+        } else {
+          float R[4];
+#pragma unroll
+          for (uint32_t q = 0; q < 4u; ++q) R[q] = q < nv ? fresnel_complex(cos_i, m[q].x, m[q].y) : 0.0f;
+          if (k == w.depth) {
+            terminate = true;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) T[q] *= R[q];
+            const float3 rd = madd(d, -2.0f * dot(d, n), n);
+            const float3 po = madd(p, S.eps, n);
+            emit_next = true;
+            n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid));
+            n1 = make_float4(rd.x, rd.y, rd.z, 0.0f);
+          }
+        }
+      }
+      if (terminate && !emit_shadow) {
+        finalize4(w, id, L, sg, accum, probe, RECORD);
+      } else {
+        L4[pid] = make_float4(L[0], L[1], L[2], L[3]);
+        if (RECORD) sigbuf[pid] = sg;
+      }
+      if (emit_next) T4[pid] = make_float4(T[0], T[1], T[2], T[3]);
+    }
+    const uint32_t slot_n = warp_append(&cnt[k + 1].q_count, emit_next);
+    const uint32_t slot_s = warp_append(&cnt[k].s_count, emit_shadow);
+    if (emit_next) {
+      if (slot_n < cap) {
+        __stcs(qout + 2 * slot_n, n0);
+        __stcs(qout + 2 * slot_n + 1, n1);
+      } else {
+        atomicOr(status, ST_QUEUE);
+      }
+    }
+    if (emit_shadow) {
+      if (slot_s < cap) {
+        __stcs(sq + 2 * slot_s, s0);
+        __stcs(sq + 2 * slot_s + 1, s1);
+      } else {
+        atomicOr(status, ST_QUEUE);
+      }
+    }
+  }
+}
+
+// NB = 4: every sun ray belongs to a path that carries four bands; the ray
+// gathers one transmittance per band and the contributions wait in C4.
+template <bool RECORD, bool COUNT, int MODE, int NB = 1>
 __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
                                                 uint32_t* status, int steps, int refill, float* Lfinal,
-                                                GuideWave gw, int leaf_min, const uint32_t* __restrict__ perm) {
+                                                GuideWave gw, int leaf_min, const uint32_t* __restrict__ perm,
+                                                float4* __restrict__ L4, const float4* __restrict__ C4) {
+  static_assert(NB == 1 || (NB == 4 && MODE >= 2), "four-band sun rays use the leaf-batched traversal");
   const bool rec_sun = gw.on && gw.collect != 0u && k <= gw.depth && k < w.depth;
   const uint32_t count = min(cnt[k].s_count, cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tot->shadow_rays, (unsigned long long)count);
@@ -879,8 +1197,10 @@ __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, De
   uint32_t nn = 0, nt = 0;
   Trav tv;
   uint2 stack[kStack];
-  uint32_t ray = kNoRay, bits = 0, band = 0, ng = 0;
-  float contrib = 0.0f, T = 1.0f;
+  uint32_t ray = kNoRay, bits = 0, band = 0, ng = 0, nv = 1;
+  float contrib = 0.0f, T[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) T[q] = 1.0f;
   float3 dir = make_float3(0.0f, 0.0f, 0.0f);
   bool drained = count == 0u;
   for (;;) {
@@ -900,8 +1220,11 @@ __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, De
           bits = __float_as_uint(a.w);
           contrib = b.w;
           dir = f3(b);
-          band = w.band_first + path_id(w, bits & kPidMask).j;
-          T = 1.0f;
+          const uint32_t j = path_id(w, bits & kPidMask).j;
+          band = w.band_first + j;
+          if (NB == 4) nv = four_band_count(w, j);
+#pragma unroll
+          for (int q = 0; q < NB; ++q) T[q] = 1.0f;
           ng = 0;
           if (!init_w<MODE == 3, true>(tv, S, f3(a), dir)) tv.sp = -1;  // misses everything: finished
         }
@@ -926,7 +1249,10 @@ __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, De
             atomicOr(status, ST_ITER);
             done = true;
           } else if (leaf_phase) {
-            done = shadow_leaf(tv, S, P, dir, band, T, ng, nt, COUNT) || !trav_pop(tv, stack, INFINITY);
+            bool opaque;
+            if constexpr (NB == 4) opaque = shadow_leaf4(tv, S, P, dir, band, w.band_count, nv, T, ng, nt, COUNT);
+            else opaque = shadow_leaf(tv, S, P, dir, band, T[0], ng, nt, COUNT);
+            done = opaque || !trav_pop(tv, stack, INFINITY);
           } else if (!interior_w<MODE == 3, true, COUNT, kShadowAnyOrder>(tv, stack, S, INFINITY, status, nn)) {
             done = !trav_pop(tv, stack, INFINITY);
           }
@@ -935,15 +1261,32 @@ __global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, De
     } else if (ray != kNoRay) {
       done = tv.sp < 0;
       for (int i = 0; i < steps && !done; ++i)
-        done = shadow_step<true, COUNT, MODE == 1>(tv, stack, S, P, dir, band, T, ng, icap, status, nn, nt);
+        done = shadow_step<true, COUNT, MODE == 1>(tv, stack, S, P, dir, band, T[0], ng, icap, status, nn, nt);
+    }
+    if constexpr (NB == 4) {
+      if (done) {
+        const uint32_t pid = bits & kPidMask;
+        const float4 c4 = C4[pid], l4 = L4[pid];
+        const float L[4] = {l4.x + c4.x * T[0], l4.y + c4.y * T[1], l4.z + c4.z * T[2], l4.w + c4.w * T[3]};
+        uint32_t sg = 0;
+        if (RECORD) sg = mix_sig(sigbuf[pid], ng);
+        if (bits & kFlagTerm) {
+          finalize4(w, path_id(w, pid), L, sg, accum, probe, RECORD);
+        } else {
+          L4[pid] = make_float4(L[0], L[1], L[2], L[3]);
+          if (RECORD) sigbuf[pid] = sg;
+        }
+        ray = kNoRay;
+      }
+      continue;
     }
     if (done) {
       const uint32_t pid = bits & kPidMask;
       const PathId id = path_id(w, pid);
-      const float Lp = Lbuf[pid] + contrib * T;
+      const float Lp = Lbuf[pid] + contrib * T[0];
       if (rec_sun && pid % gw.collect == 0u)
         ((float*)(gw.raw + kRawF4 * ((k - 1u) * gw.slots_per_vertex + pid / gw.collect) + 5u))[0] =
-            T * __ldg(P.sunL + w.band_first + id.j);
+            T[0] * __ldg(P.sunL + w.band_first + id.j);
       uint32_t sg = 0;
       if (RECORD) sg = mix_sig(sigbuf[pid], ng);
       if (bits & kFlagTerm) {
@@ -1056,20 +1399,23 @@ void launch_trace(const LaunchCfg& lc, bool robust, const DevScene& S, const flo
   }
 }
 
-template <bool RECORD, bool COUNT, int MODE>
+template <bool RECORD, bool COUNT, int MODE, int NB = 1>
 void shadow_t(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
               const WaveBufs& b, double* accum, const Probe& probe, float* Lfinal, const GuideWave& gw,
               cudaStream_t st) {
   const uint32_t* perm = (lc.sort_rays && b.rperm) ? b.rperm : nullptr;
-  k_shadow<RECORD, COUNT, MODE><<<lc.grid_shadow, lc.block_trace, 0, st>>>(
+  k_shadow<RECORD, COUNT, MODE, NB><<<lc.grid_shadow, lc.block_trace, 0, st>>>(
       S, P, w, k, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe, b.tot, b.status, lc.shadow_steps, lc.shadow_refill,
-      Lfinal, gw, lc.leaf_min, perm);
+      Lfinal, gw, lc.leaf_min, perm, b.L4, b.C4);
 }
 
 template <bool RECORD, bool COUNT>
 void shadow_m(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const WaveParams& w, uint32_t k,
               const WaveBufs& b, double* accum, const Probe& probe, float* Lf, const GuideWave& gw, cudaStream_t st) {
-  if (lc.variant == 3) shadow_t<RECORD, COUNT, 2>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  // four bands per path: the four-wide tree with leaf batching (the host
+  // refuses other traversal variants there)
+  if (w.nb == 4u) shadow_t<RECORD, COUNT, 3, 4>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  else if (lc.variant == 3) shadow_t<RECORD, COUNT, 2>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   else if (lc.variant == 2) shadow_t<RECORD, COUNT, 0>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   else if (lc.variant == 1) shadow_t<RECORD, COUNT, 1>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   else shadow_t<RECORD, COUNT, 3>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
@@ -1115,7 +1461,7 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
   const bool guided = gw.on;
   const bool rec = lc.record;
   if (tm) tm->begin(STG_CAMERA, st);
-  k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec);
+  k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec, b.L4, b.T4);
   if (tm) tm->end(STG_CAMERA, st);
   int nl = 1;
   for (uint32_t k = 1; k <= w.depth; ++k) {
@@ -1131,7 +1477,14 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
     launch_trace(lc, k == 1, S, qin, b, k, st);
     if (tm) tm->end(STG_TRACE, st);
     if (tm) tm->begin(STG_SHADE, st);
-    if (guided) {
+    if (w.nb == 4u) {
+      if (rec)
+        k_shade4<true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L4, b.T4, b.C4,
+                                                                 b.sig, b.cnt, b.cap, accum, probe, b.status);
+      else
+        k_shade4<false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L4, b.T4,
+                                                                  b.C4, b.sig, b.cnt, b.cap, accum, probe, b.status);
+    } else if (guided) {
       if (rec)
         k_shade<true, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
                                                                      b.cnt, b.cap, accum, probe, b.status, gw);

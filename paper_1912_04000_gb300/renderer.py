@@ -107,7 +107,8 @@ class Renderer:
                trace_steps: int = 0, trace_refill: int = 0, shadow_steps: int = 0, shadow_refill: int = 0,
                guided: bool = False, guide_collect: int = 0, guide_train_steps: int = 0, guide_batch: int = 0,
                sample_first: int = 0, accumulate: bool = False, spp_total: int = 0, use_graph: bool = False,
-               tuned: Optional[dict] = None, leaf_batch: int = 0, guide_order: int = 0, ray_order: int = 0):
+               tuned: Optional[dict] = None, leaf_batch: int = 0, guide_order: int = 0, ray_order: int = 0,
+               bands_per_path: int = 1):
         """Returns dict(spectral [P, band_count] f64 sums over samples,
         xyz [P, 3] f32, stats, and probe_L / probe_sig [n_probe, spp, band_count]
         when probe_pixels is given)."""
@@ -129,6 +130,7 @@ class Renderer:
         opts.leaf_batch = leaf_batch
         opts.guide_order = guide_order
         opts.ray_order = ray_order
+        opts.bands_per_path = bands_per_path
         opts.trace_steps, opts.trace_refill = trace_steps, trace_refill
         opts.shadow_steps, opts.shadow_refill = shadow_steps, shadow_refill
         opts.guided, opts.guide_collect = int(guided), guide_collect

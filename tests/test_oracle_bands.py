@@ -30,12 +30,13 @@ def _flatten(wl, src_band):
 def test_flat_spectrum_paths_equal_one_band_paths():
     # before any refraction every choice is the one-band choice of the
     # group's first band, so each band's path value is that band's value
+    # (path unit g carries bands g, g + 2, g + 4, g + 6 of 8)
     wl = _flatten(scenes.tiny_box(width=24, height=18, n_bands=8, spp=3, depth=6), 0)
     one = _render(wl, 1)["path_L"]
     four = _render(wl, 4)["path_L"]
     for g in range(2):
         for q in range(4):
-            np.testing.assert_allclose(four[:, :, 4 * g + q], one[:, :, 4 * g], rtol=1e-12, atol=1e-15)
+            np.testing.assert_allclose(four[:, :, g + 2 * q], one[:, :, g], rtol=1e-12, atol=1e-15)
 
 
 @pytest.mark.parametrize("albedo,depth", [(0.5, 5), (0.8, 3)])
@@ -105,14 +106,16 @@ def test_same_expectation_as_one_band(name):
 
 
 def test_band_groups_and_ranges():
-    wl = scenes.tiny_box(width=12, height=10, n_bands=16, spp=2)
-    full = _render(wl, 4)["spectral_sum"]
-    # a range that starts on a group boundary gives the same sums for its bands
-    part = oracle.OracleScene(wl.scene, wl.spectra).render(wl.cameras, wl.spp, wl.depth, wl.seed, band_first=4,
-                                                          band_count=8, bands_per_path=4)["spectral_sum"]
-    np.testing.assert_array_equal(part, full[:, 4:12])
-    # a partial last group (band_count not a multiple of 4)
-    odd = oracle.OracleScene(wl.scene, wl.spectra).render(wl.cameras, wl.spp, wl.depth, wl.seed, band_first=0,
-                                                         band_count=14, bands_per_path=4)["spectral_sum"]
-    np.testing.assert_array_equal(odd[:, :12], full[:, :12])
-    assert np.all(np.isfinite(odd))
+    """Groups are formed inside the rendered range: bands first + g + q G,
+    G = ceil(count / 4), with the Philox stream of band first + g; a partial
+    last row of the grouping (count not a multiple of 4) carries fewer bands."""
+    wl = _flatten(scenes.tiny_box(width=12, height=10, n_bands=16, spp=2), 3)
+    sc = oracle.OracleScene(wl.scene, wl.spectra)
+    for first, count in ((4, 8), (0, 14), (3, 5)):
+        G = (count + 3) // 4
+        one = sc.render(wl.cameras, wl.spp, wl.depth, wl.seed, band_first=first, band_count=count,
+                        record_paths=True)["path_L"]
+        four = sc.render(wl.cameras, wl.spp, wl.depth, wl.seed, band_first=first, band_count=count,
+                         record_paths=True, bands_per_path=4)["path_L"]
+        for j in range(count):
+            np.testing.assert_allclose(four[:, :, j], one[:, :, j % G], rtol=1e-12, atol=1e-15)
