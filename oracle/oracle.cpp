@@ -40,6 +40,7 @@
 #include <cstring>
 #include <numeric>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 namespace {
@@ -165,6 +166,7 @@ struct OScene {
   V3 sun{0, 0, 1};
   double cos_max = 1.0;
   double eps = 0.0;              // origin offset: 1e-4 x scene diagonal
+  V3 lo{0, 0, 0}, hi{0, 0, 0};   // vertex bounds
   bool brute = true;
   std::vector<ONode> nodes;
   std::vector<uint32_t> perm;
@@ -495,6 +497,8 @@ void* or_scene_create(const or_scene_desc* sd, int force_brute) {
     hi = {std::max(hi.x, v.x), std::max(hi.y, v.y), std::max(hi.z, v.z)};
   }
   S->eps = 1e-4 * std::sqrt(dot(hi - lo, hi - lo));
+  S->lo = lo;
+  S->hi = hi;
   for (uint32_t t = 0; t < nt; ++t) {
     S->a[t] = vtx(sd->tris[3 * t]);
     S->b[t] = vtx(sd->tris[3 * t + 1]);
@@ -904,6 +908,350 @@ void or_xyz(const double* spectral_sum, uint64_t n_pixels, uint32_t band_first, 
         acc += spectral_sum[i * band_count + j] / spp * (double)cmf_w[(band_first + j) * 3 + c];
       xyz[i * 3 + c] = acc;
     }
+}
+
+// ---------------------------------------------------------------------------
+// photon mapping (section 4: photon maps filled from the light source, then
+// direct and specular light by ray tracing, caustic and indirect diffuse light
+// from the maps)
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+enum { PH_NONE = 0, PH_DIRECT = 1, PH_CAUSTIC = 2, PH_INDIRECT = 3 };
+
+struct PhotonRec {
+  V3 x{0, 0, 0};
+  double phi = 0.0;
+  int cls = PH_NONE;
+};
+
+// Photon k-th diffuse hit slots: (j * N + i) * depth + k for band
+// band_first + j, photon i.
+//
+// Emission: the sun is a cone of radiance L_sun(lambda) and half angle a
+// around the unit direction s.  Photons start on a disk perpendicular to s,
+// tangent to the scene's bounding sphere (centre c, radius R) on the sun's
+// side: centre c + R s, radius R_d = R (tan a + 1 / cos a), wide enough that
+// every ray within the cone that meets the sphere starts on it.  Position
+// uniform on the disk (sqrt radius), direction -w with w uniform in the cone
+// (the sun-sampling formula of NEE).  A photon carries the flux
+// L_sun(lambda) cos(w, s) Omega pi R_d^2 / N, Omega = 2 pi (1 - cos a): the
+// Monte Carlo estimate of the flux the cone sends through the disk.
+//
+// Tracing: as the camera paths (the same material rules); at a Lambertian
+// (or emissive) hit the photon is stored, classed DIRECT (no event before it
+// but thin-glass transmissions, which next-event estimation already
+// covers), CAUSTIC (a reflection or refraction before its first diffuse hit)
+// or INDIRECT (after a diffuse hit), then continues by cosine sampling with
+// flux * rho.  Philox key (seed_lo, seed_hi ^ 0x50484F54), counter
+// (photon i, band, 0, 4 k + call).
+struct PhotonSetup {
+  V3 c0, t1, t2;
+  double Rd = 0.0, omega = 0.0;
+};
+
+PhotonSetup photon_setup(const OScene& S) {
+  PhotonSetup P;
+  const V3 c = 0.5 * (S.lo + S.hi);
+  const double R = 0.5 * std::sqrt(dot(S.hi - S.lo, S.hi - S.lo));
+  const double sa = std::sqrt(std::max(0.0, 1.0 - S.cos_max * S.cos_max));
+  P.c0 = c + R * S.sun;
+  P.Rd = R * (sa / S.cos_max + 1.0 / S.cos_max);
+  P.omega = 2.0 * M_PI * (1.0 - S.cos_max);
+  onb(S.sun, &P.t1, &P.t2);
+  return P;
+}
+
+void trace_photons(const OScene& S, uint32_t band_first, uint32_t band_count, uint32_t N, uint32_t depth,
+                   uint64_t seed, std::vector<PhotonRec>& out, int n_threads) {
+  out.assign((size_t)band_count * N * depth, PhotonRec{});
+  const PhotonSetup P = photon_setup(S);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ 0x50484F54u;
+  auto one = [&](uint32_t j, uint32_t i) {
+    const uint32_t b = band_first + j;
+    Ctr4 r0 = philox4x32_10(Ctr4{{i, b, 0u, 0u}}, k0, k1);
+    const double rad = P.Rd * std::sqrt(u01(r0.w[0]));
+    const double ph = 2.0 * M_PI * u01(r0.w[1]);
+    V3 o = P.c0 + (rad * std::cos(ph)) * P.t1 + (rad * std::sin(ph)) * P.t2;
+    const double ct = 1.0 - u01(r0.w[2]) * (1.0 - S.cos_max);
+    const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+    const double ph2 = 2.0 * M_PI * u01(r0.w[3]);
+    V3 w = (st * std::cos(ph2)) * P.t1 + (st * std::sin(ph2)) * P.t2 + ct * S.sun;
+    V3 d = -1.0 * w;
+    double phi = S.sunL[b] * ct * P.omega * M_PI * P.Rd * P.Rd / N;
+    bool nee_path = true;
+    uint32_t n_diff = 0;
+    const size_t slot0 = ((size_t)j * N + i) * depth;
+    for (uint32_t k = 1; k <= depth; ++k) {
+      double t;
+      uint32_t prim;
+      if (!closest(S, o, d, &t, &prim)) break;
+      V3 p = o + t * d;
+      V3 ng = normalize(cross(S.b[prim] - S.a[prim], S.c[prim] - S.a[prim]));
+      V3 n = dot(ng, d) < 0.0 ? ng : -1.0 * ng;
+      double cos_i = -dot(d, n);
+      uint32_t m = S.mat[prim];
+      size_t mb = (size_t)m * S.B + b;
+      int type = S.mtype[m];
+      Ctr4 r = philox4x32_10(Ctr4{{i, b, 0u, 4u * k}}, k0, k1);
+      if (type == M_LAMBERT || type == M_EMISSIVE) {
+        PhotonRec& rec = out[slot0 + n_diff];
+        rec.x = p;
+        rec.phi = phi;
+        rec.cls = n_diff > 0 ? PH_INDIRECT : (nee_path ? PH_DIRECT : PH_CAUSTIC);
+        ++n_diff;
+        if (k == depth) break;
+        double rr = std::sqrt(u01(r.w[2]));
+        double ph3 = 2.0 * M_PI * u01(r.w[3]);
+        double z = std::sqrt(std::max(0.0, 1.0 - u01(r.w[2])));
+        V3 b1, b2;
+        onb(n, &b1, &b2);
+        d = (rr * std::cos(ph3)) * b1 + (rr * std::sin(ph3)) * b2 + z * n;
+        o = p + S.eps * n;
+        phi *= S.rho[mb];
+      } else if (type == M_GLASS) {
+        double Rs, Ts;
+        slab(cos_i, S.ntab[mb], S.ktab[mb], S.lam[b], S.mthick[m], &Rs, &Ts);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{i, b, 0u, 4u * k + 1u}}, k0, k1);
+        if (u01(r1.w[0]) < Rs / (Rs + Ts)) {
+          d = d - (2.0 * dot(d, n)) * n;
+          o = p + S.eps * n;
+          nee_path = false;
+        } else {
+          o = p - S.eps * n;
+        }
+        phi *= Rs + Ts;
+      } else if (type == M_DIELECTRIC) {
+        const bool inside = dot(ng, d) > 0.0;
+        const double alpha = 4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9);
+        if (inside) phi *= std::exp(-alpha * t);
+        const double eta = inside ? 1.0 / S.ntab[mb] : S.ntab[mb];
+        const double R = fresnel_complex(cos_i, eta, 0.0);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{i, b, 0u, 4u * k + 1u}}, k0, k1);
+        V3 tdir;
+        if (u01(r1.w[0]) < R || !refract(d, n, eta, &tdir)) d = d - (2.0 * dot(d, n)) * n;
+        else d = normalize(tdir);
+        const double step = S.eps / std::max(std::fabs(dot(d, n)), 0.0625);
+        if (dot(d, ng) < 0.0) phi *= std::exp(-alpha * step);
+        o = p + step * d;
+        nee_path = false;
+      } else {  // conductor
+        double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
+        if (k == depth) break;
+        d = d - (2.0 * dot(d, n)) * n;
+        o = p + S.eps * n;
+        phi *= R;
+        nee_path = false;
+      }
+    }
+  };
+  std::atomic<uint64_t> next{0};
+  const uint64_t total = (uint64_t)band_count * N;
+  auto worker = [&]() {
+    for (;;) {
+      uint64_t g = next.fetch_add(1);
+      if (g >= total) break;
+      one((uint32_t)(g / N), (uint32_t)(g % N));
+    }
+  };
+  int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::thread> th;
+  for (int q = 0; q < nt; ++q) th.emplace_back(worker);
+  for (auto& q : th) q.join();
+}
+
+// Photons of one band and class in a uniform grid of cell size r; the sum of
+// the flux of the photons within distance r of x (27 cells cover the ball).
+struct PhotonGrid {
+  double r = 0.0;
+  std::unordered_map<int64_t, std::vector<uint32_t>> cells;
+  static int64_t key(int64_t ix, int64_t iy, int64_t iz) {
+    return ((ix + (1 << 20)) << 42) | ((iy + (1 << 20)) << 21) | (iz + (1 << 20));
+  }
+  void add(const PhotonRec& p, uint32_t id) {
+    cells[key((int64_t)std::floor(p.x.x / r), (int64_t)std::floor(p.x.y / r), (int64_t)std::floor(p.x.z / r))]
+        .push_back(id);
+  }
+  double flux_within(const std::vector<PhotonRec>& recs, V3 x) const {
+    const int64_t cx = (int64_t)std::floor(x.x / r), cy = (int64_t)std::floor(x.y / r),
+                  cz = (int64_t)std::floor(x.z / r);
+    double sum = 0.0;
+    for (int64_t a = -1; a <= 1; ++a)
+      for (int64_t b = -1; b <= 1; ++b)
+        for (int64_t c = -1; c <= 1; ++c) {
+          auto it = cells.find(key(cx + a, cy + b, cz + c));
+          if (it == cells.end()) continue;
+          for (uint32_t id : it->second) {
+            const V3 dx = recs[id].x - x;
+            if (dot(dx, dx) < r * r) sum += recs[id].phi;
+          }
+        }
+    return sum;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Photon records of the photon pass: pos_phi[slot] = (x, y, z, flux) and
+// cls[slot] = 0 empty, 1 direct, 2 caustic, 3 indirect.
+int or_photon_records(void* scene, uint32_t band_first, uint32_t band_count, uint32_t n_photons, uint32_t depth,
+                      uint64_t seed, double* pos_phi, uint8_t* cls, int n_threads) {
+  const OScene& S = *(OScene*)scene;
+  if (band_first + band_count > S.B || depth == 0 || n_photons == 0) return 1;
+  std::vector<PhotonRec> recs;
+  trace_photons(S, band_first, band_count, n_photons, depth, seed, recs, n_threads);
+  for (size_t q = 0; q < recs.size(); ++q) {
+    pos_phi[4 * q] = recs[q].x.x;
+    pos_phi[4 * q + 1] = recs[q].x.y;
+    pos_phi[4 * q + 2] = recs[q].x.z;
+    pos_phi[4 * q + 3] = recs[q].phi;
+    cls[q] = (uint8_t)recs[q].cls;
+  }
+  return 0;
+}
+
+// Photon-mapping render of the listed pixels (same layout as or_render):
+// camera paths follow thin-glass, conductor and solid-glass events as in
+// the path tracer; at the first Lambertian vertex they add emission, the
+// next-event estimate of the sun and the photon estimate
+//   (rho / pi) [sum_caustic(r_c) phi / (pi r_c^2) + sum_indirect(r_g) phi / (pi r_g^2)]
+// of the photons of the path's band within the two radii, and stop.
+int or_photon_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
+                     uint32_t spp, uint32_t depth, uint64_t seed, uint32_t n_photons, uint32_t photon_depth,
+                     double r_caustic, double r_global, const uint32_t* pixels, uint64_t n_pixels,
+                     double* spectral_sum, double* path_L, uint32_t* path_sig, int n_threads) {
+  const OScene& S = *(OScene*)scene;
+  if (band_first + band_count > S.B || depth == 0 || photon_depth == 0 || n_photons == 0 || !(r_caustic > 0.0) ||
+      !(r_global > 0.0))
+    return 1;
+  std::vector<PhotonRec> recs;
+  trace_photons(S, band_first, band_count, n_photons, photon_depth, seed, recs, n_threads);
+  std::vector<PhotonGrid> caus(band_count), glob(band_count);
+  const size_t per_band = (size_t)n_photons * photon_depth;
+  for (uint32_t j = 0; j < band_count; ++j) {
+    caus[j].r = r_caustic;
+    glob[j].r = r_global;
+    for (size_t q = j * per_band; q < (j + 1) * per_band; ++q) {
+      if (recs[q].cls == PH_CAUSTIC) caus[j].add(recs[q], (uint32_t)q);
+      else if (recs[q].cls == PH_INDIRECT) glob[j].add(recs[q], (uint32_t)q);
+    }
+  }
+  const std::vector<OCam> oc = setup_cams(cams, n_cams);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const double cone_w = 2.0 * (1.0 - S.cos_max);
+  auto trace = [&](uint32_t pix, uint32_t s, uint32_t j, uint32_t* sig_out) -> double {
+    const uint32_t b = band_first + j;
+    V3 o, d;
+    camera_ray(oc, pix, s, b, k0, k1, &o, &d);
+    double T = 1.0, L = 0.0;
+    bool covered = false;
+    uint32_t sig = 2166136261u;
+    for (uint32_t k = 1; k <= depth; ++k) {
+      double t;
+      uint32_t prim;
+      if (!closest(S, o, d, &t, &prim)) {
+        sig = mix(sig, 0xFFFFFFFFu);
+        if (!covered && dot(d, S.sun) >= S.cos_max) L += T * S.sunL[b];
+        break;
+      }
+      sig = mix(sig, prim);
+      V3 p = o + t * d;
+      V3 ng = normalize(cross(S.b[prim] - S.a[prim], S.c[prim] - S.a[prim]));
+      V3 n = dot(ng, d) < 0.0 ? ng : -1.0 * ng;
+      double cos_i = -dot(d, n);
+      uint32_t m = S.mat[prim];
+      size_t mb = (size_t)m * S.B + b;
+      int type = S.mtype[m];
+      Ctr4 r = philox4x32_10(Ctr4{{pix, s, b, 4u * k}}, k0, k1);
+      if (type == M_LAMBERT || type == M_EMISSIVE) {
+        if (type == M_EMISSIVE) L += T * S.le[mb];
+        double ct = 1.0 - u01(r.w[0]) * (1.0 - S.cos_max);
+        double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+        double ph = 2.0 * M_PI * u01(r.w[1]);
+        V3 t1, t2;
+        onb(S.sun, &t1, &t2);
+        V3 w = (st * std::cos(ph)) * t1 + (st * std::sin(ph)) * t2 + ct * S.sun;
+        double c = dot(n, w);
+        if (c > 0.0) {
+          uint32_t ngl;
+          double Tr = shadow_T(S, p + S.eps * n, w, b, &ngl);
+          sig = mix(sig, ngl);
+          L += T * S.rho[mb] * c * S.sunL[b] * cone_w * Tr;
+        }
+        const double E = caus[j].flux_within(recs, p) / (M_PI * r_caustic * r_caustic) +
+                         glob[j].flux_within(recs, p) / (M_PI * r_global * r_global);
+        L += T * S.rho[mb] / M_PI * E;
+        break;
+      } else if (type == M_GLASS) {
+        double Rs, Ts;
+        slab(cos_i, S.ntab[mb], S.ktab[mb], S.lam[b], S.mthick[m], &Rs, &Ts);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+        if (u01(r1.w[0]) < Rs / (Rs + Ts)) {
+          d = d - (2.0 * dot(d, n)) * n;
+          o = p + S.eps * n;
+          covered = false;
+        } else {
+          o = p - S.eps * n;
+        }
+        T *= Rs + Ts;
+      } else if (type == M_DIELECTRIC) {
+        const bool inside = dot(ng, d) > 0.0;
+        const double alpha = 4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9);
+        if (inside) T *= std::exp(-alpha * t);
+        const double eta = inside ? 1.0 / S.ntab[mb] : S.ntab[mb];
+        const double R = fresnel_complex(cos_i, eta, 0.0);
+        if (k == depth) break;
+        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+        V3 tdir;
+        if (u01(r1.w[0]) < R || !refract(d, n, eta, &tdir)) d = d - (2.0 * dot(d, n)) * n;
+        else d = normalize(tdir);
+        const double step = S.eps / std::max(std::fabs(dot(d, n)), 0.0625);
+        if (dot(d, ng) < 0.0) T *= std::exp(-alpha * step);
+        o = p + step * d;
+        covered = false;
+      } else {
+        double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
+        if (k == depth) break;
+        d = d - (2.0 * dot(d, n)) * n;
+        o = p + S.eps * n;
+        T *= R;
+        covered = false;
+      }
+    }
+    if (sig_out) *sig_out = sig;
+    return L;
+  };
+  std::atomic<uint64_t> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      uint64_t q = next.fetch_add(1);
+      if (q >= n_pixels) break;
+      uint32_t pix = pixels[q];
+      for (uint32_t j = 0; j < band_count; ++j) spectral_sum[q * band_count + j] = 0.0;
+      for (uint32_t s = 0; s < spp; ++s)
+        for (uint32_t j = 0; j < band_count; ++j) {
+          uint32_t sg = 0;
+          double L = trace(pix, s, j, path_sig ? &sg : nullptr);
+          spectral_sum[q * band_count + j] += L;
+          size_t pi = ((size_t)q * spp + s) * band_count + j;
+          if (path_L) path_L[pi] = L;
+          if (path_sig) path_sig[pi] = sg;
+        }
+    }
+  };
+  int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::thread> th;
+  for (int q = 0; q < nt; ++q) th.emplace_back(worker);
+  for (auto& q : th) q.join();
+  return 0;
 }
 
 int or_hardware_threads(void) { return (int)std::thread::hardware_concurrency(); }

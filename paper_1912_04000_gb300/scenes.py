@@ -456,6 +456,32 @@ def plate_under_sky(n_bands=2, width=8, height=8, spp=64, depth=3, seed=5, rho=1
     return Workload("plate_under_sky", scene, spec, [cam], spp, depth, seed)
 
 
+def mirror_caustic(elevation_deg=45.0, sun_half_angle=0.02, n_metal=0.3, k_metal=3.0, rho=0.8, n_bands=1,
+                   width=8, height=8, spp=4, depth=4, seed=3) -> Workload:
+    """Caustic test: a 10 x 10 m Lambertian floor (y = 0) and a vertical
+    1 x 1 m mirror (conductor, x in [-0.5, 0.5], y in [1, 2], z = 0, facing
+    -z) under a narrow sun at the given elevation from -z.  The mirror sends
+    R(theta) of the sunlight it intercepts (L pi sin^2(a) cos(e) per m^2) down
+    onto the floor patch x in [-0.5, 0.5], z in [-2 / tan e, -1 / tan e],
+    where it adds irradiance R L pi sin^2(a) sin(e) to the direct sun's
+    L pi sin^2(a) sin(e).  The camera looks down at the patch."""
+    mb = MeshBuilder()
+    mb.quad((-5.0, 0.0, -5.0), (5.0, 0.0, -5.0), (5.0, 0.0, 5.0), (-5.0, 0.0, 5.0), 0)
+    mb.quad((-0.5, 1.0, 0.0), (0.5, 1.0, 0.0), (0.5, 2.0, 0.0), (-0.5, 2.0, 0.0), 1)
+    scene = mb.build([LAMBERT, CONDUCTOR], [0.0, 0.0])
+    lam = band_wavelengths(500.0, 600.0, n_bands) if n_bands > 1 else np.array([550.0])
+    n, k, rt, le = _flat_spectra(2, n_bands)
+    rt[0] = rho
+    n[1] = n_metal
+    k[1] = k_metal
+    e = math.radians(elevation_deg)
+    sun = np.array([0.0, math.sin(e), -math.cos(e)])
+    spec = _spectra(lam, np.ones(n_bands), sun, sun_half_angle, n, k, rt, le)
+    zc = -1.5 / math.tan(e)
+    cam = Camera((0.0, 3.0, zc), (0.0, 0.0, zc + 1e-3), (0.0, 0.0, 1.0), 8.0, width, height)
+    return Workload("mirror_caustic", scene, spec, [cam], spp, depth, seed)
+
+
 def slab_view(n_glass=1.5, k_glass=1e-5, thickness=0.01, lambda_nm=(450.0, 550.0, 650.0),
               tilt_deg=30.0, spp=256, seed=7, sun_side="transmit", material=THIN_GLASS) -> Workload:
     """Camera looks at one tilted sheet with a very narrow field of view.  With
