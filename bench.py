@@ -47,6 +47,12 @@ def parse():
     ap.add_argument("--bands-mse", action="store_true",
                     help="equal-time MSE, four bands per path vs one (nave or crystal nave)")
     ap.add_argument("--bands-workload", default="nave", choices=["nave", "crystal_nave"])
+    ap.add_argument("--photon-mse", action="store_true",
+                    help="equal-time MSE, photon mapping vs path tracing (nave or crystal nave)")
+    ap.add_argument("--photons", type=int, default=1 << 16, help="photons per band")
+    ap.add_argument("--photon-depth", type=int, default=4)
+    ap.add_argument("--r-caustic", type=float, default=0.0)
+    ap.add_argument("--r-global", type=float, default=0.0)
     ap.add_argument("--mse-width", type=int, default=256)
     ap.add_argument("--mse-height", type=int, default=192)
     ap.add_argument("--mse-ref-spp", type=int, default=4096)
@@ -343,8 +349,68 @@ def run_bands_mse(args):
     return 0
 
 
+def run_photon_mse(args):
+    """Equal-time MSE of photon mapping (section 4's estimator) against path
+    tracing on a nave view at reduced resolution; the reference is the path
+    tracer at --mse-ref-spp with an independent seed.  Photon mapping is
+    biased (gather radius), so its error does not fall to zero with time."""
+    import numpy as np
+    import torch
+
+    from paper_1912_04000_gb300 import scenes
+    from paper_1912_04000_gb300.renderer import Renderer
+
+    make = scenes.crystal_nave if args.bands_workload == "crystal_nave" else scenes.nave
+    wl = make(width=args.mse_width, height=args.mse_height)
+    R = Renderer(0).load(wl)
+    dev = R.device
+    P, B = wl.n_pixels, wl.band_count
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize(dev)
+        return out, time.perf_counter() - t0
+
+    ref, t_ref = timed(lambda: R.render(wl.cameras, args.mse_ref_spp, wl.depth, 777))
+    ref_xyz = ref["xyz"].cpu().numpy().astype(np.float64)
+
+    def mse(x):
+        return float(np.mean((x - ref_xyz) ** 2))
+
+    pkw = dict(n_photons=args.photons, photon_depth=args.photon_depth, r_caustic=args.r_caustic,
+               r_global=args.r_global)
+    R.render_photons(wl.cameras, 1, wl.depth, 5, **pkw)  # warm
+    R.render(wl.cameras, 4, wl.depth, 5)
+    pt, t_pt = timed(lambda: R.render(wl.cameras, args.mse_spp, wl.depth, 0))
+    p1, t1 = timed(lambda: R.render_photons(wl.cameras, 1, wl.depth, 0, **pkw))
+    p4, t4 = timed(lambda: R.render_photons(wl.cameras, 4, wl.depth, 0, **pkw))
+    per_spp = max((t4 - t1) / 3.0, 1e-6)
+    fixed = max(t1 - per_spp, 0.0)
+    spp_pm = max(1, int(round((t_pt - fixed) / per_spp)))
+    pm, t_pm = timed(lambda: R.render_photons(wl.cameras, spp_pm, wl.depth, 0, **pkw))
+    e_pt, e_pm = mse(pt["xyz"].cpu().numpy().astype(np.float64)), mse(pm["xyz"].cpu().numpy().astype(np.float64))
+    line = {
+        "metric": "equal-time MSE, photon mapping vs path tracing (XYZ, vs a path-traced reference)",
+        "config": {"workload": f"{args.bands_workload}_{args.mse_width}x{args.mse_height}_b{B}_d{wl.depth}",
+                   "reference_spp": args.mse_ref_spp, "photons_per_band": args.photons,
+                   "photon_depth": args.photon_depth},
+        "path_tracing": {"spp": args.mse_spp, "seconds": t_pt, "mse_xyz": e_pt},
+        "photon_mapping": {"spp": spp_pm, "seconds": t_pm, "mse_xyz": e_pm,
+                           "photon_pass_ms": pm["stats"]["ms_stage"][0], "map_build_ms": pm["stats"]["ms_stage"][1],
+                           "camera_pass_ms": pm["stats"]["ms_stage"][2]},
+        "mse_ratio_pt_over_pm_equal_time": e_pt / max(e_pm, 1e-300),
+        "reference_seconds": t_ref,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.photon_mse:
+        return run_photon_mse(args)
     if args.bands_mse:
         return run_bands_mse(args)
     if args.impl == "reference":

@@ -227,6 +227,54 @@ rt_status rt_render_host(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, ui
                          const rt_render_opts* opts, double* spectral_host, float* xyz_host,
                          rt_stats* stats);
 
+/* Photon mapping (section 4), the paper's own global-illumination method, as
+ * a second estimator over the same scene and spectra.  First the photon
+ * pass: for every band, n_photons photons leave a disk perpendicular to the
+ * sun (tangent to the scene's bounding sphere, wide enough for the whole
+ * cone) with directions uniform in the sun cone and flux
+ * L_sun(lambda) cos Omega pi R_d^2 / n_photons, and follow the path tracer's
+ * material rules for up to photon_depth surface interactions; every
+ * Lambertian hit is stored, classed direct (only thin-glass transmissions
+ * before it: next-event estimation covers it, so it is left out of the
+ * maps), caustic (a reflection or refraction before the first diffuse hit:
+ * caustic map) or indirect (after a diffuse hit: global map).  Then the
+ * camera pass: camera paths follow thin-glass, conductor and solid-glass
+ * events as in rt_render; at the first Lambertian vertex they add its
+ * emission, the sun's next-event estimate and
+ *   (rho / pi) [sum of caustic flux within r_caustic / (pi r_caustic^2)
+ *             + sum of indirect flux within r_global / (pi r_global^2)]
+ * over the photons of the path's band, and stop.  The maps are spatial hash
+ * grids (cells of edge 2 r, 2^log2_cells per map and band) built on the
+ * device by a stable radix sort of the photon records; bands are processed
+ * in chunks whose photon records fit one sort (n_photons x photon_depth x
+ * chunk <= 2^24), with identical results for any chunking.  Philox: photons
+ * key (seed_lo, seed_hi ^ 0x50484F54), counter (photon, band, 0,
+ * 4 vertex + call); camera paths as rt_render.  Needs a sun half angle below
+ * 1 rad.  Outputs as rt_render; rt_stats.ms_stage[0..2] hold the photon
+ * pass, map build and camera pass times. */
+typedef struct {
+  uint32_t n_photons;     /* photons per band; 0 = 65536 */
+  uint32_t photon_depth;  /* surface interactions per photon; 0 = 4 */
+  float r_caustic;        /* caustic gather radius (m); 0 = 0.5% of the scene diagonal */
+  float r_global;         /* indirect gather radius (m); 0 = 2% of the scene diagonal */
+  uint32_t log2_cells;    /* hash cells per map and band, 8..20; 0 = 16 */
+  uint32_t xyz_mode;      /* rt_xyz_mode */
+  /* optional per-path records, as in rt_render_opts */
+  const uint32_t* probe_map_dev;
+  float* probe_L_dev;
+  uint32_t* probe_sig_dev;
+  uint32_t reserved[4];
+} rt_photon_opts;
+rt_status rt_render_photons(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
+                            uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
+                            const rt_photon_opts* opts, double* spectral_dev, float* xyz_dev, rt_stats* stats);
+/* The photon pass alone, for checks: rec_dev [band_count][n_photons][depth]
+ * float4 (device, 16-byte aligned) = {x, y, z, flux} of each photon's n-th
+ * Lambertian hit, cls_dev (device, may be NULL) the class of each slot
+ * (0 empty, 1 direct, 2 caustic, 3 indirect). */
+rt_status rt_photon_records(rt_ctx* ctx, uint32_t band_first, uint32_t band_count, uint32_t n_photons,
+                            uint32_t depth, uint64_t seed, float* rec_dev, uint8_t* cls_dev);
+
 /* Same result as rt_render, for callers that may not allocate device memory
  * (a framework that has reserved the device memory for its own pool, a fixed
  * memory budget, or a loop that cannot take the implicit synchronisation of

@@ -23,7 +23,7 @@ EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_
            "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
            "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static", "rt_guide_init",
            "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step", "rt_autotune",
-           "rt_set_bvh_builder", "rt_get_scene_info"]
+           "rt_set_bvh_builder", "rt_get_scene_info", "rt_render_photons", "rt_photon_records"]
 
 
 class RtError(RuntimeError):
@@ -47,6 +47,13 @@ class RenderOpts(C.Structure):
                 ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("leaf_batch", C.c_uint32),
                 ("guide_order", C.c_uint32), ("ray_order", C.c_uint32), ("bands_per_path", C.c_uint32),
                 ("reserved", C.c_uint32 * 2)]
+
+
+class PhotonOpts(C.Structure):
+    _fields_ = [("n_photons", C.c_uint32), ("photon_depth", C.c_uint32), ("r_caustic", C.c_float),
+                ("r_global", C.c_float), ("log2_cells", C.c_uint32), ("xyz_mode", C.c_uint32),
+                ("probe_map_dev", C.c_void_p), ("probe_L_dev", C.c_void_p), ("probe_sig_dev", C.c_void_p),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class SceneInfo(C.Structure):
@@ -126,6 +133,9 @@ def load(path: str = LIB_PATH):
         L.rt_trace_shadow.argtypes = [vp, vp, vp, vp, u64, vp, vp]
         L.rt_optics_eval.argtypes = [vp, vp, vp, vp, vp, vp, u64, vp, vp, vp]
         L.rt_xyz.argtypes = [vp, vp, u64, u32, u32, u32, u32, vp]
+        L.rt_render_photons.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(PhotonOpts),
+                                        vp, vp, C.POINTER(Stats)]
+        L.rt_photon_records.argtypes = [vp, u32, u32, u32, u32, u64, vp, vp]
         for name in EXPORTS:
             if name not in ("rt_destroy", "rt_last_error"):
                 getattr(L, name).restype = C.c_int

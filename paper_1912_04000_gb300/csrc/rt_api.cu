@@ -49,6 +49,22 @@ struct rt_ctx {
   WaveBufs wb{};
   uint32_t wave_alloc = 0;
   uint32_t four_band_alloc = 0;
+  // sun direction and cone in FP64 (photon emission geometry)
+  double sun_d[3] = {0.0, 0.0, 1.0};
+  double cos_max_d = 1.0;
+  // photon-mapping buffers: slot records, sort keys and values (two
+  // copies), radix histogram, records in key order, per-key ranges
+  struct {
+    float4* rec = nullptr;
+    float4* rec_sorted = nullptr;
+    uint32_t* keys[2] = {nullptr, nullptr};
+    uint32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;
+    size_t slots = 0;
+    uint32_t* start = nullptr;
+    uint32_t* end = nullptr;
+    size_t table = 0;
+  } ph;
   DevCam* d_cams = nullptr;
   DevCam* h_cams = nullptr;  // pinned staging
   double* d_accum = nullptr;
@@ -315,6 +331,15 @@ void rt_destroy(rt_ctx* c) {
   dfree(b.L4);
   dfree(b.T4);
   dfree(b.C4);
+  dfree(c->ph.rec);
+  dfree(c->ph.rec_sorted);
+  for (int q = 0; q < 2; ++q) {
+    dfree(c->ph.keys[q]);
+    dfree(c->ph.vals[q]);
+  }
+  dfree(c->ph.hist);
+  dfree(c->ph.start);
+  dfree(c->ph.end);
   dfree(b.cnt);
   dfree(b.tot);
   dfree(b.status);
@@ -644,8 +669,64 @@ rt_status rt_set_spectra(rt_ctx* c, const float* lambda_nm, uint32_t n_bands, co
   P.n_mat = M;
   P.sun = make_float3((float)(sun_dir[0] / sl), (float)(sun_dir[1] / sl), (float)(sun_dir[2] / sl));
   P.cos_max = (float)std::cos((double)sun_half_angle);
+  for (int a = 0; a < 3; ++a) c->sun_d[a] = sun_dir[a] / sl;
+  c->cos_max_d = std::cos((double)sun_half_angle);
   P.one_minus_cos = (float)(1.0 - std::cos((double)sun_half_angle));
   c->has_spectra = true;
+  return RT_OK;
+}
+
+// Checks the cameras and writes their device form (basis derived in FP64)
+// into the pinned staging array; *npix = pixels over all views.
+static rt_status stage_cameras(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, const char* who, uint64_t* npix_out) {
+  const std::string w(who);
+  uint64_t npix = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) {
+    const rt_camera& cm = cams[v];
+    if (cm.width == 0 || cm.height == 0) return fail(c, RT_ERR_ARG, w + ": zero-sized view");
+    if (!finite3(cm.pos) || !finite3(cm.look) || !finite3(cm.up) || !(cm.vfov_deg > 0.0f && cm.vfov_deg < 180.0f))
+      return fail(c, RT_ERR_ARG, w + ": bad camera");
+    npix += (uint64_t)cm.width * cm.height;
+  }
+  if (npix >= (1ull << 32)) return fail(c, RT_ERR_ARG, w + ": too many pixels");
+  // cameras in device form, basis in FP64
+  uint64_t off = 0;
+  for (uint32_t v = 0; v < n_cams; ++v) {
+    const rt_camera& cm = cams[v];
+    double f[3], r[3], u[3];
+    double fl = 0, rl = 0;
+    for (int a = 0; a < 3; ++a) {
+      f[a] = (double)cm.look[a] - cm.pos[a];
+      fl += f[a] * f[a];
+    }
+    fl = std::sqrt(fl);
+    if (!(fl > 0)) return fail(c, RT_ERR_ARG, w + ": camera look == pos");
+    for (int a = 0; a < 3; ++a) f[a] /= fl;
+    r[0] = f[1] * cm.up[2] - f[2] * cm.up[1];
+    r[1] = f[2] * cm.up[0] - f[0] * cm.up[2];
+    r[2] = f[0] * cm.up[1] - f[1] * cm.up[0];
+    for (int a = 0; a < 3; ++a) rl += r[a] * r[a];
+    rl = std::sqrt(rl);
+    if (!(rl > 1e-12)) return fail(c, RT_ERR_ARG, w + ": camera up parallel to the view direction");
+    for (int a = 0; a < 3; ++a) r[a] /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    DevCam& d = c->h_cams[v];
+    d.pos = make_float3(cm.pos[0], cm.pos[1], cm.pos[2]);
+    d.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
+    d.r = make_float3((float)r[0], (float)r[1], (float)r[2]);
+    d.u = make_float3((float)u[0], (float)u[1], (float)u[2]);
+    const double th = std::tan(0.5 * (double)cm.vfov_deg * M_PI / 180.0);
+    d.th = (float)th;
+    d.tha = (float)(th * (double)cm.width / (double)cm.height);
+    d.W = cm.width;
+    d.H = cm.height;
+    d.offset = (uint32_t)off;
+    d.pad = 0;
+    off += (uint64_t)cm.width * cm.height;
+  }
+  *npix_out = npix;
   return RT_OK;
 }
 
@@ -687,55 +768,12 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
       (o.probe_map_dev != nullptr) != (o.probe_sig_dev != nullptr))
     return fail(c, RT_ERR_ARG, "rt_render: probe_map, probe_L and probe_sig go together");
   uint64_t npix = 0;
-  for (uint32_t v = 0; v < n_cams; ++v) {
-    const rt_camera& cm = cams[v];
-    if (cm.width == 0 || cm.height == 0) return fail(c, RT_ERR_ARG, "rt_render: zero-sized view");
-    if (!finite3(cm.pos) || !finite3(cm.look) || !finite3(cm.up) || !(cm.vfov_deg > 0.0f && cm.vfov_deg < 180.0f))
-      return fail(c, RT_ERR_ARG, "rt_render: bad camera");
-    npix += (uint64_t)cm.width * cm.height;
-  }
+  if (rt_status e = stage_cameras(c, cams, n_cams, "rt_render", &npix)) return e;
   // path units per pixel: one per band, or one per group of four bands
   const uint32_t units = nb == 4 ? (band_count + 3) / 4 : band_count;
   const uint64_t ACC64 = npix * band_count;  // spectral slots
   const uint64_t PB64 = npix * units;
   if (ACC64 >= (1ull << 32)) return fail(c, RT_ERR_ARG, "rt_render: pixels x bands must be below 2^32");
-  // cameras in device form, basis in FP64
-  uint64_t off = 0;
-  for (uint32_t v = 0; v < n_cams; ++v) {
-    const rt_camera& cm = cams[v];
-    double f[3], r[3], u[3];
-    double fl = 0, rl = 0;
-    for (int a = 0; a < 3; ++a) {
-      f[a] = (double)cm.look[a] - cm.pos[a];
-      fl += f[a] * f[a];
-    }
-    fl = std::sqrt(fl);
-    if (!(fl > 0)) return fail(c, RT_ERR_ARG, "rt_render: camera look == pos");
-    for (int a = 0; a < 3; ++a) f[a] /= fl;
-    r[0] = f[1] * cm.up[2] - f[2] * cm.up[1];
-    r[1] = f[2] * cm.up[0] - f[0] * cm.up[2];
-    r[2] = f[0] * cm.up[1] - f[1] * cm.up[0];
-    for (int a = 0; a < 3; ++a) rl += r[a] * r[a];
-    rl = std::sqrt(rl);
-    if (!(rl > 1e-12)) return fail(c, RT_ERR_ARG, "rt_render: camera up parallel to the view direction");
-    for (int a = 0; a < 3; ++a) r[a] /= rl;
-    u[0] = r[1] * f[2] - r[2] * f[1];
-    u[1] = r[2] * f[0] - r[0] * f[2];
-    u[2] = r[0] * f[1] - r[1] * f[0];
-    DevCam& d = c->h_cams[v];
-    d.pos = make_float3(cm.pos[0], cm.pos[1], cm.pos[2]);
-    d.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
-    d.r = make_float3((float)r[0], (float)r[1], (float)r[2]);
-    d.u = make_float3((float)u[0], (float)u[1], (float)u[2]);
-    const double th = std::tan(0.5 * (double)cm.vfov_deg * M_PI / 180.0);
-    d.th = (float)th;
-    d.tha = (float)(th * (double)cm.width / (double)cm.height);
-    d.W = cm.width;
-    d.H = cm.height;
-    d.offset = (uint32_t)off;
-    d.pad = 0;
-    off += (uint64_t)cm.width * cm.height;
-  }
   cudaSetDevice(c->device);
   cudaStream_t st = c->stream;
   const uint32_t PB = (uint32_t)PB64;
@@ -1406,3 +1444,251 @@ rt_status rt_probe_l2(rt_ctx* c, uint64_t bytes, uint32_t iters, float* gbs) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// photon mapping (section 4)
+// ---------------------------------------------------------------------------
+
+// Emission geometry of the photon pass (FP64 on the host): a disk
+// perpendicular to the sun, tangent to the scene's bounding sphere (centre
+// c, radius R) on the sun's side, radius R_d = R (tan a + 1 / cos a) so that
+// every ray of the cone that meets the sphere starts on it; each of the N
+// photons of a band carries L_sun cos Omega pi R_d^2 / N.
+static void photon_setup(const rt_ctx* c, uint32_t N, uint64_t seed, PhotonPass& pp) {
+  double ctr[3], R2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    ctr[a] = 0.5 * ((double)c->lo[a] + (double)c->hi[a]);
+    const double e = (double)c->hi[a] - (double)c->lo[a];
+    R2 += e * e;
+  }
+  const double R = 0.5 * std::sqrt(R2);
+  const double cm = c->cos_max_d;
+  const double sa = std::sqrt(std::max(0.0, 1.0 - cm * cm));
+  const double Rd = R * (sa / cm + 1.0 / cm);
+  const double omega = 2.0 * M_PI * (1.0 - cm);
+  // orthonormal basis around the sun (the same construction as the kernels')
+  const double* n = c->sun_d;
+  const double sign = std::copysign(1.0, n[2]);
+  const double aa = -1.0 / (sign + n[2]);
+  const double bb = n[0] * n[1] * aa;
+  pp.t1 = make_float3((float)(1.0 + sign * n[0] * n[0] * aa), (float)(sign * bb), (float)(-sign * n[0]));
+  pp.t2 = make_float3((float)bb, (float)(sign + n[1] * n[1] * aa), (float)(-n[1]));
+  pp.c0 = make_float3((float)(ctr[0] + R * n[0]), (float)(ctr[1] + R * n[1]), (float)(ctr[2] + R * n[2]));
+  pp.Rd = (float)Rd;
+  pp.flux = (float)(omega * M_PI * Rd * Rd / (double)N);
+  pp.N = N;
+  pp.key0 = (uint32_t)seed;
+  pp.key1 = (uint32_t)(seed >> 32) ^ 0x50484F54u;
+}
+
+rt_status rt_photon_records(rt_ctx* c, uint32_t band_first, uint32_t band_count, uint32_t n_photons, uint32_t depth,
+                            uint64_t seed, float* rec_dev, uint8_t* cls_dev) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_scene || !c->has_spectra) return fail(c, RT_ERR_STATE, "rt_photon_records: scene and spectra required");
+  if (!rec_dev || ((uintptr_t)rec_dev & 15u)) return fail(c, RT_ERR_ARG, "rt_photon_records: rec_dev must be 16-byte aligned");
+  if (band_count == 0 || band_first + band_count > c->sp.n_bands || band_first + band_count < band_first)
+    return fail(c, RT_ERR_ARG, "rt_photon_records: band range outside the spectra");
+  if (n_photons == 0 || depth == 0 || depth > (uint32_t)kMaxDepth)
+    return fail(c, RT_ERR_ARG, "rt_photon_records: n_photons >= 1 and depth 1..64");
+  const uint64_t slots = (uint64_t)band_count * n_photons * depth;
+  if (slots > (1ull << 28)) return fail(c, RT_ERR_ARG, "rt_photon_records: more than 2^28 slots");
+  if (!(c->cos_max_d > std::cos(1.0))) return fail(c, RT_ERR_ARG, "rt_photon_records: sun half angle must be below 1 rad");
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  uint32_t* kv = nullptr;
+  CUDA_TRY(c, cudaMalloc(&kv, slots * 2 * sizeof(uint32_t)));
+  PhotonPass pp{};
+  photon_setup(c, n_photons, seed, pp);
+  pp.band0 = band_first;
+  pp.Bc = band_count;
+  pp.depth = depth;
+  pp.inv_cell[0] = pp.inv_cell[1] = 1.0f;
+  pp.hbits = 8;
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), st));
+  launch_photon_trace(dev_scene(c), c->sp, pp, (float4*)rec_dev, kv, kv + slots, cls_dev, c->wb.status, c->sms, st);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  dfree(kv);
+  return status_to_rt(c, *c->h_status);
+}
+
+rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
+                            uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
+                            const rt_photon_opts* opts, double* spectral_dev, float* xyz_dev, rt_stats* stats) {
+  if (rt_status e = check_ctx(c)) return e;
+  if (!c->has_scene || !c->has_spectra) return fail(c, RT_ERR_STATE, "rt_render_photons: scene and spectra must be set");
+  if (!cams || n_cams == 0 || n_cams > (uint32_t)kMaxCams) return fail(c, RT_ERR_ARG, "rt_render_photons: 1..64 cameras");
+  if (band_count == 0 || band_first + band_count > c->sp.n_bands || band_first + band_count < band_first)
+    return fail(c, RT_ERR_ARG, "rt_render_photons: band range outside the spectra");
+  if (spp == 0) return fail(c, RT_ERR_ARG, "rt_render_photons: spp must be >= 1");
+  if (depth == 0 || depth > (uint32_t)kMaxDepth) return fail(c, RT_ERR_ARG, "rt_render_photons: depth must be 1..64");
+  rt_photon_opts o{};
+  if (opts) o = *opts;
+  const uint32_t N = o.n_photons ? o.n_photons : 65536u;
+  const uint32_t pd = o.photon_depth ? o.photon_depth : 4u;
+  const uint32_t hb = o.log2_cells ? o.log2_cells : 16u;
+  if (pd > (uint32_t)kMaxDepth) return fail(c, RT_ERR_ARG, "rt_render_photons: photon_depth is 1..64");
+  if ((uint64_t)N * pd > kPhotonMaxSlots) return fail(c, RT_ERR_ARG, "rt_render_photons: n_photons x photon_depth above 2^24");
+  if (hb < 8 || hb > 20) return fail(c, RT_ERR_ARG, "rt_render_photons: log2_cells is 8..20");
+  if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render_photons: unknown xyz_mode");
+  if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
+    return fail(c, RT_ERR_ARG, "rt_render_photons: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
+  if (!(c->cos_max_d > std::cos(1.0)))
+    return fail(c, RT_ERR_ARG, "rt_render_photons: photon emission needs a sun half angle below 1 rad");
+  if ((o.probe_map_dev != nullptr) != (o.probe_L_dev != nullptr) ||
+      (o.probe_map_dev != nullptr) != (o.probe_sig_dev != nullptr))
+    return fail(c, RT_ERR_ARG, "rt_render_photons: probe_map, probe_L and probe_sig go together");
+  double diag2 = 0.0;
+  for (int a = 0; a < 3; ++a) diag2 += ((double)c->hi[a] - c->lo[a]) * ((double)c->hi[a] - c->lo[a]);
+  const double rc = o.r_caustic > 0.0f ? (double)o.r_caustic : 0.005 * std::sqrt(diag2);
+  const double rg = o.r_global > 0.0f ? (double)o.r_global : 0.02 * std::sqrt(diag2);
+  if (!(rc > 0.0) || !(rg > 0.0) || !std::isfinite(rc) || !std::isfinite(rg))
+    return fail(c, RT_ERR_ARG, "rt_render_photons: gather radii must be positive");
+  uint64_t npix = 0;
+  if (rt_status e = stage_cameras(c, cams, n_cams, "rt_render_photons", &npix)) return e;
+  const uint64_t ACC64 = npix * band_count;
+  if (ACC64 >= (1ull << 32)) return fail(c, RT_ERR_ARG, "rt_render_photons: pixels x bands must be below 2^32");
+  // bands per chunk: the chunk's slots fit one sort, and its two key tables
+  // (2 x Bc x 2^hb ranges) stay at 2^26 entries (keys far below the empty key)
+  uint32_t Bc = (uint32_t)std::min<uint64_t>(band_count, kPhotonMaxSlots / ((uint64_t)N * pd));
+  Bc = std::max<uint32_t>(1u, std::min<uint32_t>(Bc, 1u << (25 - hb)));
+  const size_t slots = (size_t)Bc * N * pd;
+  const size_t table = (size_t)2 * Bc << hb;
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  if (spectral_dev && ((uintptr_t)spectral_dev & 15u) != 0)
+    return fail(c, RT_ERR_ARG, "rt_render_photons: spectral_dev must be 16-byte aligned");
+  auto& B = c->ph;
+  if (B.slots < slots) {
+    dfree(B.rec);
+    dfree(B.rec_sorted);
+    for (int q = 0; q < 2; ++q) {
+      dfree(B.keys[q]);
+      dfree(B.vals[q]);
+    }
+    dfree(B.hist);
+    B.slots = 0;
+    CUDA_TRY(c, cudaMalloc(&B.rec, slots * sizeof(float4)));
+    CUDA_TRY(c, cudaMalloc(&B.rec_sorted, slots * sizeof(float4)));
+    for (int q = 0; q < 2; ++q) {
+      CUDA_TRY(c, cudaMalloc(&B.keys[q], slots * sizeof(uint32_t)));
+      CUDA_TRY(c, cudaMalloc(&B.vals[q], slots * sizeof(uint32_t)));
+    }
+    CUDA_TRY(c, cudaMalloc(&B.hist, radix_sort_hist_words((uint32_t)slots) * sizeof(uint32_t)));
+    B.slots = slots;
+  }
+  if (B.table < table) {
+    dfree(B.start);
+    dfree(B.end);
+    B.table = 0;
+    CUDA_TRY(c, cudaMalloc(&B.start, table * sizeof(uint32_t)));
+    CUDA_TRY(c, cudaMalloc(&B.end, table * sizeof(uint32_t)));
+    B.table = table;
+  }
+  double* accum = spectral_dev;
+  if (!accum) {
+    if (c->accum_cap < ACC64) {
+      dfree(c->d_accum);
+      c->accum_cap = 0;
+      CUDA_TRY(c, cudaMalloc(&c->d_accum, ACC64 * sizeof(double)));
+      c->accum_cap = ACC64;
+    }
+    accum = c->d_accum;
+  }
+  PhotonPass pp{};
+  photon_setup(c, N, seed, pp);
+  pp.depth = pd;
+  pp.inv_cell[0] = (float)(1.0 / (2.0 * rc));
+  pp.inv_cell[1] = (float)(1.0 / (2.0 * rg));
+  pp.hbits = hb;
+  PhotonMaps M{};
+  M.start = B.start;
+  M.end = B.end;
+  M.rec = B.rec_sorted;
+  M.r2[0] = (float)(rc * rc);
+  M.r2[1] = (float)(rg * rg);
+  M.inv_cell[0] = pp.inv_cell[0];
+  M.inv_cell[1] = pp.inv_cell[1];
+  M.norm[0] = (float)(1.0 / (M_PI * rc * rc));
+  M.norm[1] = (float)(1.0 / (M_PI * rg * rg));
+  M.hbits = hb;
+  PhotonCam pc{};
+  pc.s_base = 0;
+  pc.spp = spp;
+  pc.npix = (uint32_t)npix;
+  pc.depth = depth;
+  pc.B = band_count;
+  pc.key0 = (uint32_t)seed;
+  pc.key1 = (uint32_t)(seed >> 32);
+  const Probe probe{o.probe_map_dev, o.probe_L_dev, o.probe_sig_dev};
+  const DevScene S = dev_scene(c);
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+  };
+  int launches = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_cams, c->h_cams, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(accum, 0, ACC64 * sizeof(double), st));
+  CUDA_TRY(c, cudaMemsetAsync(c->wb.status, 0, sizeof(uint32_t), st));
+  mark();
+  for (uint32_t cb = band_first; cb < band_first + band_count; cb += Bc) {
+    const uint32_t bc = std::min<uint32_t>(Bc, band_first + band_count - cb);
+    const uint32_t n = bc * N * pd;
+    pp.band0 = cb;
+    pp.Bc = bc;
+    launch_photon_trace(S, c->sp, pp, B.rec, B.keys[0], B.vals[0], nullptr, c->wb.status, c->sms, st);
+    mark();
+    const int r = launch_radix_sort(B.keys, B.vals, n, 32, B.hist, st);
+    CUDA_TRY(c, cudaMemsetAsync(B.start, 0, ((size_t)2 * bc << hb) * sizeof(uint32_t), st));
+    CUDA_TRY(c, cudaMemsetAsync(B.end, 0, ((size_t)2 * bc << hb) * sizeof(uint32_t), st));
+    launch_photon_maps(B.keys[r], B.vals[r], n, B.rec, B.rec_sorted, B.start, B.end, c->sms, st);
+    mark();
+    M.Bc = bc;
+    pc.band0 = cb;
+    pc.Bc = bc;
+    pc.band_off = cb - band_first;
+    for (uint32_t s_ = 0; s_ < spp; ++s_) {
+      pc.s = s_;
+      launch_photon_camera(S, c->sp, c->d_cams, n_cams, pc, M, accum, probe, c->wb.status, c->sms, st);
+    }
+    mark();
+    launches += 1 + 16 + 1 + (int)spp;  // trace, 4 radix passes of 4 kernels, ranges, camera passes
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  if (xyz_dev) {
+    XyzWeights xw;
+    xw.w32 = c->d_cmfw + 3 * (size_t)band_first;
+    xw.band_count = band_count;
+    xw.kpad = (band_count + 15) / 16 * 16;
+    launch_xyz(accum, npix, xw, spp, (int)o.xyz_mode, xyz_dev, st, c->wb.status, c->sms);
+    ++launches;
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  mark();
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->paths = ACC64 * spp;
+    stats->kernel_launches = (uint32_t)launches;
+    stats->waves = (uint32_t)((band_count + Bc - 1) / Bc);
+    // stages: 0 photon pass, 1 photon maps (sort, ranges), 2 camera pass
+    for (size_t q = 0; q + 3 < ev.size(); q += 3) {
+      float a = 0, b = 0, d = 0;
+      cudaEventElapsedTime(&a, ev[q], ev[q + 1]);
+      cudaEventElapsedTime(&b, ev[q + 1], ev[q + 2]);
+      cudaEventElapsedTime(&d, ev[q + 2], ev[q + 3]);
+      stats->ms_stage[0] += a;
+      stats->ms_stage[1] += b;
+      stats->ms_stage[2] += d;
+    }
+    cudaEventElapsedTime(&stats->ms_render, ev.front(), ev[ev.size() - 2]);
+    cudaEventElapsedTime(&stats->ms_xyz, ev[ev.size() - 2], ev.back());
+  }
+  for (auto e : ev) cudaEventDestroy(e);
+  return status_to_rt(c, *c->h_status);
+}

@@ -134,7 +134,15 @@ size_t lbvh_scratch_bytes(uint32_t n);
 void launch_lbvh(const float* verts, const uint32_t* tri, uint32_t n, const float lo[3], const float hi[3], float pad,
                  const float4* tri_in, const float4* nrm_in, void* scratch, float4* nodes4, float4* tri_out,
                  float4* nrm_out, uint32_t** counts_out, int sms, cudaStream_t st);
-constexpr int kLbvhLevels = 64;  // collapse levels launched (counts has 2 + kLbvhLevels entries)
+constexpr int kLbvhLevels = 64;
+// Stable LSD radix sort of (key, value) pairs by the low key_bits bits, 8
+// bits per pass (rt_lbvh.cu): keys[0] / vals[0] in, the result in
+// keys[r] / vals[r] for the returned r; n <= 2^24; hist holds
+// radix_sort_hist_words(n) words.
+size_t radix_sort_hist_words(uint32_t n);
+int launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t n, uint32_t key_bits, uint32_t* hist,
+                      cudaStream_t st);
+  // collapse levels launched (counts has 2 + kLbvhLevels entries)
 
 // Per-wave device counters, one row per vertex k (0 .. depth).
 struct Counters {
@@ -240,6 +248,46 @@ void launch_xyz(const double* spectral, uint64_t n_pixels, const XyzWeights& w, 
                 cudaStream_t st, uint32_t* status, int sms);
 
 int num_sms(int device);
+// Photon mapping (section 4; rt_photon.cu, kernels in rt_kernels.cu).
+// Photon pass over bands band0 .. band0 + Bc - 1, N photons per band: slot
+// (j * N + i) * depth + n holds the n-th diffuse hit of photon i of band
+// band0 + j as {x, y, z, flux}; its sort key is kPhotonEmpty, or for a
+// caustic (map 0) or indirect (map 1) photon ((map * Bc + j) << hbits) |
+// hash of its cell (cells of edge 2 r of the map).
+constexpr uint32_t kPhotonEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kPhotonMaxSlots = 1u << 24;
+struct PhotonPass {
+  uint32_t band0, Bc, N, depth;
+  uint32_t key0, key1;       // Philox key of the photon pass
+  float3 c0, t1, t2;         // emission disk: centre and basis (t1, t2 span the disk)
+  float Rd, flux;            // disk radius; Omega pi Rd^2 / N
+  float inv_cell[2];         // 1 / (2 r) of the caustic and indirect maps
+  uint32_t hbits;            // 2^hbits hash cells per (map, band)
+};
+// The maps after sorting: rec holds the records in key order; start / end
+// the record range of each key (empty: start = end = 0).
+struct PhotonMaps {
+  const uint32_t* start;
+  const uint32_t* end;
+  const float4* rec;
+  float r2[2], inv_cell[2], norm[2];  // r^2, 1 / (2 r), 1 / (pi r^2) per map
+  uint32_t hbits, Bc;
+};
+// Camera pass of one sample s for the bands of the photon pass: paths
+// (pixel, j) add to accum[pixel * B + band_off + j].
+struct PhotonCam {
+  uint32_t s, s_base, spp, npix, depth;
+  uint32_t band0, Bc, band_off, B;
+  uint32_t key0, key1;
+};
+void launch_photon_trace(const DevScene& S, const DevSpectra& P, const PhotonPass& pp, float4* rec, uint32_t* keys,
+                         uint32_t* vals, uint8_t* cls, uint32_t* status, int sms, cudaStream_t st);
+void launch_photon_maps(const uint32_t* sorted_keys, const uint32_t* sorted_vals, uint32_t n, const float4* rec,
+                        float4* rec_sorted, uint32_t* start, uint32_t* end, int sms, cudaStream_t st);
+void launch_photon_camera(const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
+                          const PhotonCam& pc, const PhotonMaps& M, double* accum, const Probe& probe,
+                          uint32_t* status, int sms, cudaStream_t st);
+
 int trace_blocks_per_sm(int block);
 int shadow_blocks_per_sm(int block);
 

@@ -13,6 +13,7 @@
 // Each path owns one output slot (pixel, band) in the wave, so the FP64
 // accumulation into the spectral image needs no atomics: different samples
 // of a slot are in different waves, which run in sample order.
+#include <algorithm>
 #include <cstdio>
 
 #include "rt_device.cuh"
@@ -1319,6 +1320,303 @@ __global__ void __launch_bounds__(512) k_l2_probe(const float4* __restrict__ buf
   if (acc == 1.2345f) sink[0] = acc;
 }
 
+// ---- photon mapping (section 4) ----------------------------------------
+
+// Spatial hash of an integer cell (three large odd multipliers, xor).
+__device__ __forceinline__ uint32_t photon_cell_hash(int ix, int iy, int iz, uint32_t hbits) {
+  const uint32_t h = ((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u);
+  return h & ((1u << hbits) - 1u);
+}
+
+// Photon pass: one thread per photon.  Emission from the disk tangent to the
+// scene's bounding sphere on the sun's side, direction minus a uniform
+// sample of the sun cone, flux L_sun cos Omega pi R_d^2 / N; then the path
+// tracer's material rules, storing every Lambertian hit (direct: only
+// thin-glass transmissions before it; caustic: a reflection or refraction
+// before the first diffuse hit; indirect: after a diffuse hit).
+__global__ void __launch_bounds__(128) k_photon_trace(DevScene S, DevSpectra P, PhotonPass pp,
+                                                      float4* __restrict__ rec, uint32_t* __restrict__ keys,
+                                                      uint32_t* __restrict__ vals, uint8_t* __restrict__ cls,
+                                                      uint32_t* status) {
+  const uint32_t total = pp.Bc * pp.N;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const uint32_t j = g / pp.N, i = g - j * pp.N;
+    const uint32_t b = pp.band0 + j;
+    const size_t slot0 = (size_t)g * pp.depth;
+    for (uint32_t q = 0; q < pp.depth; ++q) {
+      keys[slot0 + q] = kPhotonEmpty;
+      vals[slot0 + q] = (uint32_t)(slot0 + q);
+      rec[slot0 + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (cls) cls[slot0 + q] = 0;
+    }
+    const uint4 r0 = philox4x32_10(make_uint4(i, b, 0u, 0u), pp.key0, pp.key1);
+    const float rad = pp.Rd * sqrtf(u01(r0.x));
+    float sp, cp;
+    sincospif(2.0f * u01(r0.y), &sp, &cp);
+    float3 o = make_float3(pp.c0.x + rad * (cp * pp.t1.x + sp * pp.t2.x), pp.c0.y + rad * (cp * pp.t1.y + sp * pp.t2.y),
+                           pp.c0.z + rad * (cp * pp.t1.z + sp * pp.t2.z));
+    const float om = u01(r0.z) * P.one_minus_cos;
+    const float ct = 1.0f - om;
+    const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
+    float sp2, cp2;
+    sincospif(2.0f * u01(r0.w), &sp2, &cp2);
+    float3 d = make_float3(-(st * cp2 * pp.t1.x + st * sp2 * pp.t2.x + ct * P.sun.x),
+                           -(st * cp2 * pp.t1.y + st * sp2 * pp.t2.y + ct * P.sun.y),
+                           -(st * cp2 * pp.t1.z + st * sp2 * pp.t2.z + ct * P.sun.z));
+    float phi = __ldg(P.sunL + b) * ct * pp.flux;
+    bool nee_path = true;
+    uint32_t n_diff = 0;
+    for (uint32_t k = 1; k <= pp.depth; ++k) {
+      float t;
+      int leaf;
+      closest_hit(S, o, d, t, leaf, status);
+      if (leaf < 0) break;
+      const float3 p = madd(o, t, d);
+      const float4 nr = ldg4(S.nrm + leaf);
+      const uint32_t mat = __float_as_uint(nr.w);
+      const float3 ng = f3(nr);
+      const float3 n = dot(ng, d) < 0.0f ? ng : neg(ng);
+      const float cos_i = -dot(d, n);
+      const float4 m = ldg4(P.mb + mat * P.n_bands + b);
+      const int type = __ldg(P.mtype + mat);
+      const uint4 u = philox4x32_10(make_uint4(i, b, 0u, 4u * k), pp.key0, pp.key1);
+      if (type == 0 || type == 3) {
+        const uint32_t c = n_diff > 0u ? 3u : (nee_path ? 1u : 2u);
+        const size_t slot = slot0 + n_diff;
+        rec[slot] = make_float4(p.x, p.y, p.z, phi);
+        if (cls) cls[slot] = (uint8_t)c;
+        if (c != 1u) {
+          const uint32_t map = c == 2u ? 0u : 1u;
+          const float ic = pp.inv_cell[map];
+          const uint32_t h = photon_cell_hash((int)floorf(p.x * ic), (int)floorf(p.y * ic), (int)floorf(p.z * ic),
+                                              pp.hbits);
+          keys[slot] = ((map * pp.Bc + j) << pp.hbits) | h;
+        }
+        ++n_diff;
+        if (k == pp.depth) break;
+        const float rr = sqrtf(u01(u.z));
+        const float zz = sqrtf(fmaxf(0.0f, 1.0f - u01(u.z)));
+        float s2, c2;
+        sincospif(2.0f * u01(u.w), &s2, &c2);
+        float3 b1, b2;
+        onb(n, b1, b2);
+        d = make_float3(rr * c2 * b1.x + rr * s2 * b2.x + zz * n.x, rr * c2 * b1.y + rr * s2 * b2.y + zz * n.y,
+                        rr * c2 * b1.z + rr * s2 * b2.z + zz * n.z);
+        o = madd(p, S.eps, n);
+        phi *= m.z;
+      } else if (type == 1) {
+        float Rs, Ts;
+        thin_sheet(cos_i, m.x, m.y, __ldg(P.ad + mat * P.n_bands + b), Rs, Ts);
+        if (k == pp.depth) break;
+        const uint4 u1 = philox4x32_10(make_uint4(i, b, 0u, 4u * k + 1u), pp.key0, pp.key1);
+        if (u01(u1.x) < Rs / (Rs + Ts)) {
+          d = madd(d, -2.0f * dot(d, n), n);
+          o = madd(p, S.eps, n);
+          nee_path = false;
+        } else {
+          o = madd(p, -S.eps, n);
+        }
+        phi *= Rs + Ts;
+      } else if (type == 4) {
+        const bool inside = dot(ng, d) > 0.0f;
+        const float alpha = __ldg(P.ad + mat * P.n_bands + b);
+        if (inside) phi *= expf(-alpha * t);
+        if (k == pp.depth) break;
+        const float eta = inside ? 1.0f / m.x : m.x;
+        const float R = fresnel_complex(cos_i, eta, 0.0f);
+        const float r = inside ? m.x : 1.0f / m.x;
+        const float kk = 1.0f - r * r * (1.0f - cos_i * cos_i);
+        const uint4 u1 = philox4x32_10(make_uint4(i, b, 0u, 4u * k + 1u), pp.key0, pp.key1);
+        if (u01(u1.x) < R || kk < 0.0f) {
+          d = madd(d, -2.0f * dot(d, n), n);
+        } else {
+          const float3 td = madd(make_float3(r * d.x, r * d.y, r * d.z), r * cos_i - sqrtf(kk), n);
+          const float il = rsqrtf(dot(td, td));
+          d = make_float3(td.x * il, td.y * il, td.z * il);
+        }
+        const float step = S.eps / fmaxf(fabsf(dot(d, n)), 0.0625f);
+        if (dot(d, ng) < 0.0f) phi *= expf(-alpha * step);
+        o = madd(p, step, d);
+        nee_path = false;
+      } else {
+        const float R = fresnel_complex(cos_i, m.x, m.y);
+        if (k == pp.depth) break;
+        d = madd(d, -2.0f * dot(d, n), n);
+        o = madd(p, S.eps, n);
+        phi *= R;
+        nee_path = false;
+      }
+    }
+  }
+}
+
+// Record ranges per key of the sorted photon slots, and the records in key
+// order.
+__global__ void k_photon_bounds(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ sv, uint32_t n,
+                                const float4* __restrict__ rec, float4* __restrict__ rs, uint32_t* __restrict__ start,
+                                uint32_t* __restrict__ end) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t key = sk[q];
+    if (key == kPhotonEmpty) continue;
+    rs[q] = rec[sv[q]];
+    if (q == 0u || sk[q - 1] != key) start[key] = q;
+    if (q + 1u == n || sk[q + 1] != key) end[key] = q + 1u;
+  }
+}
+
+// Flux of the photons of band j in map `map` within distance r of x: the
+// (at most 8) cells of edge 2 r that the ball touches, duplicates of a
+// hashed key skipped.
+__device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map, uint32_t j, float3 x) {
+  const float ic = M.inv_cell[map];
+  const float r = sqrtf(M.r2[map]);
+  const int lx = (int)floorf((x.x - r) * ic), hx = (int)floorf((x.x + r) * ic);
+  const int ly = (int)floorf((x.y - r) * ic), hy = (int)floorf((x.y + r) * ic);
+  const int lz = (int)floorf((x.z - r) * ic), hz = (int)floorf((x.z + r) * ic);
+  const uint32_t base = (map * M.Bc + j) << M.hbits;
+  uint32_t seen[8];
+  int ns = 0;
+  float sum = 0.0f;
+  for (int ix = lx; ix <= hx; ++ix)
+    for (int iy = ly; iy <= hy; ++iy)
+      for (int iz = lz; iz <= hz; ++iz) {
+        const uint32_t key = base | photon_cell_hash(ix, iy, iz, M.hbits);
+        bool dup = false;
+        for (int q = 0; q < ns; ++q) dup |= seen[q] == key;
+        if (dup || ns >= 8) continue;
+        seen[ns++] = key;
+        const uint32_t e = __ldg(M.end + key);
+        for (uint32_t q = __ldg(M.start + key); q < e; ++q) {
+          const float4 ph = ldg4(M.rec + q);
+          const float dx = ph.x - x.x, dy = ph.y - x.y, dz = ph.z - x.z;
+          if (dx * dx + dy * dy + dz * dz < M.r2[map]) sum += ph.w;
+        }
+      }
+  return sum;
+}
+
+// Camera pass of one sample: the path tracer's camera and specular events
+// up to the first Lambertian vertex, where emission, the sun's next-event
+// estimate and (rho / pi) x the photon irradiance of both maps are added.
+__global__ void __launch_bounds__(128) k_photon_camera(DevScene S, DevSpectra P, const DevCam* __restrict__ cams,
+                                                       uint32_t n_cams, PhotonCam pc, PhotonMaps M,
+                                                       double* __restrict__ accum, Probe probe, uint32_t* status) {
+  const uint32_t total = pc.npix * pc.Bc;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const uint32_t pix = q / pc.Bc, j = q - pix * pc.Bc;
+    const uint32_t b = pc.band0 + j;
+    uint32_t v = 0;
+    while (v + 1 < n_cams && cams[v + 1].offset <= pix) ++v;
+    const DevCam& C = cams[v];
+    const uint32_t local = pix - C.offset;
+    const uint32_t y = local / C.W, x = local - y * C.W;
+    const uint4 u0 = philox4x32_10(make_uint4(pix, pc.s, b, 0u), pc.key0, pc.key1);
+    const float sx = (2.0f * ((float)x + u01(u0.x)) / (float)C.W - 1.0f) * C.tha;
+    const float sy = (1.0f - 2.0f * ((float)y + u01(u0.y)) / (float)C.H) * C.th;
+    float3 d = make_float3(C.f.x + sx * C.r.x + sy * C.u.x, C.f.y + sx * C.r.y + sy * C.u.y,
+                           C.f.z + sx * C.r.z + sy * C.u.z);
+    d = mul(1.0f / sqrtf(dot(d, d)), d);
+    float3 o = C.pos;
+    float T = 1.0f, L = 0.0f;
+    bool covered = false;
+    uint32_t sg = 2166136261u;
+    for (uint32_t k = 1; k <= pc.depth; ++k) {
+      float t;
+      int leaf;
+      closest_hit(S, o, d, t, leaf, status);
+      if (leaf < 0) {
+        sg = mix_sig(sg, 0xFFFFFFFFu);
+        if (!covered && dot(d, P.sun) >= P.cos_max) L += T * __ldg(P.sunL + b);
+        break;
+      }
+      const float3 p = madd(o, t, d);
+      const float4 nr = ldg4(S.nrm + leaf);
+      const uint32_t mat = __float_as_uint(nr.w);
+      sg = mix_sig(sg, __float_as_uint(S.tris[3 * leaf].w));
+      const float3 ng = f3(nr);
+      const float3 n = dot(ng, d) < 0.0f ? ng : neg(ng);
+      const float cos_i = -dot(d, n);
+      const float4 m = ldg4(P.mb + mat * P.n_bands + b);
+      const int type = __ldg(P.mtype + mat);
+      const uint4 u = philox4x32_10(make_uint4(pix, pc.s, b, 4u * k), pc.key0, pc.key1);
+      if (type == 0 || type == 3) {
+        if (type == 3) L += T * m.w;
+        const float om = u01(u.x) * P.one_minus_cos;
+        const float ct = 1.0f - om;
+        const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
+        float sp_, cp_;
+        sincospif(2.0f * u01(u.y), &sp_, &cp_);
+        float3 t1, t2;
+        onb(P.sun, t1, t2);
+        const float3 wd = make_float3(st * cp_ * t1.x + st * sp_ * t2.x + ct * P.sun.x,
+                                      st * cp_ * t1.y + st * sp_ * t2.y + ct * P.sun.y,
+                                      st * cp_ * t1.z + st * sp_ * t2.z + ct * P.sun.z);
+        const float c = dot(n, wd);
+        if (c > 0.0f) {
+          uint32_t ngl;
+          const float Tr = shadow_T(S, P, madd(p, S.eps, n), wd, b, ngl, status);
+          sg = mix_sig(sg, ngl);
+          L += T * m.z * c * __ldg(P.sunL + b) * 2.0f * P.one_minus_cos * Tr;
+        }
+        const float E = photon_gather(M, 0u, j, p) * M.norm[0] + photon_gather(M, 1u, j, p) * M.norm[1];
+        L += T * m.z * (1.0f / 3.14159265358979f) * E;
+        break;
+      } else if (type == 1) {
+        float Rs, Ts;
+        thin_sheet(cos_i, m.x, m.y, __ldg(P.ad + mat * P.n_bands + b), Rs, Ts);
+        if (k == pc.depth) break;
+        const uint4 u1 = philox4x32_10(make_uint4(pix, pc.s, b, 4u * k + 1u), pc.key0, pc.key1);
+        if (u01(u1.x) < Rs / (Rs + Ts)) {
+          d = madd(d, -2.0f * dot(d, n), n);
+          o = madd(p, S.eps, n);
+          covered = false;
+        } else {
+          o = madd(p, -S.eps, n);
+        }
+        T *= Rs + Ts;
+      } else if (type == 4) {
+        const bool inside = dot(ng, d) > 0.0f;
+        const float alpha = __ldg(P.ad + mat * P.n_bands + b);
+        if (inside) T *= expf(-alpha * t);
+        if (k == pc.depth) break;
+        const float eta = inside ? 1.0f / m.x : m.x;
+        const float R = fresnel_complex(cos_i, eta, 0.0f);
+        const float r = inside ? m.x : 1.0f / m.x;
+        const float kk = 1.0f - r * r * (1.0f - cos_i * cos_i);
+        const uint4 u1 = philox4x32_10(make_uint4(pix, pc.s, b, 4u * k + 1u), pc.key0, pc.key1);
+        if (u01(u1.x) < R || kk < 0.0f) {
+          d = madd(d, -2.0f * dot(d, n), n);
+        } else {
+          const float3 td = madd(make_float3(r * d.x, r * d.y, r * d.z), r * cos_i - sqrtf(kk), n);
+          const float il = rsqrtf(dot(td, td));
+          d = make_float3(td.x * il, td.y * il, td.z * il);
+        }
+        const float step = S.eps / fmaxf(fabsf(dot(d, n)), 0.0625f);
+        if (dot(d, ng) < 0.0f) T *= expf(-alpha * step);
+        o = madd(p, step, d);
+        covered = false;
+      } else {
+        const float R = fresnel_complex(cos_i, m.x, m.y);
+        if (k == pc.depth) break;
+        d = madd(d, -2.0f * dot(d, n), n);
+        o = madd(p, S.eps, n);
+        T *= R;
+        covered = false;
+      }
+    }
+    const size_t slot = (size_t)pix * pc.B + pc.band_off + j;
+    if (L != 0.0f) accum[slot] += (double)L;
+    if (probe.map != nullptr) {
+      const uint32_t ps = probe.map[pix];
+      if (ps != 0xFFFFFFFFu) {
+        const size_t r = ((size_t)ps * pc.spp + (pc.s - pc.s_base)) * pc.B + pc.band_off + j;
+        probe.L[r] = L;
+        probe.sig[r] = sg;
+      }
+    }
+  }
+}
+
 // ---- single-step kernels for parity tests --------------------------------
 
 __global__ void k_philox(const uint4* __restrict__ ctr, uint4* __restrict__ out, uint64_t n, uint32_t k0, uint32_t k1) {
@@ -1516,6 +1814,26 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
     nl += 3;
   }
   if (launches) *launches += nl;
+}
+
+void launch_photon_trace(const DevScene& S, const DevSpectra& P, const PhotonPass& pp, float4* rec, uint32_t* keys,
+                         uint32_t* vals, uint8_t* cls, uint32_t* status, int sms, cudaStream_t st) {
+  const uint64_t n = (uint64_t)pp.Bc * pp.N;
+  const unsigned g = (unsigned)std::min<uint64_t>((n + 127) / 128, (uint64_t)(sms > 0 ? sms : 1) * 64);
+  k_photon_trace<<<g, 128, 0, st>>>(S, P, pp, rec, keys, vals, cls, status);
+}
+
+void launch_photon_maps(const uint32_t* sorted_keys, const uint32_t* sorted_vals, uint32_t n, const float4* rec,
+                        float4* rec_sorted, uint32_t* start, uint32_t* end, int sms, cudaStream_t st) {
+  k_photon_bounds<<<(sms > 0 ? sms : 1) * 8, 256, 0, st>>>(sorted_keys, sorted_vals, n, rec, rec_sorted, start, end);
+}
+
+void launch_photon_camera(const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
+                          const PhotonCam& pc, const PhotonMaps& M, double* accum, const Probe& probe,
+                          uint32_t* status, int sms, cudaStream_t st) {
+  const uint64_t n = (uint64_t)pc.npix * pc.Bc;
+  const unsigned g = (unsigned)std::min<uint64_t>((n + 127) / 128, (uint64_t)(sms > 0 ? sms : 1) * 64);
+  k_photon_camera<<<g, 128, 0, st>>>(S, P, cams, n_cams, pc, M, accum, probe, status);
 }
 
 void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st) {

@@ -309,6 +309,28 @@ __global__ void k_lbvh_init(int2* q0, uint32_t* counts, int* parent) {
 
 }  // namespace
 
+size_t radix_sort_hist_words(uint32_t n) {
+  const size_t nb = (n + kSortTile - 1) / kSortTile;
+  const size_t hist = (256 * nb + 32767) / 32768 * 32768;
+  return hist + hist / 1024;
+}
+
+int launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t n, uint32_t key_bits, uint32_t* hist,
+                      cudaStream_t st) {
+  const uint32_t nb = (n + kSortTile - 1) / kSortTile;
+  const size_t hist_n = ((size_t)256 * nb + 32767) / 32768 * 32768;
+  int cur = 0;
+  for (uint32_t shift = 0; shift < key_bits; shift += 8) {
+    cudaMemsetAsync(hist, 0, 4 * hist_n, st);
+    k_radix_hist<<<nb, kSortThreads, 0, st>>>(keys[cur], n, shift, hist, nb);
+    launch_scan(hist, hist_n, st);
+    k_radix_scatter<<<nb, kSortThreads, 0, st>>>(keys[cur], vals[cur], n, shift, hist, hist + hist_n, nb,
+                                                keys[cur ^ 1], vals[cur ^ 1]);
+    cur ^= 1;
+  }
+  return cur;
+}
+
 size_t lbvh_scratch_bytes(uint32_t n) {
   const size_t nb = (n + kSortTile - 1) / kSortTile;
   const size_t hist = (256 * nb + 32767) / 32768 * 32768;

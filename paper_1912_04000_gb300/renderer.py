@@ -161,6 +161,55 @@ class Renderer:
         out.update(spectral=sp, xyz=xz, stats=stats.as_dict())
         return out
 
+    def render_photons(self, cameras: Sequence, spp: int, depth: int, seed: int = 0, band_first: int = 0,
+                       band_count: Optional[int] = None, n_photons: int = 0, photon_depth: int = 0,
+                       r_caustic: float = 0.0, r_global: float = 0.0, log2_cells: int = 0,
+                       xyz_mode: int = _native.XYZ_BF16X3, probe_pixels=None, out_spectral=None):
+        """Photon-mapping render (rt_render_photons): dict(spectral [P, band_count]
+        f64 sums over samples, xyz [P, 3], stats, probe_L / probe_sig)."""
+        torch = self.torch
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        npix = sum(int(c.width) * int(c.height) for c in cameras)
+        dev = self.device
+        sp = out_spectral if out_spectral is not None else torch.empty((npix, band_count), dtype=torch.float64,
+                                                                      device=dev)
+        xz = torch.empty((npix, 3), dtype=torch.float32, device=dev)
+        o = _native.PhotonOpts()
+        o.n_photons, o.photon_depth, o.log2_cells, o.xyz_mode = n_photons, photon_depth, log2_cells, xyz_mode
+        o.r_caustic, o.r_global = r_caustic, r_global
+        out = {}
+        if probe_pixels is not None:
+            pp = torch.as_tensor(np.asarray(probe_pixels, np.int64), device=dev)
+            pmap = torch.full((npix,), -1, dtype=torch.int64, device=dev)
+            pmap[pp] = torch.arange(pp.shape[0], device=dev)
+            pmap32 = pmap.to(torch.int32)
+            pl = torch.zeros((pp.shape[0], spp, band_count), dtype=torch.float32, device=dev)
+            ps = torch.zeros((pp.shape[0], spp, band_count), dtype=torch.int32, device=dev)
+            o.probe_map_dev, o.probe_L_dev, o.probe_sig_dev = pmap32.data_ptr(), pl.data_ptr(), ps.data_ptr()
+            out.update(probe_L=pl, probe_sig=ps, _keep=pmap32)
+        stats = _native.Stats()
+        st = self.lib.rt_render_photons(self._h, _native.cameras_struct(cameras), len(cameras), band_first,
+                                        band_count, spp, depth, seed, C.byref(o), _ptr(sp), _ptr(xz),
+                                        C.byref(stats))
+        self._check("rt_render_photons", st)
+        out.update(spectral=sp, xyz=xz, stats=stats.as_dict())
+        return out
+
+    def photon_records(self, n_photons: int, depth: int, seed: int = 0, band_first: int = 0,
+                       band_count: Optional[int] = None):
+        """Photon pass alone: (records [band_count, n_photons, depth, 4] float32
+        {x, y, z, flux}, classes [band_count, n_photons, depth] uint8)."""
+        torch = self.torch
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        rec = torch.zeros((band_count, n_photons, depth, 4), dtype=torch.float32, device=self.device)
+        cls = torch.zeros((band_count, n_photons, depth), dtype=torch.uint8, device=self.device)
+        st = self.lib.rt_photon_records(self._h, band_first, band_count, n_photons, depth, seed, rec.data_ptr(),
+                                        cls.data_ptr())
+        self._check("rt_photon_records", st)
+        return rec, cls
+
     def render_host(self, cameras, spp, depth, seed=0, band_first=0, band_count=None, spectral=False,
                     xyz_mode=_native.XYZ_BF16X3, wave_capacity=0, xyz_out=None, spectral_out=None):
         """Host outputs (numpy; pinned torch tensors may be passed as outputs)."""

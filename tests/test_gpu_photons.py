@@ -1,0 +1,104 @@
+"""Photon mapping on the GPU (rt_photon_records, rt_render_photons) against
+the oracle's photon mapping: photon records slot by slot (the box, the
+dispersive prism, the mirror caustic), rendered images, the mirror
+caustic's closed form, band chunking, determinism and argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_04000_gb300 import scenes
+from paper_1912_04000_gb300._native import RtError
+
+from parity import assert_parity, xyz_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1912_04000_gb300.renderer import Renderer
+    return Renderer(0)
+
+
+def _diag(wl):
+    v = wl.scene.verts.astype(np.float64)
+    return float(np.linalg.norm(v.max(0) - v.min(0)))
+
+
+@pytest.mark.parametrize("name", ["tiny_box", "prism_room", "mirror_caustic"])
+def test_photon_records(R, name):
+    wl = {"tiny_box": lambda: scenes.tiny_box(n_bands=4),
+          "prism_room": lambda: scenes.prism_room(n_bands=4),
+          "mirror_caustic": lambda: scenes.mirror_caustic()}[name]()
+    R.load(wl)
+    N, depth = 1 << 13, 4
+    rec, cls = (x.cpu().numpy() for x in R.photon_records(N, depth, seed=5))
+    pos, ocls = oracle.OracleScene(wl.scene, wl.spectra).photon_records(N, depth, seed=5)
+    same = (cls == ocls).all(-1)                       # whole photon paths with the same classes
+    print(name, "photons with identical stores", same.mean(), "classes", np.bincount(ocls.ravel(), minlength=4))
+    assert same.mean() >= 0.99
+    st = (ocls > 0) & same[..., None]
+    np.testing.assert_allclose(rec[..., :3][st], pos[..., :3][st], rtol=0, atol=2e-5 * _diag(wl))
+    np.testing.assert_allclose(rec[..., 3][st], pos[..., 3][st], rtol=2e-5)
+
+
+@pytest.mark.parametrize("name", ["tiny_box", "prism_room", "mirror_caustic"])
+def test_photon_render(R, name):
+    if name == "tiny_box":
+        wl, kw = scenes.tiny_box(width=64, height=64, n_bands=4, spp=2, depth=6), dict(r_global=0.15)
+    elif name == "prism_room":
+        wl, kw = scenes.prism_room(width=64, height=48, n_bands=4, spp=2), dict(r_caustic=0.04, r_global=0.15)
+    else:
+        wl, kw = scenes.mirror_caustic(width=32, height=32, spp=2), dict(r_caustic=0.1, r_global=0.3)
+    R.load(wl)
+    N, pd = 1 << 15, 4
+    out = R.render_photons(wl.cameras, wl.spp, wl.depth, wl.seed, n_photons=N, photon_depth=pd, **kw)
+    o = oracle.OracleScene(wl.scene, wl.spectra).render_photons(
+        wl.cameras, wl.spp, wl.depth, wl.seed, n_photons=N, photon_depth=pd,
+        r_caustic=kw.get("r_caustic", 0.005 * _diag(wl)), r_global=kw.get("r_global", 0.02 * _diag(wl)))
+    m = xyz_parity(out["xyz"].cpu().numpy(), o["xyz"])
+    print(name, "photon-mapping parity", m, out["stats"]["ms_stage"][:3])
+    assert_parity(out["xyz"].cpu().numpy(), o["xyz"], name)
+
+
+def test_mirror_caustic_closed_form(R):
+    e, a, rho = math.radians(45.0), 0.02, 0.8
+    wl = scenes.mirror_caustic(elevation_deg=45.0, sun_half_angle=a, rho=rho, width=4, height=4, spp=8)
+    R.load(wl)
+    N, r = 1 << 20, 0.15
+    got = R.render_photons(wl.cameras, wl.spp, wl.depth, wl.seed, n_photons=N, photon_depth=3, r_caustic=r,
+                           r_global=0.3, xyz_mode=2)["spectral"].cpu().numpy()[:, 0] / wl.spp
+    Rm = oracle.fresnel(math.cos(e), 0.3, 3.0)
+    E = math.pi * math.sin(a) ** 2 * math.sin(e)
+    want = rho / math.pi * E * (1.0 + Rm)
+    assert np.all(np.abs(got / want - 1.0) < 0.05), (got, want)
+
+
+def test_chunks_hash_sizes_and_determinism(R):
+    # 40 bands: log2_cells 20 splits them into chunks of 32 and 8, 12 keeps
+    # one chunk; the hash size changes only the summation order
+    wl = scenes.tiny_box(width=32, height=32, n_bands=40, spp=1, depth=5)
+    R.load(wl)
+    kw = dict(n_photons=4096, photon_depth=4, r_global=0.15, xyz_mode=2)
+    a = R.render_photons(wl.cameras, 1, 5, 3, log2_cells=20, **kw)
+    b = R.render_photons(wl.cameras, 1, 5, 3, log2_cells=12, **kw)
+    assert a["stats"]["waves"] == 2 and b["stats"]["waves"] == 1
+    sa, sb = a["spectral"].cpu().numpy(), b["spectral"].cpu().numpy()
+    np.testing.assert_allclose(sa, sb, rtol=1e-5, atol=1e-12)
+    c = R.render_photons(wl.cameras, 1, 5, 3, log2_cells=20, **kw)["spectral"].cpu().numpy()
+    assert np.array_equal(sa, c)
+
+
+def test_arguments_checked(R):
+    wl = scenes.tiny_box(width=8, height=8, n_bands=2, spp=1)
+    R.load(wl)
+    with pytest.raises(RtError):
+        R.render_photons(wl.cameras, 1, 4, 0, n_photons=1 << 23, photon_depth=4)
+    with pytest.raises(RtError):
+        R.render_photons(wl.cameras, 1, 4, 0, log2_cells=30)
+    wide = scenes.plate_under_sky()  # half angle pi: no emission disk
+    R.load(wide)
+    with pytest.raises(RtError):
+        R.render_photons(wide.cameras, 1, 2, 0)
