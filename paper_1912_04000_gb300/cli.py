@@ -56,6 +56,9 @@ def main(argv=None):
                    help="BVH builder: binned SAH on the host or linear BVH on the device")
     r.add_argument("--bands-per-path", type=int, default=1, choices=[1, 4],
                    help="4: every path carries four bands until its first refraction")
+    r.add_argument("--estimator", default="path", choices=["path", "photon"],
+                   help="path tracing, or photon mapping (caustic + indirect maps, density estimates)")
+    r.add_argument("--photons", type=int, default=0, help="photon mapping: photons per band (0 = 65536)")
     r.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
@@ -72,6 +75,10 @@ def main(argv=None):
         tuned, _ = tuned_options(R, wl)
     out = None
     for _ in range(args.repeat):
+        if args.estimator == "photon":
+            out = R.render_photons(wl.cameras, wl.spp, wl.depth, wl.seed, n_photons=args.photons,
+                                   xyz_mode=args.xyz_mode)
+            continue
         out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=args.xyz_mode, wave_capacity=args.wave,
                        guided=args.guided, guide_collect=args.guide_collect,
                        guide_train_steps=args.guide_train_steps, use_graph=args.graph, tuned=tuned,
