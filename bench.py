@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--photon-depth", type=int, default=4)
     ap.add_argument("--r-caustic", type=float, default=0.0)
     ap.add_argument("--r-global", type=float, default=0.0)
+    ap.add_argument("--photon-emission", type=int, default=0, choices=[0, 1],
+                    help="photon emission: 0 disk around the scene, 1 thin-glass portals")
     ap.add_argument("--mse-width", type=int, default=256)
     ap.add_argument("--mse-height", type=int, default=192)
     ap.add_argument("--mse-ref-spp", type=int, default=4096)
@@ -380,7 +382,7 @@ def run_photon_mse(args):
         return float(np.mean((x - ref_xyz) ** 2))
 
     pkw = dict(n_photons=args.photons, photon_depth=args.photon_depth, r_caustic=args.r_caustic,
-               r_global=args.r_global)
+               r_global=args.r_global, emission=args.photon_emission)
     R.render_photons(wl.cameras, 1, wl.depth, 5, **pkw)  # warm
     R.render(wl.cameras, 4, wl.depth, 5)
     pt, t_pt = timed(lambda: R.render(wl.cameras, args.mse_spp, wl.depth, 0))
@@ -395,7 +397,8 @@ def run_photon_mse(args):
         "metric": "equal-time MSE, photon mapping vs path tracing (XYZ, vs a path-traced reference)",
         "config": {"workload": f"{args.bands_workload}_{args.mse_width}x{args.mse_height}_b{B}_d{wl.depth}",
                    "reference_spp": args.mse_ref_spp, "photons_per_band": args.photons,
-                   "photon_depth": args.photon_depth},
+                   "photon_depth": args.photon_depth,
+                   "photon_emission": ("disk", "portals")[args.photon_emission]},
         "path_tracing": {"spp": args.mse_spp, "seconds": t_pt, "mse_xyz": e_pt},
         "photon_mapping": {"spp": spp_pm, "seconds": t_pm, "mse_xyz": e_pm,
                            "photon_pass_ms": pm["stats"]["ms_stage"][0], "map_build_ms": pm["stats"]["ms_stage"][1],

@@ -240,10 +240,10 @@ rt_status rt_render_host(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, ui
  * caustic map) or indirect (after a diffuse hit: global map).  Then the
  * camera pass: camera paths follow thin-glass, conductor and solid-glass
  * events as in rt_render; at the first Lambertian vertex they add its
- * emission, the sun's next-event estimate and
- *   (rho / pi) [sum of caustic flux within r_caustic / (pi r_caustic^2)
- *             + sum of indirect flux within r_global / (pi r_global^2)]
- * over the photons of the path's band, and stop.  The maps are spatial hash
+ * emission, the sun's next-event estimate and (rho / pi) E, E the kernel
+ * density estimate of the irradiance over the photons of the path's band,
+ *   E = sum over both maps of (2 / (pi r^2)) sum_{d < r} flux (1 - d^2 / r^2)
+ * (Epanechnikov kernel; r = r_caustic, r_global), and stop.  The maps are spatial hash
  * grids (cells of edge 2 r, 2^log2_cells per map and band) built on the
  * device by a stable radix sort of the photon records; bands are processed
  * in chunks whose photon records fit one sort (n_photons x photon_depth x
@@ -263,7 +263,13 @@ typedef struct {
   const uint32_t* probe_map_dev;
   float* probe_L_dev;
   uint32_t* probe_sig_dev;
-  uint32_t reserved[4];
+  uint32_t emission;      /* 0: the disk above; 1: portals -- photons start on the thin-glass triangles
+                           * that face the sun, chosen by A |s . n|, uniform on the triangle, direction in
+                           * the cone, flux L_sun |w . n| Omega W / (n_photons |s . n|) (W = sum A |s . n|),
+                           * none where the way back to the sun is blocked.  For interiors lit through
+                           * glass; sunlight that reaches the glass after an outside bounce is not
+                           * emitted.  Needs a thin-glass triangle facing the sun (else RT_ERR_ARG) */
+  uint32_t reserved[3];
 } rt_photon_opts;
 rt_status rt_render_photons(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
                             uint32_t band_count, uint32_t spp, uint32_t depth, uint64_t seed,
@@ -273,7 +279,7 @@ rt_status rt_render_photons(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams,
  * Lambertian hit, cls_dev (device, may be NULL) the class of each slot
  * (0 empty, 1 direct, 2 caustic, 3 indirect). */
 rt_status rt_photon_records(rt_ctx* ctx, uint32_t band_first, uint32_t band_count, uint32_t n_photons,
-                            uint32_t depth, uint64_t seed, float* rec_dev, uint8_t* cls_dev);
+                            uint32_t depth, uint64_t seed, uint32_t emission, float* rec_dev, uint8_t* cls_dev);
 
 /* Same result as rt_render, for callers that may not allocate device memory
  * (a framework that has reserved the device memory for its own pool, a fixed

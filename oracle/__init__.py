@@ -99,11 +99,11 @@ def lib():
             L.or_render4.argtypes = L.or_render.argtypes
             L.or_photon_records.restype = C.c_int
             L.or_photon_records.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
-                                            C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.c_int]
+                                            C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint8), C.c_int]
             L.or_photon_render.restype = C.c_int
             L.or_photon_render.argtypes = [C.c_void_p, C.POINTER(_Camera), C.c_uint32, C.c_uint32, C.c_uint32,
                                            C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double,
-                                           C.c_double, C.POINTER(C.c_uint32), C.c_uint64, C.POINTER(C.c_double),
+                                           C.c_double, C.c_int, C.POINTER(C.c_uint32), C.c_uint64, C.POINTER(C.c_double),
                                            C.POINTER(C.c_double), C.POINTER(C.c_uint32), C.c_int]
             L.or_xyz.argtypes = [C.POINTER(C.c_double), C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.POINTER(C.c_float), C.POINTER(C.c_double)]
@@ -280,22 +280,24 @@ PHOTON_CLASSES = {0: "empty", 1: "direct", 2: "caustic", 3: "indirect"}
 
 
 def _photon_methods():
-    def photon_records(self, n_photons, depth, seed=0, band_first=0, band_count=None, n_threads=0):
+    def photon_records(self, n_photons, depth, seed=0, band_first=0, band_count=None, n_threads=0, emission=0):
         """Photon pass: pos_phi [band_count, n_photons, depth, 4] (position,
-        flux) and cls (0 empty, 1 direct, 2 caustic, 3 indirect)."""
+        flux) and cls (0 empty, 1 direct, 2 caustic, 3 indirect); emission 0 =
+        disk, 1 = through the thin-glass portals."""
         if band_count is None:
             band_count = self.n_bands - band_first
         n = band_count * n_photons * depth
         pos = np.zeros((n, 4), np.float64)
         cls = np.zeros(n, np.uint8)
-        rc = lib().or_photon_records(self._h, band_first, band_count, n_photons, depth, seed, _ptr(pos, C.c_double),
-                                     _ptr(cls, C.c_uint8), n_threads)
+        rc = lib().or_photon_records(self._h, band_first, band_count, n_photons, depth, seed, emission,
+                                     _ptr(pos, C.c_double), _ptr(cls, C.c_uint8), n_threads)
         if rc != 0:
             raise ValueError(f"or_photon_records failed ({rc})")
         return pos.reshape(band_count, n_photons, depth, 4), cls.reshape(band_count, n_photons, depth)
 
     def render_photons(self, cameras, spp, depth, seed=0, n_photons=1 << 14, photon_depth=4, r_caustic=0.05,
-                       r_global=0.2, band_first=0, band_count=None, pixels=None, record_paths=False, n_threads=0):
+                       r_global=0.2, band_first=0, band_count=None, pixels=None, record_paths=False, n_threads=0,
+                       emission=0):
         """Photon-mapping estimate of the listed pixels (layout as render)."""
         if band_count is None:
             band_count = self.n_bands - band_first
@@ -306,7 +308,8 @@ def _photon_methods():
         pl = np.zeros((npx, spp, band_count), np.float64) if record_paths else None
         ps = np.zeros((npx, spp, band_count), np.uint32) if record_paths else None
         rc = lib().or_photon_render(self._h, cameras_struct(cameras), len(cameras), band_first, band_count, spp, depth,
-                                    seed, n_photons, photon_depth, r_caustic, r_global, _ptr(pix, C.c_uint32), npx,
+                                    seed, n_photons, photon_depth, r_caustic, r_global, emission,
+                                    _ptr(pix, C.c_uint32), npx,
                                     _ptr(ssum, C.c_double), _ptr(pl, C.c_double) if pl is not None else None,
                                     _ptr(ps, C.c_uint32) if ps is not None else None, n_threads)
         if rc != 0:

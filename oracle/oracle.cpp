@@ -951,6 +951,12 @@ struct PhotonRec {
 struct PhotonSetup {
   V3 c0, t1, t2;
   double Rd = 0.0, omega = 0.0;
+  // portal emission: thin-glass triangles with their sun-side normal and
+  // the cumulative share of A |s . n| (the last entry 1)
+  std::vector<uint32_t> portal;
+  std::vector<V3> portal_n;
+  std::vector<double> cdf;
+  double W = 0.0;  // sum of A |s . n|
 };
 
 PhotonSetup photon_setup(const OScene& S) {
@@ -962,26 +968,76 @@ PhotonSetup photon_setup(const OScene& S) {
   P.Rd = R * (sa / S.cos_max + 1.0 / S.cos_max);
   P.omega = 2.0 * M_PI * (1.0 - S.cos_max);
   onb(S.sun, &P.t1, &P.t2);
+  for (uint32_t t = 0; t < S.a.size(); ++t) {
+    if (S.mtype[S.mat[t]] != M_GLASS) continue;
+    const V3 c = cross(S.b[t] - S.a[t], S.c[t] - S.a[t]);
+    const double area2 = std::sqrt(dot(c, c));
+    if (!(area2 > 0.0)) continue;
+    V3 n = (1.0 / area2) * c;
+    const double cs = dot(n, S.sun);
+    if (cs == 0.0) continue;
+    if (cs < 0.0) n = -1.0 * n;
+    P.portal.push_back(t);
+    P.portal_n.push_back(n);
+    P.W += 0.5 * area2 * std::fabs(cs);
+    P.cdf.push_back(P.W);
+  }
+  for (double& x : P.cdf) x /= P.W;
+  if (!P.cdf.empty()) P.cdf.back() = 1.0;
   return P;
 }
 
+// Portal emission (emission = 1), for interiors lit through thin glass: a
+// photon starts on a thin-glass triangle chosen with probability
+// proportional to A |s . n| (u0, the first triangle whose cumulative share
+// exceeds u0), at a uniform point (u1, u2: barycentrics (1 - sqrt u1,
+// sqrt u1 (1 - u2), sqrt u1 u2)), eps off its sun side, with w uniform in
+// the cone (counter call 1); it carries L_sun |w . n| Omega W / (N |s . n|),
+// W = sum A |s . n|, or nothing when w grazes the face from behind or the
+// way back to the sun is blocked.  Sunlight that reaches the glass only
+// after a bounce outside is not emitted.
 void trace_photons(const OScene& S, uint32_t band_first, uint32_t band_count, uint32_t N, uint32_t depth,
-                   uint64_t seed, std::vector<PhotonRec>& out, int n_threads) {
+                   uint64_t seed, std::vector<PhotonRec>& out, int n_threads, int emission = 0) {
   out.assign((size_t)band_count * N * depth, PhotonRec{});
   const PhotonSetup P = photon_setup(S);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ 0x50484F54u;
   auto one = [&](uint32_t j, uint32_t i) {
     const uint32_t b = band_first + j;
     Ctr4 r0 = philox4x32_10(Ctr4{{i, b, 0u, 0u}}, k0, k1);
-    const double rad = P.Rd * std::sqrt(u01(r0.w[0]));
-    const double ph = 2.0 * M_PI * u01(r0.w[1]);
-    V3 o = P.c0 + (rad * std::cos(ph)) * P.t1 + (rad * std::sin(ph)) * P.t2;
-    const double ct = 1.0 - u01(r0.w[2]) * (1.0 - S.cos_max);
-    const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
-    const double ph2 = 2.0 * M_PI * u01(r0.w[3]);
-    V3 w = (st * std::cos(ph2)) * P.t1 + (st * std::sin(ph2)) * P.t2 + ct * S.sun;
-    V3 d = -1.0 * w;
-    double phi = S.sunL[b] * ct * P.omega * M_PI * P.Rd * P.Rd / N;
+    V3 o, d;
+    double phi;
+    if (emission == 0) {
+      const double rad = P.Rd * std::sqrt(u01(r0.w[0]));
+      const double ph = 2.0 * M_PI * u01(r0.w[1]);
+      o = P.c0 + (rad * std::cos(ph)) * P.t1 + (rad * std::sin(ph)) * P.t2;
+      const double ct = 1.0 - u01(r0.w[2]) * (1.0 - S.cos_max);
+      const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+      const double ph2 = 2.0 * M_PI * u01(r0.w[3]);
+      V3 w = (st * std::cos(ph2)) * P.t1 + (st * std::sin(ph2)) * P.t2 + ct * S.sun;
+      d = -1.0 * w;
+      phi = S.sunL[b] * ct * P.omega * M_PI * P.Rd * P.Rd / N;
+    } else {
+      const double u0 = u01(r0.w[0]);
+      size_t q = 0;
+      while (q + 1 < P.cdf.size() && P.cdf[q] <= u0) ++q;
+      const uint32_t t = P.portal[q];
+      const V3 n = P.portal_n[q];
+      const double su = std::sqrt(u01(r0.w[1])), u2 = u01(r0.w[2]);
+      const V3 pg = (1.0 - su) * S.a[t] + (su * (1.0 - u2)) * S.b[t] + (su * u2) * S.c[t];
+      Ctr4 r1 = philox4x32_10(Ctr4{{i, b, 0u, 1u}}, k0, k1);
+      const double ct = 1.0 - u01(r1.w[0]) * (1.0 - S.cos_max);
+      const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+      const double ph2 = 2.0 * M_PI * u01(r1.w[1]);
+      V3 w = (st * std::cos(ph2)) * P.t1 + (st * std::sin(ph2)) * P.t2 + ct * S.sun;
+      const double wn = dot(w, n);
+      if (!(wn > 0.0)) return;
+      o = pg + S.eps * n;
+      double tb;
+      uint32_t pb;
+      if (closest(S, o, w, &tb, &pb)) return;  // the sun does not see this point
+      d = -1.0 * w;
+      phi = S.sunL[b] * wn * P.omega * P.W / (N * dot(S.sun, n));
+    }
     bool nee_path = true;
     uint32_t n_diff = 0;
     const size_t slot0 = ((size_t)j * N + i) * depth;
@@ -1065,8 +1121,9 @@ void trace_photons(const OScene& S, uint32_t band_first, uint32_t band_count, ui
   for (auto& q : th) q.join();
 }
 
-// Photons of one band and class in a uniform grid of cell size r; the sum of
-// the flux of the photons within distance r of x (27 cells cover the ball).
+// Photons of one band and class in a uniform grid of cell size r; the
+// kernel-weighted flux sum over the photons within distance r of x (27 cells
+// cover the ball), with the Epanechnikov weight 1 - d^2 / r^2.
 struct PhotonGrid {
   double r = 0.0;
   std::unordered_map<int64_t, std::vector<uint32_t>> cells;
@@ -1088,7 +1145,8 @@ struct PhotonGrid {
           if (it == cells.end()) continue;
           for (uint32_t id : it->second) {
             const V3 dx = recs[id].x - x;
-            if (dot(dx, dx) < r * r) sum += recs[id].phi;
+            const double d2 = dot(dx, dx);
+            if (d2 < r * r) sum += recs[id].phi * (1.0 - d2 / (r * r));
           }
         }
     return sum;
@@ -1102,11 +1160,12 @@ extern "C" {
 // Photon records of the photon pass: pos_phi[slot] = (x, y, z, flux) and
 // cls[slot] = 0 empty, 1 direct, 2 caustic, 3 indirect.
 int or_photon_records(void* scene, uint32_t band_first, uint32_t band_count, uint32_t n_photons, uint32_t depth,
-                      uint64_t seed, double* pos_phi, uint8_t* cls, int n_threads) {
+                      uint64_t seed, int emission, double* pos_phi, uint8_t* cls, int n_threads) {
   const OScene& S = *(OScene*)scene;
   if (band_first + band_count > S.B || depth == 0 || n_photons == 0) return 1;
+  if (emission == 1 && photon_setup(S).portal.empty()) return 2;
   std::vector<PhotonRec> recs;
-  trace_photons(S, band_first, band_count, n_photons, depth, seed, recs, n_threads);
+  trace_photons(S, band_first, band_count, n_photons, depth, seed, recs, n_threads, emission);
   for (size_t q = 0; q < recs.size(); ++q) {
     pos_phi[4 * q] = recs[q].x.x;
     pos_phi[4 * q + 1] = recs[q].x.y;
@@ -1120,19 +1179,24 @@ int or_photon_records(void* scene, uint32_t band_first, uint32_t band_count, uin
 // Photon-mapping render of the listed pixels (same layout as or_render):
 // camera paths follow thin-glass, conductor and solid-glass events as in
 // the path tracer; at the first Lambertian vertex they add emission, the
-// next-event estimate of the sun and the photon estimate
-//   (rho / pi) [sum_caustic(r_c) phi / (pi r_c^2) + sum_indirect(r_g) phi / (pi r_g^2)]
-// of the photons of the path's band within the two radii, and stop.
+// next-event estimate of the sun and the photon estimate of the reflected
+// light (rho / pi) E, the irradiance E a kernel density estimate over the
+// photons of the path's band within each map's radius r:
+//   E = sum_maps (2 / (pi r^2)) sum_{d < r} phi (1 - d^2 / r^2)
+// (the Epanechnikov kernel, normalised over the disk of radius r; section 4
+// names no kernel, and one that vanishes at r keeps the estimate continuous
+// in the photon positions), and stop.
 int or_photon_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,
                      uint32_t spp, uint32_t depth, uint64_t seed, uint32_t n_photons, uint32_t photon_depth,
-                     double r_caustic, double r_global, const uint32_t* pixels, uint64_t n_pixels,
+                     double r_caustic, double r_global, int emission, const uint32_t* pixels, uint64_t n_pixels,
                      double* spectral_sum, double* path_L, uint32_t* path_sig, int n_threads) {
   const OScene& S = *(OScene*)scene;
   if (band_first + band_count > S.B || depth == 0 || photon_depth == 0 || n_photons == 0 || !(r_caustic > 0.0) ||
       !(r_global > 0.0))
     return 1;
+  if (emission == 1 && photon_setup(S).portal.empty()) return 2;
   std::vector<PhotonRec> recs;
-  trace_photons(S, band_first, band_count, n_photons, photon_depth, seed, recs, n_threads);
+  trace_photons(S, band_first, band_count, n_photons, photon_depth, seed, recs, n_threads, emission);
   std::vector<PhotonGrid> caus(band_count), glob(band_count);
   const size_t per_band = (size_t)n_photons * photon_depth;
   for (uint32_t j = 0; j < band_count; ++j) {
@@ -1185,8 +1249,8 @@ int or_photon_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32
           sig = mix(sig, ngl);
           L += T * S.rho[mb] * c * S.sunL[b] * cone_w * Tr;
         }
-        const double E = caus[j].flux_within(recs, p) / (M_PI * r_caustic * r_caustic) +
-                         glob[j].flux_within(recs, p) / (M_PI * r_global * r_global);
+        const double E = caus[j].flux_within(recs, p) * 2.0 / (M_PI * r_caustic * r_caustic) +
+                         glob[j].flux_within(recs, p) * 2.0 / (M_PI * r_global * r_global);
         L += T * S.rho[mb] / M_PI * E;
         break;
       } else if (type == M_GLASS) {

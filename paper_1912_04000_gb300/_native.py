@@ -53,7 +53,7 @@ class PhotonOpts(C.Structure):
     _fields_ = [("n_photons", C.c_uint32), ("photon_depth", C.c_uint32), ("r_caustic", C.c_float),
                 ("r_global", C.c_float), ("log2_cells", C.c_uint32), ("xyz_mode", C.c_uint32),
                 ("probe_map_dev", C.c_void_p), ("probe_L_dev", C.c_void_p), ("probe_sig_dev", C.c_void_p),
-                ("reserved", C.c_uint32 * 4)]
+                ("emission", C.c_uint32), ("reserved", C.c_uint32 * 3)]
 
 
 class SceneInfo(C.Structure):
@@ -135,7 +135,7 @@ def load(path: str = LIB_PATH):
         L.rt_xyz.argtypes = [vp, vp, u64, u32, u32, u32, u32, vp]
         L.rt_render_photons.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(PhotonOpts),
                                         vp, vp, C.POINTER(Stats)]
-        L.rt_photon_records.argtypes = [vp, u32, u32, u32, u32, u64, vp, vp]
+        L.rt_photon_records.argtypes = [vp, u32, u32, u32, u32, u64, u32, vp, vp]
         for name in EXPORTS:
             if name not in ("rt_destroy", "rt_last_error"):
                 getattr(L, name).restype = C.c_int

@@ -49,6 +49,7 @@ struct rt_ctx {
   WaveBufs wb{};
   uint32_t wave_alloc = 0;
   uint32_t four_band_alloc = 0;
+  std::vector<float> glass;  // thin-glass triangles of the scene, 9 floats each, input order
   // sun direction and cone in FP64 (photon emission geometry)
   double sun_d[3] = {0.0, 0.0, 1.0};
   double cos_max_d = 1.0;
@@ -604,6 +605,12 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
   c->eps = (float)(1e-4 * std::sqrt(dx * dx + dy * dy + dz * dz));
   c->mtype.assign(mat_type, mat_type + n_mat);
+  // thin-glass triangles in input order (portals of the photon pass)
+  c->glass.clear();
+  for (uint32_t t = 0; t < n_tris; ++t)
+    if (mat_type[mat_id[t]] == 1)
+      for (int q = 0; q < 3; ++q)
+        for (int a = 0; a < 3; ++a) c->glass.push_back(verts[3 * (size_t)tris[3 * (size_t)t + q] + a]);
   c->mthick.assign(mat_thickness, mat_thickness + n_mat);
   for (int a = 0; a < 3; ++a) {
     c->lo[a] = (float)lo[a];
@@ -1454,6 +1461,53 @@ rt_status rt_probe_l2(rt_ctx* c, uint64_t bytes, uint32_t iters, float* gbs) {
 // c, radius R) on the sun's side, radius R_d = R (tan a + 1 / cos a) so that
 // every ray of the cone that meets the sphere starts on it; each of the N
 // photons of a band carries L_sun cos Omega pi R_d^2 / N.
+// Portal table for portal emission: the thin-glass triangles that face the
+// sun, {v0, v1, v2, (sun-side unit normal, 1 / (s . n))}, and the cumulative
+// share of A |s . n| (FP64 sums, stored as float, the last entry 1).
+static rt_status photon_portals(rt_ctx* c, float4** d_portal, float** d_cdf, uint32_t* n_out, double* W_out) {
+  std::vector<float4> tab;
+  std::vector<double> cum;
+  double W = 0.0;
+  const double* s = c->sun_d;
+  for (size_t t = 0; t + 9 <= c->glass.size(); t += 9) {
+    const float* g = c->glass.data() + t;
+    double e1[3], e2[3], n[3];
+    for (int a = 0; a < 3; ++a) {
+      e1[a] = (double)g[3 + a] - g[a];
+      e2[a] = (double)g[6 + a] - g[a];
+    }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double a2 = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(a2 > 0.0)) continue;
+    for (int a = 0; a < 3; ++a) n[a] /= a2;
+    double cs = n[0] * s[0] + n[1] * s[1] + n[2] * s[2];
+    if (cs == 0.0) continue;
+    if (cs < 0.0) {
+      for (int a = 0; a < 3; ++a) n[a] = -n[a];
+      cs = -cs;
+    }
+    tab.push_back(make_float4(g[0], g[1], g[2], 0.0f));
+    tab.push_back(make_float4(g[3], g[4], g[5], 0.0f));
+    tab.push_back(make_float4(g[6], g[7], g[8], 0.0f));
+    tab.push_back(make_float4((float)n[0], (float)n[1], (float)n[2], (float)(1.0 / cs)));
+    W += 0.5 * a2 * cs;
+    cum.push_back(W);
+  }
+  if (tab.empty()) return fail(c, RT_ERR_ARG, "portal emission: no thin-glass triangle faces the sun");
+  std::vector<float> cdf(cum.size());
+  for (size_t q = 0; q < cum.size(); ++q) cdf[q] = (float)(cum[q] / W);
+  cdf.back() = 1.0f;
+  CUDA_TRY(c, cudaMalloc(d_portal, tab.size() * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(d_cdf, cdf.size() * sizeof(float)));
+  CUDA_TRY(c, cudaMemcpy(*d_portal, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(*d_cdf, cdf.data(), cdf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  *n_out = (uint32_t)cum.size();
+  *W_out = W;
+  return RT_OK;
+}
+
 static void photon_setup(const rt_ctx* c, uint32_t N, uint64_t seed, PhotonPass& pp) {
   double ctr[3], R2 = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -1482,7 +1536,7 @@ static void photon_setup(const rt_ctx* c, uint32_t N, uint64_t seed, PhotonPass&
 }
 
 rt_status rt_photon_records(rt_ctx* c, uint32_t band_first, uint32_t band_count, uint32_t n_photons, uint32_t depth,
-                            uint64_t seed, float* rec_dev, uint8_t* cls_dev) {
+                            uint64_t seed, uint32_t emission, float* rec_dev, uint8_t* cls_dev) {
   if (rt_status e = check_ctx(c)) return e;
   if (!c->has_scene || !c->has_spectra) return fail(c, RT_ERR_STATE, "rt_photon_records: scene and spectra required");
   if (!rec_dev || ((uintptr_t)rec_dev & 15u)) return fail(c, RT_ERR_ARG, "rt_photon_records: rec_dev must be 16-byte aligned");
@@ -1493,12 +1547,23 @@ rt_status rt_photon_records(rt_ctx* c, uint32_t band_first, uint32_t band_count,
   const uint64_t slots = (uint64_t)band_count * n_photons * depth;
   if (slots > (1ull << 28)) return fail(c, RT_ERR_ARG, "rt_photon_records: more than 2^28 slots");
   if (!(c->cos_max_d > std::cos(1.0))) return fail(c, RT_ERR_ARG, "rt_photon_records: sun half angle must be below 1 rad");
+  if (emission > 1) return fail(c, RT_ERR_ARG, "rt_photon_records: emission is 0 (disk) or 1 (portals)");
   cudaSetDevice(c->device);
   cudaStream_t st = c->stream;
-  uint32_t* kv = nullptr;
-  CUDA_TRY(c, cudaMalloc(&kv, slots * 2 * sizeof(uint32_t)));
   PhotonPass pp{};
   photon_setup(c, n_photons, seed, pp);
+  float4* portal = nullptr;
+  float* cdf = nullptr;
+  if (emission == 1) {
+    double W = 0.0;
+    if (rt_status e = photon_portals(c, &portal, &cdf, &pp.n_portal, &W)) return e;
+    pp.portal = portal;
+    pp.cdf = cdf;
+    pp.emission = 1;
+    pp.flux = (float)(2.0 * M_PI * (1.0 - c->cos_max_d) * W / (double)n_photons);
+  }
+  uint32_t* kv = nullptr;
+  CUDA_TRY(c, cudaMalloc(&kv, slots * 2 * sizeof(uint32_t)));
   pp.band0 = band_first;
   pp.Bc = band_count;
   pp.depth = depth;
@@ -1510,6 +1575,8 @@ rt_status rt_photon_records(rt_ctx* c, uint32_t band_first, uint32_t band_count,
   CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
   dfree(kv);
+  dfree(portal);
+  dfree(cdf);
   return status_to_rt(c, *c->h_status);
 }
 
@@ -1596,8 +1663,19 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
     }
     accum = c->d_accum;
   }
+  if (o.emission > 1) return fail(c, RT_ERR_ARG, "rt_render_photons: emission is 0 (disk) or 1 (portals)");
   PhotonPass pp{};
   photon_setup(c, N, seed, pp);
+  float4* portal = nullptr;
+  float* cdf = nullptr;
+  if (o.emission == 1) {
+    double W = 0.0;
+    if (rt_status e = photon_portals(c, &portal, &cdf, &pp.n_portal, &W)) return e;
+    pp.portal = portal;
+    pp.cdf = cdf;
+    pp.emission = 1;
+    pp.flux = (float)(2.0 * M_PI * (1.0 - c->cos_max_d) * W / (double)N);
+  }
   pp.depth = pd;
   pp.inv_cell[0] = (float)(1.0 / (2.0 * rc));
   pp.inv_cell[1] = (float)(1.0 / (2.0 * rg));
@@ -1610,8 +1688,9 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
   M.r2[1] = (float)(rg * rg);
   M.inv_cell[0] = pp.inv_cell[0];
   M.inv_cell[1] = pp.inv_cell[1];
-  M.norm[0] = (float)(1.0 / (M_PI * rc * rc));
-  M.norm[1] = (float)(1.0 / (M_PI * rg * rg));
+  // Epanechnikov kernel 1 - d^2 / r^2 over the disk of radius r: norm 2 / (pi r^2)
+  M.norm[0] = (float)(2.0 / (M_PI * rc * rc));
+  M.norm[1] = (float)(2.0 / (M_PI * rg * rg));
   M.hbits = hb;
   PhotonCam pc{};
   pc.s_base = 0;
@@ -1690,5 +1769,7 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
     cudaEventElapsedTime(&stats->ms_xyz, ev[ev.size() - 2], ev.back());
   }
   for (auto e : ev) cudaEventDestroy(e);
+  dfree(portal);
+  dfree(cdf);
   return status_to_rt(c, *c->h_status);
 }

@@ -263,6 +263,12 @@ struct PhotonPass {
   float Rd, flux;            // disk radius; Omega pi Rd^2 / N
   float inv_cell[2];         // 1 / (2 r) of the caustic and indirect maps
   uint32_t hbits;            // 2^hbits hash cells per (map, band)
+  // emission 1: photons start on the thin-glass portals facing the sun:
+  // portal[4 q ..] = {v0, v1, v2, (sun-side normal, 1 / (s . n))}, cdf the
+  // cumulative share of A |s . n|; flux then holds Omega W / N
+  uint32_t emission, n_portal;
+  const float4* portal;
+  const float* cdf;
 };
 // The maps after sorting: rec holds the records in key order; start / end
 // the record range of each key (empty: start = end = 0).
@@ -270,7 +276,7 @@ struct PhotonMaps {
   const uint32_t* start;
   const uint32_t* end;
   const float4* rec;
-  float r2[2], inv_cell[2], norm[2];  // r^2, 1 / (2 r), 1 / (pi r^2) per map
+  float r2[2], inv_cell[2], norm[2];  // r^2, 1 / (2 r), 2 / (pi r^2) per map (Epanechnikov kernel)
   uint32_t hbits, Bc;
 };
 // Camera pass of one sample s for the bands of the photon pass: paths

@@ -1350,20 +1350,61 @@ __global__ void __launch_bounds__(128) k_photon_trace(DevScene S, DevSpectra P, 
       if (cls) cls[slot0 + q] = 0;
     }
     const uint4 r0 = philox4x32_10(make_uint4(i, b, 0u, 0u), pp.key0, pp.key1);
-    const float rad = pp.Rd * sqrtf(u01(r0.x));
-    float sp, cp;
-    sincospif(2.0f * u01(r0.y), &sp, &cp);
-    float3 o = make_float3(pp.c0.x + rad * (cp * pp.t1.x + sp * pp.t2.x), pp.c0.y + rad * (cp * pp.t1.y + sp * pp.t2.y),
-                           pp.c0.z + rad * (cp * pp.t1.z + sp * pp.t2.z));
-    const float om = u01(r0.z) * P.one_minus_cos;
-    const float ct = 1.0f - om;
-    const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
-    float sp2, cp2;
-    sincospif(2.0f * u01(r0.w), &sp2, &cp2);
-    float3 d = make_float3(-(st * cp2 * pp.t1.x + st * sp2 * pp.t2.x + ct * P.sun.x),
-                           -(st * cp2 * pp.t1.y + st * sp2 * pp.t2.y + ct * P.sun.y),
-                           -(st * cp2 * pp.t1.z + st * sp2 * pp.t2.z + ct * P.sun.z));
-    float phi = __ldg(P.sunL + b) * ct * pp.flux;
+    float3 o, d;
+    float phi;
+    if (pp.emission == 0u) {
+      const float rad = pp.Rd * sqrtf(u01(r0.x));
+      float sp, cp;
+      sincospif(2.0f * u01(r0.y), &sp, &cp);
+      o = make_float3(pp.c0.x + rad * (cp * pp.t1.x + sp * pp.t2.x), pp.c0.y + rad * (cp * pp.t1.y + sp * pp.t2.y),
+                      pp.c0.z + rad * (cp * pp.t1.z + sp * pp.t2.z));
+      const float om = u01(r0.z) * P.one_minus_cos;
+      const float ct = 1.0f - om;
+      const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
+      float sp2, cp2;
+      sincospif(2.0f * u01(r0.w), &sp2, &cp2);
+      d = make_float3(-(st * cp2 * pp.t1.x + st * sp2 * pp.t2.x + ct * P.sun.x),
+                      -(st * cp2 * pp.t1.y + st * sp2 * pp.t2.y + ct * P.sun.y),
+                      -(st * cp2 * pp.t1.z + st * sp2 * pp.t2.z + ct * P.sun.z));
+      phi = __ldg(P.sunL + b) * ct * pp.flux;
+    } else {
+      // portal emission: a thin-glass triangle by its share of A |s . n|
+      // (the first whose cumulative share exceeds u0), a uniform point on
+      // it, a direction of the cone; nothing when the direction grazes the
+      // face from behind or the way back to the sun is blocked
+      const float u0 = u01(r0.x);
+      uint32_t lo = 0, hi = pp.n_portal - 1u;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(pp.cdf + mid) > u0) hi = mid;
+        else lo = mid + 1u;
+      }
+      const float4 v0 = ldg4(pp.portal + 4u * lo), v1 = ldg4(pp.portal + 4u * lo + 1u),
+                   v2 = ldg4(pp.portal + 4u * lo + 2u), pn = ldg4(pp.portal + 4u * lo + 3u);
+      const float su = sqrtf(u01(r0.y)), u2 = u01(r0.z);
+      const float wa = 1.0f - su, wb = su * (1.0f - u2), wc = su * u2;
+      const float3 pg = make_float3(wa * v0.x + wb * v1.x + wc * v2.x, wa * v0.y + wb * v1.y + wc * v2.y,
+                                    wa * v0.z + wb * v1.z + wc * v2.z);
+      const uint4 r1 = philox4x32_10(make_uint4(i, b, 0u, 1u), pp.key0, pp.key1);
+      const float om = u01(r1.x) * P.one_minus_cos;
+      const float ct = 1.0f - om;
+      const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
+      float sp2, cp2;
+      sincospif(2.0f * u01(r1.y), &sp2, &cp2);
+      const float3 w = make_float3(st * cp2 * pp.t1.x + st * sp2 * pp.t2.x + ct * P.sun.x,
+                                   st * cp2 * pp.t1.y + st * sp2 * pp.t2.y + ct * P.sun.y,
+                                   st * cp2 * pp.t1.z + st * sp2 * pp.t2.z + ct * P.sun.z);
+      const float3 pnv = f3(pn);
+      const float wn = dot(w, pnv);
+      if (!(wn > 0.0f)) continue;
+      o = madd(pg, S.eps, pnv);
+      float tb;
+      int lb;
+      closest_hit(S, o, w, tb, lb, status);
+      if (lb >= 0) continue;
+      d = neg(w);
+      phi = __ldg(P.sunL + b) * wn * pp.flux * pn.w;
+    }
     bool nee_path = true;
     uint32_t n_diff = 0;
     for (uint32_t k = 1; k <= pp.depth; ++k) {
@@ -1464,9 +1505,9 @@ __global__ void k_photon_bounds(const uint32_t* __restrict__ sk, const uint32_t*
   }
 }
 
-// Flux of the photons of band j in map `map` within distance r of x: the
-// (at most 8) cells of edge 2 r that the ball touches, duplicates of a
-// hashed key skipped.
+// Kernel-weighted flux of the photons of band j in map `map` within distance
+// r of x, weight 1 - d^2 / r^2 (Epanechnikov): the (at most 8) cells of edge
+// 2 r that the ball touches, duplicates of a hashed key skipped.
 __device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map, uint32_t j, float3 x) {
   const float ic = M.inv_cell[map];
   const float r = sqrtf(M.r2[map]);
@@ -1489,7 +1530,8 @@ __device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map
         for (uint32_t q = __ldg(M.start + key); q < e; ++q) {
           const float4 ph = ldg4(M.rec + q);
           const float dx = ph.x - x.x, dy = ph.y - x.y, dz = ph.z - x.z;
-          if (dx * dx + dy * dy + dz * dz < M.r2[map]) sum += ph.w;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 < M.r2[map]) sum += ph.w * (1.0f - d2 / M.r2[map]);
         }
       }
   return sum;
@@ -1497,7 +1539,8 @@ __device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map
 
 // Camera pass of one sample: the path tracer's camera and specular events
 // up to the first Lambertian vertex, where emission, the sun's next-event
-// estimate and (rho / pi) x the photon irradiance of both maps are added.
+// estimate and (rho / pi) x the photon irradiance of both maps (kernel
+// density estimates, norm = 2 / (pi r^2)) are added.
 __global__ void __launch_bounds__(128) k_photon_camera(DevScene S, DevSpectra P, const DevCam* __restrict__ cams,
                                                        uint32_t n_cams, PhotonCam pc, PhotonMaps M,
                                                        double* __restrict__ accum, Probe probe, uint32_t* status) {

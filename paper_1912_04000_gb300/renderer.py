@@ -164,7 +164,7 @@ class Renderer:
     def render_photons(self, cameras: Sequence, spp: int, depth: int, seed: int = 0, band_first: int = 0,
                        band_count: Optional[int] = None, n_photons: int = 0, photon_depth: int = 0,
                        r_caustic: float = 0.0, r_global: float = 0.0, log2_cells: int = 0,
-                       xyz_mode: int = _native.XYZ_BF16X3, probe_pixels=None, out_spectral=None):
+                       xyz_mode: int = _native.XYZ_BF16X3, probe_pixels=None, out_spectral=None, emission: int = 0):
         """Photon-mapping render (rt_render_photons): dict(spectral [P, band_count]
         f64 sums over samples, xyz [P, 3], stats, probe_L / probe_sig)."""
         torch = self.torch
@@ -177,7 +177,7 @@ class Renderer:
         xz = torch.empty((npix, 3), dtype=torch.float32, device=dev)
         o = _native.PhotonOpts()
         o.n_photons, o.photon_depth, o.log2_cells, o.xyz_mode = n_photons, photon_depth, log2_cells, xyz_mode
-        o.r_caustic, o.r_global = r_caustic, r_global
+        o.r_caustic, o.r_global, o.emission = r_caustic, r_global, emission
         out = {}
         if probe_pixels is not None:
             pp = torch.as_tensor(np.asarray(probe_pixels, np.int64), device=dev)
@@ -197,7 +197,7 @@ class Renderer:
         return out
 
     def photon_records(self, n_photons: int, depth: int, seed: int = 0, band_first: int = 0,
-                       band_count: Optional[int] = None):
+                       band_count: Optional[int] = None, emission: int = 0):
         """Photon pass alone: (records [band_count, n_photons, depth, 4] float32
         {x, y, z, flux}, classes [band_count, n_photons, depth] uint8)."""
         torch = self.torch
@@ -205,8 +205,8 @@ class Renderer:
             band_count = self.n_bands - band_first
         rec = torch.zeros((band_count, n_photons, depth, 4), dtype=torch.float32, device=self.device)
         cls = torch.zeros((band_count, n_photons, depth), dtype=torch.uint8, device=self.device)
-        st = self.lib.rt_photon_records(self._h, band_first, band_count, n_photons, depth, seed, rec.data_ptr(),
-                                        cls.data_ptr())
+        st = self.lib.rt_photon_records(self._h, band_first, band_count, n_photons, depth, seed, emission,
+                                        rec.data_ptr(), cls.data_ptr())
         self._check("rt_photon_records", st)
         return rec, cls
 

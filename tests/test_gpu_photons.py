@@ -102,3 +102,32 @@ def test_arguments_checked(R):
     R.load(wide)
     with pytest.raises(RtError):
         R.render_photons(wide.cameras, 1, 2, 0)
+
+
+@pytest.mark.parametrize("name", ["tiny_box", "prism_room"])
+def test_portal_emission_records_and_image(R, name):
+    wl = scenes.tiny_box(width=48, height=48, n_bands=4, spp=2, depth=6) if name == "tiny_box" else \
+        scenes.prism_room(width=48, height=36, n_bands=4, spp=2)
+    R.load(wl)
+    sc = oracle.OracleScene(wl.scene, wl.spectra)
+    N, depth = 1 << 13, 4
+    rec, cls = (x.cpu().numpy() for x in R.photon_records(N, depth, seed=7, emission=1))
+    pos, ocls = sc.photon_records(N, depth, seed=7, emission=1)
+    same = (cls == ocls).all(-1)
+    print(name, "portal photons with identical stores", same.mean())
+    assert same.mean() >= 0.99
+    st = (ocls > 0) & same[..., None]
+    np.testing.assert_allclose(rec[..., :3][st], pos[..., :3][st], rtol=0, atol=2e-5 * _diag(wl))
+    np.testing.assert_allclose(rec[..., 3][st], pos[..., 3][st], rtol=2e-5)
+    kw = dict(n_photons=1 << 15, photon_depth=4, r_caustic=0.04, r_global=0.15)
+    out = R.render_photons(wl.cameras, wl.spp, wl.depth, wl.seed, emission=1, **kw)
+    o = sc.render_photons(wl.cameras, wl.spp, wl.depth, wl.seed, emission=1, **kw)
+    print(name, "portal photon-mapping parity", xyz_parity(out["xyz"].cpu().numpy(), o["xyz"]))
+    assert_parity(out["xyz"].cpu().numpy(), o["xyz"], name + " portals")
+
+
+def test_portal_emission_needs_glass(R):
+    wl = scenes.mirror_caustic()
+    R.load(wl)
+    with pytest.raises(RtError):
+        R.render_photons(wl.cameras, 1, 3, 0, emission=1)

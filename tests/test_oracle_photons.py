@@ -105,3 +105,32 @@ def test_photon_estimate_matches_path_tracer():
                            r_global=0.12)["spectral_sum"] / 8
     for j in range(2):
         assert abs(pm[:, j].mean() / pt[:, j].mean() - 1.0) < 0.03, (pm[:, j].mean(), pt[:, j].mean())
+
+
+def test_portal_emission_matches_disk():
+    # sunlight enters the box only through its thin-glass wall, so photons
+    # emitted on that wall (portal emission) and photons from the disk
+    # deliver the same indirect flux inside, and the same image
+    wl = scenes.tiny_box(width=24, height=24, n_bands=2, spp=4, depth=5)
+    sc = oracle.OracleScene(wl.scene, wl.spectra)
+    Nd, Np = 1 << 20, 1 << 16
+    pd, cd = sc.photon_records(Nd, 3, seed=2, emission=0)
+    pp, cp = sc.photon_records(Np, 3, seed=2, emission=1)
+    for j in range(2):
+        a = np.where(cd[j] == 3, pd[j, ..., 3], 0.0).sum(1) * Nd     # per-photon estimates of the total
+        b = np.where(cp[j] == 3, pp[j, ..., 3], 0.0).sum(1) * Np
+        se = math.sqrt(a.var() / a.size + b.var() / b.size)
+        assert abs(a.mean() - b.mean()) < 5 * se, (a.mean(), b.mean(), se)
+        # the portal sends far more of its photons inside
+        assert (cp[j] == 3).any(1).mean() > 5 * (cd[j] == 3).any(1).mean()
+    kw = dict(photon_depth=5, r_caustic=0.05, r_global=0.15)
+    imd = sc.render_photons(wl.cameras, 4, 5, 3, n_photons=Nd, emission=0, **kw)["spectral_sum"]
+    imp = sc.render_photons(wl.cameras, 4, 5, 3, n_photons=Np, emission=1, **kw)["spectral_sum"]
+    assert abs(imp.mean() / imd.mean() - 1.0) < 0.02
+
+
+def test_portal_emission_needs_glass():
+    wl = scenes.mirror_caustic()
+    sc = oracle.OracleScene(wl.scene, wl.spectra)
+    with pytest.raises(ValueError):
+        sc.photon_records(64, 2, emission=1)
