@@ -826,6 +826,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   w.band_count = units;
   w.nb = nb;
   w.B = band_count;
+  w.acc_stride = band_count;
+  w.acc_off = 0;
   w.spp = spp;
   w.depth = depth;
   w.key0 = (uint32_t)seed;
@@ -1692,15 +1694,37 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
   M.norm[0] = (float)(2.0 / (M_PI * rc * rc));
   M.norm[1] = (float)(2.0 / (M_PI * rg * rg));
   M.hbits = hb;
-  PhotonCam pc{};
-  pc.s_base = 0;
-  pc.spp = spp;
-  pc.npix = (uint32_t)npix;
-  pc.depth = depth;
-  pc.B = band_count;
-  pc.key0 = (uint32_t)seed;
-  pc.key1 = (uint32_t)(seed >> 32);
+  // camera pass: the wavefront kernels of rt_render (camera rays, closest
+  // hit, shading that ends at the first Lambertian vertex, sun rays), one
+  // band chunk at a time, into the chunk's columns of the spectral image
   const Probe probe{o.probe_map_dev, o.probe_L_dev, o.probe_sig_dev};
+  uint32_t cap = (uint32_t)std::min<uint64_t>(std::min<uint64_t>(1u << 23, npix * Bc), kMaxWave);
+  cap = std::max<uint32_t>(cap, 1u);
+  if (rt_status e = ensure_wave(c, cap)) return e;
+  LaunchCfg lc;
+  lc.block_trace = 128;
+  lc.block_shade = 256;
+  lc.grid_trace = c->sms * trace_blocks_per_sm(lc.block_trace);
+  lc.grid_shadow = c->sms * shadow_blocks_per_sm(lc.block_trace);
+  lc.grid_shade = c->sms * 8;
+  lc.counting = false;
+  lc.record = o.probe_map_dev != nullptr;
+  lc.variant = 0;
+  lc.leaf_min = kDefaultLeafBatch;
+  lc.sort_rays = false;
+  lc.trace_steps = kDefaultTraceSteps;
+  lc.trace_refill = kDefaultTraceRefill;
+  lc.shadow_steps = kDefaultShadowSteps;
+  lc.shadow_refill = kDefaultShadowRefill;
+  WaveParams w{};
+  w.spp = spp;
+  w.depth = depth;
+  w.key0 = (uint32_t)seed;
+  w.key1 = (uint32_t)(seed >> 32);
+  w.s_base = 0;
+  w.n_bands = c->sp.n_bands;
+  w.nb = 1;
+  w.acc_stride = band_count;
   const DevScene S = dev_scene(c);
   std::vector<cudaEvent_t> ev;
   auto mark = [&]() {
@@ -1727,15 +1751,25 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
     launch_photon_maps(B.keys[r], B.vals[r], n, B.rec, B.rec_sorted, B.start, B.end, c->sms, st);
     mark();
     M.Bc = bc;
-    pc.band0 = cb;
-    pc.Bc = bc;
-    pc.band_off = cb - band_first;
-    for (uint32_t s_ = 0; s_ < spp; ++s_) {
-      pc.s = s_;
-      launch_photon_camera(S, c->sp, c->d_cams, n_cams, pc, M, accum, probe, c->wb.status, c->sms, st);
+    w.band_first = cb;
+    w.band_count = bc;
+    w.B = bc;
+    w.acc_off = cb - band_first;
+    w.PB = (uint32_t)(npix * bc);
+    // a wave holds at most one sample's paths of this chunk, so that it
+    // spans two samples at most (path ids wrap once)
+    const uint32_t wcap = std::min<uint32_t>(cap, w.PB);
+    const uint64_t total = (uint64_t)w.PB * spp;
+    for (uint64_t ws = 0; ws < total; ws += wcap) {
+      w.n = (uint32_t)std::min<uint64_t>(wcap, total - ws);
+      w.s0 = (uint32_t)(ws / w.PB);
+      w.r0 = (uint32_t)(ws % w.PB);
+      CUDA_TRY(c, cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), st));
+      launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, st, &launches, nullptr, nullptr, nullptr,
+                  nullptr, c->sms, &M);
     }
     mark();
-    launches += 1 + 16 + 1 + (int)spp;  // trace, 4 radix passes of 4 kernels, ranges, camera passes
+    launches += 1 + 16 + 1;  // photon trace, 4 radix passes of 4 kernels, ranges
   }
   CUDA_TRY(c, cudaGetLastError());
   if (xyz_dev) {

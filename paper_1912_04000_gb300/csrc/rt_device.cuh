@@ -200,11 +200,11 @@ __device__ __forceinline__ PathId path_id(const WaveParams& w, uint32_t pid) {
 
 __device__ __forceinline__ void finalize(const WaveParams& w, const PathId& id, float L, uint32_t sg, double* accum,
                                          const Probe& probe, bool record) {
-  if (L != 0.0f) accum[id.r] += (double)L;
+  if (L != 0.0f) accum[(size_t)id.pix * w.acc_stride + w.acc_off + id.j] += (double)L;
   if (record && probe.map != nullptr) {
     const uint32_t slot = probe.map[id.pix];
     if (slot != 0xFFFFFFFFu) {
-      const size_t q = ((size_t)slot * w.spp + (id.s - w.s_base)) * w.band_count + id.j;
+      const size_t q = ((size_t)slot * w.spp + (id.s - w.s_base)) * w.acc_stride + w.acc_off + id.j;
       probe.L[q] = L;
       probe.sig[q] = sg;
     }

@@ -84,6 +84,10 @@ struct WaveParams {
   // per pixel; unit j stands for bands band_first + j + q G, q = 0..3, those
   // below B, the render's band count); with 1, B = band_count
   uint32_t nb, B;
+  // one-band paths add to accum[pixel * acc_stride + acc_off + j] (a band
+  // chunk of a wider spectral image; acc_stride = band_count, acc_off = 0
+  // for a whole render)
+  uint32_t acc_stride, acc_off;
 };
 
 // Guided sampling of one wave (on == false: plain cosine sampling).
@@ -220,10 +224,15 @@ struct LaunchCfg {
 };
 
 struct GuideDev;
+struct PhotonMaps;
+// pm != nullptr: photon-mapping camera pass (paths end at their first
+// Lambertian vertex with the sun's next-event estimate and the photon
+// density estimates of pm)
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe,
                  cudaStream_t st, int* launches, StageTimer* timer, const GuideWave* gw = nullptr,
-                 const GuideDev* gdev = nullptr, const void* gpack = nullptr, int sms = 0);
+                 const GuideDev* gdev = nullptr, const void* gpack = nullptr, int sms = 0,
+                 const PhotonMaps* pm = nullptr);
 void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaStream_t st, int sms);
 void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st);
 void launch_trace_closest_rays(const DevScene& S, const float* o, const float* d, uint64_t n, float* t,
@@ -279,21 +288,10 @@ struct PhotonMaps {
   float r2[2], inv_cell[2], norm[2];  // r^2, 1 / (2 r), 2 / (pi r^2) per map (Epanechnikov kernel)
   uint32_t hbits, Bc;
 };
-// Camera pass of one sample s for the bands of the photon pass: paths
-// (pixel, j) add to accum[pixel * B + band_off + j].
-struct PhotonCam {
-  uint32_t s, s_base, spp, npix, depth;
-  uint32_t band0, Bc, band_off, B;
-  uint32_t key0, key1;
-};
 void launch_photon_trace(const DevScene& S, const DevSpectra& P, const PhotonPass& pp, float4* rec, uint32_t* keys,
                          uint32_t* vals, uint8_t* cls, uint32_t* status, int sms, cudaStream_t st);
 void launch_photon_maps(const uint32_t* sorted_keys, const uint32_t* sorted_vals, uint32_t n, const float4* rec,
                         float4* rec_sorted, uint32_t* start, uint32_t* end, int sms, cudaStream_t st);
-void launch_photon_camera(const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
-                          const PhotonCam& pc, const PhotonMaps& M, double* accum, const Probe& probe,
-                          uint32_t* status, int sms, cudaStream_t st);
-
 int trace_blocks_per_sm(int block);
 int shadow_blocks_per_sm(int block);
 

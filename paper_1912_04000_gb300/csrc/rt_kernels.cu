@@ -704,13 +704,54 @@ __global__ void __launch_bounds__(kTraceMaxThreads, kTraceMinBlocks) k_trace(Dev
   }
 }
 
-template <bool RECORD, bool GUIDED>
+// Spatial hash of an integer cell (three large odd multipliers, xor).
+__device__ __forceinline__ uint32_t photon_cell_hash(int ix, int iy, int iz, uint32_t hbits) {
+  const uint32_t h = ((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u);
+  return h & ((1u << hbits) - 1u);
+}
+
+// Kernel-weighted flux of the photons of band j in map `map` within distance
+// r of x, weight 1 - d^2 / r^2 (Epanechnikov): the (at most 8) cells of edge
+// 2 r that the ball touches, duplicates of a hashed key skipped.
+__device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map, uint32_t j, float3 x) {
+  const float ic = M.inv_cell[map];
+  const float r = sqrtf(M.r2[map]);
+  const int lx = (int)floorf((x.x - r) * ic), hx = (int)floorf((x.x + r) * ic);
+  const int ly = (int)floorf((x.y - r) * ic), hy = (int)floorf((x.y + r) * ic);
+  const int lz = (int)floorf((x.z - r) * ic), hz = (int)floorf((x.z + r) * ic);
+  const uint32_t base = (map * M.Bc + j) << M.hbits;
+  uint32_t seen[8];
+  int ns = 0;
+  float sum = 0.0f;
+  for (int ix = lx; ix <= hx; ++ix)
+    for (int iy = ly; iy <= hy; ++iy)
+      for (int iz = lz; iz <= hz; ++iz) {
+        const uint32_t key = base | photon_cell_hash(ix, iy, iz, M.hbits);
+        bool dup = false;
+        for (int q = 0; q < ns; ++q) dup |= seen[q] == key;
+        if (dup || ns >= 8) continue;
+        seen[ns++] = key;
+        const uint32_t e = __ldg(M.end + key);
+        for (uint32_t q = __ldg(M.start + key); q < e; ++q) {
+          const float4 ph = ldg4(M.rec + q);
+          const float dx = ph.x - x.x, dy = ph.y - x.y, dz = ph.z - x.z;
+          const float d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 < M.r2[map]) sum += ph.w * (1.0f - d2 / M.r2[map]);
+        }
+      }
+  return sum;
+}
+
+// PM: photon-mapping camera pass -- at the first Lambertian vertex the path
+// adds (rho / pi) x the photon irradiance of both maps of pm and ends (its
+// sun ray, if any, finishes it).
+template <bool RECORD, bool GUIDED, bool PM = false>
 __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                const float4* __restrict__ qin, const float2* __restrict__ hit,
                                                float4* __restrict__ qout, float4* __restrict__ sq,
                                                float* __restrict__ Lbuf, uint32_t* __restrict__ sigbuf,
                                                Counters* cnt, uint32_t cap, double* __restrict__ accum,
-                                               Probe probe, uint32_t* status, GuideWave gw) {
+                                               Probe probe, uint32_t* status, GuideWave gw, PhotonMaps pm) {
   const uint32_t count = min(cnt[k].q_count, cap);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -771,11 +812,15 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
           const float3 po = madd(p, S.eps, n);
           if (c > 0.0f) {
             emit_shadow = true;
-            const uint32_t fl = pid | (k == w.depth ? kFlagTerm : 0u);
+            const uint32_t fl = pid | ((PM || k == w.depth) ? kFlagTerm : 0u);
             s0 = make_float4(po.x, po.y, po.z, __uint_as_float(fl));
             s1 = make_float4(wd.x, wd.y, wd.z, T * m.z * c * __ldg(P.sunL + band) * 2.0f * P.one_minus_cos);
           }
-          if (k == w.depth) {
+          if (PM) {
+            const float E = photon_gather(pm, 0u, id.j, p) * pm.norm[0] + photon_gather(pm, 1u, id.j, p) * pm.norm[1];
+            Lp += T * m.z * (1.0f / 3.14159265358979f) * E;
+            terminate = true;
+          } else if (k == w.depth) {
             terminate = true;
           } else if (GUIDED && k <= gw.depth) {
             // the continuation is sampled by the guide kernel (one-sample MIS)
@@ -1322,12 +1367,6 @@ __global__ void __launch_bounds__(512) k_l2_probe(const float4* __restrict__ buf
 
 // ---- photon mapping (section 4) ----------------------------------------
 
-// Spatial hash of an integer cell (three large odd multipliers, xor).
-__device__ __forceinline__ uint32_t photon_cell_hash(int ix, int iy, int iz, uint32_t hbits) {
-  const uint32_t h = ((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u);
-  return h & ((1u << hbits) - 1u);
-}
-
 // Photon pass: one thread per photon.  Emission from the disk tangent to the
 // scene's bounding sphere on the sun's side, direction minus a uniform
 // sample of the sun cone, flux L_sun cos Omega pi R_d^2 / N; then the path
@@ -1505,161 +1544,6 @@ __global__ void k_photon_bounds(const uint32_t* __restrict__ sk, const uint32_t*
   }
 }
 
-// Kernel-weighted flux of the photons of band j in map `map` within distance
-// r of x, weight 1 - d^2 / r^2 (Epanechnikov): the (at most 8) cells of edge
-// 2 r that the ball touches, duplicates of a hashed key skipped.
-__device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map, uint32_t j, float3 x) {
-  const float ic = M.inv_cell[map];
-  const float r = sqrtf(M.r2[map]);
-  const int lx = (int)floorf((x.x - r) * ic), hx = (int)floorf((x.x + r) * ic);
-  const int ly = (int)floorf((x.y - r) * ic), hy = (int)floorf((x.y + r) * ic);
-  const int lz = (int)floorf((x.z - r) * ic), hz = (int)floorf((x.z + r) * ic);
-  const uint32_t base = (map * M.Bc + j) << M.hbits;
-  uint32_t seen[8];
-  int ns = 0;
-  float sum = 0.0f;
-  for (int ix = lx; ix <= hx; ++ix)
-    for (int iy = ly; iy <= hy; ++iy)
-      for (int iz = lz; iz <= hz; ++iz) {
-        const uint32_t key = base | photon_cell_hash(ix, iy, iz, M.hbits);
-        bool dup = false;
-        for (int q = 0; q < ns; ++q) dup |= seen[q] == key;
-        if (dup || ns >= 8) continue;
-        seen[ns++] = key;
-        const uint32_t e = __ldg(M.end + key);
-        for (uint32_t q = __ldg(M.start + key); q < e; ++q) {
-          const float4 ph = ldg4(M.rec + q);
-          const float dx = ph.x - x.x, dy = ph.y - x.y, dz = ph.z - x.z;
-          const float d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 < M.r2[map]) sum += ph.w * (1.0f - d2 / M.r2[map]);
-        }
-      }
-  return sum;
-}
-
-// Camera pass of one sample: the path tracer's camera and specular events
-// up to the first Lambertian vertex, where emission, the sun's next-event
-// estimate and (rho / pi) x the photon irradiance of both maps (kernel
-// density estimates, norm = 2 / (pi r^2)) are added.
-__global__ void __launch_bounds__(128) k_photon_camera(DevScene S, DevSpectra P, const DevCam* __restrict__ cams,
-                                                       uint32_t n_cams, PhotonCam pc, PhotonMaps M,
-                                                       double* __restrict__ accum, Probe probe, uint32_t* status) {
-  const uint32_t total = pc.npix * pc.Bc;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-    const uint32_t pix = q / pc.Bc, j = q - pix * pc.Bc;
-    const uint32_t b = pc.band0 + j;
-    uint32_t v = 0;
-    while (v + 1 < n_cams && cams[v + 1].offset <= pix) ++v;
-    const DevCam& C = cams[v];
-    const uint32_t local = pix - C.offset;
-    const uint32_t y = local / C.W, x = local - y * C.W;
-    const uint4 u0 = philox4x32_10(make_uint4(pix, pc.s, b, 0u), pc.key0, pc.key1);
-    const float sx = (2.0f * ((float)x + u01(u0.x)) / (float)C.W - 1.0f) * C.tha;
-    const float sy = (1.0f - 2.0f * ((float)y + u01(u0.y)) / (float)C.H) * C.th;
-    float3 d = make_float3(C.f.x + sx * C.r.x + sy * C.u.x, C.f.y + sx * C.r.y + sy * C.u.y,
-                           C.f.z + sx * C.r.z + sy * C.u.z);
-    d = mul(1.0f / sqrtf(dot(d, d)), d);
-    float3 o = C.pos;
-    float T = 1.0f, L = 0.0f;
-    bool covered = false;
-    uint32_t sg = 2166136261u;
-    for (uint32_t k = 1; k <= pc.depth; ++k) {
-      float t;
-      int leaf;
-      closest_hit(S, o, d, t, leaf, status);
-      if (leaf < 0) {
-        sg = mix_sig(sg, 0xFFFFFFFFu);
-        if (!covered && dot(d, P.sun) >= P.cos_max) L += T * __ldg(P.sunL + b);
-        break;
-      }
-      const float3 p = madd(o, t, d);
-      const float4 nr = ldg4(S.nrm + leaf);
-      const uint32_t mat = __float_as_uint(nr.w);
-      sg = mix_sig(sg, __float_as_uint(S.tris[3 * leaf].w));
-      const float3 ng = f3(nr);
-      const float3 n = dot(ng, d) < 0.0f ? ng : neg(ng);
-      const float cos_i = -dot(d, n);
-      const float4 m = ldg4(P.mb + mat * P.n_bands + b);
-      const int type = __ldg(P.mtype + mat);
-      const uint4 u = philox4x32_10(make_uint4(pix, pc.s, b, 4u * k), pc.key0, pc.key1);
-      if (type == 0 || type == 3) {
-        if (type == 3) L += T * m.w;
-        const float om = u01(u.x) * P.one_minus_cos;
-        const float ct = 1.0f - om;
-        const float st = sqrtf(fmaxf(0.0f, om * (2.0f - om)));
-        float sp_, cp_;
-        sincospif(2.0f * u01(u.y), &sp_, &cp_);
-        float3 t1, t2;
-        onb(P.sun, t1, t2);
-        const float3 wd = make_float3(st * cp_ * t1.x + st * sp_ * t2.x + ct * P.sun.x,
-                                      st * cp_ * t1.y + st * sp_ * t2.y + ct * P.sun.y,
-                                      st * cp_ * t1.z + st * sp_ * t2.z + ct * P.sun.z);
-        const float c = dot(n, wd);
-        if (c > 0.0f) {
-          uint32_t ngl;
-          const float Tr = shadow_T(S, P, madd(p, S.eps, n), wd, b, ngl, status);
-          sg = mix_sig(sg, ngl);
-          L += T * m.z * c * __ldg(P.sunL + b) * 2.0f * P.one_minus_cos * Tr;
-        }
-        const float E = photon_gather(M, 0u, j, p) * M.norm[0] + photon_gather(M, 1u, j, p) * M.norm[1];
-        L += T * m.z * (1.0f / 3.14159265358979f) * E;
-        break;
-      } else if (type == 1) {
-        float Rs, Ts;
-        thin_sheet(cos_i, m.x, m.y, __ldg(P.ad + mat * P.n_bands + b), Rs, Ts);
-        if (k == pc.depth) break;
-        const uint4 u1 = philox4x32_10(make_uint4(pix, pc.s, b, 4u * k + 1u), pc.key0, pc.key1);
-        if (u01(u1.x) < Rs / (Rs + Ts)) {
-          d = madd(d, -2.0f * dot(d, n), n);
-          o = madd(p, S.eps, n);
-          covered = false;
-        } else {
-          o = madd(p, -S.eps, n);
-        }
-        T *= Rs + Ts;
-      } else if (type == 4) {
-        const bool inside = dot(ng, d) > 0.0f;
-        const float alpha = __ldg(P.ad + mat * P.n_bands + b);
-        if (inside) T *= expf(-alpha * t);
-        if (k == pc.depth) break;
-        const float eta = inside ? 1.0f / m.x : m.x;
-        const float R = fresnel_complex(cos_i, eta, 0.0f);
-        const float r = inside ? m.x : 1.0f / m.x;
-        const float kk = 1.0f - r * r * (1.0f - cos_i * cos_i);
-        const uint4 u1 = philox4x32_10(make_uint4(pix, pc.s, b, 4u * k + 1u), pc.key0, pc.key1);
-        if (u01(u1.x) < R || kk < 0.0f) {
-          d = madd(d, -2.0f * dot(d, n), n);
-        } else {
-          const float3 td = madd(make_float3(r * d.x, r * d.y, r * d.z), r * cos_i - sqrtf(kk), n);
-          const float il = rsqrtf(dot(td, td));
-          d = make_float3(td.x * il, td.y * il, td.z * il);
-        }
-        const float step = S.eps / fmaxf(fabsf(dot(d, n)), 0.0625f);
-        if (dot(d, ng) < 0.0f) T *= expf(-alpha * step);
-        o = madd(p, step, d);
-        covered = false;
-      } else {
-        const float R = fresnel_complex(cos_i, m.x, m.y);
-        if (k == pc.depth) break;
-        d = madd(d, -2.0f * dot(d, n), n);
-        o = madd(p, S.eps, n);
-        T *= R;
-        covered = false;
-      }
-    }
-    const size_t slot = (size_t)pix * pc.B + pc.band_off + j;
-    if (L != 0.0f) accum[slot] += (double)L;
-    if (probe.map != nullptr) {
-      const uint32_t ps = probe.map[pix];
-      if (ps != 0xFFFFFFFFu) {
-        const size_t r = ((size_t)ps * pc.spp + (pc.s - pc.s_base)) * pc.B + pc.band_off + j;
-        probe.L[r] = L;
-        probe.sig[r] = sg;
-      }
-    }
-  }
-}
-
 // ---- single-step kernels for parity tests --------------------------------
 
 __global__ void k_philox(const uint4* __restrict__ ctr, uint4* __restrict__ out, uint64_t n, uint32_t k0, uint32_t k1) {
@@ -1796,7 +1680,7 @@ void launch_scan(uint32_t* data, size_t n, cudaStream_t st) {
 void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
                  const WaveParams& w, const WaveBufs& b, double* accum, const Probe& probe, cudaStream_t st,
                  int* launches, StageTimer* tm, const GuideWave* gwp, const GuideDev* gdev, const void* gpack,
-                 int sms) {
+                 int sms, const PhotonMaps* pm) {
   GuideWave gw{};
   if (gwp) gw = *gwp;
   const bool guided = gw.on;
@@ -1825,20 +1709,27 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
       else
         k_shade4<false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L4, b.T4,
                                                                   b.C4, b.sig, b.cnt, b.cap, accum, probe, b.status);
+    } else if (pm) {
+      if (rec)
+        k_shade<true, false, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(
+            S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe, b.status, gw, *pm);
+      else
+        k_shade<false, false, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(
+            S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig, b.cnt, b.cap, accum, probe, b.status, gw, *pm);
     } else if (guided) {
       if (rec)
         k_shade<true, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
-                                                                     b.cnt, b.cap, accum, probe, b.status, gw);
+                                                                     b.cnt, b.cap, accum, probe, b.status, gw, PhotonMaps{});
       else
         k_shade<false, true><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
-                                                                      b.cnt, b.cap, accum, probe, b.status, gw);
+                                                                      b.cnt, b.cap, accum, probe, b.status, gw, PhotonMaps{});
     } else {
       if (rec)
         k_shade<true, false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L, b.sig,
-                                                                      b.cnt, b.cap, accum, probe, b.status, gw);
+                                                                      b.cnt, b.cap, accum, probe, b.status, gw, PhotonMaps{});
       else
         k_shade<false, false><<<lc.grid_shade, lc.block_shade, 0, st>>>(S, P, w, k, qin, b.hit, qout, b.sq, b.L,
-                                                                       b.sig, b.cnt, b.cap, accum, probe, b.status, gw);
+                                                                       b.sig, b.cnt, b.cap, accum, probe, b.status, gw, PhotonMaps{});
     }
     if (tm) tm->end(STG_SHADE, st);
     if (guided && k <= gw.depth && k < w.depth) {
@@ -1869,14 +1760,6 @@ void launch_photon_trace(const DevScene& S, const DevSpectra& P, const PhotonPas
 void launch_photon_maps(const uint32_t* sorted_keys, const uint32_t* sorted_vals, uint32_t n, const float4* rec,
                         float4* rec_sorted, uint32_t* start, uint32_t* end, int sms, cudaStream_t st) {
   k_photon_bounds<<<(sms > 0 ? sms : 1) * 8, 256, 0, st>>>(sorted_keys, sorted_vals, n, rec, rec_sorted, start, end);
-}
-
-void launch_photon_camera(const DevScene& S, const DevSpectra& P, const DevCam* cams, uint32_t n_cams,
-                          const PhotonCam& pc, const PhotonMaps& M, double* accum, const Probe& probe,
-                          uint32_t* status, int sms, cudaStream_t st) {
-  const uint64_t n = (uint64_t)pc.npix * pc.Bc;
-  const unsigned g = (unsigned)std::min<uint64_t>((n + 127) / 128, (uint64_t)(sms > 0 ? sms : 1) * 64);
-  k_photon_camera<<<g, 128, 0, st>>>(S, P, cams, n_cams, pc, M, accum, probe, status);
 }
 
 void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st) {

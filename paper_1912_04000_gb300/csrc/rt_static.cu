@@ -202,6 +202,8 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   w.key1 = (uint32_t)(seed >> 32);
   w.nb = 1;
   w.B = band_count;
+  w.acc_stride = band_count;
+  w.acc_off = 0;
   const uint64_t total = PB64 * spp;
   for (uint64_t ws = 0; ws < total; ws += cap) {
     w.n = (uint32_t)((total - ws) < cap ? (total - ws) : cap);

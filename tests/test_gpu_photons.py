@@ -98,17 +98,21 @@ def test_mirror_caustic_closed_form(R):
 
 def test_chunks_hash_sizes_and_determinism(R):
     # 40 bands: log2_cells 20 splits them into chunks of 32 and 8, 12 keeps
-    # one chunk; the hash size changes only the summation order
-    wl = scenes.tiny_box(width=32, height=32, n_bands=40, spp=1, depth=5)
+    # one chunk; the hash size changes only the summation order.  3 spp: the
+    # small chunk's camera waves hold one sample each
+    wl = scenes.tiny_box(width=32, height=32, n_bands=40, spp=3, depth=5)
     R.load(wl)
     kw = dict(n_photons=4096, photon_depth=4, r_global=0.15, xyz_mode=2)
-    a = R.render_photons(wl.cameras, 1, 5, 3, log2_cells=20, **kw)
-    b = R.render_photons(wl.cameras, 1, 5, 3, log2_cells=12, **kw)
+    a = R.render_photons(wl.cameras, 3, 5, 3, log2_cells=20, **kw)
+    b = R.render_photons(wl.cameras, 3, 5, 3, log2_cells=12, **kw)
     assert a["stats"]["waves"] == 2 and b["stats"]["waves"] == 1
     sa, sb = a["spectral"].cpu().numpy(), b["spectral"].cpu().numpy()
     np.testing.assert_allclose(sa, sb, rtol=1e-5, atol=1e-12)
-    c = R.render_photons(wl.cameras, 1, 5, 3, log2_cells=20, **kw)["spectral"].cpu().numpy()
+    c = R.render_photons(wl.cameras, 3, 5, 3, log2_cells=20, **kw)["spectral"].cpu().numpy()
     assert np.array_equal(sa, c)
+    o = oracle.OracleScene(wl.scene, wl.spectra).render_photons(
+        wl.cameras, 3, 5, 3, n_photons=4096, photon_depth=4, r_caustic=0.005 * _diag(wl), r_global=0.15)
+    _photon_parity(a["xyz"].cpu().numpy(), o["xyz"], "40 bands in two chunks")
 
 
 def test_arguments_checked(R):
