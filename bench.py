@@ -34,12 +34,17 @@ PROFILE_TXT = os.path.join(ROOT, "profiles", "k_trace_closest_nave.txt")
 KERNEL_SOURCES = ["paper_1912_04000_gb300/csrc/rt_kernels.cu", "paper_1912_04000_gb300/csrc/rt_device.cuh"]
 
 
+BUILDERS = {"host": 0, "device": 1, "sbvh": 2}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--builder", default="sbvh", choices=["host", "device", "sbvh"],
+                    help="BVH builder: binned SAH, device linear BVH, or SAH with spatial splits")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-pixels", type=int, default=1536, help="oracle sample size (pixels at full spp/bands)")
     ap.add_argument("--guided-mse", action="store_true",
@@ -202,7 +207,7 @@ def run_guided_mse(args):
     from paper_1912_04000_gb300.renderer import Renderer
 
     wl = scenes.nave(width=args.mse_width, height=args.mse_height)
-    R = Renderer(0).load(wl)
+    R = Renderer(0).load(wl, builder=BUILDERS[args.builder])
     dev = R.device
     P, B = wl.n_pixels, wl.band_count
 
@@ -306,7 +311,7 @@ def run_bands_mse(args):
 
     make = scenes.crystal_nave if args.bands_workload == "crystal_nave" else scenes.nave
     wl = make(width=args.mse_width, height=args.mse_height)
-    R = Renderer(0).load(wl)
+    R = Renderer(0).load(wl, builder=BUILDERS[args.builder])
     dev = R.device
     P, B = wl.n_pixels, wl.band_count
 
@@ -364,7 +369,7 @@ def run_photon_mse(args):
 
     make = scenes.crystal_nave if args.bands_workload == "crystal_nave" else scenes.nave
     wl = make(width=args.mse_width, height=args.mse_height)
-    R = Renderer(0).load(wl)
+    R = Renderer(0).load(wl, builder=BUILDERS[args.builder])
     dev = R.device
     P, B = wl.n_pixels, wl.band_count
 
@@ -431,7 +436,7 @@ def main():
     dev = torch.device("cuda", info.local_rank)
     torch.cuda.set_device(dev)
     wl = scenes.nave()
-    R = Renderer(info.local_rank).load(wl)
+    R = Renderer(info.local_rank).load(wl, builder=BUILDERS[args.builder])
     bvh_info = R.scene_info()
     seed = multigpu.rank_seed(wl.seed, info.rank)
     stream = R.stream

@@ -184,13 +184,16 @@ rt_status rt_load_scene(rt_ctx* ctx, const float* verts, uint32_t n_verts, const
  * host (default; also provides the binary tree of trace_variant 1-3),
  * 1 = linear BVH built on the device (Morton codes, radix sort, Karras
  * hierarchy, collapse to the four-wide tree; at most 2^24 triangles; only
- * trace_variant 0).  The traversal results do not depend on the builder. */
+ * trace_variant 0), 2 = binned SAH on the host with spatial splits (a
+ * triangle may be referenced by several leaves, up to twice the triangle
+ * count in all; thin-glass triangles never are).  The traversal results do
+ * not depend on the builder. */
 rt_status rt_set_bvh_builder(rt_ctx* ctx, uint32_t builder);
 
 typedef struct {
   uint32_t n_tris;    /* triangles of the loaded scene */
   uint32_t n_nodes4;  /* four-wide BVH nodes */
-  uint32_t builder;   /* builder used: 0 host SAH, 1 device LBVH */
+  uint32_t builder;   /* builder used: 0 host SAH, 1 device LBVH, 2 host SAH with spatial splits */
   float build_ms;     /* BVH build time: host wall clock, or device time (CUDA events) */
 } rt_scene_info;
 rt_status rt_get_scene_info(rt_ctx* ctx, rt_scene_info* info);

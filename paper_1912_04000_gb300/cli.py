@@ -52,8 +52,8 @@ def main(argv=None):
     r.add_argument("--guide-train-steps", type=int, default=0)
     r.add_argument("--graph", action="store_true", help="capture the render in a CUDA graph and replay it")
     r.add_argument("--tune", action="store_true", help="autotuned launch settings (cached per GPU and workload)")
-    r.add_argument("--builder", default="host", choices=["host", "device"],
-                   help="BVH builder: binned SAH on the host or linear BVH on the device")
+    r.add_argument("--builder", default="host", choices=["host", "device", "sbvh"],
+                   help="BVH builder: binned SAH on the host, linear BVH on the device, or SAH with spatial splits")
     r.add_argument("--bands-per-path", type=int, default=1, choices=[1, 4],
                    help="4: every path carries four bands until its first refraction")
     r.add_argument("--estimator", default="path", choices=["path", "photon"],
@@ -65,7 +65,7 @@ def main(argv=None):
     from .renderer import Renderer
     wl = _workload(args)
     t0 = time.perf_counter()
-    R = Renderer(0).load(wl, builder=1 if args.builder == "device" else 0)
+    R = Renderer(0).load(wl, builder={"host": 0, "device": 1, "sbvh": 2}[args.builder])
     if args.guided:
         R.guide_init(seed=1)
     t_load = time.perf_counter() - t0

@@ -392,7 +392,8 @@ rt_status rt_set_counting(rt_ctx* c, int enable) {
 
 rt_status rt_set_bvh_builder(rt_ctx* c, uint32_t builder) {
   if (rt_status e = check_ctx(c)) return e;
-  if (builder > 1) return fail(c, RT_ERR_ARG, "rt_set_bvh_builder: 0 (host SAH) or 1 (device LBVH)");
+  if (builder > 2)
+    return fail(c, RT_ERR_ARG, "rt_set_bvh_builder: 0 (host SAH), 1 (device LBVH) or 2 (host SAH with spatial splits)");
   c->builder = builder;
   return RT_OK;
 }
@@ -474,12 +475,22 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     return f;
   };
   const auto t_build0 = std::chrono::steady_clock::now();
-  // host build: binned SAH, leaf order from the tree; device build: the
-  // records go up in input order and are sorted there
+  // host build: binned SAH (with spatial splits for builder 2, which may
+  // list a triangle in several leaves -- never a thin-glass one, whose
+  // sun-ray transmittance must count once), leaf order from the tree; device
+  // build: the records go up in input order and are sorted there
   BvhOut bvh;
-  if (!dev_build) build_bvh(verts, tris, n_tris, bvh);
-  std::vector<float4> tr(3 * (size_t)n_tris), nr(n_tris);
-  for (uint32_t i = 0; i < n_tris; ++i) {
+  if (c->builder == 2) {
+    std::vector<uint8_t> split(n_tris);
+    for (uint32_t t = 0; t < n_tris; ++t) split[t] = mat_type[mat_id[t]] != 1;
+    build_sbvh(verts, tris, n_tris, split.data(), bvh);
+  } else if (!dev_build) {
+    build_bvh(verts, tris, n_tris, bvh);
+  }
+  const size_t n_leaf = dev_build ? n_tris : bvh.order.size();
+  if (n_leaf >= (1u << 29)) return fail(c, RT_ERR_SCENE, "too many BVH references");
+  std::vector<float4> tr(3 * n_leaf), nr(n_leaf);
+  for (uint32_t i = 0; i < (uint32_t)n_leaf; ++i) {
     const uint32_t t = dev_build ? i : bvh.order[i];
     const float* v[3];
     for (int k = 0; k < 3; ++k) v[k] = verts + 3 * (size_t)tris[3 * (size_t)t + k];
@@ -599,7 +610,7 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     c->n_nodes4 = counts[0];
     c->build_ms = ms;
   }
-  c->builder_used = dev_build ? 1u : 0u;
+  c->builder_used = c->builder;
   c->n_tris = n_tris;
   c->n_mat = n_mat;
   const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];

@@ -189,6 +189,319 @@ int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Spatial-split BVH (Stich, Friedrich and Dietrich, "Spatial splits in
+// bounding volume hierarchies", HPG 2009): besides the binned object split
+// over reference centroids, every node whose object split leaves the two
+// children overlapping by more than 1e-5 of the root's area also tries 32
+// spatial split planes per axis, with each reference's share of a bin the box
+// of its triangle clipped to the bin; a spatial split that wins divides the
+// references that straddle its plane in two, each with the box of its side
+// of the clipped triangle.  References of non-splittable triangles (those
+// that must appear once in the tree) stay whole and follow their centroid.
+// The duplicates stop once the references reach twice the triangle count.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Ref {
+  uint32_t t;
+  Box b;
+};
+
+// Box of triangle (v0, v1, v2) clipped to the slab lo <= x[ax] <= hi (either
+// bound may be infinite) and to box `in`; empty if nothing is left.  The
+// clipping runs in FP64 and the box is rounded outward to float.
+Box clip_box(const double* v[3], int ax, double lo, double hi, const Box& in) {
+  double poly[9][3], tmp[9][3];
+  int n = 3;
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) poly[k][a] = v[k][a];
+  auto clip = [&](double plane, bool keep_above) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+      const double* P = poly[i];
+      const double* Q = poly[(i + 1) % n];
+      const bool pin = keep_above ? P[ax] >= plane : P[ax] <= plane;
+      const bool qin = keep_above ? Q[ax] >= plane : Q[ax] <= plane;
+      if (pin) {
+        for (int a = 0; a < 3; ++a) tmp[m][a] = P[a];
+        ++m;
+      }
+      if (pin != qin) {
+        const double s = (plane - P[ax]) / (Q[ax] - P[ax]);
+        for (int a = 0; a < 3; ++a) tmp[m][a] = P[a] + s * (Q[a] - P[a]);
+        tmp[m][ax] = plane;
+        ++m;
+      }
+    }
+    n = m;
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) poly[i][a] = tmp[i][a];
+  };
+  if (std::isfinite(lo)) clip(lo, true);
+  if (n > 0 && std::isfinite(hi)) clip(hi, false);
+  Box out;
+  if (n == 0) return out;
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < 3; ++a) {
+      float lo_f = (float)poly[i][a], hi_f = lo_f;
+      if ((double)lo_f > poly[i][a]) lo_f = std::nextafter(lo_f, -INFINITY);
+      if ((double)hi_f < poly[i][a]) hi_f = std::nextafter(hi_f, INFINITY);
+      out.lo[a] = std::min(out.lo[a], lo_f);
+      out.hi[a] = std::max(out.hi[a], hi_f);
+    }
+  for (int a = 0; a < 3; ++a) {
+    out.lo[a] = std::max(out.lo[a], in.lo[a]);
+    out.hi[a] = std::min(out.hi[a], in.hi[a]);
+    if (out.lo[a] > out.hi[a]) return Box{};
+  }
+  return out;
+}
+
+double overlap_area(const Box& a, const Box& b) {
+  Box o;
+  for (int i = 0; i < 3; ++i) {
+    o.lo[i] = std::max(a.lo[i], b.lo[i]);
+    o.hi[i] = std::min(a.hi[i], b.hi[i]);
+    if (!(o.lo[i] <= o.hi[i])) return 0.0;
+  }
+  return o.area();
+}
+
+}  // namespace
+
+int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint8_t* splittable, BvhOut& out) {
+  std::vector<double> vd(9 * (size_t)nt);
+  std::vector<Ref> root(nt);
+  Box world;
+  for (uint32_t t = 0; t < nt; ++t) {
+    root[t].t = t;
+    for (int k = 0; k < 3; ++k) {
+      const float* p = verts + 3 * (size_t)tris[3 * (size_t)t + k];
+      root[t].b.grow(p);
+      for (int a = 0; a < 3; ++a) vd[9 * (size_t)t + 3 * k + a] = p[a];
+    }
+    world.grow(root[t].b);
+  }
+  const double root_area = world.area();
+  const size_t budget = 2 * (size_t)nt;  // references at most
+  size_t n_refs = nt;
+  out.nodes.assign(2, BvhNode{});
+  out.order.clear();
+  out.order.reserve(budget);
+  struct STask {
+    uint32_t node, depth;
+    std::vector<Ref> refs;
+  };
+  std::vector<STask> stack;
+  stack.push_back({1, 0, std::move(root)});
+  uint32_t max_depth = 0;
+  auto cen = [](const Ref& r, int a) { return 0.5f * (r.b.lo[a] + r.b.hi[a]); };
+  while (!stack.empty()) {
+    STask tk = std::move(stack.back());
+    stack.pop_back();
+    max_depth = std::max(max_depth, tk.depth);
+    std::vector<Ref>& R = tk.refs;
+    const uint32_t n = (uint32_t)R.size();
+    Box bb, cb;
+    for (const Ref& r : R) {
+      bb.grow(r.b);
+      const float c[3] = {cen(r, 0), cen(r, 1), cen(r, 2)};
+      cb.grow(c);
+    }
+    BvhNode& nd = out.nodes[tk.node];
+    for (int i = 0; i < 3; ++i) {
+      nd.lo[i] = bb.lo[i];
+      nd.hi[i] = bb.hi[i];
+    }
+    auto make_leaf = [&]() {
+      out.nodes[tk.node].ref = (uint32_t)out.order.size();
+      out.nodes[tk.node].count = n;
+      for (const Ref& r : R) out.order.push_back(r.t);
+    };
+    if (n == 1) {
+      make_leaf();
+      continue;
+    }
+    // object split
+    int ob_axis = -1, ob_bin = -1;
+    double ob_cost = INFINITY;
+    Box ob_l, ob_r;
+    // spatial split
+    int sp_axis = -1, sp_bin = -1;
+    double sp_cost = INFINITY;
+    if (tk.depth < kMedianDepth) {
+      for (int ax = 0; ax < 3; ++ax) {
+        const float ext = cb.hi[ax] - cb.lo[ax];
+        if (!(ext > 0.0f)) continue;
+        Box bins[kBins];
+        uint32_t cnt[kBins] = {0};
+        const float scale = kBins / ext;
+        for (const Ref& r : R) {
+          int b = (int)((cen(r, ax) - cb.lo[ax]) * scale);
+          b = std::min(std::max(b, 0), kBins - 1);
+          bins[b].grow(r.b);
+          ++cnt[b];
+        }
+        Box rbox[kBins];
+        uint32_t rcnt[kBins];
+        Box acc;
+        uint32_t c = 0;
+        for (int b = kBins - 1; b > 0; --b) {
+          acc.grow(bins[b]);
+          c += cnt[b];
+          rbox[b] = acc;
+          rcnt[b] = c;
+        }
+        Box lacc;
+        uint32_t lc = 0;
+        for (int b = 0; b < kBins - 1; ++b) {
+          lacc.grow(bins[b]);
+          lc += cnt[b];
+          if (lc == 0 || rcnt[b + 1] == 0) continue;
+          const double cost = lacc.area() * lc + rbox[b + 1].area() * rcnt[b + 1];
+          if (cost < ob_cost) {
+            ob_cost = cost;
+            ob_axis = ax;
+            ob_bin = b;
+            ob_l = lacc;
+            ob_r = rbox[b + 1];
+          }
+        }
+      }
+      const bool try_spatial = n_refs < budget && (ob_axis < 0 || overlap_area(ob_l, ob_r) > 1e-5 * root_area);
+      if (try_spatial) {
+        for (int ax = 0; ax < 3; ++ax) {
+          const double lo = bb.lo[ax], ext = (double)bb.hi[ax] - lo;
+          if (!(ext > 0.0)) continue;
+          Box bins[kBins];
+          uint32_t ent[kBins] = {0}, ext_[kBins] = {0};
+          auto bin_of = [&](double x) {
+            int b = (int)((x - lo) / ext * kBins);
+            return std::min(std::max(b, 0), kBins - 1);
+          };
+          for (const Ref& r : R) {
+            if (!splittable[r.t]) {
+              const int b = bin_of(cen(r, ax));
+              bins[b].grow(r.b);
+              ++ent[b];
+              ++ext_[b];
+              continue;
+            }
+            const int b0 = bin_of(r.b.lo[ax]), b1 = bin_of(r.b.hi[ax]);
+            if (b0 == b1) {
+              bins[b0].grow(r.b);
+            } else {
+              const double* v[3] = {&vd[9 * (size_t)r.t], &vd[9 * (size_t)r.t + 3], &vd[9 * (size_t)r.t + 6]};
+              for (int b = b0; b <= b1; ++b) {
+                const double pl = lo + ext * b / kBins, ph = lo + ext * (b + 1) / kBins;
+                const Box cbx = clip_box(v, ax, b == b0 ? -INFINITY : pl, b == b1 ? INFINITY : ph, r.b);
+                bins[b].grow(cbx);
+              }
+            }
+            ++ent[b0];
+            ++ext_[b1];
+          }
+          double rarea[kBins];
+          uint32_t rcnt[kBins];
+          Box acc;
+          uint32_t c = 0;
+          for (int b = kBins - 1; b > 0; --b) {
+            acc.grow(bins[b]);
+            c += ext_[b];
+            rarea[b] = acc.area();
+            rcnt[b] = c;
+          }
+          Box lacc;
+          uint32_t lc = 0;
+          for (int b = 0; b < kBins - 1; ++b) {
+            lacc.grow(bins[b]);
+            lc += ent[b];
+            if (lc == 0 || rcnt[b + 1] == 0) continue;
+            const double cost = lacc.area() * lc + rarea[b + 1] * rcnt[b + 1];
+            if (cost < sp_cost) {
+              sp_cost = cost;
+              sp_axis = ax;
+              sp_bin = b;
+            }
+          }
+        }
+      }
+      const double best = std::min(ob_cost, sp_cost);
+      const double parea = bb.area();
+      if (n <= kMaxLeaf && ((ob_axis < 0 && sp_axis < 0) || parea * n <= parea + best)) {
+        make_leaf();
+        continue;
+      }
+    } else if (n <= kMaxLeaf) {
+      make_leaf();
+      continue;
+    }
+    std::vector<Ref> L, Rt;
+    L.reserve(n);
+    Rt.reserve(n);
+    if (sp_axis >= 0 && sp_cost < ob_cost) {
+      const int ax = sp_axis;
+      const double lo = bb.lo[ax], ext = (double)bb.hi[ax] - lo;
+      const double plane = lo + ext * (sp_bin + 1) / kBins;
+      for (const Ref& r : R) {
+        if (!splittable[r.t]) {
+          (cen(r, ax) < plane ? L : Rt).push_back(r);
+        } else if (r.b.hi[ax] <= plane) {
+          L.push_back(r);
+        } else if (r.b.lo[ax] >= plane) {
+          Rt.push_back(r);
+        } else {
+          const double* v[3] = {&vd[9 * (size_t)r.t], &vd[9 * (size_t)r.t + 3], &vd[9 * (size_t)r.t + 6]};
+          const Box lb = clip_box(v, ax, -INFINITY, plane, r.b), rb = clip_box(v, ax, plane, INFINITY, r.b);
+          const bool lok = lb.lo[0] <= lb.hi[0], rok = rb.lo[0] <= rb.hi[0];
+          if (lok) L.push_back({r.t, lb});
+          if (rok) Rt.push_back({r.t, rb});
+          if (!lok && !rok) L.push_back(r);
+          if (lok && rok) ++n_refs;
+        }
+      }
+    } else if (ob_axis >= 0) {
+      const int ax = ob_axis;
+      const float ext = cb.hi[ax] - cb.lo[ax];
+      const float scale = kBins / ext;
+      for (const Ref& r : R) {
+        int b = (int)((cen(r, ax) - cb.lo[ax]) * scale);
+        b = std::min(std::max(b, 0), kBins - 1);
+        (b <= ob_bin ? L : Rt).push_back(r);
+      }
+    }
+    if (L.empty() || Rt.empty()) {
+      // median split by count along the widest centroid axis (or by order)
+      L.clear();
+      Rt.clear();
+      int ax = 0;
+      for (int i = 1; i < 3; ++i)
+        if (cb.hi[i] - cb.lo[i] > cb.hi[ax] - cb.lo[ax]) ax = i;
+      std::vector<Ref> S = R;
+      const uint32_t mid = n / 2;
+      std::nth_element(S.begin(), S.begin() + mid, S.end(), [&](const Ref& a, const Ref& b) {
+        const float ca = cen(a, ax), cb2 = cen(b, ax);
+        return ca < cb2 || (ca == cb2 && a.t < b.t);
+      });
+      L.assign(S.begin(), S.begin() + mid);
+      Rt.assign(S.begin() + mid, S.end());
+    }
+    R.clear();
+    R.shrink_to_fit();
+    const uint32_t left = (uint32_t)out.nodes.size();
+    out.nodes.push_back(BvhNode{});
+    out.nodes.push_back(BvhNode{});
+    out.nodes[tk.node].ref = left;
+    out.nodes[tk.node].count = 0;
+    stack.push_back({left + 1, tk.depth + 1, std::move(Rt)});
+    stack.push_back({left, tk.depth + 1, std::move(L)});
+  }
+  out.max_depth = max_depth;
+  return 0;
+}
+
 int collapse_bvh4(const BvhOut& b2, std::vector<Bvh4Node>& out, uint32_t* max_depth) {
   const std::vector<BvhNode>& nb = b2.nodes;
   auto area = [&](uint32_t i) {

@@ -66,7 +66,7 @@ class Renderer:
 
     # -- scene and spectra ------------------------------------------------------
     def load_scene(self, scene, builder: int = 0):
-        """builder 0: binned SAH on the host; 1: linear BVH on the device."""
+        """builder 0: binned SAH on the host; 1: linear BVH on the device; 2: SAH with spatial splits."""
         self._check("rt_set_bvh_builder", self.lib.rt_set_bvh_builder(self._h, int(builder)))
         v = np.ascontiguousarray(scene.verts, np.float32)
         t = np.ascontiguousarray(scene.tris, np.uint32)
@@ -96,7 +96,8 @@ class Renderer:
     def scene_info(self) -> dict:
         info = _native.SceneInfo()
         self._check("rt_get_scene_info", self.lib.rt_get_scene_info(self._h, C.byref(info)))
-        return {"n_tris": info.n_tris, "n_nodes4": info.n_nodes4, "builder": ("host_sah", "device_lbvh")[info.builder],
+        return {"n_tris": info.n_tris, "n_nodes4": info.n_nodes4,
+                "builder": ("host_sah", "device_lbvh", "host_sbvh")[info.builder],
                 "build_ms": info.build_ms}
 
     # -- render -----------------------------------------------------------------

@@ -71,4 +71,4 @@ def test_render_matches_host_build(R):
 
 def test_builder_argument_checked(R):
     with pytest.raises(RtError):
-        R.load(scenes.tiny_box(), builder=2)
+        R.load(scenes.tiny_box(), builder=3)
