@@ -132,6 +132,13 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// Frees a temporary device buffer when the scope ends, error paths included.
+template <class T>
+struct DevTemp {
+  T* p = nullptr;
+  ~DevTemp() { dfree(p); }
+};
+
 rt_status check_ctx(rt_ctx* c) {
   if (!c) return RT_ERR_ARG;
   if (c->poisoned) return fail(c, RT_ERR_STATE, "context unusable after a CUDA error: " + c->err);
@@ -1565,18 +1572,19 @@ rt_status rt_photon_records(rt_ctx* c, uint32_t band_first, uint32_t band_count,
   cudaStream_t st = c->stream;
   PhotonPass pp{};
   photon_setup(c, n_photons, seed, pp);
-  float4* portal = nullptr;
-  float* cdf = nullptr;
+  DevTemp<float4> portal;
+  DevTemp<float> cdf;
   if (emission == 1) {
     double W = 0.0;
-    if (rt_status e = photon_portals(c, &portal, &cdf, &pp.n_portal, &W)) return e;
-    pp.portal = portal;
-    pp.cdf = cdf;
+    if (rt_status e = photon_portals(c, &portal.p, &cdf.p, &pp.n_portal, &W)) return e;
+    pp.portal = portal.p;
+    pp.cdf = cdf.p;
     pp.emission = 1;
     pp.flux = (float)(2.0 * M_PI * (1.0 - c->cos_max_d) * W / (double)n_photons);
   }
-  uint32_t* kv = nullptr;
-  CUDA_TRY(c, cudaMalloc(&kv, slots * 2 * sizeof(uint32_t)));
+  DevTemp<uint32_t> kvt;
+  CUDA_TRY(c, cudaMalloc(&kvt.p, slots * 2 * sizeof(uint32_t)));
+  uint32_t* kv = kvt.p;
   pp.band0 = band_first;
   pp.Bc = band_count;
   pp.depth = depth;
@@ -1587,9 +1595,6 @@ rt_status rt_photon_records(rt_ctx* c, uint32_t band_first, uint32_t band_count,
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->wb.status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
-  dfree(kv);
-  dfree(portal);
-  dfree(cdf);
   return status_to_rt(c, *c->h_status);
 }
 
@@ -1679,13 +1684,13 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
   if (o.emission > 1) return fail(c, RT_ERR_ARG, "rt_render_photons: emission is 0 (disk) or 1 (portals)");
   PhotonPass pp{};
   photon_setup(c, N, seed, pp);
-  float4* portal = nullptr;
-  float* cdf = nullptr;
+  DevTemp<float4> portal;
+  DevTemp<float> cdf;
   if (o.emission == 1) {
     double W = 0.0;
-    if (rt_status e = photon_portals(c, &portal, &cdf, &pp.n_portal, &W)) return e;
-    pp.portal = portal;
-    pp.cdf = cdf;
+    if (rt_status e = photon_portals(c, &portal.p, &cdf.p, &pp.n_portal, &W)) return e;
+    pp.portal = portal.p;
+    pp.cdf = cdf.p;
     pp.emission = 1;
     pp.flux = (float)(2.0 * M_PI * (1.0 - c->cos_max_d) * W / (double)N);
   }
@@ -1737,7 +1742,13 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
   w.nb = 1;
   w.acc_stride = band_count;
   const DevScene S = dev_scene(c);
-  std::vector<cudaEvent_t> ev;
+  struct Events {
+    std::vector<cudaEvent_t> v;
+    ~Events() {
+      for (auto e : v) cudaEventDestroy(e);
+    }
+  } evs;
+  std::vector<cudaEvent_t>& ev = evs.v;
   auto mark = [&]() {
     cudaEvent_t e;
     cudaEventCreate(&e);
@@ -1813,8 +1824,5 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
     cudaEventElapsedTime(&stats->ms_render, ev.front(), ev[ev.size() - 2]);
     cudaEventElapsedTime(&stats->ms_xyz, ev[ev.size() - 2], ev.back());
   }
-  for (auto e : ev) cudaEventDestroy(e);
-  dfree(portal);
-  dfree(cdf);
   return status_to_rt(c, *c->h_status);
 }
