@@ -17,9 +17,11 @@
 // one cache line each) with the same leaves, which the default traversal
 // reads: half the dependent node fetches per ray.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "rt_bvh.h"
@@ -199,7 +201,9 @@ int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out
 // references that straddle its plane in two, each with the box of its side
 // of the clipped triangle.  References of non-splittable triangles (those
 // that must appear once in the tree) stay whole and follow their centroid.
-// The duplicates stop once the references reach twice the triangle count.
+// The duplicates stop once the references reach twice the triangle count
+// (per subtree job, twice its own references).  Below the top of the tree the
+// subtrees are built on all host threads, with the same result as one thread.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -298,10 +302,10 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
   stack.push_back({1, 0, std::move(root)});
   uint32_t max_depth = 0;
   auto cen = [](const Ref& r, int a) { return 0.5f * (r.b.lo[a] + r.b.hi[a]); };
-  while (!stack.empty()) {
-    STask tk = std::move(stack.back());
-    stack.pop_back();
-    max_depth = std::max(max_depth, tk.depth);
+  // one node: its split (or leaf) into nodes / order, children onto stk
+  auto step = [&](STask tk, std::vector<BvhNode>& nodes, std::vector<uint32_t>& order, std::vector<STask>& stk,
+                  size_t& refs_count, size_t bud, uint32_t& maxd) {
+    maxd = std::max(maxd, tk.depth);
     std::vector<Ref>& R = tk.refs;
     const uint32_t n = (uint32_t)R.size();
     Box bb, cb;
@@ -310,19 +314,19 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
       const float c[3] = {cen(r, 0), cen(r, 1), cen(r, 2)};
       cb.grow(c);
     }
-    BvhNode& nd = out.nodes[tk.node];
+    BvhNode& nd = nodes[tk.node];
     for (int i = 0; i < 3; ++i) {
       nd.lo[i] = bb.lo[i];
       nd.hi[i] = bb.hi[i];
     }
     auto make_leaf = [&]() {
-      out.nodes[tk.node].ref = (uint32_t)out.order.size();
-      out.nodes[tk.node].count = n;
-      for (const Ref& r : R) out.order.push_back(r.t);
+      nodes[tk.node].ref = (uint32_t)order.size();
+      nodes[tk.node].count = n;
+      for (const Ref& r : R) order.push_back(r.t);
     };
     if (n == 1) {
       make_leaf();
-      continue;
+      return;
     }
     // object split
     int ob_axis = -1, ob_bin = -1;
@@ -370,7 +374,7 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
           }
         }
       }
-      const bool try_spatial = n_refs < budget && (ob_axis < 0 || overlap_area(ob_l, ob_r) > 1e-5 * root_area);
+      const bool try_spatial = refs_count < bud && (ob_axis < 0 || overlap_area(ob_l, ob_r) > 1e-5 * root_area);
       if (try_spatial) {
         for (int ax = 0; ax < 3; ++ax) {
           const double lo = bb.lo[ax], ext = (double)bb.hi[ax] - lo;
@@ -432,11 +436,11 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
       const double parea = bb.area();
       if (n <= kMaxLeaf && ((ob_axis < 0 && sp_axis < 0) || parea * n <= parea + best)) {
         make_leaf();
-        continue;
+        return;
       }
     } else if (n <= kMaxLeaf) {
       make_leaf();
-      continue;
+      return;
     }
     std::vector<Ref> L, Rt;
     L.reserve(n);
@@ -459,7 +463,7 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
           if (lok) L.push_back({r.t, lb});
           if (rok) Rt.push_back({r.t, rb});
           if (!lok && !rok) L.push_back(r);
-          if (lok && rok) ++n_refs;
+          if (lok && rok) ++refs_count;
         }
       }
     } else if (ob_axis >= 0) {
@@ -490,13 +494,73 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
     }
     R.clear();
     R.shrink_to_fit();
-    const uint32_t left = (uint32_t)out.nodes.size();
-    out.nodes.push_back(BvhNode{});
-    out.nodes.push_back(BvhNode{});
-    out.nodes[tk.node].ref = left;
-    out.nodes[tk.node].count = 0;
-    stack.push_back({left + 1, tk.depth + 1, std::move(Rt)});
-    stack.push_back({left, tk.depth + 1, std::move(L)});
+    const uint32_t left = (uint32_t)nodes.size();
+    nodes.push_back(BvhNode{});
+    nodes.push_back(BvhNode{});
+    nodes[tk.node].ref = left;
+    nodes[tk.node].count = 0;
+    stk.push_back({left + 1, tk.depth + 1, std::move(Rt)});
+    stk.push_back({left, tk.depth + 1, std::move(L)});
+  };
+  // the top of the tree on this thread; subtrees of at most kParRefs
+  // references become independent jobs, built in parallel into their own
+  // node and order arrays (root at local node 0, child pairs from node 2)
+  // and stitched back in job order, so the tree does not depend on the
+  // thread count
+  const size_t kParRefs = std::max<size_t>(4096, nt / 256);
+  std::vector<STask> jobs;
+  while (!stack.empty()) {
+    STask tk = std::move(stack.back());
+    stack.pop_back();
+    if (tk.depth > 0 && tk.refs.size() <= kParRefs) {
+      jobs.push_back(std::move(tk));
+      continue;
+    }
+    step(std::move(tk), out.nodes, out.order, stack, n_refs, budget, max_depth);
+  }
+  struct Local {
+    std::vector<BvhNode> nodes;
+    std::vector<uint32_t> order;
+    uint32_t maxd = 0;
+  };
+  std::vector<Local> loc(jobs.size());
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const size_t j = next.fetch_add(1);
+      if (j >= jobs.size()) break;
+      Local& L = loc[j];
+      L.nodes.assign(2, BvhNode{});
+      std::vector<STask> stk;
+      const size_t nref = jobs[j].refs.size();
+      size_t cnt = nref;
+      STask root_task{0, jobs[j].depth, std::move(jobs[j].refs)};
+      stk.push_back(std::move(root_task));
+      while (!stk.empty()) {
+        STask tk = std::move(stk.back());
+        stk.pop_back();
+        step(std::move(tk), L.nodes, L.order, stk, cnt, 2 * nref, L.maxd);
+      }
+    }
+  };
+  const unsigned nth = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
+  std::vector<std::thread> th;
+  for (unsigned q = 0; q + 1 < nth && q + 1 < jobs.size(); ++q) th.emplace_back(worker);
+  worker();
+  for (auto& q : th) q.join();
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    const Local& L = loc[j];
+    const uint32_t base = (uint32_t)out.nodes.size();
+    const uint32_t obase = (uint32_t)out.order.size();
+    auto remap = [&](BvhNode b) {
+      if (b.count) b.ref += obase;
+      else b.ref = base + (b.ref - 2);
+      return b;
+    };
+    out.nodes[jobs[j].node] = remap(L.nodes[0]);
+    for (size_t i = 2; i < L.nodes.size(); ++i) out.nodes.push_back(remap(L.nodes[i]));
+    out.order.insert(out.order.end(), L.order.begin(), L.order.end());
+    max_depth = std::max(max_depth, L.maxd);
   }
   out.max_depth = max_depth;
   return 0;
