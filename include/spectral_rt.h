@@ -174,20 +174,21 @@ rt_status rt_set_timing(rt_ctx* ctx, int enable);
 /* Scene (the paper's first actor, section 1): n_verts float3 positions in
  * metres, n_tris uint32 index triples, a material id per triangle, and per
  * material its rt_material_type and thickness in metres (thin glass).
- * Builds a binned-SAH BVH on the host, copies it to the device; the library
+ * Builds the BVH with the builder rt_set_bvh_builder selected (default: binned
+ * SAH with spatial splits on the host), copies it to the device; the library
  * owns its copy.  Replaces any previous scene. */
 rt_status rt_load_scene(rt_ctx* ctx, const float* verts, uint32_t n_verts, const uint32_t* tris,
                         uint32_t n_tris, const uint32_t* mat_id, const int32_t* mat_type,
                         const float* mat_thickness, uint32_t n_mat);
 
 /* BVH builder of the following rt_load_scene calls: 0 = binned SAH on the
- * host (default; also provides the binary tree of trace_variant 1-3),
+ * host (also provides the binary tree of trace_variant 1-3),
  * 1 = linear BVH built on the device (Morton codes, radix sort, Karras
  * hierarchy, collapse to the four-wide tree; at most 2^24 triangles; only
- * trace_variant 0), 2 = binned SAH on the host with spatial splits (a
- * triangle may be referenced by several leaves, up to twice the triangle
- * count in all; thin-glass triangles never are).  The traversal results do
- * not depend on the builder. */
+ * trace_variant 0), 2 = binned SAH on the host with spatial splits (the
+ * default; a triangle may be referenced by several leaves, about twice the
+ * triangle count at most; thin-glass triangles never are; also provides the
+ * binary tree).  The traversal results do not depend on the builder. */
 rt_status rt_set_bvh_builder(rt_ctx* ctx, uint32_t builder);
 
 typedef struct {

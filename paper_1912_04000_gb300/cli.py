@@ -52,7 +52,7 @@ def main(argv=None):
     r.add_argument("--guide-train-steps", type=int, default=0)
     r.add_argument("--graph", action="store_true", help="capture the render in a CUDA graph and replay it")
     r.add_argument("--tune", action="store_true", help="autotuned launch settings (cached per GPU and workload)")
-    r.add_argument("--builder", default="host", choices=["host", "device", "sbvh"],
+    r.add_argument("--builder", default="sbvh", choices=["host", "device", "sbvh"],
                    help="BVH builder: binned SAH on the host, linear BVH on the device, or SAH with spatial splits")
     r.add_argument("--bands-per-path", type=int, default=1, choices=[1, 4],
                    help="4: every path carries four bands until its first refraction")

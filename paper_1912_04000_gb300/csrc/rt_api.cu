@@ -31,7 +31,8 @@ struct rt_ctx {
   uint32_t n_nodes = 0, n_nodes4 = 0, n_tris = 0, n_mat = 0;
   float eps = 0.0f;
   bool has_scene = false;
-  uint32_t builder = 0;       // BVH builder for the next rt_load_scene: 0 host SAH, 1 device LBVH
+  uint32_t builder = 2;       // BVH builder for the next rt_load_scene: 0 host SAH, 1 device LBVH,
+                              // 2 host SAH with spatial splits (default)
   uint32_t builder_used = 0;  // builder of the loaded scene
   float build_ms = 0.0f;      // its build time
   // spectra

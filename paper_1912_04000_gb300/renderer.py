@@ -65,8 +65,9 @@ class Renderer:
         return float(g.value)
 
     # -- scene and spectra ------------------------------------------------------
-    def load_scene(self, scene, builder: int = 0):
-        """builder 0: binned SAH on the host; 1: linear BVH on the device; 2: SAH with spatial splits."""
+    def load_scene(self, scene, builder: int = 2):
+        """builder 0: binned SAH on the host; 1: linear BVH on the device; 2 (default): SAH with
+        spatial splits."""
         self._check("rt_set_bvh_builder", self.lib.rt_set_bvh_builder(self._h, int(builder)))
         v = np.ascontiguousarray(scene.verts, np.float32)
         t = np.ascontiguousarray(scene.tris, np.uint32)
@@ -88,7 +89,7 @@ class Renderer:
         self._check("rt_set_spectra", st)
         self.n_bands = lam.shape[0]
 
-    def load(self, workload, builder: int = 0):
+    def load(self, workload, builder: int = 2):
         self.load_scene(workload.scene, builder)
         self.set_spectra(workload.spectra)
         return self
