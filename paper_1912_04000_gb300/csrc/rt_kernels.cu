@@ -970,9 +970,10 @@ __global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WavePar
 //     and the others stop (their radiance so far is kept).
 // "Carried" = throughput != 0; with one band left every rule is the
 // one-band rule of k_shade.  Each choice has the one-band expectation per
-// band, so the four-band estimate of every band is unbiased.
+// band, so the four-band estimate of every band is unbiased.  Three blocks
+// of 256 per SM (80 registers, a few bytes spilled) beat two blocks at 92.
 template <bool RECORD>
-__global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+__global__ void __launch_bounds__(256, 3) k_shade4(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ qin, const float2* __restrict__ hit,
                                                 float4* __restrict__ qout, float4* __restrict__ sq,
                                                 float4* __restrict__ L4, float4* __restrict__ T4,
@@ -1018,10 +1019,9 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
         const float3 n = dot(ng, d) < 0.0f ? ng : neg(ng);
         const float cos_i = -dot(d, n);
         const uint32_t mrow = mat * P.n_bands + b0;
-        float4 m[4];
-#pragma unroll
-        for (uint32_t q = 0; q < 4u; ++q)
-          m[q] = q < nv ? ldg4(P.mb + mrow + q * G) : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        // material rows of the carried bands: each branch loads only the
+        // fields it reads (n, k / rho, le), which keeps fewer registers live
+        const float4* mr = P.mb + mrow;
         const int type = __ldg(P.mtype + mat);
         const uint4 u = philox4x32_10(make_uint4(id.pix, id.s, b0, 4u * k), w.key0, w.key1);
         // the bands still carried (throughput != 0), else every band of the path
@@ -1032,9 +1032,13 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
         if (act == 0u) act = (1u << nv) - 1u;
         const float na = (float)__popc(act);
         if (type == 0 || type == 3) {
+          float rho[4];
+#pragma unroll
+          for (uint32_t q = 0; q < 4u; ++q) rho[q] = q < nv ? __ldg(&mr[q * G].z) : 0.0f;
           if (type == 3) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) L[q] += T[q] * m[q].w;
+            for (uint32_t q = 0; q < 4u; ++q)
+              if (q < nv) L[q] += T[q] * __ldg(&mr[q * G].w);
           }
           const float om = u01(u.x) * P.one_minus_cos;
           const float ct = 1.0f - om;
@@ -1053,7 +1057,7 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
             float C[4];
 #pragma unroll
             for (uint32_t q = 0; q < 4u; ++q)
-              C[q] = q < nv ? T[q] * m[q].z * c * __ldg(P.sunL + b0 + q * G) * 2.0f * P.one_minus_cos : 0.0f;
+              C[q] = q < nv ? T[q] * rho[q] * c * __ldg(P.sunL + b0 + q * G) * 2.0f * P.one_minus_cos : 0.0f;
             C4[pid] = make_float4(C[0], C[1], C[2], C[3]);
             const uint32_t fl = pid | (k == w.depth ? kFlagTerm : 0u);
             s0 = make_float4(po.x, po.y, po.z, __uint_as_float(fl));
@@ -1072,7 +1076,7 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
                                           rr * c2 * b1.y + rr * s2 * b2.y + zz * n.y,
                                           rr * c2 * b1.z + rr * s2 * b2.z + zz * n.z);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) T[q] *= m[q].z;
+            for (int q = 0; q < 4; ++q) T[q] *= rho[q];
             emit_next = true;
             n0 = make_float4(po.x, po.y, po.z, __uint_as_float(pid | kFlagCovered));
             n1 = make_float4(nd.x, nd.y, nd.z, 0.0f);
@@ -1083,7 +1087,10 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
           for (uint32_t q = 0; q < 4u; ++q) {
             Rs[q] = 0.0f;
             Ts[q] = 1.0f;
-            if (q < nv) thin_sheet(cos_i, m[q].x, m[q].y, __ldg(P.ad + mrow + q * G), Rs[q], Ts[q]);
+            if (q < nv) {
+              const float2 nk = __ldg((const float2*)(mr + q * G));
+              thin_sheet(cos_i, nk.x, nk.y, __ldg(P.ad + mrow + q * G), Rs[q], Ts[q]);
+            }
           }
           if (k == w.depth) {
             terminate = true;
@@ -1122,10 +1129,12 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
           if (k == w.depth) {
             terminate = true;
           } else {
-            float R[4];
+            float R[4], nq[4];
 #pragma unroll
-            for (uint32_t q = 0; q < 4u; ++q)
-              R[q] = q < nv ? fresnel_complex(cos_i, inside ? 1.0f / m[q].x : m[q].x, 0.0f) : 1.0f;
+            for (uint32_t q = 0; q < 4u; ++q) {
+              nq[q] = q < nv ? __ldg(&mr[q * G].x) : 1.0f;
+              R[q] = q < nv ? fresnel_complex(cos_i, inside ? 1.0f / nq[q] : nq[q], 0.0f) : 1.0f;
+            }
             const uint4 u1 = philox4x32_10(make_uint4(id.pix, id.s, b0, 4u * k + 1u), w.key0, w.key1);
             float pr = 0.0f;
 #pragma unroll
@@ -1147,12 +1156,12 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
                   if (pick == 0u) c = q;
                   pick = pick == 0u ? 0xFFFFFFFFu : pick - 1u;
                 }
-              float Rc = R[0], nc = m[0].x;
+              float Rc = R[0], nc = nq[0];
 #pragma unroll
               for (uint32_t q = 1; q < 4u; ++q)
                 if (q == c) {
                   Rc = R[q];
-                  nc = m[q].x;
+                  nc = nq[q];
                 }
               const float wgt = na * (1.0f - Rc) / (1.0f - pr);
 #pragma unroll
@@ -1180,7 +1189,13 @@ __global__ void __launch_bounds__(256) k_shade4(DevScene S, DevSpectra P, WavePa
         } else {
           float R[4];
 #pragma unroll
-          for (uint32_t q = 0; q < 4u; ++q) R[q] = q < nv ? fresnel_complex(cos_i, m[q].x, m[q].y) : 0.0f;
+          for (uint32_t q = 0; q < 4u; ++q) {
+            R[q] = 0.0f;
+            if (q < nv) {
+              const float2 nk = __ldg((const float2*)(mr + q * G));
+              R[q] = fresnel_complex(cos_i, nk.x, nk.y);
+            }
+          }
           if (k == w.depth) {
             terminate = true;
           } else {
