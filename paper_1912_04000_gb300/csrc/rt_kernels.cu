@@ -600,7 +600,10 @@ constexpr uint32_t kNoRay = 0xFFFFFFFFu;
 // closest-hit kernel: blocks of at most 128 threads, 9 of them per SM
 // (<= 56 registers, 36 warps)
 constexpr int kTraceMaxThreads = 128, kTraceMinBlocks = 9;
-// sun-ray kernel: at least 4 blocks of 256 threads per SM (<= 64 registers)
+// sun-ray kernel: one band per path as the closest-hit kernel (9 blocks of
+// 128, <= 56 registers, a few bytes spilled: measured 0.4% faster on the
+// nave than 8 blocks at 60); four bands per path at least 4 blocks of 256
+// threads' worth (<= 64 registers)
 #ifndef SRT_SHADOW_MIN_BLOCKS
 #define SRT_SHADOW_MIN_BLOCKS 4
 #endif
@@ -1241,7 +1244,8 @@ __global__ void __launch_bounds__(256, 3) k_shade4(DevScene S, DevSpectra P, Wav
 // NB = 4: every sun ray belongs to a path that carries four bands; the ray
 // gathers one transmittance per band and the contributions wait in C4.
 template <bool RECORD, bool COUNT, int MODE, int NB = 1>
-__global__ void __launch_bounds__(256, kShadowMinBlocks) k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+__global__ void __launch_bounds__(NB == 1 ? kTraceMaxThreads : 256, NB == 1 ? kTraceMinBlocks : kShadowMinBlocks)
+    k_shadow(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                 const float4* __restrict__ sq, float* __restrict__ Lbuf,
                                                 uint32_t* __restrict__ sigbuf, Counters* cnt, uint32_t cap,
                                                 double* __restrict__ accum, Probe probe, Totals* tot,
