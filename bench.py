@@ -452,6 +452,8 @@ def main():
     R.set_counting(False)
     ext_nodes = cs["nodes_visited"] / max(cs["ext_rays"], 1)
     ext_tris = cs["tris_tested"] / max(cs["ext_rays"], 1)
+    sun_slots = cs["shadow_nodes_visited"] / max(cs["shadow_rays"], 1)
+    sun_tris = cs["shadow_tris_tested"] / max(cs["shadow_rays"], 1)
 
     for _ in range(args.warmup):
         step()
@@ -536,7 +538,8 @@ def main():
                 "peak_source": "L2 streaming-read probe (rt_probe_l2, 48 MiB x 50) measured in this run",
                 "hbm_peak_measured": 6777.0,
                 "algorithmic_bytes_per_ray": bytes_per_ray, "nodes_per_ray": ext_nodes,
-                "tris_per_ray": ext_tris, "launch_ms": launch_ms, "rays_per_launch": rays_per_launch,
+                "tris_per_ray": ext_tris, "sun_child_slots_per_ray": sun_slots, "sun_tris_per_ray": sun_tris,
+                "launch_ms": launch_ms, "rays_per_launch": rays_per_launch,
                 "stage_ms_per_step": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
                                               [m / args.steps for m in stage_ms])),
             },

@@ -698,6 +698,12 @@ rt_status rt_set_spectra(rt_ctx* c, const float* lambda_nm, uint32_t n_bands, co
   for (int a = 0; a < 3; ++a) c->sun_d[a] = sun_dir[a] / sl;
   c->cos_max_d = std::cos((double)sun_half_angle);
   P.one_minus_cos = (float)(1.0 - std::cos((double)sun_half_angle));
+  // the sun-ray visit order of the four-wide tree's children
+  if (c->d_nodes4 && c->n_nodes4) {
+    launch_sun_order4(c->d_nodes4, c->n_nodes4, P.sun, c->sms, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
   c->has_spectra = true;
   return RT_OK;
 }

@@ -233,6 +233,9 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
                  cudaStream_t st, int* launches, StageTimer* timer, const GuideWave* gw = nullptr,
                  const GuideDev* gdev = nullptr, const void* gpack = nullptr, int sms = 0,
                  const PhotonMaps* pm = nullptr);
+// Sorts the children of the n four-wide nodes far-to-near along the sun
+// (the visit order of sun rays).
+void launch_sun_order4(float4* nodes4, uint32_t n, float3 sun, int sms, cudaStream_t st);
 void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaStream_t st, int sms);
 void launch_philox(const uint32_t* ctr, uint32_t* out, uint64_t n, uint32_t k0, uint32_t k1, cudaStream_t st);
 void launch_trace_closest_rays(const DevScene& S, const float* o, const float* d, uint64_t n, float* t,

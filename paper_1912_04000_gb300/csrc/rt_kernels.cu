@@ -188,8 +188,9 @@ __device__ __forceinline__ void cswap(float& ta, uint32_t& pa, float& tb, uint32
 // Interior node: test the four children, descend into the nearest entered
 // one and push the others, the nearer ones last (popped first); with ANY
 // (sun rays, which need every crossed sheet or one opaque hit, in any order)
-// descend into the first entered child and push the rest in slot order.
-// Returns false if no child is entered.
+// visit the entered children in slot order: descend into the first and push
+// the others with the next one on top.  Slot order is set by k_sun_order4
+// (farthest along the sun first).  Returns false if no child is entered.
 template <bool FMA, bool COUNT, bool ANY = false>
 __device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const DevScene& S, float tmax,
                                                uint32_t* status, uint32_t& n_nodes) {
@@ -213,21 +214,24 @@ __device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const Dev
       tv.sp = 0;
       return false;
     }
-    bool first = true;
     const float tt[4] = {t0, t1, t2, t3};
     const uint32_t pp[4] = {p0, p1, p2, p3};
+    // entered child j >= 1 (in slot order) goes to stack[sp + nh - 1 - j]
+    const int top = tv.sp + nh - 2;
+    int j = -1;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (tt[i] < INFINITY) {
-        if (first) {
+        if (j < 0) {
           tv.ref = pp[i] >> 3;
           tv.cnt = pp[i] & 7u;
-          first = false;
         } else {
-          stack[tv.sp++] = make_uint2(pp[i], 0u);
+          stack[top - j] = make_uint2(pp[i], 0u);
         }
+        ++j;
       }
     }
+    tv.sp += nh - 1;
     return true;
   }
   // sorting network of four (missed children, at +inf, end up last)
@@ -1799,6 +1803,51 @@ void launch_trace_shadow_rays(const DevScene& S, const DevSpectra& P, const floa
 void launch_optics(const float* c, const float* n, const float* k, const float* lam, const float* d, uint64_t count,
                    float* R, float* Rs, float* Ts, cudaStream_t st) {
   k_optics<<<grid_for(count, 256), 256, 0, st>>>(c, n, k, lam, d, count, R, Rs, Ts);
+}
+
+// Orders the four children of every four-wide node by the position of
+// their box centres along the sun direction s, farthest first; empty slots
+// (packed reference 0) last, ties by the packed reference, so that the order
+// depends only on the children and s.  Sun rays visit entered children in
+// slot order and stop at the first opaque triangle: in an enclosed scene the
+// occluder is most often the outer shell, which far-first order reaches
+// sooner (nave: 5.2 instead of 8.0 node visits per sun ray, counted on the
+// CPU).  Closest-hit traversal sorts children per ray and does not depend
+// on slot order.
+__global__ void k_sun_order4(float4* __restrict__ nodes4, uint32_t n, float3 s) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float* f = reinterpret_cast<float*>(nodes4 + 8 * (size_t)i);
+    float x[28];
+#pragma unroll
+    for (int q = 0; q < 28; ++q) x[q] = f[q];
+    float key[4];
+    uint32_t pk[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      pk[c] = __float_as_uint(x[24 + c]);
+      key[c] = pk[c] == 0u ? -INFINITY
+                           : (x[c] + x[4 + c]) * s.x + (x[8 + c] + x[12 + c]) * s.y + (x[16 + c] + x[20 + c]) * s.z;
+    }
+    int rank[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int r = 0;
+#pragma unroll
+      for (int d = 0; d < 4; ++d)
+        if (d != c && (key[d] > key[c] || (key[d] == key[c] && (pk[d] > pk[c] || (pk[d] == pk[c] && d < c))))) ++r;
+      rank[c] = r;
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) f[4 * q + rank[c]] = x[4 * q + c];
+  }
+}
+
+void launch_sun_order4(float4* nodes4, uint32_t n, float3 sun, int sms, cudaStream_t st) {
+  if (n == 0) return;
+  const uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)sms * 8);
+  k_sun_order4<<<grid, 256, 0, st>>>(nodes4, n, sun);
 }
 
 void launch_l2_probe(const float4* buf, size_t n4, int iters, float* sink, cudaStream_t st, int sms) {
