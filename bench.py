@@ -539,6 +539,7 @@ def main():
                 "hbm_peak_measured": 6777.0,
                 "algorithmic_bytes_per_ray": bytes_per_ray, "nodes_per_ray": ext_nodes,
                 "tris_per_ray": ext_tris, "sun_child_slots_per_ray": sun_slots, "sun_tris_per_ray": sun_tris,
+                "sun_rays_per_step": cs["shadow_rays"] * wl.spp,
                 "launch_ms": launch_ms, "rays_per_launch": rays_per_launch,
                 "stage_ms_per_step": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
                                               [m / args.steps for m in stage_ms])),
