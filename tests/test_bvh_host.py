@@ -1,7 +1,8 @@
 """Host BVH builders (binned SAH, and SAH with spatial splits) checked on the
 CPU by a small C++ program built from the library's builder source: every
 triangle is reachable through a leaf whose box covers it, thin glass is never
-split, boxes nest, and the four-wide collapse keeps every reference."""
+split, boxes nest, and the four-wide trees reach every node once, tile the
+leaf order with their leaves and cover every triangle."""
 import os
 import shutil
 import struct
