@@ -1624,6 +1624,7 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
   if ((uint64_t)N * pd > kPhotonMaxSlots) return fail(c, RT_ERR_ARG, "rt_render_photons: n_photons x photon_depth above 2^24");
   if (hb < 8 || hb > 20) return fail(c, RT_ERR_ARG, "rt_render_photons: log2_cells is 8..20");
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render_photons: unknown xyz_mode");
+  if (o.emission > 1) return fail(c, RT_ERR_ARG, "rt_render_photons: emission is 0 (disk) or 1 (portals)");
   if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
     return fail(c, RT_ERR_ARG, "rt_render_photons: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
   if (!(c->cos_max_d > std::cos(1.0)))
@@ -1688,7 +1689,6 @@ rt_status rt_render_photons(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, u
     }
     accum = c->d_accum;
   }
-  if (o.emission > 1) return fail(c, RT_ERR_ARG, "rt_render_photons: emission is 0 (disk) or 1 (portals)");
   PhotonPass pp{};
   photon_setup(c, N, seed, pp);
   DevTemp<float4> portal;

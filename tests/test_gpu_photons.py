@@ -122,6 +122,10 @@ def test_arguments_checked(R):
         R.render_photons(wl.cameras, 1, 4, 0, n_photons=1 << 23, photon_depth=4)
     with pytest.raises(RtError):
         R.render_photons(wl.cameras, 1, 4, 0, log2_cells=30)
+    with pytest.raises(RtError):
+        R.render_photons(wl.cameras, 1, 4, 0, emission=2)
+    with pytest.raises(RtError):
+        R.photon_records(64, 2, seed=0, emission=2)
     wide = scenes.plate_under_sky()  # half angle pi: no emission disk
     R.load(wide)
     with pytest.raises(RtError):
