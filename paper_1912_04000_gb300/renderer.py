@@ -18,6 +18,30 @@ def _ptr(t) -> Optional[int]:
     return None if t is None else t.data_ptr()
 
 
+def _need(ok: bool, what: str):
+    if not ok:
+        raise ValueError(what)
+
+
+def _check_device_out(t, n: int, dtype, device, what: str):
+    """A caller-supplied device output: the library writes n elements of
+    dtype through its pointer, so it must be a contiguous tensor of exactly
+    n elements of that dtype on the renderer's device."""
+    _need(hasattr(t, "data_ptr") and t.device == device and t.dtype == dtype and t.is_contiguous()
+          and t.numel() == n, f"{what}: expected a contiguous {dtype} tensor of {n} elements on {device}")
+
+
+def _check_host_out(a, n: int, np_dtype, what: str):
+    """A caller-supplied host output: a C-contiguous numpy array or a
+    contiguous CPU tensor of exactly n elements of the dtype."""
+    if hasattr(a, "data_ptr"):
+        ok = (a.device.type == "cpu" and a.is_contiguous() and a.numel() == n
+              and str(a.dtype) == "torch." + np.dtype(np_dtype).name)
+    else:
+        ok = isinstance(a, np.ndarray) and a.dtype == np_dtype and a.flags.c_contiguous and a.size == n
+    _need(ok, f"{what}: expected a contiguous host {np.dtype(np_dtype).name} buffer of {n} elements")
+
+
 class Renderer:
     def __init__(self, device: int = 0, stream=None):
         import torch
@@ -119,6 +143,10 @@ class Renderer:
             band_count = self.n_bands - band_first
         npix = sum(int(c.width) * int(c.height) for c in cameras)
         dev = self.device
+        if out_spectral is not None:
+            _check_device_out(out_spectral, npix * band_count, torch.float64, dev, "out_spectral")
+        if out_xyz is not None:
+            _check_device_out(out_xyz, npix * 3, torch.float32, dev, "out_xyz")
         sp = out_spectral if out_spectral is not None else (
             torch.empty((npix, band_count), dtype=torch.float64, device=dev) if spectral else None)
         xz = out_xyz if out_xyz is not None else (
@@ -174,6 +202,8 @@ class Renderer:
             band_count = self.n_bands - band_first
         npix = sum(int(c.width) * int(c.height) for c in cameras)
         dev = self.device
+        if out_spectral is not None:
+            _check_device_out(out_spectral, npix * band_count, torch.float64, dev, "out_spectral")
         sp = out_spectral if out_spectral is not None else torch.empty((npix, band_count), dtype=torch.float64,
                                                                       device=dev)
         xz = torch.empty((npix, 3), dtype=torch.float32, device=dev)
@@ -218,6 +248,10 @@ class Renderer:
         if band_count is None:
             band_count = self.n_bands - band_first
         npix = sum(int(c.width) * int(c.height) for c in cameras)
+        if xyz_out is not None:
+            _check_host_out(xyz_out, npix * 3, np.float32, "xyz_out")
+        if spectral_out is not None:
+            _check_host_out(spectral_out, npix * band_count, np.float64, "spectral_out")
         xz = xyz_out if xyz_out is not None else np.empty((npix, 3), np.float32)
         sp = spectral_out if spectral_out is not None else (
             np.empty((npix, band_count), np.float64) if spectral else None)
@@ -295,8 +329,12 @@ class Renderer:
         self.guide_log2_table = c.log2_table or 19
 
     def guide_set_params(self, grid=None, W=None):
-        g = None if grid is None else np.ascontiguousarray(grid, np.float32)
-        w = None if W is None else np.ascontiguousarray(W, np.float32)
+        g = None if grid is None else np.ascontiguousarray(grid, np.float32).ravel()
+        w = None if W is None else np.ascontiguousarray(W, np.float32).ravel()
+        if hasattr(self, "guide_log2_table"):  # before guide_init the library refuses the call
+            n_grid = 16 * (1 << self.guide_log2_table) * 2
+            _need(g is None or g.size == n_grid, f"grid: expected {n_grid} floats")
+        _need(w is None or w.size == _native.GUIDE_W_SIZE, f"W: expected {_native.GUIDE_W_SIZE} floats")
         st = self.lib.rt_guide_set_params(self._h, None if g is None else g.ctypes.data,
                                           None if w is None else w.ctypes.data)
         self._check("rt_guide_set_params", st)
@@ -308,8 +346,14 @@ class Renderer:
         return g, w
 
     def _records(self, rec):
+        """Guide records [n][12] float32 on the device."""
         torch = self.torch
-        return torch.as_tensor(np.ascontiguousarray(rec, np.float32), device=self.device).contiguous()
+        if hasattr(rec, "data_ptr"):
+            r = rec.to(self.device, torch.float32).contiguous()
+        else:
+            r = torch.as_tensor(np.ascontiguousarray(rec, np.float32), device=self.device).contiguous()
+        _need(r.dim() == 2 and r.shape[1] == 12, "guide records: expected an [n, 12] array")
+        return r
 
     def guide_eval(self, rec):
         torch = self.torch
@@ -331,7 +375,12 @@ class Renderer:
         return loss.value, dg, dw
 
     def guide_train_step(self, rec):
-        r = rec if hasattr(rec, "data_ptr") else self._records(rec)
+        if hasattr(rec, "data_ptr") and rec.device == self.device:
+            r = rec
+            _need(r.dtype == self.torch.float32 and r.is_contiguous() and r.dim() == 2 and r.shape[1] == 12,
+                  "guide records: expected a contiguous float32 [n, 12] tensor")
+        else:
+            r = self._records(rec)
         loss = C.c_float()
         self._check("rt_guide_train_step", self.lib.rt_guide_train_step(self._h, r.data_ptr(), r.shape[0],
                                                                          C.byref(loss)))
