@@ -204,7 +204,10 @@ rt_status rt_get_scene_info(rt_ctx* ctx, rt_scene_info* info);
  * direction sun_dir (towards the sun); per material and band the index n, the
  * extinction k (Eq. 1), the Lambertian reflectance rho and the emitted
  * radiance le ([n_mat][n_bands] each; le may be NULL = 0); cmf_w[n_bands][3]
- * the band weights of the XYZ contraction.  n_mat must match the scene. */
+ * the band weights of the XYZ contraction.  n_mat must match the scene.
+ * Also stores the children of every four-wide BVH node far-to-near along
+ * sun_dir, the order in which sun rays visit them (results do not depend on
+ * it; the work per sun ray does).  Synchronous on the context's stream. */
 rt_status rt_set_spectra(rt_ctx* ctx, const float* lambda_nm, uint32_t n_bands, const float* sun_L,
                          const float sun_dir[3], float sun_half_angle, const float* n, const float* k,
                          const float* rho, const float* le, const float* cmf_w);
