@@ -2,7 +2,10 @@
 CPU by a small C++ program built from the library's builder source: every
 triangle is reachable through a leaf whose box covers it, thin glass is never
 split, boxes nest, and the four-wide trees reach every node once, tile the
-leaf order with their leaves and cover every triangle."""
+leaf order with their leaves and cover every triangle.  A second program
+counts traversal work per ray on the CPU with the GPU kernels' visit rules:
+storing each node's children far-to-near along the sun cuts the node visits
+of sun rays on the nave by about a third."""
 import os
 import shutil
 import struct
@@ -48,3 +51,42 @@ def test_builders(checker, tmp_path, name):
     assert lines[0].startswith("sah ok") and lines[1].startswith("sbvh ok")
     refs = int(lines[1].split("refs=")[1].split()[0])
     assert sc.n_tris <= refs <= 2 * sc.n_tris
+
+
+@pytest.fixture(scope="module")
+def counter(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("trav") / "traversal_count")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, os.path.join(HERE, "native", "traversal_count.cpp"),
+                    os.path.join(CSRC, "rt_bvh.cpp"), "-o", out, "-lpthread"], check=True)
+    return out
+
+
+@pytest.mark.parametrize("name", ["nave", "crystal_nave"])
+def test_sun_ray_child_order(counter, tmp_path, name):
+    wl = {"nave": lambda: scenes.nave(width=96, height=72),
+          "crystal_nave": lambda: scenes.crystal_nave(width=96, height=72)}[name]()
+    sc, cam, sp = wl.scene, wl.cameras[0], wl.spectra
+    glass = (sc.mat_type[sc.mat_id] == scenes.THIN_GLASS).astype(np.uint8)
+    path = str(tmp_path / "scene.bin")
+    with open(path, "wb") as f:
+        f.write(struct.pack("II", sc.verts.shape[0], sc.tris.shape[0]))
+        f.write(np.ascontiguousarray(sc.verts, np.float32).tobytes())
+        f.write(np.ascontiguousarray(sc.tris, np.uint32).tobytes())
+        f.write(glass.tobytes())
+        f.write(np.array(list(cam.pos) + list(cam.look) + list(cam.up) + [cam.vfov_deg], np.float32).tobytes())
+        f.write(struct.pack("II", cam.width, cam.height))
+        f.write(np.array(list(sp.sun_dir) + [sp.sun_half_angle], np.float32).tobytes())
+    r = subprocess.run([counter, path], capture_output=True, text=True, timeout=600)
+    print(r.stdout)
+    assert r.returncode == 0, r.stdout + r.stderr
+    got = {ln.split()[0]: [float(x) for x in ln.split()[1:]] for ln in r.stdout.strip().split("\n")}
+    # the counts follow the GPU's counters on the full-size nave (10.2 nodes
+    # and 2.26 triangles per closest-hit ray)
+    assert 8.0 < got["closest"][0] < 13.0 and 1.5 < got["closest"][1] < 3.0
+    build, far = got["sun_build_order"], got["sun_far_first"]
+    assert build[2] == far[2] > 1000           # the same sun rays in both orders
+    assert far[0] < 0.75 * build[0]            # node visits per sun ray
+    assert far[1] <= build[1]                  # triangle tests per sun ray
