@@ -13,8 +13,12 @@
 //     traversal visited them before the children were ordered) and children
 //     stored far-to-near along the sun (box centre . sun, largest first,
 //     empty slots last), visited in slot order.
-// Prints "closest <nodes/ray> <tris/ray>", "sun_build_order <nodes/ray>
-// <tris/ray>" and "sun_far_first <nodes/ray> <tris/ray>".
+// It also counts closest-hit rays over an eight-wide tree collapsed the same
+// greedy way from the same binary tree, with exact child boxes and with
+// child boxes quantised to 8 bits on a per-node power-of-two grid (rounded
+// outward), the layout a wider, compressed node would use.
+// Prints "closest <nodes/ray> <tris/ray> <rays>", "sun_build_order ...",
+// "sun_far_first ...", "closest_w8 ..." and "closest_w8q ...".
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -220,6 +224,143 @@ std::vector<Bvh4Node> far_first(std::vector<Bvh4Node> B, const V3& s) {
   return B;
 }
 
+// W-wide tree by the greedy collapse (open the interior child of largest
+// area until W children); child boxes exact or quantised
+struct WideNode {
+  std::vector<std::array<double, 6>> box;  // lo xyz, hi xyz per child
+  std::vector<int> child;                  // wide node index, or -1 for a leaf
+  std::vector<uint32_t> first, count;      // leaf runs of the leaf order
+};
+
+std::vector<WideNode> collapse_wide(const BvhOut& b2, int W, bool quantise) {
+  const std::vector<BvhNode>& nb = b2.nodes;
+  auto area = [&](uint32_t i) {
+    const BvhNode& b = nb[i];
+    const double dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  };
+  std::vector<WideNode> out(1);
+  std::vector<std::pair<uint32_t, int>> todo{{1u, 0}};
+  while (!todo.empty()) {
+    const auto [b, slot] = todo.back();
+    todo.pop_back();
+    std::vector<uint32_t> ch;
+    if (nb[b].count != 0) {
+      ch.push_back(b);
+    } else {
+      ch = {nb[b].ref, nb[b].ref + 1};
+      while ((int)ch.size() < W) {
+        int best = -1;
+        double ba = -1.0;
+        for (int i = 0; i < (int)ch.size(); ++i)
+          if (nb[ch[i]].count == 0 && area(ch[i]) > ba) {
+            ba = area(ch[i]);
+            best = i;
+          }
+        if (best < 0) break;
+        const uint32_t r = nb[ch[best]].ref;
+        ch[best] = r;
+        ch.push_back(r + 1);
+      }
+    }
+    WideNode w;
+    double L[3] = {INFINITY, INFINITY, INFINITY}, Hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (const uint32_t c : ch)
+      for (int a = 0; a < 3; ++a) {
+        L[a] = std::min(L[a], (double)nb[c].lo[a]);
+        Hi[a] = std::max(Hi[a], (double)nb[c].hi[a]);
+      }
+    double scale[3];
+    for (int a = 0; a < 3; ++a) scale[a] = std::ldexp(1.0, (int)std::ceil(std::log2(std::max(Hi[a] - L[a], 1e-30) / 255.0)));
+    for (const uint32_t c : ch) {
+      std::array<double, 6> bx;
+      for (int a = 0; a < 3; ++a) {
+        bx[a] = nb[c].lo[a];
+        bx[3 + a] = nb[c].hi[a];
+        if (quantise) {
+          const double ql = std::min(255.0, std::max(0.0, std::floor((bx[a] - L[a]) / scale[a])));
+          const double qh = std::min(255.0, std::max(0.0, std::ceil((bx[3 + a] - L[a]) / scale[a])));
+          bx[a] = L[a] + ql * scale[a];
+          bx[3 + a] = L[a] + qh * scale[a];
+        }
+      }
+      w.box.push_back(bx);
+      if (nb[c].count != 0) {
+        w.child.push_back(-1);
+        w.first.push_back(nb[c].ref);
+        w.count.push_back(nb[c].count);
+      } else {
+        w.child.push_back((int)out.size());
+        w.first.push_back(0);
+        w.count.push_back(0);
+        todo.push_back({c, (int)out.size()});
+        out.emplace_back();
+      }
+    }
+    out[slot] = std::move(w);
+  }
+  return out;
+}
+
+double closest_wide(const std::vector<WideNode>& T, const std::vector<uint32_t>& order, const Scene& S, const V3& o,
+                    const V3& d, Count& C) {
+  const V3 inv = inverse(d);
+  struct E {
+    int node;
+    uint32_t first, count;
+    double t;
+  };
+  std::vector<E> st;
+  double best = INFINITY;
+  uint32_t hid = 0xFFFFFFFFu;
+  E cur{0, 0, 0, 0.0};
+  C.rays += 1;
+  for (;;) {
+    if (cur.node >= 0) {
+      const WideNode& n = T[cur.node];
+      C.nodes += 1;
+      std::vector<E> e;
+      for (size_t i = 0; i < n.box.size(); ++i) {
+        double tn = 0, tf = best;
+        for (int a = 0; a < 3; ++a) {
+          double t0 = (n.box[i][a] - o[a]) * inv[a], t1 = (n.box[i][3 + a] - o[a]) * inv[a];
+          if (t0 > t1) std::swap(t0, t1);
+          tn = std::max(tn, t0);
+          tf = std::min(tf, t1);
+        }
+        if (tn <= tf) e.push_back({n.child[i], n.first[i], n.count[i], tn});
+      }
+      std::stable_sort(e.begin(), e.end(), [](const E& a, const E& b) { return a.t < b.t; });
+      if (!e.empty()) {
+        for (size_t i = e.size() - 1; i >= 1; --i) st.push_back(e[i]);
+        cur = e[0];
+        continue;
+      }
+    } else {
+      for (uint32_t k = cur.first; k < cur.first + cur.count; ++k) {
+        C.tris += 1;
+        const uint32_t id = order[k];
+        const double t = hit_t(S, id, o, d);
+        if (t > 1e-9 && (t < best || (t == best && id < hid))) {
+          best = t;
+          hid = id;
+        }
+      }
+    }
+    bool next = false;
+    while (!st.empty()) {
+      const E e = st.back();
+      st.pop_back();
+      if (e.t <= best) {
+        cur = e;
+        next = true;
+        break;
+      }
+    }
+    if (!next) return best;
+  }
+}
+
 // orthonormal vectors t1, t2 with n
 void basis(const V3& n, V3& t1, V3& t2) {
   const double sg = std::copysign(1.0, n[2]);
@@ -255,6 +396,7 @@ int main(int argc, char** argv) {
   const V3 sun = unit({sunf[0], sunf[1], sunf[2]});
   const double cos_max = std::cos((double)sunf[3]);
   const std::vector<Bvh4Node> Bf = far_first(B, sun);
+  const std::vector<WideNode> W8 = collapse_wide(b2, 8, false), W8q = collapse_wide(b2, 8, true);
 
   // camera (pinhole, vertical field of view, y down)
   const V3 pos = {cam[0], cam[1], cam[2]};
@@ -273,7 +415,7 @@ int main(int argc, char** argv) {
   basis(sun, s1, s2);
   std::mt19937_64 rng(3);
   std::uniform_real_distribution<double> U(0, 1);
-  Count ext, sun_build, sun_far;
+  Count ext, sun_build, sun_far, ext8, ext8q;
   for (uint32_t y = 0; y < H; ++y)
     for (uint32_t x = 0; x < W; ++x) {
       const double px = (2.0 * (x + U(rng)) / W - 1.0) * th * asp, py = (1.0 - 2.0 * (y + U(rng)) / H) * th;
@@ -282,6 +424,11 @@ int main(int argc, char** argv) {
       for (int vtx = 0; vtx < 4; ++vtx) {
         uint32_t id;
         const double t = closest(B, b2.order, S, o, d, id, ext);
+        const double t8 = closest_wide(W8, b2.order, S, o, d, ext8), t8q = closest_wide(W8q, b2.order, S, o, d, ext8q);
+        if (!(t8 == t && t8q == t)) {
+          printf("wide trees disagree with the four-wide tree: %.17g %.17g %.17g\n", t, t8, t8q);
+          return 1;
+        }
         if (!(t < INFINITY)) break;
         V3 n = normal(S, id);
         if (dot(n, d) > 0) n = {-n[0], -n[1], -n[2]};
@@ -312,5 +459,7 @@ int main(int argc, char** argv) {
   printf("sun_build_order %.4f %.4f %.0f\n", sun_build.nodes / sun_build.rays, sun_build.tris / sun_build.rays,
          sun_build.rays);
   printf("sun_far_first %.4f %.4f %.0f\n", sun_far.nodes / sun_far.rays, sun_far.tris / sun_far.rays, sun_far.rays);
+  printf("closest_w8 %.4f %.4f %.0f\n", ext8.nodes / ext8.rays, ext8.tris / ext8.rays, ext8.rays);
+  printf("closest_w8q %.4f %.4f %.0f\n", ext8q.nodes / ext8q.rays, ext8q.tris / ext8q.rays, ext8q.rays);
   return 0;
 }
