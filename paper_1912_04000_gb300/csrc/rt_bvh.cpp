@@ -275,7 +275,8 @@ double overlap_area(const Box& a, const Box& b) {
 
 }  // namespace
 
-int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint8_t* splittable, BvhOut& out) {
+int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint8_t* splittable, BvhOut& out,
+               unsigned threads) {
   std::vector<double> vd(9 * (size_t)nt);
   std::vector<Ref> root(nt);
   Box world;
@@ -543,7 +544,8 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
       }
     }
   };
-  const unsigned nth = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
+  const unsigned nth =
+      threads ? threads : std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 64u));
   std::vector<std::thread> th;
   for (unsigned q = 0; q + 1 < nth && q + 1 < jobs.size(); ++q) th.emplace_back(worker);
   worker();

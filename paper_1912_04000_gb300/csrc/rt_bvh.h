@@ -24,8 +24,10 @@ struct BvhOut {
 int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out);
 
 // Builds a spatial-split BVH: order may list a triangle in several leaves
-// (at most 2 nt references), never one whose splittable[t] is 0.  Returns 0.
-int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint8_t* splittable, BvhOut& out);
+// (at most 2 nt references), never one whose splittable[t] is 0.  threads:
+// host threads to use (0 = all); the tree does not depend on it.  Returns 0.
+int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint8_t* splittable, BvhOut& out,
+               unsigned threads = 0);
 
 // Four-wide node: child boxes in structure-of-arrays order (one float4 per
 // plane), child i an interior node (cnt[i] = 0, ref[i] = node index), a leaf

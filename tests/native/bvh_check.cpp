@@ -10,12 +10,14 @@
 //   - the four-wide collapse reaches every node once, its leaves (1..4
 //     references each) tile the leaf order exactly, child boxes nest, and
 //     every sampled point of a triangle lies in the box of a wide leaf that
-//     references it.
+//     references it;
+//   - the spatial-split build on one thread gives the same tree bit for bit.
 // Prints one line per tree: "<name> ok refs=<n> nodes4=<m>" or the failure.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <array>
 #include <random>
 #include <vector>
@@ -231,5 +233,12 @@ int main(int argc, char** argv) {
   build_sbvh(v.data(), t.data(), nt, split.data(), b);
   int rc = check("sah", a, v, t, split, nt);
   rc |= check("sbvh", b, v, t, split, nt);
+  // the spatial-split build on one thread: the same tree bit for bit
+  BvhOut b1;
+  build_sbvh(v.data(), t.data(), nt, split.data(), b1, 1);
+  const bool same = b1.order == b.order && b1.nodes.size() == b.nodes.size() &&
+                    std::memcmp(b1.nodes.data(), b.nodes.data(), b.nodes.size() * sizeof(BvhNode)) == 0;
+  printf(same ? "sbvh one thread: same tree\n" : "sbvh one thread: a different tree\n");
+  rc |= same ? 0 : 1;
   return rc;
 }

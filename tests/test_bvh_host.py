@@ -50,6 +50,7 @@ def test_builders(checker, tmp_path, name):
     assert r.returncode == 0, r.stdout + r.stderr
     lines = r.stdout.split("\n")
     assert lines[0].startswith("sah ok") and lines[1].startswith("sbvh ok")
+    assert lines[2] == "sbvh one thread: same tree"
     refs = int(lines[1].split("refs=")[1].split()[0])
     assert sc.n_tris <= refs <= 2 * sc.n_tris
 
