@@ -9,7 +9,11 @@ CUDA library.  ``build()`` compiles ``oracle.cpp`` with the host compiler into
 Every function here is pinned by the ``-m "not gpu"`` tests against closed
 forms, invariants and brute force (Philox known-answer vectors, normal-incidence
 Fresnel, Brewster angle, lossless-plate 2R/(1+R), Beer-Lambert, the white
-furnace, the uniform sky, the sun-cone irradiance, brute-force intersection).
+furnace, the uniform sky, the sun-cone irradiance, the form factor of a square
+emitter, the pinhole projection, the CIE 1931 spectral locus, brute-force
+intersection; for the guided estimator: chi-square of the proposal draws
+against the density it reports, the furnace and sun-cone means, exact
+incident radiance in the training records).
 """
 from __future__ import annotations
 
@@ -29,9 +33,10 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle (plain C++17, strict IEEE double, no fast-math)."""
     srcs = [os.path.join(_HERE, "oracle.cpp"), os.path.join(_HERE, "guide_oracle.cpp")]
+    deps = srcs + [os.path.join(_HERE, "guide_net.h")]
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(s) for s in srcs)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(s) for s in deps)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
@@ -116,6 +121,17 @@ def lib():
             L.or_guide_loss_grad.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_uint64, fp, fp,
                                              up, fp, fp, C.c_int, dp, dp]
             L.or_guide_density.argtypes = [dp, C.c_uint64, dp, dp]
+            L.or_guide_net_create.restype = C.c_void_p
+            L.or_guide_net_create.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_int]
+            L.or_guide_net_destroy.argtypes = [C.c_void_p]
+            L.or_render_guided.restype = C.c_int
+            L.or_render_guided.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_uint32, C.POINTER(_Camera),
+                                           C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint64,
+                                           up, C.c_uint64, dp, dp, up, fp, C.c_int]
+            L.or_guide_step.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_uint32, C.c_uint32, C.c_uint64,
+                                        C.c_uint64, up, up, fp, fp, up, fp, dp]
+            L.or_guide_mis_draws.argtypes = [dp, dp, C.c_double, C.c_uint64, dp, dp, dp]
+            L.or_camera_rays.argtypes = [C.POINTER(_Camera), C.c_uint32, C.c_uint64, C.c_uint64, up, up, up, dp, dp]
             _lib = L
     return _lib
 
@@ -154,6 +170,20 @@ def slab(cos_i, n, k, lambda_nm, d):
     rs, ts = C.c_double(), C.c_double()
     lib().or_slab(cos_i, n, k, lambda_nm, d, C.byref(rs), C.byref(ts))
     return rs.value, ts.value
+
+
+def camera_rays(cameras, pixels, sample=0, band=0, seed=0):
+    """Primary rays (origins, unit directions [n, 3]) of the listed global
+    pixels for the given sample and band (their Philox jitter)."""
+    pix = np.ascontiguousarray(pixels, np.uint32)
+    n = pix.shape[0]
+    s = np.ascontiguousarray(np.broadcast_to(np.asarray(sample, np.uint32), (n,)))
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(band, np.uint32), (n,)))
+    o = np.zeros((n, 3))
+    d = np.zeros((n, 3))
+    lib().or_camera_rays(cameras_struct(cameras), len(cameras), seed, n, _ptr(pix, C.c_uint32), _ptr(s, C.c_uint32),
+                         _ptr(b, C.c_uint32), _ptr(o, C.c_double), _ptr(d, C.c_double))
+    return o, d
 
 
 def hardware_threads() -> int:
@@ -389,3 +419,89 @@ def guide_density(Y, omega):
 
 
 OracleScene.photon_records, OracleScene.render_photons = _photon_methods()
+
+
+class OracleGuide:
+    """The guide network in FP64 for the guided estimator (BF16 network when
+    bf16_act: layer inputs rounded to BF16 before each product)."""
+
+    def __init__(self, log2_T, lo, hi, grid, W, n_min=16.0, n_max=2048.0, bf16_act=True):
+        lo, hi, grid, W = map(_f32, (lo, hi, grid, W))
+        if grid.size != GUIDE_LEVELS * (1 << log2_T) * 2 or W.size != GUIDE_W_SIZE:
+            raise ValueError("guide parameter sizes")
+        fp = lambda a: _ptr(a, C.c_float)
+        self._h = lib().or_guide_net_create(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W),
+                                            1 if bf16_act else 0)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_guide_net_destroy(h)
+            self._h = None
+
+
+STEP_FIELDS = ("omega_x", "omega_y", "omega_z", "q", "pdf", "cos", "guide", "lobe", "lobe_margin", "nee_w", "esc_w",
+               "cont", "q_sun", "pdf_sun")
+
+
+def _guided_methods():
+    def render_guided(self, guide, cameras, spp, depth, seed=0, alpha=0.7, guide_depth=2, band_first=0,
+                      band_count=None, pixels=None, record_paths=False, records=False, n_threads=0):
+        """Guided estimate of the listed pixels (layout as render); with
+        records, the training records [n_pix, spp, band_count, guide_depth, 2, 12]."""
+        if band_count is None:
+            band_count = self.n_bands - band_first
+        n_all = sum(c.width * c.height for c in cameras)
+        pix = np.arange(n_all, dtype=np.uint32) if pixels is None else np.ascontiguousarray(pixels, np.uint32)
+        npx = pix.shape[0]
+        ssum = np.zeros((npx, band_count), np.float64)
+        pl = np.zeros((npx, spp, band_count), np.float64) if record_paths else None
+        ps = np.zeros((npx, spp, band_count), np.uint32) if record_paths else None
+        rec = np.zeros((npx, spp, band_count, guide_depth, 2, 12), np.float32) if records else None
+        rc = lib().or_render_guided(self._h, guide._h, alpha, guide_depth, cameras_struct(cameras), len(cameras),
+                                    band_first, band_count, spp, depth, seed, _ptr(pix, C.c_uint32), npx,
+                                    _ptr(ssum, C.c_double), _ptr(pl, C.c_double) if pl is not None else None,
+                                    _ptr(ps, C.c_uint32) if ps is not None else None,
+                                    _ptr(rec, C.c_float) if rec is not None else None, n_threads)
+        if rc != 0:
+            raise ValueError(f"or_render_guided failed ({rc})")
+        out = {"spectral_sum": ssum, "xyz": xyz(ssum, band_first, spp, self.cmf_w)}
+        if record_paths:
+            out["path_L"] = pl
+            out["path_sig"] = ps
+        if records:
+            out["records"] = rec
+        return out
+
+    def guide_step(self, guide, k, sample, seed, pixel, band, po, nrm, has_sun, wn, alpha=0.7):
+        """One guided vertex per query (see or_guide_step): dict of arrays
+        named by STEP_FIELDS."""
+        pixel = np.ascontiguousarray(pixel, np.uint32)
+        n = pixel.shape[0]
+        band = np.ascontiguousarray(band, np.uint32)
+        hs = np.ascontiguousarray(has_sun, np.uint32)
+        po, nrm, wn = (np.ascontiguousarray(a, np.float32) for a in (po, nrm, wn))
+        out = np.zeros((n, 16))
+        lib().or_guide_step(self._h, guide._h, alpha, k, sample, seed, n, _ptr(pixel, C.c_uint32),
+                            _ptr(band, C.c_uint32), _ptr(po, C.c_float), _ptr(nrm, C.c_float), _ptr(hs, C.c_uint32),
+                            _ptr(wn, C.c_float), _ptr(out, C.c_double))
+        return {f: out[:, i] for i, f in enumerate(STEP_FIELDS)} | {"omega": out[:, 0:3]}
+
+    return render_guided, guide_step
+
+
+OracleScene.render_guided, OracleScene.guide_step = _guided_methods()
+
+
+def guide_mis_draws(Y, normal, alpha, u):
+    """One-sample MIS draws for fixed head outputs Y [48] and normal from
+    uniforms u [n, 6]: (omega [n, 3], p_mix(omega) [n])."""
+    Y = np.ascontiguousarray(Y, np.float64)
+    nn = np.ascontiguousarray(normal, np.float64)
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, 6)
+    n = u.shape[0]
+    om = np.zeros((n, 3))
+    pdf = np.zeros(n)
+    dp = lambda a: _ptr(a, C.c_double)
+    lib().or_guide_mis_draws(dp(Y), dp(nn), alpha, n, dp(u), dp(om), dp(pdf))
+    return om, pdf

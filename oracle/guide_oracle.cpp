@@ -31,6 +31,8 @@
 #include <cstring>
 #include <vector>
 
+#include "guide_net.h"
+
 namespace {
 
 constexpr int kLevels = 16, kFeat = 2, kIn = 64, kHid = 64, kOut = 48, kLobes = 8, kGroups = 9;
@@ -353,3 +355,65 @@ void or_guide_density(const double* Y, uint64_t n, const double* omega, double* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// the network as an object, for the guided path tracer of oracle.cpp
+// ---------------------------------------------------------------------------
+namespace oguide {
+
+struct Net {
+  GCfg g;
+  std::vector<float> grid, W;
+  int bf16_act;
+};
+
+Net* net_create(uint32_t log2_T, const float* lo, const float* hi, float n_min, float n_max, const float* grid,
+                const float* W, int bf16_act) {
+  Net* net = new Net();
+  net->g = make_cfg(log2_T, lo, hi, n_min, n_max);
+  net->grid.assign(grid, grid + (size_t)kLevels * (1u << log2_T) * kFeat);
+  net->W.assign(W, W + (kIn * kHid + 2 * kHid * kHid + kHid * kOut));
+  net->bf16_act = bf16_act;
+  return net;
+}
+
+void net_destroy(Net* net) { delete net; }
+
+void net_outputs(const Net* net, const double p[3], const double n[3], uint32_t group, double Y[48]) {
+  const float* W1 = net->W.data();
+  const float* W2 = W1 + kIn * kHid;
+  const float* W3 = W2 + kHid * kHid;
+  const float* W4 = W3 + kHid * kHid;
+  double X[kIn], H1[kHid], H2[kHid], H3[kHid];
+  Enc e;
+  encode(net->g, net->grid.data(), p, n, group, X, &e);
+  maybe_round(X, kIn, net->bf16_act);
+  matvec(X, W1, kIn, kHid, H1);
+  for (double& v : H1) v = v > 0.0 ? v : 0.0;
+  maybe_round(H1, kHid, net->bf16_act);
+  matvec(H1, W2, kHid, kHid, H2);
+  for (double& v : H2) v = v > 0.0 ? v : 0.0;
+  maybe_round(H2, kHid, net->bf16_act);
+  matvec(H2, W3, kHid, kHid, H3);
+  for (double& v : H3) v = v > 0.0 ? v : 0.0;
+  maybe_round(H3, kHid, net->bf16_act);
+  matvec(H3, W4, kHid, kOut, Y);
+}
+
+void mixture_of(const double Y[48], Mixture* m) {
+  Head h;
+  head(Y, &h);
+  for (int j = 0; j < kLobes; ++j) {
+    m->pi[j] = h.pi[j];
+    m->kappa[j] = h.kappa[j];
+    for (int d = 0; d < 3; ++d) m->mu[j][d] = h.mu[j][d];
+  }
+}
+
+double mixture_density(const Mixture& m, const double w[3]) {
+  double s = 0.0;
+  for (int j = 0; j < kLobes; ++j) s += m.pi[j] * vmf(m.kappa[j], m.mu[j], w);
+  return s;
+}
+
+}  // namespace oguide

@@ -43,6 +43,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include "guide_net.h"
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -445,6 +447,314 @@ void camera_ray(const std::vector<OCam>& oc, uint32_t pix, uint32_t s, uint32_t 
   *o = C.pos;
 }
 
+// Cosine-weighted direction about the unit normal n from uniforms u, v
+// (Malley's method: a uniform point of the unit disk, sin theta = sqrt(u),
+// lifted to the hemisphere): pdf cos(theta) / pi.
+V3 cosine_dir(V3 n, double u, double v) {
+  const double rr = std::sqrt(u);
+  const double ph = 2.0 * M_PI * v;
+  const double z = std::sqrt(std::max(0.0, 1.0 - u));
+  V3 b1, b2;
+  onb(n, &b1, &b2);
+  return (rr * std::cos(ph)) * b1 + (rr * std::sin(ph)) * b2 + z * n;
+}
+
+// ---------------------------------------------------------------------------
+// learned guide inside the estimator: one-sample MIS (section 4, Eq. 2)
+// ---------------------------------------------------------------------------
+// At a guided Lambertian vertex the continuation is drawn from the guide's
+// von Mises-Fisher mixture q with probability alpha, else by cosine
+// sampling; either way it is weighted by the one-sample MIS density
+//   p_mix(w) = alpha q(w) + (1 - alpha) max(cos, 0) / pi,
+// so the throughput becomes T (rho / pi) cos / p_mix and the expectation of
+// Eq. 2 does not depend on q.  The direct sun there is estimated by two
+// strategies combined with the balance heuristic: the sun-cone sample
+// (density p_cone = 1 / (2 pi (1 - cos a))) weighted
+// p_cone / (p_cone + p_mix(w_sun)), and the continuation escaping into the
+// cone weighted p_mix / (p_mix + p_cone).
+struct GuideCtx {
+  const oguide::Net* net = nullptr;
+  double alpha = 0.7;
+  uint32_t depth = 0;    // vertices 1..depth are guided
+  uint32_t n_bands = 1;  // band group of band b: b * 9 / n_bands
+};
+
+// vMF direction around the unit mu with concentration kappa from uniforms
+// u, v (Jakob, "Numerically stable sampling of the von Mises-Fisher
+// distribution on S^2", 2012): cos = 1 + log(u + (1 - u) e^{-2 kappa}) /
+// kappa about mu, azimuth 2 pi v in the basis onb(mu).
+V3 vmf_dir(const double mu[3], double kappa, double u, double v) {
+  const double w = 1.0 + std::log(u + (1.0 - u) * std::exp(-2.0 * kappa)) / kappa;
+  const double r = std::sqrt(std::max(0.0, 1.0 - w * w));
+  const double ph = 2.0 * M_PI * v;
+  const V3 m{mu[0], mu[1], mu[2]};
+  V3 t1, t2;
+  onb(m, &t1, &t2);
+  return (r * std::cos(ph)) * t1 + (r * std::sin(ph)) * t2 + w * m;
+}
+
+// A draw of the one-sample MIS proposal: guide with probability alpha
+// (uniform ug), lobe j with probability pi_j (the first j whose cumulative
+// weight exceeds ul; the last lobe if rounding leaves none), direction by
+// vmf_dir(uv0, uv1); else cosine sampling (uc0, uc1).
+struct MisDraw {
+  V3 omega{0, 0, 1};
+  bool guide = false;
+  int lobe = -1;
+  double lobe_margin = 1.0;  // distance of ul from the nearest cumulative lobe boundary
+};
+
+MisDraw mis_draw(const oguide::Mixture& mx, V3 n, double alpha, double ug, double ul, double uv0, double uv1,
+                 double uc0, double uc1) {
+  MisDraw d;
+  d.guide = ug < alpha;
+  if (!d.guide) {
+    d.omega = cosine_dir(n, uc0, uc1);
+    return d;
+  }
+  double acc = 0.0;
+  d.lobe = oguide::kLobes - 1;
+  bool found = false;
+  for (int j = 0; j < oguide::kLobes; ++j) {
+    acc += mx.pi[j];
+    if (j + 1 < oguide::kLobes) d.lobe_margin = std::min(d.lobe_margin, std::fabs(ul - acc));
+    if (!found && ul < acc) {
+      d.lobe = j;
+      found = true;
+    }
+  }
+  d.omega = vmf_dir(mx.mu[d.lobe], mx.kappa[d.lobe], uv0, uv1);
+  return d;
+}
+
+double mis_pdf(const oguide::Mixture& mx, V3 n, double alpha, V3 w, double* q_out) {
+  const double ww[3] = {w.x, w.y, w.z};
+  const double q = oguide::mixture_density(mx, ww);
+  if (q_out) *q_out = q;
+  return alpha * q + (1.0 - alpha) * std::max(dot(n, w), 0.0) / M_PI;
+}
+
+// Everything one guided vertex decides, given its query (offset position po,
+// normal n, band group), its Philox draws r0 (counter call 0: the sun
+// sample and the cosine continuation) and r1 (call 1: the MIS choice, lobe
+// and vMF direction) and its pending sun sample (direction wn, if any).
+struct GuidedVertex {
+  MisDraw draw;
+  double q = 0.0, pdf = 0.0, c = 0.0;   // guide density, MIS density and cosine at omega
+  double q_sun = 0.0, pdf_sun = 0.0;    // the same at the sun-sample direction
+  double nee_w = 1.0;                   // balance weight of the sun sample
+  double esc_w = 0.0;                   // balance weight of a sun escape of the continuation
+  bool cont = false;                    // the path continues (cos > 0 and p_mix > 0)
+};
+
+GuidedVertex guided_vertex(const GuideCtx& g, const OScene& S, V3 po, V3 n, uint32_t group, const Ctr4& r0,
+                           const Ctr4& r1, bool has_sun, V3 wn) {
+  GuidedVertex gv;
+  double Y[48];
+  const double pp[3] = {po.x, po.y, po.z}, nn[3] = {n.x, n.y, n.z};
+  oguide::net_outputs(g.net, pp, nn, group, Y);
+  oguide::Mixture mx;
+  oguide::mixture_of(Y, &mx);
+  gv.draw = mis_draw(mx, n, g.alpha, u01(r1.w[0]), u01(r1.w[1]), u01(r1.w[2]), u01(r1.w[3]), u01(r0.w[2]),
+                     u01(r0.w[3]));
+  const double p_cone = 1.0 / (2.0 * M_PI * (1.0 - S.cos_max));
+  gv.c = dot(n, gv.draw.omega);
+  gv.pdf = mis_pdf(mx, n, g.alpha, gv.draw.omega, &gv.q);
+  if (has_sun) {
+    gv.pdf_sun = mis_pdf(mx, n, g.alpha, wn, &gv.q_sun);
+    gv.nee_w = p_cone / (p_cone + gv.pdf_sun);
+  }
+  gv.cont = gv.c > 0.0 && gv.pdf > 0.0;
+  if (gv.cont && dot(gv.draw.omega, S.sun) >= S.cos_max) gv.esc_w = gv.pdf / (gv.pdf + p_cone);
+  return gv;
+}
+
+// Training records of one guided vertex (the guide learns from the samples
+// the tracer draws): the continuation, weight L_in cos / p_mix with L_in the
+// radiance the path gathered after the vertex divided by its throughput
+// there, and the sun sample, weight L_sun T_r cos / p_cone.  Each record is
+// 12 floats {position, weight}, {normal, band group}, {direction, 0}; a
+// record of weight <= 0 is {0, 0, 0, 0}, {0, 0, 1, 0}, {0, 0, 1, 0}.
+struct GuidedSlot {
+  bool valid = false;
+  V3 po{0, 0, 0}, n{0, 0, 1}, omega{0, 0, 1}, wn{0, 0, 1};
+  double group = 0.0, pdf = 0.0, c = 0.0, Tn = 0.0, L_before = 0.0;
+  bool sun = false;
+  double sun_rad = 0.0, cn = 0.0;
+};
+
+void put_record(float* o, V3 p, double wt, V3 n, double group, V3 w) {
+  if (wt > 0.0) {
+    const float v[12] = {(float)p.x, (float)p.y, (float)p.z, (float)wt, (float)n.x, (float)n.y, (float)n.z,
+                         (float)group, (float)w.x, (float)w.y, (float)w.z, 0.0f};
+    std::memcpy(o, v, sizeof(v));
+  } else {
+    const float v[12] = {0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 1, 0};
+    std::memcpy(o, v, sizeof(v));
+  }
+}
+
+void slot_records(const GuidedSlot& sl, double L_final, double p_cone, float* out24) {
+  double wt = 0.0, ws = 0.0;
+  if (sl.valid && sl.Tn > 0.0 && sl.pdf > 0.0) wt = std::max((L_final - sl.L_before) / sl.Tn, 0.0) * sl.c / sl.pdf;
+  if (sl.valid && sl.sun && sl.cn > 0.0) ws = std::max(sl.sun_rad, 0.0) * sl.cn / p_cone;
+  put_record(out24, sl.po, wt, sl.n, sl.group, sl.omega);
+  put_record(out24 + 12, sl.po, ws, sl.n, sl.group, sl.wn);
+}
+
+// One path (pixel pix, sample s, band b) of the estimator.  Plain when g is
+// null; guided at Lambertian vertices 1..g->depth (below the last vertex)
+// otherwise, with the training slots of those vertices in slots[0..depth).
+double trace_path(const OScene& S, const std::vector<OCam>& oc, uint32_t k0, uint32_t k1, uint32_t pix, uint32_t s,
+                  uint32_t b, uint32_t depth, const GuideCtx* g, uint32_t* sig_out, GuidedSlot* slots) {
+  // f / pdf for the sun cone: (rho / pi) * 2 pi (1 - cos_max) = rho * cone_w
+  const double cone_w = 2.0 * (1.0 - S.cos_max);
+  V3 o, d;
+  camera_ray(oc, pix, s, b, k0, k1, &o, &d);
+  double T = 1.0, L = 0.0;
+  bool covered = false;   // direct sun along this segment is already counted by NEE
+  bool guided_esc = false;  // ... by NEE with a balance weight: a sun escape adds esc_w of it
+  double esc_w = 0.0;
+  GuidedSlot* open = nullptr;  // training slot waiting for the radiance gathered before the next vertex
+  uint32_t sig = 2166136261u;
+  for (uint32_t k = 1; k <= depth; ++k) {
+    if (open) {
+      open->L_before = L;
+      open = nullptr;
+    }
+    double t;
+    uint32_t prim;
+    if (!closest(S, o, d, &t, &prim)) {
+      sig = mix(sig, 0xFFFFFFFFu);
+      if (dot(d, S.sun) >= S.cos_max) {
+        if (!covered) L += T * S.sunL[b];
+        else if (guided_esc) L += T * S.sunL[b] * esc_w;
+      }
+      break;
+    }
+    sig = mix(sig, prim);
+    V3 p = o + t * d;
+    V3 ng = normalize(cross(S.b[prim] - S.a[prim], S.c[prim] - S.a[prim]));
+    V3 n = dot(ng, d) < 0.0 ? ng : -1.0 * ng;
+    double cos_i = -dot(d, n);
+    uint32_t m = S.mat[prim];
+    size_t mb = (size_t)m * S.B + b;
+    int type = S.mtype[m];
+    Ctr4 r = philox4x32_10(Ctr4{{pix, s, b, 4u * k}}, k0, k1);
+    if (type == M_LAMBERT || type == M_EMISSIVE) {
+      if (type == M_EMISSIVE) L += T * S.le[mb];
+      // next-event estimate: direction uniform in the sun cone,
+      // pdf = 1 / (2 pi (1 - cos_max)); f = rho / pi
+      double ct = 1.0 - u01(r.w[0]) * (1.0 - S.cos_max);
+      double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+      double ph = 2.0 * M_PI * u01(r.w[1]);
+      V3 t1, t2;
+      onb(S.sun, &t1, &t2);
+      V3 w = (st * std::cos(ph)) * t1 + (st * std::sin(ph)) * t2 + ct * S.sun;
+      double c = dot(n, w);
+      double nee = 0.0, Tr = 0.0;
+      if (c > 0.0) {
+        uint32_t ngl;
+        Tr = shadow_T(S, p + S.eps * n, w, b, &ngl);
+        sig = mix(sig, ngl);
+        nee = T * S.rho[mb] * c * S.sunL[b] * cone_w * Tr;
+      }
+      const bool guided = g && k <= g->depth && k < depth;
+      if (!guided) {
+        L += nee;
+        if (k == depth) break;
+        // cosine-weighted continuation: f cos / pdf = rho
+        d = cosine_dir(n, u01(r.w[2]), u01(r.w[3]));
+        o = p + S.eps * n;
+        T *= S.rho[mb];
+        covered = true;
+        guided_esc = false;
+        continue;
+      }
+      const V3 po = p + S.eps * n;
+      const uint32_t group = b * 9u / g->n_bands;
+      Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+      const GuidedVertex gv = guided_vertex(*g, S, po, n, group, r, r1, c > 0.0, w);
+      L += nee * gv.nee_w;
+      double Tn = 0.0;
+      if (gv.cont) Tn = T * S.rho[mb] / M_PI * gv.c / gv.pdf;
+      if (slots) {
+        GuidedSlot& sl = slots[k - 1];
+        sl.valid = true;
+        sl.po = po;
+        sl.n = n;
+        sl.omega = gv.draw.omega;
+        sl.group = (double)group;
+        sl.pdf = gv.pdf;
+        sl.c = gv.c;
+        sl.Tn = Tn;
+        sl.sun = c > 0.0;
+        sl.wn = sl.sun ? w : V3{0, 0, 1};
+        sl.cn = sl.sun ? c : 0.0;
+        sl.sun_rad = sl.sun ? Tr * S.sunL[b] : 0.0;
+        open = &sl;
+      }
+      if (!gv.cont) break;  // no continuation: the path ends after its sun sample
+      d = gv.draw.omega;
+      o = po;
+      T = Tn;
+      covered = true;
+      guided_esc = true;
+      esc_w = gv.esc_w;
+    } else if (type == M_GLASS) {
+      double Rs, Ts;
+      slab(cos_i, S.ntab[mb], S.ktab[mb], S.lam[b], S.mthick[m], &Rs, &Ts);
+      if (k == depth) break;
+      Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+      if (u01(r1.w[0]) < Rs / (Rs + Ts)) {
+        d = d - (2.0 * dot(d, n)) * n;
+        o = p + S.eps * n;
+        covered = false;
+        guided_esc = false;
+      } else {
+        o = p - S.eps * n;
+      }
+      T *= Rs + Ts;
+    } else if (type == M_DIELECTRIC) {
+      // solid refracting glass (a closed mesh, normals outward, holding
+      // no other surface): light is attenuated by Beer-Lambert
+      // exp(-alpha s), alpha = 4 pi k / lambda, over every stretch s it
+      // travels inside -- the segment that ends here when it arrives from
+      // inside, and the short start step of a new ray that heads inside.
+      // The face reflects with the Fresnel reflectance of the relative
+      // index (n entering, 1/n leaving; total internal reflection gives
+      // 1), else refracts (Snell; dispersion through n(lambda)).  The next
+      // ray starts on the true ray, a step eps / max(|cos|, 1/16) along
+      // it, so the distance crossed inside is exact.
+      const bool inside = dot(ng, d) > 0.0;
+      const double alpha = 4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9);
+      if (inside) T *= std::exp(-alpha * t);
+      const double eta = inside ? 1.0 / S.ntab[mb] : S.ntab[mb];
+      const double R = fresnel_complex(cos_i, eta, 0.0);
+      if (k == depth) break;
+      Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
+      V3 tdir;
+      if (u01(r1.w[0]) < R || !refract(d, n, eta, &tdir)) d = d - (2.0 * dot(d, n)) * n;
+      else d = normalize(tdir);
+      const double step = S.eps / std::max(std::fabs(dot(d, n)), 0.0625);
+      if (dot(d, ng) < 0.0) T *= std::exp(-alpha * step);
+      o = p + step * d;
+      covered = false;
+      guided_esc = false;
+    } else {  // conductor
+      double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
+      if (k == depth) break;
+      d = d - (2.0 * dot(d, n)) * n;
+      o = p + S.eps * n;
+      T *= R;
+      covered = false;
+      guided_esc = false;
+    }
+  }
+  if (sig_out) *sig_out = sig;
+  return L;
+}
+
 }  // namespace
 
 extern "C" {
@@ -568,111 +878,6 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
   if (band_first + band_count > S.B || depth == 0) return 1;
   const std::vector<OCam> oc = setup_cams(cams, n_cams);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  // f / pdf for the sun cone: (rho / pi) * 2 pi (1 - cos_max) = rho * cone_w
-  const double cone_w = 2.0 * (1.0 - S.cos_max);
-
-  auto trace = [&](uint32_t pix, uint32_t s, uint32_t b, uint32_t* sig_out) -> double {
-    V3 o, d;
-    camera_ray(oc, pix, s, b, k0, k1, &o, &d);
-    double T = 1.0, L = 0.0;
-    bool covered = false;  // direct sun along this segment is already counted by NEE
-    uint32_t sig = 2166136261u;
-    for (uint32_t k = 1; k <= depth; ++k) {
-      double t;
-      uint32_t prim;
-      if (!closest(S, o, d, &t, &prim)) {
-        sig = mix(sig, 0xFFFFFFFFu);
-        if (!covered && dot(d, S.sun) >= S.cos_max) L += T * S.sunL[b];
-        break;
-      }
-      sig = mix(sig, prim);
-      V3 p = o + t * d;
-      V3 ng = normalize(cross(S.b[prim] - S.a[prim], S.c[prim] - S.a[prim]));
-      V3 n = dot(ng, d) < 0.0 ? ng : -1.0 * ng;
-      double cos_i = -dot(d, n);
-      uint32_t m = S.mat[prim];
-      size_t mb = (size_t)m * S.B + b;
-      int type = S.mtype[m];
-      Ctr4 r = philox4x32_10(Ctr4{{pix, s, b, 4u * k}}, k0, k1);
-      if (type == M_LAMBERT || type == M_EMISSIVE) {
-        if (type == M_EMISSIVE) L += T * S.le[mb];
-        // next-event estimate: direction uniform in the sun cone,
-        // pdf = 1 / (2 pi (1 - cos_max)); f = rho / pi
-        double ct = 1.0 - u01(r.w[0]) * (1.0 - S.cos_max);
-        double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
-        double ph = 2.0 * M_PI * u01(r.w[1]);
-        V3 t1, t2;
-        onb(S.sun, &t1, &t2);
-        V3 w = (st * std::cos(ph)) * t1 + (st * std::sin(ph)) * t2 + ct * S.sun;
-        double c = dot(n, w);
-        if (c > 0.0) {
-          uint32_t ngl;
-          double Tr = shadow_T(S, p + S.eps * n, w, b, &ngl);
-          sig = mix(sig, ngl);
-          L += T * S.rho[mb] * c * S.sunL[b] * cone_w * Tr;
-        }
-        if (k == depth) break;
-        // cosine-weighted continuation: f cos / pdf = rho
-        double rr = std::sqrt(u01(r.w[2]));
-        double ph2 = 2.0 * M_PI * u01(r.w[3]);
-        double z = std::sqrt(std::max(0.0, 1.0 - u01(r.w[2])));
-        V3 b1, b2;
-        onb(n, &b1, &b2);
-        d = (rr * std::cos(ph2)) * b1 + (rr * std::sin(ph2)) * b2 + z * n;
-        o = p + S.eps * n;
-        T *= S.rho[mb];
-        covered = true;
-      } else if (type == M_GLASS) {
-        double Rs, Ts;
-        slab(cos_i, S.ntab[mb], S.ktab[mb], S.lam[b], S.mthick[m], &Rs, &Ts);
-        if (k == depth) break;
-        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
-        if (u01(r1.w[0]) < Rs / (Rs + Ts)) {
-          d = d - (2.0 * dot(d, n)) * n;
-          o = p + S.eps * n;
-          covered = false;
-        } else {
-          o = p - S.eps * n;
-        }
-        T *= Rs + Ts;
-      } else if (type == M_DIELECTRIC) {
-        // solid refracting glass (a closed mesh, normals outward, holding
-        // no other surface): light is attenuated by Beer-Lambert
-        // exp(-alpha s), alpha = 4 pi k / lambda, over every stretch s it
-        // travels inside -- the segment that ends here when it arrives from
-        // inside, and the short start step of a new ray that heads inside.
-        // The face reflects with the Fresnel reflectance of the relative
-        // index (n entering, 1/n leaving; total internal reflection gives
-        // 1), else refracts (Snell; dispersion through n(lambda)).  The next
-        // ray starts on the true ray, a step eps / max(|cos|, 1/16) along
-        // it, so the distance crossed inside is exact.
-        const bool inside = dot(ng, d) > 0.0;
-        const double alpha = 4.0 * M_PI * S.ktab[mb] / (S.lam[b] * 1e-9);
-        if (inside) T *= std::exp(-alpha * t);
-        const double eta = inside ? 1.0 / S.ntab[mb] : S.ntab[mb];
-        const double R = fresnel_complex(cos_i, eta, 0.0);
-        if (k == depth) break;
-        Ctr4 r1 = philox4x32_10(Ctr4{{pix, s, b, 4u * k + 1u}}, k0, k1);
-        V3 tdir;
-        if (u01(r1.w[0]) < R || !refract(d, n, eta, &tdir)) d = d - (2.0 * dot(d, n)) * n;
-        else d = normalize(tdir);
-        const double step = S.eps / std::max(std::fabs(dot(d, n)), 0.0625);
-        if (dot(d, ng) < 0.0) T *= std::exp(-alpha * step);
-        o = p + step * d;
-        covered = false;
-      } else {  // conductor
-        double R = fresnel_complex(cos_i, S.ntab[mb], S.ktab[mb]);
-        if (k == depth) break;
-        d = d - (2.0 * dot(d, n)) * n;
-        o = p + S.eps * n;
-        T *= R;
-        covered = false;
-      }
-    }
-    if (sig_out) *sig_out = sig;
-    return L;
-  };
-
   std::atomic<uint64_t> next{0};
   auto worker = [&]() {
     for (;;) {
@@ -683,7 +888,8 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
       for (uint32_t s = 0; s < spp; ++s)
         for (uint32_t j = 0; j < band_count; ++j) {
           uint32_t sg = 0;
-          double L = trace(pix, s, band_first + j, path_sig ? &sg : nullptr);
+          double L = trace_path(S, oc, k0, k1, pix, s, band_first + j, depth, nullptr, path_sig ? &sg : nullptr,
+                                nullptr);
           spectral_sum[i * band_count + j] += L;
           size_t pi = ((size_t)i * spp + s) * band_count + j;
           if (path_L) path_L[pi] = L;
@@ -696,6 +902,143 @@ int or_render(void* scene, const or_camera* cams, uint32_t n_cams, uint32_t band
   for (int i = 0; i < nt; ++i) th.emplace_back(worker);
   for (auto& t : th) t.join();
   return 0;
+}
+
+// Guide network of the guided estimator (FP64; bf16_act: the BF16 network).
+void* or_guide_net_create(uint32_t log2_T, const float* lo, const float* hi, float n_min, float n_max,
+                          const float* grid, const float* W, int bf16_act) {
+  return oguide::net_create(log2_T, lo, hi, n_min, n_max, grid, W, bf16_act);
+}
+
+void or_guide_net_destroy(void* net) { oguide::net_destroy((oguide::Net*)net); }
+
+// Guided render of the listed pixels: as or_render, with the continuation
+// at Lambertian vertices 1..guide_depth drawn by one-sample MIS from the
+// frozen guide `net` (probability alpha) and cosine sampling, and the sun at
+// those vertices estimated by both strategies with the balance heuristic.
+// records (optional) receives, per path [i][s][j] and guided vertex v, the
+// two training records of v: [..][guide_depth][2][12] floats.
+int or_render_guided(void* scene, void* net, double alpha, uint32_t guide_depth, const or_camera* cams,
+                     uint32_t n_cams, uint32_t band_first, uint32_t band_count, uint32_t spp, uint32_t depth,
+                     uint64_t seed, const uint32_t* pixels, uint64_t n_pixels, double* spectral_sum, double* path_L,
+                     uint32_t* path_sig, float* records, int n_threads) {
+  const OScene& S = *(OScene*)scene;
+  if (band_first + band_count > S.B || depth == 0 || !net || guide_depth == 0 || guide_depth > 64) return 1;
+  const std::vector<OCam> oc = setup_cams(cams, n_cams);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  GuideCtx g;
+  g.net = (const oguide::Net*)net;
+  g.alpha = alpha;
+  g.depth = guide_depth;
+  g.n_bands = S.B;
+  const double p_cone = 1.0 / (2.0 * M_PI * (1.0 - S.cos_max));
+  std::atomic<uint64_t> next{0};
+  auto worker = [&]() {
+    std::vector<GuidedSlot> slots(guide_depth);
+    for (;;) {
+      uint64_t i = next.fetch_add(1);
+      if (i >= n_pixels) break;
+      uint32_t pix = pixels[i];
+      for (uint32_t j = 0; j < band_count; ++j) spectral_sum[i * band_count + j] = 0.0;
+      for (uint32_t s = 0; s < spp; ++s)
+        for (uint32_t j = 0; j < band_count; ++j) {
+          uint32_t sg = 0;
+          std::fill(slots.begin(), slots.end(), GuidedSlot());
+          double L = trace_path(S, oc, k0, k1, pix, s, band_first + j, depth, &g, path_sig ? &sg : nullptr,
+                                slots.data());
+          spectral_sum[i * band_count + j] += L;
+          size_t pi = ((size_t)i * spp + s) * band_count + j;
+          if (path_L) path_L[pi] = L;
+          if (path_sig) path_sig[pi] = sg;
+          if (records)
+            for (uint32_t v = 0; v < guide_depth; ++v)
+              slot_records(slots[v], L, p_cone, records + (pi * guide_depth + v) * 24);
+        }
+    }
+  };
+  int nt = n_threads > 0 ? n_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::thread> th;
+  for (int i = 0; i < nt; ++i) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  return 0;
+}
+
+// One guided vertex per query, for checks of the sampler: query i is
+// vertex k of the path (pixel[i], sample, band[i]) at offset position po[i]
+// with normal nrm[i] and, when has_sun[i], a pending sun sample in
+// direction wn[i].  out[i][16]: omega (3), q(omega), p_mix(omega), cos,
+// guide (1) or cosine (0), lobe (or -1), lobe margin, balance weight of the
+// sun sample, balance weight of a sun escape, continues (1/0), q(wn),
+// p_mix(wn), 0, 0.
+void or_guide_step(void* scene, void* net, double alpha, uint32_t k, uint32_t sample, uint64_t seed, uint64_t n,
+                   const uint32_t* pixel, const uint32_t* band, const float* po, const float* nrm,
+                   const uint32_t* has_sun, const float* wn, double* out) {
+  const OScene& S = *(OScene*)scene;
+  GuideCtx g;
+  g.net = (const oguide::Net*)net;
+  g.alpha = alpha;
+  g.depth = 64;
+  g.n_bands = S.B;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (uint64_t i = 0; i < n; ++i) {
+    const V3 p{po[3 * i], po[3 * i + 1], po[3 * i + 2]}, nn{nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    const V3 w{wn[3 * i], wn[3 * i + 1], wn[3 * i + 2]};
+    const Ctr4 r0 = philox4x32_10(Ctr4{{pixel[i], sample, band[i], 4u * k}}, k0, k1);
+    const Ctr4 r1 = philox4x32_10(Ctr4{{pixel[i], sample, band[i], 4u * k + 1u}}, k0, k1);
+    const GuidedVertex gv = guided_vertex(g, S, p, nn, band[i] * 9u / S.B, r0, r1, has_sun[i] != 0, w);
+    double* o = out + 16 * i;
+    o[0] = gv.draw.omega.x;
+    o[1] = gv.draw.omega.y;
+    o[2] = gv.draw.omega.z;
+    o[3] = gv.q;
+    o[4] = gv.pdf;
+    o[5] = gv.c;
+    o[6] = gv.draw.guide ? 1.0 : 0.0;
+    o[7] = gv.draw.lobe;
+    o[8] = gv.draw.lobe_margin;
+    o[9] = gv.nee_w;
+    o[10] = gv.esc_w;
+    o[11] = gv.cont ? 1.0 : 0.0;
+    o[12] = gv.q_sun;
+    o[13] = gv.pdf_sun;
+    o[14] = 0.0;
+    o[15] = 0.0;
+  }
+}
+
+// Draws of the one-sample MIS proposal for fixed head outputs Y [48] and
+// normal n, from caller-given uniforms u [n][6] (choice, lobe, two vMF, two
+// cosine): omega [n][3] and p_mix(omega) [n].
+void or_guide_mis_draws(const double* Y, const double* nrm, double alpha, uint64_t n, const double* u, double* omega,
+                        double* pdf) {
+  oguide::Mixture mx;
+  oguide::mixture_of(Y, &mx);
+  const V3 nn{nrm[0], nrm[1], nrm[2]};
+  for (uint64_t i = 0; i < n; ++i) {
+    const double* v = u + 6 * i;
+    const MisDraw d = mis_draw(mx, nn, alpha, v[0], v[1], v[2], v[3], v[4], v[5]);
+    omega[3 * i] = d.omega.x;
+    omega[3 * i + 1] = d.omega.y;
+    omega[3 * i + 2] = d.omega.z;
+    pdf[i] = mis_pdf(mx, nn, alpha, d.omega, nullptr);
+  }
+}
+
+// Primary rays of the listed (pixel, sample, band) triples: origins and unit
+// directions [n][3] (the camera model of section 1's observer).
+void or_camera_rays(const or_camera* cams, uint32_t n_cams, uint64_t seed, uint64_t n, const uint32_t* pix,
+                    const uint32_t* sample, const uint32_t* band, double* o, double* d) {
+  const std::vector<OCam> oc = setup_cams(cams, n_cams);
+  for (uint64_t i = 0; i < n; ++i) {
+    V3 oo, dd;
+    camera_ray(oc, pix[i], sample[i], band[i], (uint32_t)seed, (uint32_t)(seed >> 32), &oo, &dd);
+    o[3 * i] = oo.x;
+    o[3 * i + 1] = oo.y;
+    o[3 * i + 2] = oo.z;
+    d[3 * i] = dd.x;
+    d[3 * i + 1] = dd.y;
+    d[3 * i + 2] = dd.z;
+  }
 }
 
 // The same estimate with four bands per path: path unit g of a pixel and

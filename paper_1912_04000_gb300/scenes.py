@@ -456,6 +456,58 @@ def plate_under_sky(n_bands=2, width=8, height=8, spp=64, depth=3, seed=5, rho=1
     return Workload("plate_under_sky", scene, spec, [cam], spp, depth, seed)
 
 
+def emitter_over_plate(half=1.0, height=2.0, rho=0.8, le=1.0, n_bands=2, width=4, height_px=4, spp=1024,
+                       seed=13) -> Workload:
+    """Cosine-continuation test: a 20 x 20 m Lambertian floor (y = 0, rho)
+    under a square emitter of half side `half` centred at height `height`
+    (emissive test material, rho 0, radiance le on both faces), no sun
+    (L_sun = 0).  The camera sees a sub-millimetre patch of the floor at the
+    origin; at depth 2 a path adds rho le exactly when its cosine-sampled
+    continuation hits the emitter, so a pixel's expectation is rho le F with F
+    the form factor from a differential area to a coaxial parallel square."""
+    mb = MeshBuilder()
+    mb.quad((-10.0, 0.0, -10.0), (-10.0, 0.0, 10.0), (10.0, 0.0, 10.0), (10.0, 0.0, -10.0), 0)
+    h, a = height, half
+    mb.quad((-a, h, -a), (a, h, -a), (a, h, a), (-a, h, a), 1)
+    scene = mb.build([LAMBERT, EMISSIVE], [0.0, 0.0])
+    lam = band_wavelengths(500.0, 600.0, n_bands)
+    n, k, rt, lt = _flat_spectra(2, n_bands)
+    rt[0] = rho
+    lt[1] = le
+    spec = _spectra(lam, np.zeros(n_bands), np.array([0.0, 1.0, 0.0]), 0.25, n, k, rt, lt)
+    cam = Camera((0.0, 1.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.01, width, height_px)
+    return Workload("emitter_over_plate", scene, spec, [cam], spp, 2, seed)
+
+
+def camera_marker(target_px=(6, 1), width=8, height=6, vfov_deg=60.0, distance=10.0, marker_half=0.3,
+                  spp=256, seed=17) -> Workload:
+    """Camera-convention test: a camera at the origin looking along +z (up
+    +y, so its right is f x up = -x) and one small emissive square (radiance
+    1, rho 0) facing it, centred on the point that a pinhole camera with
+    this vertical field of view, aspect width / height, x to the right and y
+    downwards shows at the centre of pixel target_px, at the given distance
+    along the view axis.  Nothing else is in the scene and there is no sun,
+    so only that pixel sees light, with expectation (marker area) / (pixel
+    footprint area)."""
+    th = math.tan(math.radians(vfov_deg) / 2.0)
+    aspect = width / height
+    x, y = target_px
+    sx = (2.0 * (x + 0.5) / width - 1.0) * th * aspect
+    sy = (1.0 - 2.0 * (y + 0.5) / height) * th
+    f, r, u = np.array([0.0, 0.0, 1.0]), np.array([-1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0])
+    c = distance * (f + sx * r + sy * u)
+    m = marker_half
+    mb = MeshBuilder()
+    mb.quad(c - m * r - m * u, c + m * r - m * u, c + m * r + m * u, c - m * r + m * u, 0)
+    scene = mb.build([EMISSIVE], [0.0])
+    lam = band_wavelengths(500.0, 600.0, 2)
+    n, k, rt, lt = _flat_spectra(1, 2)
+    lt[0] = 1.0
+    spec = _spectra(lam, np.zeros(2), np.array([0.0, 1.0, 0.0]), 0.25, n, k, rt, lt)
+    cam = Camera((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0), vfov_deg, width, height)
+    return Workload("camera_marker", scene, spec, [cam], spp, 1, seed)
+
+
 def mirror_caustic(elevation_deg=45.0, sun_half_angle=0.02, n_metal=0.3, k_metal=3.0, rho=0.8, n_bands=1,
                    width=8, height=8, spp=4, depth=4, seed=3) -> Workload:
     """Caustic test: a 10 x 10 m Lambertian floor (y = 0) and a vertical
