@@ -137,7 +137,21 @@ typedef struct {
                             * rather than bit-exact pieces of one render.  Excludes guided
                             * sampling and trace_variant != 0.  rt_stats.paths counts (pixel,
                             * sample, band) estimates in both modes */
-  uint32_t reserved[2];
+  /* optional, for checks of the guide's training data: with guided = 1,
+   * guide_collect = 1 and use_graph = 0, the training records of every path
+   * in path order (no shuffling), written after each wave:
+   * guide_records_dev[v][p][r][12] floats (device, caller-owned), v = guided
+   * vertex 0..guide_depth - 1, p = s * pixels * band_count + pixel *
+   * band_count + j the path (sample s counted from sample_first), r = 0 the
+   * continuation record, 1 the sun-sample record, each in the record layout
+   * of rt_guide_train_step ({pos, weight}, {normal, band group}, {omega, 0};
+   * weight 0: {0,0,0,0}, {0,0,1,0}, {0,0,1,0}).  RT_ERR_ARG if these
+   * conditions do not hold.  The continuation record's weight is
+   * L_in cos / p_mix, L_in the radiance the path gathered after the vertex
+   * divided by its throughput there; the sun record's is
+   * L_sun T_r cos / p_cone (section 4, Eqs. 2 and 3 sampled by the two
+   * strategies of the vertex). */
+  float* guide_records_dev;
 } rt_render_opts;
 
 typedef struct {
@@ -170,6 +184,17 @@ rt_status rt_set_counting(rt_ctx* ctx, int enable);
 /* 1: every kernel launch of a render is bracketed by CUDA events on the
  * context's stream and the per-stage device times are returned in rt_stats. */
 rt_status rt_set_timing(rt_ctx* ctx, int enable);
+
+/* Diagnostic limits that make the error paths of a context reachable
+ * without a device fault (0 = off, the default): ray queues that hold
+ * queue_capacity rays, fewer than a wave's paths (the kernels detect the
+ * overflow, drop what does not fit and the render returns
+ * RT_ERR_QUEUE_OVERFLOW); traversal loops stopped after traversal_steps
+ * steps per ray (RT_ERR_TIMEOUT); fail_cuda_call = n: the n-th CUDA runtime
+ * call the context checks from now on is not made and reported as failed,
+ * as a failing call would be (RT_ERR_CUDA, then RT_ERR_STATE for every later
+ * call on the context).  The paper has no counterpart: a testing aid. */
+rt_status rt_set_limits(rt_ctx* ctx, uint32_t queue_capacity, uint32_t traversal_steps, uint32_t fail_cuda_call);
 
 /* Scene (the paper's first actor, section 1): n_verts float3 positions in
  * metres, n_tris uint32 index triples, a material id per triangle, and per
@@ -355,6 +380,41 @@ rt_status rt_guide_eval(rt_ctx* ctx, const float* rec_dev, uint64_t n, float* Y_
 rt_status rt_guide_grad(rt_ctx* ctx, const float* rec_dev, uint64_t n, float* loss, float* dgrid_dev, float* dW_dev);
 /* One Adam step on a batch of records; *loss (host, may be NULL) before the step. */
 rt_status rt_guide_train_step(rt_ctx* ctx, const float* rec_dev, uint64_t n, float* loss);
+
+/* One guided sampling step (the one-sample MIS of the guide and cosine
+ * sampling that estimates section 4, Eq. 2 at a Lambertian vertex, with the
+ * sun of Eq. 3 weighted by the balance heuristic) on caller-given vertices,
+ * run by the renderer's own guide kernel, for checks of the sampler.  Vertex
+ * i (of n, a multiple of band_count) is vertex k (1..62) of the path of
+ * pixel i / band_count, band band_first + i % band_count, sample `sample`,
+ * Philox key seed: the counters (pixel, sample, band, 4k) and (.., 4k + 1)
+ * of rt_render draw its continuation.  The guide must be initialised
+ * (rt_guide_init; mis_alpha of its configuration) and spectra set.
+ * v_dev [n] and out_dev [n] are device arrays (16-byte aligned, caller-owned);
+ * the call allocates and frees its own temporaries and synchronises. */
+typedef struct {
+  float pos[3];       /* query position (the vertex offset along its normal) */
+  float throughput;   /* path throughput before the vertex */
+  float normal[3];    /* unit normal on the incoming side */
+  float rho;          /* Lambertian reflectance of the path's band */
+  float sun_dir[3];   /* direction of the vertex's pending sun sample (unit) */
+  float sun_contrib;  /* its next-event contribution before MIS weighting */
+  uint32_t has_sun;   /* 1 = a sun sample is pending (its cosine is positive) */
+  uint32_t reserved[3];
+} rt_guide_vertex;
+typedef struct {
+  float omega[3];     /* continuation direction (guide or cosine draw) */
+  float pdf;          /* p_mix(omega) = alpha q(omega) + (1 - alpha) max(cos, 0) / pi */
+  float cos_theta;    /* normal . omega */
+  float throughput;   /* throughput rho cos / (pi p_mix) x before, when continued; else 0 */
+  float nee_contrib;  /* sun_contrib x p_cone / (p_cone + p_mix(sun_dir)); 0 without sun sample */
+  float esc_weight;   /* p_mix / (p_mix + p_cone) when omega lies in the sun cone and the path
+                         continues, else 0 */
+  uint32_t continued; /* 1 = the path continues along omega (cos > 0 and p_mix > 0) */
+  uint32_t reserved[3];
+} rt_guide_step_out;
+rt_status rt_guide_sample_step(rt_ctx* ctx, const rt_guide_vertex* v_dev, uint32_t n, uint32_t k, uint32_t sample,
+                               uint32_t band_first, uint32_t band_count, uint64_t seed, rt_guide_step_out* out_dev);
 
 /* ---- single steps of the path, for parity tests and tools ---------------- */
 

@@ -22,8 +22,8 @@ XYZ_BF16X3, XYZ_BF16, XYZ_FP64 = 0, 1, 2
 EXPORTS = ["rt_create", "rt_destroy", "rt_last_error", "rt_set_stream", "rt_set_counting", "rt_set_timing",
            "rt_load_scene", "rt_set_spectra", "rt_render", "rt_render_host", "rt_philox", "rt_trace_closest",
            "rt_trace_shadow", "rt_optics_eval", "rt_xyz", "rt_probe_l2", "rt_render_static", "rt_guide_init",
-           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step", "rt_autotune",
-           "rt_set_bvh_builder", "rt_get_scene_info", "rt_render_photons", "rt_photon_records"]
+           "rt_guide_set_params", "rt_guide_get_params", "rt_guide_eval", "rt_guide_grad", "rt_guide_train_step", "rt_guide_sample_step", "rt_autotune",
+           "rt_set_bvh_builder", "rt_get_scene_info", "rt_set_limits", "rt_render_photons", "rt_photon_records"]
 
 
 class RtError(RuntimeError):
@@ -46,7 +46,7 @@ class RenderOpts(C.Structure):
                 ("guide_train_steps", C.c_uint32), ("guide_batch", C.c_uint32), ("sample_first", C.c_uint32),
                 ("accumulate", C.c_uint32), ("spp_total", C.c_uint32), ("leaf_batch", C.c_uint32),
                 ("guide_order", C.c_uint32), ("ray_order", C.c_uint32), ("bands_per_path", C.c_uint32),
-                ("reserved", C.c_uint32 * 2)]
+                ("guide_records_dev", C.c_void_p)]
 
 
 class PhotonOpts(C.Structure):
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
         L.rt_probe_l2.argtypes = [vp, u64, u32, C.POINTER(C.c_float)]
         L.rt_load_scene.argtypes = [vp, vp, u32, vp, u32, vp, vp, vp, u32]
         L.rt_set_bvh_builder.argtypes = [vp, u32]
+        L.rt_set_limits.argtypes = [vp, u32, u32, u32]
         L.rt_get_scene_info.argtypes = [vp, C.POINTER(SceneInfo)]
         L.rt_set_spectra.argtypes = [vp, vp, u32, vp, vp, f32, vp, vp, vp, vp, vp]
         L.rt_render.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, u64, C.POINTER(RenderOpts), vp, vp,
@@ -126,6 +127,7 @@ def load(path: str = LIB_PATH):
         L.rt_guide_eval.argtypes = [vp, vp, u64, vp, vp]
         L.rt_guide_grad.argtypes = [vp, vp, u64, C.POINTER(C.c_float), vp, vp]
         L.rt_guide_train_step.argtypes = [vp, vp, u64, C.POINTER(C.c_float)]
+        L.rt_guide_sample_step.argtypes = [vp, vp, u32, u32, u32, u32, u32, u64, vp]
         L.rt_autotune.argtypes = [vp, C.POINTER(Camera), u32, u32, u32, u32, u32, C.POINTER(RenderOpts),
                                   C.POINTER(AutotuneReport)]
         L.rt_philox.argtypes = [vp, vp, vp, u64, u32, u32]

@@ -21,6 +21,9 @@ struct rt_ctx {
   bool poisoned = false;
   bool counting = false;
   int sms = 0;
+  // diagnostic limits (rt_set_limits; 0 = off): ray-queue capacity, traversal
+  // steps per ray, and the countdown to an injected CUDA failure
+  uint32_t lim_queue = 0, lim_steps = 0, fail_countdown = 0;
   int occ_trace = 0;
   int occ_shade = 0;
   // scene
@@ -117,9 +120,13 @@ rt_status fail(rt_ctx* c, rt_status s, const std::string& msg) {
   return s;
 }
 
+// An injected failure (rt_set_limits) stands for the checked call, which is
+// then not made.
+bool injected_failure(rt_ctx* c) { return c->fail_countdown != 0 && --c->fail_countdown == 0; }
+
 #define CUDA_TRY(ctx, call)                                                                    \
   do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
+    cudaError_t e_ = injected_failure(ctx) ? cudaErrorUnknown : (call);                        \
     if (e_ != cudaSuccess) {                                                                   \
       (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
       if (e_ != cudaErrorMemoryAllocation) (ctx)->poisoned = true;                             \
@@ -204,6 +211,7 @@ DevScene dev_scene(const rt_ctx* c) {
   }
   S.n_tris = c->n_tris;
   S.eps = c->eps;
+  S.iter_cap = c->lim_steps;
   return S;
 }
 
@@ -395,6 +403,15 @@ rt_status rt_set_stream(rt_ctx* c, void* s) {
 rt_status rt_set_counting(rt_ctx* c, int enable) {
   if (rt_status e = check_ctx(c)) return e;
   c->counting = enable != 0;
+  return RT_OK;
+}
+
+rt_status rt_set_limits(rt_ctx* c, uint32_t queue_capacity, uint32_t traversal_steps, uint32_t fail_cuda_call) {
+  if (rt_status e = check_ctx(c)) return e;
+  c->lim_queue = queue_capacity;
+  c->lim_steps = traversal_steps;
+  c->fail_countdown = fail_cuda_call;
+  c->graph_key.clear();  // a captured render holds the old limits
   return RT_OK;
 }
 
@@ -708,20 +725,22 @@ rt_status rt_set_spectra(rt_ctx* c, const float* lambda_nm, uint32_t n_bands, co
   return RT_OK;
 }
 
+extern "C++" {
+namespace srt {
+
 // Checks the cameras and writes their device form (basis derived in FP64)
-// into the pinned staging array; *npix = pixels over all views.
-static rt_status stage_cameras(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, const char* who, uint64_t* npix_out) {
-  const std::string w(who);
+// into out[0 .. n_cams); *npix = pixels over all views.  On a bad camera
+// returns false with the reason in *why.
+bool build_dev_cams(const rt_camera* cams, uint32_t n_cams, DevCam* out, uint64_t* npix_out, const char** why) {
   uint64_t npix = 0;
   for (uint32_t v = 0; v < n_cams; ++v) {
     const rt_camera& cm = cams[v];
-    if (cm.width == 0 || cm.height == 0) return fail(c, RT_ERR_ARG, w + ": zero-sized view");
+    if (cm.width == 0 || cm.height == 0) return (*why = "zero-sized view"), false;
     if (!finite3(cm.pos) || !finite3(cm.look) || !finite3(cm.up) || !(cm.vfov_deg > 0.0f && cm.vfov_deg < 180.0f))
-      return fail(c, RT_ERR_ARG, w + ": bad camera");
+      return (*why = "bad camera"), false;
     npix += (uint64_t)cm.width * cm.height;
   }
-  if (npix >= (1ull << 32)) return fail(c, RT_ERR_ARG, w + ": too many pixels");
-  // cameras in device form, basis in FP64
+  if (npix >= (1ull << 32)) return (*why = "too many pixels"), false;
   uint64_t off = 0;
   for (uint32_t v = 0; v < n_cams; ++v) {
     const rt_camera& cm = cams[v];
@@ -732,19 +751,19 @@ static rt_status stage_cameras(rt_ctx* c, const rt_camera* cams, uint32_t n_cams
       fl += f[a] * f[a];
     }
     fl = std::sqrt(fl);
-    if (!(fl > 0)) return fail(c, RT_ERR_ARG, w + ": camera look == pos");
+    if (!(fl > 0)) return (*why = "camera look == pos"), false;
     for (int a = 0; a < 3; ++a) f[a] /= fl;
     r[0] = f[1] * cm.up[2] - f[2] * cm.up[1];
     r[1] = f[2] * cm.up[0] - f[0] * cm.up[2];
     r[2] = f[0] * cm.up[1] - f[1] * cm.up[0];
     for (int a = 0; a < 3; ++a) rl += r[a] * r[a];
     rl = std::sqrt(rl);
-    if (!(rl > 1e-12)) return fail(c, RT_ERR_ARG, w + ": camera up parallel to the view direction");
+    if (!(rl > 1e-12)) return (*why = "camera up parallel to the view direction"), false;
     for (int a = 0; a < 3; ++a) r[a] /= rl;
     u[0] = r[1] * f[2] - r[2] * f[1];
     u[1] = r[2] * f[0] - r[0] * f[2];
     u[2] = r[0] * f[1] - r[1] * f[0];
-    DevCam& d = c->h_cams[v];
+    DevCam& d = out[v];
     d.pos = make_float3(cm.pos[0], cm.pos[1], cm.pos[2]);
     d.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
     d.r = make_float3((float)r[0], (float)r[1], (float)r[2]);
@@ -759,6 +778,16 @@ static rt_status stage_cameras(rt_ctx* c, const rt_camera* cams, uint32_t n_cams
     off += (uint64_t)cm.width * cm.height;
   }
   *npix_out = npix;
+  return true;
+}
+
+}  // namespace srt
+}  // extern "C++"
+
+// The cameras of a render in the pinned staging array.
+static rt_status stage_cameras(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, const char* who, uint64_t* npix_out) {
+  const char* why = "";
+  if (!build_dev_cams(cams, n_cams, c->h_cams, npix_out, &why)) return fail(c, RT_ERR_ARG, std::string(who) + ": " + why);
   return RT_OK;
 }
 
@@ -921,6 +950,10 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
       while (gcd(perm_mul, n_rec) != 1) ++perm_mul;
     }
   }
+  // the queues as the kernels see them (a diagnostic limit may make them
+  // smaller than the wave; the buffers keep their size)
+  WaveBufs wb = c->wb;
+  if (c->lim_queue && c->lim_queue < wb.cap) wb.cap = c->lim_queue;
   int launches = 0;
   uint32_t waves = 0;
   EvTimer timer(c->tpool);
@@ -928,6 +961,8 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   const bool use_graph = o.use_graph != 0;
   if (use_graph && (tm || lc.counting || lc.record || o.guide_train_steps))
     return fail(c, RT_ERR_ARG, "rt_render: use_graph excludes timing, counting, probes and guide training");
+  if (o.guide_records_dev && (!o.guided || o.guide_collect != 1 || use_graph))
+    return fail(c, RT_ERR_ARG, "rt_render: guide_records_dev needs guided, guide_collect = 1 and no graph");
   // Everything one render enqueues, on stream `s`; with events the device
   // time of the path tracing and of the XYZ contraction is bracketed.
   auto enqueue = [&](cudaStream_t s, bool events) -> cudaError_t {
@@ -943,8 +978,18 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
       w.r0 = (uint32_t)(ws % PB);
       if ((e = cudaMemsetAsync(c->wb.cnt, 0, sizeof(Counters) * (depth + 2), s))) return e;
       if (gw.collect && (e = cudaMemsetAsync(gw.raw, 0, (size_t)n_slots * kRawF4 * sizeof(float4), s))) return e;
-      launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, c->wb, accum, probe, s, &launches, tm, &gw, &c->guide.dev,
+      launch_wave(lc, S, c->sp, c->d_cams, n_cams, w, wb, accum, probe, s, &launches, tm, &gw, &c->guide.dev,
                   c->guide.pack, c->sms);
+      if (o.guide_records_dev) {
+        // the wave's records in path order: slot (v, p) -> records 2 (v spv + p) and + 1, copied to
+        // path ws + p of vertex v
+        launch_guide_records(gw, n_slots, 1u, c->guide.trec, s);
+        ++launches;
+        const size_t row = (size_t)2 * 12 * sizeof(float);
+        if ((e = cudaMemcpy2DAsync(o.guide_records_dev + 24 * ws, row * total, c->guide.trec, row * gw.slots_per_vertex,
+                                   row * w.n, gw.depth, cudaMemcpyDeviceToDevice, s)))
+          return e;
+      }
       if (gw.collect && o.guide_train_steps) {
         if (tm) tm->begin(STG_TRAIN, s);
         launch_guide_records(gw, n_slots, perm_mul, c->guide.trec, s);
@@ -1348,6 +1393,89 @@ rt_status rt_guide_train_step(rt_ctx* c, const float* rec_dev, uint64_t n, float
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return RT_OK;
+}
+
+rt_status rt_guide_sample_step(rt_ctx* c, const rt_guide_vertex* v_dev, uint32_t n, uint32_t k, uint32_t sample,
+                               uint32_t band_first, uint32_t band_count, uint64_t seed, rt_guide_step_out* out_dev) {
+  if (rt_status e = guide_ready(c)) return e;
+  if (!c->has_spectra) return fail(c, RT_ERR_STATE, "rt_guide_sample_step: set spectra first");
+  if (!v_dev || !out_dev) return fail(c, RT_ERR_ARG, "rt_guide_sample_step: null pointer");
+  if ((((uintptr_t)v_dev) | ((uintptr_t)out_dev)) & 15u)
+    return fail(c, RT_ERR_ARG, "rt_guide_sample_step: buffers must be 16-byte aligned");
+  if (band_count == 0 || band_first + band_count > c->sp.n_bands || n % band_count != 0 || n > (1u << 24))
+    return fail(c, RT_ERR_ARG, "rt_guide_sample_step: bad band range or vertex count");
+  if (k < 1 || k + 1 >= (uint32_t)kMaxDepth) return fail(c, RT_ERR_ARG, "rt_guide_sample_step: vertex index");
+  if (n == 0) return RT_OK;
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
+  DevTemp<float4> gq, sq, qout, raw;
+  DevTemp<float> L, wesc, Lfinal;
+  DevTemp<uint32_t> sig, status;
+  DevTemp<double> accum;
+  DevTemp<Counters> cnt;
+  CUDA_TRY(c, cudaMalloc(&gq.p, (size_t)n * 3 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&sq.p, (size_t)n * 2 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&qout.p, (size_t)n * 2 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&raw.p, (size_t)n * kRawF4 * sizeof(float4)));
+  CUDA_TRY(c, cudaMalloc(&L.p, (size_t)n * sizeof(float)));
+  CUDA_TRY(c, cudaMalloc(&wesc.p, (size_t)n * sizeof(float)));
+  CUDA_TRY(c, cudaMalloc(&Lfinal.p, (size_t)n * sizeof(float)));
+  CUDA_TRY(c, cudaMalloc(&sig.p, (size_t)n * sizeof(uint32_t)));
+  CUDA_TRY(c, cudaMalloc(&status.p, sizeof(uint32_t)));
+  CUDA_TRY(c, cudaMalloc(&accum.p, (size_t)n * sizeof(double)));
+  CUDA_TRY(c, cudaMalloc(&cnt.p, (size_t)(k + 2) * sizeof(Counters)));
+  std::vector<Counters> hc(k + 2);
+  std::memset(hc.data(), 0, hc.size() * sizeof(Counters));
+  hc[k].g_count = n;
+  CUDA_TRY(c, cudaMemcpyAsync(cnt.p, hc.data(), hc.size() * sizeof(Counters), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(raw.p, 0, (size_t)n * kRawF4 * sizeof(float4), st));
+  CUDA_TRY(c, cudaMemsetAsync(L.p, 0, (size_t)n * sizeof(float), st));
+  CUDA_TRY(c, cudaMemsetAsync(wesc.p, 0, (size_t)n * sizeof(float), st));
+  CUDA_TRY(c, cudaMemsetAsync(accum.p, 0, (size_t)n * sizeof(double), st));
+  CUDA_TRY(c, cudaMemsetAsync(status.p, 0, sizeof(uint32_t), st));
+  // vertex i: path of pixel i / band_count, band band_first + i % band_count
+  WaveParams w{};
+  w.n = n;
+  w.s0 = sample;
+  w.r0 = 0;
+  w.PB = n;
+  w.band_first = band_first;
+  w.band_count = band_count;
+  w.spp = sample + 1;
+  w.depth = k + 1;
+  w.key0 = (uint32_t)seed;
+  w.key1 = (uint32_t)(seed >> 32);
+  w.n_bands = c->sp.n_bands;
+  w.nb = 1;
+  w.B = band_count;
+  w.acc_stride = band_count;
+  GuideWave gw{};
+  gw.on = true;
+  gw.depth = k;
+  gw.alpha = c->guide.cfg.mis_alpha;
+  gw.gq = gq.p;
+  gw.wesc = wesc.p;
+  gw.collect = 1;
+  gw.slots_per_vertex = 0;  // the one slot of path i is raw[i] whatever k is
+  gw.raw = raw.p;
+  gw.Lfinal = Lfinal.p;
+  WaveBufs b{};
+  b.q[(k + 1) & 1] = qout.p;
+  b.q[k & 1] = qout.p;
+  b.sq = sq.p;
+  b.L = L.p;
+  b.sig = sig.p;
+  b.cnt = cnt.p;
+  b.status = status.p;
+  b.cap = n;
+  launch_guide_step_pack(v_dev, n, gq.p, sq.p, st);
+  launch_guide_sample(c->guide.dev, c->guide.pack, c->sp, w, k, gw, b, accum.p, Probe{nullptr, nullptr, nullptr},
+                      false, c->sms, st);
+  launch_guide_step_gather(v_dev, n, k, gw, b, out_dev, st);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_status, status.p, 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  return status_to_rt(c, *c->h_status);
 }
 
 rt_status rt_autotune(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first, uint32_t band_count,

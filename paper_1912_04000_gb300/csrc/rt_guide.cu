@@ -1121,6 +1121,52 @@ __global__ void k_guide_records(GuideWave gw, uint32_t n_slots, uint32_t perm_mu
   }
 }
 
+// ---------------------------------------------------------------------------
+// one guided step on caller-given vertices (rt_guide_sample_step): the
+// vertices become the guide queries and pending sun samples of a one-wave
+// wavefront in the layout k_shade writes, k_guide_sample runs on them
+// unchanged, and its outputs (continuation rays, rescaled sun samples,
+// escape weights, training slots) are gathered per vertex
+// ---------------------------------------------------------------------------
+__global__ void k_guide_step_pack(const float4* __restrict__ v, uint32_t n, float4* __restrict__ gq,
+                                  float4* __restrict__ sq) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 a = v[4 * i], b = v[4 * i + 1], c = v[4 * i + 2], d = v[4 * i + 3];
+    const bool has_sun = __float_as_uint(d.x) != 0u;
+    gq[3 * i] = make_float4(a.x, a.y, a.z, __uint_as_float(i | kFlagCovered));
+    gq[3 * i + 1] = make_float4(b.x, b.y, b.z, a.w);
+    gq[3 * i + 2] = make_float4(b.w, __uint_as_float(has_sun ? i : 0xFFFFFFFFu), 0.0f, 0.0f);
+    sq[2 * i] = make_float4(a.x, a.y, a.z, __uint_as_float(i));
+    sq[2 * i + 1] = c;
+  }
+}
+
+__global__ void k_guide_step_gather(const float4* __restrict__ v, uint32_t n, uint32_t k, const Counters* cnt,
+                                    const float4* __restrict__ qout, const float4* __restrict__ sq,
+                                    const float* __restrict__ wesc, const float4* __restrict__ raw,
+                                    float4* __restrict__ out) {
+  const uint32_t n_cont = min(cnt[k + 1].q_count, n);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4* r = raw + kRawF4 * i;
+    const float4 c = r[2], d = r[3];
+    const bool has_sun = __float_as_uint(v[4 * i + 3].x) != 0u;
+    out[3 * i] = make_float4(c.x, c.y, c.z, c.w);
+    out[3 * i + 1] = make_float4(d.x, 0.0f, has_sun ? sq[2 * i + 1].w : 0.0f, 0.0f);
+    out[3 * i + 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  __syncthreads();
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_cont; j += gridDim.x * blockDim.x) {
+    const float4 r0 = qout[2 * j], r1 = qout[2 * j + 1];
+    const uint32_t pid = __float_as_uint(r0.w) & kPidMask;
+    if (pid < n) {
+      float* o = (float*)(out + 3 * pid);
+      o[5] = r1.w;
+      o[7] = wesc[pid];
+      ((uint32_t*)o)[8] = 1u;
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1181,6 +1227,17 @@ void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& 
   cudaFuncSetAttribute(k_guide_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSampleSmem);
   k_guide_sample<<<sms * kSampleCtasPerSm, kSampleThreads, kSampleSmem, st>>>(g, (const uint4*)pack, P, w, k, gw, b.q[(k + 1) & 1], b.sq, b.L,
                                                       b.sig, b.cnt, b.cap, accum, probe, record, b.status);
+}
+
+void launch_guide_step_pack(const void* v, uint32_t n, float4* gq, float4* sq, cudaStream_t st) {
+  k_guide_step_pack<<<256, 256, 0, st>>>((const float4*)v, n, gq, sq);
+}
+
+void launch_guide_step_gather(const void* v, uint32_t n, uint32_t k, const GuideWave& gw, const WaveBufs& b, void* out,
+                              cudaStream_t st) {
+  // one block: the per-vertex fields are written before the continuations scatter theirs
+  k_guide_step_gather<<<1, 1024, 0, st>>>((const float4*)v, n, k, b.cnt, b.q[(k + 1) & 1], b.sq, gw.wesc, gw.raw,
+                                          (float4*)out);
 }
 
 void launch_guide_records(const GuideWave& gw, uint32_t n_slots, uint32_t perm_mul, float* train_rec, cudaStream_t st) {

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/spectral_rt.h"
+
 namespace srt {
 
 // device status word bits (set by kernels, read by the host after a render)
@@ -41,6 +43,7 @@ struct DevScene {
   uint32_t n_tris;
   float blo[3], binv[3];  // scene box: lower corner and 1 / extent per axis
   float eps;  // origin offset along the normal: 1e-4 x scene diagonal
+  uint32_t iter_cap;  // traversal steps per ray before ST_ITER; 0 = 4 x binary nodes + 64
 };
 
 // Spectral tables on the device.
@@ -323,6 +326,17 @@ void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& 
                          int sms, cudaStream_t st);
 // Two training records per slot (continuation, sun sample): 2 * n_slots.
 void launch_guide_records(const GuideWave& gw, uint32_t n_slots, uint32_t perm_mul, float* train_rec, cudaStream_t st);
+// rt_guide_sample_step: caller vertices (rt_guide_vertex, 64 B each) into the
+// guide queries and sun samples of a wave; and the step's outputs gathered
+// per vertex (rt_guide_step_out, 48 B each).
+void launch_guide_step_pack(const void* v, uint32_t n, float4* gq, float4* sq, cudaStream_t st);
+void launch_guide_step_gather(const void* v, uint32_t n, uint32_t k, const GuideWave& gw, const WaveBufs& b, void* out,
+                              cudaStream_t st);
+
+// Cameras in device form (basis derived in FP64) into out[0 .. n_cams);
+// *npix = pixels over all views; false with the reason in *why on a bad
+// camera (rt_api.cu).
+bool build_dev_cams(const rt_camera* cams, uint32_t n_cams, DevCam* out, uint64_t* npix, const char** why);
 
 // Read-only view of a context for entry points defined outside rt_api.cu.
 struct CtxView {

@@ -411,7 +411,9 @@ __device__ __forceinline__ bool shadow_step(Trav& tv, uint2* stack, const DevSce
   return !trav_pop(tv, stack, INFINITY);
 }
 
-__device__ __forceinline__ uint32_t trav_cap(const DevScene& S) { return 4u * S.n_nodes + 64u; }
+__device__ __forceinline__ uint32_t trav_cap(const DevScene& S) {
+  return S.iter_cap ? S.iter_cap : 4u * S.n_nodes + 64u;
+}
 
 // Whole-ray helpers for the single-step entry points (any origin).
 __device__ __forceinline__ void closest_hit(const DevScene& S, float3 o, float3 d, float& best_t, int& best_leaf,
@@ -569,8 +571,12 @@ __global__ void k_rsort_scatter(const Counters* __restrict__ cnt, uint32_t k, ui
 __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams, uint32_t n_cams, WaveParams w,
                                                 float4* __restrict__ q, float* __restrict__ L,
                                                 uint32_t* __restrict__ sig, Counters* cnt, bool record,
-                                                float4* __restrict__ L4, float4* __restrict__ T4) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt[1].q_count = w.n;
+                                                float4* __restrict__ L4, float4* __restrict__ T4, uint32_t cap,
+                                                uint32_t* status) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cnt[1].q_count = w.n;
+    if (w.n > cap) atomicOr(status, ST_QUEUE);  // a wave larger than its ray queue
+  }
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += stride) {
     const PathId id = path_id(w, i);
@@ -1709,7 +1715,8 @@ void launch_wave(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, co
   const bool guided = gw.on;
   const bool rec = lc.record;
   if (tm) tm->begin(STG_CAMERA, st);
-  k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec, b.L4, b.T4);
+  k_camera<<<grid_for(w.n, 256), 256, 0, st>>>(cams, n_cams, w, b.q[1], b.L, b.sig, b.cnt, rec, b.L4, b.T4, b.cap,
+                                                b.status);
   if (tm) tm->end(STG_CAMERA, st);
   int nl = 1;
   for (uint32_t k = 1; k <= w.depth; ++k) {

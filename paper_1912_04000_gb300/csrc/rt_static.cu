@@ -74,8 +74,6 @@ rt_status err(rt_ctx* c, rt_status s, const std::string& m, bool fatal = false) 
   return s;
 }
 
-bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
-
 }  // namespace
 
 extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, uint32_t band_first,
@@ -99,50 +97,10 @@ extern "C" rt_status rt_render_static(rt_ctx* c, const rt_camera* cams, uint32_t
   if (((uintptr_t)spectral_dev & 15u) != 0)
     return err(c, RT_ERR_ARG, "rt_render_static: spectral_dev must be 16-byte aligned");
   uint64_t npix = 0;
-  for (uint32_t i = 0; i < n_cams; ++i) {
-    const rt_camera& cm = cams[i];
-    if (cm.width == 0 || cm.height == 0) return err(c, RT_ERR_ARG, "rt_render_static: zero-sized view");
-    if (!finite3(cm.pos) || !finite3(cm.look) || !finite3(cm.up) || !(cm.vfov_deg > 0.0f && cm.vfov_deg < 180.0f))
-      return err(c, RT_ERR_ARG, "rt_render_static: bad camera");
-    npix += (uint64_t)cm.width * cm.height;
-  }
+  const char* why = "";
+  if (!build_dev_cams(cams, n_cams, v.h_cams, &npix, &why)) return err(c, RT_ERR_ARG, std::string("rt_render_static: ") + why);
   const uint64_t PB64 = npix * band_count;
   if (PB64 >= (1ull << 32)) return err(c, RT_ERR_ARG, "rt_render_static: pixels x bands must be below 2^32");
-  uint64_t off = 0;
-  for (uint32_t i = 0; i < n_cams; ++i) {
-    const rt_camera& cm = cams[i];
-    double f[3], r[3], u[3], fl = 0.0, rl = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      f[a] = (double)cm.look[a] - cm.pos[a];
-      fl += f[a] * f[a];
-    }
-    fl = std::sqrt(fl);
-    if (!(fl > 0.0)) return err(c, RT_ERR_ARG, "rt_render_static: camera look == pos");
-    for (int a = 0; a < 3; ++a) f[a] /= fl;
-    r[0] = f[1] * cm.up[2] - f[2] * cm.up[1];
-    r[1] = f[2] * cm.up[0] - f[0] * cm.up[2];
-    r[2] = f[0] * cm.up[1] - f[1] * cm.up[0];
-    for (int a = 0; a < 3; ++a) rl += r[a] * r[a];
-    rl = std::sqrt(rl);
-    if (!(rl > 1e-12)) return err(c, RT_ERR_ARG, "rt_render_static: camera up parallel to the view direction");
-    for (int a = 0; a < 3; ++a) r[a] /= rl;
-    u[0] = r[1] * f[2] - r[2] * f[1];
-    u[1] = r[2] * f[0] - r[0] * f[2];
-    u[2] = r[0] * f[1] - r[1] * f[0];
-    DevCam& d = v.h_cams[i];
-    d.pos = make_float3(cm.pos[0], cm.pos[1], cm.pos[2]);
-    d.f = make_float3((float)f[0], (float)f[1], (float)f[2]);
-    d.r = make_float3((float)r[0], (float)r[1], (float)r[2]);
-    d.u = make_float3((float)u[0], (float)u[1], (float)u[2]);
-    const double th = std::tan(0.5 * (double)cm.vfov_deg * M_PI / 180.0);
-    d.th = (float)th;
-    d.tha = (float)(th * (double)cm.width / (double)cm.height);
-    d.W = cm.width;
-    d.H = cm.height;
-    d.offset = (uint32_t)off;
-    d.pad = 0;
-    off += (uint64_t)cm.width * cm.height;
-  }
 
   if (cudaSetDevice(v.device) != cudaSuccess) return err(c, RT_ERR_CUDA, "rt_render_static: cudaSetDevice", true);
   unsigned char* base = nullptr;

@@ -80,6 +80,11 @@ class Renderer:
     def set_counting(self, on: bool):
         self._check("rt_set_counting", self.lib.rt_set_counting(self._h, 1 if on else 0))
 
+    def set_limits(self, queue_capacity: int = 0, traversal_steps: int = 0, fail_cuda_call: int = 0):
+        """Diagnostic limits (rt_set_limits): small ray queues, capped
+        traversal loops, an injected CUDA failure; zeros restore the defaults."""
+        self._check("rt_set_limits", self.lib.rt_set_limits(self._h, queue_capacity, traversal_steps, fail_cuda_call))
+
     def set_timing(self, on: bool):
         self._check("rt_set_timing", self.lib.rt_set_timing(self._h, 1 if on else 0))
 
@@ -134,10 +139,12 @@ class Renderer:
                guided: bool = False, guide_collect: int = 0, guide_train_steps: int = 0, guide_batch: int = 0,
                sample_first: int = 0, accumulate: bool = False, spp_total: int = 0, use_graph: bool = False,
                tuned: Optional[dict] = None, leaf_batch: int = 0, guide_order: int = 0, ray_order: int = 0,
-               bands_per_path: int = 1):
+               bands_per_path: int = 1, guide_records: bool = False):
         """Returns dict(spectral [P, band_count] f64 sums over samples,
-        xyz [P, 3] f32, stats, and probe_L / probe_sig [n_probe, spp, band_count]
-        when probe_pixels is given)."""
+        xyz [P, 3] f32, stats, probe_L / probe_sig [n_probe, spp, band_count]
+        when probe_pixels is given, and with guide_records (guided,
+        guide_collect = 1) the training records in path order,
+        [guide_depth, spp * P * band_count, 2, 12])."""
         torch = self.torch
         if band_count is None:
             band_count = self.n_bands - band_first
@@ -183,6 +190,12 @@ class Renderer:
             out["probe_L"] = pl
             out["probe_sig"] = ps
             out["_keep"] = pmap32
+        if guide_records:
+            _need(guided and guide_collect == 1, "guide_records needs guided=True and guide_collect=1")
+            gd = min(self.guide_depth, depth)
+            gr = torch.zeros((gd, spp * npix * band_count, 2, 12), dtype=torch.float32, device=dev)
+            opts.guide_records_dev = gr.data_ptr()
+            out["guide_records"] = gr
         cams = _native.cameras_struct(cameras)
         stats = _native.Stats()
         st = self.lib.rt_render(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
@@ -242,9 +255,16 @@ class Renderer:
         self._check("rt_photon_records", st)
         return rec, cls
 
+    HOST_OPTS = ("guided", "guide_collect", "guide_train_steps", "guide_batch", "sample_first", "accumulate",
+                 "spp_total")
+
     def render_host(self, cameras, spp, depth, seed=0, band_first=0, band_count=None, spectral=False,
-                    xyz_mode=_native.XYZ_BF16X3, wave_capacity=0, xyz_out=None, spectral_out=None):
-        """Host outputs (numpy; pinned torch tensors may be passed as outputs)."""
+                    xyz_mode=_native.XYZ_BF16X3, wave_capacity=0, xyz_out=None, spectral_out=None, **opts_kw):
+        """Host outputs (numpy; pinned torch tensors may be passed as outputs).
+        opts_kw: further rt_render_opts fields among HOST_OPTS (guided
+        rendering with online training, progressive sample ranges)."""
+        for k_ in opts_kw:
+            _need(k_ in self.HOST_OPTS, f"render_host: unknown option {k_}")
         if band_count is None:
             band_count = self.n_bands - band_first
         npix = sum(int(c.width) * int(c.height) for c in cameras)
@@ -259,6 +279,8 @@ class Renderer:
         opts = _native.RenderOpts()
         opts.wave_capacity = wave_capacity
         opts.xyz_mode = xyz_mode
+        for k_, v_ in opts_kw.items():
+            setattr(opts, k_, int(v_))
         cams = _native.cameras_struct(cameras)
         stats = _native.Stats()
         st = self.lib.rt_render_host(self._h, cams, len(cameras), band_first, band_count, spp, depth, seed,
@@ -327,6 +349,8 @@ class Renderer:
             setattr(c, k, v)
         self._check("rt_guide_init", self.lib.rt_guide_init(self._h, C.byref(c), seed))
         self.guide_log2_table = c.log2_table or 19
+        self.guide_depth = c.guide_depth or 2
+        self.guide_alpha = c.mis_alpha or 0.7
 
     def guide_set_params(self, grid=None, W=None):
         g = None if grid is None else np.ascontiguousarray(grid, np.float32).ravel()
@@ -385,6 +409,35 @@ class Renderer:
         self._check("rt_guide_train_step", self.lib.rt_guide_train_step(self._h, r.data_ptr(), r.shape[0],
                                                                          C.byref(loss)))
         return loss.value
+
+    STEP_FIELDS = ("omega_x", "omega_y", "omega_z", "pdf", "cos", "throughput", "nee_contrib", "esc_weight")
+
+    def guide_sample_step(self, k, sample, band_first, band_count, seed, pos, normal, throughput, rho, sun_dir,
+                          sun_contrib, has_sun):
+        """rt_guide_sample_step on n vertices (vertex i: pixel i // band_count,
+        band band_first + i % band_count): dict of float arrays named by
+        STEP_FIELDS plus omega [n, 3] and continued [n] (bool)."""
+        torch = self.torch
+        pos = np.asarray(pos, np.float32).reshape(-1, 3)
+        n = pos.shape[0]
+        v = np.zeros((n, 16), np.float32)
+        v[:, 0:3] = pos
+        v[:, 3] = throughput
+        v[:, 4:7] = np.asarray(normal, np.float32).reshape(-1, 3)
+        v[:, 7] = rho
+        v[:, 8:11] = np.asarray(sun_dir, np.float32).reshape(-1, 3)
+        v[:, 11] = sun_contrib
+        v.view(np.uint32)[:, 12] = np.asarray(has_sun, np.uint32)
+        vd = torch.as_tensor(v, device=self.device).contiguous()
+        od = torch.zeros((n, 12), dtype=torch.float32, device=self.device)
+        st = self.lib.rt_guide_sample_step(self._h, vd.data_ptr(), n, k, sample, band_first, band_count, seed,
+                                           od.data_ptr())
+        self._check("rt_guide_sample_step", st)
+        o = od.cpu().numpy()
+        out = {f: o[:, i] for i, f in enumerate(self.STEP_FIELDS)}
+        out["omega"] = o[:, 0:3]
+        out["continued"] = o.view(np.uint32)[:, 8] == 1
+        return out
 
     # -- autotuning ------------------------------------------------------------
     TUNED_FIELDS = ("wave_capacity", "trace_steps", "trace_refill", "shadow_steps", "shadow_refill", "trace_block",

@@ -2,9 +2,23 @@
 
 Per pixel: rel = ||G - O||_1 / ||O||_1 over the three XYZ channels (0 when
 both are 0).  The bar: rel <= 1e-4 on at least 99.9% of pixels, and the
-aggregate relative L1 error sum|G - O| / sum|O| over the pixels that pass is
-at most 1e-5 (the pixels that fail are the grazing-hit divergences the bar
-allows, counted separately).
+aggregate relative L1 error sum|G - O| / sum|O| at most 1e-5.
+
+"Allowing grazing-hit divergence": the GPU traces in FP32 and the oracle in
+FP64, so a path whose ray passes within rounding of a triangle edge can hit
+a different triangle on the two sides and continue along a different path.
+On the full-size scenes the bar is therefore applied to the sampled pixels
+twice (``assert_sampled_parity``):
+
+* restricted -- every sampled pixel, both sides summed over the paths whose
+  event sequences (triangle ids, sun-ray outcomes) agree and whose radiance
+  agrees to 1e-3: rel <= 1e-4 on >= 99.9% of pixels and an aggregate
+  <= 1e-5;
+* unrestricted -- every sampled pixel as rendered: the aggregate over all
+  sampled pixels within a stated bound, and every pixel that misses 1e-4
+  holds at least one diverged path (no failure without a divergence).
+
+The fraction of diverged paths is bounded separately.
 """
 import numpy as np
 
@@ -39,7 +53,66 @@ def xyz_parity(g, o):
 
 
 def assert_parity(g, o, what=""):
+    """The bar on whole images (no divergence expected): >= 99.9% of pixels
+    within 1e-4 and the aggregate over ALL pixels within 1e-5."""
     m = xyz_parity(g, o)
     assert m["frac_ok"] >= PIX_FRAC, f"{what}: {m}"
-    assert m["mean_rel_ok"] <= MEAN_TOL, f"{what}: {m}"
+    assert m["mean_rel_all"] <= MEAN_TOL, f"{what}: {m}"
     return m
+
+
+def restricted_xyz(path_L, same, cmf_w, spp):
+    """XYZ of pixels [n, spp, bands] summed over the paths flagged `same`."""
+    s = np.where(same, np.asarray(path_L, np.float64), 0.0).sum(1)
+    return s @ np.asarray(cmf_w, np.float64) / spp
+
+
+def assert_sampled_parity(g_xyz, o_xyz, g_L, o_L, g_sig, o_sig, cmf_w, spp, what, max_diverged=1e-3,
+                          max_mean_all=MEAN_TOL, path_rtol=1e-4):
+    """The bar on sampled pixels of a full-size render (see the module text).
+    g_L / o_L / g_sig / o_sig: per-path radiance and event signatures
+    [n_pix, spp, bands]; cmf_w: the colour weights of those bands.
+
+    A path counts as diverged when its event signature differs, or when its
+    radiance differs by more than 1e-3 with the same signature: the
+    signature records how many glass sheets a sun ray crossed, not which, so
+    a sun ray that passes the neighbouring pane of a leaded window (another
+    glass, the same count) diverges unseen.  Those unseen divergences must
+    stay below 1e-4 of the paths."""
+    g_L = np.asarray(g_L, np.float64)
+    o_L = np.asarray(o_L, np.float64)
+    same = np.asarray(g_sig) == np.asarray(o_sig)
+    rel = np.abs(g_L - o_L) / np.maximum(np.abs(o_L), 1e-7)
+    unseen = same & (rel > 1e-3)
+    ok = same & ~unseen
+    diverged = 1.0 - float(ok.mean())
+    # paths with the same events carry the same radiance
+    assert np.quantile(rel[same], 0.9999) <= path_rtol, f"{what}: path radiance {np.quantile(rel[same], 0.9999)}"
+    assert unseen.sum() <= 1e-4 * same.sum(), f"{what}: {int(unseen.sum())} paths diverge with the same events"
+    assert diverged <= max_diverged, f"{what}: diverged paths {diverged}"
+    rest = xyz_parity(restricted_xyz(g_L, ok, cmf_w, spp), restricted_xyz(o_L, ok, cmf_w, spp))
+    assert rest["frac_ok"] >= PIX_FRAC, f"{what} restricted: {rest}"
+    assert rest["mean_rel_all"] <= MEAN_TOL, f"{what} restricted: {rest}"
+    full = xyz_parity(g_xyz, o_xyz)
+    bad = pixel_rel(g_xyz, o_xyz) > PIX_TOL
+    clean = ok.reshape(ok.shape[0], -1).all(1)
+    if np.any(bad & clean):
+        i = np.nonzero(bad & clean)[0]
+        print(what, "pixels failing without a diverged path:", i, np.asarray(g_xyz)[i], np.asarray(o_xyz)[i])
+    assert not np.any(bad & clean), f"{what}: {int((bad & clean).sum())} pixels fail without a diverged path"
+    assert full["mean_rel_all"] <= max_mean_all, f"{what} all pixels: {full}"
+    out = {"diverged_paths": diverged, "unseen_divergences": int(unseen.sum()),
+           "pixels_with_diverged_path": float(1 - clean.mean()), "restricted": rest, "all_pixels": full}
+    print(what, out)
+    return out
+
+
+def crop_and_subset(widths_heights, view=0, x0=0, y0=0, w=64, h=48, frac=0.01, seed=0):
+    """Global pixel ids of a w x h crop of one view plus a seeded fraction of
+    all pixels (sorted, unique)."""
+    offs = np.cumsum([0] + [W * H for W, H in widths_heights])
+    W = widths_heights[view][0]
+    crop = np.array([offs[view] + (y0 + y) * W + x0 + x for y in range(h) for x in range(w)], np.int64)
+    rng = np.random.default_rng(seed)
+    sub = rng.choice(offs[-1], max(1, int(round(offs[-1] * frac))), replace=False)
+    return np.unique(np.concatenate([crop, sub])).astype(np.int64)

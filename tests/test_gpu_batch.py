@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_1912_04000_gb300 import scenes
 
-from parity import assert_parity
+from parity import assert_sampled_parity, crop_and_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -59,25 +59,22 @@ def test_autotuner_returns_valid_setting(R, tmp_path):
 
 def test_32_views_full_size_sampled_pixels(R):
     """32 seeded views of the nave (W, H in 256..1024), 81 bands, 8 spp,
-    depth 8, autotuned and graph-captured; a seeded sample of pixels is
-    re-rendered path by path by the oracle."""
+    depth 8, autotuned and graph-captured; a 64 x 48 crop of the first view
+    and a seeded 0.1% of all 13.1M pixels are re-rendered path by path by
+    the oracle and held to the bar on every sampled pixel."""
     from paper_1912_04000_gb300 import autotune
     wl = scenes.nave_views()
     R.load(wl)
     opts, _ = autotune.tuned_options(R, wl, cache_path=None)
-    rng = np.random.default_rng(21)
-    pix = np.sort(rng.choice(wl.n_pixels, 40, replace=False)).astype(np.int64)
+    c0 = wl.cameras[0]
+    pix = crop_and_subset([(c.width, c.height) for c in wl.cameras], x0=c0.width // 2 - 32, y0=c0.height // 2 - 24,
+                          frac=0.001, seed=21)
     out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, tuned=opts, use_graph=True, xyz=True)
     probe = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, tuned=opts, probe_pixels=pix)
     assert np.array_equal(out["spectral"][pix].cpu().numpy(), probe["spectral"][pix].cpu().numpy())
     o = oracle.OracleScene(wl.scene, wl.spectra).render(wl.cameras, wl.spp, wl.depth, wl.seed,
                                                         pixels=pix.astype(np.uint32), record_paths=True)
-    same = probe["probe_sig"].cpu().numpy().view(np.uint32) == o["path_sig"]
-    print("32 views: paths with identical event signatures", same.mean(), "paths/s",
-          out["stats"]["paths"] / (out["stats"]["ms_render"] * 1e-3))
-    assert same.mean() >= 0.99
-    np.testing.assert_allclose(probe["probe_L"].cpu().numpy()[same], o["path_L"][same], rtol=1e-4, atol=1e-7)
-    clean = same.reshape(len(pix), -1).all(1)
-    g = out["xyz"].cpu().numpy()[pix]
-    if clean.any():
-        assert_parity(g[clean], o["xyz"][clean], "32 views clean pixels")
+    print("32 views: paths/s", out["stats"]["paths"] / (out["stats"]["ms_render"] * 1e-3))
+    assert_sampled_parity(out["xyz"].cpu().numpy()[pix], o["xyz"], probe["probe_L"].cpu().numpy(), o["path_L"],
+                          probe["probe_sig"].cpu().numpy().view(np.uint32), o["path_sig"], wl.spectra.cmf_w, wl.spp,
+                          "32 views crop + 0.1%", max_diverged=2e-3)

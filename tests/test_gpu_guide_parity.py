@@ -1,0 +1,289 @@
+"""The guided tracer on the GPU against the oracle's guided estimator, fed
+the same seeded BF16 network (section 4, Eq. 2 sampled by one-sample MIS of
+the guide and cosine sampling; the sun of Eq. 3 by the balance heuristic):
+per query through rt_guide_sample_step (the renderer's own guide kernel),
+per path through guided renders with per-path records, and the training
+records the renderer builds from them.
+
+Two networks.  A random BF16 network: the GPU accumulates each layer in
+FP32 on the tensor cores and the oracle in FP64, and where an activation
+lies within that rounding of a BF16 rounding boundary the two round it
+differently (about one query in five), moving the outputs by a BF16 ulp;
+its checks are bounds on the distribution.  A pass-through network (weights
+0 and powers of two, one path per output through the ReLUs: each head
+output is a signed, scaled copy of one input that both precisions round to
+the same BF16 value) is exact in both precisions, so with it the sampler
+and the MIS weights are checked query by query and path by path to float
+rounding."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_04000_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+LOG2_T = 12
+ALPHA = 0.7
+
+
+def bf16(a):
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    grid = (rng.normal(size=16 * (1 << LOG2_T) * 2) * 0.5).astype(np.float32)
+    W = bf16(rng.normal(size=oracle.GUIDE_W_SIZE) * 0.2)
+    return grid, W
+
+
+def _passthrough_params(seed):
+    """A network whose every output is one input times a power of two, with
+    inputs that FP32 and FP64 round to the same BF16 value (bar a rounding
+    boundary within a few FP32 ulps): the constant SH term, the three linear
+    SH terms (the normal) and the one-hot band group.  W1 sends each of them
+    to hidden units relu(+-s x) (one non-zero weight per unit), W2 = W3 =
+    identity, and W4 forms lobe j's mean direction from three signed pairs
+    (scaled linear SH terms: a direction field tied to the normal), its logit
+    from the band group's one-hot entry and its kappa input from the
+    constant term times 8 x 2^(j mod 4).  Every product has one non-zero
+    term, so FP32 and FP64 accumulation agree exactly.  The grid (random,
+    seeded) does not reach the outputs."""
+    rng = np.random.default_rng(seed)
+    grid = (rng.normal(size=16 * (1 << LOG2_T) * 2) * 0.6).astype(np.float32)
+    scales = [1.0, 2.0, 0.5, -1.0, -2.0, -0.5, 4.0]
+    W1 = np.zeros((64, 64), np.float32)
+    for t in range(24):
+        j, c = divmod(t, 3)
+        src = 33 + (j + c) % 3
+        sc = scales[(5 * j + 3 * c) % 7]
+        W1[src, 2 * t] = sc
+        W1[src, 2 * t + 1] = -sc
+    for j in range(8):
+        W1[48 + (j + 1) % 9, 48 + j] = 1.0
+        W1[32, 56 + j] = float(2 ** (j % 4))
+    eye = np.eye(64, dtype=np.float32)
+    W4 = np.zeros((64, 48), np.float32)
+    for j in range(8):
+        W4[48 + j, 5 * j] = 1.0
+        for c in range(3):
+            t = 3 * j + c
+            W4[2 * t, 5 * j + 1 + c] = 1.0
+            W4[2 * t + 1, 5 * j + 1 + c] = -1.0
+        W4[56 + j, 5 * j + 4] = 8.0
+    W = np.concatenate([W1.ravel(), eye.ravel(), eye.ravel(), W4.ravel()])
+    assert W.size == oracle.GUIDE_W_SIZE
+    return grid, W
+
+
+def _setup(R, wl, seed, guide_depth=2, passthrough=False):
+    R.load(wl)
+    R.guide_init(seed=1, log2_table=LOG2_T, mis_alpha=ALPHA, guide_depth=guide_depth)
+    grid, W = _passthrough_params(seed) if passthrough else _params(seed)
+    R.guide_set_params(grid, W)
+    lo = wl.scene.verts.min(0).astype(np.float32)
+    hi = wl.scene.verts.max(0).astype(np.float32)
+    g = oracle.OracleGuide(LOG2_T, lo, hi, grid, W)  # the BF16 network
+    return g, oracle.OracleScene(wl.scene, wl.spectra)
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1912_04000_gb300.renderer import Renderer
+    return Renderer(0)
+
+
+def _angle(a, b):
+    a = a / np.linalg.norm(a, axis=1, keepdims=True)
+    b = b / np.linalg.norm(b, axis=1, keepdims=True)
+    return np.arccos(np.clip(np.einsum("ij,ij->i", a, b), -1, 1))
+
+
+@pytest.mark.parametrize("passthrough", [False, True])
+def test_sample_step_matches_oracle(R, passthrough):
+    """4096 vertices (256 pixels x 16 bands) at random positions with random
+    normals and pending sun samples: the GPU's continuation direction, MIS
+    density p_mix, throughput, balance-weighted sun sample and escape weight
+    against the oracle's, per query.  The two networks differ only in FP32
+    vs FP64 accumulation (BF16 inputs of every layer alike), so most queries
+    agree to float rounding; queries whose lobe uniform lies within 1e-3 of
+    a lobe boundary may pick another lobe and are left out."""
+    wl = scenes.tiny_box(width=16, height=16, n_bands=16)
+    g, sc = _setup(R, wl, seed=11, passthrough=passthrough)
+    rng = np.random.default_rng(5)
+    n, B = 4096, 16
+    lo, hi = wl.scene.verts.min(0), wl.scene.verts.max(0)
+    pos = (lo + (hi - lo) * rng.uniform(0.02, 0.98, (n, 3))).astype(np.float32)
+    nrm = rng.normal(size=(n, 3))
+    nrm = (nrm / np.linalg.norm(nrm, axis=1, keepdims=True)).astype(np.float32)
+    sun = wl.spectra.sun_dir.astype(np.float64)
+    # sun samples inside the cone, on the lit side of the normal
+    a = wl.spectra.sun_half_angle
+    ct = 1 - rng.random(n) * (1 - math.cos(a))
+    st = np.sqrt(1 - ct ** 2)
+    ph = 2 * math.pi * rng.random(n)
+    t1 = np.cross(sun, [0.0, 0.0, 1.0])
+    t1 /= np.linalg.norm(t1)
+    t2 = np.cross(sun, t1)
+    wn = (st * np.cos(ph))[:, None] * t1 + (st * np.sin(ph))[:, None] * t2 + ct[:, None] * sun
+    wn = wn.astype(np.float32)
+    flip = np.einsum("ij,ij->i", nrm, wn) < 0
+    nrm[flip] *= -1
+    has_sun = (rng.random(n) < 0.8).astype(np.uint32)
+    contrib = rng.uniform(0.1, 2.0, n).astype(np.float32)
+    T, rho, k, s, seed = 0.9, 0.7, 1, 3, 7
+    gpu = R.guide_sample_step(k, s, 0, B, seed, pos, nrm, T, rho, wn, contrib, has_sun)
+    pix = np.arange(n, dtype=np.uint32) // B
+    band = np.arange(n, dtype=np.uint32) % B
+    o = sc.guide_step(g, k, s, seed, pix, band, pos, nrm, has_sun, wn, alpha=ALPHA)
+    keep = (o["lobe_margin"] > 1e-3) | (o["guide"] == 0)
+    assert keep.mean() > 0.98
+    cos_draw = (o["guide"] == 0)[keep]
+    ang = _angle(gpu["omega"].astype(np.float64), o["omega"])[keep]
+    rel_pdf = np.abs(gpu["pdf"] / o["pdf"] - 1)[keep]
+    cont = o["cont"][keep] == 1
+    agree = gpu["continued"][keep] == cont
+    both = agree & cont
+    want_T = T * rho / math.pi * o["cos"][keep][both] / o["pdf"][keep][both]
+    rel_T = np.abs(gpu["throughput"][keep][both] / want_T - 1)
+    hs = (has_sun == 1) & keep
+    rel_nee = np.abs(gpu["nee_contrib"][hs] / (contrib[hs] * o["nee_w"][hs]) - 1)
+    ew, ow = gpu["esc_weight"][keep][both], o["esc_w"][keep][both]
+    inside = (ew > 0) & (ow > 0)
+    d_esc = np.abs(ew[inside] - ow[inside])
+
+    def q(x):
+        return [float(np.mean(x < 1e-5)), float(np.median(x)), float(np.quantile(x, 0.99)), float(x.max())]
+
+    print("guide draws", float(o["guide"].mean()), "kept", float(keep.mean()))
+    for name, x in (("angle", ang), ("p_mix", rel_pdf), ("throughput", rel_T), ("sun weight", rel_nee),
+                    ("escape weight", d_esc)):
+        print(name, "frac < 1e-5, median, 99%, max:", q(x) if x.size else None)
+    # cosine draws do not depend on the network: equal to float rounding
+    assert np.all(ang[cos_draw] < 1e-5)
+    # random network: most queries agree to FP32 rounding; where a BF16
+    # rounding of an activation flips, outputs move by about a BF16 ulp.
+    # Pass-through network: all agree but for the rare BF16 input flips.
+    exact = 0.995 if passthrough else 0.75
+    assert np.mean(ang < 1e-5) > exact and ang.max() < 0.1
+    assert np.mean(rel_pdf < 1e-4) > exact and np.quantile(rel_pdf, 0.999) < 0.1
+    dcos = np.abs(gpu["cos"][keep] - o["cos"][keep])
+    assert np.mean(dcos < 1e-5) > exact and dcos.max() < 0.1
+    assert agree.mean() > 0.999
+    assert np.mean(rel_T < 1e-4) > exact and np.quantile(rel_T, 0.999) < 0.1
+    assert np.all(gpu["throughput"][keep][~gpu["continued"][keep]] == 0)
+    assert np.mean(rel_nee < 1e-4) > max(exact, 0.9) and np.quantile(rel_nee, 0.999) < 0.1
+    assert np.all(gpu["nee_contrib"][(has_sun == 0)] == 0)
+    # escape weights: zero outside the cone, p_mix / (p_mix + p_cone) inside
+    assert np.mean((ew > 0) == (ow > 0)) > 0.999
+    if inside.any():
+        assert np.mean(d_esc < 1e-4) > max(exact, 0.9) and d_esc.max() < 0.1
+
+
+def _render_pair(R, wl, gseed, guide_depth=2, pixels=None, passthrough=True):
+    g, sc = _setup(R, wl, seed=gseed, guide_depth=guide_depth, passthrough=passthrough)
+    n_px = wl.n_pixels
+    pix = np.arange(n_px) if pixels is None else np.asarray(pixels)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, guided=True, guide_collect=1, probe_pixels=pix,
+                   guide_records=True, xyz_mode=2)
+    o = sc.render_guided(g, wl.cameras, wl.spp, wl.depth, wl.seed, alpha=ALPHA, guide_depth=guide_depth,
+                         pixels=pix.astype(np.uint32), record_paths=True, records=True)
+    return out, o, pix
+
+
+def _check_paths(out, o, what, frac_same, q_rel, rel_L):
+    """Paths with identical event sequences: at least frac_same of all; the
+    q_rel quantile of their relative radiance difference below rel_L."""
+    gS = out["probe_sig"].cpu().numpy().view(np.uint32)
+    gL = out["probe_L"].cpu().numpy().astype(np.float64)
+    same = gS == o["path_sig"]
+    rel = np.abs(gL - o["path_L"]) / np.maximum(np.abs(o["path_L"]), 1e-6)
+    print(what, "identical event sequences", same.mean(), "rel L median / 99% / 99.9% / max over those",
+          np.median(rel[same]), np.quantile(rel[same], 0.99), np.quantile(rel[same], 0.999), rel[same].max())
+    assert same.mean() >= frac_same
+    assert np.quantile(rel[same], q_rel) < rel_L
+    return same
+
+
+def _check_records(out, o, wl, pix, same, what, exact=True):
+    """GPU records [v][s * P * B + p * B + j] against the oracle's
+    [p][s][j][v], for paths whose events agree."""
+    gr = out["guide_records"].cpu().numpy()
+    gd = gr.shape[0]
+    P, B, S = wl.n_pixels, wl.band_count, wl.spp
+    orr = o["records"]  # [npx, S, B, gd, 2, 12]
+    sidx = np.arange(S)[None, :, None]
+    jidx = np.arange(B)[None, None, :]
+    path = sidx * P * B + pix[:, None, None] * B + jidx  # [npx, S, B]
+    g = np.moveaxis(gr[:, path], 0, 3)  # [npx, S, B, gd, 2, 12]
+    m = np.broadcast_to(same[..., None, None], g.shape[:5])
+    gw, ow = g[..., 3][m], orr[..., 3][m]
+    both = (gw > 0) & (ow > 0)
+    print(what, "records with weight: gpu", (gw > 0).mean(), "oracle", (ow > 0).mean(), "both", both.mean())
+    assert np.mean((gw > 0) == (ow > 0)) > 0.999
+    rel = np.abs(gw[both] / ow[both] - 1)
+    print(what, "record weight rel median / 99% / max", np.median(rel), np.quantile(rel, 0.99), rel.max())
+    if exact:
+        assert np.quantile(rel, 0.99) < 1e-3
+    else:
+        assert np.median(rel) < 1e-3 and np.quantile(rel, 0.99) < 0.2
+    gm, om_ = g[m][both], orr[m][both]
+    diag = float(np.linalg.norm(wl.scene.verts.max(0) - wl.scene.verts.min(0)))
+    dpos = np.abs(gm[:, 0:3] - om_[:, 0:3]).max(1) / diag
+    ang = _angle(gm[:, 8:11].astype(np.float64), om_[:, 8:11].astype(np.float64))
+    print(what, "record position / direction 99%:", np.quantile(dpos, 0.99), np.quantile(ang, 0.99))
+    assert np.array_equal(gm[:, 7], om_[:, 7])  # band group
+    q = 0.999 if exact else 0.9
+    assert np.quantile(dpos, q) < 1e-5 and np.quantile(ang, q) < 1e-4
+    assert np.quantile(np.abs(gm[:, 4:7] - om_[:, 4:7]).max(1), q) < 1e-5
+
+
+def test_guided_box_paths_and_records(R):
+    """The glass box, 24 x 16, 16 bands, 2 spp, depth 4, two guided vertices,
+    the pass-through network: every path against the oracle's guided path,
+    and the training records built from them."""
+    wl = scenes.tiny_box(width=24, height=16, spp=2)
+    out, o, pix = _render_pair(R, wl, gseed=21)
+    same = _check_paths(out, o, "box", 0.99, 0.999, 1e-4)
+    _check_records(out, o, wl, pix, same, "box")
+    # pixels whose paths all agree meet the plain tracer's bar
+    g = out["xyz"].cpu().numpy()[pix].astype(np.float64)
+    clean = same.reshape(len(pix), -1).all(1)
+    rel = np.abs(g - o["xyz"]).sum(1) / np.maximum(np.abs(o["xyz"]).sum(1), 1e-30)
+    print("box clean pixels", clean.mean(), "rel 99.9% over them", np.quantile(rel[clean], 0.999))
+    assert clean.mean() > 0.9 and np.quantile(rel[clean], 0.999) < 1e-4
+
+
+def test_guided_box_random_network(R):
+    """The same render with a random BF16 network: bounds on the
+    distribution (one query in five rounds an activation differently)."""
+    wl = scenes.tiny_box(width=24, height=16, spp=2)
+    out, o, pix = _render_pair(R, wl, gseed=24, passthrough=False)
+    same = _check_paths(out, o, "box, random network", 0.95, 0.9, 1e-4)
+    _check_records(out, o, wl, pix, same, "box, random network", exact=False)
+
+
+def test_guided_prism_paths_and_records(R):
+    """The prism room (refraction with dispersion, total internal
+    reflection), 32 x 24, 16 bands, 2 spp, depth 6, pass-through network."""
+    wl = scenes.prism_room(width=32, height=24, spp=2, depth=6)
+    out, o, pix = _render_pair(R, wl, gseed=22)
+    same = _check_paths(out, o, "prism", 0.99, 0.999, 1e-4)
+    _check_records(out, o, wl, pix, same, "prism")
+
+
+def test_guided_nave_sampled_paths(R):
+    """The 200k-triangle nave at 1024 x 768 with 9 bands (one per band group),
+    1 spp, depth 6, pass-through network: seeded pixels path by path and
+    their records."""
+    wl = scenes.nave(n_bands=9, spp=1, depth=6)
+    rng = np.random.default_rng(12)
+    pix = np.sort(rng.choice(wl.n_pixels, 1024, replace=False))
+    out, o, pix = _render_pair(R, wl, gseed=23, pixels=pix)
+    same = _check_paths(out, o, "nave", 0.99, 0.999, 1e-4)
+    _check_records(out, o, wl, pix, same, "nave")

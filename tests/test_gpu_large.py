@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_1912_04000_gb300 import scenes
 
-from parity import assert_parity
+from parity import assert_sampled_parity, crop_and_subset
 
 pytestmark = pytest.mark.gpu
 
@@ -23,21 +23,21 @@ def large():
 
 
 def test_large_nave_sampled_pixels(large):
+    """A 64 x 48 crop of the first view and a seeded 0.1% of all 12.6M
+    pixels, path by path against the oracle, held to the bar on every
+    sampled pixel.  With 2M triangles more rays pass within FP32 rounding of
+    a shared edge, so up to 1% of paths may take another triangle than the
+    FP64 oracle (measured 0.6%)."""
     R, wl = large
-    rng = np.random.default_rng(31)
-    pix = np.sort(rng.choice(wl.n_pixels, 64, replace=False)).astype(np.int64)
-    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, probe_pixels=pix)
+    pix = crop_and_subset([(c.width, c.height) for c in wl.cameras], x0=992, y0=744, frac=0.001, seed=31)
+    out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, probe_pixels=pix, xyz_mode=2)
     st = out["stats"]
     print("large nave:", st["paths"], "paths in", st["ms_render"], "ms ->", st["paths"] / (st["ms_render"] * 1e-3), "paths/s")
     o = oracle.OracleScene(wl.scene, wl.spectra).render(wl.cameras, wl.spp, wl.depth, wl.seed,
                                                         pixels=pix.astype(np.uint32), record_paths=True)
-    same = out["probe_sig"].cpu().numpy().view(np.uint32) == o["path_sig"]
-    print("large nave: paths with identical event signatures", same.mean())
-    assert same.mean() >= 0.99
-    np.testing.assert_allclose(out["probe_L"].cpu().numpy()[same], o["path_L"][same], rtol=1e-4, atol=1e-7)
-    clean = same.reshape(len(pix), -1).all(1)
-    g = out["xyz"].cpu().numpy()[pix]
-    assert_parity(g[clean], o["xyz"][clean], "large nave clean pixels")
+    assert_sampled_parity(out["xyz"].cpu().numpy()[pix], o["xyz"], out["probe_L"].cpu().numpy(), o["path_L"],
+                          out["probe_sig"].cpu().numpy().view(np.uint32), o["path_sig"], wl.spectra.cmf_w, wl.spp,
+                          "large nave crop + 0.1%", max_diverged=1e-2)
 
 
 def test_large_nave_guided_runs(large):
@@ -49,8 +49,10 @@ def test_large_nave_guided_runs(large):
 
 
 def test_large_nave_device_build(large):
-    """The device builder on 2M triangles: the same closest hits as the host
-    SAH tree for seeded rays, and its build time next to the host's."""
+    """The device builder on 2M triangles: closest hits and sun-ray
+    transmittances against the FP64 oracle, the same closest hits as the
+    host SAH tree, and its build time next to the host's."""
+    from test_gpu_lbvh import check_against_oracle
     R, wl = large
     rng = np.random.default_rng(4)
     lo, hi = wl.scene.verts.min(0), wl.scene.verts.max(0)
@@ -63,7 +65,8 @@ def test_large_nave_device_build(large):
         R.load(wl, builder=1)
         dev = R.scene_info()
         t1, p1 = (x.cpu().numpy() for x in R.trace_closest(o, d))
+        check_against_oracle(R, wl, o, d, "large nave", brute=False)
     finally:
-        R.load(wl, builder=0)
+        R.load(wl)
     print("host build", host, "device build", dev)
     assert np.array_equal(p0, p1) and np.array_equal(t0, t1)
