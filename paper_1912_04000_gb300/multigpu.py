@@ -1,12 +1,17 @@
-"""Process-per-GPU helpers for benchmarking several GPUs of one node.
+"""Process-per-GPU helpers for rendering on several GPUs of one node.
 
-The path needs no exchange between GPUs: every (pixel, sample, band) path is
-independent, so ranks render disjoint units.  Two partitions are offered:
+Every (pixel, sample, band) path is independent, so ranks render disjoint
+units.  Two partitions are offered:
   - sample passes: rank r renders the whole image with Philox key seed + r
     (independent samples; weak scaling, the image of N ranks averages N x spp);
-  - band sub-domains: rank r renders a contiguous band range (the paper's
-    spectral decomposition; strong scaling, partial XYZ images add up).
-Only the timing uses a collective (a barrier and a max over ranks).
+    no data moves between ranks;
+  - band sub-domains (the paper's spectral decomposition, title and section
+    5, with wavelength ranges as the sub-domains): rank r renders the bands
+    band_shard(B, N, r) of every path; its XYZ image of those bands is a
+    partial sum of the full image's, so one reduce-sum of the [P x 3] FP32
+    partials to rank 0 (NCCL on GPUs, gloo on CPU) forms the image.  That
+    reduce is the path's only exchange.
+Timing adds a barrier and a max over ranks.
 """
 from __future__ import annotations
 
@@ -79,6 +84,26 @@ def band_shard(n_bands: int, world: int, rank: int):
     first = rank * base + min(rank, extra)
     count = base + (1 if rank < extra else 0)
     return first, count
+
+
+def render_band_sharded(info: DistInfo, renderer, cameras, spp: int, depth: int, seed: int, n_bands: int,
+                        dst: int = 0, **render_kw):
+    """Renders this rank's band sub-domain of the views and reduces the XYZ
+    partials of all ranks onto rank `dst`.  `renderer.render(cameras, spp,
+    depth, seed, band_first=, band_count=, spectral=False, **render_kw)` must
+    return {"xyz": [P, 3] float32 tensor} on the collective's device.
+    Returns (xyz, (first, count)); xyz holds the full image on `dst` and
+    this rank's partial elsewhere."""
+    first, count = band_shard(n_bands, info.world, info.rank)
+    if count == 0:
+        raise ValueError("more ranks than bands")
+    out = renderer.render(cameras, spp, depth, seed, band_first=first, band_count=count, spectral=False,
+                          **render_kw)
+    xyz = out["xyz"]
+    if info.world > 1:
+        import torch.distributed as dist
+        dist.reduce(xyz, dst=dst, op=dist.ReduceOp.SUM)
+    return xyz, (first, count)
 
 
 def finish(info: DistInfo):
