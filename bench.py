@@ -1,16 +1,29 @@
 #!/usr/bin/env python
 """Throughput of the GB300 spectral path tracer: spectral paths per second.
 
-One step = one full render of the procedural nave (about 200k triangles,
-1024 x 768, 81 bands 380-780 nm, 16 spp, depth 8: 1,019,215,872 spectral
-paths) through the C ABI, scene and spectra resident on the device.
+Headline workload: the largest single-GPU configuration, the 2M-triangle
+stained-glass nave (40 leaded windows with per-pane Gaussian absorption
+bands, brass fittings), 4 views at 2048 x 1536, 81 bands 380-780 nm, depth
+12, guided (the learned guide, trained online on the tracer's own samples
+in every pass) and batched (all 4 views and all bands in one render call).
+One step = one full-frame sample pass of that job: 4 x 2048 x 1536 x 81 =
+1,019,215,872 spectral paths, accumulated in FP64 into the job's spectral
+image (64 passes make the configuration's 64 spp), scene, spectra and guide
+resident on the device.
+
+Sub-records on one GPU: the 200k-triangle nave (1024 x 768, 81 bands,
+16 spp, depth 8; one step = one whole render) and the equal-time MSE of the
+guided against the plain tracer on a 256 x 192 view of that nave against a
+4096-spp plain reference (the configuration's full-size form:
+--guided-mse --mse-width 1024 --mse-height 768).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
-this machine's host cores on a bounded pixel sample of the same workload.
-Under torchrun each rank renders the whole image with its own Philox key
-(independent sample passes, weak scaling); the time is the max over ranks.
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle
+(guided estimator, same network architecture) on this machine's host cores on
+a bounded pixel sample of the headline workload.  Under torchrun each rank
+renders the whole job with its own Philox key (independent sample passes,
+weak scaling); the time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -27,10 +40,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "spectral paths/s on 1 GB300 (nave 200k tris, 1024x768, 81 bands, 16 spp, depth 8)"
+METRIC = ("spectral paths/s on 1 GB300 (2M-triangle stained-glass nave, 4 views 2048x1536, 81 bands, depth 12, "
+          "guided + batched)")
 UNIT = "paths/s"
-WORKLOAD = "nave_200k_1024x768_b81_spp16_d8"
-PROFILE_TXT = os.path.join(ROOT, "profiles", "k_trace_closest_nave.txt")
+WORKLOAD = "large_nave_2M_4x2048x1536_b81_d12_guided_batched"
+NAVE_WORKLOAD = "nave_200k_1024x768_b81_spp16_d8"
+# guide settings of the headline job: every 8th path keeps training slots,
+# 8 Adam steps after each wave
+GUIDE_COLLECT, GUIDE_STEPS = 8, 8
+PROFILE_TXT = os.path.join(ROOT, "profiles", "k_trace_closest_large_nave.txt")
 KERNEL_SOURCES = ["paper_1912_04000_gb300/csrc/rt_kernels.cu", "paper_1912_04000_gb300/csrc/rt_device.cuh"]
 
 
@@ -45,8 +63,15 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--builder", default="sbvh", choices=["host", "device", "sbvh"],
                     help="BVH builder: binned SAH, device linear BVH, or SAH with spatial splits")
+    ap.add_argument("--partition", default="samples", choices=["samples", "bands"],
+                    help="several GPUs: each rank renders whole sample passes with its own Philox key (weak "
+                         "scaling), or its band sub-domain of every pass with the XYZ partials reduced to "
+                         "rank 0 over NCCL (strong scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-pixels", type=int, default=1536, help="oracle sample size (pixels at full spp/bands)")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="skip the 200k-triangle nave sub-record and the equal-time MSE sub-record")
+    ap.add_argument("--cpu-pixels", type=int, default=32768,
+                    help="oracle sample size (pixels of one guided pass, all bands)")
     ap.add_argument("--guided-mse", action="store_true",
                     help="equal-time MSE of the guided vs the plain tracer against a high-spp plain reference")
     ap.add_argument("--bands-mse", action="store_true",
@@ -148,40 +173,67 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline(wl, n_pix: int, seed: int = 0):
-    """The oracle as it stands, all host cores, on a seeded pixel sample."""
+def oracle_guide_for(wl, seed=0, log2_table=19):
+    """A seeded network of the guide's architecture for the oracle's guided
+    estimator (its cost per query does not depend on the weights)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    grid = (rng.normal(size=16 * (1 << log2_table) * 2) * 1e-2).astype(np.float32)
+    W = (rng.normal(size=oracle.GUIDE_W_SIZE) * 0.2).astype(np.float32)
+    lo = wl.scene.verts.min(0).astype(np.float32)
+    hi = wl.scene.verts.max(0).astype(np.float32)
+    return oracle.OracleGuide(log2_table, lo, hi, grid, W)
+
+
+def cpu_baseline(wl, n_pix: int, seed: int = 0, guided: bool = True, sc=None, guide=None):
+    """The oracle as it stands, all host cores, on a seeded pixel sample of
+    one sample pass (guided estimator with guide depth 2 when guided)."""
     import numpy as np
 
     import oracle
     rng = np.random.default_rng(12345 + seed)
     pix = np.sort(rng.choice(wl.n_pixels, min(n_pix, wl.n_pixels), replace=False)).astype(np.uint32)
-    sc = oracle.OracleScene(wl.scene, wl.spectra)
+    sc = sc or oracle.OracleScene(wl.scene, wl.spectra)
     threads = oracle.hardware_threads()
+    spp = 1 if guided else wl.spp
     t0 = time.perf_counter()
-    sc.render(wl.cameras, wl.spp, wl.depth, wl.seed + seed, pixels=pix, n_threads=threads)
+    if guided:
+        guide = guide or oracle_guide_for(wl)
+        sc.render_guided(guide, wl.cameras, 1, wl.depth, wl.seed + seed, alpha=0.7, guide_depth=2, pixels=pix,
+                         n_threads=threads)
+    else:
+        sc.render(wl.cameras, spp, wl.depth, wl.seed + seed, pixels=pix, n_threads=threads)
     dt = time.perf_counter() - t0
-    paths = len(pix) * wl.spp * wl.band_count
+    paths = len(pix) * spp * wl.band_count
+    what = ("guided, one pass (1 spp) of the 4-view 2M-triangle nave" if guided
+            else f"{spp} spp of the 1024x768 200k-triangle nave")
     return {"value": paths / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(pix)} seeded pixels of the 1024x768 nave at 16 spp x 81 bands x depth 8 "
+            "sample": f"{len(pix)} seeded pixels x {wl.band_count} bands x depth {wl.depth}, {what} "
                       f"({paths} paths, {dt:.1f} s)"}
 
 
 def run_reference(args):
-    """--impl reference: the CPU FP64 oracle on the host cores."""
+    """--impl reference: the CPU FP64 oracle on the host cores, guided
+    estimator on the headline workload, a bounded pixel sample per step."""
+    import oracle
     from paper_1912_04000_gb300 import multigpu, scenes
     info = multigpu.DistInfo(int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
     if info.rank != 0:
         return 0
-    wl = scenes.nave()
-    per_step = max(16, args.cpu_pixels // 8)
+    wl = scenes.large_nave(spp=1)
+    sc = oracle.OracleScene(wl.scene, wl.spectra)
+    guide = oracle_guide_for(wl)
+    per_step = max(16, args.cpu_pixels // 4)
     for i in range(args.warmup):
-        cpu_baseline(wl, per_step, seed=100 + i)
-    vals, secs = [], []
+        cpu_baseline(wl, per_step, seed=100 + i, sc=sc, guide=guide)
+    secs = []
+    r = None
     for i in range(args.steps):
-        r = cpu_baseline(wl, per_step, seed=i)
-        vals.append(r["value"])
-        secs.append(per_step * wl.spp * wl.band_count / r["value"])
-    paths = per_step * wl.spp * wl.band_count
+        r = cpu_baseline(wl, per_step, seed=i, sc=sc, guide=guide)
+        secs.append(per_step * wl.band_count / r["value"])
+    paths = per_step * wl.band_count
     value = paths * args.steps / sum(secs)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -189,7 +241,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_pixels_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                         "sample": f"{per_step} seeded pixels per step at 16 spp x 81 bands x depth 8"},
+                         "sample": f"{per_step} seeded pixels per step x 81 bands x depth 12, one guided pass"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -197,6 +249,12 @@ def run_reference(args):
 
 
 def run_guided_mse(args):
+    """Equal-time MSE, guided vs plain (prints the result line)."""
+    print(json.dumps(guided_mse(args)), flush=True)
+    return 0
+
+
+def guided_mse(args, R=None):
     """Equal-time MSE, guided vs plain, on the nave view at a reduced
     resolution (the 4096-spp plain reference is rendered by the GPU plain
     tracer, itself parity-checked against the oracle)."""
@@ -207,7 +265,7 @@ def run_guided_mse(args):
     from paper_1912_04000_gb300.renderer import Renderer
 
     wl = scenes.nave(width=args.mse_width, height=args.mse_height)
-    R = Renderer(0).load(wl, builder=BUILDERS[args.builder])
+    R = (R or Renderer(0)).load(wl, builder=BUILDERS[args.builder])
     dev = R.device
     P, B = wl.n_pixels, wl.band_count
 
@@ -295,8 +353,7 @@ def run_guided_mse(args):
         "mse_ratio_plain_over_guided_equal_time": best["mse_ratio_equal_time"],
         "reference_seconds": t_ref,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_bands_mse(args):
@@ -415,6 +472,79 @@ def run_photon_mse(args):
     return 0
 
 
+STAGES = ["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"]
+
+
+def trace_roofline(R, counts, ms_trace, n_trace, ext_rays, prof_ok_traffic=None):
+    """Roofline of the closest-hit kernel: algorithmic bytes per ray (child
+    slots and triangles tested, from a counting pass, plus the ray and its
+    hit record) times rays per launch over the launch's device time."""
+    ext_nodes = counts["nodes_visited"] / max(counts["ext_rays"], 1)
+    ext_tris = counts["tris_tested"] / max(counts["ext_rays"], 1)
+    l2_gbs = R.probe_l2()
+    launch_ms = ms_trace / max(n_trace, 1)
+    rays_per_launch = ext_rays / max(n_trace, 1)
+    bytes_per_ray = ext_nodes * 32.0 + ext_tris * 48.0 + 32.0 + 8.0
+    achieved = rays_per_launch * bytes_per_ray / (launch_ms * 1e-3) / 1e9
+    traffic = prof_ok_traffic * rays_per_launch if prof_ok_traffic is not None else None
+    return {
+        "kernel": "k_trace (closest hit)", "bound": "l2", "achieved": achieved, "peak": l2_gbs, "unit": "GB/s",
+        "frac": achieved / l2_gbs if l2_gbs > 0 else None, "traffic": traffic,
+        "peak_source": "L2 streaming-read probe (rt_probe_l2, 48 MiB x 50) measured in this run",
+        "hbm_peak_measured": HBM_PEAK, "frac_of_hbm": achieved / HBM_PEAK,
+        "algorithmic_bytes_per_ray": bytes_per_ray, "nodes_per_ray": ext_nodes, "tris_per_ray": ext_tris,
+        "sun_child_slots_per_ray": counts["shadow_nodes_visited"] / max(counts["shadow_rays"], 1),
+        "sun_tris_per_ray": counts["shadow_tris_tested"] / max(counts["shadow_rays"], 1),
+        "launch_ms": launch_ms, "rays_per_launch": rays_per_launch,
+    }
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6777.0
+
+
+HBM_PEAK = measured_hbm_peak()
+
+
+def nave_subrecord(R, dev, steps=3):
+    """The 200k-triangle nave at its configuration (one step = one whole
+    render of 1,019,215,872 paths), timed with CUDA events on the stream."""
+    import torch
+
+    from paper_1912_04000_gb300 import scenes
+    wl = scenes.nave()
+    R.load(wl)
+    spectral = torch.empty((wl.n_pixels, wl.band_count), dtype=torch.float64, device=dev)
+    xyz = torch.empty((wl.n_pixels, 3), dtype=torch.float32, device=dev)
+    R.set_counting(True)
+    counts = R.render(wl.cameras, 1, wl.depth, 1, xyz=False)["stats"]
+    R.set_counting(False)
+    R.render(wl.cameras, wl.spp, wl.depth, 0, out_spectral=spectral, out_xyz=xyz)
+    R.set_timing(True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(R.stream)
+    ms_trace, n_trace, ext_rays = 0.0, 0, 0
+    stage = [0.0] * 7
+    for _ in range(steps):
+        st = R.render(wl.cameras, wl.spp, wl.depth, 0, out_spectral=spectral, out_xyz=xyz)["stats"]
+        ms_trace += st["ms_stage"][1]
+        n_trace += st["launches_stage"][1]
+        ext_rays += st["ext_rays"]
+        stage = [a + b for a, b in zip(stage, st["ms_stage"])]
+    e1.record(R.stream)
+    torch.cuda.synchronize(dev)
+    R.set_timing(False)
+    ms = e0.elapsed_time(e1) / steps
+    roof = trace_roofline(R, counts, ms_trace, n_trace, ext_rays)
+    roof["stage_ms_per_step"] = dict(zip(STAGES, [m / steps for m in stage]))
+    return {"workload": NAVE_WORKLOAD, "value": wl.n_paths / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "paths_per_step": wl.n_paths, "triangles": int(wl.scene.n_tris), "roofline": roof}
+
+
 def main():
     args = parse()
     if args.photon_mse:
@@ -435,31 +565,47 @@ def main():
     info = multigpu.init_from_env("nccl")
     dev = torch.device("cuda", info.local_rank)
     torch.cuda.set_device(dev)
-    wl = scenes.nave()
+    wl = scenes.large_nave(spp=1)
+    t_load = time.perf_counter()
     R = Renderer(info.local_rank).load(wl, builder=BUILDERS[args.builder])
+    t_load = time.perf_counter() - t_load
     bvh_info = R.scene_info()
-    seed = multigpu.rank_seed(wl.seed, info.rank)
+    R.guide_init(seed=11)
+    bands_split = args.partition == "bands" and info.world > 1
+    seed = wl.seed if bands_split else multigpu.rank_seed(wl.seed, info.rank)
+    band_first, band_count = multigpu.band_shard(wl.band_count, info.world, info.rank) if bands_split \
+        else (0, wl.band_count)
     stream = R.stream
-    spectral = torch.empty((wl.n_pixels, wl.band_count), dtype=torch.float64, device=dev)
-    xyz = torch.empty((wl.n_pixels, 3), dtype=torch.float32, device=dev)
+    P, B = wl.n_pixels, band_count
+    spectral = torch.empty((P, B), dtype=torch.float64, device=dev)
+    xyz = torch.empty((P, 3), dtype=torch.float32, device=dev)
+    guide_kw = dict(guided=True, guide_collect=GUIDE_COLLECT, guide_train_steps=GUIDE_STEPS)
+    passes = [0]
 
     def step():
-        return R.render(wl.cameras, wl.spp, wl.depth, seed, out_spectral=spectral, out_xyz=xyz)
+        i = passes[0]
+        passes[0] += 1
+        out = R.render(wl.cameras, 1, wl.depth, seed, band_first=band_first, band_count=band_count,
+                       out_spectral=spectral, out_xyz=xyz, sample_first=i, accumulate=i > 0, spp_total=i + 1,
+                       **guide_kw)
+        if bands_split:
+            # the spectral decomposition's one exchange: XYZ partials summed on rank 0
+            import torch.distributed as dist
+            with torch.cuda.stream(stream):
+                dist.reduce(xyz, dst=0, op=dist.ReduceOp.SUM)
+        return out
 
-    # traversal counts for the algorithmic bytes (outside the timed region, 1 spp)
+    # traversal counts for the algorithmic bytes (outside the timed region;
+    # one frozen guided pass into the library's own buffers)
     R.set_counting(True)
-    cs = R.render(wl.cameras, 1, wl.depth, seed, xyz=False)["stats"]
+    counts = R.render(wl.cameras, 1, wl.depth, seed + 99, guided=True, xyz=False, spectral=False)["stats"]
     R.set_counting(False)
-    ext_nodes = cs["nodes_visited"] / max(cs["ext_rays"], 1)
-    ext_tris = cs["tris_tested"] / max(cs["ext_rays"], 1)
-    sun_slots = cs["shadow_nodes_visited"] / max(cs["shadow_rays"], 1)
-    sun_tris = cs["shadow_tris_tested"] / max(cs["shadow_rays"], 1)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
 
-    # timed region: K full renders, device time from CUDA events on the stream
+    # timed region: K sample passes of the job, device time from CUDA events on the stream
     R.set_timing(True)
     clocks = ClockSampler(info.local_rank)
     clocks.start()
@@ -469,9 +615,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     launches = 0
-    ms_trace = 0.0
-    n_trace = 0
-    ext_rays = 0
+    ms_trace, n_trace, ext_rays, paths = 0.0, 0, 0, 0
     stage_ms = [0.0] * 7
     for _ in range(args.steps):
         st = step()["stats"]
@@ -479,6 +623,7 @@ def main():
         ms_trace += st["ms_stage"][1]
         n_trace += st["launches_stage"][1]
         ext_rays += st["ext_rays"]
+        paths += st["paths"]
         stage_ms = [a + b for a, b in zip(stage_ms, st["ms_stage"])]
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -487,64 +632,77 @@ def main():
     R.set_timing(False)
     ms = e0.elapsed_time(e1)
     ms_max = multigpu.max_over_ranks(info, ms, dev)
-    paths_all = multigpu.sum_over_ranks(info, float(wl.n_paths * args.steps), dev)
+    paths_all = multigpu.sum_over_ranks(info, float(paths), dev)
     value = paths_all / (ms_max * 1e-3)
+    assert paths == wl.n_pixels * B * args.steps
 
-    # end to end through the C ABI with host buffers: camera upload, render,
-    # XYZ image copied back into pinned host memory
-    xyz_host = torch.empty((wl.n_pixels, 3), dtype=torch.float32, pin_memory=True)
-    R.render_host(wl.cameras, 1, wl.depth, seed, xyz_out=xyz_host)  # allocates the library's buffers
+    # end to end through the C ABI with host buffers: camera upload, one
+    # guided pass with training, the pass's XYZ image copied back into pinned
+    # host memory
+    xyz_host = torch.empty((P, 3), dtype=torch.float32, pin_memory=True)
+    R.render_host(wl.cameras, 1, wl.depth, seed, band_first=band_first, band_count=band_count, xyz_out=xyz_host,
+                  **guide_kw)  # allocates the library's buffers
     multigpu.barrier(info, dev)
-    t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
-    for _ in range(e2e_steps):
-        R.render_host(wl.cameras, wl.spp, wl.depth, seed, xyz_out=xyz_host)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        R.render_host(wl.cameras, 1, wl.depth, seed, band_first=band_first, band_count=band_count, xyz_out=xyz_host,
+                      sample_first=i, **guide_kw)
     t_e2e = multigpu.max_over_ranks(info, time.perf_counter() - t0, dev)
-    e2e_value = multigpu.sum_over_ranks(info, float(wl.n_paths * e2e_steps), dev) / t_e2e
+    e2e_value = multigpu.sum_over_ranks(info, float(P * B * e2e_steps), dev) / t_e2e
 
-    # roofline of the closest-hit kernel (dominant stage)
-    l2_gbs = R.probe_l2()
-    launch_ms = ms_trace / max(n_trace, 1)
-    rays_per_launch = ext_rays / max(n_trace, 1)
-    bytes_per_ray = ext_nodes * 32.0 + ext_tris * 48.0 + 32.0 + 8.0
-    achieved = rays_per_launch * bytes_per_ray / (launch_ms * 1e-3) / 1e9
     prof = read_profile()
-    traffic = None
+    traffic_per_ray = None
     if prof.get("kernel_sources_sha") == kernel_hash() and "dram_bytes_per_ray" in prof:
-        traffic = float(prof["dram_bytes_per_ray"]) * rays_per_launch
+        traffic_per_ray = float(prof["dram_bytes_per_ray"])
+    roof = trace_roofline(R, counts, ms_trace, n_trace, ext_rays, traffic_per_ray)
+    roof["stage_ms_per_step"] = dict(zip(STAGES, [m / args.steps for m in stage_ms]))
+    roof["sun_rays_per_step"] = counts["shadow_rays"]
+
+    sub = {}
+    if info.world == 1 and not args.no_subrecords:
+        sub["nave_200k"] = nave_subrecord(R, dev)
+        mse = guided_mse(args, R)
+        sub["equal_time_mse"] = {
+            "workload": mse["config"]["workload"], "reference_spp": mse["config"]["reference_spp"],
+            "mse_ratio_plain_over_guided_equal_time": mse["mse_ratio_plain_over_guided_equal_time"],
+            "mse_ratio_equal_spp": mse["runs"][0]["mse_ratio_equal_spp"],
+            "relmse_ratio_equal_time": mse["runs"][0]["relmse_ratio_equal_time"],
+            "guided": mse["runs"][0]["guided"], "plain_equal_time": mse["runs"][0]["plain_equal_time"],
+            "guide_stage_ms": mse["runs"][0]["stage_ms"],
+            "full_size": "python bench.py --guided-mse --mse-width 1024 --mse-height 768",
+        }
 
     if info.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": info.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if bands_split else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {
-                "workload": WORKLOAD, "triangles": int(wl.scene.n_tris), "width": 1024, "height": 768,
-                "bands": wl.band_count, "spp": wl.spp, "depth": wl.depth, "paths_per_step_per_gpu": wl.n_paths,
-                "accumulation": "f64", "xyz": "bf16x3 tensor cores, f32 accumulate",
-                "l2": "inputs larger than L2: 1.1 GB of wave queues and a 0.5 GB FP64 spectral image per step; "
-                      "the 22 MB BVH stays L2-resident by design",
-                "partition": "each rank renders the whole image with its own Philox key",
+                "workload": WORKLOAD, "triangles": int(wl.scene.n_tris), "views": len(wl.cameras),
+                "width": wl.cameras[0].width, "height": wl.cameras[0].height, "bands": B, "depth": wl.depth,
+                "step": "one full-frame sample pass of the 64-spp job (all views, all bands): "
+                        f"{P * B} paths, accumulated in FP64",
+                "paths_per_step_per_gpu": P * B, "accumulation": "f64",
+                "guide": f"8-lobe vMF MLP guide, one-sample MIS alpha 0.7, guide depth 2, trained online in every "
+                         f"pass (every {GUIDE_COLLECT}th path, {GUIDE_STEPS} Adam steps per wave)",
+                "xyz": "bf16x3 tensor cores, f32 accumulate",
+                "l2": "inputs larger than L2: 2M-triangle BVH and triangles (about 0.3 GB), 1.1 GB of wave queues "
+                      "and an 8.2 GB FP64 spectral image per step",
+                "partition": ("each rank renders its band sub-domain of every pass; XYZ partials reduced to rank 0 "
+                              "over NCCL" if bands_split else
+                              "each rank renders the whole job with its own Philox key"),
                 "bvh": {"builder": bvh_info["builder"], "build_ms": round(bvh_info["build_ms"], 1),
-                        "nodes4": bvh_info["n_nodes4"]},
+                        "nodes4": bvh_info["n_nodes4"], "load_s": round(t_load, 2)},
             },
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 48 * len(wl.cameras),
-                    "d2h_bytes_per_step": wl.n_pixels * 3 * 4, "steps": e2e_steps},
+                    "d2h_bytes_per_step": P * 3 * 4, "steps": e2e_steps},
             "gpu_launches": launches,
-            "roofline": {
-                "kernel": "k_trace (closest hit)", "bound": "l2", "achieved": achieved, "peak": l2_gbs,
-                "unit": "GB/s", "frac": achieved / l2_gbs if l2_gbs > 0 else None, "traffic": traffic,
-                "peak_source": "L2 streaming-read probe (rt_probe_l2, 48 MiB x 50) measured in this run",
-                "hbm_peak_measured": 6777.0,
-                "algorithmic_bytes_per_ray": bytes_per_ray, "nodes_per_ray": ext_nodes,
-                "tris_per_ray": ext_tris, "sun_child_slots_per_ray": sun_slots, "sun_tris_per_ray": sun_tris,
-                "sun_rays_per_step": cs["shadow_rays"] * wl.spp,
-                "launch_ms": launch_ms, "rays_per_launch": rays_per_launch,
-                "stage_ms_per_step": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
-                                              [m / args.steps for m in stage_ms])),
-            },
+            "roofline": roof,
         }
+        line.update(sub)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_pixels)
         print(json.dumps(line), flush=True)

@@ -27,7 +27,10 @@ def test_large_nave_sampled_pixels(large):
     pixels, path by path against the oracle, held to the bar on every
     sampled pixel.  With 2M triangles more rays pass within FP32 rounding of
     a shared edge, so up to 1% of paths may take another triangle than the
-    FP64 oracle (measured 0.6%)."""
+    FP64 oracle (measured 0.6%); at one sample per pixel each diverged path
+    weighs 1/81 of its pixel, and the aggregate error over all sampled
+    pixels, diverged paths included, is 9.2e-5 (bound 2e-4).  Over the paths
+    that agree the bar holds as everywhere (restricted aggregate <= 1e-5)."""
     R, wl = large
     pix = crop_and_subset([(c.width, c.height) for c in wl.cameras], x0=992, y0=744, frac=0.001, seed=31)
     out = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, probe_pixels=pix, xyz_mode=2)
@@ -37,7 +40,7 @@ def test_large_nave_sampled_pixels(large):
                                                         pixels=pix.astype(np.uint32), record_paths=True)
     assert_sampled_parity(out["xyz"].cpu().numpy()[pix], o["xyz"], out["probe_L"].cpu().numpy(), o["path_L"],
                           out["probe_sig"].cpu().numpy().view(np.uint32), o["path_sig"], wl.spectra.cmf_w, wl.spp,
-                          "large nave crop + 0.1%", max_diverged=1e-2)
+                          "large nave crop + 0.1%", max_diverged=1e-2, max_mean_all=2e-4)
 
 
 def test_large_nave_guided_runs(large):
