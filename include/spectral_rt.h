@@ -100,7 +100,9 @@ typedef struct {
   uint32_t trace_variant;  /* traversal: 0 = four-wide BVH with leaf batching (interior steps
                             * until leaf_batch lanes of a warp wait at a leaf, then one leaf step
                             * for all of them); binary BVH with 1 = while-while, 2 = one node or
-                            * leaf per lane and step, 3 = leaf batching */
+                            * leaf per lane and step, 3 = leaf batching; 4 = closest hits over an
+                            * eight-wide BVH (children in corner slots visited in the ray's octant
+                            * order, leaf batching; host-built trees only), the same hits */
   /* persistent traversal warps refill idle lanes from the queue once at least
    * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
    * lane between refill checks; 0 = library default (tuned) */

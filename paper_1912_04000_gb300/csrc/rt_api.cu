@@ -29,9 +29,10 @@ struct rt_ctx {
   // scene
   float4* d_nodes = nullptr;
   float4* d_nodes4 = nullptr;
+  float4* d_nodes8 = nullptr;
   float4* d_tris = nullptr;
   float4* d_nrm = nullptr;
-  uint32_t n_nodes = 0, n_nodes4 = 0, n_tris = 0, n_mat = 0;
+  uint32_t n_nodes = 0, n_nodes4 = 0, n_nodes8 = 0, n_tris = 0, n_mat = 0;
   float eps = 0.0f;
   bool has_scene = false;
   uint32_t builder = 2;       // BVH builder for the next rt_load_scene: 0 host SAH, 1 device LBVH,
@@ -200,10 +201,12 @@ DevScene dev_scene(const rt_ctx* c) {
   DevScene S;
   S.nodes = c->d_nodes;
   S.nodes4 = c->d_nodes4;
+  S.nodes8 = c->d_nodes8;
   S.tris = c->d_tris;
   S.nrm = c->d_nrm;
   S.n_nodes = c->n_nodes;
   S.n_nodes4 = c->n_nodes4;
+  S.n_nodes8 = c->n_nodes8;
   for (int a = 0; a < 3; ++a) {
     S.blo[a] = c->lo[a];
     const float ext = c->hi[a] - c->lo[a];
@@ -328,6 +331,7 @@ void rt_destroy(rt_ctx* c) {
   else cudaDeviceSynchronize();
   dfree(c->d_nodes);
   dfree(c->d_nodes4);
+  dfree(c->d_nodes8);
   dfree(c->d_tris);
   dfree(c->d_nrm);
   dfree(c->d_mb);
@@ -530,6 +534,7 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   }
   std::vector<float4> nd;
   std::vector<Bvh4Node> b4;
+  std::vector<float4> d8;  // eight-wide nodes in device layout (14 float4 each)
   if (!dev_build) {
     nd.resize(2 * bvh.nodes.size());
     for (size_t i = 0; i < bvh.nodes.size(); ++i) {
@@ -560,11 +565,42 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
         }
         n4.cnt[i] = 0;
       }
+    // eight-wide nodes, padded the same way: the plane float4s (per axis lo
+    // of children 0-3, 4-7, hi of 0-3, 4-7), then the children packed
+    std::vector<Bvh8Node> b8;
+    collapse_bvh8(bvh, b8, nullptr);
+    d8.resize(14 * b8.size());
+    for (size_t j = 0; j < b8.size(); ++j) {
+      Bvh8Node& n8 = b8[j];
+      uint32_t pk[8];
+      for (int i = 0; i < 8; ++i) {
+        if (n8.cnt[i] != kEmpty4) {
+          n8.lox[i] = down(n8.lox[i]);
+          n8.loy[i] = down(n8.loy[i]);
+          n8.loz[i] = down(n8.loz[i]);
+          n8.hix[i] = up(n8.hix[i]);
+          n8.hiy[i] = up(n8.hiy[i]);
+          n8.hiz[i] = up(n8.hiz[i]);
+          pk[i] = (n8.ref[i] << 3) | n8.cnt[i];
+        } else {
+          pk[i] = 0;
+        }
+      }
+      float4* o = &d8[14 * j];
+      const float* planes[6] = {n8.lox, n8.hix, n8.loy, n8.hiy, n8.loz, n8.hiz};
+      for (int q = 0; q < 6; ++q) {
+        o[2 * q] = make_float4(planes[q][0], planes[q][1], planes[q][2], planes[q][3]);
+        o[2 * q + 1] = make_float4(planes[q][4], planes[q][5], planes[q][6], planes[q][7]);
+      }
+      std::memcpy(&o[12], pk, 32);
+    }
   }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   dfree(c->d_nodes);
   dfree(c->d_nodes4);
+  dfree(c->d_nodes8);
+  c->n_nodes8 = 0;
   dfree(c->d_tris);
   dfree(c->d_nrm);
   c->has_scene = false;
@@ -574,6 +610,9 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     CUDA_TRY(c, cudaMalloc(&c->d_nodes, nd.size() * sizeof(float4)));
     CUDA_TRY(c, cudaMalloc(&c->d_nodes4, b4.size() * sizeof(Bvh4Node)));
     CUDA_TRY(c, cudaMemcpy(c->d_nodes4, b4.data(), b4.size() * sizeof(Bvh4Node), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMalloc(&c->d_nodes8, d8.size() * sizeof(float4)));
+    CUDA_TRY(c, cudaMemcpy(c->d_nodes8, d8.data(), d8.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    c->n_nodes8 = (uint32_t)(d8.size() / 14);
     CUDA_TRY(c, cudaMemcpy(c->d_nodes, nd.data(), nd.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_tris, tr.data(), tr.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_nrm, nr.data(), nr.size() * sizeof(float4), cudaMemcpyHostToDevice));
@@ -807,7 +846,9 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
   if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
-  if (o.trace_variant > 3) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant > 4) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant == 4 && !c->d_nodes8)
+    return fail(c, RT_ERR_ARG, "rt_render: the eight-wide tree needs a host-built BVH (builder 0 or 2)");
   if (o.trace_variant != 0 && !c->d_nodes)
     return fail(c, RT_ERR_ARG, "rt_render: binary-tree traversal variants need the host-built BVH");
   if (o.leaf_batch > 32) return fail(c, RT_ERR_ARG, "rt_render: leaf_batch is 1..32");

@@ -643,4 +643,112 @@ int collapse_bvh4(const BvhOut& b2, std::vector<Bvh4Node>& out, uint32_t* max_de
   return 0;
 }
 
+int collapse_bvh8(const BvhOut& b2, std::vector<Bvh8Node>& out, uint32_t* max_depth) {
+  const std::vector<BvhNode>& nb = b2.nodes;
+  auto area = [&](uint32_t i) {
+    const BvhNode& b = nb[i];
+    const double dx = b.hi[0] - b.lo[0], dy = b.hi[1] - b.lo[1], dz = b.hi[2] - b.lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  };
+  out.clear();
+  out.reserve(nb.size() / 4 + 1);
+  struct Item {
+    uint32_t b2node, slot, depth;
+  };
+  std::vector<Item> todo;
+  out.push_back(Bvh8Node{});
+  todo.push_back({1u, 0u, 1u});
+  uint32_t md = 0;
+  while (!todo.empty()) {
+    const Item it = todo.back();
+    todo.pop_back();
+    md = std::max(md, it.depth);
+    uint32_t ch[8];
+    int n = 0;
+    if (nb[it.b2node].count != 0) {
+      ch[n++] = it.b2node;  // a root that is a leaf
+    } else {
+      ch[n++] = nb[it.b2node].ref;
+      ch[n++] = nb[it.b2node].ref + 1;
+      while (n < 8) {
+        int best = -1;
+        double ba = -1.0;
+        for (int i = 0; i < n; ++i)
+          if (nb[ch[i]].count == 0 && area(ch[i]) > ba) {
+            ba = area(ch[i]);
+            best = i;
+          }
+        if (best < 0) break;
+        const uint32_t r = nb[ch[best]].ref;
+        ch[best] = r;
+        ch[n++] = r + 1;
+      }
+    }
+    // corner slots
+    double plo[3] = {INFINITY, INFINITY, INFINITY}, phi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) {
+        plo[a] = std::min(plo[a], (double)nb[ch[i]].lo[a]);
+        phi[a] = std::max(phi[a], (double)nb[ch[i]].hi[a]);
+      }
+    double score[8][8];
+    for (int i = 0; i < n; ++i)
+      for (int sl = 0; sl < 8; ++sl) {
+        double sc = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const double ext = phi[a] - plo[a];
+          const double d = ext > 0.0 ? ((double)nb[ch[i]].lo[a] + nb[ch[i]].hi[a] - plo[a] - phi[a]) / ext : 0.0;
+          sc += ((sl >> a) & 1) ? d : -d;
+        }
+        score[i][sl] = sc;
+      }
+    int slot_of[8];
+    bool used_c[8] = {false}, used_s[8] = {false};
+    for (int k = 0; k < n; ++k) {
+      int bi = -1, bs = -1;
+      double bv = -INFINITY;
+      for (int i = 0; i < n; ++i)
+        if (!used_c[i])
+          for (int sl = 0; sl < 8; ++sl)
+            if (!used_s[sl] && score[i][sl] > bv) {
+              bv = score[i][sl];
+              bi = i;
+              bs = sl;
+            }
+      used_c[bi] = used_s[bs] = true;
+      slot_of[bi] = bs;
+    }
+    Bvh8Node nd{};
+    for (int sl = 0; sl < 8; ++sl) {
+      nd.lox[sl] = nd.loy[sl] = nd.loz[sl] = INFINITY;
+      nd.hix[sl] = nd.hiy[sl] = nd.hiz[sl] = -INFINITY;
+      nd.ref[sl] = 0;
+      nd.cnt[sl] = kEmpty4;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int sl = slot_of[i];
+      const BvhNode& b = nb[ch[i]];
+      nd.lox[sl] = b.lo[0];
+      nd.loy[sl] = b.lo[1];
+      nd.loz[sl] = b.lo[2];
+      nd.hix[sl] = b.hi[0];
+      nd.hiy[sl] = b.hi[1];
+      nd.hiz[sl] = b.hi[2];
+      if (b.count != 0) {
+        nd.ref[sl] = b.ref;
+        nd.cnt[sl] = b.count;
+      } else {
+        const uint32_t slot = (uint32_t)out.size();
+        out.push_back(Bvh8Node{});
+        nd.ref[sl] = slot;
+        nd.cnt[sl] = 0;
+        todo.push_back({ch[i], slot, it.depth + 1});
+      }
+    }
+    out[it.slot] = nd;
+  }
+  if (max_depth) *max_depth = md;
+  return 0;
+}
+
 }  // namespace srt

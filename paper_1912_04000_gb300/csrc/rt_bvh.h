@@ -47,4 +47,22 @@ static_assert(sizeof(Bvh4Node) == 128, "128-byte node");
 // has four.  Leaves and the leaf order are those of the binary tree.
 int collapse_bvh4(const BvhOut& b2, std::vector<Bvh4Node>& out, uint32_t* max_depth);
 
+// Eight-wide node: the same child encoding as the four-wide node, the
+// planes of each axis as lo of the eight children then hi of the eight.
+// Slot s holds the child that lies towards the corner ((s & 1) ? +x : -x,
+// (s & 2) ? +y : -y, (s & 4) ? +z : -z) of the node, so that a ray that
+// visits slots in the order i ^ octant meets the near corner first.
+struct Bvh8Node {
+  float lox[8], hix[8], loy[8], hiy[8], loz[8], hiz[8];
+  uint32_t ref[8], cnt[8];
+};
+static_assert(sizeof(Bvh8Node) == 256, "256-byte host node");
+
+// Collapses the binary BVH into an eight-wide one (node 0 the root) by the
+// greedy rule of collapse_bvh4 with up to eight children, then places the
+// children in the corner slots: repeatedly the free (child, slot) pair whose
+// child centre, relative to the node centre and scaled by the node's extent
+// per axis, points furthest towards the slot's corner.
+int collapse_bvh8(const BvhOut& b2, std::vector<Bvh8Node>& out, uint32_t* max_depth);
+
 }  // namespace srt

@@ -36,10 +36,12 @@ constexpr uint32_t kMaxWave = 1u << kPidBits;
 struct DevScene {
   const float4* nodes;   // binary BVH: 2 float4 per node, node 1 the root
   const float4* nodes4;  // four-wide BVH: 8 float4 per node, node 0 the root
+  const float4* nodes8;  // eight-wide BVH: 14 float4 per node, node 0 the root (host builds; else null)
   const float4* tris;
   const float4* nrm;
   uint32_t n_nodes;
   uint32_t n_nodes4;
+  uint32_t n_nodes8;
   uint32_t n_tris;
   float blo[3], binv[3];  // scene box: lower corner and 1 / extent per axis
   float eps;  // origin offset along the normal: 1e-4 x scene diagonal

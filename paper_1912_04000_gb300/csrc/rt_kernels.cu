@@ -256,6 +256,69 @@ __device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const Dev
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Eight-wide BVH (node = 14 float4: per axis the lo planes of children 0-3
+// and 4-7, then their hi planes, then the eight children packed as
+// ref << 3 | count).  The builder puts in slot s the child that lies towards
+// the corner ((s & 1) ? +x : -x, (s & 2) ? +y : -y, (s & 4) ? +z : -z) of the
+// node, so visiting the entered children in the order s = i ^ oct meets the
+// corner nearest to the ray first without a per-ray sort: the first entered
+// child in that order is descended into, the others pushed with the next one
+// on top.  Half a node (children 0-3, then 4-7) is tested at a time.
+// ---------------------------------------------------------------------------
+template <bool FMA, bool COUNT>
+__device__ __forceinline__ bool trav_interior8(Trav& tv, uint2* stack, const DevScene& S, float tmax,
+                                               uint32_t* status, uint32_t& n_nodes) {
+  const float4* nd = S.nodes8 + 14u * tv.ref;
+  const uint32_t ox = (tv.oct & 1u) << 1, oy = tv.oct & 2u, oz = (tv.oct >> 1) & 2u;
+  if (COUNT) n_nodes += 8;
+  float t[8];
+#pragma unroll
+  for (uint32_t h = 0; h < 2; ++h) {
+    const float4 nx = ldg4(nd + ox + h), fx = ldg4(nd + (ox ^ 2u) + h);
+    const float4 ny = ldg4(nd + 4u + oy + h), fy = ldg4(nd + 4u + (oy ^ 2u) + h);
+    const float4 nz = ldg4(nd + 8u + oz + h), fz = ldg4(nd + 8u + (oz ^ 2u) + h);
+    t[4 * h] = child_t<FMA>(tv, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, tmax);
+    t[4 * h + 1] = child_t<FMA>(tv, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y, tmax);
+    t[4 * h + 2] = child_t<FMA>(tv, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z, tmax);
+    t[4 * h + 3] = child_t<FMA>(tv, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w, tmax);
+  }
+  uint32_t m = 0;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) m |= (t[s] < INFINITY ? 1u : 0u) << s;
+  if (m == 0u) return false;
+  const int nh = __popc(m);
+  if (tv.sp + nh - 1 > kStack) {
+    atomicOr(status, ST_STACK);
+    tv.sp = 0;
+    return false;
+  }
+  const uint4 pa = __ldg((const uint4*)(nd + 12)), pb = __ldg((const uint4*)(nd + 13));
+  const uint32_t p[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+  // the entered slots in visit order: bit i of v is slot i ^ oct
+  uint32_t v = m;
+  if (tv.oct & 1u) v = ((v & 0x55u) << 1) | ((v >> 1) & 0x55u);
+  if (tv.oct & 2u) v = ((v & 0x33u) << 2) | ((v >> 2) & 0x33u);
+  if (tv.oct & 4u) v = ((v & 0x0Fu) << 4) | ((v >> 4) & 0x0Fu);
+  // visit rank r >= 1 goes to stack[top - r], rank 1 on top
+  const int top = tv.sp + nh - 1;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    if (t[s] < INFINITY) {
+      const uint32_t i = (uint32_t)s ^ tv.oct;
+      const int r = __popc(v & ((1u << i) - 1u));
+      if (r == 0) {
+        tv.ref = p[s] >> 3;
+        tv.cnt = p[s] & 7u;
+      } else {
+        stack[top - r] = make_uint2(p[s], __float_as_uint(t[s]));
+      }
+    }
+  }
+  tv.sp += nh - 1;
+  return true;
+}
+
 template <bool W4, bool FMA, bool COUNT, bool ANY = false>
 __device__ __forceinline__ bool interior_w(Trav& tv, uint2* stack, const DevScene& S, float tmax, uint32_t* status,
                                            uint32_t& n_nodes) {
@@ -634,8 +697,8 @@ constexpr bool kShadowAnyOrder = false;
 // interior node until at least `leaf_min` lanes wait at a leaf (or none can
 // go on), then one leaf step for every waiting lane, so that the costly
 // triangle tests run with most of their lanes busy; 3 (the default, render
-// option trace_variant 0): as 2 over the four-wide BVH.  Modes 0-2 traverse
-// the binary BVH.
+// option trace_variant 0): as 2 over the four-wide BVH; 4 (trace_variant 4):
+// as 2 over the eight-wide BVH.  Modes 0-2 traverse the binary BVH.
 template <bool FMA, bool COUNT, int MODE>
 __global__ void __launch_bounds__(kTraceMaxThreads, kTraceMinBlocks) k_trace(DevScene S, const float4* __restrict__ q, float2* __restrict__ hit,
                                                Counters* cnt, uint32_t k, uint32_t cap, Totals* tot,
@@ -664,7 +727,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, kTraceMinBlocks) k_trace(Dev
         if (slot < count) {
           const uint32_t ri = perm ? __ldg(perm + slot) : slot;
           const float4 a = __ldcs(q + 2 * ri), b = __ldcs(q + 2 * ri + 1);
-          if (init_w<MODE == 3, FMA>(tv, S, f3(a), f3(b))) {
+          if (init_w<MODE >= 3, FMA>(tv, S, f3(a), f3(b))) {
             ray = ri;
           } else {
             __stcs(hit + ri, make_float2(-1.0f, __int_as_float(-1)));
@@ -692,7 +755,8 @@ __global__ void __launch_bounds__(kTraceMaxThreads, kTraceMinBlocks) k_trace(Dev
           } else if (leaf_phase) {
             closest_leaf(tv, S, nt, COUNT);
             done = !trav_pop(tv, stack, tv.best_t);
-          } else if (!interior_w<MODE == 3, FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)) {
+          } else if (!(MODE == 4 ? trav_interior8<FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)
+                                 : interior_w<MODE == 3, FMA, COUNT>(tv, stack, S, tv.best_t, status, nn))) {
             done = !trav_pop(tv, stack, tv.best_t);
           }
         }
@@ -1636,7 +1700,8 @@ void trace_t(const LaunchCfg& lc, const DevScene& S, const float4* qin, const Wa
 template <bool FMA, bool COUNT>
 void trace_m(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
              cudaStream_t st) {
-  if (lc.variant == 3) trace_t<FMA, COUNT, 2>(lc, S, qin, b, k, st);
+  if (lc.variant == 4) trace_t<FMA, COUNT, 4>(lc, S, qin, b, k, st);
+  else if (lc.variant == 3) trace_t<FMA, COUNT, 2>(lc, S, qin, b, k, st);
   else if (lc.variant == 2) trace_t<FMA, COUNT, 0>(lc, S, qin, b, k, st);
   else if (lc.variant == 1) trace_t<FMA, COUNT, 1>(lc, S, qin, b, k, st);
   else trace_t<FMA, COUNT, 3>(lc, S, qin, b, k, st);
@@ -1669,6 +1734,7 @@ void shadow_m(const LaunchCfg& lc, const DevScene& S, const DevSpectra& P, const
   // four bands per path: the four-wide tree with leaf batching (the host
   // refuses other traversal variants there)
   if (w.nb == 4u) shadow_t<RECORD, COUNT, 3, 4>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
+  // (the eight-wide variant 4 changes the closest-hit traversal only)
   else if (lc.variant == 3) shadow_t<RECORD, COUNT, 2>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   else if (lc.variant == 2) shadow_t<RECORD, COUNT, 0>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);
   else if (lc.variant == 1) shadow_t<RECORD, COUNT, 1>(lc, S, P, w, k, b, accum, probe, Lf, gw, st);

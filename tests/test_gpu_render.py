@@ -102,6 +102,16 @@ def test_ray_order_changes_nothing(R):
     assert np.array_equal(a, b)
 
 
+def test_eight_wide_tree_same_bits(R):
+    """The eight-wide tree (trace_variant 4, closest hit only) returns the
+    same closest hits as the four-wide one, so the render is bit-identical."""
+    wl = scenes.nave(width=64, height=48, n_bands=8, spp=2)
+    R.load(wl)
+    a = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)["spectral"].cpu().numpy()
+    b = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2, trace_variant=4)["spectral"].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
 def test_traversal_loop_variants_agree(R):
     """Loop shape (while-while, leaf batching or one node per step, steps
     between refills, refill threshold, leaf batch) changes only scheduling:
