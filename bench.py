@@ -96,7 +96,7 @@ def parse():
     ap.add_argument("--mis-alpha", type=float, default=0.7)
     ap.add_argument("--mse-configs", default="",
                     help="extra guide settings depth:collect:steps:alpha[:train_spp[:order]] separated by ';' "
-                         "(one shared reference; order 1 = queue order of the guide queries)")
+                         "(one shared reference; order 1 = guide queries sorted by position)")
     return ap.parse_args()
 
 
@@ -333,7 +333,7 @@ def guided_mse(args, R=None):
         p_xyz = p_out["xyz"].cpu().numpy().astype(np.float64)
         results.append({
             "guide_depth": depth_g, "guide_collect": collect, "guide_steps_per_wave": steps, "mis_alpha": alpha,
-            "guide_order": "queue" if order else "spatial",
+            "guide_order": "spatial" if order else "queue",
             "train_spp": n_train,
             "stage_ms": dict(zip(["camera", "closest_hit", "shade_nee", "sun_rays", "xyz", "guide", "train"],
                                  [round(v_, 1) for v_ in stage])),

@@ -121,8 +121,9 @@ typedef struct {
   uint32_t accumulate;
   uint32_t spp_total;
   uint32_t leaf_batch;     /* trace_variant 0: 1..32 waiting lanes start a leaf phase; 0 = default */
-  uint32_t guide_order;    /* guided: 0 = guide queries sorted by position (Morton order of a 64^3
-                            * grid) before the network runs, 1 = queue order */
+  uint32_t guide_order;    /* guided: 0 = guide queries in queue order (the default: measured
+                            * faster), 1 = sorted by position first (Morton order of a 64^3 grid,
+                            * so that a tile's hash-grid gathers share cache lines); the same bits */
   uint32_t ray_order;      /* 0 = queue order; 1 = rays of vertices >= 2 and sun rays traced in the
                             * order of a counting sort by origin cell (and direction octant): the
                             * same result, measured no faster on the nave */

@@ -121,6 +121,8 @@ def lib():
             L.or_guide_loss_grad.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_uint64, fp, fp,
                                              up, fp, fp, C.c_int, dp, dp]
             L.or_guide_density.argtypes = [dp, C.c_uint64, dp, dp]
+            L.or_adam_step.argtypes = [C.c_uint64, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       C.c_uint32]
             L.or_guide_net_create.restype = C.c_void_p
             L.or_guide_net_create.argtypes = [C.c_uint32, fp, fp, C.c_float, C.c_float, fp, fp, C.c_int]
             L.or_guide_net_destroy.argtypes = [C.c_void_p]
@@ -408,6 +410,15 @@ def guide_loss_grad(log2_T, lo, hi, grid, W, pos, nrm, group, omega, wt, n_min=1
                                     _ptr(g, C.c_uint32), fp(omega), fp(wt), 1 if bf16_act else 0, dp(dW),
                                     dp(dgrid))
     return loss, dW, dgrid
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.99, eps=1e-15):
+    """One Adam step on float64 arrays p, m, v (updated in place) with gradient g at step t >= 1."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    dp = lambda a: _ptr(a, C.c_double)
+    lib().or_adam_step(p.size, dp(p), dp(g), dp(m), dp(v), lr, b1, b2, eps, t)
 
 
 def guide_density(Y, omega):

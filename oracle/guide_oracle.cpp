@@ -341,6 +341,19 @@ double or_guide_loss_grad(uint32_t log2_T, const float* lo, const float* hi, flo
   return loss;
 }
 
+// One Adam step (Kingma and Ba, 2015) on n parameters in place: first and
+// second moment estimates m, v with decay rates b1, b2, bias-corrected by
+// 1 - b^t for step t >= 1, then p -= lr m_hat / (sqrt(v_hat) + eps).
+void or_adam_step(uint64_t n, double* p, const double* g, double* m, double* v, double lr, double b1, double b2,
+                  double eps, uint32_t t) {
+  const double c1 = 1.0 - std::pow(b1, (double)t), c2 = 1.0 - std::pow(b2, (double)t);
+  for (uint64_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    p[i] -= lr * (m[i] / c1) / (std::sqrt(v[i] / c2) + eps);
+  }
+}
+
 // Mixture density of given head outputs Y [48] at n directions (for
 // quadrature checks of the normalisation).
 void or_guide_density(const double* Y, uint64_t n, const double* omega, double* q) {

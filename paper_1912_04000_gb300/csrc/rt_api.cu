@@ -955,7 +955,7 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
     if (!G.bins) CUDA_TRY(c, cudaMalloc(&G.bins, (size_t)(kGuideSortBins + kGuideSortBins / 1024u) * sizeof(uint32_t)));
     gw.gq = G.gq;
     gw.wesc = G.wesc;
-    if (o.guide_order == 0) {
+    if (o.guide_order == 1) {
       gw.perm = G.perm;
       gw.skey = G.skey;
       gw.bins = G.bins;

@@ -790,7 +790,13 @@ constexpr int kSampleThreads = 2 * kRows;              // two threads per query
 constexpr int kXch = 12;                               // head exchange floats per query
 constexpr uint32_t kSmXch = kSmWf + kATileB;           // one activation tile, updated in place
 constexpr uint32_t kSampleSmem = kSmXch + kRows * kXch * 4u + 128u;
-constexpr int kSampleCtasPerSm = 4;
+// three CTAs per SM (85 registers, no spills): measured 614 ms per guided
+// sample pass of the 2M-triangle nave against 911 ms with four (64
+// registers, spilled) and 668 ms with two, queries in queue order
+#ifndef SRT_GUIDE_SAMPLE_CTAS
+#define SRT_GUIDE_SAMPLE_CTAS 3
+#endif
+constexpr int kSampleCtasPerSm = SRT_GUIDE_SAMPLE_CTAS;
 
 // Guided continuation at the wave's guide queries of vertex k.  A CTA takes
 // tiles of 128 queries; thread t serves query t % 128 as half h = t / 128

@@ -822,8 +822,15 @@ __device__ __forceinline__ float photon_gather(const PhotonMaps& M, uint32_t map
 // PM: photon-mapping camera pass -- at the first Lambertian vertex the path
 // adds (rho / pi) x the photon irradiance of both maps of pm and ends (its
 // sun ray, if any, finishes it).
+// three blocks of 256 per SM (<= 85 registers, no spills; unbounded, the
+// one-band shading took 102 registers and two blocks): measured 291 instead
+// of 304 ms per guided pass of the 2M-triangle nave, 375 instead of 377 ms
+// per render of the nave; four blocks (64 registers, spilled) were slower
+#ifndef SRT_SHADE_MIN_BLOCKS
+#define SRT_SHADE_MIN_BLOCKS 3
+#endif
 template <bool RECORD, bool GUIDED, bool PM = false>
-__global__ void __launch_bounds__(256) k_shade(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
+__global__ void __launch_bounds__(256, SRT_SHADE_MIN_BLOCKS) k_shade(DevScene S, DevSpectra P, WaveParams w, uint32_t k,
                                                const float4* __restrict__ qin, const float2* __restrict__ hit,
                                                float4* __restrict__ qout, float4* __restrict__ sq,
                                                float* __restrict__ Lbuf, uint32_t* __restrict__ sigbuf,

@@ -52,7 +52,7 @@ def test_guided_is_unbiased(R, trained):
 def test_query_order_changes_nothing(R):
     """With a frozen guide every query is evaluated on its own (one MMA row,
     its own Philox counters), so sorting the queries by position before the
-    network runs changes no bit of the image."""
+    network runs (guide_order 1) changes no bit of the image."""
     wl = scenes.nave(width=96, height=64, n_bands=9, spp=2, depth=4)
     R.load(wl)
     R.guide_init(seed=3, log2_table=16)

@@ -131,3 +131,29 @@ def test_sh_inputs_orthonormal():
     S = X[:, 32:48]
     G = (S * w[:, None]).T @ S
     np.testing.assert_allclose(G, np.eye(16), atol=2e-6)
+
+
+def test_adam_closed_forms():
+    """Adam's bias correction makes a constant gradient g give m_hat = g and
+    v_hat = g^2 at every step, so each step moves every parameter by
+    lr g / (|g| + eps): lr sign(g) for |g| >> eps, nothing where g = 0."""
+    rng = np.random.default_rng(7)
+    n = 1000
+    p0 = rng.normal(size=n)
+    g = rng.normal(size=n) * 10.0 ** rng.uniform(-3, 2, n)
+    g[::17] = 0.0
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    lr = 1e-2
+    for t in range(1, 6):
+        oracle.adam_step(p, g, m, v, t, lr)
+        np.testing.assert_allclose(p, p0 - t * lr * g / (np.abs(g) + 1e-15), rtol=0, atol=1e-12)
+    # a gradient that changes: first step still lr sign(g1); the second moves
+    # by lr m_hat / sqrt(v_hat) with the hand-computed moments
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    g2 = -0.5 * g
+    oracle.adam_step(p, g, m, v, 1, lr)
+    oracle.adam_step(p, g2, m, v, 2, lr)
+    m_hat = (0.9 * 0.1 * g + 0.1 * g2) / (1 - 0.9 ** 2)
+    v_hat = (0.99 * 0.01 * g * g + 0.01 * g2 * g2) / (1 - 0.99 ** 2)
+    want = p0 - lr * g / (np.abs(g) + 1e-15) - lr * np.divide(m_hat, np.sqrt(v_hat) + 1e-15)
+    np.testing.assert_allclose(p, want, rtol=0, atol=1e-10)
