@@ -102,7 +102,9 @@ typedef struct {
                             * for all of them); binary BVH with 1 = while-while, 2 = one node or
                             * leaf per lane and step, 3 = leaf batching; 4 = closest hits over an
                             * eight-wide BVH (children in corner slots visited in the ray's octant
-                            * order, leaf batching; host-built trees only), the same hits */
+                            * order, leaf batching; host-built trees only); 5 = closest hits over
+                            * the four-wide BVH stored with 8-bit child boxes (64-byte nodes; host-
+                            * built trees only).  Every variant returns the same hits */
   /* persistent traversal warps refill idle lanes from the queue once at least
    * *_refill (1..32) lanes are idle, and run up to *_steps (>= 1) steps per
    * lane between refill checks; 0 = library default (tuned) */

@@ -30,6 +30,7 @@ struct rt_ctx {
   float4* d_nodes = nullptr;
   float4* d_nodes4 = nullptr;
   float4* d_nodes8 = nullptr;
+  float4* d_nodes4q = nullptr;  // four-wide nodes with 8-bit quantised child boxes (4 float4 each)
   float4* d_tris = nullptr;
   float4* d_nrm = nullptr;
   uint32_t n_nodes = 0, n_nodes4 = 0, n_nodes8 = 0, n_tris = 0, n_mat = 0;
@@ -202,6 +203,7 @@ DevScene dev_scene(const rt_ctx* c) {
   S.nodes = c->d_nodes;
   S.nodes4 = c->d_nodes4;
   S.nodes8 = c->d_nodes8;
+  S.nodes4q = c->d_nodes4q;
   S.tris = c->d_tris;
   S.nrm = c->d_nrm;
   S.n_nodes = c->n_nodes;
@@ -331,6 +333,7 @@ void rt_destroy(rt_ctx* c) {
   else cudaDeviceSynchronize();
   dfree(c->d_nodes);
   dfree(c->d_nodes4);
+  dfree(c->d_nodes4q);
   dfree(c->d_nodes8);
   dfree(c->d_tris);
   dfree(c->d_nrm);
@@ -535,6 +538,7 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   std::vector<float4> nd;
   std::vector<Bvh4Node> b4;
   std::vector<float4> d8;  // eight-wide nodes in device layout (14 float4 each)
+  std::vector<float4> d4q;  // four-wide nodes with 8-bit child boxes (4 float4 each)
   if (!dev_build) {
     nd.resize(2 * bvh.nodes.size());
     for (size_t i = 0; i < bvh.nodes.size(); ++i) {
@@ -565,6 +569,59 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
         }
         n4.cnt[i] = 0;
       }
+    // four-wide nodes with 8-bit child boxes: per axis a power-of-two cell
+    // 2^e >= extent / 250 and an origin two cells below the node's lowest
+    // padded plane (a float, rounded down); each child's padded planes
+    // rounded outward to the grid and one more cell out on each side, a
+    // margin that covers the traversal's half-cell rounding of the decoded
+    // planes.  Layout: {origin, bits(e_x | e_y << 8 | e_z << 16)}, {lo x of
+    // children 0-3, hi x, lo y, hi y} as bytes, {lo z, hi z, 0, 0}, children.
+    d4q.resize(4 * b4.size());
+    for (size_t j = 0; j < b4.size(); ++j) {
+      const Bvh4Node& n4 = b4[j];
+      const float* plo[3] = {n4.lox, n4.loy, n4.loz};
+      const float* phi[3] = {n4.hix, n4.hiy, n4.hiz};
+      float org[3];
+      uint32_t ebits = 0;
+      uint32_t words[6] = {0, 0, 0, 0, 0, 0};  // lo x, hi x, lo y, hi y, lo z, hi z
+      for (int a = 0; a < 3; ++a) {
+        double L = INFINITY, H = -INFINITY;
+        for (int i = 0; i < 4; ++i) {
+          if (plo[a][i] > phi[a][i]) continue;  // empty slot (lo +inf, hi -inf)
+          L = std::min(L, (double)plo[a][i]);
+          H = std::max(H, (double)phi[a][i]);
+        }
+        if (!(L <= H)) L = H = 0.0;  // no child (cannot happen below the root of a non-empty scene)
+        const double ext = std::max(H - L, 1e-30);
+        int e = (int)std::ceil(std::log2(ext / 250.0));
+        e = std::max(-120, std::min(120, e));
+        const double scale = std::ldexp(1.0, e);
+        const double o = L - 2.0 * scale;
+        float of = (float)o;
+        while ((double)of > o) of = std::nextafter(of, -INFINITY);
+        org[a] = of;
+        ebits |= ((uint32_t)(uint8_t)(int8_t)e) << (8 * a);
+        for (int i = 0; i < 4; ++i) {
+          uint32_t ql = 255u, qh = 0u;  // empty slot: never entered
+          if (!(plo[a][i] > phi[a][i])) {
+            const double fl = std::floor(((double)plo[a][i] - (double)of) / scale) - 1.0;
+            const double fh = std::ceil(((double)phi[a][i] - (double)of) / scale) + 1.0;
+            ql = (uint32_t)std::max(0.0, std::min(255.0, fl));
+            qh = (uint32_t)std::max(0.0, std::min(255.0, fh));
+          }
+          words[2 * a] |= ql << (8 * i);
+          words[2 * a + 1] |= qh << (8 * i);
+        }
+      }
+      float4* o4 = &d4q[4 * j];
+      float eb, w[6];
+      std::memcpy(&eb, &ebits, 4);
+      std::memcpy(w, words, 24);
+      o4[0] = make_float4(org[0], org[1], org[2], eb);
+      o4[1] = make_float4(w[0], w[1], w[2], w[3]);
+      o4[2] = make_float4(w[4], w[5], 0.0f, 0.0f);
+      std::memcpy(&o4[3], n4.ref, 16);
+    }
     // eight-wide nodes, padded the same way: the plane float4s (per axis lo
     // of children 0-3, 4-7, hi of 0-3, 4-7), then the children packed
     std::vector<Bvh8Node> b8;
@@ -600,6 +657,7 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
   dfree(c->d_nodes);
   dfree(c->d_nodes4);
   dfree(c->d_nodes8);
+  dfree(c->d_nodes4q);
   c->n_nodes8 = 0;
   dfree(c->d_tris);
   dfree(c->d_nrm);
@@ -610,6 +668,8 @@ rt_status rt_load_scene(rt_ctx* c, const float* verts, uint32_t n_verts, const u
     CUDA_TRY(c, cudaMalloc(&c->d_nodes, nd.size() * sizeof(float4)));
     CUDA_TRY(c, cudaMalloc(&c->d_nodes4, b4.size() * sizeof(Bvh4Node)));
     CUDA_TRY(c, cudaMemcpy(c->d_nodes4, b4.data(), b4.size() * sizeof(Bvh4Node), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMalloc(&c->d_nodes4q, d4q.size() * sizeof(float4)));
+    CUDA_TRY(c, cudaMemcpy(c->d_nodes4q, d4q.data(), d4q.size() * sizeof(float4), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMalloc(&c->d_nodes8, d8.size() * sizeof(float4)));
     CUDA_TRY(c, cudaMemcpy(c->d_nodes8, d8.data(), d8.size() * sizeof(float4), cudaMemcpyHostToDevice));
     c->n_nodes8 = (uint32_t)(d8.size() / 14);
@@ -846,7 +906,9 @@ static rt_status render_impl(rt_ctx* c, const rt_camera* cams, uint32_t n_cams, 
   if (o.xyz_mode > 2) return fail(c, RT_ERR_ARG, "rt_render: unknown xyz_mode");
   if (o.xyz_mode != 2 && band_count > kXyzMaxBandsTc)
     return fail(c, RT_ERR_ARG, "rt_render: tensor-core XYZ takes at most 192 bands (use RT_XYZ_FP64)");
-  if (o.trace_variant > 4) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant > 5) return fail(c, RT_ERR_ARG, "rt_render: unknown trace_variant");
+  if (o.trace_variant == 5 && !c->d_nodes4q)
+    return fail(c, RT_ERR_ARG, "rt_render: the quantised tree needs a host-built BVH (builder 0 or 2)");
   if (o.trace_variant == 4 && !c->d_nodes8)
     return fail(c, RT_ERR_ARG, "rt_render: the eight-wide tree needs a host-built BVH (builder 0 or 2)");
   if (o.trace_variant != 0 && !c->d_nodes)

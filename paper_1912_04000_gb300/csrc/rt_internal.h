@@ -37,6 +37,7 @@ struct DevScene {
   const float4* nodes;   // binary BVH: 2 float4 per node, node 1 the root
   const float4* nodes4;  // four-wide BVH: 8 float4 per node, node 0 the root
   const float4* nodes8;  // eight-wide BVH: 14 float4 per node, node 0 the root (host builds; else null)
+  const float4* nodes4q;  // the four-wide BVH with 8-bit child boxes: 4 float4 per node (host builds; else null)
   const float4* tris;
   const float4* nrm;
   uint32_t n_nodes;

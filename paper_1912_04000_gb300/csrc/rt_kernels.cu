@@ -257,6 +257,83 @@ __device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const Dev
 }
 
 // ---------------------------------------------------------------------------
+// Four-wide BVH with 8-bit child boxes (node = 4 float4, 64 bytes: {origin,
+// bits(e_x | e_y << 8 | e_z << 16)}, {lo x, hi x, lo y, hi y} and {lo z,
+// hi z} as one byte per child, then the children packed as in the float
+// node).  Plane q of axis a lies at origin_a + q 2^e_a; the byte becomes the
+// float 2^23 + q by a byte permute, and t = fma(2^23 + q, 2^e inv,
+// b - 2^23 2^e inv) with b = (origin - o) inv: the subtraction rounds by
+// at most half a cell, inside the cell of margin the builder leaves around
+// every child box.  Same children, same order, half the bytes per node
+// visit of the float node (the closest-hit kernel is bound by L1
+// throughput).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float qplane(uint32_t word, uint32_t sel) {
+  return __uint_as_float(__byte_perm(word, 0x4B000000u, sel));
+}
+
+template <bool FMA>
+__device__ __forceinline__ float qslab_base(float origin, float inv, float oinv) {
+  return FMA ? fmaf(origin, inv, -oinv) : __fmul_rn(__fsub_rn(origin, oinv), inv);
+}
+
+template <bool FMA, bool COUNT>
+__device__ __forceinline__ bool trav_interior4q(Trav& tv, uint2* stack, const DevScene& S, float tmax,
+                                                uint32_t* status, uint32_t& n_nodes) {
+  const float4* nd = S.nodes4q + 4u * tv.ref;
+  const float4 h = ldg4(nd), pa = ldg4(nd + 1), pb = ldg4(nd + 2);
+  const uint4 pk = __ldg((const uint4*)(nd + 3));
+  if (COUNT) n_nodes += 4;
+  const uint32_t eb = __float_as_uint(h.w);
+  // per axis: cell size times 1/d, and the offset of plane 2^23 + q
+  const float sx = __uint_as_float(((eb & 0xFFu) + 127u - ((eb & 0x80u) << 1)) << 23) * tv.inv.x;
+  const float sy = __uint_as_float((((eb >> 8) & 0xFFu) + 127u - (((eb >> 8) & 0x80u) << 1)) << 23) * tv.inv.y;
+  const float sz = __uint_as_float((((eb >> 16) & 0xFFu) + 127u - (((eb >> 16) & 0x80u) << 1)) << 23) * tv.inv.z;
+  const float bx = fmaf(-8388608.0f, sx, qslab_base<FMA>(h.x, tv.inv.x, tv.oinv.x));
+  const float by = fmaf(-8388608.0f, sy, qslab_base<FMA>(h.y, tv.inv.y, tv.oinv.y));
+  const float bz = fmaf(-8388608.0f, sz, qslab_base<FMA>(h.z, tv.inv.z, tv.oinv.z));
+  // near planes: lo when the ray runs towards +axis
+  const uint32_t wlx = __float_as_uint(pa.x), whx = __float_as_uint(pa.y);
+  const uint32_t wly = __float_as_uint(pa.z), why = __float_as_uint(pa.w);
+  const uint32_t wlz = __float_as_uint(pb.x), whz = __float_as_uint(pb.y);
+  const uint32_t nx = (tv.oct & 1u) ? whx : wlx, fx = (tv.oct & 1u) ? wlx : whx;
+  const uint32_t ny = (tv.oct & 2u) ? why : wly, fy = (tv.oct & 2u) ? wly : why;
+  const uint32_t nz = (tv.oct & 4u) ? whz : wlz, fz = (tv.oct & 4u) ? wlz : whz;
+  float t[4];
+#pragma unroll
+  for (uint32_t i = 0; i < 4; ++i) {
+    const uint32_t sel = 0x7540u | i;
+    const float tn = fmaxf(fmaxf(fmaf(qplane(nx, sel), sx, bx), fmaf(qplane(ny, sel), sy, by)),
+                           fmaxf(fmaf(qplane(nz, sel), sz, bz), 0.0f));
+    const float tf = fminf(fminf(fmaf(qplane(fx, sel), sx, bx), fmaf(qplane(fy, sel), sy, by)),
+                           fminf(fmaf(qplane(fz, sel), sz, bz), tmax));
+    t[i] = tn <= tf * 1.0000005f ? tn : INFINITY;
+  }
+  float t0 = t[0], t1 = t[1], t2 = t[2], t3 = t[3];
+  uint32_t p0 = pk.x, p1 = pk.y, p2 = pk.z, p3 = pk.w;
+  const int nh = (t0 < INFINITY) + (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
+  if (nh == 0) return false;
+  cswap(t0, p0, t1, p1);
+  cswap(t2, p2, t3, p3);
+  cswap(t0, p0, t2, p2);
+  cswap(t1, p1, t3, p3);
+  cswap(t1, p1, t2, p2);
+  if (tv.sp + nh - 1 > kStack) {
+    atomicOr(status, ST_STACK);
+    tv.sp = 0;
+    return false;
+  }
+  const int top = tv.sp + nh - 2;
+  if (nh > 1) stack[top] = make_uint2(p1, __float_as_uint(t1));
+  if (nh > 2) stack[top - 1] = make_uint2(p2, __float_as_uint(t2));
+  if (nh > 3) stack[top - 2] = make_uint2(p3, __float_as_uint(t3));
+  tv.sp += nh - 1;
+  tv.ref = p0 >> 3;
+  tv.cnt = p0 & 7u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // Eight-wide BVH (node = 14 float4: per axis the lo planes of children 0-3
 // and 4-7, then their hi planes, then the eight children packed as
 // ref << 3 | count).  The builder puts in slot s the child that lies towards
@@ -755,8 +832,9 @@ __global__ void __launch_bounds__(kTraceMaxThreads, kTraceMinBlocks) k_trace(Dev
           } else if (leaf_phase) {
             closest_leaf(tv, S, nt, COUNT);
             done = !trav_pop(tv, stack, tv.best_t);
-          } else if (!(MODE == 4 ? trav_interior8<FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)
-                                 : interior_w<MODE == 3, FMA, COUNT>(tv, stack, S, tv.best_t, status, nn))) {
+          } else if (!(MODE == 5   ? trav_interior4q<FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)
+                       : MODE == 4 ? trav_interior8<FMA, COUNT>(tv, stack, S, tv.best_t, status, nn)
+                                   : interior_w<MODE == 3, FMA, COUNT>(tv, stack, S, tv.best_t, status, nn))) {
             done = !trav_pop(tv, stack, tv.best_t);
           }
         }
@@ -1707,7 +1785,8 @@ void trace_t(const LaunchCfg& lc, const DevScene& S, const float4* qin, const Wa
 template <bool FMA, bool COUNT>
 void trace_m(const LaunchCfg& lc, const DevScene& S, const float4* qin, const WaveBufs& b, uint32_t k,
              cudaStream_t st) {
-  if (lc.variant == 4) trace_t<FMA, COUNT, 4>(lc, S, qin, b, k, st);
+  if (lc.variant == 5) trace_t<FMA, COUNT, 5>(lc, S, qin, b, k, st);
+  else if (lc.variant == 4) trace_t<FMA, COUNT, 4>(lc, S, qin, b, k, st);
   else if (lc.variant == 3) trace_t<FMA, COUNT, 2>(lc, S, qin, b, k, st);
   else if (lc.variant == 2) trace_t<FMA, COUNT, 0>(lc, S, qin, b, k, st);
   else if (lc.variant == 1) trace_t<FMA, COUNT, 1>(lc, S, qin, b, k, st);

@@ -51,6 +51,30 @@ def test_large_nave_guided_runs(large):
     assert np.isfinite(s).all() and (s >= 0).all() and s.sum() > 0
 
 
+def test_large_nave_guided_paths_match_oracle(large):
+    """The guided tracer at its configuration (the 2M-triangle nave, four
+    2048 x 1536 views, 81 bands, depth 12, two guided vertices), with the
+    pass-through network that is exact in both precisions: 512 seeded pixels
+    path by path against the oracle's guided estimator (the training records
+    are compared on the 200k-triangle nave: here they would take 196 GB)."""
+    from test_gpu_guide_parity import _check_paths, _passthrough_params, LOG2_T, ALPHA
+    R, wl = large
+    R.guide_init(seed=1, log2_table=LOG2_T, mis_alpha=ALPHA, guide_depth=2)
+    grid, W = _passthrough_params(25)
+    R.guide_set_params(grid, W)
+    lo = wl.scene.verts.min(0).astype(np.float32)
+    hi = wl.scene.verts.max(0).astype(np.float32)
+    g = oracle.OracleGuide(LOG2_T, lo, hi, grid, W)
+    rng = np.random.default_rng(41)
+    pix = np.sort(rng.choice(wl.n_pixels, 512, replace=False))
+    out = R.render(wl.cameras, 1, wl.depth, wl.seed, guided=True, probe_pixels=pix, xyz_mode=2)
+    o = oracle.OracleScene(wl.scene, wl.spectra).render_guided(g, wl.cameras, 1, wl.depth, wl.seed, alpha=ALPHA,
+                                                               guide_depth=2, pixels=pix.astype(np.uint32),
+                                                               record_paths=True)
+    # 2M triangles: FP32/FP64 edge divergences as in the plain tracer (<= 1%)
+    _check_paths(out, o, "large nave guided", 0.99, 0.99, 1e-4)
+
+
 def test_large_nave_device_build(large):
     """The device builder on 2M triangles: closest hits and sun-ray
     transmittances against the FP64 oracle, the same closest hits as the

@@ -102,14 +102,16 @@ def test_ray_order_changes_nothing(R):
     assert np.array_equal(a, b)
 
 
-def test_eight_wide_tree_same_bits(R):
-    """The eight-wide tree (trace_variant 4, closest hit only) returns the
-    same closest hits as the four-wide one, so the render is bit-identical."""
-    wl = scenes.nave(width=64, height=48, n_bands=8, spp=2)
-    R.load(wl)
-    a = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)["spectral"].cpu().numpy()
-    b = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2, trace_variant=4)["spectral"].cpu().numpy()
-    assert np.array_equal(a, b)
+@pytest.mark.parametrize("variant", [4, 5])
+def test_other_trees_same_bits(R, variant):
+    """The eight-wide tree (trace_variant 4) and the four-wide tree with 8-bit
+    child boxes (5) return the same closest hits as the float four-wide
+    tree, so the render is bit-identical."""
+    for wl in (scenes.nave(width=64, height=48, n_bands=8, spp=2), scenes.prism_room(width=48, height=36, spp=2)):
+        R.load(wl)
+        a = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2)["spectral"].cpu().numpy()
+        b = R.render(wl.cameras, wl.spp, wl.depth, wl.seed, xyz_mode=2, trace_variant=variant)["spectral"].cpu().numpy()
+        assert np.array_equal(a, b)
 
 
 def test_traversal_loop_variants_agree(R):
