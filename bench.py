@@ -658,6 +658,10 @@ def main():
     roof = trace_roofline(R, counts, ms_trace, n_trace, ext_rays, traffic_per_ray)
     roof["stage_ms_per_step"] = dict(zip(STAGES, [m / args.steps for m in stage_ms]))
     roof["sun_rays_per_step"] = counts["shadow_rays"]
+    if traffic_per_ray is not None:
+        roof["ncu"] = {k: float(prof[k]) for k in ("dram_bytes_per_ray", "l1_throughput_pct", "l1_hit_rate_pct",
+                                                    "lts_throughput_pct", "warps_active_pct") if k in prof}
+        roof["ncu"]["source"] = os.path.relpath(PROFILE_TXT, ROOT)
 
     sub = {}
     if info.world == 1 and not args.no_subrecords:
