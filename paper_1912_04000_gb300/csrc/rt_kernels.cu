@@ -2,8 +2,10 @@
 //
 // One wave holds up to C spectral paths (view, pixel, sample, band).  For each
 // vertex k = 1..depth the host enqueues three kernels:
-//   k_trace  - closest hit of every queued ray (BVH2, watertight FP32 test),
-//              persistent warps fetching 32 rays at a time;
+//   k_trace  - closest hit of every queued ray (four-wide BVH by default; the
+//              binary, eight-wide and 8-bit-quantised trees as options;
+//              watertight FP32 test), persistent warps refilling idle lanes
+//              from the queue, leaf batching;
 //   k_shade  - material event at the hit (section 4: Eq. 2 by cosine sampling
 //              for stone, thin-glass/conductor Fresnel events with the complex
 //              index of Eq. 1), next-event estimate of the sun cone (Eq. 3),
