@@ -57,7 +57,17 @@ struct Task {
 };
 
 constexpr int kBins = 32;
-constexpr uint32_t kMaxLeaf = 4;
+// SAH: cost of a node visit relative to one triangle test, and the largest
+// leaf (the node format holds counts up to 7)
+#ifndef SRT_SAH_CT
+#define SRT_SAH_CT 1.0
+#endif
+#ifndef SRT_MAX_LEAF
+#define SRT_MAX_LEAF 4
+#endif
+constexpr double kCt = SRT_SAH_CT;
+constexpr uint32_t kMaxLeaf = SRT_MAX_LEAF;
+static_assert(kMaxLeaf >= 1 && kMaxLeaf <= 7, "leaf size");
 constexpr uint32_t kMedianDepth = 40;
 
 }  // namespace
@@ -142,9 +152,9 @@ int build_bvh(const float* verts, const uint32_t* tris, uint32_t nt, BvhOut& out
           }
         }
       }
-      // SAH leaf test (traversal and intersection cost taken as equal)
+      // SAH leaf test: n triangle tests against a visit and the children's tests
       const double parea = bb.area();
-      if (n <= kMaxLeaf && (best_axis < 0 || parea * n <= parea + best_cost)) {
+      if (n <= kMaxLeaf && (best_axis < 0 || parea * n <= kCt * parea + best_cost)) {
         make_leaf();
         continue;
       }
@@ -435,7 +445,7 @@ int build_sbvh(const float* verts, const uint32_t* tris, uint32_t nt, const uint
       }
       const double best = std::min(ob_cost, sp_cost);
       const double parea = bb.area();
-      if (n <= kMaxLeaf && ((ob_axis < 0 && sp_axis < 0) || parea * n <= parea + best)) {
+      if (n <= kMaxLeaf && ((ob_axis < 0 && sp_axis < 0) || parea * n <= kCt * parea + best)) {
         make_leaf();
         return;
       }

@@ -167,6 +167,14 @@ __device__ __forceinline__ uint32_t mix_sig(uint32_t h, uint32_t v) { return (h 
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
+// Two adjacent float4 (32 bytes, 32-byte aligned) in one read-only 256-bit
+// load (sm_100 and later).
+__device__ __forceinline__ void ldg8(const float4* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 // Warp-aggregated append of one element per lane with want = true; every lane
 // of the warp must call it (converged).  Returns the slot of this lane.
 __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {

@@ -20,6 +20,11 @@
 
 #include "rt_device.cuh"
 
+// 1: four-wide node boxes read with 256-bit loads
+#ifndef SRT_NODE_LD256
+#define SRT_NODE_LD256 1
+#endif
+
 namespace srt {
 
 namespace {
@@ -197,10 +202,23 @@ template <bool FMA, bool COUNT, bool ANY = false>
 __device__ __forceinline__ bool trav_interior4(Trav& tv, uint2* stack, const DevScene& S, float tmax,
                                                uint32_t* status, uint32_t& n_nodes) {
   const float4* nd = S.nodes4 + 8u * tv.ref;
+#if SRT_NODE_LD256
+  // each axis's plane pair in one 256-bit load (4 instead of 7 loads per
+  // node: the kernel is bound by L1 wavefronts of scattered lanes)
+  float4 lx, hx, ly, hy, lz, hz;
+  ldg8(nd, lx, hx);
+  ldg8(nd + 2, ly, hy);
+  ldg8(nd + 4, lz, hz);
+  const bool sx = tv.oct & 1u, sy = tv.oct & 2u, sz = tv.oct & 4u;
+  const float4 nx = sx ? hx : lx, fx = sx ? lx : hx;
+  const float4 ny = sy ? hy : ly, fy = sy ? ly : hy;
+  const float4 nz = sz ? hz : lz, fz = sz ? lz : hz;
+#else
   const uint32_t ox = tv.oct & 1u, oy = (tv.oct >> 1) & 1u, oz = (tv.oct >> 2) & 1u;
   const float4 nx = ldg4(nd + ox), fx = ldg4(nd + (ox ^ 1u));
   const float4 ny = ldg4(nd + 2u + oy), fy = ldg4(nd + 2u + (oy ^ 1u));
   const float4 nz = ldg4(nd + 4u + oz), fz = ldg4(nd + 4u + (oz ^ 1u));
+#endif
   const uint4 pk = __ldg((const uint4*)(nd + 6));  // children: ref << 3 | count
   if (COUNT) n_nodes += 4;
   float t0 = child_t<FMA>(tv, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x, tmax);
@@ -749,13 +767,18 @@ __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams,
 }
 
 constexpr uint32_t kNoRay = 0xFFFFFFFFu;
-// closest-hit kernel: blocks of at most 128 threads, 9 of them per SM
-// (<= 56 registers, 36 warps)
-constexpr int kTraceMaxThreads = 128, kTraceMinBlocks = 9;
-// sun-ray kernel: one band per path as the closest-hit kernel (9 blocks of
-// 128, <= 56 registers, a few bytes spilled: measured 0.4% faster on the
-// nave than 8 blocks at 60); four bands per path at least 4 blocks of 256
-// threads' worth (<= 64 registers)
+// closest-hit kernel: blocks of at most 128 threads, 8 of them per SM
+// (<= 64 registers, 32 warps).  With the 256-bit node loads, measured per
+// render of the nave / the 2M-triangle nave: 8 blocks 1372 / 2141 ms, 9
+// (56 registers) 1384 / 2160, 7 and 6 about 1408 / 2200, 10 and 12 (spilled)
+// 27% and 40% slower: more warps thrash the L1 that serves the node fetches
+#ifndef SRT_TRACE_MIN_BLOCKS
+#define SRT_TRACE_MIN_BLOCKS 8
+#endif
+constexpr int kTraceMaxThreads = 128, kTraceMinBlocks = SRT_TRACE_MIN_BLOCKS;
+// sun-ray kernel: one band per path as the closest-hit kernel (8 blocks of
+// 128, <= 64 registers: 402 / 633 ms against 410 / 645 at 9 blocks); four
+// bands per path at least 4 blocks of 256 threads' worth (<= 64 registers)
 #ifndef SRT_SHADOW_MIN_BLOCKS
 #define SRT_SHADOW_MIN_BLOCKS 4
 #endif
