@@ -767,18 +767,20 @@ __global__ void __launch_bounds__(256) k_camera(const DevCam* __restrict__ cams,
 }
 
 constexpr uint32_t kNoRay = 0xFFFFFFFFu;
-// closest-hit kernel: blocks of at most 128 threads, 8 of them per SM
-// (<= 64 registers, 32 warps).  With the 256-bit node loads, measured per
-// render of the nave / the 2M-triangle nave: 8 blocks 1372 / 2141 ms, 9
-// (56 registers) 1384 / 2160, 7 and 6 about 1408 / 2200, 10 and 12 (spilled)
-// 27% and 40% slower: more warps thrash the L1 that serves the node fetches
+// closest-hit kernel: blocks of at most 128 threads, launch bound 8 blocks
+// per SM (<= 64 registers; the closest-hit kernel compiles to 56 and the
+// launch takes the occupancy limit, 9 blocks, the one-band sun-ray kernel to
+// 61 and 8 blocks).  With the 256-bit node loads, measured per render of the
+// nave / the 2M-triangle nave, closest hit: bound 8 1372 / 2141 ms, bound 9
+// 1384 / 2160, 7 and 6 about 1408 / 2200, 10 and 12 (spilled) 27% and 40%
+// slower: more warps thrash the L1 that serves the node fetches
 #ifndef SRT_TRACE_MIN_BLOCKS
 #define SRT_TRACE_MIN_BLOCKS 8
 #endif
 constexpr int kTraceMaxThreads = 128, kTraceMinBlocks = SRT_TRACE_MIN_BLOCKS;
-// sun-ray kernel: one band per path as the closest-hit kernel (8 blocks of
-// 128, <= 64 registers: 402 / 633 ms against 410 / 645 at 9 blocks); four
-// bands per path at least 4 blocks of 256 threads' worth (<= 64 registers)
+// sun-ray kernel: one band per path with the closest-hit kernel's bound
+// (402 / 633 ms against 410 / 645 at bound 9, 56 registers); four bands per
+// path at least 4 blocks of 256 threads' worth (<= 64 registers)
 #ifndef SRT_SHADOW_MIN_BLOCKS
 #define SRT_SHADOW_MIN_BLOCKS 4
 #endif
