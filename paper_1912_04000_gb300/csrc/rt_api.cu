@@ -97,6 +97,7 @@ struct rt_ctx {
     rt_guide_config cfg{};
     float *grid = nullptr, *W = nullptr, *mg = nullptr, *vg = nullptr, *mW = nullptr, *vW = nullptr;
     float *dgrid = nullptr, *dW = nullptr, *scratch = nullptr;  // scratch: wsum, loss
+    float* dWpart = nullptr;  // per-CTA partial weight gradients, sms x weights
     void* pack = nullptr;
     uint64_t n_grid = 0;
     uint32_t step = 0;
@@ -378,6 +379,7 @@ void rt_destroy(rt_ctx* c) {
   dfree(c->guide.vW);
   dfree(c->guide.dgrid);
   dfree(c->guide.dW);
+  dfree(c->guide.dWpart);
   dfree(c->guide.scratch);
   dfree(c->guide.gq);
   dfree(c->guide.wesc);
@@ -1360,6 +1362,7 @@ rt_status rt_guide_init(rt_ctx* c, const rt_guide_config* cfg_in, uint64_t seed)
     CUDA_TRY(c, cudaMalloc(&G.mW, guide_wcount() * 4));
     CUDA_TRY(c, cudaMalloc(&G.vW, guide_wcount() * 4));
     CUDA_TRY(c, cudaMalloc(&G.dW, guide_wcount() * 4));
+    CUDA_TRY(c, cudaMalloc(&G.dWpart, (size_t)c->sms * guide_wcount() * 4));
     CUDA_TRY(c, cudaMalloc(&G.scratch, 64));
     CUDA_TRY(c, cudaMalloc(&G.pack, guide_wpack_bytes()));
   }
@@ -1439,7 +1442,7 @@ static void guide_grad_enqueue(rt_ctx* c, const float* rec_dev, uint64_t n) {
   cudaMemsetAsync(G.dgrid, 0, G.n_grid * 4, c->stream);
   cudaMemsetAsync(G.dW, 0, guide_wcount() * 4, c->stream);
   cudaMemsetAsync(G.scratch, 0, 64, c->stream);
-  launch_guide_train(G.dev, G.pack, rec_dev, n, G.scratch, G.dW, G.dgrid, G.scratch + 1, c->wb.status, c->sms,
+  launch_guide_train(G.dev, G.pack, rec_dev, n, G.scratch, G.dW, G.dWpart, G.dgrid, G.scratch + 1, c->wb.status, c->sms,
                      c->stream);
 }
 

@@ -399,11 +399,14 @@ __device__ __forceinline__ void encode_levels8(const GuideDev& g, const uint32_t
 // A CTA of 256 threads serves 128 records per tile, two threads per record
 // (half h = t / 128; threads t and t + 128 share a TMEM lane).  Records of
 // zero weight add nothing to the loss or its gradient and are skipped: each
-// CTA walks a contiguous chunk of the batch and compacts the indices of the
-// weighted records into full tiles.  Weight gradients dW_l = H_{l-1}^T dZ_l
-// use A' = [H_{l-1}^T; 0] (M = 128) and B' = dZ_l^T, both made from the
-// K-major activation tiles by 8 x 8 transposes (ldmatrix / stmatrix.trans),
-// and accumulate in TMEM over all tiles of the CTA.
+// CTA walks a contiguous chunk of the batch, four records per thread and
+// round, and compacts the indices of the weighted records into full tiles.
+// Weight gradients dW_l = H_{l-1}^T dZ_l use A' = [H_{l-1}^T; 0] (M = 128)
+// and B' = dZ_l^T, both made from the K-major activation tiles by 8 x 8
+// transposes (ldmatrix / stmatrix.trans), and accumulate in TMEM over all
+// tiles of the CTA; each CTA then stores its sums as one partial (layer l's
+// block column-major: element (in, o) at w_off(l) + 64 o + in) and
+// k_dw_reduce adds the partials in a fixed order.
 constexpr int kTrainThreads = 2 * kRows;
 constexpr uint32_t kTrX = kWPack;
 constexpr uint32_t kTrH1 = kTrX + kATileB;
@@ -412,8 +415,10 @@ constexpr uint32_t kTrH3 = kTrH2 + kATileB;
 constexpr uint32_t kTrDZ = kTrH3 + kATileB;
 constexpr uint32_t kTrAp = kTrDZ + kATileB;           // [128 x 128] = 32 KB
 constexpr uint32_t kTrBp = kTrAp + 8 * kSliceA;       // <= [64 x 128] = 16 KB
-constexpr uint32_t kTrList = kTrBp + 8 * 64 * 32;     // record indices, 128 + 256 entries
-constexpr uint32_t kTrMisc = kTrList + 384 * 4;
+constexpr uint32_t kTrScan = 4;                       // records per thread and scan round
+constexpr uint32_t kTrListN = kRows + kTrScan * kTrainThreads;  // a short tile + one round
+constexpr uint32_t kTrList = kTrBp + 8 * 64 * 32;     // record indices
+constexpr uint32_t kTrMisc = kTrList + kTrListN * 4;
 constexpr uint32_t kTrainSmem = kTrMisc + 128;
 static_assert(kTrainSmem <= 227 * 1024, "training kernel shared memory");
 
@@ -456,7 +461,7 @@ __device__ __forceinline__ void transpose_tile(const unsigned char* src, unsigne
 
 __global__ void __launch_bounds__(kTrainThreads, 1)
     k_guide_train(GuideDev g, const uint4* __restrict__ wpack, const float4* __restrict__ rec, uint64_t n,
-                  const float* __restrict__ wsum, float* __restrict__ dW, float* __restrict__ dgrid,
+                  const float* __restrict__ wsum, float* __restrict__ dWpart, float* __restrict__ dgrid,
                   float* __restrict__ loss, uint32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* AX = smem + kTrX;
@@ -501,19 +506,33 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
     // compact the indices of weighted records until a tile is full
     uint32_t nl = wcnt[8];
     while (nl < (uint32_t)kRows && cur < c1) {
-      const uint64_t i = cur + tid;
-      const bool take = i < c1 && __ldg((const float*)(rec + 3 * i) + 3) > 0.0f;
-      const uint32_t m = __ballot_sync(0xffffffffu, take);
-      if (lane == 0) wcnt[warp] = __popc(m);
+      // records cur + tid + 256 q, q < 4: independent loads, one scan
+      bool take[kTrScan];
+      uint32_t cnt_t = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < kTrScan; ++q) {
+        const uint64_t i = cur + tid + (uint64_t)q * kTrainThreads;
+        take[q] = i < c1 && __ldg((const float*)(rec + 3 * i) + 3) > 0.0f;
+        cnt_t += take[q] ? 1u : 0u;
+      }
+      uint32_t incl = cnt_t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+      }
+      if (lane == 31) wcnt[warp] = incl;
       __syncthreads();
-      uint32_t off = nl;
+      uint32_t off = nl + incl - cnt_t;
       for (uint32_t w2 = 0; w2 < warp; ++w2) off += wcnt[w2];
-      if (take) list[off + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(i - c0);
+#pragma unroll
+      for (uint32_t q = 0; q < kTrScan; ++q)
+        if (take[q]) list[off++] = (uint32_t)(cur + tid + (uint64_t)q * kTrainThreads - c0);
       uint32_t tot = 0;
       for (uint32_t w2 = 0; w2 < (blockDim.x >> 5); ++w2) tot += wcnt[w2];
       __syncthreads();
       nl += tot;
-      cur += blockDim.x;
+      cur += (uint64_t)kTrScan * kTrainThreads;
     }
     if (nl == 0) break;
     const uint32_t nt = min(nl, (uint32_t)kRows);
@@ -523,10 +542,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
     if (valid) rc = load_rec(rec, ri);
     // carry the surplus indices over to the next tile
     __syncthreads();
-    uint32_t carry = 0;
-    if (tid < nl - nt) carry = list[kRows + tid];
+    uint32_t carry[kTrScan];
+#pragma unroll
+    for (uint32_t q = 0; q < kTrScan; ++q) {
+      const uint32_t t = tid + q * kTrainThreads;
+      carry[q] = t < nl - nt ? list[kRows + t] : 0u;
+    }
     __syncthreads();
-    if (tid < nl - nt) list[tid] = carry;
+#pragma unroll
+    for (uint32_t q = 0; q < kTrScan; ++q) {
+      const uint32_t t = tid + q * kTrainThreads;
+      if (t < nl - nt) list[t] = carry[q];
+    }
     if (tid == 0) wcnt[8] = nl - nt;
     // encoding: half 0 grid levels 0-7 and SH, half 1 levels 8-15 and group
     {
@@ -678,22 +705,29 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
     }
     first = false;
   }
-  // accumulated weight gradients: TMEM lanes 0..63 (warps 0, 1, 4, 5) = input rows
-  if (!first && sy.ok && (warp & 3u) < 2u) {
-    const uint32_t in = (warp & 1u) * 32u + lane;
-    for (int l = 0; l < 4; ++l) {
-      const int out = layer_out(l);
-      float row[32];
-      // half 0 columns 0..31, half 1 columns 32..out-1
-      const int o0 = 32 * (int)h, nc = min(32, out - o0);
-      const uint32_t col0 = 64u * (uint32_t)(l + 1) + (uint32_t)o0;
-      if (nc == 32) {
-        tc_tmem_ld16x2(trow + col0, row);
-      } else {
-        tc_tmem_ld16(trow + col0, row);
+  // accumulated weight gradients: TMEM lanes 0..63 (warps 0, 1, 4, 5) =
+  // input rows; this CTA's partial, element (in, o) of layer l at
+  // w_off(l) + 64 o + in (a warp stores 32 consecutive floats per column)
+  float* part = dWpart + (size_t)blockIdx.x * kWSize;
+  if (!first && sy.ok) {
+    if ((warp & 3u) < 2u) {
+      const uint32_t in = (warp & 1u) * 32u + lane;
+      for (int l = 0; l < 4; ++l) {
+        const int out = layer_out(l);
+        float row[32];
+        // half 0 columns 0..31, half 1 columns 32..out-1
+        const int o0 = 32 * (int)h, nc = min(32, out - o0);
+        const uint32_t col0 = 64u * (uint32_t)(l + 1) + (uint32_t)o0;
+        if (nc == 32) {
+          tc_tmem_ld16x2(trow + col0, row);
+        } else {
+          tc_tmem_ld16(trow + col0, row);
+        }
+        for (int o = 0; o < nc; ++o) part[w_off(l) + 64 * (o0 + o) + in] = row[o];
       }
-      for (int o = 0; o < nc; ++o) atomicAdd(dW + w_off(l) + in * out + o0 + o, row[o]);
     }
+  } else {
+    for (int e = (int)tid; e < kWSize; e += (int)blockDim.x) part[e] = 0.0f;
   }
   if (my_loss != 0.0f) atomicAdd(lsum, my_loss);
   tc_fence_before();
@@ -712,6 +746,28 @@ __global__ void k_weight_sum(const float4* __restrict__ rec, uint64_t n, float* 
     s += __ldg(rec + 3 * i).w;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// dW = sum over the CTAs' partials (column-major blocks, see k_guide_train):
+// 32 weights per block, warp w adds partials w, w + 8, ..., then the eight
+// warp sums are added in warp order (the same order every call).
+__global__ void __launch_bounds__(256) k_dw_reduce(const float* __restrict__ part, int nparts, float* __restrict__ dW) {
+  __shared__ float acc[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * 32 + lane;
+  float s = 0.0f;
+  if (e < kWSize)
+    for (int c = warp; c < nparts; c += 8) s += __ldg(part + (size_t)c * kWSize + e);
+  acc[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && e < kWSize) {
+    float t = acc[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += acc[w][lane];
+    const int l = e / 4096, loc = e - 4096 * l;
+    const int out = layer_out(l), o = loc / 64, in = loc - 64 * o;
+    if (o < out) dW[w_off(l) + in * out + o] = t;
+  }
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -1203,7 +1259,7 @@ void launch_guide_eval(const GuideDev& g, const void* pack, const float* rec, ui
 }
 
 void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* wsum, float* dW,
-                        float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st) {
+                        float* dWpart, float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st) {
   cudaMemsetAsync(wsum, 0, sizeof(float), st);
   k_weight_sum<<<sms * 4, 256, 0, st>>>((const float4*)rec, n, wsum);
   const size_t smem = guide_train_smem();
@@ -1212,8 +1268,9 @@ void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, u
   uint64_t grid = (uint64_t)sms;
   if (grid > tiles) grid = tiles;
   if (grid == 0) return;
-  k_guide_train<<<(unsigned)grid, kTrainThreads, smem, st>>>(g, (const uint4*)pack, (const float4*)rec, n, wsum, dW, dgrid,
-                                                      loss, status);
+  k_guide_train<<<(unsigned)grid, kTrainThreads, smem, st>>>(g, (const uint4*)pack, (const float4*)rec, n, wsum, dWpart,
+                                                             dgrid, loss, status);
+  k_dw_reduce<<<(kWSize + 31) / 32, 256, 0, st>>>(dWpart, (int)grid, dW);
 }
 
 void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,

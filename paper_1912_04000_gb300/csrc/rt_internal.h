@@ -320,8 +320,9 @@ void launch_guide_init(float* grid, uint64_t n_grid, float* W, uint64_t seed, cu
 void launch_guide_pack(const float* W, void* pack, cudaStream_t st);
 void launch_guide_eval(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* Y, float* q,
                        uint32_t* status, int sms, cudaStream_t st);
+// dWpart: sms x 15360 floats of per-CTA partial weight gradients (scratch)
 void launch_guide_train(const GuideDev& g, const void* pack, const float* rec, uint64_t n, float* wsum, float* dW,
-                        float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st);
+                        float* dWpart, float* dgrid, float* loss, uint32_t* status, int sms, cudaStream_t st);
 void launch_adam(float* p, const float* g, float* m, float* v, uint64_t n, float lr, float b1, float b2, float eps,
                  float c1, float c2, cudaStream_t st);
 void launch_guide_sample(const GuideDev& g, const void* pack, const DevSpectra& P, const WaveParams& w, uint32_t k,
