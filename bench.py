@@ -707,7 +707,7 @@ def main():
             "roofline": roof,
         }
         line.update(sub)
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and info.world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_pixels)
         print(json.dumps(line), flush=True)
     multigpu.finish(info)
