@@ -343,13 +343,13 @@ rt_status rt_render_static(rt_ctx* ctx, const rt_camera* cams, uint32_t n_cams, 
  * estimator: guided directions are mixed with cosine sampling by one-sample
  * MIS, so the rendered expectation of section 4, Eq. 2 is unchanged) ------
  *
- * Network: hash-grid encoding of the position (16 levels x 2 features,
- * 2^log2_table entries per level, resolutions n_min .. n_max over the scene
- * bounds), real spherical harmonics of the normal (degree <= 3), a one-hot
+ * Network: hash-grid encoding of the position (8 levels x 4 features,
+ * 2^log2_table entries per level, resolutions floor(n_min b^l), b =
+ * (n_max / n_min)^(1/7), over the scene bounds), real spherical harmonics of the normal (degree <= 3), a one-hot
  * band group (9 groups); MLP 64 -> 64 -> 64 -> 64 -> 48 (ReLU, no biases) on
  * BF16 tensor cores with FP32 accumulation; 8 von Mises-Fisher lobes (outputs
  * 5j .. 5j + 4: logit, mean direction, kappa = 0.5 + softplus).
- * Parameters: grid [16][2^log2_table][2] and W = W1 [64][64] | W2 [64][64] |
+ * Parameters: grid [8][2^log2_table][4] and W = W1 [64][64] | W2 [64][64] |
  * W3 [64][64] | W4 [64][48] (row-major [in][out]), FP32 masters.
  * Training record (12 floats): {pos.xyz, weight}, {normal.xyz, band group},
  * {omega.xyz, 0}; loss -(1/N) sum_r (weight_r / mean weight) log q_r(omega_r).

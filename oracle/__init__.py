@@ -368,7 +368,8 @@ def xyz(spectral_sum, band_first, spp, cmf_w) -> np.ndarray:
 # learned guide (hash grid + MLP + vMF mixture), FP64
 # ---------------------------------------------------------------------------
 GUIDE_W_SIZE = 64 * 64 * 3 + 64 * 48
-GUIDE_LEVELS = 16
+GUIDE_LEVELS = 8
+GUIDE_FEATURES = 4  # hash-grid features per level
 
 
 def guide_resolutions(n_min=16.0, n_max=2048.0):
@@ -398,12 +399,12 @@ def guide_forward(log2_T, lo, hi, grid, W, pos, nrm, group, omega, n_min=16.0, n
 
 
 def guide_loss_grad(log2_T, lo, hi, grid, W, pos, nrm, group, omega, wt, n_min=16.0, n_max=2048.0, bf16_act=False):
-    """(loss, dW [GUIDE_W_SIZE], dgrid [16 * 2^log2_T * 2])."""
+    """(loss, dW [GUIDE_W_SIZE], dgrid [8 * 2^log2_T * 4])."""
     lo, hi, grid, W, pos, nrm, omega, wt = map(_f32, (lo, hi, grid, W, pos, nrm, omega, wt))
     g = np.ascontiguousarray(group, np.uint32)
     n = pos.shape[0]
     dW = np.zeros(GUIDE_W_SIZE)
-    dgrid = np.zeros(GUIDE_LEVELS * (1 << log2_T) * 2)
+    dgrid = np.zeros(GUIDE_LEVELS * (1 << log2_T) * GUIDE_FEATURES)
     fp = lambda a: _ptr(a, C.c_float)
     dp = lambda a: _ptr(a, C.c_double)
     loss = lib().or_guide_loss_grad(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W), n, fp(pos), fp(nrm),
@@ -438,7 +439,7 @@ class OracleGuide:
 
     def __init__(self, log2_T, lo, hi, grid, W, n_min=16.0, n_max=2048.0, bf16_act=True):
         lo, hi, grid, W = map(_f32, (lo, hi, grid, W))
-        if grid.size != GUIDE_LEVELS * (1 << log2_T) * 2 or W.size != GUIDE_W_SIZE:
+        if grid.size != GUIDE_LEVELS * (1 << log2_T) * GUIDE_FEATURES or W.size != GUIDE_W_SIZE:
             raise ValueError("guide parameter sizes")
         fp = lambda a: _ptr(a, C.c_float)
         self._h = lib().or_guide_net_create(log2_T, fp(lo), fp(hi), n_min, n_max, fp(grid), fp(W),

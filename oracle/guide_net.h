@@ -13,7 +13,7 @@ constexpr int kLobes = 8;
 // Network parameters and encoding of one scene (a copy of the caller's data).
 struct Net;
 
-// grid [16][2^log2_T][2] and W (W1 | W2 | W3 | W4, row-major [in][out]) as
+// grid [8][2^log2_T][4] and W (W1 | W2 | W3 | W4, row-major [in][out]) as
 // floats; bf16_act: layer inputs rounded to BF16 (the BF16 network).
 Net* net_create(uint32_t log2_T, const float* lo, const float* hi, float n_min, float n_max, const float* grid,
                 const float* W, int bf16_act);

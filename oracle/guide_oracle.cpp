@@ -5,8 +5,8 @@
 // section 4, Eq. 2; it only changes the sampling density).  Its definition,
 // written here plainly in double precision, is:
 //
-//   input (64):  multiresolution hash-grid encoding of the position (16
-//                levels x 2 features, trilinear; after Mueller et al. 2022,
+//   input (64):  multiresolution hash-grid encoding of the position (8
+//                levels x 4 features, trilinear; after Mueller et al. 2022,
 //                spatial hash with primes 1, 2654435761, 805459861), real
 //                spherical harmonics of the normal up to degree 3 (16), a
 //                one-hot band group (9), zeros (7);
@@ -35,7 +35,7 @@
 
 namespace {
 
-constexpr int kLevels = 16, kFeat = 2, kIn = 64, kHid = 64, kOut = 48, kLobes = 8, kGroups = 9;
+constexpr int kLevels = 8, kFeat = 4, kIn = 64, kHid = 64, kOut = 48, kLobes = 8, kGroups = 9;
 
 struct GCfg {
   uint32_t log2_T;
@@ -106,7 +106,7 @@ void encode(const GCfg& g, const float* grid, const double p[3], const double n[
       c[a] = (uint32_t)fl;
       f[a] = s - fl;
     }
-    double acc[kFeat] = {0.0, 0.0};
+    double acc[kFeat] = {0.0, 0.0, 0.0, 0.0};
     for (int k = 0; k < 8; ++k) {
       const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
       const double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
@@ -115,8 +115,7 @@ void encode(const GCfg& g, const float* grid, const double p[3], const double n[
       e->w[l][k] = w;
       for (int q = 0; q < kFeat; ++q) acc[q] += w * (double)grid[((size_t)l * T + id) * kFeat + q];
     }
-    X[2 * l] = acc[0];
-    X[2 * l + 1] = acc[1];
+    for (int q = 0; q < kFeat; ++q) X[kFeat * l + q] = acc[q];
   }
   sh16(n[0], n[1], n[2], X + 32);
   for (int i = 48; i < kIn; ++i) X[i] = 0.0;
@@ -188,7 +187,9 @@ GCfg make_cfg(uint32_t log2_T, const float* lo, const float* hi, float n_min, fl
   }
   const double b = std::exp((std::log((double)n_max) - std::log((double)n_min)) / (kLevels - 1));
   g.res.resize(kLevels);
-  for (int l = 0; l < kLevels; ++l) g.res[l] = (uint32_t)std::floor((double)n_min * std::pow(b, l));
+  // n_min b^l rounded down; the relative 1e-12 keeps a product that is an
+  // integer in exact arithmetic (16 x 2^7 = 2048) from landing just below it
+  for (int l = 0; l < kLevels; ++l) g.res[l] = (uint32_t)std::floor((double)n_min * std::pow(b, l) * (1.0 + 1e-12));
   return g;
 }
 
@@ -244,7 +245,7 @@ void or_guide_forward(uint32_t log2_T, const float* lo, const float* hi, float n
 }
 
 // Loss and gradients for n records with weights wt (>= 0).
-// dW (same layout as W) and dgrid ([16 * T * 2]) are overwritten.
+// dW (same layout as W) and dgrid ([8 * T * 4]) are overwritten.
 double or_guide_loss_grad(uint32_t log2_T, const float* lo, const float* hi, float n_min, float n_max,
                           const float* grid, const float* W, uint64_t n, const float* pos, const float* nrm,
                           const uint32_t* group, const float* omega, const float* wt, int bf16_act, double* dW,
@@ -336,7 +337,7 @@ double or_guide_loss_grad(uint32_t log2_T, const float* lo, const float* hi, flo
     }
     for (int l = 0; l < kLevels; ++l)
       for (int k = 0; k < 8; ++k)
-        for (int f = 0; f < kFeat; ++f) dgrid[((size_t)l * T + e.idx[l][k]) * kFeat + f] += e.w[l][k] * dX[2 * l + f];
+        for (int f = 0; f < kFeat; ++f) dgrid[((size_t)l * T + e.idx[l][k]) * kFeat + f] += e.w[l][k] * dX[kFeat * l + f];
   }
   return loss;
 }

@@ -71,6 +71,7 @@ class GuideConfig(C.Structure):
 
 
 GUIDE_W_SIZE = 64 * 64 * 3 + 64 * 48
+GUIDE_GRID_LEVELS, GUIDE_GRID_FEATURES = 8, 4  # hash grid [levels][2^log2_table][features]
 
 
 class Stats(C.Structure):

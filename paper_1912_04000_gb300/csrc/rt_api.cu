@@ -1344,7 +1344,7 @@ rt_status rt_guide_init(rt_ctx* c, const rt_guide_config* cfg_in, uint64_t seed)
   auto& G = c->guide;
   cudaSetDevice(c->device);
   const uint64_t T = 1ull << cfg.log2_table;
-  const uint64_t ng = 16ull * T * 2ull;
+  const uint64_t ng = (uint64_t)kGuideLevels * T * kGuideFeatures;
   if (G.n_grid != ng) {
     dfree(G.grid);
     dfree(G.mg);
@@ -1370,10 +1370,13 @@ rt_status rt_guide_init(rt_ctx* c, const rt_guide_config* cfg_in, uint64_t seed)
   GuideDev& d = G.dev;
   d.grid = G.grid;
   d.log2T = cfg.log2_table;
-  const double b = std::exp((std::log((double)cfg.n_max) - std::log((double)cfg.n_min)) / 15.0);
+  // resolutions n_min b^l, b = (n_max / n_min)^(1 / (levels - 1)); the
+  // relative 1e-12 keeps a product that is an integer in exact arithmetic
+  // (16 x 2^7 = 2048) from rounding down to the integer below
+  const double b = std::exp((std::log((double)cfg.n_max) - std::log((double)cfg.n_min)) / (kGuideLevels - 1));
   d.dense_mask = 0;
-  for (int l = 0; l < 16; ++l) {
-    d.res[l] = (uint32_t)std::floor((double)cfg.n_min * std::pow(b, l));
+  for (int l = 0; l < kGuideLevels; ++l) {
+    d.res[l] = (uint32_t)std::floor((double)cfg.n_min * std::pow(b, l) * (1.0 + 1e-12));
     const uint64_t r1 = (uint64_t)d.res[l] + 1;
     if (r1 * r1 * r1 <= T) d.dense_mask |= 1u << l;
   }

@@ -5,7 +5,7 @@
 // kernels.
 //
 // Definition (shared with the CPU oracle, written there in FP64):
-//   X (64)  = [hash-grid features of the position (16 levels x 2, trilinear;
+//   X (64)  = [hash-grid features of the position (8 levels x 4, trilinear;
 //              after Mueller et al. 2022, primes 1, 2654435761, 805459861),
 //              real SH of the normal up to degree 3 (16), one-hot band group
 //              (9), zeros (7)]
@@ -21,7 +21,7 @@
 // data-gradient B operands are W (N = in rows, K = out).  Weight gradients
 // dW = H^T dZ use A' = [H^T; 0] (128 rows, the upper 64 the input features,
 // K = the tile's 128 records) and B' = dZ^T, accumulated in TMEM across all
-// tiles of a CTA and added to global FP32 gradients at the end.
+// tiles of a CTA and summed over the CTAs by k_dw_reduce at the end.
 #include <cmath>
 #include <cstdint>
 
@@ -33,7 +33,8 @@ namespace srt {
 
 namespace {
 
-constexpr int kIn = 64, kHid = 64, kOut = 48, kLevels = 16, kLobes = 8;
+constexpr int kIn = 64, kHid = 64, kOut = 48, kLevels = kGuideLevels, kFeat = kGuideFeatures, kLobes = 8;
+static_assert(kLevels * kFeat == 32, "32 grid features in the network input");
 constexpr int kRows = 128;
 constexpr uint32_t kATileB = 16384;   // [128 x 64] BF16 activations
 constexpr uint32_t kSliceA = 4096;    // one 128 x 16 K-slice
@@ -118,18 +119,22 @@ __device__ __forceinline__ void encode(const GuideDev& g, float3 p, float3 n, ui
 #pragma unroll 1
   for (int l = 0; l < kLevels; ++l) {
     const LevelPos lp = level_pos(g, u, l);
-    float a0 = 0.0f, a1 = 0.0f;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const uint32_t dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
       const float w = (dx ? lp.f[0] : 1.0f - lp.f[0]) * (dy ? lp.f[1] : 1.0f - lp.f[1]) * (dz ? lp.f[2] : 1.0f - lp.f[2]);
       const uint32_t id = grid_index(g, l, lp.c[0] + dx, lp.c[1] + dy, lp.c[2] + dz);
-      const float2 v = __ldg((const float2*)g.grid + (size_t)l * T + id);
+      const float4 v = __ldg((const float4*)g.grid + (size_t)l * T + id);
       a0 = fmaf(w, v.x, a0);
       a1 = fmaf(w, v.y, a1);
+      a2 = fmaf(w, v.z, a2);
+      a3 = fmaf(w, v.w, a3);
     }
-    X[2 * l] = a0;
-    X[2 * l + 1] = a1;
+    X[4 * l] = a0;
+    X[4 * l + 1] = a1;
+    X[4 * l + 2] = a2;
+    X[4 * l + 3] = a3;
   }
   sh16(n.x, n.y, n.z, X + 32);
 #pragma unroll
@@ -358,13 +363,13 @@ __device__ __forceinline__ void corner_weights(const float fr[3], float w[8]) {
   for (int k = 0; k < 8; ++k) w[k] = wxy[k & 3] * wz[k >> 2];
 }
 
-// Hash-grid features of levels l0 .. l0 + 7 (the arithmetic of encode());
-// res: the per-level resolutions, staged in shared memory.
-__device__ __forceinline__ void encode_levels8(const GuideDev& g, const uint32_t* res, const float u[3], int l0,
+// Hash-grid features of levels l0 .. l0 + 3, 16 values (the arithmetic of
+// encode()); res: the per-level resolutions, staged in shared memory.
+__device__ __forceinline__ void encode_levels4(const GuideDev& g, const uint32_t* res, const float u[3], int l0,
                                                float* f) {
   const uint32_t T = 1u << g.log2T;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 4; ++i) {
     const int l = l0 + i;
     const float rl = (float)res[l];
     uint32_t c[3];
@@ -380,16 +385,20 @@ __device__ __forceinline__ void encode_levels8(const GuideDev& g, const uint32_t
     corner_ids(g, res, l, c, T, id);
     float w[8];
     corner_weights(fr, w);
-    const float2* tab = (const float2*)g.grid + (size_t)l * T;
-    float a0 = 0.0f, a1 = 0.0f;
+    const float4* tab = (const float4*)g.grid + (size_t)l * T;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const float2 v = __ldg(tab + id[k]);
+      const float4 v = __ldg(tab + id[k]);
       a0 = fmaf(w[k], v.x, a0);
       a1 = fmaf(w[k], v.y, a1);
+      a2 = fmaf(w[k], v.z, a2);
+      a3 = fmaf(w[k], v.w, a3);
     }
-    f[2 * i] = a0;
-    f[2 * i + 1] = a1;
+    f[4 * i] = a0;
+    f[4 * i + 1] = a1;
+    f[4 * i + 2] = a2;
+    f[4 * i + 3] = a3;
   }
 }
 
@@ -473,7 +482,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
   uint32_t* tslot = (uint32_t*)(mbar + 1);
   float* lsum = (float*)(tslot + 1);
   uint32_t* wcnt = (uint32_t*)(lsum + 1);  // [8] per-warp counts, [8] list length
-  uint32_t* sres = wcnt + 9;               // [16] grid resolutions
+  uint32_t* sres = wcnt + 9;               // [kLevels] grid resolutions
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
   const uint32_t r = tid & (kRows - 1), h = tid >> 7;
   load_weights(smem, wpack);
@@ -555,12 +564,12 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
       if (t < nl - nt) list[t] = carry[q];
     }
     if (tid == 0) wcnt[8] = nl - nt;
-    // encoding: half 0 grid levels 0-7 and SH, half 1 levels 8-15 and group
+    // encoding: half 0 grid levels 0-3 and SH, half 1 levels 4-7 and group
     {
       float u[3], f[16];
       unit_pos(g, rc.p, u);
       if (valid) {
-        encode_levels8(g, sres, u, 8 * (int)h, f);
+        encode_levels4(g, sres, u, 4 * (int)h, f);
       } else {
 #pragma unroll
         for (int c = 0; c < 16; ++c) f[c] = 0.0f;
@@ -670,7 +679,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
           put8(ADZ, r, col, t);
         }
       } else {
-        // dX of grid levels 8h .. 8h + 7 -> grid gradient
+        // dX of grid levels 4h .. 4h + 3 -> grid gradient
         float dx[16];
         tc_tmem_ld16(trow + 16u * h, dx);
         if (valid && rc.weight > 0.0f && total > 0.0f) {
@@ -678,10 +687,10 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
           unit_pos(g, rc.p, u);
           const uint32_t T = 1u << g.log2T;
 #pragma unroll 1
-          for (int i = 0; i < 8; ++i) {
-            const int l2 = 8 * (int)h + i;
-            const float d0 = dx[2 * i], d1 = dx[2 * i + 1];
-            if (d0 == 0.0f && d1 == 0.0f) continue;
+          for (int i = 0; i < 4; ++i) {
+            const int l2 = 4 * (int)h + i;
+            const float d0 = dx[4 * i], d1 = dx[4 * i + 1], d2 = dx[4 * i + 2], d3 = dx[4 * i + 3];
+            if (d0 == 0.0f && d1 == 0.0f && d2 == 0.0f && d3 == 0.0f) continue;
             const float rl = (float)sres[l2];
             uint32_t c[3];
             float fr[3];
@@ -696,9 +705,9 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             corner_ids(g, sres, l2, c, T, id);
             float w[8];
             corner_weights(fr, w);
-            float2* dst = (float2*)dgrid + (size_t)l2 * T;
+            float4* dst = (float4*)dgrid + (size_t)l2 * T;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) atomicAdd(dst + id[k], make_float2(w[k] * d0, w[k] * d1));
+            for (int k = 0; k < 8; ++k) atomicAdd(dst + id[k], make_float4(w[k] * d0, w[k] * d1, w[k] * d2, w[k] * d3));
           }
         }
       }
@@ -857,7 +866,7 @@ constexpr int kSampleCtasPerSm = SRT_GUIDE_SAMPLE_CTAS;
 // Guided continuation at the wave's guide queries of vertex k.  A CTA takes
 // tiles of 128 queries; thread t serves query t % 128 as half h = t / 128
 // (threads t and t + 128 share a TMEM lane).  Encoding: half 0 the grid
-// levels 0-7 and the SH of the normal, half 1 levels 8-15 and the band
+// levels 0-3 and the SH of the normal, half 1 levels 4-7 and the band
 // group; each hidden layer runs on the tensor cores and the epilogue (ReLU,
 // BF16) rewrites the activation tile in place, half h taking columns
 // 32h .. 32h + 31.  Head: half h owns lobes 4h .. 4h + 3; the softmax
@@ -916,7 +925,7 @@ __global__ void __launch_bounds__(kSampleThreads, kSampleCtasPerSm)
     {
       float u[3], f[16];
       unit_pos(g, f3(q0), u);
-      encode_levels8(g, sres, u, 8 * (int)h, f);
+      encode_levels4(g, sres, u, 4 * (int)h, f);
       put8(A, r, 16 * (int)h, f);
       put8(A, r, 16 * (int)h + 8, f + 8);
       if (h == 0) {

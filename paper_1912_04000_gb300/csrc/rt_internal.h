@@ -305,10 +305,12 @@ int trace_blocks_per_sm(int block);
 int shadow_blocks_per_sm(int block);
 
 // Learned guide (rt_guide.cu).
+// Hash grid: kGuideLevels levels of kGuideFeatures features per entry.
+constexpr int kGuideLevels = 8, kGuideFeatures = 4;
 struct GuideDev {
-  const float* grid;      // [16][2^log2T][2] FP32
+  const float* grid;      // [kGuideLevels][2^log2T][kGuideFeatures] FP32
   uint32_t log2T;
-  uint32_t res[16];       // grid resolution per level
+  uint32_t res[kGuideLevels];  // grid resolution per level
   uint32_t dense_mask;    // bit l: level l indexed densely
   float lo[3], inv_ext[3];
 };

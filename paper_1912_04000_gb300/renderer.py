@@ -356,7 +356,7 @@ class Renderer:
         g = None if grid is None else np.ascontiguousarray(grid, np.float32).ravel()
         w = None if W is None else np.ascontiguousarray(W, np.float32).ravel()
         if hasattr(self, "guide_log2_table"):  # before guide_init the library refuses the call
-            n_grid = 16 * (1 << self.guide_log2_table) * 2
+            n_grid = _native.GUIDE_GRID_LEVELS * (1 << self.guide_log2_table) * _native.GUIDE_GRID_FEATURES
             _need(g is None or g.size == n_grid, f"grid: expected {n_grid} floats")
         _need(w is None or w.size == _native.GUIDE_W_SIZE, f"W: expected {_native.GUIDE_W_SIZE} floats")
         st = self.lib.rt_guide_set_params(self._h, None if g is None else g.ctypes.data,
@@ -364,7 +364,7 @@ class Renderer:
         self._check("rt_guide_set_params", st)
 
     def guide_get_params(self):
-        g = np.zeros(16 * (1 << self.guide_log2_table) * 2, np.float32)
+        g = np.zeros(_native.GUIDE_GRID_LEVELS * (1 << self.guide_log2_table) * _native.GUIDE_GRID_FEATURES, np.float32)
         w = np.zeros(_native.GUIDE_W_SIZE, np.float32)
         self._check("rt_guide_get_params", self.lib.rt_guide_get_params(self._h, g.ctypes.data, w.ctypes.data))
         return g, w
@@ -392,7 +392,8 @@ class Renderer:
         torch = self.torch
         r = self._records(rec)
         loss = C.c_float()
-        dg = torch.empty(16 * (1 << self.guide_log2_table) * 2, dtype=torch.float32, device=self.device)
+        dg = torch.empty(_native.GUIDE_GRID_LEVELS * (1 << self.guide_log2_table) * _native.GUIDE_GRID_FEATURES,
+                         dtype=torch.float32, device=self.device)
         dw = torch.empty(_native.GUIDE_W_SIZE, dtype=torch.float32, device=self.device)
         st = self.lib.rt_guide_grad(self._h, r.data_ptr(), r.shape[0], C.byref(loss), dg.data_ptr(), dw.data_ptr())
         self._check("rt_guide_grad", st)

@@ -47,7 +47,7 @@ def _records(rng, lo, hi, n, concentrated=False):
 
 
 def _params(rng):
-    grid = (rng.normal(size=16 * (1 << LOG2_T) * 2) * 0.5).astype(np.float32)
+    grid = (rng.normal(size=oracle.GUIDE_LEVELS * (1 << LOG2_T) * oracle.GUIDE_FEATURES) * 0.5).astype(np.float32)
     W = bf16(rng.normal(size=oracle.GUIDE_W_SIZE) * 0.2)
     return grid, W
 
@@ -112,34 +112,41 @@ def test_training_reduces_loss(setup):
 
 
 def test_adam_step_matches_oracle(setup):
-    """One training step on the GPU against the oracle's Adam step applied to
-    the oracle's gradient: at the first step a parameter with gradient g
-    moves by lr g / (|g| + eps), lr sign(g) unless g is tiny, and one with
-    g = 0 does not move (grid entries no record touches)."""
+    """One training step on the GPU against the oracle's Adam step: applied
+    to the GPU's own gradient of the step, Adam must give the GPU's
+    parameters (at the first step a parameter with gradient g moves by
+    lr g / (|g| + eps)); applied to the oracle's FP64 gradient, the entries
+    above 1% of the largest move as on the GPU (the BF16 network's gradient
+    may flip the sign of an entry close to 0, a difference the gradient test
+    bounds), and grid entries no record touches do not move."""
     R, lo, hi = setup
     rng = np.random.default_rng(8)
     grid, W = _params(rng)
     R.guide_init(seed=1, log2_table=LOG2_T, lr_grid=1e-2, lr_mlp=1e-3)
     R.guide_set_params(grid, W)  # also resets the Adam state
     rec = _records(rng, lo, hi, 777)
+    _, dg, dw = R.guide_grad(rec)  # the step's gradient (the weights' is the same on every call)
+    dg, dw = dg.cpu().numpy().astype(np.float64), dw.cpu().numpy().astype(np.float64)
     R.guide_train_step(rec)
     grid1, W1 = R.guide_get_params()
     pos, nrm, grp, om = _oracle_args(rec, lo, hi)
     _, dWo, dgo = oracle.guide_loss_grad(LOG2_T, lo, hi, grid, W, pos, nrm, grp, om, rec[:, 3], bf16_act=True)
-    for p0, p1, go, lr, what in ((grid, grid1, dgo, 1e-2, "grid"), (W, W1, dWo, 1e-3, "W")):
+    for p0, p1, g, go, lr, what in ((grid, grid1, dg, dgo, 1e-2, "grid"), (W, W1, dw, dWo, 1e-3, "W")):
+        # Adam: the oracle's step on the GPU's gradient, to float rounding
         want = p0.astype(np.float64)
-        oracle.adam_step(want, go, np.zeros_like(want), np.zeros_like(want), 1, lr)
-        # the BF16 network's gradient may flip the sign of an entry close to 0:
-        # entries above 1% of the largest all move as the oracle's, those
-        # above 0.1% nearly all (measured: 6 of 72,672 grid entries flip)
+        oracle.adam_step(want, g, np.zeros_like(want), np.zeros_like(want), 1, lr)
+        ok = np.abs(p1 - want) <= 1e-6
+        # the grid gradient is summed with float atomics in any order, so an
+        # entry near 0 can change sign between the two evaluations
+        assert np.mean(ok) >= (0.9999 if what == "grid" else 1.0), (what, np.mean(ok))
+        # the gradient: large entries as the oracle's
+        want_o = p0.astype(np.float64)
+        oracle.adam_step(want_o, go, np.zeros_like(want_o), np.zeros_like(want_o), 1, lr)
         big = np.abs(go) > 1e-2 * np.abs(go).max()
-        strong = np.abs(go) > 1e-3 * np.abs(go).max()
         assert big.sum() > 100
-        # FP32 parameters: the update of size lr, rounded to float
-        np.testing.assert_allclose(p1[big], want[big], rtol=0, atol=1e-6, err_msg=what)
-        assert np.mean(np.abs(p1[strong] - want[strong]) <= 1e-6) > 0.999, what
+        np.testing.assert_allclose(p1[big], want_o[big], rtol=0, atol=1e-6, err_msg=what)
+        moved = np.abs(p1.astype(np.float64) - p0) > 0.5 * lr
+        assert moved[big].all(), what
         zero = go == 0.0
         if zero.any():
             assert np.mean(p1[zero] == p0[zero]) > 0.9999, what
-        moved = np.abs(p1.astype(np.float64) - p0) > 0.5 * lr
-        assert np.mean(moved[strong]) == 1.0, what

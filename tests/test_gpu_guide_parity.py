@@ -37,7 +37,7 @@ def bf16(a):
 
 def _params(seed):
     rng = np.random.default_rng(seed)
-    grid = (rng.normal(size=16 * (1 << LOG2_T) * 2) * 0.5).astype(np.float32)
+    grid = (rng.normal(size=oracle.GUIDE_LEVELS * (1 << LOG2_T) * oracle.GUIDE_FEATURES) * 0.5).astype(np.float32)
     W = bf16(rng.normal(size=oracle.GUIDE_W_SIZE) * 0.2)
     return grid, W
 
@@ -55,7 +55,7 @@ def _passthrough_params(seed):
     term, so FP32 and FP64 accumulation agree exactly.  The grid (random,
     seeded) does not reach the outputs."""
     rng = np.random.default_rng(seed)
-    grid = (rng.normal(size=16 * (1 << LOG2_T) * 2) * 0.6).astype(np.float32)
+    grid = (rng.normal(size=oracle.GUIDE_LEVELS * (1 << LOG2_T) * oracle.GUIDE_FEATURES) * 0.6).astype(np.float32)
     scales = [1.0, 2.0, 0.5, -1.0, -2.0, -0.5, 4.0]
     W1 = np.zeros((64, 64), np.float32)
     for t in range(24):
@@ -167,10 +167,15 @@ def test_sample_step_matches_oracle(R, passthrough):
     # cosine draws do not depend on the network: equal to float rounding
     assert np.all(ang[cos_draw] < 1e-5)
     # random network: most queries agree to FP32 rounding; where a BF16
-    # rounding of an activation flips, outputs move by about a BF16 ulp.
-    # Pass-through network: all agree but for the rare BF16 input flips.
+    # rounding of an activation flips, outputs move by about a BF16 ulp
+    # (2^-8 relative), which can carry a lobe weight past a uniform more
+    # than 1e-3 from a boundary: another lobe, rarely.  Pass-through
+    # network: all agree but for the rare BF16 input flips, never another
+    # lobe.
     exact = 0.995 if passthrough else 0.75
-    assert np.mean(ang < 1e-5) > exact and ang.max() < 0.1
+    far = ang > 0.1
+    print("other lobe:", int(far.sum()), "of", far.size)
+    assert np.mean(ang < 1e-5) > exact and np.mean(far) <= (0.0 if passthrough else 2e-3)
     assert np.mean(rel_pdf < 1e-4) > exact and np.quantile(rel_pdf, 0.999) < 0.1
     dcos = np.abs(gpu["cos"][keep] - o["cos"][keep])
     assert np.mean(dcos < 1e-5) > exact and dcos.max() < 0.1

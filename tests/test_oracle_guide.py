@@ -1,8 +1,10 @@
 """Oracle of the learned guide pinned to mathematics: the vMF mixture is a
 density on the sphere (quadrature), the analytic loss gradient equals
 central finite differences for every parameter kind, the hash-grid encoding
-interpolates (a constant grid gives constant features; dense levels hit
-their vertices exactly), and the SH inputs are an orthonormal basis."""
+interpolates (a constant grid gives constant features; a position on a
+vertex of a dense level reads that vertex's entry, feature by feature), the
+level resolutions follow their closed form, and the SH inputs are an
+orthonormal basis."""
 import math
 
 import numpy as np
@@ -39,7 +41,7 @@ def _setup(seed, n=12, log2_T=10):
     lo = np.array([0.0, 0.0, 0.0], np.float32)
     hi = np.array([80.0, 25.0, 20.0], np.float32)
     T = 1 << log2_T
-    grid = (rng.normal(size=16 * T * 2) * 0.3).astype(np.float32)
+    grid = (rng.normal(size=oracle.GUIDE_LEVELS * T * oracle.GUIDE_FEATURES) * 0.3).astype(np.float32)
     W = (rng.normal(size=oracle.GUIDE_W_SIZE) * 0.25).astype(np.float32)
     pos = (lo + (hi - lo) * rng.random((n, 3))).astype(np.float32)
     nrm = rng.normal(size=(n, 3))
@@ -105,19 +107,46 @@ def test_loss_is_weighted_negative_log_likelihood():
 
 def test_encoding_interpolates():
     log2_T, lo, hi, grid, W, pos, nrm, group, om, wt = _setup(6, n=50)
-    const = np.full_like(grid, 0.0)
-    const[0::2] = 0.25
-    const[1::2] = -0.5
+    F = oracle.GUIDE_FEATURES
+    feat = np.array([0.25, -0.5, 1.0, -2.0], np.float32)
+    const = np.tile(feat, grid.size // F)  # entry (l, i) holds the four values
     X, _, _ = oracle.guide_forward(log2_T, lo, hi, const, W, pos, nrm, group, om)
-    np.testing.assert_allclose(X[:, 0:32:2], 0.25, atol=1e-12)
-    np.testing.assert_allclose(X[:, 1:32:2], -0.5, atol=1e-12)
+    for q in range(F):
+        np.testing.assert_allclose(X[:, q:32:F], feat[q], atol=1e-12)
     # one-hot group and zero padding
     np.testing.assert_array_equal(X[np.arange(50), 48 + group], 1.0)
     assert X[:, 48:64].sum() == 50
-    # level 0 is dense (17^3 <= 2^10 is false; use res 16 -> 17^3 = 4913 > 1024: hashed) --
-    # the resolution table follows n_min * b^l with b = (n_max / n_min)^(1 / 15)
+
+
+def test_level_resolutions_closed_form():
+    # n_min b^l with b = (n_max / n_min)^(1 / 7): 16 to 2048 doubles per level
     res = oracle.guide_resolutions(16.0, 2048.0)
-    assert res[0] == 16 and res[-1] == 2048 and (np.diff(res.astype(int)) > 0).all()
+    np.testing.assert_array_equal(res, 16 * 2 ** np.arange(8))
+    res = oracle.guide_resolutions(10.0, 1000.0)  # b = 100^(1/7)
+    np.testing.assert_array_equal(res, np.floor(10.0 * 100.0 ** (np.arange(8) / 7) * (1 + 1e-12)))
+
+
+def test_dense_vertices_read_their_entries():
+    """Positions on vertices (i, j, k) / 16 of the unit box: levels 0 and 1
+    (resolutions 16 and 32, (r + 1)^3 <= 2^16 entries, dense index x + y (r + 1)
+    + z (r + 1)^2) read exactly the vertex entry, its four features in order,
+    from the level's block of the table."""
+    log2_T = 16
+    T = 1 << log2_T
+    F = oracle.GUIDE_FEATURES
+    rng = np.random.default_rng(8)
+    grid = rng.normal(size=oracle.GUIDE_LEVELS * T * F).astype(np.float32)
+    W = np.zeros(oracle.GUIDE_W_SIZE, np.float32)
+    ijk = rng.integers(0, 16, size=(40, 3))  # each position the near corner of its cell
+    pos = (ijk / 16.0).astype(np.float32)
+    n = len(pos)
+    nrm = np.tile(np.array([[0.0, 0.0, 1.0]], np.float32), (n, 1))
+    X, _, _ = oracle.guide_forward(log2_T, [0, 0, 0], [1, 1, 1], grid, W, pos, nrm, np.zeros(n, np.uint32), nrm)
+    g = grid.reshape(oracle.GUIDE_LEVELS, T, F)
+    for level, r in ((0, 16), (1, 32)):
+        c = ijk * (r // 16)
+        idx = c[:, 0] + c[:, 1] * (r + 1) + c[:, 2] * (r + 1) ** 2
+        np.testing.assert_array_equal(X[:, F * level:F * level + F], g[level, idx].astype(np.float64))
 
 
 def test_sh_inputs_orthonormal():
@@ -125,7 +154,8 @@ def test_sh_inputs_orthonormal():
     om, w = _sphere_quadrature(60, 120)
     n = om.shape[0]
     zeros = np.zeros((n, 3), np.float32)
-    X, _, _ = oracle.guide_forward(10, [0, 0, 0], [1, 1, 1], np.zeros(16 * 1024 * 2, np.float32),
+    X, _, _ = oracle.guide_forward(10, [0, 0, 0], [1, 1, 1],
+                                   np.zeros(oracle.GUIDE_LEVELS * 1024 * oracle.GUIDE_FEATURES, np.float32),
                                    np.zeros(oracle.GUIDE_W_SIZE, np.float32), zeros, om.astype(np.float32),
                                    np.zeros(n, np.uint32), om.astype(np.float32))
     S = X[:, 32:48]

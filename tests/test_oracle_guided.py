@@ -25,7 +25,7 @@ def bf16(a):
 def guide_for(scene, seed=0, grid_scale=0.5, w_scale=0.2, bf16_act=True):
     """A seeded random network (BF16 weights) over the scene's bounds."""
     rng = np.random.default_rng(seed)
-    grid = (rng.normal(size=16 * (1 << LOG2_T) * 2) * grid_scale).astype(np.float32)
+    grid = (rng.normal(size=oracle.GUIDE_LEVELS * (1 << LOG2_T) * oracle.GUIDE_FEATURES) * grid_scale).astype(np.float32)
     W = bf16(rng.normal(size=oracle.GUIDE_W_SIZE) * w_scale)
     lo = scene.verts.min(0).astype(np.float32)
     hi = scene.verts.max(0).astype(np.float32)
