@@ -176,8 +176,12 @@ def test_sample_step_matches_oracle(R, passthrough):
     far = ang > 0.1
     print("other lobe:", int(far.sum()), "of", far.size)
     assert np.mean(ang < 1e-5) > exact and np.mean(far) <= (0.0 if passthrough else 2e-3)
+    # the values of the same draw: queries that took another lobe left out
+    rel_pdf = rel_pdf[~far]
+    rel_T = rel_T[~far[both]]
+    d_esc = d_esc[~far[both][inside]]
     assert np.mean(rel_pdf < 1e-4) > exact and np.quantile(rel_pdf, 0.999) < 0.1
-    dcos = np.abs(gpu["cos"][keep] - o["cos"][keep])
+    dcos = np.abs(gpu["cos"][keep] - o["cos"][keep])[~far]
     assert np.mean(dcos < 1e-5) > exact and dcos.max() < 0.1
     assert agree.mean() > 0.999
     assert np.mean(rel_T < 1e-4) > exact and np.quantile(rel_T, 0.999) < 0.1
@@ -186,7 +190,7 @@ def test_sample_step_matches_oracle(R, passthrough):
     assert np.all(gpu["nee_contrib"][(has_sun == 0)] == 0)
     # escape weights: zero outside the cone, p_mix / (p_mix + p_cone) inside
     assert np.mean((ew > 0) == (ow > 0)) > 0.999
-    if inside.any():
+    if d_esc.size:
         assert np.mean(d_esc < 1e-4) > max(exact, 0.9) and d_esc.max() < 0.1
 
 
