@@ -169,10 +169,12 @@ def test_sample_step_matches_oracle(R, passthrough):
     # random network: most queries agree to FP32 rounding; where a BF16
     # rounding of an activation flips, outputs move by about a BF16 ulp
     # (2^-8 relative), which can carry a lobe weight past a uniform more
-    # than 1e-3 from a boundary: another lobe, rarely.  Pass-through
-    # network: all agree but for the rare BF16 input flips, never another
-    # lobe.
+    # than 1e-3 from a boundary (another lobe, rarely) and, for a sharp
+    # lobe, move its density at the drawn direction by tens of percent (a
+    # few queries in a thousand).  Pass-through network: all agree but for
+    # the rare BF16 input flips, never another lobe.
     exact = 0.995 if passthrough else 0.75
+    tail = 1e-3 if passthrough else 1e-2  # share of queries allowed beyond 0.1
     far = ang > 0.1
     print("other lobe:", int(far.sum()), "of", far.size)
     assert np.mean(ang < 1e-5) > exact and np.mean(far) <= (0.0 if passthrough else 2e-3)
@@ -180,11 +182,11 @@ def test_sample_step_matches_oracle(R, passthrough):
     rel_pdf = rel_pdf[~far]
     rel_T = rel_T[~far[both]]
     d_esc = d_esc[~far[both][inside]]
-    assert np.mean(rel_pdf < 1e-4) > exact and np.quantile(rel_pdf, 0.999) < 0.1
+    assert np.mean(rel_pdf < 1e-4) > exact and np.mean(rel_pdf > 0.1) <= tail
     dcos = np.abs(gpu["cos"][keep] - o["cos"][keep])[~far]
     assert np.mean(dcos < 1e-5) > exact and dcos.max() < 0.1
     assert agree.mean() > 0.999
-    assert np.mean(rel_T < 1e-4) > exact and np.quantile(rel_T, 0.999) < 0.1
+    assert np.mean(rel_T < 1e-4) > exact and np.mean(rel_T > 0.1) <= tail
     assert np.all(gpu["throughput"][keep][~gpu["continued"][keep]] == 0)
     assert np.mean(rel_nee < 1e-4) > max(exact, 0.9) and np.quantile(rel_nee, 0.999) < 0.1
     assert np.all(gpu["nee_contrib"][(has_sun == 0)] == 0)
