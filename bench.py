@@ -180,7 +180,7 @@ def oracle_guide_for(wl, seed=0, log2_table=19):
 
     import oracle
     rng = np.random.default_rng(seed)
-    grid = (rng.normal(size=16 * (1 << log2_table) * 2) * 1e-2).astype(np.float32)
+    grid = (rng.normal(size=oracle.GUIDE_LEVELS * (1 << log2_table) * oracle.GUIDE_FEATURES) * 1e-2).astype(np.float32)
     W = (rng.normal(size=oracle.GUIDE_W_SIZE) * 0.2).astype(np.float32)
     lo = wl.scene.verts.min(0).astype(np.float32)
     hi = wl.scene.verts.max(0).astype(np.float32)
